@@ -1,0 +1,206 @@
+"""Oracle pins for the synthetic potentials: forces are minus the energy gradient (finite differences),
+closed forms for two- and three-atom geometries, periodic lattice sums, and extensivity under replication."""
+import numpy as np
+import pytest
+
+import oracle.oracle as O
+from paper_2606_02455_b300 import workloads as W
+
+
+def _fd_forces(system, pot, q, h=1e-4):
+    F = np.zeros_like(q)
+    for i in range(q.shape[0]):
+        for a in range(3):
+            qp = q.copy(); qp[i, a] += h
+            qm = q.copy(); qm[i, a] -= h
+            F[i, a] = -(O.energy(system, pot, qp) - O.energy(system, pot, qm)) / (2 * h)
+    return F
+
+
+def _pot(system, n_rbf=16, n_ang=0, n_layers=2, width=16, head="tanh", rc=5.0, lj=True, seed=1, scale=1.0):
+    ns = system.n_species
+    d0 = W.input_dim(ns, n_rbf, n_ang)
+    w = W.mlp_weights(d0, n_layers, width, seed) * scale if n_layers else None
+    kw = dict(lj_eps=np.array([0.0104, 0.0067, 0.005][:ns]), lj_sigma=np.array([3.0, 2.8, 2.0][:ns]),
+              lj_cutoff=4.9) if lj else {}
+    return W.Potential(**kw, n_rbf=n_rbf, n_ang=n_ang, n_layers=n_layers, width=width, desc_cutoff=rc, head=head,
+                       head_scale=0.05 if head == "tanh" else 1.0, weights=w)
+
+
+CASES = [
+    dict(n_rbf=16, n_ang=0, n_layers=2, head="tanh"),
+    dict(n_rbf=8, n_ang=16, n_layers=1, head="linear"),
+    dict(n_rbf=6, n_ang=16, n_layers=3, head="tanh", scale=3.0),
+    dict(n_rbf=0, n_ang=0, n_layers=0, head="tanh"),   # pure LJ
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_forces_are_minus_energy_gradient(case):
+    """T1: analytic forces equal the central finite difference of the energy (h = 1e-4 A)."""
+    s = W.small_system(n_cells=1, a=5.0, n_species=2, seed=3, L=10.0)
+    pot = _pot(s, **case)
+    q = s.positions + np.array([0.3, 0.1, -0.2])
+    F = O.forces(s, pot, q)
+    Ffd = _fd_forces(s, pot, q)
+    err = np.linalg.norm(F - Ffd) / np.linalg.norm(Ffd)
+    assert err < 1e-6, err
+
+
+def test_forces_fd_with_multiple_images():
+    """T1 with a cutoff larger than half the box (atoms see several images of the same neighbour)."""
+    s = W.small_system(n_cells=1, a=5.0, n_species=1, seed=4, L=7.0)
+    pot = W.Potential(lj_eps=np.array([0.0104]), lj_sigma=np.array([3.4]), lj_cutoff=6.5, n_rbf=8, n_ang=16,
+                      n_layers=1, width=8, desc_cutoff=4.0, head="tanh", head_scale=0.05,
+                      weights=W.mlp_weights(W.input_dim(1, 8, 16), 1, 8, 5))
+    q = s.positions.copy()
+    F = O.forces(s, pot, q)
+    Ffd = _fd_forces(s, pot, q)
+    assert np.linalg.norm(F - Ffd) / np.linalg.norm(Ffd) < 1e-6
+
+
+def _lj(eps, sig, rc, r):
+    return 4 * eps * ((sig / r) ** 12 - (sig / r) ** 6) - 4 * eps * ((sig / rc) ** 12 - (sig / rc) ** 6)
+
+
+def test_two_atom_lj_closed_form():
+    """Two atoms in a large box: E = U(r) - U(rc) and |F| = dU/dr along the bond."""
+    r = 3.7
+    s = W.System(positions=np.array([[5.0, 5.0, 5.0], [5.0 + r, 5.0, 5.0]]), momenta=np.zeros((2, 3)),
+                 species=np.array([0, 1], dtype=np.int32), masses=np.array([12.0, 16.0]), box=np.array([30.0] * 3))
+    pot = W.Potential(lj_eps=np.array([0.01, 0.004]), lj_sigma=np.array([3.0, 3.4]), lj_cutoff=8.0)
+    eps, sig = np.sqrt(0.01 * 0.004), 0.5 * (3.0 + 3.4)
+    res = O.energy_forces(s, pot, s.positions)
+    assert res["E"] == pytest.approx(_lj(eps, sig, 8.0, r), rel=1e-13)
+    dU = -24 * eps / r * (2 * (sig / r) ** 12 - (sig / r) ** 6)
+    assert res["F"][0, 0] == pytest.approx(dU, rel=1e-12)      # atom 0 is pushed/pulled along +x by dU/dr
+    assert res["F"][1, 0] == pytest.approx(-dU, rel=1e-12)
+    assert np.allclose(res["F"][:, 1:], 0.0)
+
+
+def test_single_atom_lattice_sum():
+    """One atom in a periodic cubic box of side 6 A with cutoff 8.5 A interacts with its own images:
+    6 at distance L and 12 at L*sqrt(2) (L*sqrt(3) is beyond the cutoff), each pair counted half."""
+    L = 6.0
+    s = W.System(positions=np.array([[1.0, 2.0, 3.0]]), momenta=np.zeros((1, 3)), species=np.array([0], np.int32),
+                 masses=np.array([40.0]), box=np.array([L] * 3))
+    pot = W.Potential(lj_eps=np.array([0.0104]), lj_sigma=np.array([3.4]), lj_cutoff=8.5)
+    expect = 0.5 * (6 * _lj(0.0104, 3.4, 8.5, L) + 12 * _lj(0.0104, 3.4, 8.5, L * np.sqrt(2)))
+    res = O.energy_forces(s, pot, s.positions)
+    assert res["E"] == pytest.approx(expect, rel=1e-12)
+    assert np.allclose(res["F"], 0.0, atol=1e-14)
+    nb = O.neighbors(s, s.positions, 8.5)
+    assert len(nb[0]) == 18
+
+
+def test_radial_descriptor_two_atoms():
+    """Two atoms of different species at distance r: atom 0's radial block for species 1 is
+    exp(-(r-mu_k)^2/(2w^2)) * (cos(pi r/rc)+1)/2 with mu_k = k rc/(n-1), w = rc/(n-1); its species-0 block is 0."""
+    r, rc, n = 2.3, 5.0, 8
+    s = W.System(positions=np.array([[4.0, 4.0, 4.0], [4.0, 4.0 + r, 4.0]]), momenta=np.zeros((2, 3)),
+                 species=np.array([0, 1], dtype=np.int32), masses=np.array([12.0, 16.0]), box=np.array([20.0] * 3))
+    pot = W.Potential(n_rbf=n, n_ang=0, n_layers=1, width=4, desc_cutoff=rc, head="linear",
+                      weights=W.mlp_weights(W.input_dim(2, n, 0), 1, 4, 0))
+    X = O.energy_forces(s, pot, s.positions, want=("X",))["X"]
+    w = rc / (n - 1)
+    mu = np.arange(n) * w
+    g = np.exp(-(r - mu) ** 2 / (2 * w * w)) * 0.5 * (np.cos(np.pi * r / rc) + 1)
+    assert np.allclose(X[0, :n], 0.0)
+    assert np.allclose(X[0, n:2 * n], g, rtol=1e-14, atol=0)
+    assert np.array_equal(X[0, 2 * n:], [1.0, 0.0]) and np.array_equal(X[1, 2 * n:], [0.0, 1.0])
+
+
+@pytest.mark.parametrize("cos_theta", [-1.0, 0.0, 1.0])
+def test_angular_descriptor_special_angles(cos_theta):
+    """Centre atom with two neighbours at r1, r2: the 16 terms 2^(1-zeta)(1+lambda c)^zeta e^{-eta(r1^2+r2^2)} fc fc
+    reduce to 2*E for c=+-1 with matching lambda, 0 for the opposite lambda, and 2^(1-zeta)*E at c=0."""
+    r1, r2, rc = 2.0, 2.5, 5.0
+    u = np.array([1.0, 0.0, 0.0])
+    v = np.array([cos_theta, np.sqrt(max(0.0, 1 - cos_theta ** 2)), 0.0])
+    c0 = np.array([8.0, 8.0, 8.0])
+    pos = np.array([c0, c0 + r1 * u, c0 + r2 * v])
+    s = W.System(positions=pos, momenta=np.zeros((3, 3)), species=np.zeros(3, np.int32), masses=np.array([12.0]),
+                 box=np.array([40.0] * 3))
+    pot = W.Potential(n_rbf=2, n_ang=16, n_layers=1, width=4, desc_cutoff=rc, head="linear",
+                      weights=W.mlp_weights(W.input_dim(1, 2, 16), 1, 4, 0))
+    X = O.energy_forces(s, pot, pos, want=("X",))["X"]
+    ang = X[0, 2:18]
+    fc = lambda r: 0.5 * (np.cos(np.pi * r / rc) + 1)
+    k = 0
+    for zeta in (1, 2, 4, 8):
+        for lam in (1, -1):
+            for eta in (0.005, 0.05):
+                E = np.exp(-eta * (r1 * r1 + r2 * r2)) * fc(r1) * fc(r2)
+                if cos_theta == 0.0:
+                    expect = 2.0 ** (1 - zeta) * E
+                elif lam * cos_theta > 0:
+                    expect = 2.0 * E
+                else:
+                    expect = 0.0
+                assert ang[k] == pytest.approx(expect, rel=1e-12, abs=1e-15), (zeta, lam, eta)
+                k += 1
+
+
+def test_isolated_atom_mlp_head():
+    """An atom with no neighbours has descriptor = one-hot of its species; its energy is
+    0.05 tanh(MLP(onehot)), evaluated here with numpy matrix products of the same packed weights."""
+    s = W.System(positions=np.array([[1.0, 1.0, 1.0], [10.0, 10.0, 10.0]]), momenta=np.zeros((2, 3)),
+                 species=np.array([1, 0], np.int32), masses=np.array([12.0, 16.0]), box=np.array([20.0] * 3))
+    d0 = W.input_dim(2, 4, 16)
+    w = W.mlp_weights(d0, 2, 8, 9)
+    w[8 * d0:8 * d0 + 8] = 0.3   # non-zero first bias
+    pot = W.Potential(n_rbf=4, n_ang=16, n_layers=2, width=8, desc_cutoff=3.0, head="tanh", head_scale=0.05, weights=w)
+    Ea = O.energy_forces(s, pot, s.positions, want=("E_atom",))["E_atom"]
+    off = 0
+    W1 = w[off:off + 8 * d0].reshape(8, d0); off += 8 * d0
+    b1 = w[off:off + 8]; off += 8
+    W2 = w[off:off + 64].reshape(8, 8); off += 64
+    b2 = w[off:off + 8]; off += 8
+    wo = w[off:off + 8]; bo = w[off + 8]
+    silu = lambda z: z / (1 + np.exp(-z))
+    for i, sp in enumerate([1, 0]):
+        x = np.zeros(d0); x[d0 - 2 + sp] = 1.0
+        y = wo @ silu(W2 @ silu(W1 @ x + b1) + b2) + bo
+        assert Ea[i] == pytest.approx(0.05 * np.tanh(y), rel=1e-13)
+
+
+def test_energy_is_extensive_under_replication():
+    """A periodic system replicated 2x2x2 has 8x the energy and the same force on every copy of an atom
+    (pins image handling of LJ, radial and angular terms together)."""
+    s = W.small_system(n_cells=1, a=5.2, n_species=2, seed=8, L=5.2)
+    pot = _pot(s, n_rbf=8, n_ang=16, n_layers=2, width=8, rc=2.5)
+    pot.lj_cutoff = 4.5
+    r1 = O.energy_forces(s, pot, s.positions)
+    L = s.box[0]
+    shifts = np.stack(np.meshgrid(*[np.arange(2)] * 3, indexing="ij"), -1).reshape(-1, 3) * L
+    big_pos = np.concatenate([s.positions + sh for sh in shifts])
+    big = W.System(positions=big_pos, momenta=np.zeros_like(big_pos), species=np.tile(s.species, 8),
+                   masses=s.masses, box=s.box * 2)
+    r8 = O.energy_forces(big, pot, big_pos)
+    assert r8["E"] == pytest.approx(8 * r1["E"], rel=1e-11)
+    assert np.allclose(r8["F"].reshape(8, -1, 3), r1["F"][None], rtol=1e-9, atol=1e-12)
+
+
+def test_translation_invariance_and_unwrapped_positions():
+    """Energy and forces do not change under a global translation or when atoms are shifted by whole boxes."""
+    s = W.small_system(n_cells=1, a=5.0, n_species=2, seed=5, L=10.0)
+    pot = _pot(s, n_rbf=8, n_ang=16, n_layers=1, width=8)
+    r0 = O.energy_forces(s, pot, s.positions)
+    q1 = s.positions + np.array([0.123, -7.5, 3.3])
+    q1[0] += s.box * np.array([2, -1, 0])
+    r1 = O.energy_forces(s, pot, q1)
+    assert r1["E"] == pytest.approx(r0["E"], rel=1e-10)
+    assert np.allclose(r1["F"], r0["F"], rtol=1e-8, atol=1e-12)
+
+
+def test_neighbor_lists_symmetric_and_canonical():
+    """Every member (i -> j, s) has its reverse (j -> i, -s); lists are sorted by (j, shift code)."""
+    w = W.config2()
+    lists = O.neighbors(w.system, w.system.positions, 5.0)
+    pairs = set()
+    for i, keys in enumerate(lists):
+        assert np.all(np.diff(keys) > 0)
+        for k in keys:
+            pairs.add((i, int(k) >> 5, int(k) & 31))
+    for (i, j, c) in pairs:
+        assert (j, i, 26 - c) in pairs
