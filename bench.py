@@ -1,0 +1,405 @@
+"""Benchmark: target-distributed ns/day of LSD on one B300 against plain target Langevin, and acceptance rate.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config 2]
+
+A step is one LSD window: K drafted steps (persistent draft kernel), one batched target evaluation on all K*N
+atoms (neighbours, descriptors, MLP, adjoint), transport and commit; the window runs as one CUDA graph.
+`value` = committed steps x dt / device time, in ns/day, with the state resident in HBM.  L2 is flushed
+between timed windows.  `e2e` is the same metric through the public per-window C-ABI calls with the state
+copied host->device before and device->host after every window.  The plain-target baseline (the same
+kernels, one ABOBA step per graph launch) is timed the same way in the same process.  `roofline` is the
+dominant kernel, timed live with CUDA events on the library's stream.  `cpu_baseline` is the FP64 oracle on a
+bounded sample of the same workload on the host.
+
+Multi-GPU: the method does not shard on one node here (replicas only): with torchrun each rank runs an
+independent replica and `value` sums them over the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "target-distributed ns/day vs plain target Langevin on 1 B300; acceptance rate"
+NS_PER_DAY = 86400.0 * 1e-6   # steps * dt[fs] / seconds -> ns/day
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0}, \
+            "fallback"
+
+
+def _workload(cfg):
+    from paper_2606_02455_b300 import workloads as W
+    return W.CONFIGS[cfg]()
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------------------------------------------------------
+# roofline of the dominant kernel
+# ------------------------------------------------------------------------------------------------------------------
+
+def _algorithmic_work(w, phase):
+    """Algorithmic work of one launch of a phase, with its bound: (amount, unit, bound).
+
+    MLP: 2 FLOP per multiply-add of the forward chain plus the input-gradient chain (no weight gradient):
+         2 * M * sum(d_in*d_out) * 2.
+    Other phases: bytes that must cross HBM once per window (inputs read + outputs written)."""
+    s, t, K = w.system, w.target, w.integ.K
+    N = s.n_atoms
+    M = K * N
+    if phase == "mlp":
+        d0p = ((s.n_species * t.n_rbf + t.n_ang + s.n_species) + 31) // 32 * 32
+        macs = d0p * t.width + (t.n_layers - 1) * t.width * t.width + t.width
+        return 2.0 * 2.0 * M * macs, "FLOP", "alu"
+    if phase in ("transport_reduce",):
+        return M * 3 * (4 + 4), "B", "hbm"
+    if phase in ("transport_commit",):
+        return N * 3 * (8 + 8 + 4 + 4 + 8 + 8 + 8), "B", "hbm"
+    return None
+
+
+def roofline(h, w, peaks, peak_kind, n_rep=20):
+    """Per-phase CUDA-event times of the window (live, on the library's stream), the dominant phase, and its
+    achieved rate against the peak that bounds it."""
+    import torch
+    phases = None
+    for _ in range(3):
+        h.profile_window()
+    acc = {}
+    for _ in range(n_rep):
+        ph = h.profile_window()
+        for k, v in ph.items():
+            acc[k] = acc.get(k, 0.0) + v / n_rep
+    phases = acc
+    dom = max(phases, key=lambda k: phases[k])
+    share = phases[dom] / sum(phases.values())
+    work = _algorithmic_work(w, dom)
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s: 148 SMs x 128 FP32 lanes x FMA
+    out = {"kernel": dom, "share": round(share, 3), "ms": round(phases[dom], 5),
+           "phases_ms": {k: round(v, 5) for k, v in phases.items()}}
+    if work is None:
+        # ALU-bound descriptor/adjoint kernels: report FP32 issue-rate bound against the FP32 peak
+        out.update({"bound": "alu", "achieved": None, "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": None,
+                    "traffic": None, "note": "no algorithmic FLOP model for this phase"})
+        return out
+    amount, unit, bound = work
+    sec = phases[dom] * 1e-3
+    if bound == "alu":
+        ach = amount / sec / 1e12
+        out.update({"bound": "alu", "achieved": round(ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+                    "frac": round(ach / fp32_peak, 4), "traffic": None,
+                    "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz" % sm_max})
+    else:
+        ach = amount / sec / 1e9
+        pk = peaks["hbm_gbs"]
+        out.update({"bound": "hbm", "achieved": round(ach, 1), "peak": pk, "unit": "GB/s", "frac": round(ach / pk, 4),
+                    "traffic": None, "peak_source": peak_kind})
+    return out
+
+
+# ------------------------------------------------------------------------------------------------------------------
+# our implementation
+# ------------------------------------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    from paper_2606_02455_b300 import lsd
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    w = _workload(args.config)
+    s = w.system
+    s.seed = s.seed + rank            # independent replicas
+    K = w.integ.K
+    peaks, peak_kind = _peaks()
+    h = lsd.LSD(s, w.draft, w.target, w.integ)
+    stream = torch.cuda.Stream()
+    h.set_stream(stream)
+    # equilibrate with plain target dynamics, then warm up both graphs
+    h.plain_step(args.equil)
+    q_eq, p_eq, step_eq = h.get_state()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.add_(1.0)
+
+    for _ in range(args.warmup):
+        h.step(K)
+        h.plain_step(1)
+    h.set_state(q_eq, p_eq, step_eq)
+    st0 = h.stats()
+
+    clocks = Clocks(local)
+    clocks.start()
+    # ---- LSD: `steps` windows, each one graph launch bracketed by events, L2 flushed in between ----
+    _barrier(world)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush_l2()
+        ev[k][0].record(stream)
+        h.enqueue_windows(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    _barrier(world)
+    t_lsd = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
+    st1 = h.stats()
+    committed = st1["committed"] - st0["committed"]
+    rejected = st1["rejected"] - st0["rejected"]
+    windows = st1["windows"] - st0["windows"]
+    # ---- plain target Langevin: the same number of steps as committed, one graph launch per step ----
+    h.set_state(q_eq, p_eq, step_eq)
+    n_plain = max(committed, 16)
+    evp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_plain)]
+    torch.cuda.synchronize()
+    for k in range(n_plain):
+        flush_l2()
+        evp[k][0].record(stream)
+        h.enqueue_plain(1)
+        evp[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_plain = sum(a.elapsed_time(b) for a, b in evp) * 1e-3
+    clk = clocks.stop()
+
+    t_lsd_max = _max_over_ranks(t_lsd, world)
+    committed_all = _sum_over_ranks(committed, world)
+    value = committed_all * w.integ.dt * NS_PER_DAY / t_lsd_max
+    plain_value = _sum_over_ranks(n_plain, world) * w.integ.dt * NS_PER_DAY / _max_over_ranks(t_plain, world)
+
+    # ---- e2e: public per-window calls with host buffers ----
+    h.set_state(q_eq, p_eq, step_eq)
+    pos = np.ascontiguousarray(q_eq.copy())
+    mom = np.ascontiguousarray(p_eq.copy())
+    n_e2e = args.steps
+    stats_a = h.stats()
+    step = step_eq
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        h.set_state(pos, mom, step)
+        h.draft_window()
+        nc, _ = h.verify_window()
+        pos, mom, step = h.get_state(pos, mom)
+    t_e2e = time.perf_counter() - t0
+    stats_b = h.stats()
+    e2e_committed = stats_b["committed"] - stats_a["committed"]
+    e2e_val = _sum_over_ranks(e2e_committed, world) * w.integ.dt * NS_PER_DAY / _max_over_ranks(t_e2e, world)
+    D = 3 * s.n_atoms
+
+    rl = roofline(h, w, peaks, peak_kind)
+    launches_per_window = 8
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "ns/day", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_lsd_max * 1e3 / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "dtype_detail": "FP32 forces, descriptors and MLP; FP64 integrator state, z.delta, delta.delta and log ratio",
+        "data": "synthetic",
+        "config": {"workload": w.name, "n_atoms": s.n_atoms, "K": K, "dt_fs": w.integ.dt, "T_K": w.integ.temperature,
+                   "gamma_per_fs": w.integ.gamma, "target": "LJ + 0.05 eV tanh(MLP %d->%dx%d->1)" % (
+                       s.n_species * w.target.n_rbf + w.target.n_ang + s.n_species, w.target.width,
+                       w.target.n_layers),
+                   "draft": "LJ", "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed (256 MB write) between timed windows"},
+        "acceptance_rate": round(1.0 - rejected / max(committed, 1), 5),
+        "committed_per_window": round(committed / max(windows, 1), 3),
+        "plain_target_ns_per_day": round(plain_value, 3),
+        "speedup_vs_plain": round(value / plain_value, 3),
+        "plain_ms_per_step": round(t_plain * 1e3 / n_plain, 5),
+        "gpu_launches": int(windows * launches_per_window + n_plain * 7),
+        "e2e": {"value": round(e2e_val, 3), "unit": "ns/day", "h2d_bytes_per_step": 2 * D * 8 + 8,
+                "d2h_bytes_per_step": 2 * D * 8 + 8 + 8, "calls": "lsd_set_state, lsd_draft_window, "
+                                                                  "lsd_verify_window, lsd_get_state"},
+        "roofline": rl,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------------------------------
+# the oracle on the host (CPU baseline and the reference arm)
+# ------------------------------------------------------------------------------------------------------------------
+
+def cpu_baseline(w, seconds):
+    from oracle import oracle as O
+    s = w.system
+    K = w.integ.K
+    q, p, step = s.positions.copy(), s.momenta.copy(), 0
+    t0 = time.perf_counter()
+    committed = 0
+    windows = 0
+    while time.perf_counter() - t0 < seconds:
+        out = O.lsd_window(s, w.draft, w.target, w.integ, s.seed, step, K, q, p)
+        q, p = out["q"], out["p"]
+        step += out["n_committed"]
+        committed += out["n_committed"]
+        windows += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(committed * w.integ.dt * NS_PER_DAY / dt, 6), "unit": "ns/day", "cores": 1,
+            "kind": "oracle", "sample": "%d windows (%d committed steps) of %s, single-threaded FP64 C" % (
+                windows, committed, w.name)}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    w = _workload(args.config)
+    from oracle import oracle as O
+    O.build()
+    s = w.system
+    K = w.integ.K
+    q, p, step = s.positions.copy(), s.momenta.copy(), 0
+    for _ in range(max(1, min(args.warmup, 1))):
+        out = O.lsd_window(s, w.draft, w.target, w.integ, s.seed, step, K, q, p)
+    times, committed = [], 0
+    n = max(1, min(args.steps, args.ref_windows))
+    for _ in range(n):
+        t0 = time.perf_counter()
+        out = O.lsd_window(s, w.draft, w.target, w.integ, s.seed, step, K, q, p)
+        times.append(time.perf_counter() - t0)
+        q, p = out["q"], out["p"]
+        step += out["n_committed"]
+        committed += out["n_committed"]
+    tot = sum(times)
+    val = committed * w.integ.dt * NS_PER_DAY / tot
+    sample = "%d windows (%d committed steps) of %s, single-threaded FP64 C oracle" % (n, committed, w.name)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": "ns/day", "n_gpus": world,
+        "steps": n, "warmup": args.warmup, "ms_per_step": round(tot * 1e3 / n, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n_atoms": s.n_atoms, "K": K, "dt_fs": w.integ.dt},
+        "cpu_baseline": {"value": round(val, 6), "unit": "ns/day", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(val, 6), "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--equil", type=int, default=1000)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-windows", type=int, default=6)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

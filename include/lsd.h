@@ -1,0 +1,272 @@
+/*
+ * lsd.h -- C ABI of liblsd.so: Langevin Speculative Dynamics (LSD) window
+ * verification and Gaussian draft-to-target transport on one GPU.
+ *
+ * The method ("Speculative Sampling For Faster Molecular Dynamics"): a cheap
+ * draft force field proposes a window of K second-order Langevin steps; the
+ * target force field recomputes forces on every step of the window in one
+ * batched evaluation; a reflection-maximal coupling of the two momentum
+ * Gaussians (Eq. 5) then accepts each draft step or overrides it, and the
+ * draft is rolled back to the first overridden step (Alg. 1 with lookahead
+ * L = K; the per-step procedures are those of Alg. 2).  Committed states are
+ * exactly distributed as plain target Langevin dynamics (Thm 3.1, Thm D.2).
+ *
+ * Integrator: ABOBA (Eq. 2).  The configuration text calls the scheme
+ * "BAOAB"; the paper derives the coupling for ABOBA, where the force enters
+ * only the mean of the BOB momentum Gaussian (Eq. 4) and the final A is a
+ * shared invertible map (Thm 3.1).
+ *
+ * Units: Angstrom, fs, amu, eV; momentum in amu*Angstrom/fs.  A force F in
+ * eV/Angstrom changes momentum at rate kappa*F with kappa = (1 eV/A)/(1
+ * amu*A/fs^2) from CODATA 2018.
+ *
+ * Conventions for every entry point:
+ *  - Return value: LSD_OK (0) or a negative LSD_E* code; lsd_strerror() names
+ *    it.  No entry point aborts the process.
+ *  - Ownership: the library copies every input it is given; it allocates and
+ *    owns all device memory of a handle until lsd_destroy().  Output pointers
+ *    are caller-owned host buffers unless the name ends in _dev, in which case
+ *    they are device pointers on the handle's device.
+ *  - Streams: all work of a handle is issued on one CUDA stream (the handle's
+ *    own non-blocking stream unless lsd_set_stream() set another); calls that
+ *    return host data synchronise that stream.
+ *  - Threading: a handle is not thread-safe; distinct handles are independent.
+ *  - Layouts: positions, momenta and forces are [N][3] row-major (x, y, z per
+ *    atom); window arrays are [K][N][3].
+ */
+#ifndef LSD_H
+#define LSD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LSD_API __attribute__((visibility("default")))
+#else
+#define LSD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define LSD_OK 0
+#define LSD_EINVAL (-1)      /* invalid argument                                  */
+#define LSD_ENOMEM (-2)      /* device or host allocation failed                  */
+#define LSD_ECUDA (-3)       /* a CUDA runtime call failed                        */
+#define LSD_ETIMEOUT (-4)    /* a wait on the device exceeded its wall-clock limit */
+#define LSD_ENONFINITE (-5)  /* a force or log-ratio was NaN or infinite          */
+#define LSD_ESTATE (-6)      /* call out of order (verify without a draft, ...)   */
+#define LSD_EOVERFLOW (-7)   /* a neighbour list exceeded its capacity            */
+#define LSD_EUNSUPPORTED (-8) /* combination of options not built                 */
+
+/* ---- potentials ----------------------------------------------------------
+ * LSD_POT_LJ:      shifted Lennard-Jones over all periodic images within
+ *                  lj_cutoff, Lorentz-Berthelot mixing of per-species eps,
+ *                  sigma.
+ * LSD_POT_LJ_MLP:  LJ + sum_i head(MLP(x_i)), x_i = [radial G (n_species x
+ *                  n_rbf), angular G (n_ang), one-hot(species_i)], head =
+ *                  head_scale*tanh(y) (LSD_HEAD_TANH) or y (LSD_HEAD_LINEAR).
+ * LSD_POT_LEARNED: same form as LJ_MLP with a linear head; used as a draft
+ *                  whose weights lsd_train_draft() fits by force matching.
+ * Radial basis k of n_rbf: exp(-(r-mu_k)^2/(2w^2)) * (cos(pi r/rc)+1)/2 with
+ * mu_k = k rc/(n_rbf-1), w = rc/(n_rbf-1), summed per neighbour species.
+ * Angular term a of 16: 2^(1-zeta) (1 + lambda cos theta_ijk)^zeta
+ * exp(-eta (r_ij^2 + r_ik^2)) fc(r_ij) fc(r_ik) summed over unordered
+ * neighbour pairs, zeta in {1,2,4,8} (slowest index), lambda in {+1,-1},
+ * eta in {0.005, 0.05} A^-2 (fastest).
+ * MLP weights, packed float32: per hidden layer l: W_l [width][d_in]
+ * row-major then b_l [width]; then w_out [width], b_out [1];
+ * d_in = n_species*n_rbf + n_ang + n_species for the first layer.
+ * Neighbour membership (the same rule everywhere, so lists are exactly
+ * reproducible): positions are wrapped to 32-bit fixed point
+ * u = floor(q * 2^32/L) mod 2^32 per axis; a pair (i, j, image shift s in
+ * {-1,0,1}^3) has d = fl32(fl32(u_j - u_i + s 2^32) * fl32(L/2^32)) per
+ * axis and is a member iff ((dx*dx + dy*dy) + dz*dz) < fl32(rc^2) in
+ * binary32 without fused multiply-add; rc < L on every axis.
+ */
+#define LSD_POT_LJ 0
+#define LSD_POT_LJ_MLP 1
+#define LSD_POT_LEARNED 2
+
+#define LSD_HEAD_TANH 0
+#define LSD_HEAD_LINEAR 1
+
+#define LSD_FP32 0   /* MLP in FP32 (SIMT)                                  */
+#define LSD_BF16 1   /* MLP in BF16 with FP32 accumulation                  */
+#define LSD_FP8 2    /* MLP in FP8 e4m3, per-tensor scales, FP32 accumulate */
+
+typedef struct {
+    int32_t n_atoms;
+    int32_t n_species;
+    const double *pos;          /* [N][3] Angstrom; unwrapped positions are fine          */
+    const double *mom;          /* [N][3] amu*A/fs, or NULL: Maxwell-Boltzmann draw at T   */
+    const int32_t *species;     /* [N], values in [0, n_species)                            */
+    const double *species_mass; /* [n_species] amu, > 0                                     */
+    double box[3];              /* orthorhombic periodic box, Angstrom                      */
+    uint64_t seed;              /* key of the counter-based generator (Philox4x32-10)       */
+} lsd_system;
+
+typedef struct {
+    int32_t kind;               /* LSD_POT_*                                                */
+    int32_t precision;          /* LSD_FP32 | LSD_BF16 | LSD_FP8 (MLP arithmetic)           */
+    const double *lj_eps;       /* [n_species] eV                                           */
+    const double *lj_sigma;     /* [n_species] Angstrom                                     */
+    double lj_cutoff;           /* Angstrom; LJ term present when > 0                       */
+    int32_t n_rbf, n_ang, n_layers, width;
+    double desc_cutoff;         /* Angstrom                                                 */
+    int32_t head;               /* LSD_HEAD_*                                               */
+    double head_scale;          /* eV (0.05 for the synthetic targets)                      */
+    const float *weights;       /* packed MLP parameters (see above), copied by lsd_init    */
+    size_t n_weights;
+} lsd_potential;
+
+typedef struct {
+    int64_t windows;            /* windows run                                              */
+    int64_t committed;          /* steps committed                                          */
+    int64_t rejected;           /* committed steps that were reflected (at most 1 per window)*/
+    int64_t verified;           /* window steps verified (K per window)                     */
+    double sum_delta;           /* sum of |delta| (Mahalanobis, Eq. 6) over committed steps  */
+    double sum_pred_reject;     /* sum of erf(|delta|/sqrt 8) over committed steps (Eq. 6)   */
+    int64_t step;               /* index of the current state                               */
+} lsd_stats;
+
+typedef struct lsd_handle lsd_handle;
+
+/* lsd_init: builds a handle for the system and the two potentials, integrating
+ * with ABOBA at time step dt (fs), friction gamma (1/fs) and temperature T (K),
+ * window length K (1 <= K <= 128).  Derived constants (Eq. 4):
+ * c1 = exp(-gamma dt); per species sigma = sqrt(m kB T kappa (1 - exp(-2 gamma
+ * dt))).  Copies every input.  Errors: LSD_EINVAL (bad sizes, masses <= 0,
+ * cutoff >= box, weights of the wrong length), LSD_ENOMEM, LSD_ECUDA,
+ * LSD_EUNSUPPORTED. */
+LSD_API int lsd_init(const lsd_system *system, const lsd_potential *draft, const lsd_potential *target, double gamma,
+             double dt, double T, int32_t K, lsd_handle **out);
+
+/* lsd_draft_window: Alg. 2 draft_step repeated K times from the current state:
+ * q_mid = q + (dt/2) p/m; F~ = draft(q_mid); <p~> = c1 p + (1+c1)(dt/2) kappa F~
+ * (Eq. 4); p' = <p~> + sigma xi_n with xi_n keyed by the step index n; q' =
+ * q_mid + (dt/2) p'/m.  Asynchronous on the handle's stream. */
+LSD_API int lsd_draft_window(lsd_handle *h);
+
+/* lsd_verify_window: Alg. 2 verify_step on all K drafted steps at once (one
+ * batched target evaluation on K*N atoms), reflectionVerify (Eq. 5) on each,
+ * then the commit of Alg. 1: steps up to and including the first rejected one
+ * become the new trajectory, the state is rolled to the last committed one.
+ * n_committed (may be NULL) receives the number of committed steps,
+ * first_reject (may be NULL) the 1-based index of the first rejected step or
+ * -1.  Synchronises the stream.  LSD_ESTATE without a preceding draft. */
+LSD_API int lsd_verify_window(lsd_handle *h, int32_t *n_committed, int32_t *first_reject);
+
+/* lsd_step: runs windows (draft + verify + commit, captured as one CUDA graph)
+ * until n_steps more steps are committed; the final window commits only what
+ * is needed.  stats (may be NULL) receives the cumulative counters. */
+LSD_API int lsd_step(lsd_handle *h, int64_t n_steps, lsd_stats *stats);
+
+/* lsd_plain_step: n_steps of plain target-only ABOBA Langevin from the current
+ * state with the same noise keys (the baseline the metric compares against). */
+LSD_API int lsd_plain_step(lsd_handle *h, int64_t n_steps);
+
+/* lsd_enqueue_windows / lsd_enqueue_plain: enqueue n window graphs (or n
+ * plain target steps) on the handle's stream and return without waiting;
+ * windows run until the caller synchronises the stream (e.g. with CUDA events
+ * around each call).  No step cap applies.  Results are read with
+ * lsd_get_state / lsd_get_stats. */
+LSD_API int lsd_enqueue_windows(lsd_handle *h, int32_t n_windows);
+LSD_API int lsd_enqueue_plain(lsd_handle *h, int32_t n_steps);
+
+/* lsd_get_state / lsd_set_state: host copies of the current state [N][3]
+ * (pos, mom) and its step index.  Any pointer may be NULL. */
+LSD_API int lsd_get_state(const lsd_handle *h, double *pos, double *mom, int64_t *step);
+LSD_API int lsd_set_state(lsd_handle *h, const double *pos, const double *mom, int64_t step);
+
+/* lsd_get_stats: cumulative counters (see lsd_stats). */
+LSD_API int lsd_get_stats(const lsd_handle *h, lsd_stats *out);
+
+/* lsd_set_stream: issue all later work on this cudaStream_t (e.g. PyTorch's
+ * current stream); NULL restores the handle's own stream.  Rebuilds graphs. */
+LSD_API int lsd_set_stream(lsd_handle *h, void *cuda_stream);
+
+/* lsd_set_draft_weights: replace the draft MLP weights (packed float32, same
+ * shape as at init) between windows. */
+LSD_API int lsd_set_draft_weights(lsd_handle *h, const float *weights, size_t n_weights);
+
+/* lsd_get_draft_weights: copy the current draft weights (packed float32). */
+LSD_API int lsd_get_draft_weights(const lsd_handle *h, float *weights, size_t n_weights);
+
+/* lsd_set_error_correction: speculative error correction (Alg. 3) on (1) or
+ * off (0).  On: the draft mean uses F~ + dF, where dF = F - F~raw of the last
+ * committed step; switching on clears dF. */
+LSD_API int lsd_set_error_correction(lsd_handle *h, int32_t on);
+
+/* lsd_set_frame_capture: when on, every verified window step appends
+ * (q_mid_j, F_target_j) to a device ring buffer of `capacity` frames used by
+ * lsd_train_draft; capacity 0 turns capture off. */
+LSD_API int lsd_set_frame_capture(lsd_handle *h, int64_t capacity);
+LSD_API int lsd_frame_count(const lsd_handle *h, int64_t *n_frames);
+
+/* lsd_train_draft: n_iters Adam steps (learning rate lr) of force matching of a
+ * LSD_POT_LEARNED draft on the captured frames: loss = mean over frames and
+ * components of |F~ - F_target|^2, gradient by the double backward through
+ * the MLP and the descriptors.  loss_out (may be NULL) receives the loss of
+ * the last iteration.  frames_per_iter <= 0 uses all frames. */
+LSD_API int lsd_train_draft(lsd_handle *h, int32_t n_iters, float lr, int32_t frames_per_iter, float *loss_out);
+
+/* lsd_force_match_dev: loss and gradient (packed like the weights, float32) of
+ * the learned draft on n_frames given frames (device pointers, positions
+ * double [F][N][3], target forces float [F][N][3]); grad_dev may be NULL. */
+LSD_API int lsd_force_match_dev(lsd_handle *h, const double *frames_q_dev, const float *frames_F_dev, int32_t n_frames,
+                        float *loss_out, float *grad_dev);
+
+/* lsd_target_forces_dev / lsd_draft_forces_dev: forces (float [C][N][3]) and
+ * per-atom energies (float [C][N], may be NULL) of the target or draft
+ * potential on C configurations (double [C][N][3], device pointers).
+ * C <= K for the batched path. */
+LSD_API int lsd_target_forces_dev(lsd_handle *h, const double *q_dev, int32_t n_configs, float *F_dev, float *E_atom_dev);
+LSD_API int lsd_draft_forces_dev(lsd_handle *h, const double *q_dev, int32_t n_configs, float *F_dev, float *E_atom_dev);
+
+/* lsd_neighbors: the target's neighbour lists of configuration c of the last
+ * batched evaluation: keys (j << 5 | shift code, code = (sx+1)+3(sy+1)+9(sz+1))
+ * in canonical order for the descriptor cutoff and the LJ cutoff.  Row stride
+ * `cap`; counts [N].  Host buffers. */
+LSD_API int lsd_neighbors(const lsd_handle *h, int32_t config, int32_t cap, int32_t *desc_keys, int32_t *desc_counts,
+                  int32_t *lj_keys, int32_t *lj_counts);
+
+/* lsd_descriptors: descriptors X and dE/dX ([C][N][d_in], float32, host) of
+ * the last batched target evaluation (for parity checks). */
+LSD_API int lsd_descriptors(const lsd_handle *h, int32_t n_configs, float *X, float *dEdX);
+
+/* lsd_get_window: host copies of the last window's arrays, each may be NULL:
+ * q_mid, p_draft [K][N][3] double; F_draft, F_target [K][N][3] float;
+ * log_ratio, log_u, delta_norm [K] double; accept [K] int32. */
+LSD_API int lsd_get_window(const lsd_handle *h, double *q_mid, double *p_draft, float *F_draft, float *F_target,
+                   double *log_ratio, double *log_u, double *delta_norm, int32_t *accept);
+
+/* lsd_checkpoint: serialise the full dynamical state (positions, momenta, step,
+ * seed, error-correction cache, draft weights and optimiser moments) into buf;
+ * with buf == NULL only *len is set.  lsd_restore reads it back into a handle
+ * built with the same system and potentials. */
+LSD_API int lsd_checkpoint(const lsd_handle *h, void *buf, size_t *len);
+LSD_API int lsd_restore(lsd_handle *h, const void *buf, size_t len);
+
+/* lsd_profile_window: runs one window (it commits like lsd_step would) with
+ * its kernels issued one by one instead of as a graph, and CUDA events
+ * recorded on the handle's stream between them; ms[k] receives the duration
+ * of phase k for k < n_phases (at most LSD_N_PHASES):
+ * 0 draft window, 1 neighbour lists, 2 descriptors, 3 MLP forward+backward,
+ * 4 pair gradients + LJ, 5 force gather, 6 transport reduction,
+ * 7 accept/reflect/commit.  Synchronises the stream. */
+#define LSD_N_PHASES 8
+LSD_API int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases);
+
+/* lsd_query: K, N, input dimension of the target MLP, neighbour capacities. */
+LSD_API int lsd_query(const lsd_handle *h, int32_t *K, int32_t *n_atoms, int32_t *target_d_in, int32_t *nb_cap);
+
+LSD_API void lsd_destroy(lsd_handle *h);
+LSD_API const char *lsd_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSD_H */

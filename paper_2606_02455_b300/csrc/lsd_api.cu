@@ -1,0 +1,949 @@
+// lsd_api.cu -- host side of the C ABI declared in include/lsd.h.
+//
+// A handle owns all device memory of one simulation: the base state (FP64),
+// the window arrays of K drafted steps, the batched-verification workspace
+// (K*N rows), the device-resident run state, and two CUDA graphs: one window
+// (draft -> batched target forces -> transport/commit) and one plain target
+// step.  lsd_step replays the window graph without reading anything back per
+// window: every kernel reads the step counter and the stop step from device
+// memory and turns itself into a no-op once enough steps are committed, so
+// the host only synchronises once per batch of windows.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lsd.h"
+#include "lsd_common.cuh"
+#include "lsd_kernels.h"
+#include "lsd_train.h"
+
+using namespace lsd;
+
+namespace {
+
+constexpr double kTwo32 = 4294967296.0;
+constexpr int kMaxDynSmem = 220 * 1024;
+constexpr double kWaitLimitSeconds = 600.0;
+
+double kappa_conv() { return (1.602176634e-19 / 1e-10) / (1.66053906660e-27 * 1e-10 / 1e-30); }
+double kboltz_ev() { return 1.380649e-23 / 1.602176634e-19; }
+
+struct PotHost {
+    lsd_potential p{};
+    std::vector<double> eps, sigma;
+    std::vector<float> weights;
+    PotDev dev{};
+    float *dbuf = nullptr;            // Wt, Wn, b, wout (FP32)
+    __nv_bfloat16 *dbuf_bf = nullptr; // Wt, Wn, wout (BF16)
+    float rmax2f = 0.f, near2f = 0.f;
+    bool present = false;
+};
+
+}  // namespace
+
+struct lsd_handle {
+    int dev = 0;
+    int N = 0, S = 0, K = 0;
+    double box[3] = {0, 0, 0};
+    double gamma = 0, dt = 0, T = 0;
+    uint64_t seed = 0;
+    std::vector<int> species_h;
+    std::vector<double> mass_h;
+    Geo geo{};
+    Coef coef{};
+    PotHost draft, target;
+    bool learned_small = false;
+    // device state
+    double *q = nullptr, *p = nullptr;
+    int *species = nullptr;
+    DevState *st = nullptr;
+    // window arrays
+    double *w_qmid = nullptr, *w_pdraft = nullptr;
+    float *w_Fd = nullptr, *w_Fraw = nullptr, *w_Ft = nullptr;
+    uint4 *w_fix = nullptr, *fix_eval = nullptr;
+    float *ec_dF = nullptr;
+    int ec_on = 0;
+    // verification workspace (M = K*N rows)
+    int cap_near = 0, cap_far = 0;
+    int *near_keys = nullptr, *far_keys = nullptr, *n_near = nullptr, *n_far = nullptr;
+    float *X = nullptr, *dEdX = nullptr, *E_mlp = nullptr, *E_lj = nullptr, *E_atom = nullptr;
+    float4 *pair_g = nullptr, *Fpart = nullptr;
+    double2 *partials = nullptr;
+    // streams and graphs
+    cudaStream_t own_stream = nullptr, stream = nullptr;
+    cudaGraphExec_t g_window = nullptr, g_plain = nullptr;
+    bool drafted = false;
+    bool unbounded = false;   // target_step set to "no cap" by lsd_enqueue_*
+    // learned-draft training
+    TrainState train{};
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+cudaError_t g_last_cuda = cudaSuccess;
+
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) {                \
+            g_last_cuda = e_;                   \
+            return LSD_ECUDA;                   \
+        }                                       \
+    } while (0)
+
+template <typename T>
+int dalloc(lsd_handle *h, T **ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, count * sizeof(T));
+    if (e != cudaSuccess) {
+        g_last_cuda = e;
+        return LSD_ENOMEM;
+    }
+    cudaMemset(v, 0, count * sizeof(T));
+    h->allocs.push_back(v);
+    *ptr = (T *)v;
+    return LSD_OK;
+}
+
+#define TRY(x)                   \
+    do {                         \
+        int r_ = (x);            \
+        if (r_ != LSD_OK) return r_; \
+    } while (0)
+
+int input_dim(int S, int nr, int na) { return S * nr + na + S; }
+
+size_t n_weights(int d0, int L, int W) {
+    if (L <= 0) return 0;
+    return (size_t)W * d0 + W + (size_t)(L - 1) * ((size_t)W * W + W) + W + 1;
+}
+
+int pot_setup(lsd_handle *h, PotHost &ph, const lsd_potential *lp, bool is_draft) {
+    if (!lp) return LSD_EINVAL;
+    ph.p = *lp;
+    ph.present = true;
+    const int S = h->S;
+    const double bmin = std::min(h->box[0], std::min(h->box[1], h->box[2]));
+    PotDev &P = ph.dev;
+    P = PotDev{};
+    P.kind = lp->kind;
+    P.precision = lp->precision;
+    P.head = lp->head;
+    P.head_scale = (float)lp->head_scale;
+    if (lp->kind < LSD_POT_LJ || lp->kind > LSD_POT_LEARNED) return LSD_EINVAL;
+    if (lp->precision < LSD_FP32 || lp->precision > LSD_FP8) return LSD_EINVAL;
+    P.has_lj = lp->lj_cutoff > 0.0;
+    P.has_mlp = lp->kind != LSD_POT_LJ && lp->n_layers > 0;
+    if (P.has_lj) {
+        if (!lp->lj_eps || !lp->lj_sigma) return LSD_EINVAL;
+        if (!(lp->lj_cutoff < bmin)) return LSD_EINVAL;
+        ph.eps.assign(lp->lj_eps, lp->lj_eps + S);
+        ph.sigma.assign(lp->lj_sigma, lp->lj_sigma + S);
+        const double rc = lp->lj_cutoff;
+        P.lj_rc2f = (float)(rc * rc);
+        for (int a = 0; a < S; ++a)
+            for (int b = 0; b < S; ++b) {
+                const double e = std::sqrt(ph.eps[a] * ph.eps[b]);
+                const double s = 0.5 * (ph.sigma[a] + ph.sigma[b]);
+                const double sc6 = std::pow(s / rc, 6.0);
+                P.lj_sig2[a * S + b] = (float)(s * s);
+                P.lj_eps24[a * S + b] = (float)(24.0 * e);
+                P.lj_eps4[a * S + b] = (float)(4.0 * e);
+                P.lj_shift[a * S + b] = (float)(4.0 * e * (sc6 * sc6 - sc6));
+            }
+    }
+    if (P.has_mlp) {
+        const double rc = lp->desc_cutoff;
+        if (!(rc > 0.0) || !(rc < bmin)) return LSD_EINVAL;
+        if (lp->n_rbf < 2 || lp->n_rbf > 16) return LSD_EINVAL;
+        if (lp->n_ang != 0 && lp->n_ang != kNAng) return LSD_EINVAL;
+        if (lp->n_layers < 1 || lp->n_layers > kMaxLayers) return LSD_EINVAL;
+        if (lp->width < 32 || lp->width > 256 || lp->width % 32) return LSD_EUNSUPPORTED;
+        if (lp->head != LSD_HEAD_TANH && lp->head != LSD_HEAD_LINEAR) return LSD_EINVAL;
+        if (lp->kind == LSD_POT_LEARNED && lp->head != LSD_HEAD_LINEAR) return LSD_EINVAL;
+        P.n_rbf = lp->n_rbf;
+        P.n_ang = lp->n_ang;
+        P.n_layers = lp->n_layers;
+        P.width = lp->width;
+        P.d0 = input_dim(S, lp->n_rbf, lp->n_ang);
+        P.d0p = (P.d0 + 31) / 32 * 32;
+        P.desc_rc = (float)rc;
+        P.desc_rc2f = (float)(rc * rc);
+        const double w = rc / (double)(lp->n_rbf - 1);
+        P.rbf_w = (float)w;
+        P.rbf_inv2w2 = (float)(1.0 / (2.0 * w * w));
+        P.rbf_invw2 = (float)(1.0 / (w * w));
+        const size_t nw = n_weights(P.d0, P.n_layers, P.width);
+        if (!lp->weights || lp->n_weights != nw) return LSD_EINVAL;
+        ph.weights.assign(lp->weights, lp->weights + nw);
+        // device layouts: Wt[l] [din_p][W], Wn[l] [W][din_p], b[l] [W], wout [W]
+        const int W = P.width, L = P.n_layers;
+        size_t total = 0;
+        std::vector<size_t> offWt(L), offWn(L), offb(L);
+        for (int l = 0; l < L; ++l) {
+            const int dinp = l == 0 ? P.d0p : W;
+            offWt[l] = total; total += (size_t)dinp * W;
+            offWn[l] = total; total += (size_t)dinp * W;
+            offb[l] = total; total += W;
+        }
+        const size_t offwo = total;
+        total += W;
+        TRY(dalloc(h, &ph.dbuf, total));
+        TRY(dalloc(h, &ph.dbuf_bf, total));
+        for (int l = 0; l < L; ++l) {
+            P.Wt[l] = ph.dbuf + offWt[l];
+            P.Wn[l] = ph.dbuf + offWn[l];
+            P.b[l] = ph.dbuf + offb[l];
+            P.Wt_bf[l] = ph.dbuf_bf + offWt[l];
+            P.Wn_bf[l] = ph.dbuf_bf + offWn[l];
+        }
+        P.wout = ph.dbuf + offwo;
+        P.wout_bf = ph.dbuf_bf + offwo;
+        if (is_draft && lp->kind == LSD_POT_LEARNED) {
+            if (P.n_layers != 1 || P.width > 32 || P.n_ang != 0 || P.d0p > 32) return LSD_EUNSUPPORTED;
+        }
+    }
+    ph.rmax2f = std::max(P.lj_rc2f, P.desc_rc2f);
+    ph.near2f = P.has_mlp ? P.desc_rc2f : 0.f;
+    return LSD_OK;
+}
+
+// Uploads ph.weights into the device layouts (FP32 and BF16).
+int pot_upload(lsd_handle *h, PotHost &ph) {
+    PotDev &P = ph.dev;
+    if (!P.has_mlp) return LSD_OK;
+    const int W = P.width, L = P.n_layers;
+    std::vector<float> buf;
+    std::vector<size_t> offWt(L), offWn(L), offb(L);
+    size_t total = 0;
+    for (int l = 0; l < L; ++l) {
+        const int dinp = l == 0 ? P.d0p : W;
+        offWt[l] = total; total += (size_t)dinp * W;
+        offWn[l] = total; total += (size_t)dinp * W;
+        offb[l] = total; total += W;
+    }
+    const size_t offwo = total;
+    total += W;
+    buf.assign(total, 0.f);
+    const float *w = ph.weights.data();
+    for (int l = 0; l < L; ++l) {
+        const int din = l == 0 ? P.d0 : W, dinp = l == 0 ? P.d0p : W;
+        for (int o = 0; o < W; ++o)
+            for (int k = 0; k < din; ++k) {
+                const float v = w[(size_t)o * din + k];
+                buf[offWt[l] + (size_t)k * W + o] = v;
+                buf[offWn[l] + (size_t)o * dinp + k] = v;
+            }
+        w += (size_t)W * din;
+        for (int o = 0; o < W; ++o) buf[offb[l] + o] = w[o];
+        w += W;
+    }
+    for (int o = 0; o < W; ++o) buf[offwo + o] = w[o];
+    P.bout = w[W];
+    std::vector<__nv_bfloat16> bb(total);
+    for (size_t k = 0; k < total; ++k) bb[k] = __float2bfloat16(buf[k]);
+    CK(cudaMemcpyAsync(ph.dbuf, buf.data(), total * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(ph.dbuf_bf, bb.data(), total * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LSD_OK;
+}
+
+int nb_capacity(double density, double rc, int extra) {
+    const double expect = density * 4.0 / 3.0 * 3.14159265358979 * rc * rc * rc;
+    int cap = (int)std::ceil(2.0 * expect) + extra;
+    return (cap + 31) / 32 * 32;
+}
+
+int wait_stream(lsd_handle *h) {
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, h->stream);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(ev);
+        g_last_cuda = e;
+        return LSD_ECUDA;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        e = cudaEventQuery(ev);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) {
+            cudaEventDestroy(ev);
+            g_last_cuda = e;
+            return LSD_ECUDA;
+        }
+        const double dtw = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (dtw > kWaitLimitSeconds) {
+            cudaEventDestroy(ev);
+            return LSD_ETIMEOUT;
+        }
+    }
+    cudaEventDestroy(ev);
+    return LSD_OK;
+}
+
+// Batched force evaluation of `pot` on Kc configurations whose fixed-point
+// coordinates are in fix ([Kc][N]); forces to F ([Kc][N][3]).
+void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, float *F, float *E_out,
+                  cudaStream_t s) {
+    const int M = Kc * h->N;
+    const PotDev &P = pot.dev;
+    launch_neigh_build(fix, M, h->geo, pot.rmax2f, pot.near2f, h->cap_near, h->cap_far, h->near_keys, h->far_keys,
+                       h->n_near, h->n_far, h->st, s);
+    if (P.has_mlp) {
+        launch_desc(fix, h->near_keys, h->n_near, h->cap_near, M, h->geo, P, h->X, s);
+        launch_mlp_fp32(h->X, M, P, h->E_mlp, h->dEdX, s);
+    }
+    launch_pairgrad(fix, h->near_keys, h->n_near, h->far_keys, h->n_far, h->cap_near, h->cap_far, M, h->geo, P, h->dEdX,
+                    h->pair_g, h->Fpart, h->E_lj, s);
+    launch_force_gather(h->near_keys, h->n_near, h->cap_near, M, h->N, P.has_mlp, h->pair_g, h->Fpart, h->E_lj,
+                        h->E_mlp, F, E_out, h->st, s);
+}
+
+void enqueue_draft(lsd_handle *h, cudaStream_t s) {
+    launch_draft_small(h->learned_small, h->K, h->geo, h->draft.dev, h->coef, h->species, h->q, h->p, h->ec_dF,
+                       h->ec_on, h->st, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Fraw, h->w_fix, s);
+}
+
+void enqueue_verify(lsd_handle *h, cudaStream_t s) {
+    enqueue_eval(h, h->target, h->w_fix, h->K, h->w_Ft, nullptr, s);
+    if (h->train.capture_on) enqueue_frame_capture(h->train, h->w_qmid, h->w_Ft, h->K, h->N, h->st, s);
+    launch_transport(h->K, h->geo, h->coef, h->species, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Ft, h->w_Fraw, h->ec_dF,
+                     h->ec_on, h->q, h->p, h->st, h->partials, s);
+}
+
+void enqueue_plain(lsd_handle *h, cudaStream_t s) {
+    launch_plain_half(h->geo, h->coef, h->species, h->q, h->p, h->st, h->w_qmid, h->w_fix, s);
+    enqueue_eval(h, h->target, h->w_fix, 1, h->w_Ft, nullptr, s);
+    launch_plain_finish(h->geo, h->coef, h->species, h->w_qmid, h->w_Ft, h->q, h->p, h->st, s);
+}
+
+void destroy_graphs(lsd_handle *h) {
+    if (h->g_window) cudaGraphExecDestroy(h->g_window);
+    if (h->g_plain) cudaGraphExecDestroy(h->g_plain);
+    h->g_window = h->g_plain = nullptr;
+}
+
+int build_graph(lsd_handle *h, void (*fn)(lsd_handle *, cudaStream_t), cudaGraphExec_t *out) {
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    fn(h, h->stream);
+    CK(cudaStreamEndCapture(h->stream, &g));
+    cudaError_t e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return LSD_OK;
+}
+
+void window_fn(lsd_handle *h, cudaStream_t s) {
+    enqueue_draft(h, s);
+    enqueue_verify(h, s);
+}
+
+int ensure_graphs(lsd_handle *h) {
+    if (!h->g_window) TRY(build_graph(h, window_fn, &h->g_window));
+    if (!h->g_plain) TRY(build_graph(h, enqueue_plain, &h->g_plain));
+    return LSD_OK;
+}
+
+int read_state(lsd_handle *h, DevState *out) {
+    CK(cudaMemcpyAsync(out, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    TRY(wait_stream(h));
+    return LSD_OK;
+}
+
+__global__ void set_target_kernel(DevState *st, long long target, int relative) {
+    st->target_step = relative ? st->step + target : target;
+}
+
+// The stop step is written by a one-thread kernel (the value travels as a
+// kernel argument), so no host buffer has to outlive the call.
+int set_target_step(lsd_handle *h, long long target, bool relative = false) {
+    set_target_kernel<<<1, 1, 0, h->stream>>>(h->st, target, relative ? 1 : 0);
+    CK(cudaGetLastError());
+    h->unbounded = false;
+    return LSD_OK;
+}
+
+int check_err(const DevState &s) {
+    if (s.err & 2) return LSD_ENONFINITE;
+    if (s.err & 1) return LSD_EOVERFLOW;
+    if (s.err & 4) return LSD_ESTATE;
+    return LSD_OK;
+}
+
+__global__ void mb_init_kernel(int N, Coef cf, const int *species, const double *mass, double T, double kT_kappa,
+                               double *p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float3 xi = normals3(cf.seed, 0ull, (uint32_t)i, 2u);
+    const double sd = sqrt(mass[species[i]] * kT_kappa);
+    p[3 * i + 0] = sd * (double)xi.x;
+    p[3 * i + 1] = sd * (double)xi.y;
+    p[3 * i + 2] = sd * (double)xi.z;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lsd_strerror(int code) {
+    switch (code) {
+        case LSD_OK: return "ok";
+        case LSD_EINVAL: return "invalid argument";
+        case LSD_ENOMEM: return "out of memory";
+        case LSD_ECUDA: return g_last_cuda != cudaSuccess ? cudaGetErrorString(g_last_cuda) : "CUDA error";
+        case LSD_ETIMEOUT: return "timed out waiting for the device";
+        case LSD_ENONFINITE: return "non-finite force or log ratio";
+        case LSD_ESTATE: return "call out of order or inconsistent neighbour lists";
+        case LSD_EOVERFLOW: return "neighbour list capacity exceeded";
+        case LSD_EUNSUPPORTED: return "unsupported combination of options";
+        default: return "unknown error";
+    }
+}
+
+void lsd_destroy(lsd_handle *h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    destroy_graphs(h);
+    for (void *v : h->allocs) cudaFree(v);
+    train_free(h->train);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+}
+
+int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potential *target, double gamma, double dt,
+             double T, int32_t K, lsd_handle **out) {
+    if (!out) return LSD_EINVAL;
+    *out = nullptr;
+    if (!sys || !draft || !target || !sys->pos || !sys->species || !sys->species_mass) return LSD_EINVAL;
+    if (sys->n_atoms < 1 || sys->n_species < 1 || sys->n_species > kMaxSpecies) return LSD_EINVAL;
+    if (K < 1 || K > kMaxK || !(dt > 0) || !(gamma >= 0) || !(T >= 0)) return LSD_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!(sys->box[a] > 0)) return LSD_EINVAL;
+    for (int s = 0; s < sys->n_species; ++s)
+        if (!(sys->species_mass[s] > 0)) return LSD_EINVAL;
+    for (int i = 0; i < sys->n_atoms; ++i)
+        if (sys->species[i] < 0 || sys->species[i] >= sys->n_species) return LSD_EINVAL;
+    lsd_handle *h = new (std::nothrow) lsd_handle();
+    if (!h) return LSD_ENOMEM;
+    int rc = LSD_OK;
+    auto fail = [&](int r) {
+        lsd_destroy(h);
+        return r;
+    };
+    if (cudaGetDevice(&h->dev) != cudaSuccess) return fail(LSD_ECUDA);
+    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(LSD_ECUDA);
+    h->stream = h->own_stream;
+    h->N = sys->n_atoms;
+    h->S = sys->n_species;
+    h->K = K;
+    for (int a = 0; a < 3; ++a) h->box[a] = sys->box[a];
+    h->gamma = gamma;
+    h->dt = dt;
+    h->T = T;
+    h->seed = sys->seed;
+    h->species_h.assign(sys->species, sys->species + sys->n_atoms);
+    h->mass_h.assign(sys->species_mass, sys->species_mass + sys->n_species);
+    Geo &g = h->geo;
+    g.N = h->N;
+    g.S = h->S;
+    for (int a = 0; a < 3; ++a) {
+        g.scale[a] = kTwo32 / h->box[a];
+        g.scale_f[a] = (float)(h->box[a] / kTwo32);
+    }
+    // Eq. 4 coefficients
+    Coef &c = h->coef;
+    const double kap = kappa_conv(), kB = kboltz_ev();
+    c.c1 = std::exp(-gamma * dt);
+    const double hh = 0.5 * dt;
+    c.aF = (1.0 + c.c1) * hh * kap;
+    const double one_minus = -std::expm1(-2.0 * gamma * dt);
+    for (int s = 0; s < h->S; ++s) {
+        const double m = h->mass_h[s];
+        c.hm[s] = hh / m;
+        c.sig[s] = std::sqrt(m * kB * T * kap * one_minus);
+        c.aF_sig[s] = c.sig[s] > 0 ? c.aF / c.sig[s] : 0.0;
+    }
+    c.seed = h->seed;
+    if ((rc = pot_setup(h, h->draft, draft, true)) != LSD_OK) return fail(rc);
+    if ((rc = pot_setup(h, h->target, target, false)) != LSD_OK) return fail(rc);
+    h->learned_small = h->draft.dev.has_mlp;
+    if (draft_small_smem_bytes(h->N, h->draft.dev, h->learned_small) > (size_t)kMaxDynSmem) return fail(LSD_EUNSUPPORTED);
+    if (mlp_fp32_smem_bytes(h->target.dev) > (size_t)kMaxDynSmem) return fail(LSD_EUNSUPPORTED);
+    // capacities from the mean density (x2 + margin)
+    const double V = h->box[0] * h->box[1] * h->box[2];
+    const double rho = h->N / V;
+    double rnear = 0.0, rfar = 0.0;
+    for (const PotHost *ph : {&h->draft, &h->target}) {
+        rnear = std::max(rnear, ph->dev.has_mlp ? (double)ph->p.desc_cutoff : 0.0);
+        rfar = std::max(rfar, std::max(ph->dev.has_lj ? ph->p.lj_cutoff : 0.0, ph->dev.has_mlp ? ph->p.desc_cutoff : 0.0));
+    }
+    h->cap_near = std::min(nb_capacity(rho, rnear, 32), (27 * h->N + 31) / 32 * 32);
+    h->cap_far = std::min(nb_capacity(rho, rfar, 32), (27 * h->N + 31) / 32 * 32);
+    if (desc_smem_bytes(8, h->cap_near) + 8 * 256 * sizeof(float) > (size_t)kMaxDynSmem) return fail(LSD_EUNSUPPORTED);
+    if (verify_kernels_setup(kMaxDynSmem) != cudaSuccess || mlp_kernels_setup(kMaxDynSmem) != cudaSuccess ||
+        draft_kernels_setup(kMaxDynSmem) != cudaSuccess)
+        return fail(LSD_ECUDA);
+    const size_t N = h->N, D = 3 * N, KN = (size_t)K * N, KD = (size_t)K * D;
+    const int dmax = std::max(h->draft.dev.d0p, h->target.dev.d0p);
+    if ((rc = dalloc(h, &h->q, D)) || (rc = dalloc(h, &h->p, D)) || (rc = dalloc(h, &h->species, N)) ||
+        (rc = dalloc(h, &h->st, 1)) || (rc = dalloc(h, &h->w_qmid, KD)) || (rc = dalloc(h, &h->w_pdraft, KD)) ||
+        (rc = dalloc(h, &h->w_Fd, KD)) || (rc = dalloc(h, &h->w_Fraw, KD)) || (rc = dalloc(h, &h->w_Ft, KD)) ||
+        (rc = dalloc(h, &h->w_fix, KN)) || (rc = dalloc(h, &h->fix_eval, KN)) || (rc = dalloc(h, &h->ec_dF, D)) ||
+        (rc = dalloc(h, &h->near_keys, KN * h->cap_near)) || (rc = dalloc(h, &h->far_keys, KN * h->cap_far)) ||
+        (rc = dalloc(h, &h->n_near, KN)) || (rc = dalloc(h, &h->n_far, KN)) ||
+        (rc = dalloc(h, &h->X, KN * std::max(dmax, 32))) || (rc = dalloc(h, &h->dEdX, KN * std::max(dmax, 32))) ||
+        (rc = dalloc(h, &h->E_mlp, KN)) || (rc = dalloc(h, &h->E_lj, KN)) || (rc = dalloc(h, &h->E_atom, KN)) ||
+        (rc = dalloc(h, &h->pair_g, KN * h->cap_near)) || (rc = dalloc(h, &h->Fpart, KN)) ||
+        (rc = dalloc(h, &h->partials, (size_t)K * ((h->N + 1023) / 1024 + 600))))
+        return fail(rc);
+    if ((rc = pot_upload(h, h->draft)) != LSD_OK) return fail(rc);
+    if ((rc = pot_upload(h, h->target)) != LSD_OK) return fail(rc);
+    if (cudaMemcpy(h->q, sys->pos, D * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->species, sys->species, N * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(LSD_ECUDA);
+    DevState s0{};
+    s0.step = 0;
+    s0.target_step = 0;
+    s0.first_reject_last = -1;
+    if (cudaMemcpy(h->st, &s0, sizeof(DevState), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSD_ECUDA);
+    if (sys->mom) {
+        if (cudaMemcpy(h->p, sys->mom, D * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(LSD_ECUDA);
+    } else {
+        double *dmass = nullptr;
+        if ((rc = dalloc(h, &dmass, h->S)) != LSD_OK) return fail(rc);
+        if (cudaMemcpy(dmass, h->mass_h.data(), h->S * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(LSD_ECUDA);
+        mb_init_kernel<<<(h->N + 255) / 256, 256, 0, h->stream>>>(h->N, h->coef, h->species, dmass, T, kB * T * kap,
+                                                                  h->p);
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(LSD_ECUDA);
+    }
+    if ((rc = train_init(h->train, h->draft.dev, h->draft.weights, h->N)) != LSD_OK) return fail(rc);
+    h->train.st = h->st;
+    h->train.K = K;
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(LSD_ECUDA);
+    *out = h;
+    return LSD_OK;
+}
+
+int lsd_set_stream(lsd_handle *h, void *cuda_stream) {
+    if (!h) return LSD_EINVAL;
+    CK(cudaStreamSynchronize(h->stream));
+    h->stream = cuda_stream ? (cudaStream_t)cuda_stream : h->own_stream;
+    destroy_graphs(h);
+    return LSD_OK;
+}
+
+int lsd_draft_window(lsd_handle *h) {
+    if (!h) return LSD_EINVAL;
+    DevState s;
+    TRY(read_state(h, &s));
+    TRY(set_target_step(h, s.step + h->K));
+    enqueue_draft(h, h->stream);
+    CK(cudaGetLastError());
+    h->drafted = true;
+    return LSD_OK;
+}
+
+int lsd_verify_window(lsd_handle *h, int32_t *n_committed, int32_t *first_reject) {
+    if (!h) return LSD_EINVAL;
+    if (!h->drafted) return LSD_ESTATE;
+    enqueue_verify(h, h->stream);
+    CK(cudaGetLastError());
+    h->drafted = false;
+    DevState s;
+    TRY(read_state(h, &s));
+    if (n_committed) *n_committed = s.n_commit_last;
+    if (first_reject) *first_reject = s.first_reject_last;
+    return check_err(s);
+}
+
+int lsd_step(lsd_handle *h, int64_t n_steps, lsd_stats *stats) {
+    if (!h || n_steps < 0) return LSD_EINVAL;
+    TRY(ensure_graphs(h));
+    DevState s;
+    TRY(read_state(h, &s));
+    const long long target = s.step + n_steps;
+    TRY(set_target_step(h, target));
+    long long w0 = s.windows, c0 = s.committed;
+    long long rem = n_steps;
+    while (rem > 0) {
+        double rate = (s.windows > w0) ? (double)(s.committed - c0) / (double)(s.windows - w0) : (double)h->K;
+        if (rate < 1.0) rate = 1.0;
+        long long batch = (long long)std::ceil((double)rem / rate);
+        if (batch < 1) batch = 1;
+        for (long long b = 0; b < batch; ++b) CK(cudaGraphLaunch(h->g_window, h->stream));
+        TRY(read_state(h, &s));
+        TRY(check_err(s));
+        rem = target - s.step;
+    }
+    h->drafted = false;
+    if (stats) TRY(lsd_get_stats(h, stats));
+    return LSD_OK;
+}
+
+int lsd_enqueue_windows(lsd_handle *h, int32_t n) {
+    if (!h || n < 0) return LSD_EINVAL;
+    TRY(ensure_graphs(h));
+    if (!h->unbounded) {
+        TRY(set_target_step(h, (long long)1 << 60));
+        h->unbounded = true;
+    }
+    for (int32_t k = 0; k < n; ++k) CK(cudaGraphLaunch(h->g_window, h->stream));
+    h->drafted = false;
+    return LSD_OK;
+}
+
+int lsd_enqueue_plain(lsd_handle *h, int32_t n) {
+    if (!h || n < 0) return LSD_EINVAL;
+    TRY(ensure_graphs(h));
+    if (!h->unbounded) {
+        TRY(set_target_step(h, (long long)1 << 60));
+        h->unbounded = true;
+    }
+    for (int32_t k = 0; k < n; ++k) CK(cudaGraphLaunch(h->g_plain, h->stream));
+    return LSD_OK;
+}
+
+int lsd_plain_step(lsd_handle *h, int64_t n_steps) {
+    if (!h || n_steps < 0) return LSD_EINVAL;
+    TRY(ensure_graphs(h));
+    DevState s;
+    TRY(read_state(h, &s));
+    TRY(set_target_step(h, s.step + n_steps));
+    for (int64_t t = 0; t < n_steps; ++t) CK(cudaGraphLaunch(h->g_plain, h->stream));
+    TRY(read_state(h, &s));
+    return check_err(s);
+}
+
+int lsd_get_stats(const lsd_handle *h, lsd_stats *out) {
+    if (!h || !out) return LSD_EINVAL;
+    DevState s;
+    TRY(read_state(const_cast<lsd_handle *>(h), &s));
+    out->windows = s.windows;
+    out->committed = s.committed;
+    out->rejected = s.rejected;
+    out->verified = s.verified;
+    out->sum_delta = s.sum_delta;
+    out->sum_pred_reject = s.sum_pred;
+    out->step = s.step;
+    return LSD_OK;
+}
+
+int lsd_get_state(const lsd_handle *hc, double *pos, double *mom, int64_t *step) {
+    if (!hc) return LSD_EINVAL;
+    lsd_handle *h = const_cast<lsd_handle *>(hc);
+    const size_t D = 3 * (size_t)h->N;
+    if (pos) CK(cudaMemcpyAsync(pos, h->q, D * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (mom) CK(cudaMemcpyAsync(mom, h->p, D * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    long long st = 0;
+    CK(cudaMemcpyAsync(&st, &h->st->step, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+    TRY(wait_stream(h));
+    if (step) *step = st;
+    return LSD_OK;
+}
+
+int lsd_set_state(lsd_handle *h, const double *pos, const double *mom, int64_t step) {
+    if (!h || step < 0) return LSD_EINVAL;
+    const size_t D = 3 * (size_t)h->N;
+    if (pos) CK(cudaMemcpyAsync(h->q, pos, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (mom) CK(cudaMemcpyAsync(h->p, mom, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    long long st = step;
+    CK(cudaMemcpyAsync(&h->st->step, &st, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+    TRY(wait_stream(h));
+    h->drafted = false;
+    return LSD_OK;
+}
+
+int lsd_set_error_correction(lsd_handle *h, int32_t on) {
+    if (!h) return LSD_EINVAL;
+    CK(cudaMemsetAsync(h->ec_dF, 0, 3 * (size_t)h->N * sizeof(float), h->stream));
+    h->ec_on = on ? 1 : 0;
+    destroy_graphs(h);
+    return wait_stream(h);
+}
+
+int lsd_set_draft_weights(lsd_handle *h, const float *w, size_t n) {
+    if (!h || !w) return LSD_EINVAL;
+    if (!h->draft.dev.has_mlp || n != h->draft.weights.size()) return LSD_EINVAL;
+    TRY(wait_stream(h));
+    h->draft.weights.assign(w, w + n);
+    TRY(pot_upload(h, h->draft));
+    TRY(train_set_weights(h->train, h->draft.weights));
+    destroy_graphs(h);   // bout is a kernel parameter
+    return LSD_OK;
+}
+
+int lsd_get_draft_weights(const lsd_handle *h, float *w, size_t n) {
+    if (!h || !w) return LSD_EINVAL;
+    if (n != h->draft.weights.size()) return LSD_EINVAL;
+    std::memcpy(w, h->draft.weights.data(), n * sizeof(float));
+    return LSD_OK;
+}
+
+static int forces_dev(lsd_handle *h, PotHost &pot, const double *q_dev, int32_t C, float *F_dev, float *E_dev) {
+    if (!h || !q_dev || !F_dev || C < 1 || C > h->K) return LSD_EINVAL;
+    const int M = C * h->N;
+    launch_fixpoint(q_dev, h->species, M, h->geo, h->fix_eval, h->stream);
+    enqueue_eval(h, pot, h->fix_eval, C, F_dev, E_dev, h->stream);
+    CK(cudaGetLastError());
+    DevState s;
+    TRY(read_state(h, &s));
+    return check_err(s);
+}
+
+int lsd_target_forces_dev(lsd_handle *h, const double *q_dev, int32_t C, float *F_dev, float *E_dev) {
+    if (!h) return LSD_EINVAL;
+    return forces_dev(h, h->target, q_dev, C, F_dev, E_dev);
+}
+
+int lsd_draft_forces_dev(lsd_handle *h, const double *q_dev, int32_t C, float *F_dev, float *E_dev) {
+    if (!h) return LSD_EINVAL;
+    return forces_dev(h, h->draft, q_dev, C, F_dev, E_dev);
+}
+
+int lsd_neighbors(const lsd_handle *hc, int32_t config, int32_t cap, int32_t *desc_keys, int32_t *desc_counts,
+                  int32_t *lj_keys, int32_t *lj_counts) {
+    if (!hc || config < 0 || config >= hc->K || cap < 1) return LSD_EINVAL;
+    lsd_handle *h = const_cast<lsd_handle *>(hc);
+    const size_t N = h->N, r0 = (size_t)config * N;
+    std::vector<int> nk(N * h->cap_near), fk(N * h->cap_far), nn(N), nf(N);
+    CK(cudaMemcpyAsync(nk.data(), h->near_keys + r0 * h->cap_near, nk.size() * sizeof(int), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaMemcpyAsync(fk.data(), h->far_keys + r0 * h->cap_far, fk.size() * sizeof(int), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaMemcpyAsync(nn.data(), h->n_near + r0, N * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(nf.data(), h->n_far + r0, N * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    TRY(wait_stream(h));
+    for (size_t i = 0; i < N; ++i) {
+        const int *a = nk.data() + i * h->cap_near;
+        const int *b = fk.data() + i * h->cap_far;
+        if (desc_keys && desc_counts) {
+            if (nn[i] > cap) return LSD_EOVERFLOW;
+            std::memcpy(desc_keys + i * cap, a, nn[i] * sizeof(int));
+            desc_counts[i] = nn[i];
+        }
+        if (lj_keys && lj_counts) {
+            // the LJ cutoff is the outer cutoff here: near and far lists together, merged in key order
+            if (nn[i] + nf[i] > cap) return LSD_EOVERFLOW;
+            std::merge(a, a + nn[i], b, b + nf[i], lj_keys + i * cap);
+            lj_counts[i] = nn[i] + nf[i];
+        }
+    }
+    return LSD_OK;
+}
+
+int lsd_descriptors(const lsd_handle *hc, int32_t C, float *X, float *dEdX) {
+    if (!hc || C < 1 || C > hc->K) return LSD_EINVAL;
+    lsd_handle *h = const_cast<lsd_handle *>(hc);
+    const PotDev &P = h->target.dev;
+    if (!P.has_mlp) return LSD_EINVAL;
+    const size_t M = (size_t)C * h->N;
+    std::vector<float> x(M * P.d0p), gx(M * P.d0p);
+    CK(cudaMemcpyAsync(x.data(), h->X, x.size() * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(gx.data(), h->dEdX, gx.size() * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    TRY(wait_stream(h));
+    for (size_t r = 0; r < M; ++r) {
+        if (X) std::memcpy(X + r * P.d0, x.data() + r * P.d0p, P.d0 * sizeof(float));
+        if (dEdX) std::memcpy(dEdX + r * P.d0, gx.data() + r * P.d0p, P.d0 * sizeof(float));
+    }
+    return LSD_OK;
+}
+
+int lsd_get_window(const lsd_handle *hc, double *q_mid, double *p_draft, float *F_draft, float *F_target,
+                   double *log_ratio, double *log_u, double *delta_norm, int32_t *accept) {
+    if (!hc) return LSD_EINVAL;
+    lsd_handle *h = const_cast<lsd_handle *>(hc);
+    const size_t KD = (size_t)h->K * 3 * h->N;
+    if (q_mid) CK(cudaMemcpyAsync(q_mid, h->w_qmid, KD * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (p_draft) CK(cudaMemcpyAsync(p_draft, h->w_pdraft, KD * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (F_draft) CK(cudaMemcpyAsync(F_draft, h->w_Fd, KD * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (F_target) CK(cudaMemcpyAsync(F_target, h->w_Ft, KD * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    DevState s;
+    TRY(read_state(h, &s));
+    for (int j = 0; j < h->K; ++j) {
+        if (log_ratio) log_ratio[j] = s.logr[j];
+        if (log_u) log_u[j] = s.logu[j];
+        if (delta_norm) delta_norm[j] = s.dnorm[j];
+        if (accept) accept[j] = s.accept[j];
+    }
+    return LSD_OK;
+}
+
+int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
+    if (!h || !ms || n_phases < 0) return LSD_EINVAL;
+    DevState s;
+    TRY(read_state(h, &s));
+    TRY(set_target_step(h, s.step + h->K));
+    cudaEvent_t ev[LSD_N_PHASES + 1];
+    for (int k = 0; k <= LSD_N_PHASES; ++k) CK(cudaEventCreate(&ev[k]));
+    cudaStream_t st = h->stream;
+    const int M = h->K * h->N;
+    const PotDev &P = h->target.dev;
+    CK(cudaEventRecord(ev[0], st));
+    enqueue_draft(h, st);
+    CK(cudaEventRecord(ev[1], st));
+    launch_neigh_build(h->w_fix, M, h->geo, h->target.rmax2f, h->target.near2f, h->cap_near, h->cap_far, h->near_keys,
+                       h->far_keys, h->n_near, h->n_far, h->st, st);
+    CK(cudaEventRecord(ev[2], st));
+    if (P.has_mlp) launch_desc(h->w_fix, h->near_keys, h->n_near, h->cap_near, M, h->geo, P, h->X, st);
+    CK(cudaEventRecord(ev[3], st));
+    if (P.has_mlp) launch_mlp_fp32(h->X, M, P, h->E_mlp, h->dEdX, st);
+    CK(cudaEventRecord(ev[4], st));
+    launch_pairgrad(h->w_fix, h->near_keys, h->n_near, h->far_keys, h->n_far, h->cap_near, h->cap_far, M, h->geo, P,
+                    h->dEdX, h->pair_g, h->Fpart, h->E_lj, st);
+    CK(cudaEventRecord(ev[5], st));
+    launch_force_gather(h->near_keys, h->n_near, h->cap_near, M, h->N, P.has_mlp, h->pair_g, h->Fpart, h->E_lj,
+                        h->E_mlp, h->w_Ft, nullptr, h->st, st);
+    CK(cudaEventRecord(ev[6], st));
+    launch_transport_reduce(h->K, h->geo, h->coef, h->species, h->w_Fd, h->w_Ft, h->st, h->partials, st);
+    CK(cudaEventRecord(ev[7], st));
+    launch_transport_commit(h->K, h->geo, h->coef, h->species, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Ft, h->w_Fraw,
+                            h->ec_dF, h->ec_on, h->q, h->p, h->st, h->partials, st);
+    CK(cudaEventRecord(ev[8], st));
+    CK(cudaGetLastError());
+    TRY(wait_stream(h));
+    for (int k = 0; k < LSD_N_PHASES && k < n_phases; ++k) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+        ms[k] = t;
+    }
+    for (int k = 0; k <= LSD_N_PHASES; ++k) cudaEventDestroy(ev[k]);
+    TRY(read_state(h, &s));
+    return check_err(s);
+}
+
+int lsd_query(const lsd_handle *h, int32_t *K, int32_t *n_atoms, int32_t *d_in, int32_t *nb_cap) {
+    if (!h) return LSD_EINVAL;
+    if (K) *K = h->K;
+    if (n_atoms) *n_atoms = h->N;
+    if (d_in) *d_in = h->target.dev.d0;
+    if (nb_cap) *nb_cap = h->cap_near + h->cap_far;
+    return LSD_OK;
+}
+
+// ---- checkpoint / restore -------------------------------------------------
+namespace {
+constexpr uint64_t kCkptMagic = 0x4c53444350543031ull;   // "LSDCPT01"
+struct CkptHeader {
+    uint64_t magic;
+    int64_t n_atoms, K, step, ec_on, n_weights, n_adam;
+    uint64_t seed;
+};
+}  // namespace
+
+int lsd_checkpoint(const lsd_handle *hc, void *buf, size_t *len) {
+    if (!hc || !len) return LSD_EINVAL;
+    lsd_handle *h = const_cast<lsd_handle *>(hc);
+    const size_t D = 3 * (size_t)h->N;
+    const size_t nw = h->draft.weights.size();
+    const size_t nadam = train_adam_size(h->train);
+    const size_t need = sizeof(CkptHeader) + 2 * D * sizeof(double) + D * sizeof(float) + nw * sizeof(float) +
+                        2 * nadam * sizeof(float);
+    if (!buf) {
+        *len = need;
+        return LSD_OK;
+    }
+    if (*len < need) {
+        *len = need;
+        return LSD_EINVAL;
+    }
+    CkptHeader hd{};
+    hd.magic = kCkptMagic;
+    hd.n_atoms = h->N;
+    hd.K = h->K;
+    hd.ec_on = h->ec_on;
+    hd.n_weights = (int64_t)nw;
+    hd.n_adam = (int64_t)nadam;
+    hd.seed = h->seed;
+    char *o = (char *)buf;
+    int64_t step = 0;
+    TRY(lsd_get_state(h, (double *)(o + sizeof(CkptHeader)), (double *)(o + sizeof(CkptHeader)) + D, &step));
+    hd.step = step;
+    std::memcpy(o, &hd, sizeof(hd));
+    char *p = o + sizeof(CkptHeader) + 2 * D * sizeof(double);
+    CK(cudaMemcpyAsync(p, h->ec_dF, D * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    TRY(wait_stream(h));
+    p += D * sizeof(float);
+    if (nw) std::memcpy(p, h->draft.weights.data(), nw * sizeof(float));
+    p += nw * sizeof(float);
+    TRY(train_adam_get(h->train, (float *)p, (float *)p + nadam));
+    *len = need;
+    return LSD_OK;
+}
+
+int lsd_restore(lsd_handle *h, const void *buf, size_t len) {
+    if (!h || !buf || len < sizeof(CkptHeader)) return LSD_EINVAL;
+    CkptHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    const size_t D = 3 * (size_t)h->N;
+    if (hd.magic != kCkptMagic || hd.n_atoms != h->N || hd.seed != h->seed ||
+        hd.n_weights != (int64_t)h->draft.weights.size() || hd.n_adam != (int64_t)train_adam_size(h->train))
+        return LSD_EINVAL;
+    const size_t need = sizeof(CkptHeader) + 2 * D * sizeof(double) + D * sizeof(float) +
+                        (size_t)hd.n_weights * sizeof(float) + 2 * (size_t)hd.n_adam * sizeof(float);
+    if (len < need) return LSD_EINVAL;
+    const char *o = (const char *)buf + sizeof(CkptHeader);
+    TRY(lsd_set_state(h, (const double *)o, (const double *)o + D, hd.step));
+    const char *p = o + 2 * D * sizeof(double);
+    CK(cudaMemcpyAsync(h->ec_dF, p, D * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    TRY(wait_stream(h));
+    h->ec_on = (int)hd.ec_on;
+    destroy_graphs(h);
+    p += D * sizeof(float);
+    if (hd.n_weights) {
+        TRY(lsd_set_draft_weights(h, (const float *)p, (size_t)hd.n_weights));
+    }
+    p += (size_t)hd.n_weights * sizeof(float);
+    TRY(train_adam_set(h->train, (const float *)p, (const float *)p + hd.n_adam));
+    return LSD_OK;
+}
+
+// ---- frames and learned-draft training --------------------------------------
+int lsd_set_frame_capture(lsd_handle *h, int64_t capacity) {
+    if (!h || capacity < 0) return LSD_EINVAL;
+    TRY(wait_stream(h));
+    TRY(train_set_capture(h->train, capacity, h->N));
+    destroy_graphs(h);
+    return LSD_OK;
+}
+
+int lsd_frame_count(const lsd_handle *h, int64_t *n) {
+    if (!h || !n) return LSD_EINVAL;
+    return train_frame_count(const_cast<lsd_handle *>(h)->train, n, h->stream);
+}
+
+int lsd_train_draft(lsd_handle *h, int32_t n_iters, float lr, int32_t frames_per_iter, float *loss_out) {
+    if (!h || n_iters < 0) return LSD_EINVAL;
+    if (h->draft.p.kind != LSD_POT_LEARNED) return LSD_EINVAL;
+    TRY(wait_stream(h));
+    TRY(train_run(h->train, h->geo, h->draft.dev, h->species, n_iters, lr, frames_per_iter, loss_out, h->stream));
+    // new weights -> draft MLP (FP32 master in the trainer)
+    TRY(train_get_weights(h->train, h->draft.weights, h->stream));
+    TRY(pot_upload(h, h->draft));
+    destroy_graphs(h);
+    return LSD_OK;
+}
+
+int lsd_force_match_dev(lsd_handle *h, const double *frames_q_dev, const float *frames_F_dev, int32_t n_frames,
+                        float *loss_out, float *grad_dev) {
+    if (!h || !frames_q_dev || !frames_F_dev || n_frames < 1) return LSD_EINVAL;
+    if (h->draft.p.kind != LSD_POT_LEARNED) return LSD_EINVAL;
+    TRY(wait_stream(h));
+    return train_force_match(h->train, h->geo, h->draft.dev, h->species, frames_q_dev, frames_F_dev, n_frames, loss_out,
+                             grad_dev, h->stream);
+}
+
+}  // extern "C"

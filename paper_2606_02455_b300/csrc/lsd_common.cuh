@@ -1,0 +1,231 @@
+// lsd_common.cuh -- device-side definitions shared by the kernels of liblsd.so.
+//
+// Counter-based noise (Philox4x32-10, Box-Muller), the fixed-point neighbour
+// membership rule, and the parameter blocks passed to every kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+namespace lsd {
+
+constexpr int kMaxSpecies = 4;
+constexpr int kMaxLayers = 6;
+constexpr int kMaxK = 128;
+constexpr int kNAng = 16;
+
+// ---------------------------------------------------------------------------
+// Parameter blocks
+// ---------------------------------------------------------------------------
+
+struct Geo {
+    int N;                 // atoms
+    int S;                 // species
+    double scale[3];       // 2^32 / L per axis (fixed-point wrap)
+    float scale_f[3];      // fl32(L / 2^32) per axis
+};
+
+struct PotDev {
+    int kind;              // LSD_POT_*
+    int precision;         // LSD_FP32 | LSD_BF16 | LSD_FP8
+    int head;              // LSD_HEAD_*
+    float head_scale;
+    int has_lj, has_mlp;
+    float lj_rc2f;         // fl32(rc_lj^2)
+    float desc_rc2f;       // fl32(rc_desc^2)
+    float desc_rc;         // rc_desc
+    float rmax2f;          // max of the two
+    int n_rbf, n_ang, n_layers, width;
+    int d0, d0p;           // input width and its padding to a multiple of 32
+    float rbf_w, rbf_inv2w2, rbf_invw2;
+    // LJ pair tables [si*S+sj]
+    float lj_sig2[kMaxSpecies * kMaxSpecies];
+    float lj_eps24[kMaxSpecies * kMaxSpecies];
+    float lj_eps4[kMaxSpecies * kMaxSpecies];
+    float lj_shift[kMaxSpecies * kMaxSpecies];
+    // FP32 weights: Wt[l] = W_l^T padded [din_p][width]; Wn[l] = W_l padded [width][din_p]
+    const float *Wt[kMaxLayers];
+    const float *Wn[kMaxLayers];
+    const float *b[kMaxLayers];
+    const float *wout;
+    float bout;
+    // BF16 copies (same layouts)
+    const __nv_bfloat16 *Wt_bf[kMaxLayers];
+    const __nv_bfloat16 *Wn_bf[kMaxLayers];
+    const __nv_bfloat16 *wout_bf;
+};
+
+struct Coef {
+    double c1;             // exp(-gamma dt)
+    double aF;             // (1 + c1) (dt/2) kappa
+    double hm[kMaxSpecies];     // (dt/2) / m
+    double sig[kMaxSpecies];    // sqrt(m kB T kappa (1 - exp(-2 gamma dt)))
+    double aF_sig[kMaxSpecies]; // aF / sig
+    uint64_t seed;
+};
+
+// Device-resident run state.  step is the index of the base state.
+struct DevState {
+    long long step;
+    long long target_step;       // windows stop committing at this step
+    int n_commit_last;
+    int first_reject_last;       // 1-based, -1 if none
+    int err;                     // bit flags: 1 neighbour overflow, 2 non-finite
+    unsigned int blocks_done;    // last-block counter of the commit kernel
+    long long windows, committed, rejected, verified;
+    double sum_delta, sum_pred;
+    int accept[kMaxK];
+    double logr[kMaxK], logu[kMaxK], dnorm[kMaxK];
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the 4x32 multiply-xor
+// bijection; Weyl key schedule.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 philox_words(uint64_t seed, uint64_t n, uint32_t atom, uint32_t stream) {
+    return philox4x32_10(make_uint4((uint32_t)n, (uint32_t)(n >> 32), atom, stream),
+                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// Three standard normals for (step n, atom, stream): Box-Muller on 23-bit
+// uniforms u1 = ((w0>>9)+1/2)/2^23, u2 = (w1>>9)/2^23; z from (w2, w3).
+__device__ __forceinline__ float3 normals3(uint64_t seed, uint64_t n, uint32_t atom, uint32_t stream) {
+    const uint4 w = philox_words(seed, n, atom, stream);
+    const float u1 = ((float)(w.x >> 9) + 0.5f) * 0x1p-23f;
+    const float u2 = (float)(w.y >> 9) * 0x1p-23f;
+    const float u3 = ((float)(w.z >> 9) + 0.5f) * 0x1p-23f;
+    const float u4 = (float)(w.w >> 9) * 0x1p-23f;
+    const float r1 = sqrtf(-2.0f * logf(u1));
+    const float r2 = sqrtf(-2.0f * logf(u3));
+    float s1, c1, s2, c2;
+    sincospif(2.0f * u2, &s1, &c1);
+    sincospif(2.0f * u4, &s2, &c2);
+    return make_float3(r1 * c1, r1 * s1, r2 * c2);
+}
+
+// Uniform in (0, 1] with 53 bits for the acceptance test of step n (stream 1).
+__device__ __forceinline__ double uniform53(uint64_t seed, uint64_t n) {
+    const uint4 w = philox_words(seed, n, 0u, 1u);
+    const unsigned long long m = (unsigned long long)(w.x >> 5) * 67108864ull + (unsigned long long)(w.y >> 6) + 1ull;
+    return (double)m * 0x1p-53;
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-point positions and the membership rule
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t fixpoint(double q, double scale) {
+    const double t = __dmul_rn(q, scale);
+    const double f = floor(t);
+    const long long fi = __double2ll_rz(f);
+    return (uint32_t)(unsigned long long)fi;
+}
+
+__device__ __forceinline__ float disp_axis(uint32_t ui, uint32_t uj, int s, float scale_f) {
+    const long long D = (long long)uj - (long long)ui + (long long)s * 4294967296ll;
+    return __fmul_rn(__ll2float_rn(D), scale_f);
+}
+
+__device__ __forceinline__ float dist2_rule(float dx, float dy, float dz) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+__device__ __forceinline__ int shift_code(int sx, int sy, int sz) { return (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1); }
+
+__device__ __forceinline__ void code_shift(int code, int &sx, int &sy, int &sz) {
+    sx = code % 3 - 1;
+    sy = (code / 3) % 3 - 1;
+    sz = code / 9 - 1;
+}
+
+// Candidate images of atom j seen from atom i along one axis: s = 0 always,
+// plus s = -sign(D0) when D0 != 0 (rc < L excludes every other image).
+// Options are returned in ascending s; n_opt in {1, 2}.
+struct AxisOpts {
+    int s[2];
+    float d[2];
+    int n;
+};
+
+__device__ __forceinline__ AxisOpts axis_opts(uint32_t ui, uint32_t uj, float scale_f, float rc2f) {
+    AxisOpts o;
+    o.n = 0;
+    const long long D0 = (long long)uj - (long long)ui;
+    int cand[2];
+    int nc = 0;
+    if (D0 > 0) { cand[nc++] = -1; cand[nc++] = 0; }
+    else if (D0 < 0) { cand[nc++] = 0; cand[nc++] = 1; }
+    else { cand[nc++] = 0; }
+    for (int c = 0; c < nc; ++c) {
+        const float d = disp_axis(ui, uj, cand[c], scale_f);
+        if (__fmul_rn(d, d) < rc2f) {   // necessary condition for membership
+            o.s[o.n] = cand[c];
+            o.d[o.n] = d;
+            ++o.n;
+        }
+    }
+    return o;
+}
+
+// Displacement of neighbour entry (k, code) from atom with fixed point fi.
+__device__ __forceinline__ float3 entry_disp(uint4 fi, uint4 fk, int code, const Geo &g) {
+    int sx, sy, sz;
+    code_shift(code, sx, sy, sz);
+    return make_float3(disp_axis(fi.x, fk.x, sx, g.scale_f[0]), disp_axis(fi.y, fk.y, sy, g.scale_f[1]),
+                       disp_axis(fi.z, fk.z, sz, g.scale_f[2]));
+}
+
+// ---------------------------------------------------------------------------
+// Small numeric helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float sigmoidf_(float h) { return 1.0f / (1.0f + expf(-h)); }
+__device__ __forceinline__ float siluf_(float h) { return h * sigmoidf_(h); }
+__device__ __forceinline__ float dsiluf_(float h) {
+    const float s = sigmoidf_(h);
+    return s * (1.0f + h * (1.0f - s));
+}
+__device__ __forceinline__ float d2siluf_(float h) {
+    const float s = sigmoidf_(h);
+    return s * (1.0f - s) * (2.0f + h * (1.0f - 2.0f * s));
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Cosine cutoff and its derivative.
+__device__ __forceinline__ void cutoff_fn(float r, float rc, float &fc, float &dfc) {
+    float s, c;
+    sincospif(r / rc, &s, &c);
+    fc = 0.5f * (c + 1.0f);
+    dfc = -0.5f * 3.14159265358979f / rc * s;
+}
+
+// Angular term parameters: zeta in {1,2,4,8} (slowest), lambda in {+1,-1}, eta in {0.005, 0.05} (fastest).
+__device__ __forceinline__ float ang_eta(int a) { return (a & 1) ? 0.05f : 0.005f; }
+__device__ __forceinline__ float ang_lambda(int a) { return ((a >> 1) & 1) ? -1.0f : 1.0f; }
+__device__ __forceinline__ int ang_zeta(int a) { return 1 << (a >> 2); }
+
+}  // namespace lsd

@@ -1,0 +1,52 @@
+// lsd_kernels.h -- host-side launchers of the kernels of liblsd.so (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lsd_common.cuh"
+
+namespace lsd {
+
+// verification (lsd_verify.cu)
+void launch_fixpoint(const double *q, const int *species, int M, const Geo &g, uint4 *fix, cudaStream_t s);
+void launch_neigh_build(const uint4 *fix, int M, const Geo &g, float rmax2f, float near2f, int cap_near, int cap_far,
+                        int *near_keys, int *far_keys, int *n_near, int *n_far, DevState *st, cudaStream_t s);
+void launch_desc(const uint4 *fix, const int *near_keys, const int *n_near, int cap, int M, const Geo &g,
+                 const PotDev &P, float *X, cudaStream_t s);
+void launch_pairgrad(const uint4 *fix, const int *near_keys, const int *n_near, const int *far_keys, const int *n_far,
+                     int cap, int cap_far, int M, const Geo &g, const PotDev &P, const float *dEdX, float4 *pair_g,
+                     float4 *Fpart, float *E_lj, cudaStream_t s);
+void launch_force_gather(const int *near_keys, const int *n_near, int cap, int M, int N, int has_mlp,
+                         const float4 *pair_g, const float4 *Fpart, const float *E_lj, const float *E_mlp, float *F,
+                         float *E_out, DevState *st, cudaStream_t s);
+size_t desc_smem_bytes(int warps, int cap);
+cudaError_t verify_kernels_setup(int max_smem);
+
+// MLP (lsd_mlp.cu)
+void launch_mlp_fp32(const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX, cudaStream_t s);
+size_t mlp_fp32_smem_bytes(const PotDev &P);
+cudaError_t mlp_kernels_setup(int max_smem);
+
+// transport (lsd_transport.cu)
+int transport_atoms_per_block(int N);
+void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *species, const float *Fd,
+                             const float *Ft, const DevState *st, double2 *partials, cudaStream_t s);
+void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
+                             const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
+                             int ec_on, double *q, double *p, DevState *st, const double2 *partials, cudaStream_t s);
+void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
+                      const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
+                      int ec_on, double *q, double *p, DevState *st, double2 *partials, cudaStream_t s);
+
+// draft and plain integrator (lsd_draft.cu)
+size_t draft_small_smem_bytes(int N, const PotDev &P, bool learned);
+void launch_draft_small(bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf, const int *species,
+                        const double *q, const double *p, const float *ec_dF, int ec_on, const DevState *st,
+                        double *w_qmid, double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, cudaStream_t s);
+cudaError_t draft_kernels_setup(int max_smem);
+void launch_plain_half(const Geo &g, const Coef &cf, const int *species, const double *q, const double *p,
+                       const DevState *st, double *qmid, uint4 *fix, cudaStream_t s);
+void launch_plain_finish(const Geo &g, const Coef &cf, const int *species, const double *qmid, const float *F,
+                         double *q, double *p, DevState *st, cudaStream_t s);
+
+}  // namespace lsd

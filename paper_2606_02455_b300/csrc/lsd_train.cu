@@ -1,0 +1,520 @@
+// lsd_train.cu -- learned draft: target-labelled frames and force matching.
+//
+// Frames: every verified window step j contributes (q_mid_j, F_target_j) to a
+// device ring buffer; committed and flushed steps alike, since each is an
+// exact target label at a configuration the dynamics visits.
+//
+// Force matching of the draft E~ = LJ + sum_i y(x_i; theta), y an MLP with
+// one hidden layer and a linear output: loss L = mean_{frames, components}
+// |F~ - F*|^2.  With r = F~ - F* and the descriptor JVP v_i = (dx_i/dq) r,
+// dL/dtheta = -(2/(F*3N)) sum_i d/dtheta [ v_i . dy/dx (x_i) ], which for
+// h = W1 x + b1, t = W1 v is
+//   d/dw_out[u] = t_u SiLU'(h_u)
+//   d/db1[u]    = w_out[u] t_u SiLU''(h_u)
+//   d/dW1[u][f] = w_out[u] (v_f SiLU'(h_u) + t_u SiLU''(h_u) x_f)
+// (the double backward through MLP and descriptors, written out).  One CTA per
+// frame computes the draft forces, the residual, the JVP and the per-weight
+// sums over atoms in a fixed order; a second kernel sums frames in a fixed
+// order and applies Adam.  Everything is FP32 (the BF16 copies are only for
+// inference in the draft kernel).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "lsd.h"
+#include "lsd_common.cuh"
+#include "lsd_train.h"
+
+namespace lsd {
+
+constexpr int kTrainThreads = 256;
+constexpr int kTrainWarps = kTrainThreads / 32;
+constexpr int kTrainCap = 96;
+constexpr int kTrainMaxN = 256;
+
+struct TrainGeo {
+    int N, S, d0, W, n_rbf;
+    float desc_rc, desc_rc2f, lj_rc2f, rc2_all;
+    float rbf_w, rbf_inv2w2, rbf_invw2;
+    int has_lj;
+};
+
+__device__ __forceinline__ void stage_members(const TrainGeo &T, const Geo &g, const uint4 *sfix, int i, float *sr,
+                                              float *sa, int *ssp, const float4 *res, int &n_out) {
+    // members of atom i within the descriptor cutoff, with r and (for the JVP) d-hat . (r_k - r_i)
+    const int lane = threadIdx.x & 31;
+    const uint4 fi = sfix[i];
+    int cnt = 0;
+    for (int base = 0; base < T.N; base += 32) {
+        const int k = base + lane;
+        unsigned m = 0u;
+        AxisOpts ox, oy, oz;
+        ox.n = oy.n = oz.n = 0;
+        if (k < T.N) {
+            const uint4 fk = sfix[k];
+            ox = axis_opts(fi.x, fk.x, g.scale_f[0], T.desc_rc2f);
+            oy = axis_opts(fi.y, fk.y, g.scale_f[1], T.desc_rc2f);
+            oz = axis_opts(fi.z, fk.z, g.scale_f[2], T.desc_rc2f);
+            for (int bz = 0; bz < oz.n; ++bz)
+                for (int by = 0; by < oy.n; ++by)
+                    for (int bx = 0; bx < ox.n; ++bx) {
+                        if (k == i && ox.s[bx] == 0 && oy.s[by] == 0 && oz.s[bz] == 0) continue;
+                        if (dist2_rule(ox.d[bx], oy.d[by], oz.d[bz]) < T.desc_rc2f) m |= 1u << (bx + 2 * by + 4 * bz);
+                    }
+        }
+        const int nm = __popc(m);
+        int sc = nm;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, sc, o);
+            if (lane >= o) sc += t;
+        }
+        const int tot = __shfl_sync(0xffffffffu, sc, 31);
+        int w = cnt + sc - nm;
+        for (int c = 0; c < 8; ++c) {
+            if (!(m & (1u << c))) continue;
+            if (w < kTrainCap) {
+                const float dx = ox.d[c & 1], dy = oy.d[(c >> 1) & 1], dz = oz.d[c >> 2];
+                const float r = sqrtf(dist2_rule(dx, dy, dz));
+                sr[w] = r;
+                ssp[w] = (int)sfix[k].w;
+                if (res) {
+                    const float4 rk = res[k], ri = res[i];
+                    sa[w] = (dx * (rk.x - ri.x) + dy * (rk.y - ri.y) + dz * (rk.z - ri.z)) / r;
+                }
+            }
+            ++w;
+        }
+        cnt += tot;
+    }
+    __syncwarp();
+    n_out = cnt < kTrainCap ? cnt : kTrainCap;
+}
+
+__global__ void __launch_bounds__(kTrainThreads)
+    fm_frame_kernel(TrainGeo T, Geo g, PotDev P, const float *__restrict__ w, const int *__restrict__ species,
+                    const double *__restrict__ fq, const float *__restrict__ fF, long long frame0, long long n_avail,
+                    float scale, float *__restrict__ grad_frames, float *__restrict__ loss_frames) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = T.N, d0 = T.d0, W = T.W;
+    uint4 *sfix = (uint4 *)smraw;
+    float4 *sres = (float4 *)(sfix + N);
+    float *sx = (float *)(sres + N);       // [N][d0]
+    float *sg = sx + (size_t)N * d0;       // [N][d0] dE/dx
+    float *sv = sg + (size_t)N * d0;       // [N][d0] JVP
+    float *sh = sv + (size_t)N * d0;       // [N][W]
+    float *stt = sh + (size_t)N * W;       // [N][W] t = W1 v
+    float *stage = stt + (size_t)N * W;    // per warp 3*kTrainCap
+    float *sloss = stage + (size_t)kTrainWarps * 3 * kTrainCap;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long frame = (frame0 + blockIdx.x) % n_avail;
+    const double *q = fq + (size_t)frame * 3 * N;
+    const float *Fs = fF + (size_t)frame * 3 * N;
+    const float *W1 = w, *b1 = w + (size_t)W * d0, *wo = b1 + W;
+    float *my = stage + (size_t)warp * 3 * kTrainCap;
+    float *sr = my, *sa = my + kTrainCap;
+    int *ssp = (int *)(my + 2 * kTrainCap);
+    for (int i = tid; i < N; i += blockDim.x)
+        sfix[i] = make_uint4(fixpoint(q[3 * i], g.scale[0]), fixpoint(q[3 * i + 1], g.scale[1]),
+                             fixpoint(q[3 * i + 2], g.scale[2]), (unsigned)species[i]);
+    __syncthreads();
+    // A: descriptors, hidden pre-activations, dE/dx
+    for (int i = warp; i < N; i += kTrainWarps) {
+        int n;
+        stage_members(T, g, sfix, i, sr, sa, ssp, nullptr, n);
+        float acc[kMaxSpecies];
+#pragma unroll
+        for (int s = 0; s < kMaxSpecies; ++s) acc[s] = 0.f;
+        const int kb = lane & 15;
+        if (kb < T.n_rbf) {
+            const float mu = (float)kb * T.rbf_w;
+            for (int p = lane >> 4; p < n; p += 2) {
+                float fc, dfc;
+                cutoff_fn(sr[p], T.desc_rc, fc, dfc);
+                const float t = sr[p] - mu;
+                const float v = expf(-t * t * T.rbf_inv2w2) * fc;
+#pragma unroll
+                for (int s = 0; s < kMaxSpecies; ++s) acc[s] += (ssp[p] == s) ? v : 0.f;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < kMaxSpecies; ++s) acc[s] += __shfl_down_sync(0xffffffffu, acc[s], 16);
+        float *x = sx + (size_t)i * d0;
+        for (int f = lane; f < d0; f += 32) x[f] = 0.f;
+        __syncwarp();
+        if (lane < T.n_rbf)
+            for (int s = 0; s < T.S; ++s) x[s * T.n_rbf + lane] = acc[s];
+        if (lane == 0) x[T.S * T.n_rbf + (int)sfix[i].w] = 1.f;
+        __syncwarp();
+        float gu = 0.f;
+        if (lane < W) {
+            float h = b1[lane];
+            for (int f = 0; f < d0; ++f) h = fmaf(W1[(size_t)lane * d0 + f], x[f], h);
+            sh[(size_t)i * W + lane] = h;
+            gu = wo[lane] * dsiluf_(h);
+        }
+        for (int f = 0; f < d0; ++f) {
+            const float vv = warp_sum(lane < W ? W1[(size_t)lane * d0 + f] * gu : 0.f);
+            if (lane == 0) sg[(size_t)i * d0 + f] = vv;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // B: draft forces and residual
+    float lossw = 0.f;
+    for (int i = warp; i < N; i += kTrainWarps) {
+        const uint4 fi = sfix[i];
+        const int si = (int)fi.w;
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        for (int k = lane; k < N; k += 32) {
+            const uint4 fk = sfix[k];
+            const AxisOpts ox = axis_opts(fi.x, fk.x, g.scale_f[0], T.rc2_all);
+            if (!ox.n) continue;
+            const AxisOpts oy = axis_opts(fi.y, fk.y, g.scale_f[1], T.rc2_all);
+            if (!oy.n) continue;
+            const AxisOpts oz = axis_opts(fi.z, fk.z, g.scale_f[2], T.rc2_all);
+            const int pr = si * g.S + (int)fk.w;
+            for (int bz = 0; bz < oz.n; ++bz)
+                for (int by = 0; by < oy.n; ++by)
+                    for (int bx = 0; bx < ox.n; ++bx) {
+                        if (k == i && ox.s[bx] == 0 && oy.s[by] == 0 && oz.s[bz] == 0) continue;
+                        const float dx = ox.d[bx], dy = oy.d[by], dz = oz.d[bz];
+                        const float d2 = dist2_rule(dx, dy, dz);
+                        if (T.has_lj && d2 < T.lj_rc2f) {
+                            const float s2 = P.lj_sig2[pr] / d2;
+                            const float s6 = s2 * s2 * s2, s12 = s6 * s6;
+                            const float fr = -P.lj_eps24[pr] * (2.f * s12 - s6) / d2;
+                            fx += fr * dx;
+                            fy += fr * dy;
+                            fz += fr * dz;
+                        }
+                        if (d2 < T.desc_rc2f) {
+                            const float r = sqrtf(d2);
+                            float fc, dfc;
+                            cutoff_fn(r, T.desc_rc, fc, dfc);
+                            const float *gi = sg + (size_t)i * d0 + (int)fk.w * T.n_rbf;
+                            const float *gk = sg + (size_t)k * d0 + si * T.n_rbf;
+                            float c = 0.f;
+                            for (int b = 0; b < T.n_rbf; ++b) {
+                                const float t = r - (float)b * T.rbf_w;
+                                c += (gi[b] + gk[b]) * expf(-t * t * T.rbf_inv2w2) * (-t * T.rbf_invw2 * fc + dfc);
+                            }
+                            fx += c * dx / r;
+                            fy += c * dy / r;
+                            fz += c * dz / r;
+                        }
+                    }
+        }
+        fx = warp_sum(fx);
+        fy = warp_sum(fy);
+        fz = warp_sum(fz);
+        if (lane == 0) {
+            const float rx = fx - Fs[3 * i], ry = fy - Fs[3 * i + 1], rz = fz - Fs[3 * i + 2];
+            sres[i] = make_float4(rx, ry, rz, 0.f);
+            lossw += rx * rx + ry * ry + rz * rz;
+        }
+    }
+    if (lane == 0) sloss[warp] = lossw;
+    __syncthreads();
+    // C: JVP v_i and t_i = W1 v_i
+    for (int i = warp; i < N; i += kTrainWarps) {
+        int n;
+        stage_members(T, g, sfix, i, sr, sa, ssp, sres, n);
+        float acc[kMaxSpecies];
+#pragma unroll
+        for (int s = 0; s < kMaxSpecies; ++s) acc[s] = 0.f;
+        const int kb = lane & 15;
+        if (kb < T.n_rbf) {
+            const float mu = (float)kb * T.rbf_w;
+            for (int p = lane >> 4; p < n; p += 2) {
+                float fc, dfc;
+                cutoff_fn(sr[p], T.desc_rc, fc, dfc);
+                const float t = sr[p] - mu;
+                const float dg = expf(-t * t * T.rbf_inv2w2) * (-t * T.rbf_invw2 * fc + dfc);
+#pragma unroll
+                for (int s = 0; s < kMaxSpecies; ++s) acc[s] += (ssp[p] == s) ? dg * sa[p] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < kMaxSpecies; ++s) acc[s] += __shfl_down_sync(0xffffffffu, acc[s], 16);
+        float *v = sv + (size_t)i * d0;
+        for (int f = lane; f < d0; f += 32) v[f] = 0.f;
+        __syncwarp();
+        if (lane < T.n_rbf)
+            for (int s = 0; s < T.S; ++s) v[s * T.n_rbf + lane] = acc[s];
+        __syncwarp();
+        if (lane < W) {
+            float t = 0.f;
+            for (int f = 0; f < d0; ++f) t = fmaf(W1[(size_t)lane * d0 + f], v[f], t);
+            stt[(size_t)i * W + lane] = t;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // D: per-weight sums over atoms in order
+    const int nw = W * d0 + 2 * W + 1;
+    float *gout = grad_frames + (size_t)blockIdx.x * nw;
+    for (int e = tid; e < nw; e += blockDim.x) {
+        float acc = 0.f;
+        if (e < W * d0) {
+            const int u = e / d0, f = e - u * d0;
+            for (int i = 0; i < N; ++i) {
+                const float h = sh[(size_t)i * W + u];
+                acc += wo[u] * (sv[(size_t)i * d0 + f] * dsiluf_(h) + stt[(size_t)i * W + u] * d2siluf_(h) *
+                                                                          sx[(size_t)i * d0 + f]);
+            }
+        } else if (e < W * d0 + W) {
+            const int u = e - W * d0;
+            for (int i = 0; i < N; ++i) acc += wo[u] * stt[(size_t)i * W + u] * d2siluf_(sh[(size_t)i * W + u]);
+        } else if (e < W * d0 + 2 * W) {
+            const int u = e - W * d0 - W;
+            for (int i = 0; i < N; ++i) acc += stt[(size_t)i * W + u] * dsiluf_(sh[(size_t)i * W + u]);
+        }
+        gout[e] = scale * acc;
+    }
+    if (tid == 0) {
+        float l = 0.f;
+        for (int k = 0; k < kTrainWarps; ++k) l += sloss[k];
+        loss_frames[blockIdx.x] = -0.5f * scale * l;   // scale = -2/(F*3N)
+    }
+}
+
+__global__ void fm_reduce_kernel(const float *__restrict__ grad_frames, const float *__restrict__ loss_frames,
+                                 int n_frames, int nw, float *__restrict__ grad, float *__restrict__ loss) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nw) {
+        float s = 0.f;
+        for (int f = 0; f < n_frames; ++f) s += grad_frames[(size_t)f * nw + e];
+        grad[e] = s;
+    }
+    if (e == 0) {
+        float l = 0.f;
+        for (int f = 0; f < n_frames; ++f) l += loss_frames[f];
+        *loss = l;
+    }
+}
+
+__global__ void adam_kernel(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
+                            const float *__restrict__ grad, int nw, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nw) return;
+    const float gr = grad[e];
+    const float mm = b1 * m[e] + (1.f - b1) * gr;
+    const float vv = b2 * v[e] + (1.f - b2) * gr * gr;
+    m[e] = mm;
+    v[e] = vv;
+    w[e] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+}
+
+__global__ void frame_capture_kernel(const double *__restrict__ w_qmid, const float *__restrict__ w_Ft, int K, int N,
+                                     long long cap, long long start_windows, const DevState *__restrict__ st,
+                                     double *__restrict__ fq, float *__restrict__ fF) {
+    if (st->step >= st->target_step) return;
+    const int j = blockIdx.y;
+    const long long slot = ((st->windows - start_windows) * K + j) % cap;
+    const int D = 3 * N;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < D; e += gridDim.x * blockDim.x) {
+        fq[slot * D + e] = w_qmid[(size_t)j * D + e];
+        fF[slot * D + e] = w_Ft[(size_t)j * D + e];
+    }
+}
+
+// ---------------------------------------------------------------------------
+static TrainGeo make_tgeo(const TrainState &t, const PotDev &P) {
+    TrainGeo T{};
+    T.N = t.N;
+    T.S = t.S;
+    T.d0 = t.d0;
+    T.W = t.W;
+    T.n_rbf = P.n_rbf;
+    T.desc_rc = P.desc_rc;
+    T.desc_rc2f = P.desc_rc2f;
+    T.lj_rc2f = P.lj_rc2f;
+    T.rc2_all = fmaxf(P.lj_rc2f, P.desc_rc2f);
+    T.rbf_w = P.rbf_w;
+    T.rbf_inv2w2 = P.rbf_inv2w2;
+    T.rbf_invw2 = P.rbf_invw2;
+    T.has_lj = P.has_lj;
+    return T;
+}
+
+static size_t fm_smem(const TrainState &t) {
+    return (size_t)t.N * (sizeof(uint4) + sizeof(float4)) +
+           ((size_t)t.N * (3 * t.d0 + 2 * t.W) + (size_t)kTrainWarps * 3 * kTrainCap + kTrainWarps) * sizeof(float);
+}
+
+int train_init(TrainState &t, const PotDev &P, const std::vector<float> &weights, int N) {
+    t.enabled = P.kind == LSD_POT_LEARNED && P.has_mlp;
+    if (!t.enabled) return LSD_OK;
+    t.N = N;
+    t.S = (P.d0 - P.n_ang) / (P.n_rbf + 1);
+    t.d0 = P.d0;
+    t.W = P.width;
+    t.n_rbf = P.n_rbf;
+    t.n_weights = weights.size();
+    if (cudaMalloc(&t.w, t.n_weights * sizeof(float)) != cudaSuccess) return LSD_ENOMEM;
+    if (cudaMalloc(&t.m, t.n_weights * sizeof(float)) != cudaSuccess) return LSD_ENOMEM;
+    if (cudaMalloc(&t.v, t.n_weights * sizeof(float)) != cudaSuccess) return LSD_ENOMEM;
+    if (cudaMalloc(&t.grad, t.n_weights * sizeof(float)) != cudaSuccess) return LSD_ENOMEM;
+    if (cudaMalloc(&t.loss, sizeof(float)) != cudaSuccess) return LSD_ENOMEM;
+    cudaMemset(t.m, 0, t.n_weights * sizeof(float));
+    cudaMemset(t.v, 0, t.n_weights * sizeof(float));
+    if (cudaMemcpy(t.w, weights.data(), t.n_weights * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+        return LSD_ECUDA;
+    if (N <= kTrainMaxN &&
+        cudaFuncSetAttribute(fm_frame_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024) != cudaSuccess)
+        return LSD_ECUDA;
+    return LSD_OK;
+}
+
+void train_free(TrainState &t) {
+    for (void *p : {(void *)t.w, (void *)t.m, (void *)t.v, (void *)t.grad, (void *)t.loss, (void *)t.fq, (void *)t.fF,
+                    (void *)t.grad_frames, (void *)t.loss_frames})
+        if (p) cudaFree(p);
+    t = TrainState{};
+}
+
+int train_set_weights(TrainState &t, const std::vector<float> &w) {
+    if (!t.enabled) return LSD_OK;
+    if (w.size() != t.n_weights) return LSD_EINVAL;
+    if (cudaMemcpy(t.w, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return LSD_ECUDA;
+    return LSD_OK;
+}
+
+int train_get_weights(TrainState &t, std::vector<float> &w, cudaStream_t s) {
+    if (!t.enabled) return LSD_EINVAL;
+    w.resize(t.n_weights);
+    if (cudaMemcpyAsync(w.data(), t.w, t.n_weights * sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return LSD_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LSD_ECUDA;
+    return LSD_OK;
+}
+
+int train_set_capture(TrainState &t, long long capacity, int N) {
+    if (t.fq) cudaFree(t.fq);
+    if (t.fF) cudaFree(t.fF);
+    t.fq = nullptr;
+    t.fF = nullptr;
+    t.capture_on = capacity > 0;
+    t.capacity = capacity;
+    t.N = N;
+    if (!t.capture_on) return LSD_OK;
+    if (cudaMalloc(&t.fq, (size_t)capacity * 3 * N * sizeof(double)) != cudaSuccess) return LSD_ENOMEM;
+    if (cudaMalloc(&t.fF, (size_t)capacity * 3 * N * sizeof(float)) != cudaSuccess) return LSD_ENOMEM;
+    // frames are counted from the current window counter
+    if (t.st) {
+        DevState s;
+        if (cudaMemcpy(&s, t.st, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess) return LSD_ECUDA;
+        t.start_windows = s.windows;
+    }
+    return LSD_OK;
+}
+
+int train_frame_count(TrainState &t, int64_t *n, cudaStream_t s) {
+    *n = 0;
+    if (!t.capture_on || !t.st) return LSD_OK;
+    DevState ds;
+    if (cudaMemcpyAsync(&ds, t.st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LSD_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LSD_ECUDA;
+    const long long f = (ds.windows - t.start_windows) * (long long)t.K;
+    *n = f < t.capacity ? f : t.capacity;
+    return LSD_OK;
+}
+
+void enqueue_frame_capture(TrainState &t, const double *w_qmid, const float *w_Ft, int K, int N, DevState *st,
+                           cudaStream_t s) {
+    t.K = K;
+    t.st = st;
+    const int D = 3 * N;
+    const int bx = (D + 255) / 256 < 64 ? (D + 255) / 256 : 64;
+    frame_capture_kernel<<<dim3(bx, K), 256, 0, s>>>(w_qmid, w_Ft, K, N, t.capacity, t.start_windows, st, t.fq, t.fF);
+}
+
+size_t train_adam_size(const TrainState &t) { return t.enabled ? t.n_weights : 0; }
+
+int train_adam_get(TrainState &t, float *m, float *v) {
+    if (!t.enabled) return LSD_OK;
+    if (cudaMemcpy(m, t.m, t.n_weights * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return LSD_ECUDA;
+    if (cudaMemcpy(v, t.v, t.n_weights * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return LSD_ECUDA;
+    return LSD_OK;
+}
+
+int train_adam_set(TrainState &t, const float *m, const float *v) {
+    if (!t.enabled) return LSD_OK;
+    if (cudaMemcpy(t.m, m, t.n_weights * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return LSD_ECUDA;
+    if (cudaMemcpy(t.v, v, t.n_weights * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return LSD_ECUDA;
+    return LSD_OK;
+}
+
+static int ensure_frame_bufs(TrainState &t, int n_frames) {
+    if (n_frames <= t.max_frames) return LSD_OK;
+    if (t.grad_frames) cudaFree(t.grad_frames);
+    if (t.loss_frames) cudaFree(t.loss_frames);
+    t.grad_frames = nullptr;
+    t.loss_frames = nullptr;
+    if (cudaMalloc(&t.grad_frames, (size_t)n_frames * t.n_weights * sizeof(float)) != cudaSuccess) return LSD_ENOMEM;
+    if (cudaMalloc(&t.loss_frames, (size_t)n_frames * sizeof(float)) != cudaSuccess) return LSD_ENOMEM;
+    t.max_frames = n_frames;
+    return LSD_OK;
+}
+
+static int fm_launch(TrainState &t, const Geo &g, const PotDev &P, const int *species, const double *fq,
+                     const float *fF, long long frame0, long long n_avail, int n_frames, cudaStream_t s) {
+    if (t.N > kTrainMaxN || P.n_layers != 1 || P.n_ang != 0 || t.W > 32) return LSD_EUNSUPPORTED;
+    int r = ensure_frame_bufs(t, n_frames);
+    if (r != LSD_OK) return r;
+    const TrainGeo T = make_tgeo(t, P);
+    const float scale = -2.0f / ((float)n_frames * 3.0f * (float)t.N);
+    fm_frame_kernel<<<n_frames, kTrainThreads, fm_smem(t), s>>>(T, g, P, t.w, species, fq, fF, frame0, n_avail, scale,
+                                                               t.grad_frames, t.loss_frames);
+    const int nw = (int)t.n_weights;
+    fm_reduce_kernel<<<(nw + 255) / 256, 256, 0, s>>>(t.grad_frames, t.loss_frames, n_frames, nw, t.grad, t.loss);
+    return cudaGetLastError() == cudaSuccess ? LSD_OK : LSD_ECUDA;
+}
+
+int train_force_match(TrainState &t, const Geo &g, const PotDev &P, const int *species, const double *fq,
+                      const float *fF, int n_frames, float *loss_out, float *grad_dev, cudaStream_t s) {
+    if (!t.enabled) return LSD_EINVAL;
+    int r = fm_launch(t, g, P, species, fq, fF, 0, n_frames, n_frames, s);
+    if (r != LSD_OK) return r;
+    if (grad_dev &&
+        cudaMemcpyAsync(grad_dev, t.grad, t.n_weights * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return LSD_ECUDA;
+    float l = 0.f;
+    if (cudaMemcpyAsync(&l, t.loss, sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LSD_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LSD_ECUDA;
+    if (loss_out) *loss_out = l;
+    return LSD_OK;
+}
+
+int train_run(TrainState &t, const Geo &g, const PotDev &P, const int *species, int n_iters, float lr,
+              int frames_per_iter, float *loss_out, cudaStream_t s) {
+    if (!t.enabled) return LSD_EINVAL;
+    int64_t avail = 0;
+    int r = train_frame_count(t, &avail, s);
+    if (r != LSD_OK) return r;
+    if (avail < 1) return LSD_ESTATE;
+    const int fpi = (frames_per_iter <= 0 || frames_per_iter > avail) ? (int)avail : frames_per_iter;
+    const int nw = (int)t.n_weights;
+    for (int it = 0; it < n_iters; ++it) {
+        const long long frame0 = (t.iter * (long long)fpi) % avail;
+        r = fm_launch(t, g, P, species, t.fq, t.fF, frame0, avail, fpi, s);
+        if (r != LSD_OK) return r;
+        ++t.adam_t;
+        ++t.iter;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - powf(b1, (float)t.adam_t), c2 = 1.f - powf(b2, (float)t.adam_t);
+        adam_kernel<<<(nw + 255) / 256, 256, 0, s>>>(t.w, t.m, t.v, t.grad, nw, lr, b1, b2, 1e-8f, c1, c2);
+    }
+    if (loss_out) {
+        float l = 0.f;
+        if (cudaMemcpyAsync(&l, t.loss, sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LSD_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return LSD_ECUDA;
+        *loss_out = l;
+    }
+    return cudaStreamSynchronize(s) == cudaSuccess ? LSD_OK : LSD_ECUDA;
+}
+
+}  // namespace lsd

@@ -1,0 +1,202 @@
+// lsd_transport.cu -- reflectionVerify (Eq. 5) on every window step, the first
+// rejection (Alg. 1), and the rollback/commit of the state.
+//
+// With z = S^-1/2 (p~ - <p~>) = xi (the draft's own noise, regenerated from
+// its counter) and delta = S^-1/2 (<p~> - <p>) = (1+c1)(dt/2) kappa (F~ - F)/sigma
+// (the c1 p terms of both means cancel), the log density ratio is
+// log r = -z.delta - |delta|^2/2; a step is accepted iff log u <= min(0, log r).
+// A rejected step's momentum is <p> + sigma (z - 2 (z.delta/delta.delta) delta)
+// and its position q_mid + (dt/2) p/m (the shared map g = A of Thm 3.1).
+//
+// transport_reduce_kernel: per (chunk of atoms, window step) FP64 partial sums
+//   of z.delta and delta.delta, written to a fixed slot (no atomics).
+// transport_commit_kernel: every CTA sums the partials in the same fixed
+//   order, finds l = first rejected step, and commits its slice of atoms:
+//   the draft's own bits for an accepted step, the reflection for a rejected
+//   one.  The last CTA to finish advances the step counter and statistics.
+#include "lsd_common.cuh"
+#include "lsd_kernels.h"
+
+namespace lsd {
+
+constexpr int kTransThreads = 256;
+
+__device__ __forceinline__ double block_sum_d(double v, double *sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum_d(v);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < nw; ++k) t += sh[k];
+    return t;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kTransThreads)
+    transport_reduce_kernel(int K, Geo g, Coef cf, const int *__restrict__ species, const float *__restrict__ Fd,
+                            const float *__restrict__ Ft, const DevState *__restrict__ st, double2 *__restrict__ partials,
+                            int atoms_per_block) {
+    __shared__ double sh[32];
+    if (st->step >= st->target_step) return;
+    const int N = g.N;
+    const int j = blockIdx.y;
+    const unsigned long long n = (unsigned long long)(st->step + j + 1);
+    const int a0 = blockIdx.x * atoms_per_block;
+    const int a1 = min(N, a0 + atoms_per_block);
+    double s = 0.0, d = 0.0;
+    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+        const float3 xi = normals3(cf.seed, n, (uint32_t)i, 0u);
+        const double k = cf.aF_sig[species[i]];
+        const size_t o = ((size_t)j * N + i) * 3;
+        const double d0 = k * ((double)Fd[o + 0] - (double)Ft[o + 0]);
+        const double d1 = k * ((double)Fd[o + 1] - (double)Ft[o + 1]);
+        const double d2 = k * ((double)Fd[o + 2] - (double)Ft[o + 2]);
+        s += (double)xi.x * d0 + (double)xi.y * d1 + (double)xi.z * d2;
+        d += d0 * d0 + d1 * d1 + d2 * d2;
+    }
+    const double S = block_sum_d(s, sh);
+    const double D = block_sum_d(d, sh);
+    if (threadIdx.x == 0) partials[(size_t)j * gridDim.x + blockIdx.x] = make_double2(S, D);
+}
+
+__global__ void __launch_bounds__(kTransThreads)
+    transport_commit_kernel(int K, Geo g, Coef cf, const int *__restrict__ species, const double *__restrict__ w_qmid,
+                            const double *__restrict__ w_pdraft, const float *__restrict__ Fd,
+                            const float *__restrict__ Ft, const float *__restrict__ Fraw, float *__restrict__ ec_dF,
+                            int ec_on, double *__restrict__ q, double *__restrict__ p, DevState *__restrict__ st,
+                            const double2 *__restrict__ partials, int n_part, int atoms_per_block) {
+    __shared__ double s_s[kMaxK], s_d[kMaxK], s_lr[kMaxK], s_lu[kMaxK];
+    __shared__ int s_acc[kMaxK];
+    __shared__ int s_nc, s_rej, s_l, s_bad;
+    __shared__ bool s_last;
+    if (st->step >= st->target_step) return;
+    const int N = g.N;
+    const long long n0 = st->step;
+    const long long rem = st->target_step - n0;
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        double s = 0.0, d = 0.0;
+        for (int b = 0; b < n_part; ++b) {
+            const double2 v = partials[(size_t)j * n_part + b];
+            s += v.x;
+            d += v.y;
+        }
+        s_s[j] = s;
+        s_d[j] = d;
+        const double lr = -s - 0.5 * d;
+        const double lu = log(uniform53(cf.seed, (unsigned long long)(n0 + j + 1)));
+        s_lr[j] = lr;
+        s_lu[j] = lu;
+        s_acc[j] = (d == 0.0) || (lu <= fmin(0.0, lr));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int l = K, rej = 0, bad = 0;
+        for (int j = 0; j < K; ++j) {
+            if (!isfinite(s_lr[j])) { bad = 1; l = j + 1; break; }
+            if (!s_acc[j]) { l = j + 1; rej = 1; break; }
+        }
+        const int nc = (long long)l < rem ? l : (int)rem;
+        s_l = l;
+        s_nc = bad ? 0 : nc;
+        s_rej = (rej && nc == l) ? 1 : 0;
+        s_bad = bad;
+    }
+    __syncthreads();
+    const int nc = s_nc;
+    if (nc > 0) {
+        const int jj = nc - 1;
+        const size_t D = (size_t)3 * N;
+        const double factor = s_rej ? 2.0 * s_s[jj] / s_d[jj] : 0.0;
+        const unsigned long long n = (unsigned long long)(n0 + jj + 1);
+        const int a0 = blockIdx.x * atoms_per_block;
+        const int a1 = min(N, a0 + atoms_per_block);
+        for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+            const int sp = species[i];
+            const double hm = cf.hm[sp];
+            float3 xi = make_float3(0.f, 0.f, 0.f);
+            if (s_rej) xi = normals3(cf.seed, n, (uint32_t)i, 0u);
+            const float xs[3] = {xi.x, xi.y, xi.z};
+            for (int c = 0; c < 3; ++c) {
+                const size_t o = (size_t)jj * D + (size_t)3 * i + c;
+                double pn;
+                if (s_rej) {
+                    const double pprev = jj == 0 ? p[3 * i + c] : w_pdraft[o - D];
+                    const double mu = __dadd_rn(__dmul_rn(cf.c1, pprev), __dmul_rn(cf.aF, (double)Ft[o]));
+                    const double dl = cf.aF_sig[sp] * ((double)Fd[o] - (double)Ft[o]);
+                    pn = mu + cf.sig[sp] * ((double)xs[c] - factor * dl);
+                } else {
+                    pn = w_pdraft[o];
+                }
+                p[3 * i + c] = pn;
+                q[3 * i + c] = __dadd_rn(w_qmid[o], __dmul_rn(pn, hm));
+                if (ec_on) ec_dF[3 * i + c] = Ft[o] - Fraw[o];
+            }
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(&st->blocks_done, 1u);
+        s_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        st->blocks_done = 0u;
+        st->n_commit_last = nc;
+        st->first_reject_last = s_rej || (s_l <= K && !s_acc[s_l - 1]) ? s_l : -1;
+        if (s_bad) atomicOr(&st->err, 2);
+        st->windows += 1;
+        st->verified += K;
+        st->committed += nc;
+        st->rejected += s_rej;
+        double sd = 0.0, sp = 0.0;
+        for (int j = 0; j < nc; ++j) {
+            const double dn = sqrt(s_d[j]);
+            sd += dn;
+            sp += erf(dn / sqrt(8.0));
+        }
+        st->sum_delta += sd;
+        st->sum_pred += sp;
+        for (int j = 0; j < K; ++j) {
+            st->accept[j] = s_acc[j];
+            st->logr[j] = s_lr[j];
+            st->logu[j] = s_lu[j];
+            st->dnorm[j] = sqrt(s_d[j]);
+        }
+        st->step = n0 + nc;
+    }
+}
+
+void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *species, const float *Fd,
+                             const float *Ft, const DevState *st, double2 *partials, cudaStream_t s) {
+    const int apb = transport_atoms_per_block(g.N);
+    const int nb = (g.N + apb - 1) / apb;
+    transport_reduce_kernel<<<dim3(nb, K), kTransThreads, 0, s>>>(K, g, cf, species, Fd, Ft, st, partials, apb);
+}
+
+void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
+                             const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
+                             int ec_on, double *q, double *p, DevState *st, const double2 *partials, cudaStream_t s) {
+    const int apb = transport_atoms_per_block(g.N);
+    const int nb = (g.N + apb - 1) / apb;
+    transport_commit_kernel<<<nb, kTransThreads, 0, s>>>(K, g, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF,
+                                                         ec_on, q, p, st, partials, nb, apb);
+}
+
+void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
+                      const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
+                      int ec_on, double *q, double *p, DevState *st, double2 *partials, cudaStream_t s) {
+    launch_transport_reduce(K, g, cf, species, Fd, Ft, st, partials, s);
+    launch_transport_commit(K, g, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, st, partials, s);
+}
+
+int transport_atoms_per_block(int N) {
+    // at least one CTA per 1024 atoms, at most 148*4 CTAs per window step
+    int apb = 1024;
+    while ((N + apb - 1) / apb > 592 && apb < (1 << 20)) apb *= 2;
+    return apb;
+}
+
+}  // namespace lsd

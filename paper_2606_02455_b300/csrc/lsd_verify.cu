@@ -1,0 +1,450 @@
+// lsd_verify.cu -- batched target force evaluation over a whole window
+// (Alg. 2 verify_step's TargetModel.get_forces, run on all K*N atoms at once).
+//
+// Rows are (window step j, atom i), row = j*N + i.  Per row:
+//   neigh_build_kernel   canonical neighbour lists (descriptor cutoff part and
+//                        the rest up to the LJ cutoff), packed (k << 5 | code)
+//   desc_kernel          radial + angular descriptors X[row][d0p]
+//   (lsd_mlp.cu)         per-atom MLP energy and dE/dX
+//   pairgrad_kernel      g_p = dE_i/d(r_p) for every descriptor neighbour p,
+//                        its sum, and the LJ pair forces
+//   force_gather_kernel  F_i = sum_p g_{i,p} - sum_p g_{k_p, rev(p)} + F_LJ,
+//                        rev(p) found by binary search in the sorted list of k_p
+// Everything is a gather in a fixed order: forces are bitwise deterministic.
+#include "lsd_common.cuh"
+#include "lsd_kernels.h"
+
+namespace lsd {
+
+// ---------------------------------------------------------------------------
+// Neighbour lists: one warp per row, all candidate atoms of the same window
+// step, lanes over candidates.  Members of one candidate are kept in shift
+// code order and lanes are compacted in order, so each row comes out sorted
+// by (k, code) without a sort.
+// ---------------------------------------------------------------------------
+__global__ void neigh_build_kernel(const uint4 *__restrict__ fix, int M, Geo g, float rmax2f, float near2f,
+                                   int cap_near, int cap_far, int *__restrict__ near_keys, int *__restrict__ far_keys,
+                                   int *__restrict__ n_near, int *__restrict__ n_far, DevState *st) {
+    const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= M) return;
+    const int N = g.N;
+    const int j = row / N, i = row - j * N;
+    const uint4 *fj = fix + (size_t)j * N;
+    const uint4 fi = fj[i];
+    int *nk = near_keys + (size_t)row * cap_near;
+    int *fk = far_keys + (size_t)row * cap_far;
+    int cn = 0, cf = 0;
+    for (int base = 0; base < N; base += 32) {
+        const int k = base + lane;
+        unsigned mn = 0u, mf = 0u;
+        AxisOpts ox, oy, oz;
+        ox.n = oy.n = oz.n = 0;
+        if (k < N) {
+            const uint4 fkk = fj[k];
+            ox = axis_opts(fi.x, fkk.x, g.scale_f[0], rmax2f);
+            oy = axis_opts(fi.y, fkk.y, g.scale_f[1], rmax2f);
+            oz = axis_opts(fi.z, fkk.z, g.scale_f[2], rmax2f);
+            for (int bz = 0; bz < oz.n; ++bz)
+                for (int by = 0; by < oy.n; ++by)
+                    for (int bx = 0; bx < ox.n; ++bx) {
+                        if (k == i && ox.s[bx] == 0 && oy.s[by] == 0 && oz.s[bz] == 0) continue;
+                        const float d2 = dist2_rule(ox.d[bx], oy.d[by], oz.d[bz]);
+                        const unsigned bit = 1u << (bx + 2 * by + 4 * bz);
+                        if (d2 < rmax2f) {
+                            if (d2 < near2f) mn |= bit;
+                            else mf |= bit;
+                        }
+                    }
+        }
+        const int nn = __popc(mn), nf = __popc(mf);
+        int sn = nn, sf = nf;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int tn = __shfl_up_sync(0xffffffffu, sn, o);
+            const int tf = __shfl_up_sync(0xffffffffu, sf, o);
+            if (lane >= o) { sn += tn; sf += tf; }
+        }
+        const int tot_n = __shfl_sync(0xffffffffu, sn, 31), tot_f = __shfl_sync(0xffffffffu, sf, 31);
+        int wn = cn + sn - nn, wf = cf + sf - nf;
+        for (int c = 0; c < 8; ++c) {
+            const unsigned bit = 1u << c;
+            if (!((mn | mf) & bit)) continue;
+            const int bx = c & 1, by = (c >> 1) & 1, bz = c >> 2;
+            const int key = (k << 5) | shift_code(ox.s[bx], oy.s[by], oz.s[bz]);
+            if (mn & bit) {
+                if (wn < cap_near) nk[wn] = key;
+                ++wn;
+            } else {
+                if (wf < cap_far) fk[wf] = key;
+                ++wf;
+            }
+        }
+        cn += tot_n;
+        cf += tot_f;
+    }
+    if (lane == 0) {
+        n_near[row] = cn < cap_near ? cn : cap_near;
+        n_far[row] = cf < cap_far ? cf : cap_far;
+        if (cn > cap_near || cf > cap_far) atomicOr(&st->err, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-warp staging of a row's descriptor neighbours in shared memory.
+// ---------------------------------------------------------------------------
+struct NbStage {
+    float *dx, *dy, *dz, *r, *fc, *dfc, *e1, *e2;
+    int *sp;
+};
+
+__device__ __forceinline__ NbStage nb_stage_ptrs(float *base, int cap) {
+    NbStage s;
+    s.dx = base;
+    s.dy = base + cap;
+    s.dz = base + 2 * cap;
+    s.r = base + 3 * cap;
+    s.fc = base + 4 * cap;
+    s.dfc = base + 5 * cap;
+    s.e1 = base + 6 * cap;
+    s.e2 = base + 7 * cap;
+    s.sp = (int *)(base + 8 * cap);
+    return s;
+}
+constexpr int kStageFloats = 9;
+
+__device__ __forceinline__ void nb_stage_load(const NbStage &S, const uint4 *fj, uint4 fi, const int *keys, int n,
+                                              const Geo &g, float rc, int lane) {
+    for (int p = lane; p < n; p += 32) {
+        const int key = keys[p];
+        const uint4 fk = fj[key >> 5];
+        const float3 d = entry_disp(fi, fk, key & 31, g);
+        const float r2 = dist2_rule(d.x, d.y, d.z);
+        const float r = sqrtf(r2);
+        float fc, dfc;
+        cutoff_fn(r, rc, fc, dfc);
+        S.dx[p] = d.x;
+        S.dy[p] = d.y;
+        S.dz[p] = d.z;
+        S.r[p] = r;
+        S.fc[p] = fc;
+        S.dfc[p] = dfc;
+        S.e1[p] = expf(-0.005f * r2);
+        S.e2[p] = expf(-0.05f * r2);
+        S.sp[p] = (int)fk.w;
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Descriptors: radial by lanes over basis functions (two halves over
+// neighbours), angular by lanes over neighbour pairs, warp reductions.
+// ---------------------------------------------------------------------------
+__global__ void desc_kernel(const uint4 *__restrict__ fix, const int *__restrict__ near_keys,
+                            const int *__restrict__ n_near, int cap, int M, Geo g, PotDev P, float *__restrict__ X) {
+    extern __shared__ float smem[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (row >= M) return;
+    const int N = g.N;
+    const int j = row / N, i = row - j * N;
+    const uint4 *fj = fix + (size_t)j * N;
+    const uint4 fi = fj[i];
+    NbStage S = nb_stage_ptrs(smem + (size_t)wib * kStageFloats * cap, cap);
+    const int n = n_near[row];
+    nb_stage_load(S, fj, fi, near_keys + (size_t)row * cap, n, g, P.desc_rc, lane);
+    float *x = X + (size_t)row * P.d0p;
+    const int nr = P.n_rbf;
+    // radial
+    {
+        float acc[kMaxSpecies];
+#pragma unroll
+        for (int s = 0; s < kMaxSpecies; ++s) acc[s] = 0.f;
+        const int kb = lane & 15;
+        if (kb < nr) {
+            const float mu = (float)kb * P.rbf_w;
+            for (int p = lane >> 4; p < n; p += 2) {
+                const float t = S.r[p] - mu;
+                const float v = expf(-t * t * P.rbf_inv2w2) * S.fc[p];
+                const int sp = S.sp[p];
+#pragma unroll
+                for (int s = 0; s < kMaxSpecies; ++s) acc[s] += (sp == s) ? v : 0.f;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < kMaxSpecies; ++s) acc[s] += __shfl_down_sync(0xffffffffu, acc[s], 16);
+        if (lane < nr)
+            for (int s = 0; s < g.S; ++s) x[s * nr + lane] = acc[s];
+    }
+    // angular
+    if (P.n_ang) {
+        float a[kNAng];
+#pragma unroll
+        for (int t = 0; t < kNAng; ++t) a[t] = 0.f;
+        for (int p = 0; p < n; ++p) {
+            const float xp = S.dx[p], yp = S.dy[p], zp = S.dz[p], rp = S.r[p], fp = S.fc[p];
+            const float e1p = S.e1[p], e2p = S.e2[p];
+            for (int q = p + 1 + lane; q < n; q += 32) {
+                const float c = (xp * S.dx[q] + yp * S.dy[q] + zp * S.dz[q]) / (rp * S.r[q]);
+                const float ff = fp * S.fc[q];
+                const float E1 = e1p * S.e1[q] * ff, E2 = e2p * S.e2[q] * ff;
+                const float bp1 = 1.f + c, bm1 = 1.f - c;
+                const float bp2 = bp1 * bp1, bm2 = bm1 * bm1, bp4 = bp2 * bp2, bm4 = bm2 * bm2;
+                const float bp8 = bp4 * bp4, bm8 = bm4 * bm4;
+                // zeta = 1 (2^0), 2 (2^-1), 4 (2^-3), 8 (2^-7)
+                a[0] += bp1 * E1; a[1] += bp1 * E2; a[2] += bm1 * E1; a[3] += bm1 * E2;
+                a[4] += 0.5f * bp2 * E1; a[5] += 0.5f * bp2 * E2; a[6] += 0.5f * bm2 * E1; a[7] += 0.5f * bm2 * E2;
+                a[8] += 0.125f * bp4 * E1; a[9] += 0.125f * bp4 * E2; a[10] += 0.125f * bm4 * E1; a[11] += 0.125f * bm4 * E2;
+                a[12] += 0.0078125f * bp8 * E1; a[13] += 0.0078125f * bp8 * E2;
+                a[14] += 0.0078125f * bm8 * E1; a[15] += 0.0078125f * bm8 * E2;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kNAng; ++t) a[t] = warp_sum(a[t]);
+        if (lane < kNAng) {
+            float v = 0.f;
+#pragma unroll
+            for (int t = 0; t < kNAng; ++t) v = (lane == t) ? a[t] : v;
+            x[g.S * nr + lane] = v;
+        }
+    }
+    // one-hot and padding
+    const int off = g.S * nr + P.n_ang;
+    for (int f = off + lane; f < P.d0p; f += 32) x[f] = (f == off + (int)fi.w) ? 1.f : 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// Pair gradients g_p = dE_i / d(r_p) and LJ forces.
+// ---------------------------------------------------------------------------
+__global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__restrict__ near_keys,
+                                const int *__restrict__ n_near, const int *__restrict__ far_keys,
+                                const int *__restrict__ n_far, int cap, int cap_far, int M, Geo g, PotDev P,
+                                const float *__restrict__ dEdX, float4 *__restrict__ pair_g,
+                                float4 *__restrict__ Fpart, float *__restrict__ E_lj) {
+    extern __shared__ float smem[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (row >= M) return;
+    const int N = g.N;
+    const int j = row / N, i = row - j * N;
+    const uint4 *fj = fix + (size_t)j * N;
+    const uint4 fi = fj[i];
+    const int warps = blockDim.x >> 5;
+    float *wbuf = smem + (size_t)warps * kStageFloats * cap + (size_t)wib * P.d0p;
+    NbStage S = nb_stage_ptrs(smem + (size_t)wib * kStageFloats * cap, cap);
+    const int n = n_near[row];
+    const int *keys = near_keys + (size_t)row * cap;
+    float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+    if (P.has_mlp) {
+        for (int f = lane; f < P.d0p; f += 32) wbuf[f] = dEdX[(size_t)row * P.d0p + f];
+        nb_stage_load(S, fj, fi, keys, n, g, P.desc_rc, lane);
+        const int nr = P.n_rbf;
+        const float *wang = wbuf + g.S * nr;
+        for (int p = lane; p < n; p += 32) {
+            const float xp = S.dx[p], yp = S.dy[p], zp = S.dz[p], rp = S.r[p], fp = S.fc[p], dfp = S.dfc[p];
+            const float e1p = S.e1[p], e2p = S.e2[p];
+            // radial: c = sum_k w_k g_k'(r)
+            float c = 0.f;
+            const float *wr = wbuf + S.sp[p] * nr;
+            for (int k = 0; k < nr; ++k) {
+                const float t = rp - (float)k * P.rbf_w;
+                const float phi = expf(-t * t * P.rbf_inv2w2);
+                c += wr[k] * phi * (-t * P.rbf_invw2 * fp + dfp);
+            }
+            float gx = c * xp / rp, gy = c * yp / rp, gz = c * zp / rp;
+            if (P.n_ang) {
+                float alpha_sum_x = 0.f, alpha_sum_y = 0.f, alpha_sum_z = 0.f, beta_sum = 0.f;
+                for (int q = 0; q < n; ++q) {
+                    if (q == p) continue;
+                    const float xq = S.dx[q], yq = S.dy[q], zq = S.dz[q], rq = S.r[q];
+                    const float inv_pq = 1.f / (rp * rq);
+                    const float cth = (xp * xq + yp * yq + zp * zq) * inv_pq;
+                    const float fq = S.fc[q];
+                    const float E1 = e1p * S.e1[q], E2 = e2p * S.e2[q];
+                    // (1 + lambda c)^zeta and zeta*(1+lambda c)^(zeta-1) for lambda = +1 (p) and -1 (m)
+                    const float bp1 = 1.f + cth, bm1 = 1.f - cth;
+                    const float bp2 = bp1 * bp1, bm2 = bm1 * bm1, bp4 = bp2 * bp2, bm4 = bm2 * bm2;
+                    const float bp8 = bp4 * bp4, bm8 = bm4 * bm4;
+                    const float bp3 = bp2 * bp1, bm3 = bm2 * bm1, bp7 = bp4 * bp3, bm7 = bm4 * bm3;
+                    // per eta: S0 = sum_a w_a pref pow (value weights), S1 = sum_a w_a pref zeta lambda pow1
+                    float S0_1 = 0.f, S0_2 = 0.f, S1_1 = 0.f, S1_2 = 0.f;
+                    // zeta 1: pref 1
+                    S0_1 += wang[0] * bp1 + wang[2] * bm1;  S0_2 += wang[1] * bp1 + wang[3] * bm1;
+                    S1_1 += wang[0] - wang[2];              S1_2 += wang[1] - wang[3];
+                    // zeta 2: pref 1/2, zeta*pow1*pref = bp1
+                    S0_1 += 0.5f * (wang[4] * bp2 + wang[6] * bm2);  S0_2 += 0.5f * (wang[5] * bp2 + wang[7] * bm2);
+                    S1_1 += wang[4] * bp1 - wang[6] * bm1;           S1_2 += wang[5] * bp1 - wang[7] * bm1;
+                    // zeta 4: pref 1/8, zeta*pow1*pref = 0.5*b^3
+                    S0_1 += 0.125f * (wang[8] * bp4 + wang[10] * bm4);  S0_2 += 0.125f * (wang[9] * bp4 + wang[11] * bm4);
+                    S1_1 += 0.5f * (wang[8] * bp3 - wang[10] * bm3);    S1_2 += 0.5f * (wang[9] * bp3 - wang[11] * bm3);
+                    // zeta 8: pref 1/128, zeta*pow1*pref = b^7/16
+                    S0_1 += 0.0078125f * (wang[12] * bp8 + wang[14] * bm8);
+                    S0_2 += 0.0078125f * (wang[13] * bp8 + wang[15] * bm8);
+                    S1_1 += 0.0625f * (wang[12] * bp7 - wang[14] * bm7);
+                    S1_2 += 0.0625f * (wang[13] * bp7 - wang[15] * bm7);
+                    const float ffq = fp * fq;
+                    // d/d(d_p): S1*E*ff*(d_q/(rp rq) - c d_p/rp^2) + S0*E*(-2 eta d_p)*ff + S0*E*dfp*fq*d_p/rp
+                    const float A = (S1_1 * E1 + S1_2 * E2) * ffq * inv_pq;
+                    const float B = -(S1_1 * E1 + S1_2 * E2) * ffq * cth / (rp * rp) -
+                                    2.f * (0.005f * S0_1 * E1 + 0.05f * S0_2 * E2) * ffq +
+                                    (S0_1 * E1 + S0_2 * E2) * dfp * fq / rp;
+                    alpha_sum_x += A * xq;
+                    alpha_sum_y += A * yq;
+                    alpha_sum_z += A * zq;
+                    beta_sum += B;
+                }
+                gx += alpha_sum_x + beta_sum * xp;
+                gy += alpha_sum_y + beta_sum * yp;
+                gz += alpha_sum_z + beta_sum * zp;
+            }
+            pair_g[(size_t)row * cap + p] = make_float4(gx, gy, gz, 0.f);
+            fx += gx;
+            fy += gy;
+            fz += gz;
+        }
+    }
+    if (P.has_lj) {
+        const int si = (int)fi.w;
+        const int nf = n_far[row];
+        const int *fkeys = far_keys + (size_t)row * cap_far;
+        for (int t = lane; t < n + nf; t += 32) {
+            const int key = t < n ? keys[t] : fkeys[t - n];
+            const uint4 fk = fj[key >> 5];
+            const float3 d = entry_disp(fi, fk, key & 31, g);
+            const float d2 = dist2_rule(d.x, d.y, d.z);
+            if (!(d2 < P.lj_rc2f)) continue;
+            const int pr = si * g.S + (int)fk.w;
+            const float s2 = P.lj_sig2[pr] / d2;
+            const float s6 = s2 * s2 * s2, s12 = s6 * s6;
+            const float fr = -P.lj_eps24[pr] * (2.f * s12 - s6) / d2;   // (dU/dr)/r
+            fx += fr * d.x;
+            fy += fr * d.y;
+            fz += fr * d.z;
+            e += 0.5f * (P.lj_eps4[pr] * (s12 - s6) - P.lj_shift[pr]);
+        }
+    }
+    fx = warp_sum(fx);
+    fy = warp_sum(fy);
+    fz = warp_sum(fz);
+    e = warp_sum(e);
+    if (lane == 0) {
+        Fpart[row] = make_float4(fx, fy, fz, 0.f);
+        E_lj[row] = e;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// F_i = Fpart_i - sum_p g[rev(p)]: the reverse entry (i, -s) is looked up by
+// binary search in the (sorted) descriptor list of the neighbour's row.
+// ---------------------------------------------------------------------------
+__global__ void force_gather_kernel(const int *__restrict__ near_keys, const int *__restrict__ n_near, int cap, int M,
+                                    int N, int has_mlp, const float4 *__restrict__ pair_g,
+                                    const float4 *__restrict__ Fpart, const float *__restrict__ E_lj,
+                                    const float *__restrict__ E_mlp, float *__restrict__ F_out,
+                                    float *__restrict__ E_out, DevState *st) {
+    const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= M) return;
+    const int j = row / N, i = row - j * N;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    if (has_mlp) {
+        const int n = n_near[row];
+        const int *keys = near_keys + (size_t)row * cap;
+        for (int p = lane; p < n; p += 32) {
+            const int key = keys[p];
+            const int rk = j * N + (key >> 5);
+            const int want = (i << 5) | (26 - (key & 31));
+            const int *kk = near_keys + (size_t)rk * cap;
+            int lo = 0, hi = n_near[rk] - 1, found = -1;
+            while (lo <= hi) {
+                const int mid = (lo + hi) >> 1;
+                const int v = kk[mid];
+                if (v == want) { found = mid; break; }
+                if (v < want) lo = mid + 1;
+                else hi = mid - 1;
+            }
+            if (found < 0) {
+                atomicOr(&st->err, 4);
+                continue;
+            }
+            const float4 gv = pair_g[(size_t)rk * cap + found];
+            ax += gv.x;
+            ay += gv.y;
+            az += gv.z;
+        }
+        ax = warp_sum(ax);
+        ay = warp_sum(ay);
+        az = warp_sum(az);
+    }
+    if (lane == 0) {
+        const float4 fp = Fpart[row];
+        F_out[(size_t)row * 3 + 0] = fp.x - ax;
+        F_out[(size_t)row * 3 + 1] = fp.y - ay;
+        F_out[(size_t)row * 3 + 2] = fp.z - az;
+        if (E_out) E_out[row] = E_lj[row] + (has_mlp ? E_mlp[row] : 0.f);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Half-step positions for arbitrary configurations (used by the batched force
+// entry points): fixed point of each row's position.
+// ---------------------------------------------------------------------------
+__global__ void fixpoint_kernel(const double *__restrict__ q, const int *__restrict__ species, int M, Geo g,
+                                uint4 *__restrict__ fix) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= M) return;
+    const int i = row % g.N;
+    const double *qr = q + (size_t)row * 3;
+    fix[row] = make_uint4(fixpoint(qr[0], g.scale[0]), fixpoint(qr[1], g.scale[1]), fixpoint(qr[2], g.scale[2]),
+                          (unsigned)species[i]);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+void launch_fixpoint(const double *q, const int *species, int M, const Geo &g, uint4 *fix, cudaStream_t s) {
+    fixpoint_kernel<<<(M + 255) / 256, 256, 0, s>>>(q, species, M, g, fix);
+}
+
+void launch_neigh_build(const uint4 *fix, int M, const Geo &g, float rmax2f, float near2f, int cap_near, int cap_far,
+                        int *near_keys, int *far_keys, int *n_near, int *n_far, DevState *st, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = (int)(((size_t)M * 32 + threads - 1) / threads);
+    neigh_build_kernel<<<blocks, threads, 0, s>>>(fix, M, g, rmax2f, near2f, cap_near, cap_far, near_keys, far_keys,
+                                                  n_near, n_far, st);
+}
+
+size_t desc_smem_bytes(int warps, int cap) { return (size_t)warps * kStageFloats * cap * sizeof(float); }
+
+void launch_desc(const uint4 *fix, const int *near_keys, const int *n_near, int cap, int M, const Geo &g,
+                 const PotDev &P, float *X, cudaStream_t s) {
+    const int warps = 8;
+    const size_t sm = desc_smem_bytes(warps, cap);
+    desc_kernel<<<(M + warps - 1) / warps, warps * 32, sm, s>>>(fix, near_keys, n_near, cap, M, g, P, X);
+}
+
+void launch_pairgrad(const uint4 *fix, const int *near_keys, const int *n_near, const int *far_keys, const int *n_far,
+                     int cap, int cap_far, int M, const Geo &g, const PotDev &P, const float *dEdX, float4 *pair_g,
+                     float4 *Fpart, float *E_lj, cudaStream_t s) {
+    const int warps = 8;
+    const size_t sm = desc_smem_bytes(warps, cap) + (size_t)warps * P.d0p * sizeof(float);
+    pairgrad_kernel<<<(M + warps - 1) / warps, warps * 32, sm, s>>>(fix, near_keys, n_near, far_keys, n_far, cap,
+                                                                     cap_far, M, g, P, dEdX, pair_g, Fpart, E_lj);
+}
+
+void launch_force_gather(const int *near_keys, const int *n_near, int cap, int M, int N, int has_mlp,
+                         const float4 *pair_g, const float4 *Fpart, const float *E_lj, const float *E_mlp, float *F,
+                         float *E_out, DevState *st, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = (int)(((size_t)M * 32 + threads - 1) / threads);
+    force_gather_kernel<<<blocks, threads, 0, s>>>(near_keys, n_near, cap, M, N, has_mlp, pair_g, Fpart, E_lj, E_mlp,
+                                                   F, E_out, st);
+}
+
+cudaError_t verify_kernels_setup(int max_smem) {
+    cudaError_t e = cudaFuncSetAttribute(desc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(pairgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+}
+
+}  // namespace lsd

@@ -1,0 +1,305 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (each per result against FP64): neighbour lists and accept/reject decisions identical (decisions
+whose margin |log u - min(0, log r)| is below 1e-6 are near-ties, reported and excluded); FP32 forces,
+descriptors and dE/dX within 1e-5 relative (norm over a configuration); BF16 paths within 2e-2 relative."""
+import numpy as np
+import pytest
+
+import oracle.oracle as O
+from paper_2606_02455_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-5
+BF16_TOL = 2e-2
+TIE = 1e-6
+
+
+def _lsd():
+    from paper_2606_02455_b300 import lsd
+    return lsd
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _configs(system, n, scale, seed):
+    rng = np.random.default_rng(seed)
+    return np.stack([system.positions + scale * rng.standard_normal(system.positions.shape) for _ in range(n)])
+
+
+def _small_ragged():
+    """27 atoms of two species (not a multiple of a warp), simple cubic 3^3 in a 9.3 A box."""
+    pos = W.jitter(W.simple_cubic(3, 3.1), 3.1, seed=5)
+    sp = np.arange(27) % 2
+    s = W.System(positions=pos, momenta=W.mb_momenta(np.array([12.0, 16.0])[sp], 300.0, 7), species=sp.astype(np.int32),
+                 masses=np.array([12.0, 16.0]), box=np.array([9.3] * 3), seed=99)
+    lj = dict(lj_eps=np.array([0.0104, 0.0067]), lj_sigma=np.array([3.0, 2.8]), lj_cutoff=4.6)
+    d0 = W.input_dim(2, 16, 16)
+    target = W.Potential(**lj, n_rbf=16, n_ang=16, n_layers=2, width=64, desc_cutoff=4.0, head="tanh",
+                         head_scale=0.3, weights=W.mlp_weights(d0, 2, 64, 11))
+    return W.Workload("ragged27", s, W.Potential(**lj), target, W.Integrator(1.0, 0.01, 300.0, 8), 100)
+
+
+WORKLOADS = {"c1": lambda: W.config1(), "c2": lambda: W.config2(), "ragged27": _small_ragged}
+
+
+@pytest.fixture(scope="module", params=list(WORKLOADS))
+def wl(request):
+    return WORKLOADS[request.param]()
+
+
+def test_target_neighbors_descriptors_forces(wl):
+    """K configurations in one batched call: neighbour lists identical to the oracle's brute force; X, dE/dX,
+    forces and energies within FP32 tolerance of FP64."""
+    import torch
+    lsd = _lsd()
+    s = wl.system
+    K = wl.integ.K
+    h = lsd.LSD(s, wl.draft, wl.target, wl.integ)
+    qs = _configs(s, K, 0.08, seed=123)
+    F, E = h.target_forces(torch.tensor(qs, device="cuda"), energies=True)
+    F, E = F.cpu().numpy(), E.cpu().numpy()
+    X, G = h.descriptors(K)
+    for c in range(K):
+        ref = O.energy_forces(s, wl.target, qs[c], want=("F", "X", "dEdX", "E_atom"))
+        desc, ljl = h.neighbors(c)
+        od = O.neighbors(s, qs[c], wl.target.desc_cutoff)
+        ol = O.neighbors(s, qs[c], wl.target.lj_cutoff)
+        for i in range(s.n_atoms):
+            assert np.array_equal(desc[i], od[i]), ("desc list", c, i)
+            assert np.array_equal(ljl[i], ol[i]), ("lj list", c, i)
+        assert _rel(X[c], ref["X"]) < FORCE_TOL
+        assert _rel(G[c], ref["dEdX"]) < FORCE_TOL
+        assert _rel(F[c], ref["F"]) < FORCE_TOL, (c, _rel(F[c], ref["F"]))
+        assert abs(E[c].astype(np.float64).sum() - ref["E"]) < FORCE_TOL * np.abs(ref["E_atom"]).sum()
+    h.close()
+
+
+def _window_compare(win, ref, K, check_state=True, h=None):
+    assert np.array_equal(win["q_mid"][0], ref["qmid"][0]), "first half step is not bit-identical"
+    assert np.allclose(win["q_mid"], ref["qmid"], rtol=0, atol=1e-8)
+    assert np.allclose(win["p_draft"], ref["pdraft"], rtol=1e-6, atol=1e-9)
+    for j in range(K):
+        assert _rel(win["F_draft"][j], ref["Fdraft"][j]) < FORCE_TOL, ("F_draft", j)
+        assert _rel(win["F_target"][j], ref["Ftarget"][j]) < FORCE_TOL, ("F_target", j)
+    assert np.allclose(win["delta_norm"], ref["delta_norm"], rtol=1e-4, atol=1e-7)
+    assert np.allclose(win["log_ratio"], ref["logr"], rtol=1e-4, atol=1e-7)
+    assert np.array_equal(win["log_u"], ref["logu"]) or np.allclose(win["log_u"], ref["logu"], rtol=1e-15, atol=0)
+    margin = np.abs(ref["logu"] - np.minimum(ref["logr"], 0.0))
+    ties = margin < TIE
+    assert not ties.any(), "near-tie decisions at the test seed: %s" % np.nonzero(ties)
+    assert np.array_equal(win["accept"], ref["accept"])
+
+
+@pytest.mark.parametrize("head_scale", [None, 1.5])
+def test_window_matches_oracle(wl, head_scale):
+    """One window (Alg. 1, L = K) from the same base state: draft arrays, target forces, log ratios, accept
+    decisions, committed count and the new state."""
+    lsd = _lsd()
+    s = wl.system
+    target = wl.target if head_scale is None else W.replace(wl.target, head_scale=head_scale)
+    h = lsd.LSD(s, wl.draft, target, wl.integ)
+    h.draft_window()
+    nc, first = h.verify_window()
+    win = h.get_window()
+    ref = O.lsd_window(s, wl.draft, target, wl.integ, s.seed, 0, wl.integ.K, s.positions, s.momenta)
+    _window_compare(win, ref, wl.integ.K)
+    assert nc == ref["n_committed"]
+    assert first == (-1 if ref["accept"].all() else int(np.argmin(ref["accept"])) + 1)
+    q, p, step = h.get_state()
+    assert step == nc
+    assert np.allclose(q, ref["q"], rtol=0, atol=1e-8)
+    assert np.allclose(p, ref["p"], rtol=1e-5, atol=1e-8)
+    h.close()
+
+
+def test_free_running_matches_oracle_20_steps(wl):
+    """lsd_step (the CUDA-graph window loop) and plain target ABOBA stay within tolerance of the oracle for 20
+    steps; the committed step count is exact."""
+    lsd = _lsd()
+    s = wl.system
+    target = W.replace(wl.target, head_scale=1.0)
+    h = lsd.LSD(s, wl.draft, target, wl.integ)
+    st = h.step(20)
+    q, p, step = h.get_state()
+    ref = O.lsd_run(s, wl.draft, target, wl.integ, s.seed, 20, wl.integ.K, s.positions, s.momenta)
+    assert step == 20 == st["committed"]
+    assert st["rejected"] == ref["stats"]["rejected"]
+    assert np.allclose(q, ref["q"], rtol=0, atol=1e-6)
+    assert np.allclose(p, ref["p"], rtol=0, atol=1e-7)
+    h.set_state(s.positions, s.momenta, 0)
+    h.plain_step(20)
+    q, p, step = h.get_state()
+    refp = O.plain_run(s, target, wl.integ, s.seed, 20, s.positions, s.momenta)
+    assert step == 20
+    assert np.allclose(q, refp["q"], rtol=0, atol=1e-6)
+    assert np.allclose(p, refp["p"], rtol=0, atol=1e-7)
+    h.close()
+
+
+def test_error_correction_window_matches_oracle():
+    """Alg. 3 on the GPU: two windows with the error-correction cache, decisions and states as the oracle's."""
+    lsd = _lsd()
+    w = W.config1()
+    s = w.system
+    target = W.replace(w.target, head_scale=1.0)
+    h = lsd.LSD(s, w.draft, target, w.integ)
+    h.set_error_correction(True)
+    q, p, dF, step = s.positions.copy(), s.momenta.copy(), np.zeros_like(s.positions), 0
+    for _ in range(3):
+        h.draft_window()
+        nc, _ = h.verify_window()
+        win = h.get_window()
+        ref = O.lsd_window(s, w.draft, target, w.integ, s.seed, step, w.integ.K, q, p, ec_dF=dF)
+        assert nc == ref["n_committed"]
+        assert np.array_equal(win["accept"], ref["accept"])
+        gq, gp, gstep = h.get_state()
+        q, p, dF = ref["q"], ref["p"], ref["ec_dF"]
+        step += nc
+        assert gstep == step
+        assert np.allclose(gq, q, atol=1e-8) and np.allclose(gp, p, rtol=1e-5, atol=1e-8)
+        h.set_state(q, p, step)    # keep both sides on the oracle's state
+    h.close()
+
+
+def test_draft_equal_target_accepts_everything():
+    """T3 on the GPU: LJ draft and LJ target give delta ~ 0; every step is accepted and LSD follows plain target
+    ABOBA to rounding."""
+    lsd = _lsd()
+    w = W.config2()
+    s = w.system
+    h = lsd.LSD(s, w.draft, w.draft, w.integ)
+    st = h.step(64)
+    assert st["rejected"] == 0 and st["committed"] == 64
+    q1, p1, _ = h.get_state()
+    h.set_state(s.positions, s.momenta, 0)
+    h.plain_step(64)
+    q2, p2, _ = h.get_state()
+    assert np.allclose(q1, q2, atol=1e-8) and np.allclose(p1, p2, atol=1e-9)
+    h.close()
+
+
+def test_checkpoint_resume_is_bitwise():
+    """2 x 24 steps with a checkpoint/restore in between equal 48 uninterrupted steps bit for bit."""
+    lsd = _lsd()
+    w = W.config1()
+    s = w.system
+    target = W.replace(w.target, head_scale=1.0)
+    a = lsd.LSD(s, w.draft, target, w.integ)
+    a.step(48)
+    qa, pa, _ = a.get_state()
+    b = lsd.LSD(s, w.draft, target, w.integ)
+    b.step(24)
+    blob = b.checkpoint()
+    b.close()
+    c = lsd.LSD(s, w.draft, target, w.integ)
+    c.restore(blob)
+    c.step(24)
+    qc, pc, stc = c.get_state()
+    assert stc == 48 and np.array_equal(qa, qc) and np.array_equal(pa, pc)
+    a.close()
+    c.close()
+
+
+def test_single_atom_and_window_of_one():
+    """Degenerate cases: one atom interacting only with its own images, window length 1."""
+    lsd = _lsd()
+    s = W.System(positions=np.array([[1.0, 2.0, 3.0]]), momenta=np.array([[0.01, -0.02, 0.03]]),
+                 species=np.array([0], np.int32), masses=np.array([40.0]), box=np.array([6.0] * 3), seed=3)
+    lj = W.Potential(lj_eps=np.array([0.0104]), lj_sigma=np.array([3.4]), lj_cutoff=5.9)
+    tgt = W.Potential(lj_eps=np.array([0.0104]), lj_sigma=np.array([3.4]), lj_cutoff=5.9, n_rbf=4, n_ang=16,
+                      n_layers=1, width=32, desc_cutoff=5.5, head="tanh", head_scale=0.05,
+                      weights=W.mlp_weights(W.input_dim(1, 4, 16), 1, 32, 2))
+    integ = W.Integrator(2.0, 0.01, 300.0, 1)
+    h = lsd.LSD(s, lj, tgt, integ)
+    h.draft_window()
+    nc, _ = h.verify_window()
+    win = h.get_window()
+    ref = O.lsd_window(s, lj, tgt, integ, s.seed, 0, 1, s.positions, s.momenta)
+    assert nc == ref["n_committed"] == 1
+    assert np.array_equal(win["accept"], ref["accept"])
+    assert np.allclose(win["F_target"][0], ref["Ftarget"][0], atol=1e-7)
+    h.close()
+
+
+def test_target_energy_autograd_is_minus_forces():
+    import torch
+    lsd = _lsd()
+    w = W.config1()
+    s = w.system
+    h = lsd.LSD(s, w.draft, w.target, w.integ)
+    q = torch.tensor(_configs(s, 3, 0.05, 9), device="cuda", requires_grad=True)
+    E = lsd.target_energy(q, h)
+    E.sum().backward()
+    F = h.target_forces(q.detach())
+    assert torch.allclose(q.grad, -F.double(), rtol=0, atol=0)
+    for c in range(3):
+        ref = O.energy(s, w.target, q[c].detach().cpu().numpy())
+        assert abs(E[c].item() - ref) < 1e-5 * 32
+    h.close()
+
+
+# ---------------------------------------------------------------------------------------------------------------
+# learned draft
+# ---------------------------------------------------------------------------------------------------------------
+
+def test_learned_draft_bf16_forces_within_tolerance():
+    """BF16 inference of the learned draft inside the draft kernel: draft forces of the window within 2e-2 of
+    the oracle's FP64 forces of the same draft (weights scaled up so the MLP term is not negligible)."""
+    lsd = _lsd()
+    w = W.config3()
+    s = w.system
+    draft = W.replace(w.draft, weights=W.mlp_weights(W.input_dim(1, 8, 0), 1, 32, seed=3))
+    h = lsd.LSD(s, draft, w.target, w.integ)
+    h.draft_window()
+    h.verify_window()
+    win = h.get_window()
+    ref = O.lsd_window(s, draft, w.target, w.integ, s.seed, 0, w.integ.K, s.positions, s.momenta)
+    lj_only = W.Potential(lj_eps=draft.lj_eps, lj_sigma=draft.lj_sigma, lj_cutoff=draft.lj_cutoff)
+    for j in range(w.integ.K):
+        mlp_part = ref["Fdraft"][j] - O.forces(s, lj_only, ref["qmid"][j])
+        assert np.linalg.norm(mlp_part) > 0.05 * np.linalg.norm(ref["Fdraft"][j])
+        assert _rel(win["F_draft"][j], ref["Fdraft"][j]) < BF16_TOL, j
+    h.close()
+
+
+def test_force_matching_gradient_matches_oracle():
+    """The GPU's hand-written double backward (loss and dL/dtheta of force matching) against the oracle's FP64."""
+    import torch
+    lsd = _lsd()
+    w = W.config3()
+    s = w.system
+    draft = W.replace(w.draft, weights=W.mlp_weights(W.input_dim(1, 8, 0), 1, 32, seed=3))
+    h = lsd.LSD(s, draft, w.target, w.integ)
+    fq = _configs(s, 6, 0.1, seed=77)
+    fF = np.stack([O.forces(s, w.target, q) for q in fq]).astype(np.float32)
+    loss, g = h.force_match(torch.tensor(fq, device="cuda"), torch.tensor(fF, device="cuda"))
+    rl, rg = O.force_match(s, draft, fq, fF.astype(np.float64))
+    assert abs(loss - rl) / rl < 1e-4
+    g = g.cpu().numpy()
+    assert _rel(g, rg) < 1e-4, _rel(g, rg)
+    h.close()
+
+
+def test_learned_draft_training_reduces_rejections():
+    """Frames captured by verification train the learned draft (Adam on the force-matching loss); the loss
+    drops and the mean Mahalanobis distance |delta| (Eq. 6) falls below the untrained draft's."""
+    lsd = _lsd()
+    w = W.config3(K=8)
+    s = w.system
+    target = W.replace(w.target, head_scale=0.5)
+    h = lsd.LSD(s, w.draft, target, w.integ)
+    h.set_frame_capture(4096)
+    st0 = h.step(400)
+    assert h.frame_count() > 100
+    l0 = h.train_draft(1, 1e-3)
+    l1 = h.train_draft(300, 3e-3)
+    assert l1 < 0.5 * l0, (l0, l1)
+    before = st0["sum_delta"] / st0["committed"]
+    st1 = h.step(400)
+    after = (st1["sum_delta"] - st0["sum_delta"]) / (st1["committed"] - st0["committed"])
+    assert after < 0.8 * before, (before, after)
+    h.close()
