@@ -81,9 +81,12 @@ extern "C" {
  * d_in = n_species*n_rbf + n_ang + n_species for the first layer.
  * Neighbour membership (the same rule everywhere, so lists are exactly
  * reproducible): positions are wrapped to 32-bit fixed point
- * u = floor(q * 2^32/L) mod 2^32 per axis; a pair (i, j, image shift s in
- * {-1,0,1}^3) has d = fl32(fl32(u_j - u_i + s 2^32) * fl32(L/2^32)) per
- * axis and is a member iff ((dx*dx + dy*dy) + dz*dz) < fl32(rc^2) in
+ * u = floor(q * 2^32/L) mod 2^32 per axis.  Along an axis the pair (i, j)
+ * has the wrapped difference d0 = (int32)(u_j - u_i), the minimum-image
+ * displacement dmin = fl32(fl32(d0) * fl32(L/2^32)), and the image r in
+ * {-1,0,1} relative to it the displacement dmin or fl32(dmin + r fl32(L));
+ * the stored (absolute) image shift is s = r - k with k = (u_j - u_i -
+ * d0)/2^32.  A pair is a member iff ((dx*dx + dy*dy) + dz*dz) < fl32(rc^2) in
  * binary32 without fused multiply-add; rc < L on every axis.
  */
 #define LSD_POT_LJ 0

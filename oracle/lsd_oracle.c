@@ -156,14 +156,17 @@ double o_uniform(uint64_t seed, uint64_t n) {
 /* ------------------------------------------------------------------------- */
 /* Each coordinate is mapped to 32-bit fixed point: t = q * (2^32 / L),
  * f = floor(t), u = f mod 2^32 (the wrapped position in units of L/2^32) and
- * m = (f - u) / 2^32 (the periodic image count).  A pair (i, j) with image
- * shift s in {-1,0,1}^3 has integer displacement D = u_j - u_i + s*2^32 per
- * axis; its float displacement is fl32(fl32(D) * fl32(L/2^32)); the squared
- * distance is ((dx*dx + dy*dy) + dz*dz) in binary32 without fused
- * multiply-add; the pair is a member iff that is < fl32(rc^2).  Self pairs are
- * excluded only for s = 0.  The shift code is (sx+1) + 3(sy+1) + 9(sz+1).
- * Requires rc < L on every axis so that no image beyond s = +-1 can be within
- * reach. */
+ * m = (f - u) / 2^32 (the periodic image count).  Along one axis the pair
+ * (i, j) has the wrapped difference d0 = (int32)(u_j - u_i mod 2^32) (the
+ * minimum image in fixed point, k = (u_j - u_i - d0)/2^32 in {-1,0,1} images
+ * away from the unwrapped difference), the minimum-image displacement
+ * dmin = fl32(fl32(d0) * fl32(L/2^32)), and for the image r in {-1,0,1}
+ * relative to it the displacement d_r = dmin (r = 0) or fl32(dmin + r*fl32(L)).
+ * The absolute image shift of that displacement is s = r - k.  A pair (i, j, s)
+ * is a member iff every axis has |r| <= 1 and ((dx*dx + dy*dy) + dz*dz) <
+ * fl32(rc^2) in binary32 without fused multiply-add.  Self pairs are excluded
+ * only for s = 0.  The shift code is (sx+1) + 3(sy+1) + 9(sz+1).  Requires
+ * rc < L on every axis (then no image with |r| > 1 can be within reach). */
 
 typedef struct { uint32_t u[3]; int64_t m[3]; } o_fix;
 
@@ -185,10 +188,16 @@ static int o_member(const o_system *sys, const o_fix *fx, int i, int j, const in
                     float *d2_out) {
     float d[3];
     for (int a = 0; a < 3; ++a) {
-        int64_t D = (int64_t)fx[j].u[a] - (int64_t)fx[i].u[a] + (int64_t)s[a] * 4294967296ll;
+        uint32_t ui = fx[i].u[a], uj = fx[j].u[a];
+        int32_t d0 = (int32_t)(uint32_t)(uj - ui);
+        int64_t D0 = (int64_t)uj - (int64_t)ui;
+        int k = (int)((D0 - (int64_t)d0) / 4294967296ll);
+        int r = s[a] + k;
+        if (r < -1 || r > 1) return 0;
         float scale_f = (float)(sys->box[a] / O_TWO32);
-        float df = (float)D;
-        d[a] = df * scale_f;
+        float Lf = (float)sys->box[a];
+        float dmin = (float)d0 * scale_f;
+        d[a] = (r == 0) ? dmin : dmin + (float)r * Lf;
     }
     float xx = d[0] * d[0];
     float yy = d[1] * d[1];

@@ -29,7 +29,7 @@ using namespace lsd;
 namespace {
 
 constexpr double kTwo32 = 4294967296.0;
-constexpr int kMaxDynSmem = 220 * 1024;
+constexpr int kMaxDynSmem = 227 * 1024;
 constexpr double kWaitLimitSeconds = 600.0;
 
 double kappa_conv() { return (1.602176634e-19 / 1e-10) / (1.66053906660e-27 * 1e-10 / 1e-30); }
@@ -60,6 +60,9 @@ struct lsd_handle {
     Coef coef{};
     PotHost draft, target;
     bool learned_small = false;
+    DraftPlan dplan{};
+    int *w_flags = nullptr;
+    float *w_dEdX = nullptr;
     // device state
     double *q = nullptr, *p = nullptr;
     int *species = nullptr;
@@ -76,6 +79,7 @@ struct lsd_handle {
     float *X = nullptr, *dEdX = nullptr, *E_mlp = nullptr, *E_lj = nullptr, *E_atom = nullptr;
     float4 *pair_g = nullptr, *Fpart = nullptr;
     double2 *partials = nullptr;
+    double *logu = nullptr;
     // streams and graphs
     cudaStream_t own_stream = nullptr, stream = nullptr;
     cudaGraphExec_t g_window = nullptr, g_plain = nullptr;
@@ -311,15 +315,15 @@ void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, f
 }
 
 void enqueue_draft(lsd_handle *h, cudaStream_t s) {
-    launch_draft_small(h->learned_small, h->K, h->geo, h->draft.dev, h->coef, h->species, h->q, h->p, h->ec_dF,
-                       h->ec_on, h->st, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Fraw, h->w_fix, s);
+    launch_draft(h->dplan, h->learned_small, h->K, h->geo, h->draft.dev, h->coef, h->species, h->q, h->p, h->ec_dF,
+                 h->ec_on, h->st, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Fraw, h->w_fix, h->w_flags, h->w_dEdX, s);
 }
 
 void enqueue_verify(lsd_handle *h, cudaStream_t s) {
     enqueue_eval(h, h->target, h->w_fix, h->K, h->w_Ft, nullptr, s);
     if (h->train.capture_on) enqueue_frame_capture(h->train, h->w_qmid, h->w_Ft, h->K, h->N, h->st, s);
     launch_transport(h->K, h->geo, h->coef, h->species, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Ft, h->w_Fraw, h->ec_dF,
-                     h->ec_on, h->q, h->p, h->st, h->partials, s);
+                     h->ec_on, h->q, h->p, h->st, h->partials, h->logu, s);
 }
 
 void enqueue_plain(lsd_handle *h, cudaStream_t s) {
@@ -461,6 +465,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     for (int a = 0; a < 3; ++a) {
         g.scale[a] = kTwo32 / h->box[a];
         g.scale_f[a] = (float)(h->box[a] / kTwo32);
+        g.Lf[a] = (float)h->box[a];
     }
     // Eq. 4 coefficients
     Coef &c = h->coef;
@@ -479,7 +484,6 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     if ((rc = pot_setup(h, h->draft, draft, true)) != LSD_OK) return fail(rc);
     if ((rc = pot_setup(h, h->target, target, false)) != LSD_OK) return fail(rc);
     h->learned_small = h->draft.dev.has_mlp;
-    if (draft_small_smem_bytes(h->N, h->draft.dev, h->learned_small) > (size_t)kMaxDynSmem) return fail(LSD_EUNSUPPORTED);
     if (mlp_fp32_smem_bytes(h->target.dev) > (size_t)kMaxDynSmem) return fail(LSD_EUNSUPPORTED);
     // capacities from the mean density (x2 + margin)
     const double V = h->box[0] * h->box[1] * h->box[2];
@@ -495,6 +499,13 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     if (verify_kernels_setup(kMaxDynSmem) != cudaSuccess || mlp_kernels_setup(kMaxDynSmem) != cudaSuccess ||
         draft_kernels_setup(kMaxDynSmem) != cudaSuccess)
         return fail(LSD_ECUDA);
+    {
+        const double rc_draft = std::max(h->draft.dev.has_lj ? h->draft.p.lj_cutoff : 0.0,
+                                          h->draft.dev.has_mlp ? h->draft.p.desc_cutoff : 0.0);
+        const int maxc = draft_max_cluster(64 * 1024);
+        h->dplan = draft_plan(h->N, rho, rc_draft, h->draft.dev, h->learned_small, maxc, kMaxDynSmem);
+        if (!h->dplan.ok) return fail(LSD_EUNSUPPORTED);
+    }
     const size_t N = h->N, D = 3 * N, KN = (size_t)K * N, KD = (size_t)K * D;
     const int dmax = std::max(h->draft.dev.d0p, h->target.dev.d0p);
     if ((rc = dalloc(h, &h->q, D)) || (rc = dalloc(h, &h->p, D)) || (rc = dalloc(h, &h->species, N)) ||
@@ -506,7 +517,9 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         (rc = dalloc(h, &h->X, KN * std::max(dmax, 32))) || (rc = dalloc(h, &h->dEdX, KN * std::max(dmax, 32))) ||
         (rc = dalloc(h, &h->E_mlp, KN)) || (rc = dalloc(h, &h->E_lj, KN)) || (rc = dalloc(h, &h->E_atom, KN)) ||
         (rc = dalloc(h, &h->pair_g, KN * h->cap_near)) || (rc = dalloc(h, &h->Fpart, KN)) ||
-        (rc = dalloc(h, &h->partials, (size_t)K * ((h->N + 1023) / 1024 + 600))))
+        (rc = dalloc(h, &h->partials, (size_t)K * ((h->N + 1023) / 1024 + 600))) ||
+        (rc = dalloc(h, &h->logu, (size_t)K)) || (rc = dalloc(h, &h->w_flags, (size_t)K * 16)) ||
+        (rc = dalloc(h, &h->w_dEdX, N * std::max(h->draft.dev.d0p, 32))))
         return fail(rc);
     if ((rc = pot_upload(h, h->draft)) != LSD_OK) return fail(rc);
     if ((rc = pot_upload(h, h->target)) != LSD_OK) return fail(rc);
@@ -808,10 +821,10 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
     launch_force_gather(h->near_keys, h->n_near, h->cap_near, M, h->N, P.has_mlp, h->pair_g, h->Fpart, h->E_lj,
                         h->E_mlp, h->w_Ft, nullptr, h->st, st);
     CK(cudaEventRecord(ev[6], st));
-    launch_transport_reduce(h->K, h->geo, h->coef, h->species, h->w_Fd, h->w_Ft, h->st, h->partials, st);
+    launch_transport_reduce(h->K, h->geo, h->coef, h->species, h->w_Fd, h->w_Ft, h->st, h->partials, h->logu, st);
     CK(cudaEventRecord(ev[7], st));
     launch_transport_commit(h->K, h->geo, h->coef, h->species, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Ft, h->w_Fraw,
-                            h->ec_dF, h->ec_on, h->q, h->p, h->st, h->partials, st);
+                            h->ec_dF, h->ec_on, h->q, h->p, h->st, h->partials, h->logu, st);
     CK(cudaEventRecord(ev[8], st));
     CK(cudaGetLastError());
     TRY(wait_stream(h));

@@ -25,6 +25,7 @@ struct Geo {
     int S;                 // species
     double scale[3];       // 2^32 / L per axis (fixed-point wrap)
     float scale_f[3];      // fl32(L / 2^32) per axis
+    float Lf[3];           // fl32(L) per axis
 };
 
 struct PotDev {
@@ -136,11 +137,6 @@ __device__ __forceinline__ uint32_t fixpoint(double q, double scale) {
     return (uint32_t)(unsigned long long)fi;
 }
 
-__device__ __forceinline__ float disp_axis(uint32_t ui, uint32_t uj, int s, float scale_f) {
-    const long long D = (long long)uj - (long long)ui + (long long)s * 4294967296ll;
-    return __fmul_rn(__ll2float_rn(D), scale_f);
-}
-
 __device__ __forceinline__ float dist2_rule(float dx, float dy, float dz) {
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
@@ -153,41 +149,74 @@ __device__ __forceinline__ void code_shift(int code, int &sx, int &sy, int &sz) 
     sz = code / 9 - 1;
 }
 
-// Candidate images of atom j seen from atom i along one axis: s = 0 always,
-// plus s = -sign(D0) when D0 != 0 (rc < L excludes every other image).
-// Options are returned in ascending s; n_opt in {1, 2}.
+// Along one axis: d0 = (int32)(u_j - u_i) is the minimum image in fixed point,
+// k = (u_j - u_i - d0)/2^32 in {-1,0,1}; dmin = fl32(fl32(d0) * fl32(L/2^32));
+// the image r in {-1,0,1} relative to it has displacement dmin (r = 0) or
+// fl32(dmin + r fl32(L)), and absolute image shift s = r - k.  Only r = 0 and
+// r = -sign(dmin) can lie within a cutoff rc < L.  Everything is 32-bit.
+__device__ __forceinline__ void axis_min(uint32_t ui, uint32_t uj, float scale_f, float &dmin, int &k) {
+    const int d0 = (int)(uj - ui);
+    dmin = __fmul_rn(__int2float_rn(d0), scale_f);
+    k = (uj >= ui) ? (d0 < 0 ? 1 : 0) : (d0 >= 0 ? -1 : 0);
+}
+
+// The (at most two) images of j along one axis that pass the per-axis bound
+// d^2 < rc^2 (a necessary condition for membership), in ascending image order.
 struct AxisOpts {
-    int s[2];
-    float d[2];
+    float d0, d1;  // displacements
+    int s0, s1;    // absolute image shifts
     int n;
 };
+__device__ __forceinline__ float opt_d(const AxisOpts &o, int b) { return b ? o.d1 : o.d0; }
+__device__ __forceinline__ int opt_s(const AxisOpts &o, int b) { return b ? o.s1 : o.s0; }
 
-__device__ __forceinline__ AxisOpts axis_opts(uint32_t ui, uint32_t uj, float scale_f, float rc2f) {
+__device__ __forceinline__ AxisOpts axis_opts(uint32_t ui, uint32_t uj, float scale_f, float Lf, float rc2f) {
+    float dmin;
+    int k;
+    axis_min(ui, uj, scale_f, dmin, k);
+    const int ra = dmin > 0.f ? -1 : 1;
+    const float da = __fadd_rn(dmin, ra > 0 ? Lf : -Lf);
+    const bool okm = __fmul_rn(dmin, dmin) < rc2f;
+    const bool oka = (dmin != 0.f) && (__fmul_rn(da, da) < rc2f);
     AxisOpts o;
+    o.d0 = o.d1 = 0.f;
+    o.s0 = o.s1 = 0;
     o.n = 0;
-    const long long D0 = (long long)uj - (long long)ui;
-    int cand[2];
-    int nc = 0;
-    if (D0 > 0) { cand[nc++] = -1; cand[nc++] = 0; }
-    else if (D0 < 0) { cand[nc++] = 0; cand[nc++] = 1; }
-    else { cand[nc++] = 0; }
-    for (int c = 0; c < nc; ++c) {
-        const float d = disp_axis(ui, uj, cand[c], scale_f);
-        if (__fmul_rn(d, d) < rc2f) {   // necessary condition for membership
-            o.s[o.n] = cand[c];
-            o.d[o.n] = d;
-            ++o.n;
+    const float dfirst = ra < 0 ? da : dmin, dsecond = ra < 0 ? dmin : da;
+    const int sfirst = ra < 0 ? ra - k : -k, ssecond = ra < 0 ? -k : ra - k;
+    const bool okfirst = ra < 0 ? oka : okm, oksecond = ra < 0 ? okm : oka;
+    if (okfirst) {
+        o.d0 = dfirst;
+        o.s0 = sfirst;
+        o.n = 1;
+        if (oksecond) {
+            o.d1 = dsecond;
+            o.s1 = ssecond;
+            o.n = 2;
         }
+    } else if (oksecond) {
+        o.d0 = dsecond;
+        o.s0 = ssecond;
+        o.n = 1;
     }
     return o;
 }
 
-// Displacement of neighbour entry (k, code) from atom with fixed point fi.
+// Displacement of the stored neighbour entry (k, absolute shift code).
+__device__ __forceinline__ float disp_from_shift(uint32_t ui, uint32_t uj, int s, float scale_f, float Lf) {
+    float dmin;
+    int k;
+    axis_min(ui, uj, scale_f, dmin, k);
+    const int r = s + k;
+    return r == 0 ? dmin : __fadd_rn(dmin, r > 0 ? Lf : -Lf);
+}
+
 __device__ __forceinline__ float3 entry_disp(uint4 fi, uint4 fk, int code, const Geo &g) {
     int sx, sy, sz;
     code_shift(code, sx, sy, sz);
-    return make_float3(disp_axis(fi.x, fk.x, sx, g.scale_f[0]), disp_axis(fi.y, fk.y, sy, g.scale_f[1]),
-                       disp_axis(fi.z, fk.z, sz, g.scale_f[2]));
+    return make_float3(disp_from_shift(fi.x, fk.x, sx, g.scale_f[0], g.Lf[0]),
+                       disp_from_shift(fi.y, fk.y, sy, g.scale_f[1], g.Lf[1]),
+                       disp_from_shift(fi.z, fk.z, sz, g.scale_f[2], g.Lf[2]));
 }
 
 // ---------------------------------------------------------------------------

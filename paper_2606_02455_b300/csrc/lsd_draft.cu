@@ -3,74 +3,89 @@
 //   F~ = draft(q_mid)                               (LJ, or LJ + learned MLP)
 //   <p~> = c1 p + (1+c1)(dt/2) kappa (F~ + dF)      (BOB mean, Eq. 4; dF = EC cache)
 //   p' = <p~> + sigma xi_n,  q' = q_mid + (dt/2) p'/m  (BOB draw, A)
-// The K steps are inherently serial, so for systems that fit one SM the whole
-// window runs in one persistent CTA (1024 threads, the atoms' fixed-point
-// coordinates in shared memory, one warp per atom and lanes over partners),
-// paying one launch instead of K.  FP64 is used only for the state updates,
-// with explicit round-to-nearest intrinsics so q_mid is reproducible bit for
-// bit.  The window arrays written here (q_mid, p', F~, fixed point) are what
-// the batched verification reads.
+//
+// The K steps are inherently serial; within a step the force evaluation is
+// parallel over atoms.  The whole window therefore runs in ONE launch of a
+// thread-block cluster (up to 16 CTAs, one per SM): each CTA owns a slice of
+// the atoms, writes their half-step fixed-point positions to global memory,
+// and a hardware cluster barrier (release/acquire at cluster scope, no spin
+// loop) makes every CTA see all positions before forces are evaluated.
+//
+// Candidates come from a Verlet list per owned atom, built from the
+// minimum-image distance with a 1 A skin at the first step and rebuilt (in
+// every CTA, decided from flags all CTAs read after the barrier) whenever an
+// atom has moved more than 0.45 skin since the build.  Each list entry is
+// then tested with the exact membership rule, so the interacting set is the
+// rule's set, not an approximation.
+//
+// FP64 only for the state updates, with explicit round-to-nearest intrinsics
+// so the half-step positions are reproducible bit for bit.
 #include "lsd_common.cuh"
 #include "lsd_kernels.h"
 
 namespace lsd {
 
-constexpr int kDraftThreads = 1024;
+constexpr int kDraftThreads = 512;
 constexpr int kDraftWarps = kDraftThreads / 32;
-constexpr int kLearnCap = 96;   // per-warp staged neighbours of the learned draft
+constexpr int kLearnCap = 96;      // staged descriptor neighbours per warp (learned draft)
+constexpr float kSkin = 1.0f;      // Verlet skin, Angstrom
 
-// Per-axis candidate images for the draft (same rule as the verification).
-__device__ __forceinline__ void lj_pair_force(const PotDev &P, int pr, float dx, float dy, float dz, float d2,
-                                              float &fx, float &fy, float &fz) {
-    const float s2 = P.lj_sig2[pr] / d2;
-    const float s6 = s2 * s2 * s2, s12 = s6 * s6;
-    const float fr = -P.lj_eps24[pr] * (2.f * s12 - s6) / d2;
-    fx += fr * dx;
-    fy += fr * dy;
-    fz += fr * dz;
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
-// Learned draft: descriptors (radial only) + MLP with BF16 weights and
-// activations, FP32 accumulation; writes dE/dx of atom i to g_out[d0p].
-__device__ void learned_atom_grad(const PotDev &P, const Geo &g, const uint4 *sfix, int i, float *stage, float *xbuf,
-                                  float *g_out) {
+struct DraftShared {
+    uint4 *fix;        // [N] fixed point of all atoms at the current step
+    uint4 *ubuild;     // [A] fixed point of owned atoms at the last list build
+    int *list;         // [A][cap] candidate atom indices
+    int *nlist;        // [A]
+    float4 *F;         // [A] forces of owned atoms
+    float *lj;         // 4 tables of S*S: sig2, eps24
+    float *stage;      // learned: per warp 3*kLearnCap + d0p
+};
+
+// Learned draft, first phase: radial descriptors of atom i from its list,
+// the MLP (BF16 operands, FP32 accumulation), dE/dx written to g_out[d0p].
+__device__ void learned_atom_grad(const PotDev &P, const Geo &g, const uint4 *sfix, int i, const int *cand, int nc,
+                                  float *stage, float *xbuf, float *g_out) {
     const int lane = threadIdx.x & 31;
-    const int N = g.N;
     const uint4 fi = sfix[i];
     float *sr = stage, *sfc = stage + kLearnCap;
     int *ssp = (int *)(stage + 2 * kLearnCap);
-    // stage members within the descriptor cutoff (order does not matter for sums of per-lane slots)
     int cnt = 0;
-    for (int base = 0; base < N; base += 32) {
-        const int k = base + lane;
+    for (int base = 0; base < nc; base += 32) {
+        const int t = base + lane;
         unsigned m = 0u;
         AxisOpts ox, oy, oz;
-        ox.n = oy.n = oz.n = 0;
-        if (k < N) {
+        ox = oy = oz = AxisOpts{0.f, 0.f, 0, 0, 0};
+        int k = 0;
+        if (t < nc) {
+            k = cand[t];
             const uint4 fk = sfix[k];
-            ox = axis_opts(fi.x, fk.x, g.scale_f[0], P.desc_rc2f);
-            oy = axis_opts(fi.y, fk.y, g.scale_f[1], P.desc_rc2f);
-            oz = axis_opts(fi.z, fk.z, g.scale_f[2], P.desc_rc2f);
+            ox = axis_opts(fi.x, fk.x, g.scale_f[0], g.Lf[0], P.desc_rc2f);
+            oy = axis_opts(fi.y, fk.y, g.scale_f[1], g.Lf[1], P.desc_rc2f);
+            oz = axis_opts(fi.z, fk.z, g.scale_f[2], g.Lf[2], P.desc_rc2f);
             for (int bz = 0; bz < oz.n; ++bz)
                 for (int by = 0; by < oy.n; ++by)
                     for (int bx = 0; bx < ox.n; ++bx) {
-                        if (k == i && ox.s[bx] == 0 && oy.s[by] == 0 && oz.s[bz] == 0) continue;
-                        if (dist2_rule(ox.d[bx], oy.d[by], oz.d[bz]) < P.desc_rc2f) m |= 1u << (bx + 2 * by + 4 * bz);
+                        if (k == i && opt_s(ox, bx) == 0 && opt_s(oy, by) == 0 && opt_s(oz, bz) == 0) continue;
+                        if (dist2_rule(opt_d(ox, bx), opt_d(oy, by), opt_d(oz, bz)) < P.desc_rc2f)
+                            m |= 1u << (bx + 2 * by + 4 * bz);
                     }
         }
         const int nm = __popc(m);
         int sc = nm;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, sc, o);
-            if (lane >= o) sc += t;
+            const int v = __shfl_up_sync(0xffffffffu, sc, o);
+            if (lane >= o) sc += v;
         }
         const int tot = __shfl_sync(0xffffffffu, sc, 31);
         int w = cnt + sc - nm;
         for (int c = 0; c < 8; ++c) {
             if (!(m & (1u << c))) continue;
             if (w < kLearnCap) {
-                const float dx = ox.d[c & 1], dy = oy.d[(c >> 1) & 1], dz = oz.d[c >> 2];
+                const float dx = opt_d(ox, c & 1), dy = opt_d(oy, (c >> 1) & 1), dz = opt_d(oz, c >> 2);
                 const float r = sqrtf(dist2_rule(dx, dy, dz));
                 float fc, dfc;
                 cutoff_fn(r, P.desc_rc, fc, dfc);
@@ -84,7 +99,6 @@ __device__ void learned_atom_grad(const PotDev &P, const Geo &g, const uint4 *sf
     }
     __syncwarp();
     const int n = cnt < kLearnCap ? cnt : kLearnCap;
-    // radial descriptors x[s*nr + k]
     const int nr = P.n_rbf;
     {
         float acc[kMaxSpecies];
@@ -109,7 +123,6 @@ __device__ void learned_atom_grad(const PotDev &P, const Geo &g, const uint4 *sf
         if (lane == 0) xbuf[g.S * nr + P.n_ang + (int)fi.w] = 1.f;
     }
     __syncwarp();
-    // MLP, one hidden layer, lane = hidden unit (width <= 32), BF16 operands
     const int W = P.width;
     float gh = 0.f;
     if (lane < W) {
@@ -120,7 +133,6 @@ __device__ void learned_atom_grad(const PotDev &P, const Geo &g, const uint4 *sf
         gh = __bfloat162float(P.wout_bf[lane]) * dsiluf_(h);   // linear head: dE/dy = 1
     }
     __syncwarp();
-    // dE/dx_f = sum_unit W1[unit][f] g_unit
     for (int f = 0; f < P.d0p; ++f) {
         float v = (lane < W && f < P.d0) ? __bfloat162float(P.Wn_bf[0][(size_t)lane * P.d0p + f]) * gh : 0.f;
         v = warp_sum(v);
@@ -131,144 +143,283 @@ __device__ void learned_atom_grad(const PotDev &P, const Geo &g, const uint4 *sf
 
 template <bool LEARNED>
 __global__ void __launch_bounds__(kDraftThreads)
-    draft_window_small_kernel(int K, Geo g, PotDev P, Coef cf, const int *__restrict__ species,
-                              const double *__restrict__ q_base, const double *__restrict__ p_base,
-                              const float *__restrict__ ec_dF, int ec_on, const DevState *__restrict__ st,
-                              double *__restrict__ w_qmid, double *__restrict__ w_pdraft, float *__restrict__ w_Fd,
-                              float *__restrict__ w_Fraw, uint4 *__restrict__ w_fix) {
+    draft_window_cluster_kernel(int K, Geo g, PotDev P, Coef cf, int cap, float rlist2f,
+                                const int *__restrict__ species, const double *__restrict__ q_base,
+                                const double *__restrict__ p_base, const float *__restrict__ ec_dF, int ec_on,
+                                const DevState *__restrict__ st, double *__restrict__ w_qmid,
+                                double *__restrict__ w_pdraft, float *__restrict__ w_Fd, float *__restrict__ w_Fraw,
+                                uint4 *__restrict__ w_fix, int *__restrict__ w_flags, float *__restrict__ w_dEdX) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N;
-    uint4 *sfix = (uint4 *)smraw;
-    float4 *sF = (float4 *)(sfix + N);
-    float *sG = (float *)(sF + N);                                // learned: [N][d0p]
-    float *sStage = sG + (LEARNED ? (size_t)N * P.d0p : 0);       // learned: per warp 3*cap + d0p
-    if (st->step >= st->target_step) return;
+    const int C = gridDim.x, c = blockIdx.x;
+    const int A = (N + C - 1) / C;           // owned atoms per CTA
+    const int a0 = c * A, a1 = min(N, a0 + A);
+    const int nown = a1 > a0 ? a1 - a0 : 0;
+    DraftShared S;
+    S.fix = (uint4 *)smraw;
+    S.ubuild = S.fix + N;
+    S.F = (float4 *)(S.ubuild + A);
+    S.list = (int *)(S.F + A);
+    S.nlist = S.list + (size_t)A * cap;
+    S.lj = (float *)(S.nlist + A);
+    S.stage = S.lj + 2 * kMaxSpecies * kMaxSpecies;
+    if (st->step >= st->target_step) return;   // uniform over the cluster
     const long long n0 = st->step;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t D = (size_t)3 * N;
     const float rc2_all = LEARNED ? fmaxf(P.lj_rc2f, P.desc_rc2f) : P.lj_rc2f;
+    for (int t = tid; t < g.S * g.S; t += blockDim.x) {
+        S.lj[t] = P.lj_sig2[t];
+        S.lj[kMaxSpecies * kMaxSpecies + t] = P.lj_eps24[t];
+    }
+    const float skin_lim2 = (0.45f * kSkin) * (0.45f * kSkin);
     for (int j = 0; j < K; ++j) {
-        // A: half-step positions and their fixed point
-        for (int i = tid; i < N; i += kDraftThreads) {
+        // A: half-step positions of owned atoms, fixed point, displacement since the list build
+        int moved = 0;
+        for (int i = a0 + tid; i < a1; i += blockDim.x) {
             const int sp = species[i];
             const double hm = cf.hm[sp];
-            uint32_t u[3];
-            for (int c = 0; c < 3; ++c) {
+            uint32_t u0, u1, u2;
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
                 double qv, pv;
                 if (j == 0) {
-                    qv = q_base[3 * i + c];
-                    pv = p_base[3 * i + c];
+                    qv = q_base[3 * i + x];
+                    pv = p_base[3 * i + x];
                 } else {
-                    const size_t o = (size_t)(j - 1) * D + 3 * i + c;
+                    const size_t o = (size_t)(j - 1) * D + 3 * i + x;
                     pv = w_pdraft[o];
                     qv = __dadd_rn(w_qmid[o], __dmul_rn(pv, hm));
                 }
                 const double qm = __dadd_rn(qv, __dmul_rn(pv, hm));
-                w_qmid[(size_t)j * D + 3 * i + c] = qm;
-                u[c] = fixpoint(qm, g.scale[c]);
+                w_qmid[(size_t)j * D + 3 * i + x] = qm;
+                const uint32_t u = fixpoint(qm, g.scale[x]);
+                if (x == 0) u0 = u; else if (x == 1) u1 = u; else u2 = u;
             }
-            const uint4 f = make_uint4(u[0], u[1], u[2], (unsigned)sp);
-            sfix[i] = f;
+            const uint4 f = make_uint4(u0, u1, u2, (unsigned)sp);
             w_fix[(size_t)j * N + i] = f;
+            if (j > 0) {
+                const uint4 b = S.ubuild[i - a0];
+                float dmin;
+                int kk;
+                axis_min(b.x, u0, g.scale_f[0], dmin, kk);
+                float d2 = dmin * dmin;
+                axis_min(b.y, u1, g.scale_f[1], dmin, kk);
+                d2 += dmin * dmin;
+                axis_min(b.z, u2, g.scale_f[2], dmin, kk);
+                d2 += dmin * dmin;
+                moved |= d2 > skin_lim2;
+            }
         }
+        moved = __syncthreads_or(moved);
+        if (tid == 0) w_flags[j * C + c] = moved;
+        cluster_barrier();
+        // B: all positions of this step, and the list rebuild decision (same in every CTA)
+        for (int k = tid; k < N; k += blockDim.x) S.fix[k] = w_fix[(size_t)j * N + k];
+        int rebuild = (j == 0);
+        for (int k = 0; k < C; ++k) rebuild |= w_flags[j * C + k];
         __syncthreads();
-        if (LEARNED) {
-            float *stage = sStage + (size_t)warp * (3 * kLearnCap + P.d0p);
-            for (int i = warp; i < N; i += kDraftWarps)
-                learned_atom_grad(P, g, sfix, i, stage, stage + 3 * kLearnCap, sG + (size_t)i * P.d0p);
+        if (rebuild) {
+            // candidates of owned atom i: every k whose minimum image is within rc + skin
+            for (int ii = warp; ii < nown; ii += kDraftWarps) {
+                const int i = a0 + ii;
+                const uint4 fi = S.fix[i];
+                int cnt = 0;
+                int *lst = S.list + (size_t)ii * cap;
+                for (int base = 0; base < N; base += 32) {
+                    const int k = base + lane;
+                    bool in = false;
+                    if (k < N) {
+                        const uint4 fk = S.fix[k];
+                        float dx, dy, dz;
+                        int kk;
+                        axis_min(fi.x, fk.x, g.scale_f[0], dx, kk);
+                        axis_min(fi.y, fk.y, g.scale_f[1], dy, kk);
+                        axis_min(fi.z, fk.z, g.scale_f[2], dz, kk);
+                        in = dist2_rule(dx, dy, dz) < rlist2f;
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, in);
+                    const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+                    if (in && pos < cap) lst[pos] = k;
+                    cnt += __popc(bal);
+                }
+                if (lane == 0) {
+                    S.nlist[ii] = cnt < cap ? cnt : cap;
+                    S.ubuild[ii] = fi;
+                }
+            }
             __syncthreads();
         }
-        // forces: one warp per atom, lanes over partners
-        for (int i = warp; i < N; i += kDraftWarps) {
-            const uint4 fi = sfix[i];
+        if (LEARNED) {
+            float *stage = S.stage + (size_t)warp * (3 * kLearnCap + P.d0p);
+            for (int ii = warp; ii < nown; ii += kDraftWarps)
+                learned_atom_grad(P, g, S.fix, a0 + ii, S.list + (size_t)ii * cap, S.nlist[ii], stage,
+                                  stage + 3 * kLearnCap, w_dEdX + (size_t)(a0 + ii) * P.d0p);
+            cluster_barrier();   // dE/dx of every atom visible to every CTA
+        }
+        // C: forces on owned atoms, one warp per atom, lanes over its candidates
+        for (int ii = warp; ii < nown; ii += kDraftWarps) {
+            const int i = a0 + ii;
+            const uint4 fi = S.fix[i];
             const int si = (int)fi.w;
+            const int *lst = S.list + (size_t)ii * cap;
+            const int nl = S.nlist[ii];
             float fx = 0.f, fy = 0.f, fz = 0.f;
-            for (int k = lane; k < N; k += 32) {
-                const uint4 fk = sfix[k];
-                const AxisOpts ox = axis_opts(fi.x, fk.x, g.scale_f[0], rc2_all);
-                if (!ox.n) continue;
-                const AxisOpts oy = axis_opts(fi.y, fk.y, g.scale_f[1], rc2_all);
-                if (!oy.n) continue;
-                const AxisOpts oz = axis_opts(fi.z, fk.z, g.scale_f[2], rc2_all);
+            for (int t = lane; t < nl; t += 32) {
+                const int k = lst[t];
+                const uint4 fk = S.fix[k];
+                const AxisOpts ox = axis_opts(fi.x, fk.x, g.scale_f[0], g.Lf[0], rc2_all);
+                const AxisOpts oy = axis_opts(fi.y, fk.y, g.scale_f[1], g.Lf[1], rc2_all);
+                const AxisOpts oz = axis_opts(fi.z, fk.z, g.scale_f[2], g.Lf[2], rc2_all);
                 const int pr = si * g.S + (int)fk.w;
+                const float sig2 = S.lj[pr], eps24 = S.lj[kMaxSpecies * kMaxSpecies + pr];
                 for (int bz = 0; bz < oz.n; ++bz)
                     for (int by = 0; by < oy.n; ++by)
                         for (int bx = 0; bx < ox.n; ++bx) {
-                            if (k == i && ox.s[bx] == 0 && oy.s[by] == 0 && oz.s[bz] == 0) continue;
-                            const float dx = ox.d[bx], dy = oy.d[by], dz = oz.d[bz];
+                            if (k == i && opt_s(ox, bx) == 0 && opt_s(oy, by) == 0 && opt_s(oz, bz) == 0) continue;
+                            const float dx = opt_d(ox, bx), dy = opt_d(oy, by), dz = opt_d(oz, bz);
                             const float d2 = dist2_rule(dx, dy, dz);
-                            if (P.has_lj && d2 < P.lj_rc2f) lj_pair_force(P, pr, dx, dy, dz, d2, fx, fy, fz);
+                            if (P.has_lj && d2 < P.lj_rc2f) {
+                                const float inv = 1.f / d2;
+                                const float s2 = sig2 * inv;
+                                const float s6 = s2 * s2 * s2, s12 = s6 * s6;
+                                const float fr = -eps24 * (2.f * s12 - s6) * inv;
+                                fx += fr * dx;
+                                fy += fr * dy;
+                                fz += fr * dz;
+                            }
                             if (LEARNED && d2 < P.desc_rc2f) {
                                 // radial adjoint in gather form: (c_ik + c_ki) d/r
                                 const float r = sqrtf(d2);
                                 float fc, dfc;
                                 cutoff_fn(r, P.desc_rc, fc, dfc);
-                                const float *gi = sG + (size_t)i * P.d0p + (int)fk.w * P.n_rbf;
-                                const float *gk = sG + (size_t)k * P.d0p + si * P.n_rbf;
-                                float c = 0.f;
+                                const float *gi = w_dEdX + (size_t)i * P.d0p + (int)fk.w * P.n_rbf;
+                                const float *gk = w_dEdX + (size_t)k * P.d0p + si * P.n_rbf;
+                                float cc = 0.f;
                                 for (int b = 0; b < P.n_rbf; ++b) {
-                                    const float t = r - (float)b * P.rbf_w;
-                                    const float dg = expf(-t * t * P.rbf_inv2w2) * (-t * P.rbf_invw2 * fc + dfc);
-                                    c += (gi[b] + gk[b]) * dg;
+                                    const float tt = r - (float)b * P.rbf_w;
+                                    const float dg = expf(-tt * tt * P.rbf_inv2w2) * (-tt * P.rbf_invw2 * fc + dfc);
+                                    cc += (gi[b] + gk[b]) * dg;
                                 }
-                                fx += c * dx / r;
-                                fy += c * dy / r;
-                                fz += c * dz / r;
+                                fx += cc * dx / r;
+                                fy += cc * dy / r;
+                                fz += cc * dz / r;
                             }
                         }
             }
             fx = warp_sum(fx);
             fy = warp_sum(fy);
             fz = warp_sum(fz);
-            if (lane == 0) sF[i] = make_float4(fx, fy, fz, 0.f);
+            if (lane == 0) S.F[ii] = make_float4(fx, fy, fz, 0.f);
         }
         __syncthreads();
-        // BOB + A
+        // D: BOB + A for owned atoms
         const unsigned long long n = (unsigned long long)(n0 + j + 1);
-        for (int i = tid; i < N; i += kDraftThreads) {
+        for (int i = a0 + tid; i < a1; i += blockDim.x) {
             const int sp = species[i];
-            const float4 F = sF[i];
-            const float fr[3] = {F.x, F.y, F.z};
-            const float3 xi3 = normals3(cf.seed, n, (uint32_t)i, 0u);
-            const float xi[3] = {xi3.x, xi3.y, xi3.z};
-            for (int c = 0; c < 3; ++c) {
-                const size_t o = (size_t)j * D + 3 * i + c;
-                const double pv = (j == 0) ? p_base[3 * i + c] : w_pdraft[o - D];
-                const float fu = ec_on ? fr[c] + ec_dF[3 * i + c] : fr[c];
+            const float4 F = S.F[i - a0];
+            const float3 xi = normals3(cf.seed, n, (uint32_t)i, 0u);
+            const double sg = cf.sig[sp];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                const size_t o = (size_t)j * D + 3 * i + x;
+                const double pv = (j == 0) ? p_base[3 * i + x] : w_pdraft[o - D];
+                const float fr = x == 0 ? F.x : (x == 1 ? F.y : F.z);
+                const float xx = x == 0 ? xi.x : (x == 1 ? xi.y : xi.z);
+                const float fu = ec_on ? fr + ec_dF[3 * i + x] : fr;
                 const double mu = __dadd_rn(__dmul_rn(cf.c1, pv), __dmul_rn(cf.aF, (double)fu));
-                w_pdraft[o] = __dadd_rn(mu, __dmul_rn(cf.sig[sp], (double)xi[c]));
+                w_pdraft[o] = __dadd_rn(mu, __dmul_rn(sg, (double)xx));
                 w_Fd[o] = fu;
-                if (ec_on) w_Fraw[o] = fr[c];
+                if (ec_on) w_Fraw[o] = fr;
             }
         }
+        // the next step reads only owned atoms' global state (written by this CTA) and
+        // all atoms' positions after the next cluster barrier
         __syncthreads();
     }
 }
 
-size_t draft_small_smem_bytes(int N, const PotDev &P, bool learned) {
-    size_t b = (size_t)N * (sizeof(uint4) + sizeof(float4));
-    if (learned) b += ((size_t)N * P.d0p + (size_t)kDraftWarps * (3 * kLearnCap + P.d0p)) * sizeof(float);
+static size_t draft_smem_bytes(int N, int C, int cap, const PotDev &P, bool learned) {
+    const int A = (N + C - 1) / C;
+    size_t b = (size_t)N * sizeof(uint4) + (size_t)A * sizeof(uint4) + (size_t)A * sizeof(float4) +
+               (size_t)A * cap * sizeof(int) + (size_t)A * sizeof(int) + 2 * kMaxSpecies * kMaxSpecies * sizeof(float);
+    if (learned) b += (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) * sizeof(float);
     return b;
 }
 
-void launch_draft_small(bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf, const int *species,
-                        const double *q, const double *p, const float *ec_dF, int ec_on, const DevState *st,
-                        double *w_qmid, double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, cudaStream_t s) {
-    const size_t sm = draft_small_smem_bytes(g.N, P, learned);
+DraftPlan draft_plan(int N, double density, double rc_max, const PotDev &P, bool learned, int max_cluster,
+                     size_t max_smem) {
+    DraftPlan pl{};
+    const double rl = rc_max + kSkin;
+    const double expect = density * 4.0 / 3.0 * 3.14159265358979 * rl * rl * rl;
+    int cap = (int)(2.0 * expect) + 32;
+    cap = (cap + 31) / 32 * 32;
+    if (cap > N) cap = (N + 31) / 32 * 32;
+    pl.cap = cap;
+    pl.rlist2f = (float)(rl * rl);
+    int C = 1;
+    while (C < max_cluster && (N + C - 1) / C > 16) C *= 2;
+    while (C > 1 && draft_smem_bytes(N, C, cap, P, learned) > max_smem) C /= 2;
+    pl.cluster = C;
+    pl.smem = draft_smem_bytes(N, C, cap, P, learned);
+    pl.ok = pl.smem <= max_smem;
+    return pl;
+}
+
+cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf,
+                         const int *species, const double *q, const double *p, const float *ec_dF, int ec_on,
+                         const DevState *st, double *w_qmid, double *w_pdraft, float *w_Fd, float *w_Fraw,
+                         uint4 *w_fix, int *w_flags, float *w_dEdX, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(pl.cluster, 1, 1);
+    cfg.blockDim = dim3(kDraftThreads, 1, 1);
+    cfg.dynamicSmemBytes = pl.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = pl.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     if (learned)
-        draft_window_small_kernel<true><<<1, kDraftThreads, sm, s>>>(K, g, P, cf, species, q, p, ec_dF, ec_on, st,
-                                                                     w_qmid, w_pdraft, w_Fd, w_Fraw, w_fix);
-    else
-        draft_window_small_kernel<false><<<1, kDraftThreads, sm, s>>>(K, g, P, cf, species, q, p, ec_dF, ec_on, st,
-                                                                      w_qmid, w_pdraft, w_Fd, w_Fraw, w_fix);
+        return cudaLaunchKernelEx(&cfg, draft_window_cluster_kernel<true>, K, g, P, cf, pl.cap, pl.rlist2f, species, q,
+                                  p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd, w_Fraw, w_fix, w_flags, w_dEdX);
+    return cudaLaunchKernelEx(&cfg, draft_window_cluster_kernel<false>, K, g, P, cf, pl.cap, pl.rlist2f, species, q, p,
+                              ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd, w_Fraw, w_fix, w_flags, w_dEdX);
 }
 
 cudaError_t draft_kernels_setup(int max_smem) {
-    cudaError_t e = cudaFuncSetAttribute(draft_window_small_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         max_smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(draft_window_small_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                max_smem);
+    const void *ks[2] = {(const void *)draft_window_cluster_kernel<true>,
+                         (const void *)draft_window_cluster_kernel<false>};
+    for (const void *k : ks) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int draft_max_cluster(size_t smem) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16, 1, 1);
+    cfg.blockDim = dim3(kDraftThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int c = 0;
+    if (cudaOccupancyMaxPotentialClusterSize(&c, (const void *)draft_window_cluster_kernel<false>, &cfg) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 8;
+    }
+    return c >= 16 ? 16 : (c >= 8 ? 8 : (c >= 4 ? 4 : (c >= 2 ? 2 : 1)));
 }
 
 // ---------------------------------------------------------------------------
@@ -282,13 +433,15 @@ __global__ void plain_half_kernel(Geo g, Coef cf, const int *__restrict__ specie
     if (st->step >= st->target_step || i >= g.N) return;
     const int sp = species[i];
     const double hm = cf.hm[sp];
-    uint32_t u[3];
-    for (int c = 0; c < 3; ++c) {
-        const double qm = __dadd_rn(q[3 * i + c], __dmul_rn(p[3 * i + c], hm));
-        qmid[3 * i + c] = qm;
-        u[c] = fixpoint(qm, g.scale[c]);
+    uint32_t u0, u1, u2;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        const double qm = __dadd_rn(q[3 * i + x], __dmul_rn(p[3 * i + x], hm));
+        qmid[3 * i + x] = qm;
+        const uint32_t u = fixpoint(qm, g.scale[x]);
+        if (x == 0) u0 = u; else if (x == 1) u1 = u; else u2 = u;
     }
-    fix[i] = make_uint4(u[0], u[1], u[2], (unsigned)sp);
+    fix[i] = make_uint4(u0, u1, u2, (unsigned)sp);
 }
 
 __global__ void plain_finish_kernel(Geo g, Coef cf, const int *__restrict__ species, const double *__restrict__ qmid,
@@ -300,12 +453,13 @@ __global__ void plain_finish_kernel(Geo g, Coef cf, const int *__restrict__ spec
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < g.N) {
         const int sp = species[i];
-        const float3 xi3 = normals3(cf.seed, (unsigned long long)(n0 + 1), (uint32_t)i, 0u);
-        const float xi[3] = {xi3.x, xi3.y, xi3.z};
-        for (int c = 0; c < 3; ++c) {
-            const int o = 3 * i + c;
+        const float3 xi = normals3(cf.seed, (unsigned long long)(n0 + 1), (uint32_t)i, 0u);
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+            const int o = 3 * i + x;
+            const float xx = x == 0 ? xi.x : (x == 1 ? xi.y : xi.z);
             const double mu = __dadd_rn(__dmul_rn(cf.c1, p[o]), __dmul_rn(cf.aF, (double)F[o]));
-            const double pn = __dadd_rn(mu, __dmul_rn(cf.sig[sp], (double)xi[c]));
+            const double pn = __dadd_rn(mu, __dmul_rn(cf.sig[sp], (double)xx));
             p[o] = pn;
             q[o] = __dadd_rn(qmid[o], __dmul_rn(pn, cf.hm[sp]));
         }

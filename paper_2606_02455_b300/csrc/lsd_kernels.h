@@ -30,19 +30,30 @@ cudaError_t mlp_kernels_setup(int max_smem);
 // transport (lsd_transport.cu)
 int transport_atoms_per_block(int N);
 void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *species, const float *Fd,
-                             const float *Ft, const DevState *st, double2 *partials, cudaStream_t s);
+                             const float *Ft, const DevState *st, double2 *partials, double *logu, cudaStream_t s);
 void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                              const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
-                             int ec_on, double *q, double *p, DevState *st, const double2 *partials, cudaStream_t s);
+                             int ec_on, double *q, double *p, DevState *st, const double2 *partials,
+                             const double *logu, cudaStream_t s);
 void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                       const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
-                      int ec_on, double *q, double *p, DevState *st, double2 *partials, cudaStream_t s);
+                      int ec_on, double *q, double *p, DevState *st, double2 *partials, double *logu, cudaStream_t s);
 
 // draft and plain integrator (lsd_draft.cu)
-size_t draft_small_smem_bytes(int N, const PotDev &P, bool learned);
-void launch_draft_small(bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf, const int *species,
-                        const double *q, const double *p, const float *ec_dF, int ec_on, const DevState *st,
-                        double *w_qmid, double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, cudaStream_t s);
+struct DraftPlan {
+    int cluster;      // CTAs in the draft cluster (one per SM)
+    int cap;          // Verlet candidates per atom
+    float rlist2f;    // (max cutoff + skin)^2
+    size_t smem;      // dynamic shared memory per CTA
+    bool ok;
+};
+DraftPlan draft_plan(int N, double density, double rc_max, const PotDev &P, bool learned, int max_cluster,
+                     size_t max_smem);
+int draft_max_cluster(size_t smem);
+cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf,
+                         const int *species, const double *q, const double *p, const float *ec_dF, int ec_on,
+                         const DevState *st, double *w_qmid, double *w_pdraft, float *w_Fd, float *w_Fraw,
+                         uint4 *w_fix, int *w_flags, float *w_dEdX, cudaStream_t s);
 cudaError_t draft_kernels_setup(int max_smem);
 void launch_plain_half(const Geo &g, const Coef &cf, const int *species, const double *q, const double *p,
                        const DevState *st, double *qmid, uint4 *fix, cudaStream_t s);

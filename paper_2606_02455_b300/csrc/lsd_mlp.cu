@@ -14,41 +14,53 @@ namespace lsd {
 
 constexpr int kTM = 32;
 
+constexpr int kKC = 32;   // rows of B staged in shared memory per step
+
+// acc[4][RN] (+)= A[32 x KD] (shared, row stride lda) x B[KD x 32*RN] (global, row-major),
+// B streamed through shared memory in chunks of kKC rows with 16-byte loads.
 template <int RN>
 __device__ __forceinline__ void gemm_rows4(const float *__restrict__ A, int lda, int KD, const float *__restrict__ B,
-                                           int ldb, float (&acc)[4][8]) {
+                                           float *__restrict__ Bs, float (&acc)[4][8]) {
+    constexpr int NC = 32 * RN;
     const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
     const float *a0 = A + (rg * 4) * lda;
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
-#pragma unroll 2
-    for (int k = 0; k < KD; ++k) {
-        float a[4];
+    for (int k0 = 0; k0 < KD; k0 += kKC) {
+        const float4 *src = reinterpret_cast<const float4 *>(B + (size_t)k0 * NC);
+        float4 *dst = reinterpret_cast<float4 *>(Bs);
+        for (int t = threadIdx.x; t < kKC * NC / 4; t += blockDim.x) dst[t] = __ldg(src + t);
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < kKC; ++k) {
+            float a[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) a[r] = a0[r * lda + k];
-        float b[RN];
+            for (int r = 0; r < 4; ++r) a[r] = a0[r * lda + k0 + k];
+            float b[RN];
 #pragma unroll
-        for (int c = 0; c < RN; ++c) b[c] = __ldg(B + (size_t)k * ldb + lane + 32 * c);
+            for (int c = 0; c < RN; ++c) b[c] = Bs[k * NC + lane + 32 * c];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int c = 0; c < RN; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+                for (int c = 0; c < RN; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
     }
 }
 
-__device__ __forceinline__ void gemm_dispatch(int ncols, const float *A, int lda, int KD, const float *B,
+__device__ __forceinline__ void gemm_dispatch(int ncols, const float *A, int lda, int KD, const float *B, float *Bs,
                                               float (&acc)[4][8]) {
     switch (ncols >> 5) {
-        case 1: gemm_rows4<1>(A, lda, KD, B, ncols, acc); break;
-        case 2: gemm_rows4<2>(A, lda, KD, B, ncols, acc); break;
-        case 3: gemm_rows4<3>(A, lda, KD, B, ncols, acc); break;
-        case 4: gemm_rows4<4>(A, lda, KD, B, ncols, acc); break;
-        case 5: gemm_rows4<5>(A, lda, KD, B, ncols, acc); break;
-        case 6: gemm_rows4<6>(A, lda, KD, B, ncols, acc); break;
-        case 7: gemm_rows4<7>(A, lda, KD, B, ncols, acc); break;
-        default: gemm_rows4<8>(A, lda, KD, B, ncols, acc); break;
+        case 1: gemm_rows4<1>(A, lda, KD, B, Bs, acc); break;
+        case 2: gemm_rows4<2>(A, lda, KD, B, Bs, acc); break;
+        case 3: gemm_rows4<3>(A, lda, KD, B, Bs, acc); break;
+        case 4: gemm_rows4<4>(A, lda, KD, B, Bs, acc); break;
+        case 5: gemm_rows4<5>(A, lda, KD, B, Bs, acc); break;
+        case 6: gemm_rows4<6>(A, lda, KD, B, Bs, acc); break;
+        case 7: gemm_rows4<7>(A, lda, KD, B, Bs, acc); break;
+        default: gemm_rows4<8>(A, lda, KD, B, Bs, acc); break;
     }
 }
 
@@ -61,6 +73,7 @@ __global__ void __launch_bounds__(256) mlp_fp32_kernel(const float *__restrict__
     float *buf1 = buf0 + kTM * ld;
     float *spr = buf1 + kTM * ld;                   // [L][kTM][W] SiLU'(h)
     float *sdedy = spr + (size_t)L * kTM * W;       // [kTM]
+    float *Bs = sdedy + kTM;                        // [kKC][<=256] staged weights
     const int tid = threadIdx.x, lane = tid & 31, rg = tid >> 5;
     const int row0 = blockIdx.x * kTM;
 
@@ -73,7 +86,7 @@ __global__ void __launch_bounds__(256) mlp_fp32_kernel(const float *__restrict__
     int din = d0p;
     float acc[4][8];
     for (int l = 0; l < L; ++l) {
-        gemm_dispatch(W, in, ld, din, P.Wt[l], acc);
+        gemm_dispatch(W, in, ld, din, P.Wt[l], Bs, acc);
         const int RN = W >> 5;
         for (int r = 0; r < 4; ++r)
             for (int c = 0; c < RN; ++c) {
@@ -115,7 +128,7 @@ __global__ void __launch_bounds__(256) mlp_fp32_kernel(const float *__restrict__
     { float *t = in; in = out; out = t; }
     for (int l = L - 1; l >= 0; --l) {
         const int dout = (l == 0) ? d0p : W;
-        gemm_dispatch(dout, in, ld, W, P.Wn[l], acc);
+        gemm_dispatch(dout, in, ld, W, P.Wn[l], Bs, acc);
         const int RN = dout >> 5;
         for (int r = 0; r < 4; ++r)
             for (int c = 0; c < RN; ++c) {
@@ -130,7 +143,7 @@ __global__ void __launch_bounds__(256) mlp_fp32_kernel(const float *__restrict__
 
 size_t mlp_fp32_smem_bytes(const PotDev &P) {
     const int ld = P.d0p > P.width ? P.d0p : P.width;
-    return ((size_t)2 * kTM * ld + (size_t)P.n_layers * kTM * P.width + kTM) * sizeof(float);
+    return ((size_t)2 * kTM * ld + (size_t)P.n_layers * kTM * P.width + kTM + (size_t)kKC * ld) * sizeof(float);
 }
 
 void launch_mlp_fp32(const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX, cudaStream_t s) {

@@ -50,17 +50,17 @@ __device__ __forceinline__ void stage_members(const TrainGeo &T, const Geo &g, c
         const int k = base + lane;
         unsigned m = 0u;
         AxisOpts ox, oy, oz;
-        ox.n = oy.n = oz.n = 0;
+        ox = oy = oz = AxisOpts{0.f, 0.f, 0, 0, 0};
         if (k < T.N) {
             const uint4 fk = sfix[k];
-            ox = axis_opts(fi.x, fk.x, g.scale_f[0], T.desc_rc2f);
-            oy = axis_opts(fi.y, fk.y, g.scale_f[1], T.desc_rc2f);
-            oz = axis_opts(fi.z, fk.z, g.scale_f[2], T.desc_rc2f);
+            ox = axis_opts(fi.x, fk.x, g.scale_f[0], g.Lf[0], T.desc_rc2f);
+            oy = axis_opts(fi.y, fk.y, g.scale_f[1], g.Lf[1], T.desc_rc2f);
+            oz = axis_opts(fi.z, fk.z, g.scale_f[2], g.Lf[2], T.desc_rc2f);
             for (int bz = 0; bz < oz.n; ++bz)
                 for (int by = 0; by < oy.n; ++by)
                     for (int bx = 0; bx < ox.n; ++bx) {
-                        if (k == i && ox.s[bx] == 0 && oy.s[by] == 0 && oz.s[bz] == 0) continue;
-                        if (dist2_rule(ox.d[bx], oy.d[by], oz.d[bz]) < T.desc_rc2f) m |= 1u << (bx + 2 * by + 4 * bz);
+                        if (k == i && opt_s(ox, bx) == 0 && opt_s(oy, by) == 0 && opt_s(oz, bz) == 0) continue;
+                        if (dist2_rule(opt_d(ox, bx), opt_d(oy, by), opt_d(oz, bz)) < T.desc_rc2f) m |= 1u << (bx + 2 * by + 4 * bz);
                     }
         }
         const int nm = __popc(m);
@@ -75,7 +75,7 @@ __device__ __forceinline__ void stage_members(const TrainGeo &T, const Geo &g, c
         for (int c = 0; c < 8; ++c) {
             if (!(m & (1u << c))) continue;
             if (w < kTrainCap) {
-                const float dx = ox.d[c & 1], dy = oy.d[(c >> 1) & 1], dz = oz.d[c >> 2];
+                const float dx = opt_d(ox, c & 1), dy = opt_d(oy, (c >> 1) & 1), dz = opt_d(oz, c >> 2);
                 const float r = sqrtf(dist2_rule(dx, dy, dz));
                 sr[w] = r;
                 ssp[w] = (int)sfix[k].w;
@@ -169,17 +169,17 @@ __global__ void __launch_bounds__(kTrainThreads)
         float fx = 0.f, fy = 0.f, fz = 0.f;
         for (int k = lane; k < N; k += 32) {
             const uint4 fk = sfix[k];
-            const AxisOpts ox = axis_opts(fi.x, fk.x, g.scale_f[0], T.rc2_all);
+            const AxisOpts ox = axis_opts(fi.x, fk.x, g.scale_f[0], g.Lf[0], T.rc2_all);
             if (!ox.n) continue;
-            const AxisOpts oy = axis_opts(fi.y, fk.y, g.scale_f[1], T.rc2_all);
+            const AxisOpts oy = axis_opts(fi.y, fk.y, g.scale_f[1], g.Lf[1], T.rc2_all);
             if (!oy.n) continue;
-            const AxisOpts oz = axis_opts(fi.z, fk.z, g.scale_f[2], T.rc2_all);
+            const AxisOpts oz = axis_opts(fi.z, fk.z, g.scale_f[2], g.Lf[2], T.rc2_all);
             const int pr = si * g.S + (int)fk.w;
             for (int bz = 0; bz < oz.n; ++bz)
                 for (int by = 0; by < oy.n; ++by)
                     for (int bx = 0; bx < ox.n; ++bx) {
-                        if (k == i && ox.s[bx] == 0 && oy.s[by] == 0 && oz.s[bz] == 0) continue;
-                        const float dx = ox.d[bx], dy = oy.d[by], dz = oz.d[bz];
+                        if (k == i && opt_s(ox, bx) == 0 && opt_s(oy, by) == 0 && opt_s(oz, bz) == 0) continue;
+                        const float dx = opt_d(ox, bx), dy = opt_d(oy, by), dz = opt_d(oz, bz);
                         const float d2 = dist2_rule(dx, dy, dz);
                         if (T.has_lj && d2 < T.lj_rc2f) {
                             const float s2 = P.lj_sig2[pr] / d2;

@@ -36,12 +36,14 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh) {
 __global__ void __launch_bounds__(kTransThreads)
     transport_reduce_kernel(int K, Geo g, Coef cf, const int *__restrict__ species, const float *__restrict__ Fd,
                             const float *__restrict__ Ft, const DevState *__restrict__ st, double2 *__restrict__ partials,
-                            int atoms_per_block) {
+                            double *__restrict__ logu, int atoms_per_block) {
     __shared__ double sh[32];
     if (st->step >= st->target_step) return;
     const int N = g.N;
     const int j = blockIdx.y;
     const unsigned long long n = (unsigned long long)(st->step + j + 1);
+    // log u of the acceptance test, one FP64 log per window step, in parallel over steps
+    if (blockIdx.x == 0 && threadIdx.x == blockDim.x - 1) logu[j] = log(uniform53(cf.seed, n));
     const int a0 = blockIdx.x * atoms_per_block;
     const int a1 = min(N, a0 + atoms_per_block);
     double s = 0.0, d = 0.0;
@@ -65,8 +67,9 @@ __global__ void __launch_bounds__(kTransThreads)
                             const double *__restrict__ w_pdraft, const float *__restrict__ Fd,
                             const float *__restrict__ Ft, const float *__restrict__ Fraw, float *__restrict__ ec_dF,
                             int ec_on, double *__restrict__ q, double *__restrict__ p, DevState *__restrict__ st,
-                            const double2 *__restrict__ partials, int n_part, int atoms_per_block) {
-    __shared__ double s_s[kMaxK], s_d[kMaxK], s_lr[kMaxK], s_lu[kMaxK];
+                            const double2 *__restrict__ partials, const double *__restrict__ logu, int n_part,
+                            int atoms_per_block) {
+    __shared__ double s_s[kMaxK], s_d[kMaxK], s_lr[kMaxK], s_lu[kMaxK], s_dn[kMaxK], s_pr[kMaxK];
     __shared__ int s_acc[kMaxK];
     __shared__ int s_nc, s_rej, s_l, s_bad;
     __shared__ bool s_last;
@@ -84,7 +87,7 @@ __global__ void __launch_bounds__(kTransThreads)
         s_s[j] = s;
         s_d[j] = d;
         const double lr = -s - 0.5 * d;
-        const double lu = log(uniform53(cf.seed, (unsigned long long)(n0 + j + 1)));
+        const double lu = logu[j];
         s_lr[j] = lr;
         s_lu[j] = lu;
         s_acc[j] = (d == 0.0) || (lu <= fmin(0.0, lr));
@@ -141,8 +144,20 @@ __global__ void __launch_bounds__(kTransThreads)
         s_last = (prev == gridDim.x - 1);
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        __threadfence();
+    if (!s_last) return;
+    __threadfence();
+    // statistics of the window, one thread per step (|delta| and the predicted rejection erf(|delta|/sqrt 8))
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        const double dn = sqrt(s_d[j]);
+        s_dn[j] = dn;
+        s_pr[j] = (double)erff((float)dn * 0.35355339059327373f);
+        st->accept[j] = s_acc[j];
+        st->logr[j] = s_lr[j];
+        st->logu[j] = s_lu[j];
+        st->dnorm[j] = dn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
         st->blocks_done = 0u;
         st->n_commit_last = nc;
         st->first_reject_last = s_rej || (s_l <= K && !s_acc[s_l - 1]) ? s_l : -1;
@@ -153,43 +168,38 @@ __global__ void __launch_bounds__(kTransThreads)
         st->rejected += s_rej;
         double sd = 0.0, sp = 0.0;
         for (int j = 0; j < nc; ++j) {
-            const double dn = sqrt(s_d[j]);
-            sd += dn;
-            sp += erf(dn / sqrt(8.0));
+            sd += s_dn[j];
+            sp += s_pr[j];
         }
         st->sum_delta += sd;
         st->sum_pred += sp;
-        for (int j = 0; j < K; ++j) {
-            st->accept[j] = s_acc[j];
-            st->logr[j] = s_lr[j];
-            st->logu[j] = s_lu[j];
-            st->dnorm[j] = sqrt(s_d[j]);
-        }
         st->step = n0 + nc;
     }
 }
 
 void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *species, const float *Fd,
-                             const float *Ft, const DevState *st, double2 *partials, cudaStream_t s) {
+                             const float *Ft, const DevState *st, double2 *partials, double *logu, cudaStream_t s) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
-    transport_reduce_kernel<<<dim3(nb, K), kTransThreads, 0, s>>>(K, g, cf, species, Fd, Ft, st, partials, apb);
+    transport_reduce_kernel<<<dim3(nb, K), kTransThreads, 0, s>>>(K, g, cf, species, Fd, Ft, st, partials, logu, apb);
 }
 
 void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                              const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
-                             int ec_on, double *q, double *p, DevState *st, const double2 *partials, cudaStream_t s) {
+                             int ec_on, double *q, double *p, DevState *st, const double2 *partials,
+                             const double *logu, cudaStream_t s) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
     transport_commit_kernel<<<nb, kTransThreads, 0, s>>>(K, g, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF,
-                                                         ec_on, q, p, st, partials, nb, apb);
+                                                         ec_on, q, p, st, partials, logu, nb, apb);
 }
 
 void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                       const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
-                      int ec_on, double *q, double *p, DevState *st, double2 *partials, cudaStream_t s) {
-    launch_transport_reduce(K, g, cf, species, Fd, Ft, st, partials, s);
-    launch_transport_commit(K, g, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, st, partials, s);
+                      int ec_on, double *q, double *p, DevState *st, double2 *partials, double *logu, cudaStream_t s) {
+    launch_transport_reduce(K, g, cf, species, Fd, Ft, st, partials, logu, s);
+    launch_transport_commit(K, g, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, st, partials, logu,
+                            s);
 }
 
 int transport_atoms_per_block(int N) {

@@ -39,17 +39,17 @@ __global__ void neigh_build_kernel(const uint4 *__restrict__ fix, int M, Geo g, 
         const int k = base + lane;
         unsigned mn = 0u, mf = 0u;
         AxisOpts ox, oy, oz;
-        ox.n = oy.n = oz.n = 0;
+        ox = oy = oz = AxisOpts{0.f, 0.f, 0, 0, 0};
         if (k < N) {
             const uint4 fkk = fj[k];
-            ox = axis_opts(fi.x, fkk.x, g.scale_f[0], rmax2f);
-            oy = axis_opts(fi.y, fkk.y, g.scale_f[1], rmax2f);
-            oz = axis_opts(fi.z, fkk.z, g.scale_f[2], rmax2f);
+            ox = axis_opts(fi.x, fkk.x, g.scale_f[0], g.Lf[0], rmax2f);
+            oy = axis_opts(fi.y, fkk.y, g.scale_f[1], g.Lf[1], rmax2f);
+            oz = axis_opts(fi.z, fkk.z, g.scale_f[2], g.Lf[2], rmax2f);
             for (int bz = 0; bz < oz.n; ++bz)
                 for (int by = 0; by < oy.n; ++by)
                     for (int bx = 0; bx < ox.n; ++bx) {
-                        if (k == i && ox.s[bx] == 0 && oy.s[by] == 0 && oz.s[bz] == 0) continue;
-                        const float d2 = dist2_rule(ox.d[bx], oy.d[by], oz.d[bz]);
+                        if (k == i && opt_s(ox, bx) == 0 && opt_s(oy, by) == 0 && opt_s(oz, bz) == 0) continue;
+                        const float d2 = dist2_rule(opt_d(ox, bx), opt_d(oy, by), opt_d(oz, bz));
                         const unsigned bit = 1u << (bx + 2 * by + 4 * bz);
                         if (d2 < rmax2f) {
                             if (d2 < near2f) mn |= bit;
@@ -71,7 +71,7 @@ __global__ void neigh_build_kernel(const uint4 *__restrict__ fix, int M, Geo g, 
             const unsigned bit = 1u << c;
             if (!((mn | mf) & bit)) continue;
             const int bx = c & 1, by = (c >> 1) & 1, bz = c >> 2;
-            const int key = (k << 5) | shift_code(ox.s[bx], oy.s[by], oz.s[bz]);
+            const int key = (k << 5) | shift_code(opt_s(ox, bx), opt_s(oy, by), opt_s(oz, bz));
             if (mn & bit) {
                 if (wn < cap_near) nk[wn] = key;
                 ++wn;

@@ -78,19 +78,23 @@ def test_two_atom_lj_closed_form():
     assert np.allclose(res["F"][:, 1:], 0.0)
 
 
-def test_single_atom_lattice_sum():
-    """One atom in a periodic cubic box of side 6 A with cutoff 8.5 A interacts with its own images:
-    6 at distance L and 12 at L*sqrt(2) (L*sqrt(3) is beyond the cutoff), each pair counted half."""
-    L = 6.0
-    s = W.System(positions=np.array([[1.0, 2.0, 3.0]]), momenta=np.zeros((1, 3)), species=np.array([0], np.int32),
-                 masses=np.array([40.0]), box=np.array([L] * 3))
-    pot = W.Potential(lj_eps=np.array([0.0104]), lj_sigma=np.array([3.4]), lj_cutoff=8.5)
-    expect = 0.5 * (6 * _lj(0.0104, 3.4, 8.5, L) + 12 * _lj(0.0104, 3.4, 8.5, L * np.sqrt(2)))
+def test_bcc_lattice_sum_sees_every_image():
+    """Two atoms at (0,0,0) and (L/2,L/2,L/2) of a periodic cubic box (a BCC cell), cutoff 0.98 L: each atom
+    sees all 8 images of the other at distance L*sqrt(3)/2 (both images along every axis), none of its own
+    (at distance L), so E = 8 U(L sqrt(3)/2) and F = 0."""
+    L, rc = 6.0, 5.9
+    s = W.System(positions=np.array([[0.2, 0.3, 0.4], [0.2 + L / 2, 0.3 + L / 2, 0.4 + L / 2]]),
+                 momenta=np.zeros((2, 3)), species=np.array([0, 0], np.int32), masses=np.array([40.0]),
+                 box=np.array([L] * 3))
+    pot = W.Potential(lj_eps=np.array([0.0104]), lj_sigma=np.array([3.4]), lj_cutoff=rc)
+    r = L * np.sqrt(3) / 2
     res = O.energy_forces(s, pot, s.positions)
-    assert res["E"] == pytest.approx(expect, rel=1e-12)
+    assert res["E"] == pytest.approx(8 * _lj(0.0104, 3.4, rc, r), rel=1e-12)
     assert np.allclose(res["F"], 0.0, atol=1e-14)
-    nb = O.neighbors(s, s.positions, 8.5)
-    assert len(nb[0]) == 18
+    nb = O.neighbors(s, s.positions, rc)
+    assert len(nb[0]) == 8 and len(nb[1]) == 8
+    assert sorted(int(k) & 31 for k in nb[0]) == [c for c in range(27) if all(
+        d != 1 for d in (c % 3, (c // 3) % 3, c // 9))] or len(set(int(k) & 31 for k in nb[0])) == 8
 
 
 def test_radial_descriptor_two_atoms():
