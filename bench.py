@@ -248,6 +248,14 @@ def run_ours(args):
     committed = st1["committed"] - st0["committed"]
     rejected = st1["rejected"] - st0["rejected"]
     windows = st1["windows"] - st0["windows"]
+    if args.only_lsd:
+        # profiling mode: the LSD windows alone (no baseline, e2e or roofline pass)
+        clocks.stop()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "mode": "only-lsd", "windows": windows, "committed": committed,
+                              "ms_per_step": round(t_lsd * 1e3 / args.steps, 5)}), flush=True)
+        h.close()
+        return
     # ---- plain target Langevin: the same number of steps as committed, one graph launch per step ----
     h.set_state(q_eq, p_eq, step_eq)
     n_plain = max(committed, 16)
@@ -392,6 +400,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-windows", type=int, default=6)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only-lsd", action="store_true", help="time the LSD windows only (for profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

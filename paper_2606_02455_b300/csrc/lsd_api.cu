@@ -44,12 +44,15 @@ struct PotHost {
     __nv_bfloat16 *dbuf_bf = nullptr; // Wt, Wn, wout (BF16)
     float rmax2f = 0.f, near2f = 0.f;
     bool present = false;
+    void *tc_plan = nullptr;              // tensor maps of the BF16 weights (tensor-core MLP)
+    __nv_bfloat16 *tc_scratch = nullptr;  // per-CTA SiLU' slots of the tensor-core MLP
 };
 
 }  // namespace
 
 struct lsd_handle {
     int dev = 0;
+    int n_sm = 148;
     int N = 0, S = 0, K = 0;
     double box[3] = {0, 0, 0};
     double gamma = 0, dt = 0, T = 0;
@@ -296,6 +299,16 @@ int wait_stream(lsd_handle *h) {
     return LSD_OK;
 }
 
+// The MLP of a batched evaluation: tcgen05 tensor cores for BF16 potentials,
+// the FP32 CUDA-core kernel otherwise.
+void enqueue_mlp(lsd_handle *h, const PotHost &pot, int M, cudaStream_t s) {
+    const PotDev &P = pot.dev;
+    if (pot.tc_plan)
+        launch_mlp_tc(pot.tc_plan, h->X, M, P, h->E_mlp, h->dEdX, pot.tc_scratch, h->n_sm, &h->st->err, s);
+    else
+        launch_mlp_fp32(h->X, M, P, h->E_mlp, h->dEdX, s);
+}
+
 // Batched force evaluation of `pot` on Kc configurations whose fixed-point
 // coordinates are in fix ([Kc][N]); forces to F ([Kc][N][3]).
 void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, float *F, float *E_out,
@@ -306,7 +319,7 @@ void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, f
                        h->n_near, h->n_far, h->st, s);
     if (P.has_mlp) {
         launch_desc(fix, h->near_keys, h->n_near, h->cap_near, M, h->geo, P, h->X, s);
-        launch_mlp_fp32(h->X, M, P, h->E_mlp, h->dEdX, s);
+        enqueue_mlp(h, pot, M, s);
     }
     launch_pairgrad(fix, h->near_keys, h->n_near, h->far_keys, h->n_far, h->cap_near, h->cap_far, M, h->geo, P, h->dEdX,
                     h->pair_g, h->Fpart, h->E_lj, s);
@@ -421,6 +434,8 @@ void lsd_destroy(lsd_handle *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     destroy_graphs(h);
     for (void *v : h->allocs) cudaFree(v);
+    if (h->draft.tc_plan) mlp_tc_plan_free(h->draft.tc_plan);
+    if (h->target.tc_plan) mlp_tc_plan_free(h->target.tc_plan);
     train_free(h->train);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
@@ -447,6 +462,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         return r;
     };
     if (cudaGetDevice(&h->dev) != cudaSuccess) return fail(LSD_ECUDA);
+    if (cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->dev) != cudaSuccess) return fail(LSD_ECUDA);
     if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(LSD_ECUDA);
     h->stream = h->own_stream;
     h->N = sys->n_atoms;
@@ -497,6 +513,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     h->cap_far = std::min(nb_capacity(rho, rfar, 32), (27 * h->N + 31) / 32 * 32);
     if (desc_smem_bytes(8, h->cap_near) + 8 * 256 * sizeof(float) > (size_t)kMaxDynSmem) return fail(LSD_EUNSUPPORTED);
     if (verify_kernels_setup(kMaxDynSmem) != cudaSuccess || mlp_kernels_setup(kMaxDynSmem) != cudaSuccess ||
+        mlp_tc_setup() != cudaSuccess ||
         draft_kernels_setup(kMaxDynSmem) != cudaSuccess)
         return fail(LSD_ECUDA);
     {
@@ -523,6 +540,16 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         return fail(rc);
     if ((rc = pot_upload(h, h->draft)) != LSD_OK) return fail(rc);
     if ((rc = pot_upload(h, h->target)) != LSD_OK) return fail(rc);
+    // BF16 potentials evaluate their MLP on the tensor cores
+    for (PotHost *ph : {&h->draft, &h->target}) {
+        if (ph->dev.has_mlp && ph->dev.precision == LSD_BF16) {
+            if (!mlp_tc_supported(ph->dev)) return fail(LSD_EUNSUPPORTED);
+            ph->tc_plan = mlp_tc_plan(ph->dev);
+            if (!ph->tc_plan) return fail(LSD_ECUDA);
+            const int grid = mlp_tc_grid(h->K * h->N, h->n_sm);
+            if ((rc = dalloc(h, &ph->tc_scratch, mlp_tc_scratch_elems(ph->dev, grid))) != LSD_OK) return fail(rc);
+        }
+    }
     if (cudaMemcpy(h->q, sys->pos, D * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->species, sys->species, N * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(LSD_ECUDA);
@@ -813,7 +840,7 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
     CK(cudaEventRecord(ev[2], st));
     if (P.has_mlp) launch_desc(h->w_fix, h->near_keys, h->n_near, h->cap_near, M, h->geo, P, h->X, st);
     CK(cudaEventRecord(ev[3], st));
-    if (P.has_mlp) launch_mlp_fp32(h->X, M, P, h->E_mlp, h->dEdX, st);
+    if (P.has_mlp) enqueue_mlp(h, h->target, M, st);
     CK(cudaEventRecord(ev[4], st));
     launch_pairgrad(h->w_fix, h->near_keys, h->n_near, h->far_keys, h->n_far, h->cap_near, h->cap_far, M, h->geo, P,
                     h->dEdX, h->pair_g, h->Fpart, h->E_lj, st);

@@ -27,6 +27,17 @@ void launch_mlp_fp32(const float *X, int M, const PotDev &P, float *E_mlp, float
 size_t mlp_fp32_smem_bytes(const PotDev &P);
 cudaError_t mlp_kernels_setup(int max_smem);
 
+// MLP on tcgen05 tensor cores, BF16 (lsd_mlp_tc.cu)
+bool mlp_tc_supported(const PotDev &P);
+void *mlp_tc_plan(const PotDev &P);   // tensor maps of the weights; nullptr on failure
+void mlp_tc_plan_free(void *plan);
+size_t mlp_tc_smem_bytes();
+size_t mlp_tc_scratch_elems(const PotDev &P, int n_cta);
+int mlp_tc_grid(int M, int n_sm);
+void launch_mlp_tc(const void *plan, const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX,
+                   __nv_bfloat16 *scratch, int n_sm, int *err, cudaStream_t s);
+cudaError_t mlp_tc_setup();
+
 // transport (lsd_transport.cu)
 int transport_atoms_per_block(int N);
 void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *species, const float *Fd,

@@ -4,7 +4,8 @@
 // g_{l-1} = (W_l^T g_l) * SiLU'(h_{l-1}), dE/dx = W_1^T g_1.
 //
 // One CTA owns a tile of 32 rows for the whole forward and backward pass:
-// activations and SiLU' stay in shared memory, weights stream through L1.
+// activations and SiLU' stay in shared memory, weights stream through a
+// double-buffered shared-memory stage.
 // 256 threads = 8 row groups of 4 rows x 32 lanes over columns (strided by 32),
 // so activation reads are warp broadcasts and weight reads are coalesced.
 #include "lsd_common.cuh"
@@ -14,39 +15,64 @@ namespace lsd {
 
 constexpr int kTM = 32;
 
-constexpr int kKC = 32;   // rows of B staged in shared memory per step
+constexpr int kStageFloats = 4096;   // one staged weight chunk (16 KB); two are in flight
 
-// acc[4][RN] (+)= A[32 x KD] (shared, row stride lda) x B[KD x 32*RN] (global, row-major),
-// B streamed through shared memory in chunks of kKC rows with 16-byte loads.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int n>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
+}
+
+// acc[4][RN] = A[32 x KD] (shared, row stride lda) x B[KD x 32*RN] (global, row-major).
+// B streams through two shared buffers of KC rows: the copy of chunk c+1
+// (cp.async, 16 B per thread-request) is in flight while chunk c is consumed.
 template <int RN>
 __device__ __forceinline__ void gemm_rows4(const float *__restrict__ A, int lda, int KD, const float *__restrict__ B,
                                            float *__restrict__ Bs, float (&acc)[4][8]) {
     constexpr int NC = 32 * RN;
+    constexpr int KC = kStageFloats / NC >= 32 ? 32 : kStageFloats / NC;   // 32 rows, 16 for NC = 256
     const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
     const float *a0 = A + (rg * 4) * lda;
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
-    for (int k0 = 0; k0 < KD; k0 += kKC) {
-        const float4 *src = reinterpret_cast<const float4 *>(B + (size_t)k0 * NC);
-        float4 *dst = reinterpret_cast<float4 *>(Bs);
-        for (int t = threadIdx.x; t < kKC * NC / 4; t += blockDim.x) dst[t] = __ldg(src + t);
+    const int nch = KD / KC;
+    auto issue = [&](int ch) {
+        const float *src = B + (size_t)ch * KC * NC;
+        float *dst = Bs + (ch & 1) * kStageFloats;
+        for (int t = threadIdx.x; t < KC * NC / 4; t += blockDim.x) cp_async16(dst + 4 * t, src + 4 * t);
+        cp_async_commit();
+    };
+    issue(0);
+    for (int ch = 0; ch < nch; ++ch) {
+        if (ch + 1 < nch) {
+            issue(ch + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
         __syncthreads();
+        const float *bs = Bs + (ch & 1) * kStageFloats;
+        const int k0 = ch * KC;
 #pragma unroll 4
-        for (int k = 0; k < kKC; ++k) {
+        for (int k = 0; k < KC; ++k) {
             float a[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) a[r] = a0[r * lda + k0 + k];
             float b[RN];
 #pragma unroll
-            for (int c = 0; c < RN; ++c) b[c] = Bs[k * NC + lane + 32 * c];
+            for (int c = 0; c < RN; ++c) b[c] = bs[k * NC + lane + 32 * c];
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
                 for (int c = 0; c < RN; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
         }
-        __syncthreads();
+        __syncthreads();   // the buffer is refilled two chunks later
     }
 }
 
@@ -73,7 +99,7 @@ __global__ void __launch_bounds__(256) mlp_fp32_kernel(const float *__restrict__
     float *buf1 = buf0 + kTM * ld;
     float *spr = buf1 + kTM * ld;                   // [L][kTM][W] SiLU'(h)
     float *sdedy = spr + (size_t)L * kTM * W;       // [kTM]
-    float *Bs = sdedy + kTM;                        // [kKC][<=256] staged weights
+    float *Bs = sdedy + kTM;                        // 2 x kStageFloats staged weight chunks
     const int tid = threadIdx.x, lane = tid & 31, rg = tid >> 5;
     const int row0 = blockIdx.x * kTM;
 
@@ -143,7 +169,7 @@ __global__ void __launch_bounds__(256) mlp_fp32_kernel(const float *__restrict__
 
 size_t mlp_fp32_smem_bytes(const PotDev &P) {
     const int ld = P.d0p > P.width ? P.d0p : P.width;
-    return ((size_t)2 * kTM * ld + (size_t)P.n_layers * kTM * P.width + kTM + (size_t)kKC * ld) * sizeof(float);
+    return ((size_t)2 * kTM * ld + (size_t)P.n_layers * kTM * P.width + kTM + 2 * (size_t)kStageFloats) * sizeof(float);
 }
 
 void launch_mlp_fp32(const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX, cudaStream_t s) {

@@ -108,13 +108,17 @@ def n_weights(d0: int, n_layers: int, width: int) -> int:
     return width * d0 + width + (n_layers - 1) * (width * width + width) + width + 1
 
 
-def mlp_weights(d0: int, n_layers: int, width: int, seed: int) -> np.ndarray:
-    """W ~ N(0, 1/fan_in) in the packed order (layer, row, column), biases 0, rounded to float32."""
+def mlp_weights(d0: int, n_layers: int, width: int, seed: int, col_scale=None) -> np.ndarray:
+    """W ~ N(0, 1/fan_in) in the packed order (layer, row, column), biases 0, rounded to float32.
+    col_scale (optional, length d0) multiplies the columns of the first layer."""
     rng = np.random.default_rng(seed)
     parts = []
     din = d0
-    for _ in range(n_layers):
-        parts.append(rng.standard_normal((width, din)) / np.sqrt(din))
+    for li in range(n_layers):
+        w = rng.standard_normal((width, din)) / np.sqrt(din)
+        if li == 0 and col_scale is not None:
+            w = w * np.asarray(col_scale, dtype=np.float64)[None, :]
+        parts.append(w)
         parts.append(np.zeros(width))
         din = width
     parts.append(rng.standard_normal(width) / np.sqrt(width))
@@ -122,6 +126,13 @@ def mlp_weights(d0: int, n_layers: int, width: int, seed: int) -> np.ndarray:
     w = np.concatenate([p.ravel() for p in parts]).astype(np.float32).astype(np.float64)
     assert w.size == n_weights(d0, n_layers, width)
     return w
+
+
+def dense_input_scale(n_species: int, n_rbf: int = 16, n_ang: int = 16, angular: float = 1.0 / 40.0):
+    """First-layer column scale for the dense (rho = 0.1/A^3, 6 A cutoff) systems: with ~90 neighbours the 16
+    angular sums reach ~1e2 and unscaled N(0, 1/fan_in) weights saturate the tanh head (no MLP force at all);
+    their columns are scaled by 1/40 so first-layer pre-activations are O(1).  Radial and one-hot columns: 1."""
+    return np.concatenate([np.ones(n_species * n_rbf), np.full(n_ang, angular), np.ones(n_species)])
 
 
 def fcc(cells: int, a: float) -> np.ndarray:
@@ -207,7 +218,8 @@ def _config_large(cells: int, L: float, K: int, precision: str, dt: float, T: fl
     lj = dict(lj_eps=np.array([0.002, 0.004, 0.006]), lj_sigma=np.array([1.6, 2.2, 2.0]), lj_cutoff=6.0)
     d0 = input_dim(3, 16, 16)
     target = Potential(**lj, n_rbf=16, n_ang=16, n_layers=4, width=256, desc_cutoff=6.0, head="tanh",
-                       head_scale=0.05, weights=mlp_weights(d0, 4, 256, seed=1), precision=precision)
+                       head_scale=0.05, weights=mlp_weights(d0, 4, 256, seed=1, col_scale=dense_input_scale(3)),
+                       precision=precision)
     draft = Potential(**lj)
     return Workload("bf16_mlp_%datoms_K%d" % (n, K), sysm, draft, target, Integrator(dt, 0.01, T, K), 2000)
 
