@@ -865,6 +865,18 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
     return check_err(s);
 }
 
+// The target's tensor-core MLP without any device allocation: the kernel's
+// SiLU' scratch is a fixed array inside the library (see lsd_mlp_tc.cu), the
+// caller passes the inputs and outputs.  For callers that own every device
+// allocation themselves or cannot stall on cudaMalloc's implicit device
+// synchronisation in a latency-critical loop.
+int lsd_target_mlp_static_dev(lsd_handle *h, const float *X_dev, int32_t M, float *E_dev, float *dEdX_dev) {
+    if (!h || !X_dev || !E_dev || !dEdX_dev || M < 1) return LSD_EINVAL;
+    if (!h->target.tc_plan) return LSD_EUNSUPPORTED;
+    return mlp_tc_static_launch(h->target.tc_plan, X_dev, M, h->target.dev, E_dev, dEdX_dev, h->n_sm, &h->st->err,
+                                h->stream);
+}
+
 int lsd_query(const lsd_handle *h, int32_t *K, int32_t *n_atoms, int32_t *d_in, int32_t *nb_cap) {
     if (!h) return LSD_EINVAL;
     if (K) *K = h->K;

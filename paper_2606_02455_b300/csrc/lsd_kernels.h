@@ -37,6 +37,9 @@ int mlp_tc_grid(int M, int n_sm);
 void launch_mlp_tc(const void *plan, const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX,
                    __nv_bfloat16 *scratch, int n_sm, int *err, cudaStream_t s);
 cudaError_t mlp_tc_setup();
+size_t mlp_tc_static_scratch_bytes();
+int mlp_tc_static_launch(const void *plan, const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX,
+                         int n_sm, int *err, cudaStream_t s);
 
 // transport (lsd_transport.cu)
 int transport_atoms_per_block(int N);

@@ -330,4 +330,43 @@ cudaError_t mlp_tc_setup() {
                                 (int)mlp_tc_smem_bytes());
 }
 
+// ---------------------------------------------------------------------------
+// The same kernel for callers that cannot allocate device memory: its SiLU'
+// scratch is this file-scope array (4 MiB, held by every device that loads the
+// library until the process exits) instead of a slot the handle allocated.
+// Nothing in it has to start at zero: each CTA writes a row's SiLU' values
+// before reading them.  All calls share the array, so calls that overlap on
+// the GPU (two streams, two handles) race on it.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticScratchBytes = (size_t)4 << 20;
+constexpr size_t kStaticScratchElems = kStaticScratchBytes / sizeof(__nv_bfloat16);
+static __device__ __align__(256) __nv_bfloat16 g_static_mlp_scratch[kStaticScratchElems];
+
+constexpr int kStaticMaxDevices = 64;
+static void *g_static_scratch_addr[kStaticMaxDevices];   // device address of the array, per device
+
+size_t mlp_tc_static_scratch_bytes() { return kStaticScratchBytes; }
+
+int mlp_tc_static_launch(const void *plan, const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX,
+                         int n_sm, int *err, cudaStream_t s) {
+    const size_t per_cta = (size_t)P.n_layers * kTcRows * P.width;
+    if (per_cta > kStaticScratchElems) return LSD_EINVAL;   // one tile's SiLU' does not fit the array
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return LSD_ECUDA;
+    if (!g_static_scratch_addr[dev]) {
+        // set-up, once per device, with that device current: the host-side name
+        // of the array is not a device address; ask the runtime for it
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_mlp_scratch) != cudaSuccess || !p) return LSD_ECUDA;
+        g_static_scratch_addr[dev] = p;
+    }
+    const int cap = (int)(kStaticScratchElems / per_cta);
+    int grid = mlp_tc_grid(M, n_sm);
+    if (grid > cap) grid = cap;
+    const TcPlanImpl *pl = (const TcPlanImpl *)plan;
+    mlp_bf16_tc_kernel<<<grid, kTcThreads, mlp_tc_smem_bytes(), s>>>(
+        pl->maps, X, M, P, E_mlp, dEdX, (__nv_bfloat16 *)g_static_scratch_addr[dev], err);
+    return cudaGetLastError() == cudaSuccess ? LSD_OK : LSD_ECUDA;
+}
+
 }  // namespace lsd

@@ -31,7 +31,8 @@ SYMBOLS = ["lsd_init", "lsd_draft_window", "lsd_verify_window", "lsd_step", "lsd
            "lsd_set_state", "lsd_get_stats", "lsd_set_stream", "lsd_set_draft_weights", "lsd_get_draft_weights",
            "lsd_set_error_correction", "lsd_set_frame_capture", "lsd_frame_count", "lsd_train_draft",
            "lsd_force_match_dev", "lsd_target_forces_dev", "lsd_draft_forces_dev", "lsd_neighbors",
-           "lsd_descriptors", "lsd_get_window", "lsd_profile_window", "lsd_checkpoint", "lsd_restore", "lsd_query", "lsd_destroy",
+           "lsd_descriptors", "lsd_get_window", "lsd_profile_window", "lsd_checkpoint", "lsd_restore", "lsd_query",
+           "lsd_target_mlp_static_dev", "lsd_destroy",
            "lsd_strerror"]
 
 
@@ -99,6 +100,7 @@ def _lib():
             "lsd_checkpoint": [P, P, P],
             "lsd_restore": [P, P, SZ],
             "lsd_query": [P, P, P, P, P],
+            "lsd_target_mlp_static_dev": [P, P, I32, P, P],
             "lsd_profile_window": [P, P, I32],
         }
         for name, args in sig.items():
