@@ -545,6 +545,92 @@ double o_energy_forces(const o_system *sys, const o_potential *pot, const double
     return bad ? NAN : E;
 }
 
+/* Forces on selected atoms only, one atom at a time, for systems too large
+ * for a full pass: F_a = -dE/dq_a collects the LJ pairs of a and, for every
+ * atom i whose descriptor depends on q_a (i = a and the descriptor neighbours
+ * of a), the terms of E_i that involve a.  Same definitions as
+ * o_energy_forces (LJ + MLP potentials; no tether or shear field).
+ * F_out: [n_sel][3].  Returns 0, or -1 when a neighbour list overflows. */
+int o_forces_subset(const o_system *sys, const o_potential *pot, const double *q, int32_t n_sel,
+                    const int32_t *sel, double *F_out) {
+    int N = sys->n_atoms, ns = sys->n_species;
+    for (int t = 0; t < n_sel; ++t)
+        if (sel[t] < 0 || sel[t] >= N) return -2;
+    o_fix *fx = (o_fix *)malloc(sizeof(o_fix) * (size_t)N);
+    o_nb *nb = (o_nb *)malloc(sizeof(o_nb) * O_NB_CAP);
+    o_nb *nbi = (o_nb *)malloc(sizeof(o_nb) * O_NB_CAP);
+    o_fixpoint(sys, q, fx);
+    int d0 = pot->n_layers > 0 ? o_input_dim(ns, pot->n_rbf, pot->n_ang) : 1;
+    double *x = (double *)malloc(sizeof(double) * (size_t)d0);
+    double *gx = (double *)malloc(sizeof(double) * (size_t)d0);
+    double *h = (double *)malloc(sizeof(double) * (size_t)(pot->n_layers > 0 ? pot->n_layers * pot->width : 1));
+    int ret = 0;
+    for (int t = 0; t < n_sel && ret == 0; ++t) {
+        int a = sel[t];
+        double Fa[3] = {0.0, 0.0, 0.0};
+        if (pot->lj_cutoff > 0.0) {
+            int n = o_list(sys, q, fx, a, pot->lj_cutoff, nb, O_NB_CAP);
+            if (n < 0) { ret = -1; break; }
+            int sa = sys->species[a];
+            for (int p = 0; p < n; ++p) {
+                int sj = sys->species[nb[p].j];
+                double eps = sqrt(pot->lj_eps[sa] * pot->lj_eps[sj]);
+                double sig = 0.5 * (pot->lj_sigma[sa] + pot->lj_sigma[sj]);
+                double U, dU;
+                o_lj_pair(eps, sig, pot->lj_cutoff, nb[p].r, &U, &dU);
+                for (int c = 0; c < 3; ++c) Fa[c] += dU * nb[p].d[c] / nb[p].r;
+            }
+        }
+        if (pot->n_layers > 0) {
+            int na = o_list(sys, q, fx, a, pot->desc_cutoff, nb, O_NB_CAP);
+            if (na < 0) { ret = -1; break; }
+            int nr = pot->n_rbf;
+            /* candidates i: a itself and its descriptor neighbours (several images of one atom count once) */
+            for (int cnd = -1; cnd < na; ++cnd) {
+                int i = cnd < 0 ? a : nb[cnd].j;
+                int dup = 0;
+                if (cnd >= 0) {
+                    if (i == a) dup = 1;
+                    for (int e = 0; e < cnd && !dup; ++e) dup = (nb[e].j == i);
+                }
+                if (dup) continue;
+                int n = o_list(sys, q, fx, i, pot->desc_cutoff, nbi, O_NB_CAP);
+                if (n < 0) { ret = -1; break; }
+                o_descriptor(sys, pot, i, nbi, n, x);
+                double y = o_mlp_forward(pot, d0, x, h);
+                double dedy;
+                o_head(pot, y, &dedy);
+                o_mlp_backward(pot, d0, h, dedy, gx);
+                /* -dE_i/dq_a: radial and angular terms of E_i through the displacement vectors */
+                for (int p = 0; p < n; ++p) {
+                    int sj = sys->species[nbi[p].j];
+                    double cr = 0.0;
+                    for (int k = 0; k < nr; ++k) {
+                        double g, dg;
+                        o_rbf(k, nr, pot->desc_cutoff, nbi[p].r, &g, &dg);
+                        cr += gx[sj * nr + k] * dg;
+                    }
+                    double coef = (nbi[p].j == a ? -1.0 : 0.0) + (i == a ? 1.0 : 0.0);
+                    for (int c = 0; c < 3; ++c) Fa[c] += coef * cr * nbi[p].d[c] / nbi[p].r;
+                }
+                for (int p = 0; p < n; ++p)
+                    for (int q2 = p + 1; q2 < n; ++q2)
+                        for (int an = 0; an < pot->n_ang; ++an) {
+                            double gp[3], gq[3];
+                            o_ang_term(an, pot->desc_cutoff, &nbi[p], &nbi[q2], gp, gq);
+                            double wgt = gx[ns * nr + an];
+                            double cp = (nbi[p].j == a ? -1.0 : 0.0) + (i == a ? 1.0 : 0.0);
+                            double cq = (nbi[q2].j == a ? -1.0 : 0.0) + (i == a ? 1.0 : 0.0);
+                            for (int c = 0; c < 3; ++c) Fa[c] += wgt * (cp * gp[c] + cq * gq[c]);
+                        }
+            }
+        }
+        for (int c = 0; c < 3; ++c) F_out[3 * t + c] = Fa[c];
+    }
+    free(x); free(gx); free(h); free(nb); free(nbi); free(fx);
+    return ret;
+}
+
 /* ------------------------------------------------------------------------- */
 /* ABOBA (Eq. 2) and the BOB Gaussian (Eq. 4)                                 */
 /* ------------------------------------------------------------------------- */

@@ -85,6 +85,7 @@ def _L():
                 "o_lsd_run": (ctypes.c_int, [P, P, P, P, I64, I32, I32, P, P, P, P, P, P]),
                 "o_plain_run": (ctypes.c_int, [P, P, P, I64, P, P, P, P, P]),
                 "o_force_match": (D, [P, P, I32, P, P, P]),
+                "o_forces_subset": (ctypes.c_int, [P, P, P, I32, P, P]),
             }
             for name, (res, args) in sigs.items():
                 f = getattr(lib, name)
@@ -363,3 +364,19 @@ def force_match(system, draft, frames_q, frames_F, grad=True):
     g = np.zeros(len(draft.weights)) if grad else None
     loss = _L().o_force_match(ctypes.byref(s), ctypes.byref(pd_), int(nf), _ptr(fq), _ptr(fF), _ptr(g))
     return loss, g
+
+
+def forces_subset(system, pot, q, atoms):
+    """Forces on the selected atoms only (for systems too large for a full oracle pass)."""
+    keep = _Keep()
+    s = _csys(system, keep)
+    p = _cpot(pot, keep)
+    qq = keep.arr(q, np.float64)
+    sel = keep.arr(np.asarray(atoms), np.int32)
+    out = np.zeros((sel.size, 3))
+    r = _L().o_forces_subset(ctypes.byref(s), ctypes.byref(p), _ptr(qq), int(sel.size), _ptr(sel), _ptr(out))
+    if r == -2:
+        raise IndexError("atom index out of range")
+    if r != 0:
+        raise RuntimeError("oracle neighbour list overflow")
+    return out

@@ -64,6 +64,8 @@ struct lsd_handle {
     PotHost draft, target;
     bool learned_small = false;
     DraftPlan dplan{};
+    VerletPlan vplan{};
+    VerletBufs vbufs{};
     int *w_flags = nullptr;
     float *w_dEdX = nullptr;
     // device state
@@ -311,12 +313,18 @@ void enqueue_mlp(lsd_handle *h, const PotHost &pot, int M, cudaStream_t s) {
 
 // Batched force evaluation of `pot` on Kc configurations whose fixed-point
 // coordinates are in fix ([Kc][N]); forces to F ([Kc][N][3]).
+// With use_list the candidates are the window's Verlet lists (the window and
+// plain-step paths); otherwise all atoms (explicit configurations).
 void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, float *F, float *E_out,
-                  cudaStream_t s) {
+                  cudaStream_t s, bool use_list = false) {
     const int M = Kc * h->N;
     const PotDev &P = pot.dev;
-    launch_neigh_build(fix, M, h->geo, pot.rmax2f, pot.near2f, h->cap_near, h->cap_far, h->near_keys, h->far_keys,
-                       h->n_near, h->n_far, h->st, s);
+    if (use_list)
+        launch_neigh_list(fix, h->vbufs.vlist, h->vbufs.vcount, h->vplan.cap, M, h->geo, pot.rmax2f, pot.near2f,
+                          h->cap_near, h->cap_far, h->near_keys, h->far_keys, h->n_near, h->n_far, h->st, s);
+    else
+        launch_neigh_build(fix, M, h->geo, pot.rmax2f, pot.near2f, h->cap_near, h->cap_far, h->near_keys,
+                           h->far_keys, h->n_near, h->n_far, h->st, s);
     if (P.has_mlp) {
         launch_desc(fix, h->near_keys, h->n_near, h->cap_near, M, h->geo, P, h->X, s);
         enqueue_mlp(h, pot, M, s);
@@ -327,21 +335,25 @@ void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, f
                         h->E_mlp, F, E_out, h->st, s);
 }
 
+// The window's Verlet lists around the base state, then the draft.
 void enqueue_draft(lsd_handle *h, cudaStream_t s) {
-    launch_draft(h->dplan, h->learned_small, h->K, h->geo, h->draft.dev, h->coef, h->species, h->q, h->p, h->ec_dF,
-                 h->ec_on, h->st, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Fraw, h->w_fix, h->w_flags, h->w_dEdX, s);
+    launch_verlet_build(h->vplan, h->q, h->species, h->geo, h->vbufs, h->st, s);
+    launch_draft(h->dplan, h->learned_small, h->K, h->geo, h->draft.dev, h->coef, h->vplan, h->vbufs, h->species,
+                 h->q, h->p, h->ec_dF, h->ec_on, h->st, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Fraw, h->w_fix,
+                 h->w_flags, h->w_dEdX, s);
 }
 
 void enqueue_verify(lsd_handle *h, cudaStream_t s) {
-    enqueue_eval(h, h->target, h->w_fix, h->K, h->w_Ft, nullptr, s);
+    enqueue_eval(h, h->target, h->w_fix, h->K, h->w_Ft, nullptr, s, true);
     if (h->train.capture_on) enqueue_frame_capture(h->train, h->w_qmid, h->w_Ft, h->K, h->N, h->st, s);
     launch_transport(h->K, h->geo, h->coef, h->species, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Ft, h->w_Fraw, h->ec_dF,
                      h->ec_on, h->q, h->p, h->st, h->partials, h->logu, s);
 }
 
 void enqueue_plain(lsd_handle *h, cudaStream_t s) {
+    launch_verlet_build(h->vplan, h->q, h->species, h->geo, h->vbufs, h->st, s);
     launch_plain_half(h->geo, h->coef, h->species, h->q, h->p, h->st, h->w_qmid, h->w_fix, s);
-    enqueue_eval(h, h->target, h->w_fix, 1, h->w_Ft, nullptr, s);
+    enqueue_eval(h, h->target, h->w_fix, 1, h->w_Ft, nullptr, s, true);
     launch_plain_finish(h->geo, h->coef, h->species, h->w_qmid, h->w_Ft, h->q, h->p, h->st, s);
 }
 
@@ -513,14 +525,26 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     h->cap_far = std::min(nb_capacity(rho, rfar, 32), (27 * h->N + 31) / 32 * 32);
     if (desc_smem_bytes(8, h->cap_near) + 8 * 256 * sizeof(float) > (size_t)kMaxDynSmem) return fail(LSD_EUNSUPPORTED);
     if (verify_kernels_setup(kMaxDynSmem) != cudaSuccess || mlp_kernels_setup(kMaxDynSmem) != cudaSuccess ||
-        mlp_tc_setup() != cudaSuccess ||
-        draft_kernels_setup(kMaxDynSmem) != cudaSuccess)
+        mlp_tc_setup() != cudaSuccess || draft_kernels_setup(kMaxDynSmem) != cudaSuccess ||
+        verlet_setup(kMaxDynSmem) != cudaSuccess)
         return fail(LSD_ECUDA);
     {
-        const double rc_draft = std::max(h->draft.dev.has_lj ? h->draft.p.lj_cutoff : 0.0,
-                                          h->draft.dev.has_mlp ? h->draft.p.desc_cutoff : 0.0);
+        // Verlet lists: skin from the lightest species' thermal speed over a window (1 to 2.5 A)
+        double mmin = h->mass_h[0];
+        for (double m : h->mass_h) mmin = std::min(mmin, m);
+        const double v1 = std::sqrt(kB * T * kap / mmin);
+        const double skin = std::min(2.5, std::max(1.0, 5.0 * v1 * K * dt));
+        const double rlist = rfar + skin;
+        VerletPlan &vp = h->vplan;
+        for (int a = 0; a < 3; ++a) vp.nc[a] = std::max(1, (int)std::floor(h->box[a] / rlist));
+        vp.rlist2f = (float)(rlist * rlist);
+        vp.move2f = (float)((0.45 * skin) * (0.45 * skin));
+        vp.cap = std::min(nb_capacity(rho, rlist, 32), (h->N + 31) / 32 * 32);
+        vp.cap_pow2 = 32;
+        while (vp.cap_pow2 < vp.cap) vp.cap_pow2 *= 2;
+        if ((size_t)8 * vp.cap_pow2 * sizeof(int) > (size_t)kMaxDynSmem) return fail(LSD_EUNSUPPORTED);
         const int maxc = draft_max_cluster(64 * 1024);
-        h->dplan = draft_plan(h->N, rho, rc_draft, h->draft.dev, h->learned_small, maxc, kMaxDynSmem);
+        h->dplan = draft_plan(h->N, h->draft.dev, h->learned_small, maxc, kMaxDynSmem);
         if (!h->dplan.ok) return fail(LSD_EUNSUPPORTED);
     }
     const size_t N = h->N, D = 3 * N, KN = (size_t)K * N, KD = (size_t)K * D;
@@ -536,7 +560,12 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         (rc = dalloc(h, &h->pair_g, KN * h->cap_near)) || (rc = dalloc(h, &h->Fpart, KN)) ||
         (rc = dalloc(h, &h->partials, (size_t)K * ((h->N + 1023) / 1024 + 600))) ||
         (rc = dalloc(h, &h->logu, (size_t)K)) || (rc = dalloc(h, &h->w_flags, (size_t)K * 16)) ||
-        (rc = dalloc(h, &h->w_dEdX, N * std::max(h->draft.dev.d0p, 32))))
+        (rc = dalloc(h, &h->w_dEdX, N * std::max(h->draft.dev.d0p, 32))) ||
+        (rc = dalloc(h, &h->vbufs.fix_base, N)) || (rc = dalloc(h, &h->vbufs.cell_of_atom, N)) ||
+        (rc = dalloc(h, &h->vbufs.cell_count, (size_t)h->vplan.nc[0] * h->vplan.nc[1] * h->vplan.nc[2])) ||
+        (rc = dalloc(h, &h->vbufs.cell_start, (size_t)h->vplan.nc[0] * h->vplan.nc[1] * h->vplan.nc[2] + 1)) ||
+        (rc = dalloc(h, &h->vbufs.cell_atoms, N)) || (rc = dalloc(h, &h->vbufs.cell_scratch, 1)) ||
+        (rc = dalloc(h, &h->vbufs.vlist, N * h->vplan.cap)) || (rc = dalloc(h, &h->vbufs.vcount, N)))
         return fail(rc);
     if ((rc = pot_upload(h, h->draft)) != LSD_OK) return fail(rc);
     if ((rc = pot_upload(h, h->target)) != LSD_OK) return fail(rc);
@@ -835,8 +864,9 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
     CK(cudaEventRecord(ev[0], st));
     enqueue_draft(h, st);
     CK(cudaEventRecord(ev[1], st));
-    launch_neigh_build(h->w_fix, M, h->geo, h->target.rmax2f, h->target.near2f, h->cap_near, h->cap_far, h->near_keys,
-                       h->far_keys, h->n_near, h->n_far, h->st, st);
+    launch_neigh_list(h->w_fix, h->vbufs.vlist, h->vbufs.vcount, h->vplan.cap, M, h->geo, h->target.rmax2f,
+                      h->target.near2f, h->cap_near, h->cap_far, h->near_keys, h->far_keys, h->n_near, h->n_far, h->st,
+                      st);
     CK(cudaEventRecord(ev[2], st));
     if (P.has_mlp) launch_desc(h->w_fix, h->near_keys, h->n_near, h->cap_near, M, h->geo, P, h->X, st);
     CK(cudaEventRecord(ev[3], st));

@@ -73,6 +73,7 @@ struct DevState {
     long long target_step;       // windows stop committing at this step
     int n_commit_last;
     int first_reject_last;       // 1-based, -1 if none
+    int k_eff;                   // window steps drafted (the draft stops early if an atom left the list's skin)
     int err;                     // bit flags: 1 neighbour overflow, 2 non-finite
     unsigned int blocks_done;    // last-block counter of the commit kernel
     long long windows, committed, rejected, verified;

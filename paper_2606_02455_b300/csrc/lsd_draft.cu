@@ -11,12 +11,13 @@
 // and a hardware cluster barrier (release/acquire at cluster scope, no spin
 // loop) makes every CTA see all positions before forces are evaluated.
 //
-// Candidates come from a Verlet list per owned atom, built from the
-// minimum-image distance with a 1 A skin at the first step and rebuilt (in
-// every CTA, decided from flags all CTAs read after the barrier) whenever an
-// atom has moved more than 0.45 skin since the build.  Each list entry is
-// then tested with the exact membership rule, so the interacting set is the
-// rule's set, not an approximation.
+// Candidates come from the window's Verlet lists (lsd_verlet.cu: cutoff +
+// skin around the base positions).  At every step each CTA checks its atoms'
+// displacement from the base; if any atom moved more than 0.45 skin the whole
+// cluster stops drafting at that step (k_eff < K, decided identically in every
+// CTA from flags read after the barrier), because the lists are no longer
+// guaranteed complete.  Each list entry is tested with the exact membership
+// rule, so the interacting set is the rule's set, not an approximation.
 //
 // FP64 only for the state updates, with explicit round-to-nearest intrinsics
 // so the half-step positions are reproducible bit for bit.
@@ -28,28 +29,26 @@ namespace lsd {
 constexpr int kDraftThreads = 512;
 constexpr int kDraftWarps = kDraftThreads / 32;
 constexpr int kLearnCap = 96;      // staged descriptor neighbours per warp (learned draft)
-constexpr float kSkin = 1.0f;      // Verlet skin, Angstrom
 
 __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
-struct DraftShared {
-    uint4 *fix;        // [N] fixed point of all atoms at the current step
-    uint4 *ubuild;     // [A] fixed point of owned atoms at the last list build
-    int *list;         // [A][cap] candidate atom indices
-    int *nlist;        // [A]
-    float4 *F;         // [A] forces of owned atoms
-    float *lj;         // 4 tables of S*S: sig2, eps24
-    float *stage;      // learned: per warp 3*kLearnCap + d0p
+
+// Positions of window step j: staged in shared memory when they fit, else read
+// through L2 (ld.global.cg: other CTAs of the cluster wrote them this launch).
+struct FixView {
+    const uint4 *smem;
+    const uint4 *glob;
+    __device__ __forceinline__ uint4 operator[](int k) const { return smem ? smem[k] : __ldcg(glob + k); }
 };
 
-// Learned draft, first phase: radial descriptors of atom i from its list,
-// the MLP (BF16 operands, FP32 accumulation), dE/dx written to g_out[d0p].
-__device__ void learned_atom_grad(const PotDev &P, const Geo &g, const uint4 *sfix, int i, const int *cand, int nc,
+// Learned draft, first phase: radial descriptors of atom i from its candidate
+// list, the MLP (BF16 operands, FP32 accumulation), dE/dx written to g_out[d0p].
+__device__ void learned_atom_grad(const PotDev &P, const Geo &g, const FixView &fx, int i, const int *cand, int nc,
                                   float *stage, float *xbuf, float *g_out) {
     const int lane = threadIdx.x & 31;
-    const uint4 fi = sfix[i];
+    const uint4 fi = fx[i];
     float *sr = stage, *sfc = stage + kLearnCap;
     int *ssp = (int *)(stage + 2 * kLearnCap);
     int cnt = 0;
@@ -58,20 +57,19 @@ __device__ void learned_atom_grad(const PotDev &P, const Geo &g, const uint4 *sf
         unsigned m = 0u;
         AxisOpts ox, oy, oz;
         ox = oy = oz = AxisOpts{0.f, 0.f, 0, 0, 0};
-        int k = 0;
+        int sk = 0;
         if (t < nc) {
-            k = cand[t];
-            const uint4 fk = sfix[k];
+            const int k = __ldg(cand + t);
+            const uint4 fk = fx[k];
+            sk = (int)fk.w;
             ox = axis_opts(fi.x, fk.x, g.scale_f[0], g.Lf[0], P.desc_rc2f);
             oy = axis_opts(fi.y, fk.y, g.scale_f[1], g.Lf[1], P.desc_rc2f);
             oz = axis_opts(fi.z, fk.z, g.scale_f[2], g.Lf[2], P.desc_rc2f);
             for (int bz = 0; bz < oz.n; ++bz)
                 for (int by = 0; by < oy.n; ++by)
-                    for (int bx = 0; bx < ox.n; ++bx) {
-                        if (k == i && opt_s(ox, bx) == 0 && opt_s(oy, by) == 0 && opt_s(oz, bz) == 0) continue;
+                    for (int bx = 0; bx < ox.n; ++bx)
                         if (dist2_rule(opt_d(ox, bx), opt_d(oy, by), opt_d(oz, bz)) < P.desc_rc2f)
                             m |= 1u << (bx + 2 * by + 4 * bz);
-                    }
         }
         const int nm = __popc(m);
         int sc = nm;
@@ -91,7 +89,7 @@ __device__ void learned_atom_grad(const PotDev &P, const Geo &g, const uint4 *sf
                 cutoff_fn(r, P.desc_rc, fc, dfc);
                 sr[w] = r;
                 sfc[w] = fc;
-                ssp[w] = (int)sfix[k].w;
+                ssp[w] = sk;
             }
             ++w;
         }
@@ -143,38 +141,36 @@ __device__ void learned_atom_grad(const PotDev &P, const Geo &g, const uint4 *sf
 
 template <bool LEARNED>
 __global__ void __launch_bounds__(kDraftThreads)
-    draft_window_cluster_kernel(int K, Geo g, PotDev P, Coef cf, int cap, float rlist2f,
-                                const int *__restrict__ species, const double *__restrict__ q_base,
-                                const double *__restrict__ p_base, const float *__restrict__ ec_dF, int ec_on,
-                                const DevState *__restrict__ st, double *__restrict__ w_qmid,
-                                double *__restrict__ w_pdraft, float *__restrict__ w_Fd, float *__restrict__ w_Fraw,
-                                uint4 *__restrict__ w_fix, int *__restrict__ w_flags, float *__restrict__ w_dEdX) {
+    draft_window_cluster_kernel(int K, Geo g, PotDev P, Coef cf, const int *__restrict__ vlist,
+                                const int *__restrict__ vcount, int vcap, const uint4 *__restrict__ fix_base,
+                                float move2f, int stage_fix, const int *__restrict__ species,
+                                const double *__restrict__ q_base, const double *__restrict__ p_base,
+                                const float *__restrict__ ec_dF, int ec_on, DevState *__restrict__ st,
+                                double *__restrict__ w_qmid, double *__restrict__ w_pdraft, float *__restrict__ w_Fd,
+                                float *__restrict__ w_Fraw, uint4 *__restrict__ w_fix, int *__restrict__ w_flags,
+                                float *__restrict__ w_dEdX) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N;
     const int C = gridDim.x, c = blockIdx.x;
     const int A = (N + C - 1) / C;           // owned atoms per CTA
     const int a0 = c * A, a1 = min(N, a0 + A);
     const int nown = a1 > a0 ? a1 - a0 : 0;
-    DraftShared S;
-    S.fix = (uint4 *)smraw;
-    S.ubuild = S.fix + N;
-    S.F = (float4 *)(S.ubuild + A);
-    S.list = (int *)(S.F + A);
-    S.nlist = S.list + (size_t)A * cap;
-    S.lj = (float *)(S.nlist + A);
-    S.stage = S.lj + 2 * kMaxSpecies * kMaxSpecies;
+    float4 *sF = (float4 *)smraw;                               // [A]
+    float *slj = (float *)(sF + A);                             // sig2, eps24 tables
+    float *sstage = slj + 2 * kMaxSpecies * kMaxSpecies;        // learned: per warp 3*cap + d0p
+    uint4 *sfix = (uint4 *)(sstage + (LEARNED ? (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) : 0));
     if (st->step >= st->target_step) return;   // uniform over the cluster
     const long long n0 = st->step;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t D = (size_t)3 * N;
     const float rc2_all = LEARNED ? fmaxf(P.lj_rc2f, P.desc_rc2f) : P.lj_rc2f;
     for (int t = tid; t < g.S * g.S; t += blockDim.x) {
-        S.lj[t] = P.lj_sig2[t];
-        S.lj[kMaxSpecies * kMaxSpecies + t] = P.lj_eps24[t];
+        slj[t] = P.lj_sig2[t];
+        slj[kMaxSpecies * kMaxSpecies + t] = P.lj_eps24[t];
     }
-    const float skin_lim2 = (0.45f * kSkin) * (0.45f * kSkin);
+    int keff = K;
     for (int j = 0; j < K; ++j) {
-        // A: half-step positions of owned atoms, fixed point, displacement since the list build
+        // A: half-step positions of owned atoms, fixed point, displacement from the list's base
         int moved = 0;
         for (int i = a0 + tid; i < a1; i += blockDim.x) {
             const int sp = species[i];
@@ -196,87 +192,61 @@ __global__ void __launch_bounds__(kDraftThreads)
                 const uint32_t u = fixpoint(qm, g.scale[x]);
                 if (x == 0) u0 = u; else if (x == 1) u1 = u; else u2 = u;
             }
-            const uint4 f = make_uint4(u0, u1, u2, (unsigned)sp);
-            w_fix[(size_t)j * N + i] = f;
-            if (j > 0) {
-                const uint4 b = S.ubuild[i - a0];
-                float dmin;
-                int kk;
-                axis_min(b.x, u0, g.scale_f[0], dmin, kk);
-                float d2 = dmin * dmin;
-                axis_min(b.y, u1, g.scale_f[1], dmin, kk);
-                d2 += dmin * dmin;
-                axis_min(b.z, u2, g.scale_f[2], dmin, kk);
-                d2 += dmin * dmin;
-                moved |= d2 > skin_lim2;
-            }
+            w_fix[(size_t)j * N + i] = make_uint4(u0, u1, u2, (unsigned)sp);
+            const uint4 b = fix_base[i];
+            float dmin, d2;
+            int kk;
+            axis_min(b.x, u0, g.scale_f[0], dmin, kk);
+            d2 = dmin * dmin;
+            axis_min(b.y, u1, g.scale_f[1], dmin, kk);
+            d2 += dmin * dmin;
+            axis_min(b.z, u2, g.scale_f[2], dmin, kk);
+            d2 += dmin * dmin;
+            moved |= d2 > move2f;
         }
         moved = __syncthreads_or(moved);
         if (tid == 0) w_flags[j * C + c] = moved;
         cluster_barrier();
-        // B: all positions of this step, and the list rebuild decision (same in every CTA)
-        for (int k = tid; k < N; k += blockDim.x) S.fix[k] = w_fix[(size_t)j * N + k];
-        int rebuild = (j == 0);
-        for (int k = 0; k < C; ++k) rebuild |= w_flags[j * C + k];
-        __syncthreads();
-        if (rebuild) {
-            // candidates of owned atom i: every k whose minimum image is within rc + skin
-            for (int ii = warp; ii < nown; ii += kDraftWarps) {
-                const int i = a0 + ii;
-                const uint4 fi = S.fix[i];
-                int cnt = 0;
-                int *lst = S.list + (size_t)ii * cap;
-                for (int base = 0; base < N; base += 32) {
-                    const int k = base + lane;
-                    bool in = false;
-                    if (k < N) {
-                        const uint4 fk = S.fix[k];
-                        float dx, dy, dz;
-                        int kk;
-                        axis_min(fi.x, fk.x, g.scale_f[0], dx, kk);
-                        axis_min(fi.y, fk.y, g.scale_f[1], dy, kk);
-                        axis_min(fi.z, fk.z, g.scale_f[2], dz, kk);
-                        in = dist2_rule(dx, dy, dz) < rlist2f;
-                    }
-                    const unsigned bal = __ballot_sync(0xffffffffu, in);
-                    const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-                    if (in && pos < cap) lst[pos] = k;
-                    cnt += __popc(bal);
-                }
-                if (lane == 0) {
-                    S.nlist[ii] = cnt < cap ? cnt : cap;
-                    S.ubuild[ii] = fi;
-                }
-            }
+        // B: stop drafting when any atom left the skin (same decision in every CTA)
+        int stop = 0;
+        for (int k = 0; k < C; ++k) stop |= __ldcg(w_flags + j * C + k);
+        if (stop) {
+            keff = j;
+            break;
+        }
+        FixView fx{stage_fix ? sfix : nullptr, w_fix + (size_t)j * N};
+        if (stage_fix) {
+            for (int k = tid; k < N; k += blockDim.x) sfix[k] = __ldcg(w_fix + (size_t)j * N + k);
             __syncthreads();
         }
         if (LEARNED) {
-            float *stage = S.stage + (size_t)warp * (3 * kLearnCap + P.d0p);
-            for (int ii = warp; ii < nown; ii += kDraftWarps)
-                learned_atom_grad(P, g, S.fix, a0 + ii, S.list + (size_t)ii * cap, S.nlist[ii], stage,
-                                  stage + 3 * kLearnCap, w_dEdX + (size_t)(a0 + ii) * P.d0p);
+            float *stage = sstage + (size_t)warp * (3 * kLearnCap + P.d0p);
+            for (int ii = warp; ii < nown; ii += kDraftWarps) {
+                const int i = a0 + ii;
+                learned_atom_grad(P, g, fx, i, vlist + (size_t)i * vcap, vcount[i], stage, stage + 3 * kLearnCap,
+                                  w_dEdX + (size_t)i * P.d0p);
+            }
             cluster_barrier();   // dE/dx of every atom visible to every CTA
         }
         // C: forces on owned atoms, one warp per atom, lanes over its candidates
         for (int ii = warp; ii < nown; ii += kDraftWarps) {
             const int i = a0 + ii;
-            const uint4 fi = S.fix[i];
+            const uint4 fi = fx[i];
             const int si = (int)fi.w;
-            const int *lst = S.list + (size_t)ii * cap;
-            const int nl = S.nlist[ii];
-            float fx = 0.f, fy = 0.f, fz = 0.f;
+            const int *lst = vlist + (size_t)i * vcap;
+            const int nl = vcount[i];
+            float fxx = 0.f, fyy = 0.f, fzz = 0.f;
             for (int t = lane; t < nl; t += 32) {
-                const int k = lst[t];
-                const uint4 fk = S.fix[k];
+                const int k = __ldg(lst + t);
+                const uint4 fk = fx[k];
                 const AxisOpts ox = axis_opts(fi.x, fk.x, g.scale_f[0], g.Lf[0], rc2_all);
                 const AxisOpts oy = axis_opts(fi.y, fk.y, g.scale_f[1], g.Lf[1], rc2_all);
                 const AxisOpts oz = axis_opts(fi.z, fk.z, g.scale_f[2], g.Lf[2], rc2_all);
                 const int pr = si * g.S + (int)fk.w;
-                const float sig2 = S.lj[pr], eps24 = S.lj[kMaxSpecies * kMaxSpecies + pr];
+                const float sig2 = slj[pr], eps24 = slj[kMaxSpecies * kMaxSpecies + pr];
                 for (int bz = 0; bz < oz.n; ++bz)
                     for (int by = 0; by < oy.n; ++by)
                         for (int bx = 0; bx < ox.n; ++bx) {
-                            if (k == i && opt_s(ox, bx) == 0 && opt_s(oy, by) == 0 && opt_s(oz, bz) == 0) continue;
                             const float dx = opt_d(ox, bx), dy = opt_d(oy, by), dz = opt_d(oz, bz);
                             const float d2 = dist2_rule(dx, dy, dz);
                             if (P.has_lj && d2 < P.lj_rc2f) {
@@ -284,9 +254,9 @@ __global__ void __launch_bounds__(kDraftThreads)
                                 const float s2 = sig2 * inv;
                                 const float s6 = s2 * s2 * s2, s12 = s6 * s6;
                                 const float fr = -eps24 * (2.f * s12 - s6) * inv;
-                                fx += fr * dx;
-                                fy += fr * dy;
-                                fz += fr * dz;
+                                fxx += fr * dx;
+                                fyy += fr * dy;
+                                fzz += fr * dz;
                             }
                             if (LEARNED && d2 < P.desc_rc2f) {
                                 // radial adjoint in gather form: (c_ik + c_ki) d/r
@@ -299,25 +269,25 @@ __global__ void __launch_bounds__(kDraftThreads)
                                 for (int b = 0; b < P.n_rbf; ++b) {
                                     const float tt = r - (float)b * P.rbf_w;
                                     const float dg = expf(-tt * tt * P.rbf_inv2w2) * (-tt * P.rbf_invw2 * fc + dfc);
-                                    cc += (gi[b] + gk[b]) * dg;
+                                    cc += (__ldcg(gi + b) + __ldcg(gk + b)) * dg;
                                 }
-                                fx += cc * dx / r;
-                                fy += cc * dy / r;
-                                fz += cc * dz / r;
+                                fxx += cc * dx / r;
+                                fyy += cc * dy / r;
+                                fzz += cc * dz / r;
                             }
                         }
             }
-            fx = warp_sum(fx);
-            fy = warp_sum(fy);
-            fz = warp_sum(fz);
-            if (lane == 0) S.F[ii] = make_float4(fx, fy, fz, 0.f);
+            fxx = warp_sum(fxx);
+            fyy = warp_sum(fyy);
+            fzz = warp_sum(fzz);
+            if (lane == 0) sF[ii] = make_float4(fxx, fyy, fzz, 0.f);
         }
         __syncthreads();
         // D: BOB + A for owned atoms
         const unsigned long long n = (unsigned long long)(n0 + j + 1);
         for (int i = a0 + tid; i < a1; i += blockDim.x) {
             const int sp = species[i];
-            const float4 F = S.F[i - a0];
+            const float4 F = sF[i - a0];
             const float3 xi = normals3(cf.seed, n, (uint32_t)i, 0u);
             const double sg = cf.sig[sp];
 #pragma unroll
@@ -333,43 +303,37 @@ __global__ void __launch_bounds__(kDraftThreads)
                 if (ec_on) w_Fraw[o] = fr;
             }
         }
-        // the next step reads only owned atoms' global state (written by this CTA) and
+        // the next step reads owned atoms' global state (written by this CTA) and
         // all atoms' positions after the next cluster barrier
         __syncthreads();
     }
+    if (c == 0 && tid == 0) st->k_eff = keff;
 }
 
-static size_t draft_smem_bytes(int N, int C, int cap, const PotDev &P, bool learned) {
+static size_t draft_smem_bytes(int N, int C, const PotDev &P, bool learned, bool stage_fix) {
     const int A = (N + C - 1) / C;
-    size_t b = (size_t)N * sizeof(uint4) + (size_t)A * sizeof(uint4) + (size_t)A * sizeof(float4) +
-               (size_t)A * cap * sizeof(int) + (size_t)A * sizeof(int) + 2 * kMaxSpecies * kMaxSpecies * sizeof(float);
+    size_t b = (size_t)A * sizeof(float4) + 2 * kMaxSpecies * kMaxSpecies * sizeof(float);
     if (learned) b += (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) * sizeof(float);
+    if (stage_fix) b += (size_t)N * sizeof(uint4);
     return b;
 }
 
-DraftPlan draft_plan(int N, double density, double rc_max, const PotDev &P, bool learned, int max_cluster,
-                     size_t max_smem) {
+DraftPlan draft_plan(int N, const PotDev &P, bool learned, int max_cluster, size_t max_smem) {
     DraftPlan pl{};
-    const double rl = rc_max + kSkin;
-    const double expect = density * 4.0 / 3.0 * 3.14159265358979 * rl * rl * rl;
-    int cap = (int)(2.0 * expect) + 32;
-    cap = (cap + 31) / 32 * 32;
-    if (cap > N) cap = (N + 31) / 32 * 32;
-    pl.cap = cap;
-    pl.rlist2f = (float)(rl * rl);
     int C = 1;
     while (C < max_cluster && (N + C - 1) / C > 16) C *= 2;
-    while (C > 1 && draft_smem_bytes(N, C, cap, P, learned) > max_smem) C /= 2;
     pl.cluster = C;
-    pl.smem = draft_smem_bytes(N, C, cap, P, learned);
+    pl.stage_fix = (size_t)N * sizeof(uint4) <= 64 * 1024;
+    pl.smem = draft_smem_bytes(N, C, P, learned, pl.stage_fix);
     pl.ok = pl.smem <= max_smem;
     return pl;
 }
 
 cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf,
-                         const int *species, const double *q, const double *p, const float *ec_dF, int ec_on,
-                         const DevState *st, double *w_qmid, double *w_pdraft, float *w_Fd, float *w_Fraw,
-                         uint4 *w_fix, int *w_flags, float *w_dEdX, cudaStream_t s) {
+                         const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
+                         const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
+                         double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, int *w_flags, float *w_dEdX,
+                         cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(pl.cluster, 1, 1);
     cfg.blockDim = dim3(kDraftThreads, 1, 1);
@@ -382,11 +346,14 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    const int stage = pl.stage_fix ? 1 : 0;
     if (learned)
-        return cudaLaunchKernelEx(&cfg, draft_window_cluster_kernel<true>, K, g, P, cf, pl.cap, pl.rlist2f, species, q,
-                                  p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd, w_Fraw, w_fix, w_flags, w_dEdX);
-    return cudaLaunchKernelEx(&cfg, draft_window_cluster_kernel<false>, K, g, P, cf, pl.cap, pl.rlist2f, species, q, p,
-                              ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd, w_Fraw, w_fix, w_flags, w_dEdX);
+        return cudaLaunchKernelEx(&cfg, draft_window_cluster_kernel<true>, K, g, P, cf, (const int *)vb.vlist,
+                                  (const int *)vb.vcount, vp.cap, (const uint4 *)vb.fix_base, vp.move2f, stage, species,
+                                  q, p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd, w_Fraw, w_fix, w_flags, w_dEdX);
+    return cudaLaunchKernelEx(&cfg, draft_window_cluster_kernel<false>, K, g, P, cf, (const int *)vb.vlist,
+                              (const int *)vb.vcount, vp.cap, (const uint4 *)vb.fix_base, vp.move2f, stage, species, q,
+                              p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd, w_Fraw, w_fix, w_flags, w_dEdX);
 }
 
 cudaError_t draft_kernels_setup(int max_smem) {
@@ -427,10 +394,11 @@ int draft_max_cluster(size_t smem) {
 // evaluation, BOB + A after it.  Multi-CTA; the last CTA advances the step.
 // ---------------------------------------------------------------------------
 __global__ void plain_half_kernel(Geo g, Coef cf, const int *__restrict__ species, const double *__restrict__ q,
-                                  const double *__restrict__ p, const DevState *__restrict__ st,
+                                  const double *__restrict__ p, DevState *__restrict__ st,
                                   double *__restrict__ qmid, uint4 *__restrict__ fix) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (st->step >= st->target_step || i >= g.N) return;
+    if (i == 0) st->k_eff = 1;   // one step, always inside the lists' skin
     const int sp = species[i];
     const double hm = cf.hm[sp];
     uint32_t u0, u1, u2;
@@ -476,7 +444,7 @@ __global__ void plain_finish_kernel(Geo g, Coef cf, const int *__restrict__ spec
 }
 
 void launch_plain_half(const Geo &g, const Coef &cf, const int *species, const double *q, const double *p,
-                       const DevState *st, double *qmid, uint4 *fix, cudaStream_t s) {
+                       DevState *st, double *qmid, uint4 *fix, cudaStream_t s) {
     plain_half_kernel<<<(g.N + 255) / 256, 256, 0, s>>>(g, cf, species, q, p, st, qmid, fix);
 }
 

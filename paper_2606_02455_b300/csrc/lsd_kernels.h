@@ -22,6 +22,30 @@ void launch_force_gather(const int *near_keys, const int *n_near, int cap, int M
 size_t desc_smem_bytes(int warps, int cap);
 cudaError_t verify_kernels_setup(int max_smem);
 
+// per-window Verlet candidate lists (lsd_verlet.cu)
+struct VerletPlan {
+    int nc[3];          // cells per axis (a grid narrower than 3 cells scans all atoms)
+    float rlist2f;      // (max cutoff + skin)^2
+    float move2f;       // (0.45 skin)^2: largest allowed displacement^2 from the list's base
+    int cap, cap_pow2;  // list capacity per atom and its power-of-two sort width
+};
+struct VerletBufs {
+    uint4 *fix_base = nullptr;   // [N] fixed point of the base positions
+    int *cell_of_atom = nullptr;
+    int *cell_count = nullptr;   // [ncells] counts, then fill cursors
+    int *cell_start = nullptr;   // [ncells + 1]
+    int *cell_atoms = nullptr;   // [N]
+    int *cell_scratch = nullptr; // [1] counter of the single-cell case
+    int *vlist = nullptr;        // [N][cap] sorted candidate atom indices
+    int *vcount = nullptr;       // [N]
+};
+void launch_verlet_build(const VerletPlan &vp, const double *q, const int *species, const Geo &g, VerletBufs &b,
+                         DevState *st, cudaStream_t s);
+cudaError_t verlet_setup(int max_smem);
+void launch_neigh_list(const uint4 *fix, const int *vlist, const int *vcount, int vcap, int M, const Geo &g,
+                       float rmax2f, float near2f, int cap_near, int cap_far, int *near_keys, int *far_keys,
+                       int *n_near, int *n_far, DevState *st, cudaStream_t s);
+
 // MLP (lsd_mlp.cu)
 void launch_mlp_fp32(const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX, cudaStream_t s);
 size_t mlp_fp32_smem_bytes(const PotDev &P);
@@ -56,21 +80,20 @@ void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, c
 // draft and plain integrator (lsd_draft.cu)
 struct DraftPlan {
     int cluster;      // CTAs in the draft cluster (one per SM)
-    int cap;          // Verlet candidates per atom
-    float rlist2f;    // (max cutoff + skin)^2
+    bool stage_fix;   // positions of a step staged in shared memory
     size_t smem;      // dynamic shared memory per CTA
     bool ok;
 };
-DraftPlan draft_plan(int N, double density, double rc_max, const PotDev &P, bool learned, int max_cluster,
-                     size_t max_smem);
+DraftPlan draft_plan(int N, const PotDev &P, bool learned, int max_cluster, size_t max_smem);
 int draft_max_cluster(size_t smem);
 cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf,
-                         const int *species, const double *q, const double *p, const float *ec_dF, int ec_on,
-                         const DevState *st, double *w_qmid, double *w_pdraft, float *w_Fd, float *w_Fraw,
-                         uint4 *w_fix, int *w_flags, float *w_dEdX, cudaStream_t s);
+                         const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
+                         const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
+                         double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, int *w_flags, float *w_dEdX,
+                         cudaStream_t s);
 cudaError_t draft_kernels_setup(int max_smem);
 void launch_plain_half(const Geo &g, const Coef &cf, const int *species, const double *q, const double *p,
-                       const DevState *st, double *qmid, uint4 *fix, cudaStream_t s);
+                       DevState *st, double *qmid, uint4 *fix, cudaStream_t s);
 void launch_plain_finish(const Geo &g, const Coef &cf, const int *species, const double *qmid, const float *F,
                          double *q, double *p, DevState *st, cudaStream_t s);
 

@@ -309,11 +309,13 @@ __global__ void adam_kernel(float *__restrict__ w, float *__restrict__ m, float 
 }
 
 __global__ void frame_capture_kernel(const double *__restrict__ w_qmid, const float *__restrict__ w_Ft, int K, int N,
-                                     long long cap, long long start_windows, const DevState *__restrict__ st,
+                                     long long cap, long long start_verified, const DevState *__restrict__ st,
                                      double *__restrict__ fq, float *__restrict__ fF) {
     if (st->step >= st->target_step) return;
     const int j = blockIdx.y;
-    const long long slot = ((st->windows - start_windows) * K + j) % cap;
+    if (j >= st->k_eff) return;   // steps the draft did not reach carry no target label
+    // frames are numbered by verified window steps (the commit kernel adds k_eff afterwards)
+    const long long slot = (st->verified - start_verified + j) % cap;
     const int D = 3 * N;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < D; e += gridDim.x * blockDim.x) {
         fq[slot * D + e] = w_qmid[(size_t)j * D + e];
@@ -403,11 +405,11 @@ int train_set_capture(TrainState &t, long long capacity, int N) {
     if (!t.capture_on) return LSD_OK;
     if (cudaMalloc(&t.fq, (size_t)capacity * 3 * N * sizeof(double)) != cudaSuccess) return LSD_ENOMEM;
     if (cudaMalloc(&t.fF, (size_t)capacity * 3 * N * sizeof(float)) != cudaSuccess) return LSD_ENOMEM;
-    // frames are counted from the current window counter
+    // frames are counted from the current verified-steps counter
     if (t.st) {
         DevState s;
         if (cudaMemcpy(&s, t.st, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess) return LSD_ECUDA;
-        t.start_windows = s.windows;
+        t.start_verified = s.verified;
     }
     return LSD_OK;
 }
@@ -418,7 +420,7 @@ int train_frame_count(TrainState &t, int64_t *n, cudaStream_t s) {
     DevState ds;
     if (cudaMemcpyAsync(&ds, t.st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LSD_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return LSD_ECUDA;
-    const long long f = (ds.windows - t.start_windows) * (long long)t.K;
+    const long long f = ds.verified - t.start_verified;
     *n = f < t.capacity ? f : t.capacity;
     return LSD_OK;
 }
@@ -429,7 +431,7 @@ void enqueue_frame_capture(TrainState &t, const double *w_qmid, const float *w_F
     t.st = st;
     const int D = 3 * N;
     const int bx = (D + 255) / 256 < 64 ? (D + 255) / 256 : 64;
-    frame_capture_kernel<<<dim3(bx, K), 256, 0, s>>>(w_qmid, w_Ft, K, N, t.capacity, t.start_windows, st, t.fq, t.fF);
+    frame_capture_kernel<<<dim3(bx, K), 256, 0, s>>>(w_qmid, w_Ft, K, N, t.capacity, t.start_verified, st, t.fq, t.fF);
 }
 
 size_t train_adam_size(const TrainState &t) { return t.enabled ? t.n_weights : 0; }

@@ -16,7 +16,7 @@ struct TrainState {
     // frame ring buffer (positions FP64, target forces FP32)
     bool capture_on = false;
     long long capacity = 0;
-    long long start_windows = 0; // windows counter when capture started
+    long long start_verified = 0; // verified-steps counter when capture started
     int K = 0;
     double *fq = nullptr;
     float *fF = nullptr;

@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(kTransThreads)
                             double *__restrict__ logu, int atoms_per_block) {
     __shared__ double sh[32];
     if (st->step >= st->target_step) return;
+    if ((int)blockIdx.y >= st->k_eff) return;   // window step the draft did not reach
     const int N = g.N;
     const int j = blockIdx.y;
     const unsigned long long n = (unsigned long long)(st->step + j + 1);
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(kTransThreads)
     __shared__ int s_nc, s_rej, s_l, s_bad;
     __shared__ bool s_last;
     if (st->step >= st->target_step) return;
+    K = min(K, st->k_eff);   // the window holds the k_eff steps the draft reached
     const int N = g.N;
     const long long n0 = st->step;
     const long long rem = st->target_step - n0;

@@ -22,7 +22,12 @@ namespace lsd {
 // code order and lanes are compacted in order, so each row comes out sorted
 // by (k, code) without a sort.
 // ---------------------------------------------------------------------------
-__global__ void neigh_build_kernel(const uint4 *__restrict__ fix, int M, Geo g, float rmax2f, float near2f,
+// LIST = false: candidates are all atoms of the window step (any configuration);
+// LIST = true: candidates are the atom's sorted Verlet list, and rows of window
+// steps the draft did not reach (j >= k_eff) are left empty.
+template <bool LIST>
+__global__ void neigh_build_kernel(const uint4 *__restrict__ fix, const int *__restrict__ vlist,
+                                   const int *__restrict__ vcount, int vcap, int M, Geo g, float rmax2f, float near2f,
                                    int cap_near, int cap_far, int *__restrict__ near_keys, int *__restrict__ far_keys,
                                    int *__restrict__ n_near, int *__restrict__ n_far, DevState *st) {
     const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
@@ -30,13 +35,23 @@ __global__ void neigh_build_kernel(const uint4 *__restrict__ fix, int M, Geo g, 
     if (row >= M) return;
     const int N = g.N;
     const int j = row / N, i = row - j * N;
+    if (LIST && j >= st->k_eff) {
+        if (lane == 0) {
+            n_near[row] = 0;
+            n_far[row] = 0;
+        }
+        return;
+    }
     const uint4 *fj = fix + (size_t)j * N;
     const uint4 fi = fj[i];
     int *nk = near_keys + (size_t)row * cap_near;
     int *fk = far_keys + (size_t)row * cap_far;
+    const int *cand = LIST ? vlist + (size_t)i * vcap : nullptr;
+    const int ncand = LIST ? vcount[i] : N;
     int cn = 0, cf = 0;
-    for (int base = 0; base < N; base += 32) {
-        const int k = base + lane;
+    for (int base = 0; base < ncand; base += 32) {
+        const int t = base + lane;
+        const int k = LIST ? (t < ncand ? cand[t] : N) : t;
         unsigned mn = 0u, mf = 0u;
         AxisOpts ox, oy, oz;
         ox = oy = oz = AxisOpts{0.f, 0.f, 0, 0, 0};
@@ -410,8 +425,17 @@ void launch_neigh_build(const uint4 *fix, int M, const Geo &g, float rmax2f, flo
                         int *near_keys, int *far_keys, int *n_near, int *n_far, DevState *st, cudaStream_t s) {
     const int threads = 256;
     const int blocks = (int)(((size_t)M * 32 + threads - 1) / threads);
-    neigh_build_kernel<<<blocks, threads, 0, s>>>(fix, M, g, rmax2f, near2f, cap_near, cap_far, near_keys, far_keys,
-                                                  n_near, n_far, st);
+    neigh_build_kernel<false><<<blocks, threads, 0, s>>>(fix, nullptr, nullptr, 0, M, g, rmax2f, near2f, cap_near,
+                                                         cap_far, near_keys, far_keys, n_near, n_far, st);
+}
+
+void launch_neigh_list(const uint4 *fix, const int *vlist, const int *vcount, int vcap, int M, const Geo &g,
+                       float rmax2f, float near2f, int cap_near, int cap_far, int *near_keys, int *far_keys,
+                       int *n_near, int *n_far, DevState *st, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = (int)(((size_t)M * 32 + threads - 1) / threads);
+    neigh_build_kernel<true><<<blocks, threads, 0, s>>>(fix, vlist, vcount, vcap, M, g, rmax2f, near2f, cap_near,
+                                                        cap_far, near_keys, far_keys, n_near, n_far, st);
 }
 
 size_t desc_smem_bytes(int warps, int cap) { return (size_t)warps * kStageFloats * cap * sizeof(float); }

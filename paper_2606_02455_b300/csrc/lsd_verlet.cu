@@ -1,0 +1,186 @@
+// lsd_verlet.cu -- per-window Verlet candidate lists from a cell grid.
+//
+// At the start of every window (and of every plain step) the base positions
+// are binned into a cell grid with cells at least r_list = r_cut + skin wide,
+// and every atom gets the sorted list of atoms whose minimum image lies within
+// r_list.  The draft then verifies, at every step, that no atom has moved more
+// than 0.45 skin from the base (otherwise it stops drafting: the window is
+// truncated at that step), so for every drafted step each pair within r_cut
+// is in the list; every list entry is still tested with the exact membership
+// rule, so the interacting sets are exactly the rule's.
+//
+// cell_count_kernel   fixed point of the base positions, cell of each atom, counts
+// cell_scan_kernel    exclusive scan of the counts (one CTA)
+// cell_fill_kernel    atom indices in cell order (slot order inside a cell does
+//                     not matter: lists are sorted afterwards)
+// verlet_list_kernel  one warp per atom: 27 neighbouring cells (or all atoms
+//                     for a grid narrower than 3 cells), minimum-image test,
+//                     bitonic sort in shared memory, sorted list out
+#include "lsd_common.cuh"
+#include "lsd_kernels.h"
+
+namespace lsd {
+
+__device__ __forceinline__ int cell_of(uint32_t u, int nc) { return (int)(((unsigned long long)u * (unsigned)nc) >> 32); }
+
+__global__ void cell_count_kernel(const double *__restrict__ q, const int *__restrict__ species, Geo g, int3 nc,
+                                  uint4 *__restrict__ fix_base, int *__restrict__ cell_of_atom,
+                                  int *__restrict__ cell_count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    const uint32_t ux = fixpoint(q[3 * i], g.scale[0]), uy = fixpoint(q[3 * i + 1], g.scale[1]),
+                   uz = fixpoint(q[3 * i + 2], g.scale[2]);
+    fix_base[i] = make_uint4(ux, uy, uz, (unsigned)species[i]);
+    const int c = (cell_of(uz, nc.z) * nc.y + cell_of(uy, nc.y)) * nc.x + cell_of(ux, nc.x);
+    cell_of_atom[i] = c;
+    atomicAdd(&cell_count[c], 1);
+}
+
+__global__ void cell_scan_kernel(int ncells, int *__restrict__ cell_count, int *__restrict__ cell_start) {
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < ncells; base += blockDim.x) {
+        const int c = base + threadIdx.x;
+        const int v = c < ncells ? cell_count[c] : 0;
+        int s = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += t;
+        }
+        if (lane == 31) warp_tot[w] = s;
+        __syncthreads();
+        if (w == 0) {
+            int t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += u;
+            }
+            warp_tot[lane] = t;
+        }
+        __syncthreads();
+        const int excl = carry + (w > 0 ? warp_tot[w - 1] : 0) + s - v;
+        if (c < ncells) {
+            cell_start[c] = excl;
+            cell_count[c] = 0;   // reused as the fill cursor
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) cell_start[ncells] = carry;
+}
+
+__global__ void cell_fill_kernel(int N, const int *__restrict__ cell_of_atom, const int *__restrict__ cell_start,
+                                 int *__restrict__ cursor, int *__restrict__ cell_atoms) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int c = cell_of_atom[i];
+    cell_atoms[cell_start[c] + atomicAdd(&cursor[c], 1)] = i;
+}
+
+__global__ void verlet_list_kernel(const uint4 *__restrict__ fix_base, const int *__restrict__ cell_of_atom,
+                                   const int *__restrict__ cell_start, const int *__restrict__ cell_atoms, Geo g,
+                                   int3 nc, float rlist2f, int cap, int cap_pow2, int *__restrict__ vlist,
+                                   int *__restrict__ vcount, DevState *st) {
+    extern __shared__ int sbuf[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (i >= g.N) return;
+    int *buf = sbuf + (size_t)wib * cap_pow2;
+    const uint4 fi = fix_base[i];
+    const bool one_cell = nc.x < 3 || nc.y < 3 || nc.z < 3;
+    const int ci = cell_of_atom[i];
+    const int cx = ci % nc.x, cy = (ci / nc.x) % nc.y, cz = ci / (nc.x * nc.y);
+    int cnt = 0;
+    const int ncell_scan = one_cell ? 1 : 27;
+    for (int t = 0; t < ncell_scan; ++t) {
+        int s0, s1;
+        if (one_cell) {
+            s0 = 0;
+            s1 = g.N;
+        } else {
+            const int ox = t % 3 - 1, oy = (t / 3) % 3 - 1, oz = t / 9 - 1;
+            const int c = (((cz + oz + nc.z) % nc.z) * nc.y + (cy + oy + nc.y) % nc.y) * nc.x + (cx + ox + nc.x) % nc.x;
+            s0 = cell_start[c];
+            s1 = cell_start[c + 1];
+        }
+        for (int base = s0; base < s1; base += 32) {
+            const int p = base + lane;
+            int k = -1;
+            bool in = false;
+            if (p < s1) {
+                k = one_cell ? p : cell_atoms[p];
+                if (k != i) {
+                    const uint4 fk = fix_base[k];
+                    float dx, dy, dz;
+                    int kk;
+                    axis_min(fi.x, fk.x, g.scale_f[0], dx, kk);
+                    axis_min(fi.y, fk.y, g.scale_f[1], dy, kk);
+                    axis_min(fi.z, fk.z, g.scale_f[2], dz, kk);
+                    in = dist2_rule(dx, dy, dz) < rlist2f;
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, in);
+            const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+            if (in && pos < cap_pow2) buf[pos] = k;
+            cnt += __popc(bal);
+        }
+    }
+    // (an atom's own images lie at least one box length away, beyond any cutoff rc < L)
+    const int n = cnt < cap ? cnt : cap;
+    for (int p = n + lane; p < cap_pow2; p += 32) buf[p] = 0x7fffffff;
+    __syncwarp();
+    // bitonic sort of cap_pow2 entries by atom index
+    for (int k2 = 2; k2 <= cap_pow2; k2 <<= 1) {
+        for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
+            for (int a = lane; a < cap_pow2; a += 32) {
+                const int b = a ^ j2;
+                if (b > a) {
+                    const int x = buf[a], y = buf[b];
+                    const bool up = (a & k2) == 0;
+                    if (up ? x > y : x < y) {
+                        buf[a] = y;
+                        buf[b] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    int *out = vlist + (size_t)i * cap;
+    for (int p = lane; p < n; p += 32) out[p] = buf[p];
+    if (lane == 0) {
+        vcount[i] = n;
+        if (cnt > cap) atomicOr(&st->err, 1);
+    }
+}
+
+void launch_verlet_build(const VerletPlan &vp, const double *q, const int *species, const Geo &g, VerletBufs &b,
+                         DevState *st, cudaStream_t s) {
+    const int N = g.N;
+    const int3 nc = make_int3(vp.nc[0], vp.nc[1], vp.nc[2]);
+    const int ncells = vp.nc[0] * vp.nc[1] * vp.nc[2];
+    const bool one_cell = vp.nc[0] < 3 || vp.nc[1] < 3 || vp.nc[2] < 3;
+    if (!one_cell) cudaMemsetAsync(b.cell_count, 0, (size_t)ncells * sizeof(int), s);
+    cell_count_kernel<<<(N + 255) / 256, 256, 0, s>>>(q, species, g, one_cell ? make_int3(1, 1, 1) : nc, b.fix_base,
+                                                       b.cell_of_atom, one_cell ? b.cell_scratch : b.cell_count);
+    if (!one_cell) {
+        cell_scan_kernel<<<1, 1024, 0, s>>>(ncells, b.cell_count, b.cell_start);
+        cell_fill_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, b.cell_of_atom, b.cell_start, b.cell_count, b.cell_atoms);
+    }
+    const int warps = 8;
+    verlet_list_kernel<<<(N + warps - 1) / warps, warps * 32, (size_t)warps * vp.cap_pow2 * sizeof(int), s>>>(
+        b.fix_base, b.cell_of_atom, b.cell_start, b.cell_atoms, g, nc, vp.rlist2f, vp.cap, vp.cap_pow2, b.vlist,
+        b.vcount, st);
+}
+
+cudaError_t verlet_setup(int max_smem) {
+    return cudaFuncSetAttribute(verlet_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+}
+
+}  // namespace lsd

@@ -208,3 +208,26 @@ def test_neighbor_lists_symmetric_and_canonical():
             pairs.add((i, int(k) >> 5, int(k) & 31))
     for (i, j, c) in pairs:
         assert (j, i, 26 - c) in pairs
+
+
+@pytest.mark.parametrize("case", CASES[:3])
+def test_forces_on_selected_atoms_equal_full_pass(case):
+    """The atom-by-atom force routine used for large-system sampling equals the full evaluation."""
+    s = W.small_system(n_cells=2, a=4.0, n_species=2, seed=6, L=8.0)
+    pot = _pot(s, **case)
+    q = s.positions + np.array([0.2, -0.1, 0.05])
+    F = O.forces(s, pot, q)
+    sel = [0, 3, 5, 7, 30]
+    Fs = O.forces_subset(s, pot, q, sel)
+    assert np.allclose(Fs, F[sel], rtol=1e-11, atol=1e-14)
+
+
+def test_forces_on_selected_atoms_with_images():
+    """Same with a cutoff larger than half the box (several images of one neighbour)."""
+    s = W.small_system(n_cells=1, a=5.0, n_species=1, seed=4, L=7.0)
+    pot = W.Potential(lj_eps=np.array([0.0104]), lj_sigma=np.array([3.4]), lj_cutoff=6.5, n_rbf=8, n_ang=16,
+                      n_layers=1, width=8, desc_cutoff=4.0, head="tanh", head_scale=0.05,
+                      weights=W.mlp_weights(W.input_dim(1, 8, 16), 1, 8, 5))
+    F = O.forces(s, pot, s.positions)
+    Fs = O.forces_subset(s, pot, s.positions, [0, 1, 2, 3])
+    assert np.allclose(Fs, F, rtol=1e-11, atol=1e-14)
