@@ -66,7 +66,6 @@ struct lsd_handle {
     DraftPlan dplan{};
     VerletPlan vplan{};
     VerletBufs vbufs{};
-    int *w_flags = nullptr;
     float *w_dEdX = nullptr;
     // device state
     double *q = nullptr, *p = nullptr;
@@ -337,23 +336,23 @@ void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, f
 
 // The window's Verlet lists around the base state, then the draft.
 void enqueue_draft(lsd_handle *h, cudaStream_t s) {
-    launch_verlet_build(h->vplan, h->q, h->species, h->geo, h->vbufs, h->st, s);
+    if (!h->vplan.all_pairs) launch_verlet_build(h->vplan, h->q, h->species, h->geo, h->vbufs, h->st, s);
     launch_draft(h->dplan, h->learned_small, h->K, h->geo, h->draft.dev, h->coef, h->vplan, h->vbufs, h->species,
                  h->q, h->p, h->ec_dF, h->ec_on, h->st, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Fraw, h->w_fix,
-                 h->w_flags, h->w_dEdX, s);
+                 h->w_dEdX, s);
 }
 
 void enqueue_verify(lsd_handle *h, cudaStream_t s) {
-    enqueue_eval(h, h->target, h->w_fix, h->K, h->w_Ft, nullptr, s, true);
+    enqueue_eval(h, h->target, h->w_fix, h->K, h->w_Ft, nullptr, s, !h->vplan.all_pairs);
     if (h->train.capture_on) enqueue_frame_capture(h->train, h->w_qmid, h->w_Ft, h->K, h->N, h->st, s);
     launch_transport(h->K, h->geo, h->coef, h->species, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Ft, h->w_Fraw, h->ec_dF,
                      h->ec_on, h->q, h->p, h->st, h->partials, h->logu, s);
 }
 
 void enqueue_plain(lsd_handle *h, cudaStream_t s) {
-    launch_verlet_build(h->vplan, h->q, h->species, h->geo, h->vbufs, h->st, s);
+    if (!h->vplan.all_pairs) launch_verlet_build(h->vplan, h->q, h->species, h->geo, h->vbufs, h->st, s);
     launch_plain_half(h->geo, h->coef, h->species, h->q, h->p, h->st, h->w_qmid, h->w_fix, s);
-    enqueue_eval(h, h->target, h->w_fix, 1, h->w_Ft, nullptr, s, true);
+    enqueue_eval(h, h->target, h->w_fix, 1, h->w_Ft, nullptr, s, !h->vplan.all_pairs);
     launch_plain_finish(h->geo, h->coef, h->species, h->w_qmid, h->w_Ft, h->q, h->p, h->st, s);
 }
 
@@ -537,14 +536,23 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         const double rlist = rfar + skin;
         VerletPlan &vp = h->vplan;
         for (int a = 0; a < 3; ++a) vp.nc[a] = std::max(1, (int)std::floor(h->box[a] / rlist));
+        vp.all_pairs = vp.nc[0] < 3 || vp.nc[1] < 3 || vp.nc[2] < 3;
         vp.rlist2f = (float)(rlist * rlist);
         vp.move2f = (float)((0.45 * skin) * (0.45 * skin));
         vp.cap = std::min(nb_capacity(rho, rlist, 32), (h->N + 31) / 32 * 32);
         vp.cap_pow2 = 32;
         while (vp.cap_pow2 < vp.cap) vp.cap_pow2 *= 2;
         if ((size_t)8 * vp.cap_pow2 * sizeof(int) > (size_t)kMaxDynSmem) return fail(LSD_EUNSUPPORTED);
-        const int maxc = draft_max_cluster(64 * 1024);
-        h->dplan = draft_plan(h->N, h->draft.dev, h->learned_small, maxc, kMaxDynSmem);
+        // the largest cluster the hardware co-schedules with the plan's shared memory
+        h->dplan = draft_plan(h->N, h->draft.dev, h->learned_small, 16, kMaxDynSmem);
+        const int maxc = draft_max_cluster(h->dplan.smem, h->learned_small);
+        if (maxc < h->dplan.cluster) h->dplan = draft_plan(h->N, h->draft.dev, h->learned_small, maxc, kMaxDynSmem);
+        {
+            double rcd = h->draft.p.lj_cutoff;
+            if (h->learned_small) rcd = std::max(rcd, h->draft.p.desc_cutoff);
+            const double lmin = std::min(h->box[0], std::min(h->box[1], h->box[2]));
+            h->dplan.minimg = rcd < 0.499 * lmin;
+        }
         if (!h->dplan.ok) return fail(LSD_EUNSUPPORTED);
     }
     const size_t N = h->N, D = 3 * N, KN = (size_t)K * N, KD = (size_t)K * D;
@@ -559,8 +567,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         (rc = dalloc(h, &h->E_mlp, KN)) || (rc = dalloc(h, &h->E_lj, KN)) || (rc = dalloc(h, &h->E_atom, KN)) ||
         (rc = dalloc(h, &h->pair_g, KN * h->cap_near)) || (rc = dalloc(h, &h->Fpart, KN)) ||
         (rc = dalloc(h, &h->partials, (size_t)K * ((h->N + 1023) / 1024 + 600))) ||
-        (rc = dalloc(h, &h->logu, (size_t)K)) || (rc = dalloc(h, &h->w_flags, (size_t)K * 16)) ||
-        (rc = dalloc(h, &h->w_dEdX, N * std::max(h->draft.dev.d0p, 32))) ||
+        (rc = dalloc(h, &h->logu, (size_t)K)) ||         (rc = dalloc(h, &h->w_dEdX, N * std::max(h->draft.dev.d0p, 32))) ||
         (rc = dalloc(h, &h->vbufs.fix_base, N)) || (rc = dalloc(h, &h->vbufs.cell_of_atom, N)) ||
         (rc = dalloc(h, &h->vbufs.cell_count, (size_t)h->vplan.nc[0] * h->vplan.nc[1] * h->vplan.nc[2])) ||
         (rc = dalloc(h, &h->vbufs.cell_start, (size_t)h->vplan.nc[0] * h->vplan.nc[1] * h->vplan.nc[2] + 1)) ||
@@ -864,9 +871,13 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
     CK(cudaEventRecord(ev[0], st));
     enqueue_draft(h, st);
     CK(cudaEventRecord(ev[1], st));
-    launch_neigh_list(h->w_fix, h->vbufs.vlist, h->vbufs.vcount, h->vplan.cap, M, h->geo, h->target.rmax2f,
-                      h->target.near2f, h->cap_near, h->cap_far, h->near_keys, h->far_keys, h->n_near, h->n_far, h->st,
-                      st);
+    if (h->vplan.all_pairs)
+        launch_neigh_build(h->w_fix, M, h->geo, h->target.rmax2f, h->target.near2f, h->cap_near, h->cap_far,
+                           h->near_keys, h->far_keys, h->n_near, h->n_far, h->st, st);
+    else
+        launch_neigh_list(h->w_fix, h->vbufs.vlist, h->vbufs.vcount, h->vplan.cap, M, h->geo, h->target.rmax2f,
+                          h->target.near2f, h->cap_near, h->cap_far, h->near_keys, h->far_keys, h->n_near, h->n_far,
+                          h->st, st);
     CK(cudaEventRecord(ev[2], st));
     if (P.has_mlp) launch_desc(h->w_fix, h->near_keys, h->n_near, h->cap_near, M, h->geo, P, h->X, st);
     CK(cudaEventRecord(ev[3], st));

@@ -138,6 +138,13 @@ __device__ __forceinline__ uint32_t fixpoint(double q, double scale) {
     return (uint32_t)(unsigned long long)fi;
 }
 
+// Entry s of a per-species array inside a by-value kernel parameter, by
+// selection: a dynamic index would copy the whole parameter struct to local
+// memory.
+__device__ __forceinline__ double species_pick(const double (&a)[kMaxSpecies], int s) {
+    return s == 0 ? a[0] : (s == 1 ? a[1] : (s == 2 ? a[2] : a[3]));
+}
+
 __device__ __forceinline__ float dist2_rule(float dx, float dy, float dz) {
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }

@@ -17,7 +17,9 @@
 // cluster stops drafting at that step (k_eff < K, decided identically in every
 // CTA from flags read after the barrier), because the lists are no longer
 // guaranteed complete.  Each list entry is tested with the exact membership
-// rule, so the interacting set is the rule's set, not an approximation.
+// rule, so the interacting set is the rule's set, not an approximation.  When
+// the cell grid is narrower than three cells every atom is a candidate: no
+// lists, no displacement check, k_eff = K.
 //
 // FP64 only for the state updates, with explicit round-to-nearest intrinsics
 // so the half-step positions are reproducible bit for bit.
@@ -43,10 +45,37 @@ struct FixView {
     __device__ __forceinline__ uint4 operator[](int k) const { return smem ? smem[k] : __ldcg(glob + k); }
 };
 
+// Every image of atom k that passes the per-axis bound around atom i, as
+// fn(dx, dy, dz, d2).  With minimg (every cutoff below 0.499 of every box side)
+// only the minimum image can lie within the cutoff: the other image along an
+// axis is at least L/2 (less rounding) away, so the rule's set is the set of
+// minimum images that pass d2 < rc2, and the general enumeration is skipped.
+template <class Fn>
+__device__ __forceinline__ void for_images(const Geo &g, uint4 fi, uint4 fk, float rc2, bool minimg, Fn &&fn) {
+    if (minimg) {
+        float dx, dy, dz;
+        int kk;
+        axis_min(fi.x, fk.x, g.scale_f[0], dx, kk);
+        axis_min(fi.y, fk.y, g.scale_f[1], dy, kk);
+        axis_min(fi.z, fk.z, g.scale_f[2], dz, kk);
+        fn(dx, dy, dz, dist2_rule(dx, dy, dz));
+        return;
+    }
+    const AxisOpts ox = axis_opts(fi.x, fk.x, g.scale_f[0], g.Lf[0], rc2);
+    const AxisOpts oy = axis_opts(fi.y, fk.y, g.scale_f[1], g.Lf[1], rc2);
+    const AxisOpts oz = axis_opts(fi.z, fk.z, g.scale_f[2], g.Lf[2], rc2);
+    for (int bz = 0; bz < oz.n; ++bz)
+        for (int by = 0; by < oy.n; ++by)
+            for (int bx = 0; bx < ox.n; ++bx) {
+                const float dx = opt_d(ox, bx), dy = opt_d(oy, by), dz = opt_d(oz, bz);
+                fn(dx, dy, dz, dist2_rule(dx, dy, dz));
+            }
+}
+
 // Learned draft, first phase: radial descriptors of atom i from its candidate
-// list, the MLP (BF16 operands, FP32 accumulation), dE/dx written to g_out[d0p].
+// list (all atoms when cand is null), the MLP (BF16 operands, FP32 accumulation), dE/dx written to g_out[d0p].
 __device__ void learned_atom_grad(const PotDev &P, const Geo &g, const FixView &fx, int i, const int *cand, int nc,
-                                  float *stage, float *xbuf, float *g_out) {
+                                  bool minimg, float *stage, float *xbuf, float *g_out) {
     const int lane = threadIdx.x & 31;
     const uint4 fi = fx[i];
     float *sr = stage, *sfc = stage + kLearnCap;
@@ -54,24 +83,17 @@ __device__ void learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
     int cnt = 0;
     for (int base = 0; base < nc; base += 32) {
         const int t = base + lane;
-        unsigned m = 0u;
-        AxisOpts ox, oy, oz;
-        ox = oy = oz = AxisOpts{0.f, 0.f, 0, 0, 0};
-        int sk = 0;
-        if (t < nc) {
-            const int k = __ldg(cand + t);
+        // the (at most 8) images of k within the descriptor cutoff, in enumeration order
+        float rs[8];
+        int nm = 0, sk = 0;
+        const int k = t < nc ? (cand ? __ldg(cand + t) : t) : i;
+        if (k != i) {
             const uint4 fk = fx[k];
             sk = (int)fk.w;
-            ox = axis_opts(fi.x, fk.x, g.scale_f[0], g.Lf[0], P.desc_rc2f);
-            oy = axis_opts(fi.y, fk.y, g.scale_f[1], g.Lf[1], P.desc_rc2f);
-            oz = axis_opts(fi.z, fk.z, g.scale_f[2], g.Lf[2], P.desc_rc2f);
-            for (int bz = 0; bz < oz.n; ++bz)
-                for (int by = 0; by < oy.n; ++by)
-                    for (int bx = 0; bx < ox.n; ++bx)
-                        if (dist2_rule(opt_d(ox, bx), opt_d(oy, by), opt_d(oz, bz)) < P.desc_rc2f)
-                            m |= 1u << (bx + 2 * by + 4 * bz);
+            for_images(g, fi, fk, P.desc_rc2f, minimg, [&](float, float, float, float d2) {
+                if (d2 < P.desc_rc2f && nm < 8) rs[nm++] = sqrtf(d2);
+            });
         }
-        const int nm = __popc(m);
         int sc = nm;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -80,11 +102,9 @@ __device__ void learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
         }
         const int tot = __shfl_sync(0xffffffffu, sc, 31);
         int w = cnt + sc - nm;
-        for (int c = 0; c < 8; ++c) {
-            if (!(m & (1u << c))) continue;
+        for (int c = 0; c < nm; ++c) {
             if (w < kLearnCap) {
-                const float dx = opt_d(ox, c & 1), dy = opt_d(oy, (c >> 1) & 1), dz = opt_d(oz, c >> 2);
-                const float r = sqrtf(dist2_rule(dx, dy, dz));
+                const float r = rs[c];
                 float fc, dfc;
                 cutoff_fn(r, P.desc_rc, fc, dfc);
                 sr[w] = r;
@@ -139,16 +159,48 @@ __device__ void learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
     __syncwarp();
 }
 
-template <bool LEARNED>
-__global__ void __launch_bounds__(kDraftThreads)
+// Store v at the same shared-memory offset as `local` in CTA `rank` of the cluster.
+__device__ __forceinline__ void st_cluster(const void *local, uint32_t rank, uint4 v) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(ra), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ void st_cluster(const int *local, uint32_t rank, int v) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
+}
+
+// One launch drafts the whole window.  Per step:
+//   A  half-step positions of owned atoms (FP64, one lane per coordinate, four
+//      lanes per atom), their fixed point written to global memory for the
+//      verification and, when the positions fit in shared memory, stored
+//      directly into every CTA's copy (distributed shared memory,
+//      double-buffered by step parity, so one cluster barrier per step orders
+//      both the writes of step j and the reads of step j-1); with Verlet lists,
+//      the displacement check, whose flag is stored the same way
+//   B  cluster barrier; stop when any CTA flagged a displacement
+//   C  forces on owned atoms (one warp per atom, lanes over the candidates:
+//      the atom's Verlet list, or all atoms when vlist is null)
+//   D  BOB + A, one lane per coordinate
+// REG keeps owned atoms' FP64 state in registers (a CTA owns at most
+// kRegPasses * kGroups atoms); otherwise it is re-read from the window arrays.
+constexpr int kGroups = kDraftThreads / 4;   // four-lane groups: one atom, lanes 0..2 its coordinates
+constexpr int kRegPasses = 2;
+
+template <bool LEARNED, bool REG>
+__global__ void __launch_bounds__(kDraftThreads, 1)
     draft_window_cluster_kernel(int K, Geo g, PotDev P, Coef cf, const int *__restrict__ vlist,
                                 const int *__restrict__ vcount, int vcap, const uint4 *__restrict__ fix_base,
-                                float move2f, int stage_fix, const int *__restrict__ species,
+                                float move2f, int stage_fix, int minimg, const int *__restrict__ species,
                                 const double *__restrict__ q_base, const double *__restrict__ p_base,
                                 const float *__restrict__ ec_dF, int ec_on, DevState *__restrict__ st,
                                 double *__restrict__ w_qmid, double *__restrict__ w_pdraft, float *__restrict__ w_Fd,
-                                float *__restrict__ w_Fraw, uint4 *__restrict__ w_fix, int *__restrict__ w_flags,
-                                float *__restrict__ w_dEdX) {
+                                float *__restrict__ w_Fraw, uint4 *__restrict__ w_fix, float *__restrict__ w_dEdX) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N;
     const int C = gridDim.x, c = blockIdx.x;
@@ -158,28 +210,60 @@ __global__ void __launch_bounds__(kDraftThreads)
     float4 *sF = (float4 *)smraw;                               // [A]
     float *slj = (float *)(sF + A);                             // sig2, eps24 tables
     float *sstage = slj + 2 * kMaxSpecies * kMaxSpecies;        // learned: per warp 3*cap + d0p
-    uint4 *sfix = (uint4 *)(sstage + (LEARNED ? (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) : 0));
+    uint4 *sfix = (uint4 *)(sstage + (LEARNED ? (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) : 0));  // [2][N]
+    int *sflag = (int *)(sfix + (stage_fix ? 2 * (size_t)N : 0));                                        // [2]
     if (st->step >= st->target_step) return;   // uniform over the cluster
     const long long n0 = st->step;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int grp = tid >> 2, x = tid & 3, gl = lane & ~3;
     const size_t D = (size_t)3 * N;
+    const bool use_list = vlist != nullptr;
+    const int passes = (nown + kGroups - 1) / kGroups;
+    constexpr int kP = REG ? kRegPasses : 1;
     const float rc2_all = LEARNED ? fmaxf(P.lj_rc2f, P.desc_rc2f) : P.lj_rc2f;
+    const double scale_x = x == 0 ? g.scale[0] : (x == 1 ? g.scale[1] : g.scale[2]);
     for (int t = tid; t < g.S * g.S; t += blockDim.x) {
         slj[t] = P.lj_sig2[t];
         slj[kMaxSpecies * kMaxSpecies + t] = P.lj_eps24[t];
     }
+    if (tid < 2) sflag[tid] = 0;
+    // REG: coordinate x of owned atoms grp + p * kGroups
+    double qr[kP], pr[kP];
+    float dfr[kP], xr[kP];
+#pragma unroll
+    for (int p = 0; p < kP; ++p) {
+        qr[p] = pr[p] = 0.0;
+        dfr[p] = xr[p] = 0.f;
+        const int ii = grp + p * kGroups;
+        if (REG && ii < nown && x < 3) {
+            const int i = a0 + ii;
+            qr[p] = q_base[3 * i + x];
+            pr[p] = p_base[3 * i + x];
+            dfr[p] = ec_on ? ec_dF[3 * i + x] : 0.f;
+        }
+    }
+    // every CTA has started and zeroed its flags before the first remote store
+    if (stage_fix || use_list) cluster_barrier();
+    __syncthreads();
     int keff = K;
     for (int j = 0; j < K; ++j) {
-        // A: half-step positions of owned atoms, fixed point, displacement from the list's base
+        const int par = j & 1;
+        const unsigned long long n = (unsigned long long)(n0 + j + 1);
+        // A: half-step positions, fixed point, broadcast, displacement from the list's base
         int moved = 0;
-        for (int i = a0 + tid; i < a1; i += blockDim.x) {
-            const int sp = species[i];
-            const double hm = cf.hm[sp];
-            uint32_t u0, u1, u2;
-#pragma unroll
-            for (int x = 0; x < 3; ++x) {
+        auto step_a = [&](int p, double &qreg, double &preg) {
+            const int ii = grp + p * kGroups;
+            const bool own = ii < nown;
+            const int i = a0 + (own ? ii : 0);
+            const int sp = own ? species[i] : 0;
+            uint32_t u = 0u;
+            if (own && x < 3) {
+                const double hm = species_pick(cf.hm, sp);
                 double qv, pv;
-                if (j == 0) {
+                if (REG) {
+                    pv = preg;
+                    qv = j == 0 ? qreg : __dadd_rn(qreg, __dmul_rn(pv, hm));
+                } else if (j == 0) {
                     qv = q_base[3 * i + x];
                     pv = p_base[3 * i + x];
                 } else {
@@ -188,42 +272,67 @@ __global__ void __launch_bounds__(kDraftThreads)
                     qv = __dadd_rn(w_qmid[o], __dmul_rn(pv, hm));
                 }
                 const double qm = __dadd_rn(qv, __dmul_rn(pv, hm));
+                if (REG) qreg = qm;
                 w_qmid[(size_t)j * D + 3 * i + x] = qm;
-                const uint32_t u = fixpoint(qm, g.scale[x]);
-                if (x == 0) u0 = u; else if (x == 1) u1 = u; else u2 = u;
+                u = fixpoint(qm, scale_x);
             }
-            w_fix[(size_t)j * N + i] = make_uint4(u0, u1, u2, (unsigned)sp);
-            const uint4 b = fix_base[i];
-            float dmin, d2;
-            int kk;
-            axis_min(b.x, u0, g.scale_f[0], dmin, kk);
-            d2 = dmin * dmin;
-            axis_min(b.y, u1, g.scale_f[1], dmin, kk);
-            d2 += dmin * dmin;
-            axis_min(b.z, u2, g.scale_f[2], dmin, kk);
-            d2 += dmin * dmin;
-            moved |= d2 > move2f;
+            const uint32_t ux = __shfl_sync(0xffffffffu, u, gl), uy = __shfl_sync(0xffffffffu, u, gl + 1),
+                           uz = __shfl_sync(0xffffffffu, u, gl + 2);
+            if (own) {
+                const uint4 fv = make_uint4(ux, uy, uz, (unsigned)sp);
+                if (x == 0) w_fix[(size_t)j * N + i] = fv;
+                if (stage_fix)
+                    for (int r = x; r < C; r += 4) st_cluster(sfix + (size_t)par * N + i, (uint32_t)r, fv);
+                if (use_list && x == 0) {
+                    const uint4 b = fix_base[i];
+                    float dmin, d2;
+                    int kk;
+                    axis_min(b.x, ux, g.scale_f[0], dmin, kk);
+                    d2 = dmin * dmin;
+                    axis_min(b.y, uy, g.scale_f[1], dmin, kk);
+                    d2 += dmin * dmin;
+                    axis_min(b.z, uz, g.scale_f[2], dmin, kk);
+                    d2 += dmin * dmin;
+                    moved |= d2 > move2f;
+                }
+            }
+        };
+        if (REG) {
+#pragma unroll
+            for (int p = 0; p < kP; ++p)
+                if (p < passes) step_a(p, qr[p], pr[p]);
+        } else {
+            double dq, dp;
+            for (int p = 0; p < passes; ++p) step_a(p, dq, dp);
         }
-        moved = __syncthreads_or(moved);
-        if (tid == 0) w_flags[j * C + c] = moved;
+        if (use_list) {
+            moved = __syncthreads_or(moved);
+            if (moved && tid < C) st_cluster(sflag + par, (uint32_t)tid, 1);
+        }
+        // noise of this step's B, independent of the positions: drawn while the barrier completes
+        if (REG) {
+#pragma unroll
+            for (int p = 0; p < kP; ++p) {
+                const int ii = grp + p * kGroups;
+                if (p < passes && ii < nown && x < 3) {
+                    const float3 xi = normals3(cf.seed, n, (uint32_t)(a0 + ii), 0u);
+                    xr[p] = x == 0 ? xi.x : (x == 1 ? xi.y : xi.z);
+                }
+            }
+        }
         cluster_barrier();
-        // B: stop drafting when any atom left the skin (same decision in every CTA)
-        int stop = 0;
-        for (int k = 0; k < C; ++k) stop |= __ldcg(w_flags + j * C + k);
-        if (stop) {
+        // B: stop drafting when any atom left the skin (same flags in every CTA)
+        if (use_list && sflag[par]) {
             keff = j;
             break;
         }
-        FixView fx{stage_fix ? sfix : nullptr, w_fix + (size_t)j * N};
-        if (stage_fix) {
-            for (int k = tid; k < N; k += blockDim.x) sfix[k] = __ldcg(w_fix + (size_t)j * N + k);
-            __syncthreads();
-        }
+        FixView fx{stage_fix ? sfix + (size_t)par * N : nullptr, w_fix + (size_t)j * N};
         if (LEARNED) {
             float *stage = sstage + (size_t)warp * (3 * kLearnCap + P.d0p);
             for (int ii = warp; ii < nown; ii += kDraftWarps) {
                 const int i = a0 + ii;
-                learned_atom_grad(P, g, fx, i, vlist + (size_t)i * vcap, vcount[i], stage, stage + 3 * kLearnCap,
+                learned_atom_grad(P, g, fx, i, use_list ? vlist + (size_t)i * vcap : nullptr,
+                                  use_list ? vcount[i] : N, minimg != 0, stage, stage + 3 * kLearnCap,
                                   w_dEdX + (size_t)i * P.d0p);
             }
             cluster_barrier();   // dE/dx of every atom visible to every CTA
@@ -233,49 +342,43 @@ __global__ void __launch_bounds__(kDraftThreads)
             const int i = a0 + ii;
             const uint4 fi = fx[i];
             const int si = (int)fi.w;
-            const int *lst = vlist + (size_t)i * vcap;
-            const int nl = vcount[i];
+            const int *lst = use_list ? vlist + (size_t)i * vcap : nullptr;
+            const int nl = use_list ? vcount[i] : N;
             float fxx = 0.f, fyy = 0.f, fzz = 0.f;
             for (int t = lane; t < nl; t += 32) {
-                const int k = __ldg(lst + t);
+                const int k = use_list ? __ldg(lst + t) : t;
+                if (k == i) continue;
                 const uint4 fk = fx[k];
-                const AxisOpts ox = axis_opts(fi.x, fk.x, g.scale_f[0], g.Lf[0], rc2_all);
-                const AxisOpts oy = axis_opts(fi.y, fk.y, g.scale_f[1], g.Lf[1], rc2_all);
-                const AxisOpts oz = axis_opts(fi.z, fk.z, g.scale_f[2], g.Lf[2], rc2_all);
-                const int pr = si * g.S + (int)fk.w;
-                const float sig2 = slj[pr], eps24 = slj[kMaxSpecies * kMaxSpecies + pr];
-                for (int bz = 0; bz < oz.n; ++bz)
-                    for (int by = 0; by < oy.n; ++by)
-                        for (int bx = 0; bx < ox.n; ++bx) {
-                            const float dx = opt_d(ox, bx), dy = opt_d(oy, by), dz = opt_d(oz, bz);
-                            const float d2 = dist2_rule(dx, dy, dz);
-                            if (P.has_lj && d2 < P.lj_rc2f) {
-                                const float inv = 1.f / d2;
-                                const float s2 = sig2 * inv;
-                                const float s6 = s2 * s2 * s2, s12 = s6 * s6;
-                                const float fr = -eps24 * (2.f * s12 - s6) * inv;
-                                fxx += fr * dx;
-                                fyy += fr * dy;
-                                fzz += fr * dz;
-                            }
-                            if (LEARNED && d2 < P.desc_rc2f) {
-                                // radial adjoint in gather form: (c_ik + c_ki) d/r
-                                const float r = sqrtf(d2);
-                                float fc, dfc;
-                                cutoff_fn(r, P.desc_rc, fc, dfc);
-                                const float *gi = w_dEdX + (size_t)i * P.d0p + (int)fk.w * P.n_rbf;
-                                const float *gk = w_dEdX + (size_t)k * P.d0p + si * P.n_rbf;
-                                float cc = 0.f;
-                                for (int b = 0; b < P.n_rbf; ++b) {
-                                    const float tt = r - (float)b * P.rbf_w;
-                                    const float dg = expf(-tt * tt * P.rbf_inv2w2) * (-tt * P.rbf_invw2 * fc + dfc);
-                                    cc += (__ldcg(gi + b) + __ldcg(gk + b)) * dg;
-                                }
-                                fxx += cc * dx / r;
-                                fyy += cc * dy / r;
-                                fzz += cc * dz / r;
-                            }
+                const int pr2 = si * g.S + (int)fk.w;
+                const float sig2 = slj[pr2], eps24 = slj[kMaxSpecies * kMaxSpecies + pr2];
+                for_images(g, fi, fk, rc2_all, minimg != 0, [&](float dx, float dy, float dz, float d2) {
+                    if (P.has_lj && d2 < P.lj_rc2f) {
+                        const float inv = 1.f / d2;
+                        const float s2 = sig2 * inv;
+                        const float s6 = s2 * s2 * s2, s12 = s6 * s6;
+                        const float fr = -eps24 * (2.f * s12 - s6) * inv;
+                        fxx += fr * dx;
+                        fyy += fr * dy;
+                        fzz += fr * dz;
+                    }
+                    if (LEARNED && d2 < P.desc_rc2f) {
+                        // radial adjoint in gather form: (c_ik + c_ki) d/r
+                        const float r = sqrtf(d2);
+                        float fc, dfc;
+                        cutoff_fn(r, P.desc_rc, fc, dfc);
+                        const float *gi = w_dEdX + (size_t)i * P.d0p + (int)fk.w * P.n_rbf;
+                        const float *gk = w_dEdX + (size_t)k * P.d0p + si * P.n_rbf;
+                        float cc = 0.f;
+                        for (int b = 0; b < P.n_rbf; ++b) {
+                            const float tt = r - (float)b * P.rbf_w;
+                            const float dg = expf(-tt * tt * P.rbf_inv2w2) * (-tt * P.rbf_invw2 * fc + dfc);
+                            cc += (__ldcg(gi + b) + __ldcg(gk + b)) * dg;
                         }
+                        fxx += cc * dx / r;
+                        fyy += cc * dy / r;
+                        fzz += cc * dz / r;
+                    }
+                });
             }
             fxx = warp_sum(fxx);
             fyy = warp_sum(fyy);
@@ -283,28 +386,41 @@ __global__ void __launch_bounds__(kDraftThreads)
             if (lane == 0) sF[ii] = make_float4(fxx, fyy, fzz, 0.f);
         }
         __syncthreads();
-        // D: BOB + A for owned atoms
-        const unsigned long long n = (unsigned long long)(n0 + j + 1);
-        for (int i = a0 + tid; i < a1; i += blockDim.x) {
+        // the flag of this parity is next written (by any CTA) after the next barrier
+        if (use_list && tid == 0) sflag[par] = 0;
+        // D: BOB + A, one lane per coordinate
+        auto step_d = [&](int p, double &preg, float dfreg, float xreg) {
+            const int ii = grp + p * kGroups;
+            if (ii >= nown || x >= 3) return;
+            const int i = a0 + ii;
             const int sp = species[i];
-            const float4 F = sF[i - a0];
-            const float3 xi = normals3(cf.seed, n, (uint32_t)i, 0u);
-            const double sg = cf.sig[sp];
-#pragma unroll
-            for (int x = 0; x < 3; ++x) {
-                const size_t o = (size_t)j * D + 3 * i + x;
-                const double pv = (j == 0) ? p_base[3 * i + x] : w_pdraft[o - D];
-                const float fr = x == 0 ? F.x : (x == 1 ? F.y : F.z);
-                const float xx = x == 0 ? xi.x : (x == 1 ? xi.y : xi.z);
-                const float fu = ec_on ? fr + ec_dF[3 * i + x] : fr;
-                const double mu = __dadd_rn(__dmul_rn(cf.c1, pv), __dmul_rn(cf.aF, (double)fu));
-                w_pdraft[o] = __dadd_rn(mu, __dmul_rn(sg, (double)xx));
-                w_Fd[o] = fu;
-                if (ec_on) w_Fraw[o] = fr;
+            const float4 F = sF[ii];
+            const float fr = x == 0 ? F.x : (x == 1 ? F.y : F.z);
+            float xx = xreg;
+            if (!REG) {
+                const float3 xi = normals3(cf.seed, n, (uint32_t)i, 0u);
+                xx = x == 0 ? xi.x : (x == 1 ? xi.y : xi.z);
             }
+            const size_t o = (size_t)j * D + 3 * i + x;
+            const double pv = REG ? preg : ((j == 0) ? p_base[3 * i + x] : w_pdraft[o - D]);
+            const float fu = ec_on ? fr + (REG ? dfreg : ec_dF[3 * i + x]) : fr;
+            const double mu = __dadd_rn(__dmul_rn(cf.c1, pv), __dmul_rn(cf.aF, (double)fu));
+            const double pn = __dadd_rn(mu, __dmul_rn(species_pick(cf.sig, sp), (double)xx));
+            if (REG) preg = pn;
+            w_pdraft[o] = pn;
+            w_Fd[o] = fu;
+            if (ec_on) w_Fraw[o] = fr;
+        };
+        if (REG) {
+#pragma unroll
+            for (int p = 0; p < kP; ++p)
+                if (p < passes) step_d(p, pr[p], dfr[p], xr[p]);
+        } else {
+            double dp;
+            for (int p = 0; p < passes; ++p) step_d(p, dp, 0.f, 0.f);
         }
-        // the next step reads owned atoms' global state (written by this CTA) and
-        // all atoms' positions after the next cluster barrier
+        // the next step reads owned atoms' state (registers, or this CTA's
+        // global writes) and all positions after the next barrier
         __syncthreads();
     }
     if (c == 0 && tid == 0) st->k_eff = keff;
@@ -314,8 +430,8 @@ static size_t draft_smem_bytes(int N, int C, const PotDev &P, bool learned, bool
     const int A = (N + C - 1) / C;
     size_t b = (size_t)A * sizeof(float4) + 2 * kMaxSpecies * kMaxSpecies * sizeof(float);
     if (learned) b += (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) * sizeof(float);
-    if (stage_fix) b += (size_t)N * sizeof(uint4);
-    return b;
+    if (stage_fix) b += 2 * (size_t)N * sizeof(uint4);
+    return b + 4 * sizeof(int);
 }
 
 DraftPlan draft_plan(int N, const PotDev &P, bool learned, int max_cluster, size_t max_smem) {
@@ -323,8 +439,9 @@ DraftPlan draft_plan(int N, const PotDev &P, bool learned, int max_cluster, size
     int C = 1;
     while (C < max_cluster && (N + C - 1) / C > 16) C *= 2;
     pl.cluster = C;
-    pl.stage_fix = (size_t)N * sizeof(uint4) <= 64 * 1024;
+    pl.stage_fix = 2 * (size_t)N * sizeof(uint4) <= 128 * 1024;
     pl.smem = draft_smem_bytes(N, C, P, learned, pl.stage_fix);
+    pl.reg = (N + C - 1) / C <= kRegPasses * kGroups;
     pl.ok = pl.smem <= max_smem;
     return pl;
 }
@@ -332,8 +449,7 @@ DraftPlan draft_plan(int N, const PotDev &P, bool learned, int max_cluster, size
 cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf,
                          const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
                          const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
-                         double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, int *w_flags, float *w_dEdX,
-                         cudaStream_t s) {
+                         double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(pl.cluster, 1, 1);
     cfg.blockDim = dim3(kDraftThreads, 1, 1);
@@ -347,19 +463,21 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const int stage = pl.stage_fix ? 1 : 0;
-    if (learned)
-        return cudaLaunchKernelEx(&cfg, draft_window_cluster_kernel<true>, K, g, P, cf, (const int *)vb.vlist,
-                                  (const int *)vb.vcount, vp.cap, (const uint4 *)vb.fix_base, vp.move2f, stage, species,
-                                  q, p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd, w_Fraw, w_fix, w_flags, w_dEdX);
-    return cudaLaunchKernelEx(&cfg, draft_window_cluster_kernel<false>, K, g, P, cf, (const int *)vb.vlist,
-                              (const int *)vb.vcount, vp.cap, (const uint4 *)vb.fix_base, vp.move2f, stage, species, q,
-                              p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd, w_Fraw, w_fix, w_flags, w_dEdX);
+    const int *vl = vp.all_pairs ? nullptr : (const int *)vb.vlist;
+    const int mi = pl.minimg ? 1 : 0;
+    auto kern = learned ? (pl.reg ? draft_window_cluster_kernel<true, true> : draft_window_cluster_kernel<true, false>)
+                        : (pl.reg ? draft_window_cluster_kernel<false, true> : draft_window_cluster_kernel<false, false>);
+    return cudaLaunchKernelEx(&cfg, kern, K, g, P, cf, vl, (const int *)vb.vcount, vp.cap, (const uint4 *)vb.fix_base,
+                              vp.move2f, stage, mi, species, q, p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd, w_Fraw,
+                              w_fix, w_dEdX);
 }
 
+static const void *draft_kernel_ptrs[4] = {
+    (const void *)draft_window_cluster_kernel<false, false>, (const void *)draft_window_cluster_kernel<false, true>,
+    (const void *)draft_window_cluster_kernel<true, false>, (const void *)draft_window_cluster_kernel<true, true>};
+
 cudaError_t draft_kernels_setup(int max_smem) {
-    const void *ks[2] = {(const void *)draft_window_cluster_kernel<true>,
-                         (const void *)draft_window_cluster_kernel<false>};
-    for (const void *k : ks) {
+    for (const void *k : draft_kernel_ptrs) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -368,7 +486,7 @@ cudaError_t draft_kernels_setup(int max_smem) {
     return cudaSuccess;
 }
 
-int draft_max_cluster(size_t smem) {
+int draft_max_cluster(size_t smem, bool learned) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16, 1, 1);
     cfg.blockDim = dim3(kDraftThreads, 1, 1);
@@ -381,8 +499,8 @@ int draft_max_cluster(size_t smem) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int c = 0;
-    if (cudaOccupancyMaxPotentialClusterSize(&c, (const void *)draft_window_cluster_kernel<false>, &cfg) !=
-        cudaSuccess) {
+    const void *k = draft_kernel_ptrs[learned ? 3 : 1];
+    if (cudaOccupancyMaxPotentialClusterSize(&c, k, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 8;
     }
@@ -400,7 +518,7 @@ __global__ void plain_half_kernel(Geo g, Coef cf, const int *__restrict__ specie
     if (st->step >= st->target_step || i >= g.N) return;
     if (i == 0) st->k_eff = 1;   // one step, always inside the lists' skin
     const int sp = species[i];
-    const double hm = cf.hm[sp];
+    const double hm = species_pick(cf.hm, sp);
     uint32_t u0, u1, u2;
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
@@ -427,9 +545,9 @@ __global__ void plain_finish_kernel(Geo g, Coef cf, const int *__restrict__ spec
             const int o = 3 * i + x;
             const float xx = x == 0 ? xi.x : (x == 1 ? xi.y : xi.z);
             const double mu = __dadd_rn(__dmul_rn(cf.c1, p[o]), __dmul_rn(cf.aF, (double)F[o]));
-            const double pn = __dadd_rn(mu, __dmul_rn(cf.sig[sp], (double)xx));
+            const double pn = __dadd_rn(mu, __dmul_rn(species_pick(cf.sig, sp), (double)xx));
             p[o] = pn;
-            q[o] = __dadd_rn(qmid[o], __dmul_rn(pn, cf.hm[sp]));
+            q[o] = __dadd_rn(qmid[o], __dmul_rn(pn, species_pick(cf.hm, sp)));
         }
     }
     __threadfence();

@@ -28,6 +28,7 @@ struct VerletPlan {
     float rlist2f;      // (max cutoff + skin)^2
     float move2f;       // (0.45 skin)^2: largest allowed displacement^2 from the list's base
     int cap, cap_pow2;  // list capacity per atom and its power-of-two sort width
+    bool all_pairs;     // grid narrower than 3 cells: every atom is a candidate, no lists are built
 };
 struct VerletBufs {
     uint4 *fix_base = nullptr;   // [N] fixed point of the base positions
@@ -82,15 +83,16 @@ struct DraftPlan {
     int cluster;      // CTAs in the draft cluster (one per SM)
     bool stage_fix;   // positions of a step staged in shared memory
     size_t smem;      // dynamic shared memory per CTA
+    bool reg;         // owned atoms' FP64 state in registers
+    bool minimg;      // every draft cutoff below 0.499 of every box side: minimum images only
     bool ok;
 };
 DraftPlan draft_plan(int N, const PotDev &P, bool learned, int max_cluster, size_t max_smem);
-int draft_max_cluster(size_t smem);
+int draft_max_cluster(size_t smem, bool learned);
 cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf,
                          const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
                          const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
-                         double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, int *w_flags, float *w_dEdX,
-                         cudaStream_t s);
+                         double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX, cudaStream_t s);
 cudaError_t draft_kernels_setup(int max_smem);
 void launch_plain_half(const Geo &g, const Coef &cf, const int *species, const double *q, const double *p,
                        DevState *st, double *qmid, uint4 *fix, cudaStream_t s);

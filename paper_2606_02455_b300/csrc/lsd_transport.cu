@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kTransThreads)
     double s = 0.0, d = 0.0;
     for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
         const float3 xi = normals3(cf.seed, n, (uint32_t)i, 0u);
-        const double k = cf.aF_sig[species[i]];
+        const double k = species_pick(cf.aF_sig, species[i]);
         const size_t o = ((size_t)j * N + i) * 3;
         const double d0 = k * ((double)Fd[o + 0] - (double)Ft[o + 0]);
         const double d1 = k * ((double)Fd[o + 1] - (double)Ft[o + 1]);
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kTransThreads)
         const int a1 = min(N, a0 + atoms_per_block);
         for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
             const int sp = species[i];
-            const double hm = cf.hm[sp];
+            const double hm = species_pick(cf.hm, sp);
             float3 xi = make_float3(0.f, 0.f, 0.f);
             if (s_rej) xi = normals3(cf.seed, n, (uint32_t)i, 0u);
             const float xs[3] = {xi.x, xi.y, xi.z};
@@ -128,8 +128,8 @@ __global__ void __launch_bounds__(kTransThreads)
                 if (s_rej) {
                     const double pprev = jj == 0 ? p[3 * i + c] : w_pdraft[o - D];
                     const double mu = __dadd_rn(__dmul_rn(cf.c1, pprev), __dmul_rn(cf.aF, (double)Ft[o]));
-                    const double dl = cf.aF_sig[sp] * ((double)Fd[o] - (double)Ft[o]);
-                    pn = mu + cf.sig[sp] * ((double)xs[c] - factor * dl);
+                    const double dl = species_pick(cf.aF_sig, sp) * ((double)Fd[o] - (double)Ft[o]);
+                    pn = mu + species_pick(cf.sig, sp) * ((double)xs[c] - factor * dl);
                 } else {
                     pn = w_pdraft[o];
                 }

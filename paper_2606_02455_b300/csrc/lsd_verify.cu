@@ -11,6 +11,8 @@
 //   force_gather_kernel  F_i = sum_p g_{i,p} - sum_p g_{k_p, rev(p)} + F_LJ,
 //                        rev(p) found by binary search in the sorted list of k_p
 // Everything is a gather in a fixed order: forces are bitwise deterministic.
+#include <cmath>
+
 #include "lsd_common.cuh"
 #include "lsd_kernels.h"
 
@@ -25,7 +27,11 @@ namespace lsd {
 // LIST = false: candidates are all atoms of the window step (any configuration);
 // LIST = true: candidates are the atom's sorted Verlet list, and rows of window
 // steps the draft did not reach (j >= k_eff) are left empty.
-template <bool LIST>
+// MINIMG (the cutoff below 0.499 of every box side): only the minimum image
+// of a candidate can pass the rule (any other image along an axis is at least
+// L/2, less rounding, away), and an atom's own images are beyond the cutoff, so
+// each candidate gives at most one entry, with shift -k per axis.
+template <bool LIST, bool MINIMG>
 __global__ void neigh_build_kernel(const uint4 *__restrict__ fix, const int *__restrict__ vlist,
                                    const int *__restrict__ vcount, int vcap, int M, Geo g, float rmax2f, float near2f,
                                    int cap_near, int cap_far, int *__restrict__ near_keys, int *__restrict__ far_keys,
@@ -49,7 +55,34 @@ __global__ void neigh_build_kernel(const uint4 *__restrict__ fix, const int *__r
     const int *cand = LIST ? vlist + (size_t)i * vcap : nullptr;
     const int ncand = LIST ? vcount[i] : N;
     int cn = 0, cf = 0;
-    for (int base = 0; base < ncand; base += 32) {
+    if (MINIMG) {
+        const unsigned below = (1u << lane) - 1u;
+        for (int base = 0; base < ncand; base += 32) {
+            const int t = base + lane;
+            const int k = LIST ? (t < ncand ? cand[t] : N) : t;
+            bool in_n = false, in_f = false;
+            int key = 0;
+            if (k < N && k != i) {
+                const uint4 fkk = fj[k];
+                float dx, dy, dz;
+                int kx, ky, kz;
+                axis_min(fi.x, fkk.x, g.scale_f[0], dx, kx);
+                axis_min(fi.y, fkk.y, g.scale_f[1], dy, ky);
+                axis_min(fi.z, fkk.z, g.scale_f[2], dz, kz);
+                const float d2 = dist2_rule(dx, dy, dz);
+                in_n = d2 < rmax2f && d2 < near2f;
+                in_f = d2 < rmax2f && !(d2 < near2f);
+                key = (k << 5) | shift_code(-kx, -ky, -kz);
+            }
+            const unsigned bn = __ballot_sync(0xffffffffu, in_n), bf = __ballot_sync(0xffffffffu, in_f);
+            const int wn = cn + __popc(bn & below), wf = cf + __popc(bf & below);
+            if (in_n && wn < cap_near) nk[wn] = key;
+            if (in_f && wf < cap_far) fk[wf] = key;
+            cn += __popc(bn);
+            cf += __popc(bf);
+        }
+    }
+    for (int base = 0; base < (MINIMG ? 0 : ncand); base += 32) {
         const int t = base + lane;
         const int k = LIST ? (t < ncand ? cand[t] : N) : t;
         unsigned mn = 0u, mf = 0u;
@@ -421,12 +454,19 @@ void launch_fixpoint(const double *q, const int *species, int M, const Geo &g, u
     fixpoint_kernel<<<(M + 255) / 256, 256, 0, s>>>(q, species, M, g, fix);
 }
 
+// rc < 0.499 min(L): the minimum-image form of the rule applies
+static bool min_image_only(const Geo &g, float rmax2f) {
+    const float lmin = fminf(g.Lf[0], fminf(g.Lf[1], g.Lf[2]));
+    return std::sqrt((double)rmax2f) < 0.499 * (double)lmin;
+}
+
 void launch_neigh_build(const uint4 *fix, int M, const Geo &g, float rmax2f, float near2f, int cap_near, int cap_far,
                         int *near_keys, int *far_keys, int *n_near, int *n_far, DevState *st, cudaStream_t s) {
     const int threads = 256;
     const int blocks = (int)(((size_t)M * 32 + threads - 1) / threads);
-    neigh_build_kernel<false><<<blocks, threads, 0, s>>>(fix, nullptr, nullptr, 0, M, g, rmax2f, near2f, cap_near,
-                                                         cap_far, near_keys, far_keys, n_near, n_far, st);
+    auto k = min_image_only(g, rmax2f) ? neigh_build_kernel<false, true> : neigh_build_kernel<false, false>;
+    k<<<blocks, threads, 0, s>>>(fix, nullptr, nullptr, 0, M, g, rmax2f, near2f, cap_near, cap_far, near_keys,
+                                 far_keys, n_near, n_far, st);
 }
 
 void launch_neigh_list(const uint4 *fix, const int *vlist, const int *vcount, int vcap, int M, const Geo &g,
@@ -434,8 +474,9 @@ void launch_neigh_list(const uint4 *fix, const int *vlist, const int *vcount, in
                        int *n_near, int *n_far, DevState *st, cudaStream_t s) {
     const int threads = 256;
     const int blocks = (int)(((size_t)M * 32 + threads - 1) / threads);
-    neigh_build_kernel<true><<<blocks, threads, 0, s>>>(fix, vlist, vcount, vcap, M, g, rmax2f, near2f, cap_near,
-                                                        cap_far, near_keys, far_keys, n_near, n_far, st);
+    auto k = min_image_only(g, rmax2f) ? neigh_build_kernel<true, true> : neigh_build_kernel<true, false>;
+    k<<<blocks, threads, 0, s>>>(fix, vlist, vcount, vcap, M, g, rmax2f, near2f, cap_near, cap_far, near_keys,
+                                 far_keys, n_near, n_far, st);
 }
 
 size_t desc_smem_bytes(int warps, int cap) { return (size_t)warps * kStageFloats * cap * sizeof(float); }

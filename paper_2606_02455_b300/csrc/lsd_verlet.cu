@@ -135,8 +135,8 @@ __global__ void verlet_list_kernel(const uint4 *__restrict__ fix_base, const int
     const int n = cnt < cap ? cnt : cap;
     for (int p = n + lane; p < cap_pow2; p += 32) buf[p] = 0x7fffffff;
     __syncwarp();
-    // bitonic sort of cap_pow2 entries by atom index
-    for (int k2 = 2; k2 <= cap_pow2; k2 <<= 1) {
+    // bitonic sort of cap_pow2 entries by atom index (a single-cell scan is already in index order)
+    for (int k2 = 2; k2 <= (one_cell ? 1 : cap_pow2); k2 <<= 1) {
         for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
             for (int a = lane; a < cap_pow2; a += 32) {
                 const int b = a ^ j2;
