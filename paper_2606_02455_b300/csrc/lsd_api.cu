@@ -46,6 +46,9 @@ struct PotHost {
     bool present = false;
     void *tc_plan = nullptr;              // tensor maps of the BF16 weights (tensor-core MLP)
     __nv_bfloat16 *tc_scratch = nullptr;  // per-CTA SiLU' slots of the tensor-core MLP
+    size_t n_dbuf = 0;                    // floats in dbuf
+    float *dbuf_tf = nullptr;             // TF32 hi parts of the FP32 layouts, then the lo parts
+    void *tf_plan = nullptr;              // tensor maps of those (FP32 MLP on the tensor cores)
 };
 
 }  // namespace
@@ -149,7 +152,7 @@ int pot_setup(lsd_handle *h, PotHost &ph, const lsd_potential *lp, bool is_draft
     P.head = lp->head;
     P.head_scale = (float)lp->head_scale;
     if (lp->kind < LSD_POT_LJ || lp->kind > LSD_POT_LEARNED) return LSD_EINVAL;
-    if (lp->precision < LSD_FP32 || lp->precision > LSD_FP8) return LSD_EINVAL;
+    if (lp->precision < LSD_FP32 || lp->precision > LSD_FP32_CUDA_CORES) return LSD_EINVAL;
     P.has_lj = lp->lj_cutoff > 0.0;
     P.has_mlp = lp->kind != LSD_POT_LJ && lp->n_layers > 0;
     if (P.has_lj) {
@@ -206,8 +209,10 @@ int pot_setup(lsd_handle *h, PotHost &ph, const lsd_potential *lp, bool is_draft
         }
         const size_t offwo = total;
         total += W;
+        ph.n_dbuf = total;
         TRY(dalloc(h, &ph.dbuf, total));
         TRY(dalloc(h, &ph.dbuf_bf, total));
+        if (lp->precision == LSD_FP32) TRY(dalloc(h, &ph.dbuf_tf, 2 * total));
         for (int l = 0; l < L; ++l) {
             P.Wt[l] = ph.dbuf + offWt[l];
             P.Wn[l] = ph.dbuf + offWn[l];
@@ -262,6 +267,25 @@ int pot_upload(lsd_handle *h, PotHost &ph) {
     for (size_t k = 0; k < total; ++k) bb[k] = __float2bfloat16(buf[k]);
     CK(cudaMemcpyAsync(ph.dbuf, buf.data(), total * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(ph.dbuf_bf, bb.data(), total * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, h->stream));
+    std::vector<float> tf;
+    if (ph.dbuf_tf) {
+        // TF32 split, round to nearest with ties away from zero on the magnitude
+        // (the low 13 of 23 fraction bits dropped): hi = tf32(w), lo = tf32(w - hi)
+        auto tf32 = [](float x) {
+            uint32_t u;
+            std::memcpy(&u, &x, 4);
+            if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+            float r;
+            std::memcpy(&r, &u, 4);
+            return r;
+        };
+        tf.resize(2 * total);
+        for (size_t k = 0; k < total; ++k) {
+            tf[k] = tf32(buf[k]);
+            tf[total + k] = tf32(buf[k] - tf[k]);
+        }
+        CK(cudaMemcpyAsync(ph.dbuf_tf, tf.data(), 2 * total * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    }
     CK(cudaStreamSynchronize(h->stream));
     return LSD_OK;
 }
@@ -306,6 +330,8 @@ void enqueue_mlp(lsd_handle *h, const PotHost &pot, int M, cudaStream_t s) {
     const PotDev &P = pot.dev;
     if (pot.tc_plan)
         launch_mlp_tc(pot.tc_plan, h->X, M, P, h->E_mlp, h->dEdX, pot.tc_scratch, h->n_sm, &h->st->err, s);
+    else if (pot.tf_plan)
+        launch_mlp_tf32(pot.tf_plan, h->X, M, P, h->E_mlp, h->dEdX, h->n_sm, &h->st->err, s);
     else
         launch_mlp_fp32(h->X, M, P, h->E_mlp, h->dEdX, s);
 }
@@ -447,6 +473,8 @@ void lsd_destroy(lsd_handle *h) {
     for (void *v : h->allocs) cudaFree(v);
     if (h->draft.tc_plan) mlp_tc_plan_free(h->draft.tc_plan);
     if (h->target.tc_plan) mlp_tc_plan_free(h->target.tc_plan);
+    if (h->draft.tf_plan) mlp_tf32_plan_free(h->draft.tf_plan);
+    if (h->target.tf_plan) mlp_tf32_plan_free(h->target.tf_plan);
     train_free(h->train);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
@@ -524,7 +552,8 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     h->cap_far = std::min(nb_capacity(rho, rfar, 32), (27 * h->N + 31) / 32 * 32);
     if (desc_smem_bytes(8, h->cap_near) + 8 * 256 * sizeof(float) > (size_t)kMaxDynSmem) return fail(LSD_EUNSUPPORTED);
     if (verify_kernels_setup(kMaxDynSmem) != cudaSuccess || mlp_kernels_setup(kMaxDynSmem) != cudaSuccess ||
-        mlp_tc_setup() != cudaSuccess || draft_kernels_setup(kMaxDynSmem) != cudaSuccess ||
+        mlp_tc_setup() != cudaSuccess || mlp_tf32_setup() != cudaSuccess ||
+        draft_kernels_setup(kMaxDynSmem) != cudaSuccess ||
         verlet_setup(kMaxDynSmem) != cudaSuccess)
         return fail(LSD_ECUDA);
     {
@@ -584,6 +613,20 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
             if (!ph->tc_plan) return fail(LSD_ECUDA);
             const int grid = mlp_tc_grid(h->K * h->N, h->n_sm);
             if ((rc = dalloc(h, &ph->tc_scratch, mlp_tc_scratch_elems(ph->dev, grid))) != LSD_OK) return fail(rc);
+        }
+        // FP32 potentials: three TF32 products per term on the tensor cores
+        if (ph->dev.has_mlp && ph->dev.precision == LSD_FP32 && ph->dbuf_tf && mlp_tf32_supported(ph->dev)) {
+            const PotDev &P = ph->dev;
+            const size_t n_all = ph->n_dbuf;   // the lo parts follow the hi parts; offsets as in dbuf
+            Tf32Weights w{};
+            for (int l = 0; l < P.n_layers; ++l) {
+                w.wn_hi[l] = ph->dbuf_tf + (P.Wn[l] - ph->dbuf);
+                w.wn_lo[l] = ph->dbuf_tf + n_all + (P.Wn[l] - ph->dbuf);
+                w.wt_hi[l] = ph->dbuf_tf + (P.Wt[l] - ph->dbuf);
+                w.wt_lo[l] = ph->dbuf_tf + n_all + (P.Wt[l] - ph->dbuf);
+            }
+            ph->tf_plan = mlp_tf32_plan(P, w);
+            if (!ph->tf_plan) return fail(LSD_ECUDA);
         }
     }
     if (cudaMemcpy(h->q, sys->pos, D * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||

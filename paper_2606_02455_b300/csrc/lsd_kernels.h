@@ -62,6 +62,18 @@ int mlp_tc_grid(int M, int n_sm);
 void launch_mlp_tc(const void *plan, const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX,
                    __nv_bfloat16 *scratch, int n_sm, int *err, cudaStream_t s);
 cudaError_t mlp_tc_setup();
+// FP32 potentials: three TF32 products per term (lsd_mlp_tc.cu)
+struct Tf32Weights {
+    const float *wn_hi[kMaxLayers], *wn_lo[kMaxLayers];   // W_l   [W][din_p], TF32 hi / lo parts
+    const float *wt_hi[kMaxLayers], *wt_lo[kMaxLayers];   // W_l^T [din_p][W]
+};
+bool mlp_tf32_supported(const PotDev &P);
+size_t mlp_tf32_smem_bytes();
+void *mlp_tf32_plan(const PotDev &P, const Tf32Weights &w);
+void mlp_tf32_plan_free(void *plan);
+void launch_mlp_tf32(const void *plan, const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX, int n_sm,
+                     int *err, cudaStream_t s);
+cudaError_t mlp_tf32_setup();
 size_t mlp_tc_static_scratch_bytes();
 int mlp_tc_static_launch(const void *plan, const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX,
                          int n_sm, int *err, cudaStream_t s);
