@@ -132,9 +132,8 @@ __device__ __forceinline__ double uniform53(uint64_t seed, uint64_t n) {
 // Fixed-point positions and the membership rule
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t fixpoint(double q, double scale) {
-    const double t = __dmul_rn(q, scale);
-    const double f = floor(t);
-    const long long fi = __double2ll_rz(f);
+    // floor(fl64(q * scale)) as one round-toward-minus-infinity conversion
+    const long long fi = __double2ll_rd(__dmul_rn(q, scale));
     return (uint32_t)(unsigned long long)fi;
 }
 
@@ -143,6 +142,15 @@ __device__ __forceinline__ uint32_t fixpoint(double q, double scale) {
 // memory.
 __device__ __forceinline__ double species_pick(const double (&a)[kMaxSpecies], int s) {
     return s == 0 ? a[0] : (s == 1 ? a[1] : (s == 2 ? a[2] : a[3]));
+}
+
+// Layer l's bias pointer by selection (a dynamic index into the by-value
+// PotDev would copy it to local memory).
+__device__ __forceinline__ const float *layer_bias(const PotDev &P, int l) {
+    const float *b = P.b[0];
+#pragma unroll
+    for (int k = 1; k < kMaxLayers; ++k) b = l == k ? P.b[k] : b;
+    return b;
 }
 
 __device__ __forceinline__ float dist2_rule(float dx, float dy, float dz) {
@@ -235,6 +243,15 @@ __device__ __forceinline__ float siluf_(float h) { return h * sigmoidf_(h); }
 __device__ __forceinline__ float dsiluf_(float h) {
     const float s = sigmoidf_(h);
     return s * (1.0f + h * (1.0f - s));
+}
+// SiLU and its derivative from one exponential and one reciprocal (hardware
+// approximations, a few ulp): the tensor-core epilogues, where they are the
+// bulk of the per-element work.  h is clamped at -80 so exp(-h) stays finite.
+__device__ __forceinline__ void silu_dsilu_fast(float h, float &a, float &d) {
+    const float e = __expf(-fmaxf(h, -80.f));
+    const float s = __frcp_rn(1.0f + e);
+    a = h * s;
+    d = s * (1.0f + h * (1.0f - s));
 }
 __device__ __forceinline__ float d2siluf_(float h) {
     const float s = sigmoidf_(h);

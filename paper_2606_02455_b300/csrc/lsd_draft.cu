@@ -196,7 +196,8 @@ template <bool LEARNED, bool REG>
 __global__ void __launch_bounds__(kDraftThreads, 1)
     draft_window_cluster_kernel(int K, Geo g, PotDev P, Coef cf, const int *__restrict__ vlist,
                                 const int *__restrict__ vcount, int vcap, const uint4 *__restrict__ fix_base,
-                                float move2f, int stage_fix, int minimg, const int *__restrict__ species,
+                                float move2f, int stage_fix, int minimg, int noise_smem,
+                                const int *__restrict__ species,
                                 const double *__restrict__ q_base, const double *__restrict__ p_base,
                                 const float *__restrict__ ec_dF, int ec_on, DevState *__restrict__ st,
                                 double *__restrict__ w_qmid, double *__restrict__ w_pdraft, float *__restrict__ w_Fd,
@@ -212,6 +213,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     float *sstage = slj + 2 * kMaxSpecies * kMaxSpecies;        // learned: per warp 3*cap + d0p
     uint4 *sfix = (uint4 *)(sstage + (LEARNED ? (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) : 0));  // [2][N]
     int *sflag = (int *)(sfix + (stage_fix ? 2 * (size_t)N : 0));                                        // [2]
+    float *snoise = (float *)(sflag + 4);   // [K][A][3] when noise_smem: the window's xi, drawn up front
     if (st->step >= st->target_step) return;   // uniform over the cluster
     const long long n0 = st->step;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -240,6 +242,17 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
             qr[p] = q_base[3 * i + x];
             pr[p] = p_base[3 * i + x];
             dfr[p] = ec_on ? ec_dF[3 * i + x] : 0.f;
+        }
+    }
+    // the noise of every step of the window, when it fits: off the per-step critical path
+    if (noise_smem) {
+        for (int idx = tid; idx < K * nown; idx += blockDim.x) {
+            const int j = idx / nown, ii = idx - j * nown;
+            const float3 xi = normals3(cf.seed, (unsigned long long)(n0 + j + 1), (uint32_t)(a0 + ii), 0u);
+            float *o = snoise + ((size_t)j * A + ii) * 3;
+            o[0] = xi.x;
+            o[1] = xi.y;
+            o[2] = xi.z;
         }
     }
     // every CTA has started and zeroed its flags before the first remote store
@@ -310,7 +323,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
             if (moved && tid < C) st_cluster(sflag + par, (uint32_t)tid, 1);
         }
         // noise of this step's B, independent of the positions: drawn while the barrier completes
-        if (REG) {
+        if (REG && !noise_smem) {
 #pragma unroll
             for (int p = 0; p < kP; ++p) {
                 const int ii = grp + p * kGroups;
@@ -345,7 +358,40 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
             const int *lst = use_list ? vlist + (size_t)i * vcap : nullptr;
             const int nl = use_list ? vcount[i] : N;
             float fxx = 0.f, fyy = 0.f, fzz = 0.f;
-            for (int t = lane; t < nl; t += 32) {
+            if (!LEARNED && minimg) {
+                // pair-only draft, minimum images: four independent candidates per
+                // lane in flight (loads first, then arithmetic), LJ by predication
+                for (int t0 = lane; t0 < nl; t0 += 128) {
+                    uint4 fk[4];
+                    int kk[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int t = t0 + 32 * u;
+                        kk[u] = t < nl ? (use_list ? __ldg(lst + t) : t) : i;
+                        fk[u] = fx[kk[u]];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        float dx, dy, dz;
+                        int kx;
+                        axis_min(fi.x, fk[u].x, g.scale_f[0], dx, kx);
+                        axis_min(fi.y, fk[u].y, g.scale_f[1], dy, kx);
+                        axis_min(fi.z, fk[u].z, g.scale_f[2], dz, kx);
+                        const float d2 = dist2_rule(dx, dy, dz);
+                        const bool in = kk[u] != i && d2 < P.lj_rc2f;
+                        const int pr2 = si * g.S + (int)fk[u].w;
+                        const float sig2 = slj[pr2], eps24 = slj[kMaxSpecies * kMaxSpecies + pr2];
+                        const float inv = __fdividef(1.f, in ? d2 : 1.f);
+                        const float s2 = sig2 * inv;
+                        const float s6 = s2 * s2 * s2, s12 = s6 * s6;
+                        const float fr = in ? -eps24 * (2.f * s12 - s6) * inv : 0.f;
+                        fxx += fr * dx;
+                        fyy += fr * dy;
+                        fzz += fr * dz;
+                    }
+                }
+            }
+            for (int t = lane; t < ((!LEARNED && minimg) ? 0 : nl); t += 32) {
                 const int k = use_list ? __ldg(lst + t) : t;
                 if (k == i) continue;
                 const uint4 fk = fx[k];
@@ -397,7 +443,9 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
             const float4 F = sF[ii];
             const float fr = x == 0 ? F.x : (x == 1 ? F.y : F.z);
             float xx = xreg;
-            if (!REG) {
+            if (noise_smem) {
+                xx = snoise[((size_t)j * A + ii) * 3 + x];
+            } else if (!REG) {
                 const float3 xi = normals3(cf.seed, n, (uint32_t)i, 0u);
                 xx = x == 0 ? xi.x : (x == 1 ? xi.y : xi.z);
             }
@@ -419,28 +467,33 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
             double dp;
             for (int p = 0; p < passes; ++p) step_d(p, dp, 0.f, 0.f);
         }
-        // the next step reads owned atoms' state (registers, or this CTA's
-        // global writes) and all positions after the next barrier
-        __syncthreads();
+        // the next step reads owned atoms' state from this thread's registers or
+        // its own global writes, and sF is rewritten only after the next cluster
+        // barrier: no CTA barrier is needed here
     }
     if (c == 0 && tid == 0) st->k_eff = keff;
 }
 
-static size_t draft_smem_bytes(int N, int C, const PotDev &P, bool learned, bool stage_fix) {
+static size_t draft_smem_bytes(int N, int C, const PotDev &P, bool learned, bool stage_fix, int noise_K) {
     const int A = (N + C - 1) / C;
     size_t b = (size_t)A * sizeof(float4) + 2 * kMaxSpecies * kMaxSpecies * sizeof(float);
     if (learned) b += (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) * sizeof(float);
     if (stage_fix) b += 2 * (size_t)N * sizeof(uint4);
-    return b + 4 * sizeof(int);
+    return b + 4 * sizeof(int) + (size_t)noise_K * A * 3 * sizeof(float);
 }
 
-DraftPlan draft_plan(int N, const PotDev &P, bool learned, int max_cluster, size_t max_smem) {
+constexpr size_t kNoiseSmemMax = 32 * 1024;   // the window's noise is staged up front when it fits
+
+DraftPlan draft_plan(int N, int K, const PotDev &P, bool learned, int max_cluster, size_t max_smem) {
     DraftPlan pl{};
     int C = 1;
     while (C < max_cluster && (N + C - 1) / C > 16) C *= 2;
     pl.cluster = C;
     pl.stage_fix = 2 * (size_t)N * sizeof(uint4) <= 128 * 1024;
-    pl.smem = draft_smem_bytes(N, C, P, learned, pl.stage_fix);
+    const size_t noise = (size_t)K * ((N + C - 1) / C) * 3 * sizeof(float);
+    pl.noise_smem = noise <= kNoiseSmemMax;
+    pl.K = K;
+    pl.smem = draft_smem_bytes(N, C, P, learned, pl.stage_fix, pl.noise_smem ? K : 0);
     pl.reg = (N + C - 1) / C <= kRegPasses * kGroups;
     pl.ok = pl.smem <= max_smem;
     return pl;
@@ -465,11 +518,12 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
     const int stage = pl.stage_fix ? 1 : 0;
     const int *vl = vp.all_pairs ? nullptr : (const int *)vb.vlist;
     const int mi = pl.minimg ? 1 : 0;
+    const int ns = (pl.noise_smem && K <= pl.K) ? 1 : 0;
     auto kern = learned ? (pl.reg ? draft_window_cluster_kernel<true, true> : draft_window_cluster_kernel<true, false>)
                         : (pl.reg ? draft_window_cluster_kernel<false, true> : draft_window_cluster_kernel<false, false>);
     return cudaLaunchKernelEx(&cfg, kern, K, g, P, cf, vl, (const int *)vb.vcount, vp.cap, (const uint4 *)vb.fix_base,
-                              vp.move2f, stage, mi, species, q, p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd, w_Fraw,
-                              w_fix, w_dEdX);
+                              vp.move2f, stage, mi, ns, species, q, p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd,
+                              w_Fraw, w_fix, w_dEdX);
 }
 
 static const void *draft_kernel_ptrs[4] = {

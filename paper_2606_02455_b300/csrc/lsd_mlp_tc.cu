@@ -37,11 +37,14 @@ constexpr int kStageBytes = 256 * 128;            // one B chunk: up to 256 rows
 
 struct TcSmem {
     uint32_t a;          // A operand panels
-    uint32_t b[2];       // B stages
-    uint32_t full[2];    // TMA landed
-    uint32_t empty[2];   // MMAs done with the stage
+    uint32_t b0;         // B stage s at b0 + s kStageBytes
+    uint32_t full0;      // TMA landed (stage s at full0 + 8 s)
+    uint32_t empty0;     // MMAs done with the stage (empty0 + 8 s)
     uint32_t done;       // all MMAs of a GEMM done
     uint32_t tslot;      // TMEM base address
+    __device__ __forceinline__ uint32_t b(int s) const { return b0 + (uint32_t)s * kStageBytes; }
+    __device__ __forceinline__ uint32_t full(int s) const { return full0 + 8u * (uint32_t)s; }
+    __device__ __forceinline__ uint32_t empty(int s) const { return empty0 + 8u * (uint32_t)s; }
 };
 
 // One GEMM: thread 0 streams the K-chunks of B by TMA and issues the MMAs;
@@ -57,10 +60,10 @@ __device__ __forceinline__ bool tc_gemm(const TcSmem &S, const CUtensorMap *map,
         const uint32_t bytes = (uint32_t)N * 128u;
         auto issue = [&](uint32_t c, int kc) {
             const int s = c & 1;
-            if (c >= 2 && ok) ok = tc::mbar_wait(S.empty[s], ((c >> 1) - 1) & 1);
+            if (c >= 2 && ok) ok = tc::mbar_wait(S.empty(s), ((c >> 1) - 1) & 1);
             if (!ok) return;
-            tc::mbar_expect_tx(S.full[s], bytes);
-            tc::tma_load_2d(S.b[s], map, kc * kPanelElems, 0, S.full[s]);
+            tc::mbar_expect_tx(S.full(s), bytes);
+            tc::tma_load_2d(S.b(s), map, kc * kPanelElems, 0, S.full(s));
         };
         const uint32_t c0 = chunk;
         issue(c0, 0);
@@ -68,15 +71,15 @@ __device__ __forceinline__ bool tc_gemm(const TcSmem &S, const CUtensorMap *map,
             const uint32_t c = c0 + kc;
             if (kc + 1 < nk) issue(c + 1, kc + 1);
             const int s = c & 1;
-            if (!tc::mbar_wait(S.full[s], (c >> 1) & 1)) { ok = false; break; }
+            if (!tc::mbar_wait(S.full(s), (c >> 1) & 1)) { ok = false; break; }
             tc::fence_after_sync();
             const int kend = min(kPanelElems, K - kc * kPanelElems);
             for (int k16 = 0; k16 < kend; k16 += 16) {
                 const uint64_t ad = tc::sdesc_sw128(S.a + kc * kPanelBytes + k16 * 2);
-                const uint64_t bd = tc::sdesc_sw128(S.b[s] + k16 * 2);
+                const uint64_t bd = tc::sdesc_sw128(S.b(s) + k16 * 2);
                 tc::mma_f16(tmem, ad, bd, idesc, (kc | k16) != 0);
             }
-            tc::mma_commit(S.empty[s]);
+            tc::mma_commit(S.empty(s));
         }
         tc::mma_commit(S.done);
     }
@@ -120,23 +123,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t base = (tc::smem_u32(smraw) + 1023u) & ~1023u;
     TcSmem S;
     S.a = base;
-    S.b[0] = base + kMaxPanels * kPanelBytes;
-    S.b[1] = S.b[0] + kStageBytes;
-    const uint32_t bars = S.b[1] + kStageBytes;
-    S.full[0] = bars;
-    S.full[1] = bars + 8;
-    S.empty[0] = bars + 16;
-    S.empty[1] = bars + 24;
+    S.b0 = base + kMaxPanels * kPanelBytes;
+    const uint32_t bars = S.b0 + 2 * kStageBytes;
+    S.full0 = bars;
+    S.empty0 = bars + 16;
     S.done = bars + 32;
     S.tslot = bars + 40;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int W = P.width, L = P.n_layers, d0p = P.d0p;
     const uint32_t ncols = 256;
     if (tid == 0) {
-        tc::mbar_init(S.full[0], 1);
-        tc::mbar_init(S.full[1], 1);
-        tc::mbar_init(S.empty[0], 1);
-        tc::mbar_init(S.empty[1], 1);
+        tc::mbar_init(S.full(0), 1);
+        tc::mbar_init(S.full(1), 1);
+        tc::mbar_init(S.empty(0), 1);
+        tc::mbar_init(S.empty(1), 1);
         tc::mbar_init(S.done, 1);
         tc::mbar_fence_init();
     }
@@ -359,11 +359,17 @@ constexpr int kTfEpiWarps = 16;
 constexpr int kTfEpiThreads = kTfEpiWarps * 32;
 constexpr int kTfThreads = kTfEpiThreads + 32;     // + the TMA producer warp
 
+// Shared-memory addresses; per-stage ones are computed, not stored in arrays
+// (a runtime-indexed array would live in local memory).
 struct TfSmem {
     uint32_t ahi, alo;     // A operand panels
-    uint32_t bhi[kTfStages], blo[kTfStages];
-    uint32_t full[kTfStages], empty[kTfStages], done, tslot;
+    uint32_t b0;           // stage s: hi chunk at b0 + 2 s C, lo chunk C after it
+    uint32_t full0, empty0, done, tslot;
     float *ypart;          // [3][128] partial head sums of column blocks 1..3
+    __device__ __forceinline__ uint32_t bhi(int s) const { return b0 + (uint32_t)s * 2u * kTfChunkBytes; }
+    __device__ __forceinline__ uint32_t blo(int s) const { return bhi(s) + kTfChunkBytes; }
+    __device__ __forceinline__ uint32_t full(int s) const { return full0 + 8u * (uint32_t)s; }
+    __device__ __forceinline__ uint32_t empty(int s) const { return empty0 + 8u * (uint32_t)s; }
 };
 
 // barrier 1: the epilogue warps only (the producer warp runs on its own)
@@ -390,18 +396,18 @@ __device__ __forceinline__ bool tf_mma(const TfSmem &S, int K, int N, uint32_t t
         for (int kc = 0; kc < nk; ++kc) {
             const uint32_t c = chunk + kc;
             const int s = c % kTfStages;
-            if (!tc::mbar_wait(S.full[s], (c / kTfStages) & 1)) { ok = false; break; }
+            if (!tc::mbar_wait(S.full(s), (c / kTfStages) & 1)) { ok = false; break; }
             tc::fence_after_sync();
             const int kend = min(kTfPanelElems, K - kc * kTfPanelElems);
             for (int k8 = 0; k8 < kend; k8 += 8) {
                 const uint32_t ao = kc * kPanelBytes + k8 * 4;
                 const uint64_t ahd = tc::sdesc_sw128(S.ahi + ao), ald = tc::sdesc_sw128(S.alo + ao);
-                const uint64_t bhd = tc::sdesc_sw128(S.bhi[s] + k8 * 4), bld = tc::sdesc_sw128(S.blo[s] + k8 * 4);
+                const uint64_t bhd = tc::sdesc_sw128(S.bhi(s) + k8 * 4), bld = tc::sdesc_sw128(S.blo(s) + k8 * 4);
                 tc::mma_tf32(tmem, ald, bhd, idesc, (kc | k8) != 0);
                 tc::mma_tf32(tmem, ahd, bld, idesc, 1u);
                 tc::mma_tf32(tmem, ahd, bhd, idesc, 1u);
             }
-            tc::mma_commit(S.empty[s]);
+            tc::mma_commit(S.empty(s));
         }
         if (ok) tc::mma_commit(S.done);
     }
@@ -418,16 +424,19 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
     return r;
 }
 
-// Writes the hi and lo TF32 parts of 32 consecutive FP32 columns [c0, c0+32)
-// of row r (one full swizzled row of panel c0/32).
-__device__ __forceinline__ void store_split_row32(uint32_t ahi, uint32_t alo, int r, int c0, const float (&v)[32]) {
-    const int panel = c0 / kTfPanelElems;
+// Writes the hi and lo TF32 parts of NC (16 or 32) consecutive FP32 columns
+// [c0, c0 + NC) of row r; c0 is a multiple of 16 (half or all of the
+// swizzled row of panel c0 / 32).
+template <int NC>
+__device__ __forceinline__ void store_split_row(uint32_t ahi, uint32_t alo, int r, int c0, const float (&v)[NC]) {
+    const int panel = c0 / kTfPanelElems, q0 = (c0 % kTfPanelElems) / 4;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int qq = 0; qq < NC / 4; ++qq) {
+        const int q = q0 + qq;
         uint32_t h[4], l[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const float x = v[4 * q + e];
+            const float x = v[4 * qq + e];
             h[e] = tf32_rna(x);
             l[e] = tf32_rna(x - __uint_as_float(h[e]));
         }
@@ -458,13 +467,13 @@ __device__ void tf_producer(const TfSmem &S, const TfMaps &maps, int M, const Po
         const int nk = (K + kTfPanelElems - 1) / kTfPanelElems;
         for (int kc = 0; kc < nk && ok; ++kc, ++c) {
             const int s = c % kTfStages;
-            if (c >= (uint32_t)kTfStages && !tc::mbar_wait(S.empty[s], ((c / kTfStages) - 1) & 1)) {
+            if (c >= (uint32_t)kTfStages && !tc::mbar_wait(S.empty(s), ((c / kTfStages) - 1) & 1)) {
                 ok = false;
                 break;
             }
-            tc::mbar_expect_tx(S.full[s], 2u * (uint32_t)N * 128u);
-            tc::tma_load_2d(S.bhi[s], mhi, kc * kTfPanelElems, 0, S.full[s]);
-            tc::tma_load_2d(S.blo[s], mlo, kc * kTfPanelElems, 0, S.full[s]);
+            tc::mbar_expect_tx(S.full(s), 2u * (uint32_t)N * 128u);
+            tc::tma_load_2d(S.bhi(s), mhi, kc * kTfPanelElems, 0, S.full(s));
+            tc::tma_load_2d(S.blo(s), mlo, kc * kTfPanelElems, 0, S.full(s));
         }
     };
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
@@ -474,7 +483,7 @@ __device__ void tf_producer(const TfSmem &S, const TfMaps &maps, int M, const Po
     // the copies of the last (up to kTfStages) chunks issued
     const uint32_t first = c > (uint32_t)kTfStages ? c - kTfStages : 0u;
     for (uint32_t k = first; k < c; ++k)
-        if (!tc::mbar_wait(S.full[k % kTfStages], (k / kTfStages) & 1)) ok = false;
+        if (!tc::mbar_wait(S.full(k % kTfStages), (k / kTfStages) & 1)) ok = false;
     if (!ok) atomicOr(err, 8);
 }
 
@@ -486,16 +495,10 @@ __global__ void __launch_bounds__(kTfThreads, 1)
     TfSmem S;
     S.ahi = base;
     S.alo = S.ahi + kTfMaxPanels * kPanelBytes;
-    uint32_t at = S.alo + kTfMaxPanels * kPanelBytes;
-    for (int st = 0; st < kTfStages; ++st) {
-        S.bhi[st] = at;
-        S.blo[st] = at + kTfChunkBytes;
-        at += 2 * kTfChunkBytes;
-    }
-    for (int st = 0; st < kTfStages; ++st) {
-        S.full[st] = at + 8 * st;
-        S.empty[st] = at + 8 * (kTfStages + st);
-    }
+    S.b0 = S.alo + kTfMaxPanels * kPanelBytes;
+    const uint32_t at = S.b0 + 2 * kTfStages * kTfChunkBytes;
+    S.full0 = at;
+    S.empty0 = at + 8 * kTfStages;
     S.done = at + 16 * kTfStages;
     S.tslot = S.done + 8;
     S.ypart = reinterpret_cast<float *>(smraw + (S.tslot + 8 - tc::smem_u32(smraw)));
@@ -503,8 +506,8 @@ __global__ void __launch_bounds__(kTfThreads, 1)
     const int W = P.width, L = P.n_layers, d0p = P.d0p;
     if (tid == 0) {
         for (int st = 0; st < kTfStages; ++st) {
-            tc::mbar_init(S.full[st], 1);
-            tc::mbar_init(S.empty[st], 1);
+            tc::mbar_init(S.full(st), 1);
+            tc::mbar_init(S.empty(st), 1);
         }
         tc::mbar_init(S.done, 1);
         tc::mbar_fence_init();
@@ -546,7 +549,7 @@ __global__ void __launch_bounds__(kTfThreads, 1)
 #pragma unroll
                     for (int i = 0; i < 32; ++i) v[i] = 0.f;
                 }
-                store_split_row32(S.ahi, S.alo, r, c0, v);
+                store_split_row<32>(S.ahi, S.alo, r, c0, v);
             }
             tc::fence_async_shared();
             tc::fence_before_sync();
@@ -557,30 +560,27 @@ __global__ void __launch_bounds__(kTfThreads, 1)
                 ok = epi_and(tf_mma(S, din, W, tmem, chunk, gemm));
                 if (!ok) break;
                 if (c0 < W) {
-                    const float4 *bl = reinterpret_cast<const float4 *>(P.b[l] + c0);
-                    float v[32], d[32];
-                    tc::tmem_ld32(taddr, v);
+                    const float4 *bl = reinterpret_cast<const float4 *>(layer_bias(P, l) + c0);
+#pragma unroll 1
+                    for (int hf = 0; hf < 2; ++hf) {
+                        float v[16], d[16];
+                        tc::tmem_ld16(taddr + 16 * hf, v);
 #pragma unroll
-                    for (int i = 0; i < 32; i += 4) {
-                        const float4 b4 = __ldg(bl + i / 4);
-                        const float h0 = v[i] + b4.x, h1 = v[i + 1] + b4.y;
-                        const float h2 = v[i + 2] + b4.z, h3 = v[i + 3] + b4.w;
-                        v[i] = siluf_(h0);
-                        v[i + 1] = siluf_(h1);
-                        v[i + 2] = siluf_(h2);
-                        v[i + 3] = siluf_(h3);
-                        d[i] = dsiluf_(h0);
-                        d[i + 1] = dsiluf_(h1);
-                        d[i + 2] = dsiluf_(h2);
-                        d[i + 3] = dsiluf_(h3);
-                    }
-                    tc::tmem_st32(taddr + kTfAccCols + l * W, d);
-                    if (l == L - 1) {
+                        for (int i = 0; i < 16; i += 4) {
+                            const float4 b4 = __ldg(bl + 4 * hf + i / 4);
+                            silu_dsilu_fast(v[i] + b4.x, v[i], d[i]);
+                            silu_dsilu_fast(v[i + 1] + b4.y, v[i + 1], d[i + 1]);
+                            silu_dsilu_fast(v[i + 2] + b4.z, v[i + 2], d[i + 2]);
+                            silu_dsilu_fast(v[i + 3] + b4.w, v[i + 3], d[i + 3]);
+                        }
+                        tc::tmem_st16(taddr + kTfAccCols + l * W + 16 * hf, d);
+                        if (l == L - 1) {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) y += v[i] * P.wout[c0 + i];
-                        if (cb > 0) S.ypart[(cb - 1) * kTcRows + r] = y;
+                            for (int i = 0; i < 16; ++i) y += v[i] * P.wout[c0 + 16 * hf + i];
+                        }
+                        store_split_row<16>(S.ahi, S.alo, r, c0 + 16 * hf, v);
                     }
-                    store_split_row32(S.ahi, S.alo, r, c0, v);
+                    if (l == L - 1 && cb > 0) S.ypart[(cb - 1) * kTcRows + r] = y;
                 }
                 tc::fence_async_shared();
                 tc::fence_before_sync();
@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(kTfThreads, 1)
                 tc::tmem_ld32(taddr + kTfAccCols + (L - 1) * W, v);
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] *= dedy * P.wout[c0 + i];
-                store_split_row32(S.ahi, S.alo, r, c0, v);
+                store_split_row<32>(S.ahi, S.alo, r, c0, v);
             }
             tc::fence_async_shared();
             tc::fence_before_sync();
@@ -627,7 +627,7 @@ __global__ void __launch_bounds__(kTfThreads, 1)
                         tc::tmem_ld32(taddr + kTfAccCols + (l - 1) * W, d);
 #pragma unroll
                         for (int i = 0; i < 32; ++i) v[i] *= d[i];
-                        store_split_row32(S.ahi, S.alo, r, c0, v);
+                        store_split_row<32>(S.ahi, S.alo, r, c0, v);
                     } else if (live) {
                         float4 *dst = reinterpret_cast<float4 *>(dEdX + (size_t)row * d0p + c0);
 #pragma unroll
