@@ -134,30 +134,54 @@ def _barrier(world):
 # roofline of the dominant kernel
 # ------------------------------------------------------------------------------------------------------------------
 
-def _algorithmic_work(w, phase):
-    """Algorithmic work of one launch of a phase, with its bound: (amount, unit, bound).
+def _lj_pairs_per_atom(w, q):
+    """Mean number of LJ partners per atom (r < LJ cutoff, minimum image; every cutoff here is below half the box)
+    at positions q: brute force up to 4,096 atoms, the density estimate above."""
+    s = w.system
+    rc = w.draft.lj_cutoff
+    N = s.n_atoms
+    if N > 4096:
+        return N / float(np.prod(s.box)) * 4.0 / 3.0 * np.pi * rc ** 3
+    tot = 0
+    for i0 in range(0, N, 512):
+        d = q[None, :, :] - q[i0:i0 + 512, None, :]
+        d -= s.box * np.round(d / s.box)
+        r2 = (d * d).sum(-1)
+        tot += int(((r2 < rc * rc) & (r2 > 0)).sum())
+    return tot / N
 
-    MLP: 2 FLOP per multiply-add of the forward chain plus the input-gradient chain (no weight gradient):
-         2 * M * sum(d_in*d_out) * 2.
-    Other phases: bytes that must cross HBM once per window (inputs read + outputs written)."""
+
+def _algorithmic_work(w, phase, q):
+    """Algorithmic work of one launch of a phase, with its bound: (amount, unit, bound, detail).
+
+    mlp:   2 FLOP per multiply-add of the forward chain plus the input-gradient chain (no weight gradient):
+           2 * M * sum(d_in * d_out) * 2, M = K N rows.  FP32 targets run it as three TF32 tensor-core
+           products per term (3x the algorithmic MACs executed); BF16 targets as one BF16 product.
+    draft: per drafted step, every LJ pair within the cutoff costs 8 FLOP of distance and 15 of force
+           (gather form: each ordered pair once), plus 24 FP64 FLOP per atom of BOB + A;
+           K steps per launch, serial.
+    transport: bytes that must cross HBM once per window."""
     s, t, K = w.system, w.target, w.integ.K
     N = s.n_atoms
     M = K * N
     if phase == "mlp":
         d0p = ((s.n_species * t.n_rbf + t.n_ang + s.n_species) + 31) // 32 * 32
         macs = d0p * t.width + (t.n_layers - 1) * t.width * t.width + t.width
-        return 2.0 * 2.0 * M * macs, "FLOP", "alu"
+        return 2.0 * 2.0 * M * macs, "FLOP", "tensor", {"precision": t.precision, "rows": M}
+    if phase == "draft":
+        nb = _lj_pairs_per_atom(w, q)
+        flop = K * (N * nb * (8 + 15) + N * 24)
+        return flop, "FLOP", "alu", {"lj_pairs_per_atom": round(nb, 1), "steps_per_launch": K}
     if phase in ("transport_reduce",):
-        return M * 3 * (4 + 4), "B", "hbm"
+        return M * 3 * (4 + 4), "B", "hbm", {}
     if phase in ("transport_commit",):
-        return N * 3 * (8 + 8 + 4 + 4 + 8 + 8 + 8), "B", "hbm"
+        return N * 3 * (8 + 8 + 4 + 4 + 8 + 8 + 8), "B", "hbm", {}
     return None
 
 
-def roofline(h, w, peaks, peak_kind, n_rep=20):
+def roofline(h, w, peaks, peak_kind, q, n_rep=20):
     """Per-phase CUDA-event times of the window (live, on the library's stream), the dominant phase, and its
     achieved rate against the peak that bounds it."""
-    import torch
     phases = None
     for _ in range(3):
         h.profile_window()
@@ -169,23 +193,39 @@ def roofline(h, w, peaks, peak_kind, n_rep=20):
     phases = acc
     dom = max(phases, key=lambda k: phases[k])
     share = phases[dom] / sum(phases.values())
-    work = _algorithmic_work(w, dom)
+    work = _algorithmic_work(w, dom, q)
     sm_max = peaks.get("sm_max_mhz", 2032.0)
     fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s: 148 SMs x 128 FP32 lanes x FMA
     out = {"kernel": dom, "share": round(share, 3), "ms": round(phases[dom], 5),
            "phases_ms": {k: round(v, 5) for k, v in phases.items()}}
     if work is None:
-        # ALU-bound descriptor/adjoint kernels: report FP32 issue-rate bound against the FP32 peak
         out.update({"bound": "alu", "achieved": None, "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": None,
-                    "traffic": None, "note": "no algorithmic FLOP model for this phase"})
+                    "traffic": None, "note": "no algorithmic model for this phase"})
         return out
-    amount, unit, bound = work
+    amount, unit, bound, detail = work
     sec = phases[dom] * 1e-3
+    out.update(detail)
     if bound == "alu":
         ach = amount / sec / 1e12
-        out.update({"bound": "alu", "achieved": round(ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
-                    "frac": round(ach / fp32_peak, 4), "traffic": None,
+        out.update({"bound": "alu", "achieved": round(ach, 4), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+                    "frac": round(ach / fp32_peak, 5), "traffic": None,
                     "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz" % sm_max})
+        if dom == "draft":
+            out["us_per_step"] = round(phases[dom] * 1e3 / w.integ.K, 3)
+            out["note"] = ("serial chain of K drafted steps in one thread-block cluster (at most 16 SMs); "
+                           "latency-bound: the per-step time, not FLOP/s, is the figure of merit")
+    elif bound == "tensor":
+        ach = amount / sec / 1e12
+        bf16 = peaks["bf16_tflops"]
+        if w.target.precision == "bf16":
+            pk, src = bf16, "%s bf16 burst" % peak_kind
+        else:
+            # TF32 dense = bf16 x (1.1 / 2.25), the nominal ratio
+            pk, src = bf16 * 1.1 / 2.25, "%s bf16 burst x 1.1/2.25 (nominal TF32:BF16)" % peak_kind
+        out.update({"bound": "tensor", "achieved": round(ach, 2), "peak": round(pk, 1), "unit": "TFLOP/s",
+                    "frac": round(ach / pk, 5), "traffic": None, "peak_source": src})
+        if w.target.precision in ("fp32", "fp32-cuda-cores"):
+            out["tensor_flop_executed_per_algorithmic"] = 3
     else:
         ach = amount / sec / 1e9
         pk = peaks["hbm_gbs"]
@@ -295,13 +335,17 @@ def run_ours(args):
     e2e_val = _sum_over_ranks(e2e_committed, world) * w.integ.dt * NS_PER_DAY / _max_over_ranks(t_e2e, world)
     D = 3 * s.n_atoms
 
-    rl = roofline(h, w, peaks, peak_kind)
+    rl = roofline(h, w, peaks, peak_kind, pos)
     launches_per_window = 8
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "ns/day", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_lsd_max * 1e3 / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "dtype_detail": "FP32 forces, descriptors and MLP; FP64 integrator state, z.delta, delta.delta and log ratio",
+        "dtype_detail": ("FP32 forces and descriptors; MLP %s; FP64 integrator state, z.delta, delta.delta and "
+                         "log ratio" % {"fp32": "at FP32 accuracy as three TF32 tensor-core products per term",
+                                        "bf16": "in BF16 on the tensor cores with FP32 accumulation",
+                                        "fp8": "in FP32 on the CUDA cores (FP8 not built)",
+                                        "fp32-cuda-cores": "in FP32 on the CUDA cores"}[w.target.precision]),
         "data": "synthetic",
         "config": {"workload": w.name, "n_atoms": s.n_atoms, "K": K, "dt_fs": w.integ.dt, "T_K": w.integ.temperature,
                    "gamma_per_fs": w.integ.gamma, "target": "LJ + 0.05 eV tanh(MLP %d->%dx%d->1)" % (
