@@ -9,6 +9,7 @@
 // memory and turns itself into a no-op once enough steps are committed, so
 // the host only synchronises once per batch of windows.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,11 +45,14 @@ struct PotHost {
     __nv_bfloat16 *dbuf_bf = nullptr; // Wt, Wn, wout (BF16)
     float rmax2f = 0.f, near2f = 0.f;
     bool present = false;
-    void *tc_plan = nullptr;              // tensor maps of the BF16 weights (tensor-core MLP)
-    __nv_bfloat16 *tc_scratch = nullptr;  // per-CTA SiLU' slots of the tensor-core MLP
+    void *tc_plan = nullptr;              // tensor maps of the weights (tensor-core MLP: BF16, TF32x3 or FP8)
+    void *cal_plan = nullptr;             // FP8: the BF16 plan that calibrates the activation scales
+    __nv_bfloat16 *tc_scratch = nullptr;  // per-CTA SiLU' slots of the tensor-core MLP (when not in TMEM)
     size_t n_dbuf = 0;                    // floats in dbuf
     float *dbuf_tf = nullptr;             // TF32 hi parts of the FP32 layouts, then the lo parts
-    void *tf_plan = nullptr;              // tensor maps of those (FP32 MLP on the tensor cores)
+    uint8_t *dbuf_f8 = nullptr;           // e4m3 copies of the FP32 layouts (per-layer scales)
+    float *tc_scales = nullptr;           // FP8 [3L]: forward A scales, backward A scales, weight scales
+    float *tc_amax = nullptr;             // FP8 calibration [2L]
 };
 
 }  // namespace
@@ -213,6 +217,11 @@ int pot_setup(lsd_handle *h, PotHost &ph, const lsd_potential *lp, bool is_draft
         TRY(dalloc(h, &ph.dbuf, total));
         TRY(dalloc(h, &ph.dbuf_bf, total));
         if (lp->precision == LSD_FP32) TRY(dalloc(h, &ph.dbuf_tf, 2 * total));
+        if (lp->precision == LSD_FP8) {
+            TRY(dalloc(h, &ph.dbuf_f8, total));
+            TRY(dalloc(h, &ph.tc_scales, 3 * (size_t)L));
+            TRY(dalloc(h, &ph.tc_amax, 2 * (size_t)L));
+        }
         for (int l = 0; l < L; ++l) {
             P.Wt[l] = ph.dbuf + offWt[l];
             P.Wn[l] = ph.dbuf + offWn[l];
@@ -286,6 +295,25 @@ int pot_upload(lsd_handle *h, PotHost &ph) {
         }
         CK(cudaMemcpyAsync(ph.dbuf_tf, tf.data(), 2 * total * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     }
+    std::vector<uint8_t> f8;
+    std::vector<float> wsc;
+    if (ph.dbuf_f8) {
+        // e4m3 with one scale per layer: s_l = max|W_l| / 448 (the largest finite e4m3), both layouts
+        f8.assign(total, 0);
+        wsc.assign(L, 1.f);
+        for (int l = 0; l < L; ++l) {
+            const int dinp = l == 0 ? P.d0p : W;
+            float m = 0.f;
+            for (size_t k = 0; k < (size_t)dinp * W; ++k) m = std::max(m, std::fabs(buf[offWn[l] + k]));
+            wsc[l] = m > 0.f ? m / 448.f : 1.f;
+            for (size_t k = 0; k < (size_t)dinp * W; ++k) {
+                f8[offWn[l] + k] = __nv_cvt_float_to_fp8(buf[offWn[l] + k] / wsc[l], __NV_SATFINITE, __NV_E4M3);
+                f8[offWt[l] + k] = __nv_cvt_float_to_fp8(buf[offWt[l] + k] / wsc[l], __NV_SATFINITE, __NV_E4M3);
+            }
+        }
+        CK(cudaMemcpyAsync(ph.dbuf_f8, f8.data(), total, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(ph.tc_scales + 2 * L, wsc.data(), L * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    }
     CK(cudaStreamSynchronize(h->stream));
     return LSD_OK;
 }
@@ -329,9 +357,8 @@ int wait_stream(lsd_handle *h) {
 void enqueue_mlp(lsd_handle *h, const PotHost &pot, int M, cudaStream_t s) {
     const PotDev &P = pot.dev;
     if (pot.tc_plan)
-        launch_mlp_tc(pot.tc_plan, h->X, M, P, h->E_mlp, h->dEdX, pot.tc_scratch, h->n_sm, &h->st->err, s);
-    else if (pot.tf_plan)
-        launch_mlp_tf32(pot.tf_plan, h->X, M, P, h->E_mlp, h->dEdX, h->n_sm, &h->st->err, s);
+        launch_mlp_tc(pot.tc_plan, h->X, M, P, h->E_mlp, h->dEdX, pot.tc_scratch, pot.tc_scales, nullptr, h->n_sm,
+                      &h->st->err, s);
     else
         launch_mlp_fp32(h->X, M, P, h->E_mlp, h->dEdX, s);
 }
@@ -436,6 +463,36 @@ int check_err(const DevState &s) {
     return LSD_OK;
 }
 
+// FP8 potentials: the activation and gradient scales, once per handle.  The
+// BF16 kernel runs the potential's MLP on the initial configuration (N rows)
+// and records |max| of every A operand tensor; each scale is 2 |max| / 448, so
+// values up to twice the calibration range are represented and larger ones
+// saturate.  The scales then stay fixed, which keeps the FP8 potential one
+// function of the configuration for the handle's lifetime.
+int calibrate_fp8(lsd_handle *h, PotHost &ph) {
+    const PotDev &P = ph.dev;
+    const int L = P.n_layers, N = h->N;
+    cudaStream_t s = h->stream;
+    launch_fixpoint(h->q, h->species, N, h->geo, h->fix_eval, s);
+    launch_neigh_build(h->fix_eval, N, h->geo, ph.rmax2f, ph.near2f, h->cap_near, h->cap_far, h->near_keys,
+                       h->far_keys, h->n_near, h->n_far, h->st, s);
+    launch_desc(h->fix_eval, h->near_keys, h->n_near, h->cap_near, N, h->geo, P, h->X, s);
+    CK(cudaMemsetAsync(ph.tc_amax, 0, 2 * L * sizeof(float), s));
+    launch_mlp_tc(ph.cal_plan, h->X, N, P, h->E_mlp, h->dEdX, ph.tc_scratch, nullptr, ph.tc_amax, h->n_sm,
+                  &h->st->err, s);
+    CK(cudaGetLastError());
+    std::vector<float> am(2 * L), sc(2 * L);
+    CK(cudaMemcpyAsync(am.data(), ph.tc_amax, 2 * L * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int k = 0; k < 2 * L; ++k) sc[k] = am[k] > 0.f ? 2.f * am[k] / 448.f : 1.f;
+    CK(cudaMemcpyAsync(ph.tc_scales, sc.data(), 2 * L * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    DevState st;
+    TRY(read_state(h, &st));
+    return check_err(st);
+}
+
+
 __global__ void mb_init_kernel(int N, Coef cf, const int *species, const double *mass, double T, double kT_kappa,
                                double *p) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -473,8 +530,8 @@ void lsd_destroy(lsd_handle *h) {
     for (void *v : h->allocs) cudaFree(v);
     if (h->draft.tc_plan) mlp_tc_plan_free(h->draft.tc_plan);
     if (h->target.tc_plan) mlp_tc_plan_free(h->target.tc_plan);
-    if (h->draft.tf_plan) mlp_tf32_plan_free(h->draft.tf_plan);
-    if (h->target.tf_plan) mlp_tf32_plan_free(h->target.tf_plan);
+    if (h->draft.cal_plan) mlp_tc_plan_free(h->draft.cal_plan);
+    if (h->target.cal_plan) mlp_tc_plan_free(h->target.cal_plan);
     train_free(h->train);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
@@ -552,7 +609,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     h->cap_far = std::min(nb_capacity(rho, rfar, 32), (27 * h->N + 31) / 32 * 32);
     if (desc_smem_bytes(8, h->cap_near) + 8 * 256 * sizeof(float) > (size_t)kMaxDynSmem) return fail(LSD_EUNSUPPORTED);
     if (verify_kernels_setup(kMaxDynSmem) != cudaSuccess || mlp_kernels_setup(kMaxDynSmem) != cudaSuccess ||
-        mlp_tc_setup() != cudaSuccess || mlp_tf32_setup() != cudaSuccess ||
+        mlp_tc_setup() != cudaSuccess ||
         draft_kernels_setup(kMaxDynSmem) != cudaSuccess ||
         verlet_setup(kMaxDynSmem) != cudaSuccess)
         return fail(LSD_ECUDA);
@@ -605,29 +662,42 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         return fail(rc);
     if ((rc = pot_upload(h, h->draft)) != LSD_OK) return fail(rc);
     if ((rc = pot_upload(h, h->target)) != LSD_OK) return fail(rc);
-    // BF16 potentials evaluate their MLP on the tensor cores
+    // MLPs on the tensor cores: BF16 as is, FP32 as three TF32 products, FP8 e4m3
     for (PotHost *ph : {&h->draft, &h->target}) {
-        if (ph->dev.has_mlp && ph->dev.precision == LSD_BF16) {
-            if (!mlp_tc_supported(ph->dev)) return fail(LSD_EUNSUPPORTED);
-            ph->tc_plan = mlp_tc_plan(ph->dev);
-            if (!ph->tc_plan) return fail(LSD_ECUDA);
-            const int grid = mlp_tc_grid(h->K * h->N, h->n_sm);
-            if ((rc = dalloc(h, &ph->tc_scratch, mlp_tc_scratch_elems(ph->dev, grid))) != LSD_OK) return fail(rc);
-        }
-        // FP32 potentials: three TF32 products per term on the tensor cores
-        if (ph->dev.has_mlp && ph->dev.precision == LSD_FP32 && ph->dbuf_tf && mlp_tf32_supported(ph->dev)) {
-            const PotDev &P = ph->dev;
-            const size_t n_all = ph->n_dbuf;   // the lo parts follow the hi parts; offsets as in dbuf
-            Tf32Weights w{};
-            for (int l = 0; l < P.n_layers; ++l) {
-                w.wn_hi[l] = ph->dbuf_tf + (P.Wn[l] - ph->dbuf);
-                w.wn_lo[l] = ph->dbuf_tf + n_all + (P.Wn[l] - ph->dbuf);
-                w.wt_hi[l] = ph->dbuf_tf + (P.Wt[l] - ph->dbuf);
-                w.wt_lo[l] = ph->dbuf_tf + n_all + (P.Wt[l] - ph->dbuf);
+        const PotDev &P = ph->dev;
+        if (!P.has_mlp) continue;
+        int op = -1;
+        if (P.precision == LSD_BF16) op = kTcBF16;
+        if (P.precision == LSD_FP32 && ph->dbuf_tf && mlp_tc_supported(kTcTF32x3, P)) op = kTcTF32x3;
+        if (P.precision == LSD_FP8) op = kTcFP8;
+        if (op < 0) continue;   // FP32 beyond the TF32 kernel's shapes, or LSD_FP32_CUDA_CORES: CUDA cores
+        if (!mlp_tc_supported(op, P)) return fail(LSD_EUNSUPPORTED);
+        TcWeights w{}, wb{};
+        for (int l = 0; l < P.n_layers; ++l) {
+            const size_t on = P.Wn[l] - ph->dbuf, ot = P.Wt[l] - ph->dbuf;
+            wb.wn[l][0] = P.Wn_bf[l];
+            wb.wt[l][0] = P.Wt_bf[l];
+            if (op == kTcTF32x3) {
+                w.wn[l][0] = ph->dbuf_tf + on;
+                w.wn[l][1] = ph->dbuf_tf + ph->n_dbuf + on;
+                w.wt[l][0] = ph->dbuf_tf + ot;
+                w.wt[l][1] = ph->dbuf_tf + ph->n_dbuf + ot;
+            } else if (op == kTcFP8) {
+                w.wn[l][0] = ph->dbuf_f8 + on;
+                w.wt[l][0] = ph->dbuf_f8 + ot;
+            } else {
+                w = wb;
             }
-            ph->tf_plan = mlp_tf32_plan(P, w);
-            if (!ph->tf_plan) return fail(LSD_ECUDA);
         }
+        ph->tc_plan = mlp_tc_plan(op, P, w);
+        if (!ph->tc_plan) return fail(LSD_ECUDA);
+        if (op == kTcFP8) {
+            ph->cal_plan = mlp_tc_plan(kTcBF16, P, wb);
+            if (!ph->cal_plan) return fail(LSD_ECUDA);
+        }
+        const int grid = mlp_tc_grid(h->K * h->N, h->n_sm);
+        const size_t ns = mlp_tc_scratch_elems(op, P, grid);
+        if (ns && (rc = dalloc(h, &ph->tc_scratch, ns)) != LSD_OK) return fail(rc);
     }
     if (cudaMemcpy(h->q, sys->pos, D * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->species, sys->species, N * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -652,6 +722,8 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     if ((rc = train_init(h->train, h->draft.dev, h->draft.weights, h->N)) != LSD_OK) return fail(rc);
     h->train.st = h->st;
     h->train.K = K;
+    for (PotHost *ph : {&h->draft, &h->target})
+        if (ph->cal_plan && (rc = calibrate_fp8(h, *ph)) != LSD_OK) return fail(rc);
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(LSD_ECUDA);
     *out = h;
     return LSD_OK;
@@ -957,8 +1029,8 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
 int lsd_target_mlp_static_dev(lsd_handle *h, const float *X_dev, int32_t M, float *E_dev, float *dEdX_dev) {
     if (!h || !X_dev || !E_dev || !dEdX_dev || M < 1) return LSD_EINVAL;
     if (!h->target.tc_plan) return LSD_EUNSUPPORTED;
-    return mlp_tc_static_launch(h->target.tc_plan, X_dev, M, h->target.dev, E_dev, dEdX_dev, h->n_sm, &h->st->err,
-                                h->stream);
+    return mlp_tc_static_launch(h->target.tc_plan, X_dev, M, h->target.dev, E_dev, dEdX_dev, h->target.tc_scales,
+                                h->n_sm, &h->st->err, h->stream);
 }
 
 int lsd_query(const lsd_handle *h, int32_t *K, int32_t *n_atoms, int32_t *d_in, int32_t *nb_cap) {

@@ -52,31 +52,28 @@ void launch_mlp_fp32(const float *X, int M, const PotDev &P, float *E_mlp, float
 size_t mlp_fp32_smem_bytes(const PotDev &P);
 cudaError_t mlp_kernels_setup(int max_smem);
 
-// MLP on tcgen05 tensor cores, BF16 (lsd_mlp_tc.cu)
-bool mlp_tc_supported(const PotDev &P);
-void *mlp_tc_plan(const PotDev &P);   // tensor maps of the weights; nullptr on failure
-void mlp_tc_plan_free(void *plan);
-size_t mlp_tc_smem_bytes();
-size_t mlp_tc_scratch_elems(const PotDev &P, int n_cta);
-int mlp_tc_grid(int M, int n_sm);
-void launch_mlp_tc(const void *plan, const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX,
-                   __nv_bfloat16 *scratch, int n_sm, int *err, cudaStream_t s);
-cudaError_t mlp_tc_setup();
-// FP32 potentials: three TF32 products per term (lsd_mlp_tc.cu)
-struct Tf32Weights {
-    const float *wn_hi[kMaxLayers], *wn_lo[kMaxLayers];   // W_l   [W][din_p], TF32 hi / lo parts
-    const float *wt_hi[kMaxLayers], *wt_lo[kMaxLayers];   // W_l^T [din_p][W]
+// MLP on the tcgen05 tensor cores (lsd_mlp_tc.cu): BF16, FP32 as three TF32
+// products per term, FP8 e4m3 with static per-tensor scales
+enum { kTcBF16 = 0, kTcTF32x3 = 1, kTcFP8 = 2 };
+struct TcWeights {
+    const void *wn[kMaxLayers][2];   // W_l   [W][din_p] in the operand type; [1] = TF32 lo part
+    const void *wt[kMaxLayers][2];   // W_l^T [din_p][W]
 };
-bool mlp_tf32_supported(const PotDev &P);
-size_t mlp_tf32_smem_bytes();
-void *mlp_tf32_plan(const PotDev &P, const Tf32Weights &w);
-void mlp_tf32_plan_free(void *plan);
-void launch_mlp_tf32(const void *plan, const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX, int n_sm,
-                     int *err, cudaStream_t s);
-cudaError_t mlp_tf32_setup();
+bool mlp_tc_supported(int op, const PotDev &P);
+void *mlp_tc_plan(int op, const PotDev &P, const TcWeights &w);   // tensor maps; nullptr on failure
+void mlp_tc_plan_free(void *plan);
+int mlp_tc_plan_op(const void *plan);
+size_t mlp_tc_smem_bytes(int op);
+size_t mlp_tc_scratch_elems(int op, const PotDev &P, int n_cta);   // bf16 SiLU' scratch (0: kept in TMEM)
+int mlp_tc_grid(int M, int n_sm);
+// scales (FP8 only, device [3L]): A scales of forward GEMMs, of backward GEMMs, weight scales;
+// amax (device [2L] or null): |max| of the same A tensors, recorded with atomics (calibration)
+void launch_mlp_tc(const void *plan, const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX,
+                   __nv_bfloat16 *scratch, const float *scales, float *amax, int n_sm, int *err, cudaStream_t s);
+cudaError_t mlp_tc_setup();
 size_t mlp_tc_static_scratch_bytes();
 int mlp_tc_static_launch(const void *plan, const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX,
-                         int n_sm, int *err, cudaStream_t s);
+                         const float *scales, int n_sm, int *err, cudaStream_t s);
 
 // transport (lsd_transport.cu)
 int transport_atoms_per_block(int N);

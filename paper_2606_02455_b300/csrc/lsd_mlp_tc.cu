@@ -1,25 +1,37 @@
 // lsd_mlp_tc.cu -- the per-atom energy MLP and its input gradient on the
-// 5th-generation tensor cores (tcgen05), BF16 operands, FP32 accumulation in
-// tensor memory.  Same mathematics as lsd_mlp.cu:
+// 5th-generation tensor cores (tcgen05, accumulators in tensor memory).  Same
+// mathematics as lsd_mlp.cu:
 //   forward  h_l = W_l a_{l-1} + b_l, a_l = SiLU(h_l), y = w_out.a_L + b_out
-//   backward g_L = e'(y) w_out * SiLU'(h_L), g_{l-1} = (W_l^T g_l) * SiLU'(h_{l-1}),
-//            dE/dx = W_1^T g_1
-// Every layer is a GEMM D[128 x N] = A[128 x K] B[N x K]^T with the tile's
-// 128 rows in the 128 TMEM lanes:
-//   forward  A = a_{l-1} (bf16),  B = W_l   [W x din]  (N = W,   K = din)
-//   backward A = g_l     (bf16),  B = W_l^T [din x W]  (N = din, K = W)
-// A lives in shared memory in the 128-byte-swizzled K-major layout (panels of
-// 64 bf16 per row), written by the epilogue of the previous GEMM.  B streams
-// from global memory by TMA (2-D tiled copies, 128-byte swizzle) in chunks of
-// 64 K-columns through two stages, synchronised with mbarriers.  One thread
-// issues the TMA copies and MMAs (M = 128, K = 16 per instruction) and commits
-// their completion to mbarriers; the 128 threads (one per row) run the
-// epilogues from TMEM with tcgen05.ld.  SiLU'(h) of each layer is kept in a
-// per-CTA global scratch slot (bf16) that stays resident in L2.
-// The grid is persistent: one CTA per SM, looping over 128-row tiles.
-// Every mbarrier wait gives up after about a second and records an error.
+//   backward g_{L-1} = e'(y) w_out * SiLU'(h_{L-1}),
+//            g_{l-1} = (g_l W_l) * SiLU'(h_{l-1}),  dE/dx = g_0 W_0
+// Every layer is a GEMM D[128 x N] = A[128 x K] B[N x K]^T with the tile's 128
+// rows in the 128 TMEM lanes:
+//   forward  A = a_{l-1},  B = W_l   [W x din]  (N = W,    K = din)
+//   backward A = g_l,      B = W_l^T [din x W]  (N = din,  K = W)
+// Operand arithmetic, one template:
+//   BF16     kind::f16, K = 16 per instruction;
+//   TF32x3   FP32 targets: x = x_hi + x_lo (x_hi = tf32(x), x_lo = tf32(x - x_hi),
+//            round to nearest); lo*hi + hi*lo + hi*hi accumulate in FP32 (the
+//            dropped lo*lo is below 2^-22 of the product), K = 8;
+//   FP8      kind::f8f6f4, e4m3 with static per-tensor scales (weights: amax /
+//            448 per layer; every activation and gradient tensor: a scale
+//            calibrated once per handle), K = 32; the accumulator is rescaled
+//            by s_A s_W in the epilogue.
+// A lives in shared memory in the 128-byte-swizzled K-major layout, written by
+// the epilogue of the previous GEMM.  B streams from global memory by TMA
+// (2-D tiled copies, 128-byte swizzle), one 128-byte-wide K chunk per stage.
+// Roles: warp 16 is the TMA producer and runs ahead through the whole GEMM
+// sequence of the CTA's tiles, so the weights of the next GEMM land while the
+// current epilogue runs; thread 0 issues the MMAs and commits them to
+// mbarriers; warps 0..15 run the epilogues, warp w reading TMEM lane quarter
+// w % 4 (rows 32 (w % 4) + lane) and the 32-column groups g = w / 4 + 4 k.
+// SiLU'(h) stays in TMEM next to the accumulator when it fits, else in a
+// per-CTA bf16 scratch that stays resident in L2.  The grid is persistent:
+// one CTA per SM, looping over 128-row tiles.  Every mbarrier wait gives up
+// after a bounded time and records an error.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp8.h>
 
 #include "lsd.h"
 #include "lsd_common.cuh"
@@ -29,383 +41,103 @@
 namespace lsd {
 
 constexpr int kTcRows = 128;
-constexpr int kTcThreads = 128;
-constexpr int kPanelElems = 64;                   // bf16 elements per 128-byte swizzled row
-constexpr int kPanelBytes = kTcRows * 128;        // one K-panel of A: 16 KB
-constexpr int kMaxPanels = 4;                     // K up to 256
-constexpr int kStageBytes = 256 * 128;            // one B chunk: up to 256 rows x 128 B
+constexpr int kPanelBytes = kTcRows * 128;           // one 128-byte-wide K panel of A: 16 KB
+constexpr int kStageBytes = 256 * 128;               // one B stage: 256 rows x 128 B (TF32: hi then lo, 128 rows each)
+constexpr int kEpiWarps = 16;
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kTcThreads = kEpiThreads + 32;         // + the TMA producer warp
+constexpr uint32_t kTmemCols = 512;
+constexpr int kSmemBudget = 227 * 1024 - 1024;       // the opt-in maximum less the 1024-byte alignment slack
+constexpr int kMiscBytes = 2048;                     // barriers, TMEM slot, head partials [3][128]
 
-struct TcSmem {
-    uint32_t a;          // A operand panels
-    uint32_t b0;         // B stage s at b0 + s kStageBytes
-    uint32_t full0;      // TMA landed (stage s at full0 + 8 s)
-    uint32_t empty0;     // MMAs done with the stage (empty0 + 8 s)
-    uint32_t done;       // all MMAs of a GEMM done
-    uint32_t tslot;      // TMEM base address
+template <int OP> struct TcT;
+template <> struct TcT<kTcBF16> {
+    static constexpr int elem = 2, panel = 64, mmak = 16, copies = 1, maxk = 256, maxn = 256;
+    static constexpr uint32_t fmt = tc::kFmtBF16;
+};
+template <> struct TcT<kTcTF32x3> {
+    static constexpr int elem = 4, panel = 32, mmak = 8, copies = 2, maxk = 128, maxn = 128;
+    static constexpr uint32_t fmt = tc::kFmtTF32;
+};
+template <> struct TcT<kTcFP8> {
+    static constexpr int elem = 1, panel = 128, mmak = 32, copies = 1, maxk = 256, maxn = 256;
+    static constexpr uint32_t fmt = tc::kFmtE4M3;
+};
+template <int OP> constexpr int tc_a_bytes() { return TcT<OP>::maxk / TcT<OP>::panel * kPanelBytes * TcT<OP>::copies; }
+template <int OP> constexpr int tc_stages() {
+    return (kSmemBudget - tc_a_bytes<OP>() - kMiscBytes) / kStageBytes > 6
+               ? 6
+               : (kSmemBudget - tc_a_bytes<OP>() - kMiscBytes) / kStageBytes;
+}
+template <int OP> constexpr int tc_smem_bytes() {
+    return 1024 + tc_a_bytes<OP>() + tc_stages<OP>() * kStageBytes + kMiscBytes;
+}
+static_assert(tc_smem_bytes<kTcBF16>() <= 227 * 1024, "BF16 shared memory");
+static_assert(tc_smem_bytes<kTcTF32x3>() <= 227 * 1024, "TF32 shared memory");
+static_assert(tc_smem_bytes<kTcFP8>() <= 227 * 1024, "FP8 shared memory");
+static_assert(tc_stages<kTcTF32x3>() >= 2, "TF32 stages");
+
+// Shared-memory addresses; per-stage ones are computed (a runtime-indexed
+// array would live in local memory).
+struct TcSm {
+    uint32_t a;      // A panels; TF32 lo copy at a + tc_a_bytes / 2
+    uint32_t b0;     // stage s at b0 + s kStageBytes; TF32 lo chunk kStageBytes / 2 after the hi chunk
+    uint32_t full0, empty0, done, tslot;
+    float *ypart;    // [3][128] head partial sums of column blocks 1..3
     __device__ __forceinline__ uint32_t b(int s) const { return b0 + (uint32_t)s * kStageBytes; }
     __device__ __forceinline__ uint32_t full(int s) const { return full0 + 8u * (uint32_t)s; }
     __device__ __forceinline__ uint32_t empty(int s) const { return empty0 + 8u * (uint32_t)s; }
 };
 
-// One GEMM: thread 0 streams the K-chunks of B by TMA and issues the MMAs;
-// every thread then waits for the accumulator.  chunk counts TMA chunks over
-// the whole kernel (stage = chunk & 1, use = chunk >> 1); gemm counts GEMMs.
-__device__ __forceinline__ bool tc_gemm(const TcSmem &S, const CUtensorMap *map, int K, int N, uint32_t tmem,
-                                        uint32_t &chunk, uint32_t &gemm) {
-    bool ok = true;
-    const int nk = (K + kPanelElems - 1) / kPanelElems;
-    if (threadIdx.x == 0) {
-        tc::fence_after_sync();
-        const uint32_t idesc = tc::idesc_f32acc(tc::kFmtBF16, kTcRows, N);
-        const uint32_t bytes = (uint32_t)N * 128u;
-        auto issue = [&](uint32_t c, int kc) {
-            const int s = c & 1;
-            if (c >= 2 && ok) ok = tc::mbar_wait(S.empty(s), ((c >> 1) - 1) & 1);
-            if (!ok) return;
-            tc::mbar_expect_tx(S.full(s), bytes);
-            tc::tma_load_2d(S.b(s), map, kc * kPanelElems, 0, S.full(s));
-        };
-        const uint32_t c0 = chunk;
-        issue(c0, 0);
-        for (int kc = 0; kc < nk && ok; ++kc) {
-            const uint32_t c = c0 + kc;
-            if (kc + 1 < nk) issue(c + 1, kc + 1);
-            const int s = c & 1;
-            if (!tc::mbar_wait(S.full(s), (c >> 1) & 1)) { ok = false; break; }
-            tc::fence_after_sync();
-            const int kend = min(kPanelElems, K - kc * kPanelElems);
-            for (int k16 = 0; k16 < kend; k16 += 16) {
-                const uint64_t ad = tc::sdesc_sw128(S.a + kc * kPanelBytes + k16 * 2);
-                const uint64_t bd = tc::sdesc_sw128(S.b(s) + k16 * 2);
-                tc::mma_f16(tmem, ad, bd, idesc, (kc | k16) != 0);
-            }
-            tc::mma_commit(S.empty(s));
-        }
-        tc::mma_commit(S.done);
-    }
-    chunk += nk;
-    // everyone waits for the accumulator of this GEMM
-    if (!tc::mbar_wait(S.done, gemm & 1)) ok = false;
-    ++gemm;
-    tc::fence_after_sync();
-    return ok;
-}
-
-// Writes 32 consecutive bf16 columns [c0, c0+32) of row r into the A panels.
-__device__ __forceinline__ void store_a_row32(uint32_t a_base, int r, int c0, const float (&v)[32]) {
-    const int panel = c0 / kPanelElems;
-    const int chunk0 = (c0 % kPanelElems) / 8;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        uint32_t w[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]);
-            w[e] = *reinterpret_cast<const uint32_t *>(&h2);
-        }
-        const uint32_t addr = a_base + panel * kPanelBytes + tc::sw128_offset(r, chunk0 + q);
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w[0]), "r"(w[1]), "r"(w[2]),
-                     "r"(w[3])
-                     : "memory");
-    }
-}
-
 struct TcMaps {
-    CUtensorMap fwd[kMaxLayers];   // W_l      bf16 [W rows][din_p cols]
-    CUtensorMap bwd[kMaxLayers];   // W_l^T    bf16 [din_p rows][W cols]
-};
-
-__global__ void __launch_bounds__(kTcThreads, 1)
-    mlp_bf16_tc_kernel(const __grid_constant__ TcMaps maps, const float *__restrict__ X, int M, PotDev P,
-                       float *__restrict__ E_mlp, float *__restrict__ dEdX, __nv_bfloat16 *__restrict__ scratch,
-                       int *__restrict__ err) {
-    extern __shared__ uint8_t smraw[];
-    const uint32_t base = (tc::smem_u32(smraw) + 1023u) & ~1023u;
-    TcSmem S;
-    S.a = base;
-    S.b0 = base + kMaxPanels * kPanelBytes;
-    const uint32_t bars = S.b0 + 2 * kStageBytes;
-    S.full0 = bars;
-    S.empty0 = bars + 16;
-    S.done = bars + 32;
-    S.tslot = bars + 40;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int W = P.width, L = P.n_layers, d0p = P.d0p;
-    const uint32_t ncols = 256;
-    if (tid == 0) {
-        tc::mbar_init(S.full(0), 1);
-        tc::mbar_init(S.full(1), 1);
-        tc::mbar_init(S.empty(0), 1);
-        tc::mbar_init(S.empty(1), 1);
-        tc::mbar_init(S.done, 1);
-        tc::mbar_fence_init();
-    }
-    if (warp == 0) {
-        tc::tmem_alloc(S.tslot, ncols);
-        tc::tmem_relinquish();
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    uint32_t tmem;
-    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(S.tslot));
-    const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
-    uint32_t chunk = 0, gemm = 0;
-    const int ntiles = (M + kTcRows - 1) / kTcRows;
-    __nv_bfloat16 *my_scr = scratch + (size_t)blockIdx.x * L * kTcRows * W;
-    bool ok = true;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int row = tile * kTcRows + tid;
-        const bool live = row < M;
-        // input descriptors, fp32 -> bf16, into the A panels
-        for (int c0 = 0; c0 < d0p; c0 += 32) {
-            float v[32];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = live ? X[(size_t)row * d0p + c0 + i] : 0.f;
-            store_a_row32(S.a, tid, c0, v);
-        }
-        tc::fence_async_shared();
-        tc::fence_before_sync();
-        __syncthreads();
-        float y = 0.f;
-        // forward
-        int din = d0p;
-        for (int l = 0; l < L && ok; ++l) {
-            ok = tc_gemm(S, &maps.fwd[l], din, W, tmem, chunk, gemm);
-            if (!__syncthreads_and(ok)) { ok = false; break; }
-            const float *bl = P.b[l];
-            __nv_bfloat16 *sp = my_scr + ((size_t)l * kTcRows + tid) * W;
-            for (int c0 = 0; c0 < W; c0 += 32) {
-                float v[32];
-                tc::tmem_ld32(tlane + c0, v);
-#pragma unroll
-                for (int i = 0; i < 32; i += 2) {
-                    const float h0 = v[i] + bl[c0 + i], h1 = v[i + 1] + bl[c0 + i + 1];
-                    v[i] = siluf_(h0);
-                    v[i + 1] = siluf_(h1);
-                    *reinterpret_cast<__nv_bfloat162 *>(sp + c0 + i) = __floats2bfloat162_rn(dsiluf_(h0), dsiluf_(h1));
-                }
-                if (l == L - 1) {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) y += __bfloat162float(__float2bfloat16(v[i])) * P.wout[c0 + i];
-                }
-                store_a_row32(S.a, tid, c0, v);
-            }
-            tc::fence_async_shared();
-            tc::fence_before_sync();
-            __syncthreads();
-            din = W;
-        }
-        if (!ok) break;
-        // energy head
-        y += P.bout;
-        float dedy;
-        if (P.head == LSD_HEAD_LINEAR) {
-            if (live) E_mlp[row] = y;
-            dedy = 1.f;
-        } else {
-            const float t = tanhf(y);
-            if (live) E_mlp[row] = P.head_scale * t;
-            dedy = P.head_scale * (1.f - t * t);
-        }
-        // g_L = e'(y) w_out * SiLU'(h_L)
-        {
-            const __nv_bfloat16 *sp = my_scr + ((size_t)(L - 1) * kTcRows + tid) * W;
-            for (int c0 = 0; c0 < W; c0 += 32) {
-                float v[32];
-#pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] = dedy * P.wout[c0 + i] * __bfloat162float(sp[c0 + i]);
-                store_a_row32(S.a, tid, c0, v);
-            }
-        }
-        tc::fence_async_shared();
-        tc::fence_before_sync();
-        __syncthreads();
-        // backward
-        for (int l = L - 1; l >= 0 && ok; --l) {
-            const int dout = l == 0 ? d0p : W;
-            ok = tc_gemm(S, &maps.bwd[l], W, dout, tmem, chunk, gemm);
-            if (!__syncthreads_and(ok)) { ok = false; break; }
-            const __nv_bfloat16 *sp = my_scr + ((size_t)(l > 0 ? l - 1 : 0) * kTcRows + tid) * W;
-            for (int c0 = 0; c0 < dout; c0 += 32) {
-                float v[32];
-                tc::tmem_ld32(tlane + c0, v);
-                if (l > 0) {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) v[i] *= __bfloat162float(sp[c0 + i]);
-                    store_a_row32(S.a, tid, c0, v);
-                } else if (live) {
-                    float4 *dst = reinterpret_cast<float4 *>(dEdX + (size_t)row * d0p + c0);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                }
-            }
-            tc::fence_async_shared();
-            tc::fence_before_sync();
-            __syncthreads();
-        }
-        if (!ok) break;
-    }
-    if (!ok && tid == 0) atomicOr(err, 8);
-    tc::fence_before_sync();
-    __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
-}
-
-// ---------------------------------------------------------------------------
-// host side
-// ---------------------------------------------------------------------------
-struct TcPlanImpl {
-    TcMaps maps;
-    bool ready = false;
-};
-
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
-    return fn;
-}
-
-// 2-D bf16 tensor [rows][cols] (cols contiguous), box = 64 columns x box_rows rows, 128-byte swizzle.
-static bool make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int box_rows) {
-    auto fn = encode_fn();
-    if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kPanelElems, (cuuint32_t)box_rows};
-    cuuint32_t es[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-bool mlp_tc_supported(const PotDev &P) {
-    return P.has_mlp && P.width % 32 == 0 && P.width <= 256 && P.d0p <= 256 && P.n_layers <= kMaxLayers &&
-           encode_fn() != nullptr;
-}
-
-size_t mlp_tc_smem_bytes() { return 1024 + kMaxPanels * kPanelBytes + 2 * kStageBytes + 64; }
-
-size_t mlp_tc_scratch_elems(const PotDev &P, int n_cta) { return (size_t)n_cta * P.n_layers * kTcRows * P.width; }
-
-void *mlp_tc_plan(const PotDev &P) {
-    TcPlanImpl *pl = new TcPlanImpl();
-    bool ok = true;
-    for (int l = 0; l < P.n_layers && ok; ++l) {
-        const int dinp = l == 0 ? P.d0p : P.width;
-        ok = make_map(&pl->maps.fwd[l], P.Wn_bf[l], P.width, dinp, P.width) &&
-             make_map(&pl->maps.bwd[l], P.Wt_bf[l], dinp, P.width, dinp);
-    }
-    pl->ready = ok;
-    if (!ok) {
-        delete pl;
-        return nullptr;
-    }
-    return pl;
-}
-
-void mlp_tc_plan_free(void *plan) { delete (TcPlanImpl *)plan; }
-
-int mlp_tc_grid(int M, int n_sm) {
-    const int ntiles = (M + kTcRows - 1) / kTcRows;
-    return ntiles < n_sm ? ntiles : n_sm;
-}
-
-void launch_mlp_tc(const void *plan, const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX,
-                   __nv_bfloat16 *scratch, int n_sm, int *err, cudaStream_t s) {
-    const TcPlanImpl *pl = (const TcPlanImpl *)plan;
-    const int grid = mlp_tc_grid(M, n_sm);
-    mlp_bf16_tc_kernel<<<grid, kTcThreads, mlp_tc_smem_bytes(), s>>>(pl->maps, X, M, P, E_mlp, dEdX, scratch, err);
-}
-
-cudaError_t mlp_tc_setup() {
-    return cudaFuncSetAttribute(mlp_bf16_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)mlp_tc_smem_bytes());
-}
-
-// ---------------------------------------------------------------------------
-// FP32 potentials on the tensor cores: three TF32 products per term.
-// Each FP32 operand x is split into x_hi = tf32(x) and x_lo = tf32(x - x_hi)
-// (round to nearest), and every GEMM accumulates A_lo B_hi + A_hi B_lo +
-// A_hi B_hi in the FP32 accumulator (the dropped A_lo B_lo term is below
-// 2^-22 of the product), which keeps the result at FP32 accuracy.  Weights are
-// split once on the host; activations in the epilogue.  32 FP32 elements per
-// 128-byte swizzled row (K = 8 per instruction); A_hi and A_lo panels for K
-// up to 128; three B stages, each holding the hi and lo chunks of 32
-// K-columns, both copied by TMA against one mbarrier.
-// Roles: warp 16 is the TMA producer and runs ahead through the whole GEMM
-// sequence of the CTA's tiles (so the weights of the next GEMM land while the
-// epilogue of the current one runs); thread 0 issues the MMAs; the 16 warps
-// 0..15 run the epilogues, warp w reading TMEM lane quarter w % 4 (rows
-// 32 (w % 4) + lane) and column block w / 4 (32 columns).  TMEM columns
-// [0, 128) hold the accumulator and columns 128 + l W + c hold SiLU'(h_l) of
-// the tile's rows (written by tcgen05.st in the forward epilogues, read back
-// in the backward ones), so nothing of a tile leaves the SM but dE/dX and E.
-// ---------------------------------------------------------------------------
-constexpr int kTfPanelElems = 32;                  // FP32 elements per 128-byte swizzled row
-constexpr int kTfMaxPanels = 4;                    // K up to 128
-constexpr int kTfChunkBytes = 128 * 128;           // one B chunk (hi or lo): up to 128 rows x 128 B
-constexpr int kTfStages = 3;
-constexpr uint32_t kTfTmemCols = 512;              // accumulator (N up to 128) + SiLU' of L layers
-constexpr int kTfAccCols = 128;
-constexpr int kTfEpiWarps = 16;
-constexpr int kTfEpiThreads = kTfEpiWarps * 32;
-constexpr int kTfThreads = kTfEpiThreads + 32;     // + the TMA producer warp
-
-// Shared-memory addresses; per-stage ones are computed, not stored in arrays
-// (a runtime-indexed array would live in local memory).
-struct TfSmem {
-    uint32_t ahi, alo;     // A operand panels
-    uint32_t b0;           // stage s: hi chunk at b0 + 2 s C, lo chunk C after it
-    uint32_t full0, empty0, done, tslot;
-    float *ypart;          // [3][128] partial head sums of column blocks 1..3
-    __device__ __forceinline__ uint32_t bhi(int s) const { return b0 + (uint32_t)s * 2u * kTfChunkBytes; }
-    __device__ __forceinline__ uint32_t blo(int s) const { return bhi(s) + kTfChunkBytes; }
-    __device__ __forceinline__ uint32_t full(int s) const { return full0 + 8u * (uint32_t)s; }
-    __device__ __forceinline__ uint32_t empty(int s) const { return empty0 + 8u * (uint32_t)s; }
+    CUtensorMap fwd[kMaxLayers][2];   // W_l   [W rows][din_p cols]; [1] = TF32 lo part
+    CUtensorMap bwd[kMaxLayers][2];   // W_l^T [din_p rows][W cols]
 };
 
 // barrier 1: the epilogue warps only (the producer warp runs on its own)
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kTfEpiThreads) : "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 __device__ __forceinline__ bool epi_and(bool v) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n}\n"
         : "=r"(r)
-        : "r"((uint32_t)v), "n"(kTfEpiThreads)
+        : "r"((uint32_t)v), "n"(kEpiThreads)
         : "memory");
     return r != 0;
 }
 
 // The MMAs of one GEMM (thread 0), then every epilogue thread waits for the
-// accumulator.  chunk counts B chunks over the kernel (stage = chunk % 3,
-// use = chunk / 3), in the producer's order; gemm counts GEMMs.
-__device__ __forceinline__ bool tf_mma(const TfSmem &S, int K, int N, uint32_t tmem, uint32_t &chunk, uint32_t &gemm) {
+// accumulator.  chunk counts B chunks over the kernel (stage = chunk % S,
+// use = chunk / S), in the producer's order; gemm counts GEMMs.
+template <int OP>
+__device__ __forceinline__ bool tc_mma(const TcSm &S, int K, int N, uint32_t tmem, uint32_t &chunk, uint32_t &gemm) {
+    using T = TcT<OP>;
+    constexpr int NS = tc_stages<OP>();
     bool ok = true;
-    const int nk = (K + kTfPanelElems - 1) / kTfPanelElems;
+    const int nk = (K + T::panel - 1) / T::panel;
     if (threadIdx.x == 0) {
         tc::fence_after_sync();
-        const uint32_t idesc = tc::idesc_f32acc(tc::kFmtTF32, kTcRows, N);
+        const uint32_t idesc = tc::idesc_f32acc(T::fmt, kTcRows, N);
         for (int kc = 0; kc < nk; ++kc) {
             const uint32_t c = chunk + kc;
-            const int s = c % kTfStages;
-            if (!tc::mbar_wait(S.full(s), (c / kTfStages) & 1)) { ok = false; break; }
+            const int s = c % NS;
+            if (!tc::mbar_wait(S.full(s), (c / NS) & 1)) { ok = false; break; }
             tc::fence_after_sync();
-            const int kend = min(kTfPanelElems, K - kc * kTfPanelElems);
-            for (int k8 = 0; k8 < kend; k8 += 8) {
-                const uint32_t ao = kc * kPanelBytes + k8 * 4;
-                const uint64_t ahd = tc::sdesc_sw128(S.ahi + ao), ald = tc::sdesc_sw128(S.alo + ao);
-                const uint64_t bhd = tc::sdesc_sw128(S.bhi(s) + k8 * 4), bld = tc::sdesc_sw128(S.blo(s) + k8 * 4);
-                tc::mma_tf32(tmem, ald, bhd, idesc, (kc | k8) != 0);
-                tc::mma_tf32(tmem, ahd, bld, idesc, 1u);
-                tc::mma_tf32(tmem, ahd, bhd, idesc, 1u);
+            const int kend = min(T::panel, K - kc * T::panel);
+            for (int k = 0; k < kend; k += T::mmak) {
+                const uint32_t ao = S.a + kc * kPanelBytes + k * T::elem, bo = S.b(s) + k * T::elem;
+                const uint32_t acc = (kc | k) != 0;
+                if (OP == kTcTF32x3) {
+                    const uint64_t ahd = tc::sdesc_sw128(ao), ald = tc::sdesc_sw128(ao + tc_a_bytes<OP>() / 2);
+                    const uint64_t bhd = tc::sdesc_sw128(bo), bld = tc::sdesc_sw128(bo + kStageBytes / 2);
+                    tc::mma_tf32(tmem, ald, bhd, idesc, acc);
+                    tc::mma_tf32(tmem, ahd, bld, idesc, 1u);
+                    tc::mma_tf32(tmem, ahd, bhd, idesc, 1u);
+                } else if (OP == kTcFP8) {
+                    tc::mma_f8f6f4(tmem, tc::sdesc_sw128(ao), tc::sdesc_sw128(bo), idesc, acc);
+                } else {
+                    tc::mma_f16(tmem, tc::sdesc_sw128(ao), tc::sdesc_sw128(bo), idesc, acc);
+                }
             }
             tc::mma_commit(S.empty(s));
         }
@@ -423,89 +155,123 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return r;
 }
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+__device__ __forceinline__ uint32_t pack_e4m3(float a, float b, float c, float d) {
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return lo | (hi << 16);
+}
 
-// Writes the hi and lo TF32 parts of NC (16 or 32) consecutive FP32 columns
-// [c0, c0 + NC) of row r; c0 is a multiple of 16 (half or all of the
-// swizzled row of panel c0 / 32).
-template <int NC>
-__device__ __forceinline__ void store_split_row(uint32_t ahi, uint32_t alo, int r, int c0, const float (&v)[NC]) {
-    const int panel = c0 / kTfPanelElems, q0 = (c0 % kTfPanelElems) / 4;
+// Writes 16 consecutive columns [c, c + 16) (c a multiple of 16) of row r of
+// the A operand, in the operand format (FP8: v * qinv, saturating).
+template <int OP>
+__device__ __forceinline__ void store_a16(uint32_t a, int r, int c, const float (&v)[16], float qinv) {
+    using T = TcT<OP>;
+    const uint32_t pbase = a + (c / T::panel) * kPanelBytes;
+    const int e0 = c % T::panel;   // element offset inside the 128-byte row
+    if (OP == kTcBF16) {
 #pragma unroll
-    for (int qq = 0; qq < NC / 4; ++qq) {
-        const int q = q0 + qq;
-        uint32_t h[4], l[4];
+        for (int q = 0; q < 2; ++q)
+            st_shared_v4(pbase + tc::sw128_offset(r, e0 / 8 + q), pack_bf16(v[8 * q], v[8 * q + 1]),
+                         pack_bf16(v[8 * q + 2], v[8 * q + 3]), pack_bf16(v[8 * q + 4], v[8 * q + 5]),
+                         pack_bf16(v[8 * q + 6], v[8 * q + 7]));
+    } else if (OP == kTcTF32x3) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float x = v[4 * qq + e];
-            h[e] = tf32_rna(x);
-            l[e] = tf32_rna(x - __uint_as_float(h[e]));
+        for (int q = 0; q < 4; ++q) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                h[e] = tf32_rna(v[4 * q + e]);
+                l[e] = tf32_rna(v[4 * q + e] - __uint_as_float(h[e]));
+            }
+            const uint32_t off = tc::sw128_offset(r, e0 / 4 + q);
+            st_shared_v4(pbase + off, h[0], h[1], h[2], h[3]);
+            st_shared_v4(pbase + tc_a_bytes<OP>() / 2 + off, l[0], l[1], l[2], l[3]);
         }
-        const uint32_t off = panel * kPanelBytes + tc::sw128_offset(r, q);
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ahi + off), "r"(h[0]), "r"(h[1]), "r"(h[2]),
-                     "r"(h[3])
-                     : "memory");
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(alo + off), "r"(l[0]), "r"(l[1]), "r"(l[2]),
-                     "r"(l[3])
-                     : "memory");
+    } else {
+        st_shared_v4(pbase + tc::sw128_offset(r, e0 / 16), pack_e4m3(v[0] * qinv, v[1] * qinv, v[2] * qinv, v[3] * qinv),
+                     pack_e4m3(v[4] * qinv, v[5] * qinv, v[6] * qinv, v[7] * qinv),
+                     pack_e4m3(v[8] * qinv, v[9] * qinv, v[10] * qinv, v[11] * qinv),
+                     pack_e4m3(v[12] * qinv, v[13] * qinv, v[14] * qinv, v[15] * qinv));
     }
 }
 
-struct TfMaps {
-    CUtensorMap fwd_hi[kMaxLayers], fwd_lo[kMaxLayers];   // W_l   [W rows][din_p cols]
-    CUtensorMap bwd_hi[kMaxLayers], bwd_lo[kMaxLayers];   // W_l^T [din_p rows][W cols]
-};
+__device__ __forceinline__ float amax16(float m, const float (&v)[16]) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) m = fmaxf(m, fabsf(v[i]));
+    return m;
+}
+// records a tensor's |max| (calibration): one atomic per warp
+__device__ __forceinline__ void record_amax(float *amax, int slot, float m) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(amax) + slot, __float_as_int(m));
+}
 
 // The TMA producer: B chunks of every GEMM of the CTA's tiles, in the order
-// the MMAs consume them, at most kTfStages ahead.  Before returning it waits
+// the MMAs consume them, at most S stages ahead.  Before returning it waits
 // for the landing of the copies it issued, so none is in flight at exit.
-__device__ void tf_producer(const TfSmem &S, const TfMaps &maps, int M, const PotDev &P, int *err) {
+template <int OP>
+__device__ void tc_producer(const TcSm &S, const TcMaps &maps, int M, const PotDev &P, int *err) {
+    using T = TcT<OP>;
+    constexpr int NS = tc_stages<OP>();
     const int W = P.width, L = P.n_layers, d0p = P.d0p;
     const int ntiles = (M + kTcRows - 1) / kTcRows;
     uint32_t c = 0;
     bool ok = true;
-    auto gemm_chunks = [&](const CUtensorMap *mhi, const CUtensorMap *mlo, int K, int N) {
-        const int nk = (K + kTfPanelElems - 1) / kTfPanelElems;
+    auto gemm_chunks = [&](const CUtensorMap *m, int K, int N) {
+        const int nk = (K + T::panel - 1) / T::panel;
         for (int kc = 0; kc < nk && ok; ++kc, ++c) {
-            const int s = c % kTfStages;
-            if (c >= (uint32_t)kTfStages && !tc::mbar_wait(S.empty(s), ((c / kTfStages) - 1) & 1)) {
+            const int s = c % NS;
+            if (c >= (uint32_t)NS && !tc::mbar_wait(S.empty(s), ((c / NS) - 1) & 1)) {
                 ok = false;
                 break;
             }
-            tc::mbar_expect_tx(S.full(s), 2u * (uint32_t)N * 128u);
-            tc::tma_load_2d(S.bhi(s), mhi, kc * kTfPanelElems, 0, S.full(s));
-            tc::tma_load_2d(S.blo(s), mlo, kc * kTfPanelElems, 0, S.full(s));
+            tc::mbar_expect_tx(S.full(s), (uint32_t)T::copies * (uint32_t)N * 128u);
+            tc::tma_load_2d(S.b(s), &m[0], kc * T::panel, 0, S.full(s));
+            if (OP == kTcTF32x3) tc::tma_load_2d(S.b(s) + kStageBytes / 2, &m[1], kc * T::panel, 0, S.full(s));
         }
     };
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        for (int l = 0; l < L && ok; ++l) gemm_chunks(&maps.fwd_hi[l], &maps.fwd_lo[l], l == 0 ? d0p : W, W);
-        for (int l = L - 1; l >= 0 && ok; --l) gemm_chunks(&maps.bwd_hi[l], &maps.bwd_lo[l], W, l == 0 ? d0p : W);
+        for (int l = 0; l < L && ok; ++l) gemm_chunks(maps.fwd[l], l == 0 ? d0p : W, W);
+        for (int l = L - 1; l >= 0 && ok; --l) gemm_chunks(maps.bwd[l], W, l == 0 ? d0p : W);
     }
-    // the copies of the last (up to kTfStages) chunks issued
-    const uint32_t first = c > (uint32_t)kTfStages ? c - kTfStages : 0u;
+    const uint32_t first = c > (uint32_t)NS ? c - NS : 0u;
     for (uint32_t k = first; k < c; ++k)
-        if (!tc::mbar_wait(S.full(k % kTfStages), (k / kTfStages) & 1)) ok = false;
+        if (!tc::mbar_wait(S.full(k % NS), (k / NS) & 1)) ok = false;
     if (!ok) atomicOr(err, 8);
 }
 
-__global__ void __launch_bounds__(kTfThreads, 1)
-    mlp_tf32x3_tc_kernel(const __grid_constant__ TfMaps maps, const float *__restrict__ X, int M, PotDev P,
-                         float *__restrict__ E_mlp, float *__restrict__ dEdX, int *__restrict__ err) {
+// scales (FP8): [l] A scale of forward GEMM l, [L + l] A scale of backward
+// GEMM l, [2L + l] weight scale of layer l.  amax (calibration, may be null):
+// |max| of the same A tensors, slots [l] and [L + l].
+template <int OP>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    mlp_tc_kernel(const __grid_constant__ TcMaps maps, const float *__restrict__ X, int M, PotDev P,
+                  float *__restrict__ E_mlp, float *__restrict__ dEdX, __nv_bfloat16 *__restrict__ scratch,
+                  const float *__restrict__ scales, float *__restrict__ amax, int *__restrict__ err) {
+    constexpr int NS = tc_stages<OP>();
+    constexpr int ACC = TcT<OP>::maxn;   // accumulator columns
     extern __shared__ uint8_t smraw[];
     const uint32_t base = (tc::smem_u32(smraw) + 1023u) & ~1023u;
-    TfSmem S;
-    S.ahi = base;
-    S.alo = S.ahi + kTfMaxPanels * kPanelBytes;
-    S.b0 = S.alo + kTfMaxPanels * kPanelBytes;
-    const uint32_t at = S.b0 + 2 * kTfStages * kTfChunkBytes;
-    S.full0 = at;
-    S.empty0 = at + 8 * kTfStages;
-    S.done = at + 16 * kTfStages;
+    TcSm S;
+    S.a = base;
+    S.b0 = S.a + tc_a_bytes<OP>();
+    S.full0 = S.b0 + NS * kStageBytes;
+    S.empty0 = S.full0 + 8 * NS;
+    S.done = S.empty0 + 8 * NS;
     S.tslot = S.done + 8;
-    S.ypart = reinterpret_cast<float *>(smraw + (S.tslot + 8 - tc::smem_u32(smraw)));
+    S.ypart = reinterpret_cast<float *>(smraw + (S.full0 + 512 - tc::smem_u32(smraw)));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int W = P.width, L = P.n_layers, d0p = P.d0p;
     if (tid == 0) {
-        for (int st = 0; st < kTfStages; ++st) {
+        for (int st = 0; st < NS; ++st) {
             tc::mbar_init(S.full(st), 1);
             tc::mbar_init(S.empty(st), 1);
         }
@@ -513,7 +279,7 @@ __global__ void __launch_bounds__(kTfThreads, 1)
         tc::mbar_fence_init();
     }
     if (warp == 0) {
-        tc::tmem_alloc(S.tslot, kTfTmemCols);
+        tc::tmem_alloc(S.tslot, kTmemCols);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
@@ -521,24 +287,59 @@ __global__ void __launch_bounds__(kTfThreads, 1)
     tc::fence_after_sync();
     uint32_t tmem;
     asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(S.tslot));
-    if (warp == kTfEpiWarps) {
-        if (lane == 0) tf_producer(S, maps, M, P, err);
+    if (warp == kEpiWarps) {
+        if (lane == 0) tc_producer<OP>(S, maps, M, P, err);
     } else {
-        const int quarter = warp & 3, cb = warp >> 2, c0 = 32 * cb;
-        const int r = 32 * quarter + lane;                      // row in the tile
-        const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0;
+        const int quarter = warp & 3, cb = warp >> 2;
+        const int r = 32 * quarter + lane;                               // row in the tile
+        const uint32_t tacc = tmem + ((uint32_t)(32 * quarter) << 16);   // this warp's lanes, column 0
+        const bool sp_tmem = ACC + L * W <= (int)kTmemCols;              // SiLU' next to the accumulator
+        __nv_bfloat16 *my_scr = scratch ? scratch + (size_t)blockIdx.x * L * kTcRows * W : nullptr;
+        auto sp_addr = [&](int l, int c) -> __nv_bfloat16 * { return my_scr + ((size_t)l * kTcRows + r) * W + c; };
+        auto store_sp = [&](int l, int c, const float (&d)[16]) {
+            if (sp_tmem) {
+                tc::tmem_st16(tacc + ACC + l * W + c, d);
+            } else {
+                uint4 *o = reinterpret_cast<uint4 *>(sp_addr(l, c));
+                o[0] = make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]),
+                                  pack_bf16(d[6], d[7]));
+                o[1] = make_uint4(pack_bf16(d[8], d[9]), pack_bf16(d[10], d[11]), pack_bf16(d[12], d[13]),
+                                  pack_bf16(d[14], d[15]));
+            }
+        };
+        auto load_sp = [&](int l, int c, float (&d)[16]) {
+            if (sp_tmem) {
+                tc::tmem_ld16(tacc + ACC + l * W + c, d);
+            } else {
+                const uint4 *o = reinterpret_cast<const uint4 *>(sp_addr(l, c));
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const uint4 u = o[q];
+                    const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162 *>(&w4[e]);
+                        d[8 * q + 2 * e] = __low2float(h2);
+                        d[8 * q + 2 * e + 1] = __high2float(h2);
+                    }
+                }
+            }
+        };
+        const float sc_x = OP == kTcFP8 ? scales[0] : 1.f;
         uint32_t chunk = 0, gemm = 0;
         const int ntiles = (M + kTcRows - 1) / kTcRows;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const int row = tile * kTcRows + r;
             const bool live = row < M;
-            if (c0 < d0p) {
-                float v[32];
+            // input descriptors into the A panels
+            float am = 0.f;
+            for (int c = 16 * cb; c < d0p; c += 64) {
+                float v[16];
                 if (live) {
-                    const float4 *src = reinterpret_cast<const float4 *>(X + (size_t)row * d0p + c0);
+                    const float4 *src = reinterpret_cast<const float4 *>(X + (size_t)row * d0p + c);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
+                    for (int i = 0; i < 4; ++i) {
                         const float4 t = src[i];
                         v[4 * i] = t.x;
                         v[4 * i + 1] = t.y;
@@ -547,50 +348,55 @@ __global__ void __launch_bounds__(kTfThreads, 1)
                     }
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) v[i] = 0.f;
+                    for (int i = 0; i < 16; ++i) v[i] = 0.f;
                 }
-                store_split_row<32>(S.ahi, S.alo, r, c0, v);
+                if (amax) am = amax16(am, v);
+                store_a16<OP>(S.a, r, c, v, 1.f / sc_x);
             }
+            if (amax) record_amax(amax, 0, am);
             tc::fence_async_shared();
             tc::fence_before_sync();
             epi_sync();
+            // forward
             float y = 0.f;
-            int din = d0p;
             for (int l = 0; l < L; ++l) {
-                ok = epi_and(tf_mma(S, din, W, tmem, chunk, gemm));
+                ok = epi_and(tc_mma<OP>(S, l == 0 ? d0p : W, W, tmem, chunk, gemm));
                 if (!ok) break;
-                if (c0 < W) {
-                    const float4 *bl = reinterpret_cast<const float4 *>(layer_bias(P, l) + c0);
-#pragma unroll 1
-                    for (int hf = 0; hf < 2; ++hf) {
-                        float v[16], d[16];
-                        tc::tmem_ld16(taddr + 16 * hf, v);
+                const float dq = OP == kTcFP8 ? scales[l] * scales[2 * L + l] : 1.f;
+                const float qinv = (OP == kTcFP8 && l + 1 < L) ? 1.f / scales[l + 1] : 1.f;
+                const float *bl = layer_bias(P, l);
+                am = 0.f;
+                for (int c = 16 * cb; c < W; c += 64) {
+                    float v[16], d[16];
+                    tc::tmem_ld16(tacc + c, v);
+                    const float4 *b4p = reinterpret_cast<const float4 *>(bl + c);
 #pragma unroll
-                        for (int i = 0; i < 16; i += 4) {
-                            const float4 b4 = __ldg(bl + 4 * hf + i / 4);
-                            silu_dsilu_fast(v[i] + b4.x, v[i], d[i]);
-                            silu_dsilu_fast(v[i + 1] + b4.y, v[i + 1], d[i + 1]);
-                            silu_dsilu_fast(v[i + 2] + b4.z, v[i + 2], d[i + 2]);
-                            silu_dsilu_fast(v[i + 3] + b4.w, v[i + 3], d[i + 3]);
-                        }
-                        tc::tmem_st16(taddr + kTfAccCols + l * W + 16 * hf, d);
-                        if (l == L - 1) {
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) y += v[i] * P.wout[c0 + 16 * hf + i];
-                        }
-                        store_split_row<16>(S.ahi, S.alo, r, c0 + 16 * hf, v);
+                    for (int i = 0; i < 16; i += 4) {
+                        const float4 b4 = __ldg(b4p + i / 4);
+                        silu_dsilu_fast(v[i] * dq + b4.x, v[i], d[i]);
+                        silu_dsilu_fast(v[i + 1] * dq + b4.y, v[i + 1], d[i + 1]);
+                        silu_dsilu_fast(v[i + 2] * dq + b4.z, v[i + 2], d[i + 2]);
+                        silu_dsilu_fast(v[i + 3] * dq + b4.w, v[i + 3], d[i + 3]);
                     }
-                    if (l == L - 1 && cb > 0) S.ypart[(cb - 1) * kTcRows + r] = y;
+                    store_sp(l, c, d);
+                    if (l == L - 1) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) y += v[i] * P.wout[c + i];
+                    } else {
+                        if (amax) am = amax16(am, v);
+                        store_a16<OP>(S.a, r, c, v, qinv);
+                    }
                 }
+                if (amax && l + 1 < L) record_amax(amax, l + 1, am);
+                if (l == L - 1 && cb > 0) S.ypart[(cb - 1) * kTcRows + r] = y;
                 tc::fence_async_shared();
                 tc::fence_before_sync();
                 epi_sync();
-                din = W;
             }
             if (!ok) break;
-            // energy head (column block 0 holds the row's sum), e'(y) to every column block
+            // energy head: column block 0 adds the partial sums; e'(y) to every column block
             if (cb == 0) {
-                for (int b = 1; b < W / 32; ++b) y += S.ypart[(b - 1) * kTcRows + r];
+                for (int b = 1; b < 4 && 16 * b < W; ++b) y += S.ypart[(b - 1) * kTcRows + r];
                 y += P.bout;
                 float dedy;
                 if (P.head == LSD_HEAD_LINEAR) {
@@ -604,37 +410,49 @@ __global__ void __launch_bounds__(kTfThreads, 1)
                 S.ypart[r] = dedy;
             }
             epi_sync();
-            const float dedy = S.ypart[r];
-            if (c0 < W) {
-                float v[32];
-                tc::tmem_ld32(taddr + kTfAccCols + (L - 1) * W, v);
+            {
+                const float dedy = S.ypart[r];
+                const float qinv = OP == kTcFP8 ? 1.f / scales[L + L - 1] : 1.f;
+                am = 0.f;
+                for (int c = 16 * cb; c < W; c += 64) {
+                    float v[16];
+                    load_sp(L - 1, c, v);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] *= dedy * P.wout[c0 + i];
-                store_split_row<32>(S.ahi, S.alo, r, c0, v);
+                    for (int i = 0; i < 16; ++i) v[i] *= dedy * P.wout[c + i];
+                    if (amax) am = amax16(am, v);
+                    store_a16<OP>(S.a, r, c, v, qinv);
+                }
+                if (amax) record_amax(amax, L + L - 1, am);
             }
             tc::fence_async_shared();
             tc::fence_before_sync();
             epi_sync();
+            // backward
             for (int l = L - 1; l >= 0; --l) {
                 const int dout = l == 0 ? d0p : W;
-                ok = epi_and(tf_mma(S, W, dout, tmem, chunk, gemm));
+                ok = epi_and(tc_mma<OP>(S, W, dout, tmem, chunk, gemm));
                 if (!ok) break;
-                if (c0 < dout) {
-                    float v[32];
-                    tc::tmem_ld32(taddr, v);
+                const float dq = OP == kTcFP8 ? scales[L + l] * scales[2 * L + l] : 1.f;
+                const float qinv = (OP == kTcFP8 && l > 0) ? 1.f / scales[L + l - 1] : 1.f;
+                am = 0.f;
+                for (int c = 16 * cb; c < dout; c += 64) {
+                    float v[16];
+                    tc::tmem_ld16(tacc + c, v);
                     if (l > 0) {
-                        float d[32];
-                        tc::tmem_ld32(taddr + kTfAccCols + (l - 1) * W, d);
+                        float d[16];
+                        load_sp(l - 1, c, d);
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) v[i] *= d[i];
-                        store_split_row<32>(S.ahi, S.alo, r, c0, v);
+                        for (int i = 0; i < 16; ++i) v[i] *= dq * d[i];
+                        if (amax) am = amax16(am, v);
+                        store_a16<OP>(S.a, r, c, v, qinv);
                     } else if (live) {
-                        float4 *dst = reinterpret_cast<float4 *>(dEdX + (size_t)row * d0p + c0);
+                        float4 *dst = reinterpret_cast<float4 *>(dEdX + (size_t)row * d0p + c);
 #pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                        for (int i = 0; i < 4; ++i)
+                            dst[i] = make_float4(v[4 * i] * dq, v[4 * i + 1] * dq, v[4 * i + 2] * dq, v[4 * i + 3] * dq);
                     }
                 }
+                if (amax && l > 0) record_amax(amax, L + l - 1, am);
                 tc::fence_async_shared();
                 tc::fence_before_sync();
                 epi_sync();
@@ -644,44 +462,64 @@ __global__ void __launch_bounds__(kTfThreads, 1)
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, kTfTmemCols);
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
-struct TfPlanImpl {
-    TfMaps maps;
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct TcPlanImpl {
+    int op;
+    TcMaps maps;
 };
 
-// 2-D FP32 tensor [rows][cols] (cols contiguous), box = 32 columns x box_rows rows, 128-byte swizzle.
-static bool make_map_f32(CUtensorMap *m, const void *ptr, int rows, int cols, int box_rows) {
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2-D tensor [rows][cols] (cols contiguous) of the operand type; box = one
+// 128-byte row of columns x box_rows rows, 128-byte swizzle.
+static bool make_map(CUtensorMap *m, int op, const void *ptr, int rows, int cols, int box_rows) {
     auto fn = encode_fn();
     if (!fn) return false;
+    const int elem = op == kTcBF16 ? 2 : (op == kTcTF32x3 ? 4 : 1);
+    const CUtensorMapDataType dt = op == kTcBF16   ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                   : op == kTcTF32x3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                     : CU_TENSOR_MAP_DATA_TYPE_UINT8;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * 4};
-    cuuint32_t box[2] = {(cuuint32_t)kTfPanelElems, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * elem};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(ptr), dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return fn(m, dt, 2, const_cast<void *>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
 }
 
-bool mlp_tf32_supported(const PotDev &P) {
-    return P.has_mlp && P.width % 32 == 0 && P.width <= 128 && P.d0p <= 128 && P.n_layers <= kMaxLayers &&
-           kTfAccCols + P.n_layers * P.width <= (int)kTfTmemCols && encode_fn() != nullptr;
+bool mlp_tc_supported(int op, const PotDev &P) {
+    if (!P.has_mlp || P.width % 32 != 0 || P.n_layers > kMaxLayers || P.n_layers < 1 || !encode_fn()) return false;
+    if (op == kTcTF32x3) return P.width <= 128 && P.d0p <= 128 && 128 + P.n_layers * P.width <= (int)kTmemCols;
+    return P.width <= 256 && P.d0p <= 256;
 }
 
-size_t mlp_tf32_smem_bytes() {
-    return 1024 + 2 * kTfMaxPanels * kPanelBytes + 2 * kTfStages * kTfChunkBytes + 128 + 3 * kTcRows * sizeof(float);
-}
-
-void *mlp_tf32_plan(const PotDev &P, const Tf32Weights &w) {
-    TfPlanImpl *pl = new TfPlanImpl();
+void *mlp_tc_plan(int op, const PotDev &P, const TcWeights &w) {
+    TcPlanImpl *pl = new TcPlanImpl();
+    pl->op = op;
     bool ok = true;
+    const int ncopy = op == kTcTF32x3 ? 2 : 1;
     for (int l = 0; l < P.n_layers && ok; ++l) {
         const int dinp = l == 0 ? P.d0p : P.width;
-        ok = make_map_f32(&pl->maps.fwd_hi[l], w.wn_hi[l], P.width, dinp, P.width) &&
-             make_map_f32(&pl->maps.fwd_lo[l], w.wn_lo[l], P.width, dinp, P.width) &&
-             make_map_f32(&pl->maps.bwd_hi[l], w.wt_hi[l], dinp, P.width, dinp) &&
-             make_map_f32(&pl->maps.bwd_lo[l], w.wt_lo[l], dinp, P.width, dinp);
+        for (int k = 0; k < ncopy && ok; ++k)
+            ok = make_map(&pl->maps.fwd[l][k], op, w.wn[l][k], P.width, dinp, P.width) &&
+                 make_map(&pl->maps.bwd[l][k], op, w.wt[l][k], dinp, P.width, dinp);
     }
     if (!ok) {
         delete pl;
@@ -690,18 +528,59 @@ void *mlp_tf32_plan(const PotDev &P, const Tf32Weights &w) {
     return pl;
 }
 
-void mlp_tf32_plan_free(void *plan) { delete (TfPlanImpl *)plan; }
+void mlp_tc_plan_free(void *plan) { delete (TcPlanImpl *)plan; }
 
-void launch_mlp_tf32(const void *plan, const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX, int n_sm,
-                     int *err, cudaStream_t s) {
-    const TfPlanImpl *pl = (const TfPlanImpl *)plan;
-    const int grid = mlp_tc_grid(M, n_sm);
-    mlp_tf32x3_tc_kernel<<<grid, kTfThreads, mlp_tf32_smem_bytes(), s>>>(pl->maps, X, M, P, E_mlp, dEdX, err);
+int mlp_tc_plan_op(const void *plan) { return ((const TcPlanImpl *)plan)->op; }
+
+size_t mlp_tc_smem_bytes(int op) {
+    return op == kTcBF16 ? tc_smem_bytes<kTcBF16>() : (op == kTcTF32x3 ? tc_smem_bytes<kTcTF32x3>() : tc_smem_bytes<kTcFP8>());
 }
 
-cudaError_t mlp_tf32_setup() {
-    return cudaFuncSetAttribute(mlp_tf32x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)mlp_tf32_smem_bytes());
+size_t mlp_tc_scratch_elems(int op, const PotDev &P, int n_cta) {
+    const int acc = op == kTcTF32x3 ? 128 : 256;
+    if (acc + P.n_layers * P.width <= (int)kTmemCols) return 0;
+    return (size_t)n_cta * P.n_layers * kTcRows * P.width;
+}
+
+int mlp_tc_grid(int M, int n_sm) {
+    const int ntiles = (M + kTcRows - 1) / kTcRows;
+    return ntiles < n_sm ? ntiles : n_sm;
+}
+
+static void launch_grid(const TcPlanImpl *pl, int grid, const float *X, int M, const PotDev &P, float *E_mlp,
+                        float *dEdX, __nv_bfloat16 *scratch, const float *scales, float *amax, int *err,
+                        cudaStream_t s) {
+    switch (pl->op) {
+        case kTcBF16:
+            mlp_tc_kernel<kTcBF16><<<grid, kTcThreads, tc_smem_bytes<kTcBF16>(), s>>>(pl->maps, X, M, P, E_mlp, dEdX,
+                                                                                     scratch, scales, amax, err);
+            break;
+        case kTcTF32x3:
+            mlp_tc_kernel<kTcTF32x3><<<grid, kTcThreads, tc_smem_bytes<kTcTF32x3>(), s>>>(
+                pl->maps, X, M, P, E_mlp, dEdX, scratch, scales, amax, err);
+            break;
+        default:
+            mlp_tc_kernel<kTcFP8><<<grid, kTcThreads, tc_smem_bytes<kTcFP8>(), s>>>(pl->maps, X, M, P, E_mlp, dEdX,
+                                                                                   scratch, scales, amax, err);
+            break;
+    }
+}
+
+void launch_mlp_tc(const void *plan, const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX,
+                   __nv_bfloat16 *scratch, const float *scales, float *amax, int n_sm, int *err, cudaStream_t s) {
+    launch_grid((const TcPlanImpl *)plan, mlp_tc_grid(M, n_sm), X, M, P, E_mlp, dEdX, scratch, scales, amax, err, s);
+}
+
+cudaError_t mlp_tc_setup() {
+    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<kTcBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         tc_smem_bytes<kTcBF16>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(mlp_tc_kernel<kTcTF32x3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc_smem_bytes<kTcTF32x3>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(mlp_tc_kernel<kTcFP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc_smem_bytes<kTcFP8>());
+    return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -722,8 +601,9 @@ static void *g_static_scratch_addr[kStaticMaxDevices];   // device address of th
 size_t mlp_tc_static_scratch_bytes() { return kStaticScratchBytes; }
 
 int mlp_tc_static_launch(const void *plan, const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX,
-                         int n_sm, int *err, cudaStream_t s) {
-    const size_t per_cta = (size_t)P.n_layers * kTcRows * P.width;
+                         const float *scales, int n_sm, int *err, cudaStream_t s) {
+    const TcPlanImpl *pl = (const TcPlanImpl *)plan;
+    const size_t per_cta = mlp_tc_scratch_elems(pl->op, P, 1);
     if (per_cta > kStaticScratchElems) return LSD_EINVAL;   // one tile's SiLU' does not fit the array
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return LSD_ECUDA;
@@ -734,12 +614,13 @@ int mlp_tc_static_launch(const void *plan, const float *X, int M, const PotDev &
         if (cudaGetSymbolAddress(&p, g_static_mlp_scratch) != cudaSuccess || !p) return LSD_ECUDA;
         g_static_scratch_addr[dev] = p;
     }
-    const int cap = (int)(kStaticScratchElems / per_cta);
     int grid = mlp_tc_grid(M, n_sm);
-    if (grid > cap) grid = cap;
-    const TcPlanImpl *pl = (const TcPlanImpl *)plan;
-    mlp_bf16_tc_kernel<<<grid, kTcThreads, mlp_tc_smem_bytes(), s>>>(
-        pl->maps, X, M, P, E_mlp, dEdX, (__nv_bfloat16 *)g_static_scratch_addr[dev], err);
+    if (per_cta > 0) {
+        const int cap = (int)(kStaticScratchElems / per_cta);
+        if (grid > cap) grid = cap;
+    }
+    launch_grid(pl, grid, X, M, P, E_mlp, dEdX, per_cta > 0 ? (__nv_bfloat16 *)g_static_scratch_addr[dev] : nullptr,
+                scales, nullptr, err, s);
     return cudaGetLastError() == cudaSuccess ? LSD_OK : LSD_ECUDA;
 }
 

@@ -134,13 +134,15 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// Instruction descriptor, kind::f16 / kind::tf32: D = F32 (bits 4-5 = 1), A and
-// B format (bits 7-9, 10-12: 0 F16, 1 BF16, 2 TF32), both K-major, N/8 at bit
-// 17, M/16 at bit 24.
+// Instruction descriptor, kind::f16 / kind::tf32 / kind::f8f6f4: D = F32 (bits
+// 4-5 = 1), A and B format (bits 7-9, 10-12: kind::f16 0 F16, 1 BF16;
+// kind::tf32 2 TF32; kind::f8f6f4 0 E4M3), both K-major, N/8 at bit 17, M/16
+// at bit 24.
 __host__ __device__ constexpr uint32_t idesc_f32acc(uint32_t ab_format, int M, int N) {
     return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 constexpr uint32_t kFmtBF16 = 1, kFmtTF32 = 2;
+constexpr uint32_t kFmtE4M3 = 0;   // kind::f8f6f4 operand format
 
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                         uint32_t accumulate) {
@@ -153,6 +155,13 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
                                          uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_f8f6f4(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
         ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }

@@ -114,3 +114,48 @@ def test_fp32_tensor_core_mlp_matches_oracle(cfg):
         assert _rel(F[c], Fc[c].astype(np.float64)) < 1e-5
     h.close()
     hc.close()
+
+
+# stated per-result bars of the FP8 path (3-bit mantissa through 4 + 4 GEMMs; measured on this system:
+# dE/dX 8.8 %, forces 0.41 %, per-atom MLP energy 11.1 %)
+FP8_TOL = {"dEdX": 0.15, "F": 0.02, "E": 0.2}
+
+
+def test_fp8_tensor_core_mlp_against_oracle():
+    """FP8 e4m3 target MLP (static per-tensor scales calibrated at init, FP32 accumulation) on the config-4
+    architecture: its stated per-result error against FP64, which the FP8 path has no tighter bar for."""
+    import torch
+    from paper_2606_02455_b300 import lsd
+    s, draft, tgt = _system(precision="fp8")
+    integ = W.Integrator(0.5, 0.01, 350.0, 4)
+    h = lsd.LSD(s, draft, tgt, integ)
+    rng = np.random.default_rng(7)
+    qs = np.stack([s.positions + 0.05 * rng.standard_normal(s.positions.shape) for _ in range(4)])
+    F, E = h.target_forces(torch.tensor(qs, device="cuda"), energies=True)
+    F, E = F.cpu().numpy(), E.cpu().numpy()
+    X, G = h.descriptors(4)
+    errs = []
+    for c in range(4):
+        ref = O.energy_forces(s, tgt, qs[c], want=("F", "X", "dEdX", "E_atom"))
+        e_lj = O.energy_forces(s, draft, qs[c], want=("E_atom",))["E_atom"]
+        e = (_rel(G[c], ref["dEdX"]), _rel(F[c], ref["F"]), _rel(E[c].astype(np.float64) - e_lj, ref["E_atom"] - e_lj))
+        errs.append(e)
+        assert _rel(X[c], ref["X"]) < 1e-5
+        assert e[0] < FP8_TOL["dEdX"] and e[1] < FP8_TOL["F"] and e[2] < FP8_TOL["E"], e
+    print("fp8 relative errors (dEdX, F, E_mlp):", errs)
+    h.close()
+
+
+def test_fp8_potential_is_one_function():
+    """The FP8 scales are calibrated once: the same configuration gives bit-identical forces before and after a
+    window of dynamics, and in a second evaluation."""
+    import torch
+    from paper_2606_02455_b300 import lsd
+    s, draft, tgt = _system(cells=6, precision="fp8")
+    h = lsd.LSD(s, draft, tgt, W.Integrator(0.5, 0.01, 350.0, 4))
+    q = torch.tensor(s.positions[None] + 0.02, device="cuda")
+    F0 = h.target_forces(q).cpu().numpy()
+    h.step(8)
+    F1 = h.target_forces(q).cpu().numpy()
+    assert np.array_equal(F0, F1)
+    h.close()
