@@ -104,30 +104,38 @@ def _dist():
     return world, rank, local
 
 
-def _max_over_ranks(x, world):
+def _reduce_over_ranks(x, world, op, device):
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
 
 
-def _sum_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+def _max_over_ranks(x, world, device="cuda"):
+    return _reduce_over_ranks(x, world, "max", device)
+
+
+def _sum_over_ranks(x, world, device="cuda"):
+    return _reduce_over_ranks(x, world, "sum", device)
 
 
 def _barrier(world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def replica_seed(base_seed, rank):
+    """Replicas only: rank r runs an independent copy of the workload with its own noise key."""
+    return base_seed + rank
+
+
+def whole_job_rate(units_local, seconds_local, world, device="cuda"):
+    """Whole-job throughput of independent replicas: the units all ranks processed over the slowest rank's time."""
+    return _sum_over_ranks(units_local, world, device) / _max_over_ranks(seconds_local, world, device)
 
 
 # ------------------------------------------------------------------------------------------------------------------
@@ -249,7 +257,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     w = _workload(args.config)
     s = w.system
-    s.seed = s.seed + rank            # independent replicas
+    s.seed = replica_seed(s.seed, rank)   # independent replicas
     K = w.integ.K
     peaks, peak_kind = _peaks()
     h = lsd.LSD(s, w.draft, w.target, w.integ)
@@ -311,9 +319,8 @@ def run_ours(args):
     clk = clocks.stop()
 
     t_lsd_max = _max_over_ranks(t_lsd, world)
-    committed_all = _sum_over_ranks(committed, world)
-    value = committed_all * w.integ.dt * NS_PER_DAY / t_lsd_max
-    plain_value = _sum_over_ranks(n_plain, world) * w.integ.dt * NS_PER_DAY / _max_over_ranks(t_plain, world)
+    value = whole_job_rate(committed, t_lsd, world) * w.integ.dt * NS_PER_DAY
+    plain_value = whole_job_rate(n_plain, t_plain, world) * w.integ.dt * NS_PER_DAY
 
     # ---- e2e: public per-window calls with host buffers ----
     h.set_state(q_eq, p_eq, step_eq)
@@ -332,7 +339,7 @@ def run_ours(args):
     t_e2e = time.perf_counter() - t0
     stats_b = h.stats()
     e2e_committed = stats_b["committed"] - stats_a["committed"]
-    e2e_val = _sum_over_ranks(e2e_committed, world) * w.integ.dt * NS_PER_DAY / _max_over_ranks(t_e2e, world)
+    e2e_val = whole_job_rate(e2e_committed, t_e2e, world) * w.integ.dt * NS_PER_DAY
     D = 3 * s.n_atoms
 
     rl = roofline(h, w, peaks, peak_kind, pos)
