@@ -187,6 +187,22 @@ def _algorithmic_work(w, phase, q):
     return None
 
 
+def _analysis(st1, st0, rl, K, t_plain_step):
+    """The paper's bounds at the measured operating point (paper_2606_02455_b300.analysis): per-step rejection
+    rate <beta> = rejections / verified steps, cost ratio c = drafted-step time / plain-step time, the pipelined
+    bound 1 / (c + <beta>) (Eq. 8) and the synchronous lookahead-K bound."""
+    from paper_2606_02455_b300 import analysis as A
+    verified = max(st1["verified"] - st0["verified"], 1)
+    beta = (st1["rejected"] - st0["rejected"]) / verified
+    ph = rl["phases_ms"]
+    t_draft = ph["draft"] * 1e-3 / K
+    c = t_draft / t_plain_step
+    return {"beta": round(beta, 5), "c": round(c, 5),
+            "speedup_async_bound": round(float(A.speedup_async(beta, c)), 3),
+            "speedup_sync_bound_K": round(float(A.speedup_sync(beta, c, K)), 3),
+            "expected_committed_per_window": round(float(A.expected_committed(beta, K)), 3)}
+
+
 def roofline(h, w, peaks, peak_kind, q, n_rep=20):
     """Per-phase CUDA-event times of the window (live, on the library's stream), the dominant phase, and its
     achieved rate against the peak that bounds it."""
@@ -361,6 +377,7 @@ def run_ours(args):
                    "draft": "LJ", "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed (256 MB write) between timed windows"},
         "acceptance_rate": round(1.0 - rejected / max(committed, 1), 5),
+        "analysis": _analysis(st1, st0, rl, K, t_plain / n_plain),
         "committed_per_window": round(committed / max(windows, 1), 3),
         "plain_target_ns_per_day": round(plain_value, 3),
         "speedup_vs_plain": round(value / plain_value, 3),
