@@ -75,11 +75,14 @@ typedef struct {
     double shear;
 } o_potential;
 
+enum { O_ABOBA = 0, O_OBABO = 1 };
+
 typedef struct {
     double dt;          /* fs */
     double gamma;       /* 1/fs */
     double temperature; /* K */
     uint64_t seed;
+    int32_t integrator; /* O_ABOBA (Eq. 2), or O_OBABO in the staggered frame of App. E */
 } o_params;
 
 int32_t o_input_dim(int32_t n_species, int32_t n_rbf, int32_t n_ang) {
@@ -641,6 +644,12 @@ typedef struct {
     double aF;     /* (1 + c1) (dt/2) kappa: force -> mean momentum shift */
     double *hm;    /* per species (dt/2)/m */
     double *sig;   /* per species sqrt(m kB T kappa (1 - exp(-2 gamma dt))) */
+    /* OBABO (App. E) */
+    int obabo;
+    double ch;     /* exp(-gamma dt/2): friction of a half-step O */
+    double bF;     /* (dt/2) kappa: one B half-step kick per unit force */
+    double *hmf;   /* per species dt/m: the full-step A of the staggered frame */
+    double *sigh;  /* per species sqrt(m kB T kappa (1 - exp(-gamma dt))): half-step O noise, Sigma_1/2 */
 } o_coef;
 
 static void o_coef_init(const o_system *sys, const o_params *prm, o_coef *c) {
@@ -650,14 +659,22 @@ static void o_coef_init(const o_system *sys, const o_params *prm, o_coef *c) {
     c->aF = (1.0 + c->c1) * c->h * kappa;
     c->hm = (double *)malloc(sizeof(double) * (size_t)sys->n_species);
     c->sig = (double *)malloc(sizeof(double) * (size_t)sys->n_species);
+    c->hmf = (double *)malloc(sizeof(double) * (size_t)sys->n_species);
+    c->sigh = (double *)malloc(sizeof(double) * (size_t)sys->n_species);
+    c->obabo = prm->integrator == O_OBABO;
+    c->ch = exp(-0.5 * prm->gamma * prm->dt);
+    c->bF = c->h * kappa;
     double one_minus = -expm1(-2.0 * prm->gamma * prm->dt);
+    double one_minus_half = -expm1(-prm->gamma * prm->dt);
     for (int s = 0; s < sys->n_species; ++s) {
         double m = sys->species_mass[s];
         c->hm[s] = c->h / m;
         c->sig[s] = sqrt(m * kB * prm->temperature * kappa * one_minus);
+        c->hmf[s] = prm->dt / m;
+        c->sigh[s] = sqrt(m * kB * prm->temperature * kappa * one_minus_half);
     }
 }
-static void o_coef_free(o_coef *c) { free(c->hm); free(c->sig); }
+static void o_coef_free(o_coef *c) { free(c->hm); free(c->sig); free(c->hmf); free(c->sigh); }
 
 /* Exported so tests can see the coefficients the oracle uses. */
 void o_coefficients(const o_system *sys, const o_params *prm, double *c1, double *aF, double *hm, double *sig) {
@@ -689,8 +706,9 @@ static int o_aboba(const o_system *sys, const o_potential *pot, const o_params *
                    double *q_new, double *p_new) {
     int N = sys->n_atoms;
     for (int i = 0; i < N; ++i) {
-        double hm = c->hm[sys->species[i]];
-        for (int a = 0; a < 3; ++a) qmid[3 * i + a] = q[3 * i + a] + p[3 * i + a] * hm;   /* A */
+        /* A: half step of ABOBA, or the full step of the staggered OBABO frame (App. E) */
+        double hm = c->obabo ? c->hmf[sys->species[i]] : c->hm[sys->species[i]];
+        for (int a = 0; a < 3; ++a) qmid[3 * i + a] = q[3 * i + a] + p[3 * i + a] * hm;
     }
     double E = o_energy_forces(sys, pot, qmid, Fraw, NULL, NULL, NULL);
     if (isnan(E)) return -1;
@@ -703,7 +721,7 @@ static int o_aboba(const o_system *sys, const o_potential *pot, const o_params *
             double Fk = dF ? Fraw[k] + dF[k] : Fraw[k];
             mu[k] = c->c1 * p[k] + c->aF * Fk;          /* BOB mean, Eq. 4 */
             p_new[k] = mu[k] + c->sig[s] * xi[a];         /* BOB draw */
-            q_new[k] = qmid[k] + p_new[k] * c->hm[s];     /* A */
+            q_new[k] = c->obabo ? qmid[k] : qmid[k] + p_new[k] * c->hm[s];   /* A (ABOBA); none (staggered OBABO) */
         }
     }
     return 0;
@@ -751,7 +769,7 @@ static o_verdict o_reflection_verify(const o_system *sys, const o_coef *c, doubl
             double dl = (mu_draft[k] - mu_target[k]) / sg;
             p_out[k] = mu_target[k] + sg * (z - 2.0 * (zd / dd) * dl);   /* Householder reflection */
         }
-        q_out[k] = qmid[k] + p_out[k] * c->hm[s];   /* map g = A */
+        q_out[k] = c->obabo ? qmid[k] : qmid[k] + p_out[k] * c->hm[s];   /* map g = A (ABOBA), id (OBABO) */
     }
     return v;
 }
@@ -783,6 +801,111 @@ int o_transport(int32_t D, const double *sig, double u, const double *p_draft, c
 }
 
 /* ------------------------------------------------------------------------- */
+/* OBABO through the staggered frame (App. E)                                  */
+/* ------------------------------------------------------------------------- */
+
+/* The OBABO output momentum of staggered step n (App. E): with the staggered
+ * momenta p_prev (before) and p_new (after) and the step's target force F,
+ * p_in = p_prev + (dt/2) kappa F, and w = Sigma_1/2^-1/2 (p_new - c1 p_prev -
+ * (1 + c1) (dt/2) kappa F) fixes e^(-gamma dt/2) xi1 + xi2.  xi1 is drawn from
+ * its conditional law N(e^(-gamma dt/2) w / (1 + c1), 1 / (1 + c1)) with the
+ * standard normal eta of stream 3 at step n, and p_mid = e^(-gamma dt/2) p_in +
+ * Sigma_1/2^1/2 xi1. */
+static void o_obabo_recover(const o_system *sys, const o_coef *c, uint64_t seed, uint64_t n, const double *p_prev,
+                            const double *F, const double *p_new, double *p_mid) {
+    double a = c->ch / (1.0 + c->c1), b = sqrt(1.0 / (1.0 + c->c1));
+    for (int i = 0; i < sys->n_atoms; ++i) {
+        double eta[3];
+        o_normals(seed, n, (uint32_t)i, 3u, eta);
+        double sh = c->sigh[sys->species[i]];
+        for (int x = 0; x < 3; ++x) {
+            int k = 3 * i + x;
+            double p_in = p_prev[k] + c->bF * F[k];
+            double w = (p_new[k] - c->c1 * p_prev[k] - c->aF * F[k]) / sh;
+            double xi1 = a * w + b * eta[x];
+            p_mid[k] = c->ch * p_in + sh * xi1;
+        }
+    }
+}
+
+void o_obabo_output(const o_system *sys, const o_params *prm, int64_t n, const double *p_prev, const double *F,
+                    const double *p_new, double *p_mid) {
+    o_coef c;
+    o_coef_init(sys, prm, &c);
+    o_obabo_recover(sys, &c, prm->seed, (uint64_t)n, p_prev, F, p_new, p_mid);
+    o_coef_free(&c);
+}
+
+/* Enters the staggered frame from an OBABO state (q, p) at step index n: the
+ * leading O half-step (noise of stream 4 at n) and B half-step at q,
+ * p <- e^(-gamma dt/2) p + Sigma_1/2^1/2 xi + (dt/2) kappa F(q). */
+int o_obabo_enter(const o_system *sys, const o_potential *target, const o_params *prm, int64_t n, const double *q,
+                  double *p) {
+    int D = 3 * sys->n_atoms;
+    o_coef c;
+    o_coef_init(sys, prm, &c);
+    double *F = (double *)malloc(sizeof(double) * (size_t)D);
+    double E = o_energy_forces(sys, target, q, F, NULL, NULL, NULL);
+    int ret = isnan(E) ? -1 : 0;
+    for (int i = 0; i < sys->n_atoms && ret == 0; ++i) {
+        double xi[3];
+        o_normals(prm->seed, (uint64_t)n, (uint32_t)i, 4u, xi);
+        double sh = c.sigh[sys->species[i]];
+        for (int x = 0; x < 3; ++x) {
+            int k = 3 * i + x;
+            p[k] = (c.ch * p[k] + sh * xi[x]) + c.bF * F[k];
+        }
+    }
+    free(F);
+    o_coef_free(&c);
+    return ret;
+}
+
+/* The OBABO integrator written out literally (O, B, A, B, O per step, noise of
+ * streams 5 and 6 at the produced step index), for distribution tests of the
+ * staggered construction.  traj as in o_plain_run. */
+int o_obabo_literal(const o_system *sys, const o_potential *pot, const o_params *prm, int64_t n_steps, double *q,
+                    double *p, int64_t *step, double *traj_q, double *traj_p) {
+    int N = sys->n_atoms, D = 3 * N;
+    o_coef c;
+    o_coef_init(sys, prm, &c);
+    double *F = (double *)malloc(sizeof(double) * (size_t)D);
+    int ret = 0;
+    if (isnan(o_energy_forces(sys, pot, q, F, NULL, NULL, NULL))) ret = -1;
+    for (int64_t t = 0; t < n_steps && ret == 0; ++t) {
+        uint64_t n = (uint64_t)(*step + 1);
+        for (int i = 0; i < N; ++i) {
+            double xi[3];
+            o_normals(prm->seed, n, (uint32_t)i, 5u, xi);
+            int s = sys->species[i];
+            for (int x = 0; x < 3; ++x) {
+                int k = 3 * i + x;
+                p[k] = c.ch * p[k] + c.sigh[s] * xi[x];   /* O */
+                p[k] += c.bF * F[k];                      /* B */
+                q[k] += c.hmf[s] * p[k];                  /* A, full step */
+            }
+        }
+        if (isnan(o_energy_forces(sys, pot, q, F, NULL, NULL, NULL))) { ret = -1; break; }
+        for (int i = 0; i < N; ++i) {
+            double xi[3];
+            o_normals(prm->seed, n, (uint32_t)i, 6u, xi);
+            int s = sys->species[i];
+            for (int x = 0; x < 3; ++x) {
+                int k = 3 * i + x;
+                p[k] += c.bF * F[k];                      /* B */
+                p[k] = c.ch * p[k] + c.sigh[s] * xi[x];   /* O */
+            }
+        }
+        *step += 1;
+        if (traj_q) memcpy(traj_q + (size_t)t * D, q, sizeof(double) * (size_t)D);
+        if (traj_p) memcpy(traj_p + (size_t)t * D, p, sizeof(double) * (size_t)D);
+    }
+    free(F);
+    o_coef_free(&c);
+    return ret;
+}
+
+/* ------------------------------------------------------------------------- */
 /* One synchronous speculative window (Alg. 1 with lookahead L = K), ABOBA     */
 /* draft_step / verify_step of Alg. 2, optional error correction (Alg. 3).    */
 /* ------------------------------------------------------------------------- */
@@ -798,7 +921,7 @@ int o_transport(int32_t D, const double *sig, double u, const double *p_draft, c
 int o_lsd_window(const o_system *sys, const o_potential *draft, const o_potential *target, const o_params *prm,
                  int64_t n0, int32_t K, int32_t max_commit, double *q, double *p, double *ec_dF, double *w_qmid,
                  double *w_pdraft, double *w_mudraft, double *w_Fdraft, double *w_Ftarget, double *w_logr,
-                 double *w_logu, double *w_dnorm, int32_t *w_accept) {
+                 double *w_logu, double *w_dnorm, int32_t *w_accept, double *p_obabo) {
     int N = sys->n_atoms, D = 3 * N;
     o_coef c;
     o_coef_init(sys, prm, &c);
@@ -845,6 +968,12 @@ int o_lsd_window(const o_system *sys, const o_potential *draft, const o_potentia
         for (int j = 0; j < K; ++j) if (!acc[j]) { l = j + 1; break; }
         n_commit = l < max_commit ? l : max_commit;
         int last = n_commit - 1;
+        if (c.obabo && p_obabo) {
+            /* the OBABO output of the last committed step, from its staggered momenta and target force */
+            const double *pprev = last == 0 ? p : pd + (size_t)(last - 1) * D;
+            o_obabo_recover(sys, &c, prm->seed, (uint64_t)(n0 + last + 1), pprev, Ft + (size_t)last * D,
+                            px + (size_t)last * D, p_obabo);
+        }
         memcpy(q, qx + (size_t)last * D, sizeof(double) * (size_t)D);
         memcpy(p, px + (size_t)last * D, sizeof(double) * (size_t)D);
         if (ec_dF)
@@ -869,7 +998,7 @@ int o_lsd_window(const o_system *sys, const o_potential *draft, const o_potentia
  * steps, verified steps.  Returns 0 or < 0. */
 int o_lsd_run(const o_system *sys, const o_potential *draft, const o_potential *target, const o_params *prm,
               int64_t n_steps, int32_t K, int32_t use_ec, double *q, double *p, int64_t *step, double *traj_q,
-              double *traj_p, double *stats) {
+              double *traj_p, double *stats, double *p_obabo) {
     int N = sys->n_atoms, D = 3 * N;
     size_t KD = (size_t)K * D;
     double *pd = (double *)malloc(sizeof(double) * KD);
@@ -879,6 +1008,9 @@ int o_lsd_run(const o_system *sys, const o_potential *draft, const o_potential *
     double *dn = (double *)malloc(sizeof(double) * (size_t)K);
     int32_t *acc = (int32_t *)malloc(sizeof(int32_t) * (size_t)K);
     double *dF = use_ec ? (double *)calloc((size_t)D, sizeof(double)) : NULL;
+    double *Ft = (double *)malloc(sizeof(double) * KD);
+    double *pbase = (double *)malloc(sizeof(double) * (size_t)D);
+    double *pout = (double *)malloc(sizeof(double) * (size_t)D);
     o_coef c;
     o_coef_init(sys, prm, &c);
     double st[6] = {0, 0, 0, 0, 0, 0};
@@ -887,15 +1019,25 @@ int o_lsd_run(const o_system *sys, const o_potential *draft, const o_potential *
     while (done < n_steps) {
         int64_t rem = n_steps - done;
         int32_t kk = (int32_t)(rem < K ? rem : K);
-        int nc = o_lsd_window(sys, draft, target, prm, *step, kk, kk, q, p, dF, qmid, pd, NULL, NULL, NULL, logr,
-                              logu, dn, acc);
+        memcpy(pbase, p, sizeof(double) * (size_t)D);
+        int nc = o_lsd_window(sys, draft, target, prm, *step, kk, kk, q, p, dF, qmid, pd, NULL, NULL, Ft, logr,
+                              logu, dn, acc, pout);
         if (nc < 0) { ret = nc; break; }
         st[0] += 1; st[1] += nc; st[5] += kk;
         for (int j = 0; j < nc; ++j) {
             st[3] += erf(dn[j] / sqrt(8.0));
             st[4] += dn[j];
             if (!acc[j]) st[2] += 1;
-            if (traj_q || traj_p) {
+            if ((traj_q || traj_p) && c.obabo) {
+                /* OBABO outputs: positions of the staggered states, recovered momenta */
+                size_t off = (size_t)(done + j) * D;
+                const double *pprev = j == 0 ? pbase : pd + (size_t)(j - 1) * D;
+                const double *pnew = j == nc - 1 ? p : pd + (size_t)j * D;
+                if (traj_q) memcpy(traj_q + off, j == nc - 1 ? q : qmid + (size_t)j * D, sizeof(double) * (size_t)D);
+                if (traj_p)
+                    o_obabo_recover(sys, &c, prm->seed, (uint64_t)(*step + j + 1), pprev, Ft + (size_t)j * D, pnew,
+                                    traj_p + off);
+            } else if (traj_q || traj_p) {
                 size_t off = (size_t)(done + j) * D;
                 if (j == nc - 1) {
                     if (traj_q) memcpy(traj_q + off, q, sizeof(double) * (size_t)D);
@@ -911,9 +1053,10 @@ int o_lsd_run(const o_system *sys, const o_potential *draft, const o_potential *
         }
         done += nc;
         *step += nc;
+        if (p_obabo && c.obabo) memcpy(p_obabo, pout, sizeof(double) * (size_t)D);
     }
     if (stats) memcpy(stats, st, sizeof(st));
-    free(pd); free(qmid); free(logr); free(logu); free(dn); free(acc); free(dF);
+    free(pd); free(qmid); free(logr); free(logu); free(dn); free(acc); free(dF); free(Ft); free(pbase); free(pout);
     o_coef_free(&c);
     return ret;
 }
@@ -921,7 +1064,7 @@ int o_lsd_run(const o_system *sys, const o_potential *draft, const o_potential *
 /* Plain target Langevin: n_steps ABOBA steps with the target force field, noise
  * keyed by the step index exactly as in the draft.  traj as in o_lsd_run. */
 int o_plain_run(const o_system *sys, const o_potential *target, const o_params *prm, int64_t n_steps, double *q,
-                double *p, int64_t *step, double *traj_q, double *traj_p) {
+                double *p, int64_t *step, double *traj_q, double *traj_p, double *p_obabo) {
     int D = 3 * sys->n_atoms;
     o_coef c;
     o_coef_init(sys, prm, &c);
@@ -930,19 +1073,24 @@ int o_plain_run(const o_system *sys, const o_potential *target, const o_params *
     double *mu = (double *)malloc(sizeof(double) * (size_t)D);
     double *qn = (double *)malloc(sizeof(double) * (size_t)D);
     double *pn = (double *)malloc(sizeof(double) * (size_t)D);
+    double *pm = (double *)malloc(sizeof(double) * (size_t)D);
     int ret = 0;
     for (int64_t t = 0; t < n_steps; ++t) {
         if (o_aboba(sys, target, prm, &c, (uint64_t)(*step + 1), q, p, NULL, qmid, F, mu, qn, pn) != 0) {
             ret = -1;
             break;
         }
+        if (c.obabo) {   /* OBABO output of this step (App. E) */
+            o_obabo_recover(sys, &c, prm->seed, (uint64_t)(*step + 1), p, F, pn, pm);
+            if (p_obabo) memcpy(p_obabo, pm, sizeof(double) * (size_t)D);
+        }
         memcpy(q, qn, sizeof(double) * (size_t)D);
         memcpy(p, pn, sizeof(double) * (size_t)D);
         *step += 1;
         if (traj_q) memcpy(traj_q + (size_t)t * D, q, sizeof(double) * (size_t)D);
-        if (traj_p) memcpy(traj_p + (size_t)t * D, p, sizeof(double) * (size_t)D);
+        if (traj_p) memcpy(traj_p + (size_t)t * D, c.obabo ? pm : p, sizeof(double) * (size_t)D);
     }
-    free(qmid); free(F); free(mu); free(qn); free(pn);
+    free(qmid); free(F); free(mu); free(qn); free(pn); free(pm);
     o_coef_free(&c);
     return ret;
 }

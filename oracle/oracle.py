@@ -58,7 +58,7 @@ class _Pot(ctypes.Structure):
 
 class _Prm(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("gamma", ctypes.c_double), ("temperature", ctypes.c_double),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("integrator", ctypes.c_int32)]
 
 
 def _L():
@@ -81,9 +81,12 @@ def _L():
                 "o_coefficients": (None, [P, P, P, P, P, P]),
                 "o_mb_momenta": (None, [P, P, P]),
                 "o_transport": (ctypes.c_int, [I32, P, D, P, P, P, P, P]),
-                "o_lsd_window": (ctypes.c_int, [P, P, P, P, I64, I32, I32, P, P, P, P, P, P, P, P, P, P, P, P]),
-                "o_lsd_run": (ctypes.c_int, [P, P, P, P, I64, I32, I32, P, P, P, P, P, P]),
-                "o_plain_run": (ctypes.c_int, [P, P, P, I64, P, P, P, P, P]),
+                "o_lsd_window": (ctypes.c_int, [P, P, P, P, I64, I32, I32, P, P, P, P, P, P, P, P, P, P, P, P, P]),
+                "o_lsd_run": (ctypes.c_int, [P, P, P, P, I64, I32, I32, P, P, P, P, P, P, P]),
+                "o_plain_run": (ctypes.c_int, [P, P, P, I64, P, P, P, P, P, P]),
+                "o_obabo_output": (None, [P, P, I64, P, P, P, P]),
+                "o_obabo_enter": (ctypes.c_int, [P, P, P, I64, P, P]),
+                "o_obabo_literal": (ctypes.c_int, [P, P, P, I64, P, P, P, P, P]),
                 "o_force_match": (D, [P, P, I32, P, P, P]),
                 "o_forces_subset": (ctypes.c_int, [P, P, P, I32, P, P]),
             }
@@ -144,12 +147,16 @@ def _cpot(pot, keep):
     return p
 
 
+SCHEMES = {"aboba": 0, "obabo": 1}
+
+
 def _cprm(integ, seed):
     p = _Prm()
     p.dt = float(integ.dt)
     p.gamma = float(integ.gamma)
     p.temperature = float(integ.temperature)
     p.seed = int(seed)
+    p.integrator = SCHEMES[getattr(integ, "scheme", "aboba")]
     return p
 
 
@@ -303,14 +310,16 @@ def lsd_window(system, draft, target, integ, seed, n0, K, q, p, ec_dF=None, max_
     logr, logu, dn = np.zeros(K), np.zeros(K), np.zeros(K)
     acc = np.zeros(K, dtype=np.int32)
     mc = K if max_commit is None else int(max_commit)
+    pob = np.zeros((N, 3))
     nc = _L().o_lsd_window(ctypes.byref(s), ctypes.byref(pd_), ctypes.byref(pt_), ctypes.byref(prm), int(n0), int(K),
                            mc, _ptr(qq), _ptr(pp), _ptr(dF), _ptr(arrs["qmid"]), _ptr(arrs["pdraft"]),
                            _ptr(arrs["mudraft"]), _ptr(arrs["Fdraft"]), _ptr(arrs["Ftarget"]), _ptr(logr), _ptr(logu),
-                           _ptr(dn), _ptr(acc))
+                           _ptr(dn), _ptr(acc), _ptr(pob))
     if nc < 0:
         raise RuntimeError("oracle window failed (%d)" % nc)
     out = dict(arrs)
-    out.update(n_committed=nc, q=qq, p=pp, logr=logr, logu=logu, delta_norm=dn, accept=acc.astype(bool), ec_dF=dF)
+    out.update(n_committed=nc, q=qq, p=pp, logr=logr, logu=logu, delta_norm=dn, accept=acc.astype(bool), ec_dF=dF,
+               p_obabo=pob)
     return out
 
 
@@ -327,12 +336,14 @@ def lsd_run(system, draft, target, integ, seed, n_steps, K, q, p, step=0, use_ec
     tq = np.zeros((n_steps, N, 3)) if traj else None
     tp = np.zeros((n_steps, N, 3)) if traj else None
     stats = np.zeros(6)
+    pob = np.zeros((N, 3))
     r = _L().o_lsd_run(ctypes.byref(s), ctypes.byref(pd_), ctypes.byref(pt_), ctypes.byref(prm), int(n_steps), int(K),
-                       int(bool(use_ec)), _ptr(qq), _ptr(pp), ctypes.byref(st), _ptr(tq), _ptr(tp), _ptr(stats))
+                       int(bool(use_ec)), _ptr(qq), _ptr(pp), ctypes.byref(st), _ptr(tq), _ptr(tp), _ptr(stats),
+                       _ptr(pob))
     if r != 0:
         raise RuntimeError("oracle LSD run failed (%d)" % r)
     keys = ("windows", "committed", "rejected", "pred_rejected", "sum_delta", "verified")
-    return dict(q=qq, p=pp, step=st.value, traj_q=tq, traj_p=tp, stats=dict(zip(keys, stats.tolist())))
+    return dict(q=qq, p=pp, step=st.value, traj_q=tq, traj_p=tp, stats=dict(zip(keys, stats.tolist())), p_obabo=pob)
 
 
 def plain_run(system, target, integ, seed, n_steps, q, p, step=0, traj=False):
@@ -346,10 +357,59 @@ def plain_run(system, target, integ, seed, n_steps, q, p, step=0, traj=False):
     st = ctypes.c_int64(int(step))
     tq = np.zeros((n_steps, N, 3)) if traj else None
     tp = np.zeros((n_steps, N, 3)) if traj else None
+    pob = np.zeros((N, 3))
     r = _L().o_plain_run(ctypes.byref(s), ctypes.byref(pt_), ctypes.byref(prm), int(n_steps), _ptr(qq), _ptr(pp),
-                         ctypes.byref(st), _ptr(tq), _ptr(tp))
+                         ctypes.byref(st), _ptr(tq), _ptr(tp), _ptr(pob))
     if r != 0:
         raise RuntimeError("oracle plain run failed (%d)" % r)
+    return dict(q=qq, p=pp, step=st.value, traj_q=tq, traj_p=tp, p_obabo=pob)
+
+
+# ----------------------------------------------------------------------------------------------
+# OBABO in the staggered frame (App. E)
+# ----------------------------------------------------------------------------------------------
+
+def obabo_output(system, integ, seed, n, p_prev, F, p_new):
+    """The OBABO output momentum of staggered step n from the staggered momenta around it and its target force."""
+    keep = _Keep()
+    s = _csys(system, keep)
+    prm = _cprm(integ, seed)
+    out = np.zeros_like(np.asarray(p_new, np.float64))
+    _L().o_obabo_output(ctypes.byref(s), ctypes.byref(prm), int(n), _ptr(keep.arr(p_prev, np.float64)),
+                        _ptr(keep.arr(F, np.float64)), _ptr(keep.arr(p_new, np.float64)), _ptr(out))
+    return out
+
+
+def obabo_enter(system, target, integ, seed, n, q, p):
+    """The staggered momentum OB(q, p) of an OBABO state at step index n."""
+    keep = _Keep()
+    s = _csys(system, keep)
+    pt_ = _cpot(target, keep)
+    prm = _cprm(integ, seed)
+    pp = np.array(p, dtype=np.float64).copy()
+    r = _L().o_obabo_enter(ctypes.byref(s), ctypes.byref(pt_), ctypes.byref(prm), int(n),
+                           _ptr(keep.arr(q, np.float64)), _ptr(pp))
+    if r != 0:
+        raise RuntimeError("oracle OB step failed (%d)" % r)
+    return pp
+
+
+def obabo_literal(system, pot, integ, seed, n_steps, q, p, step=0, traj=False):
+    """OBABO written out literally (O B A B O), for distribution tests of the staggered construction."""
+    keep = _Keep()
+    s = _csys(system, keep)
+    pt_ = _cpot(pot, keep)
+    prm = _cprm(integ, seed)
+    N = system.n_atoms
+    qq = np.array(q, dtype=np.float64).reshape(N, 3).copy()
+    pp = np.array(p, dtype=np.float64).reshape(N, 3).copy()
+    st = ctypes.c_int64(int(step))
+    tq = np.zeros((n_steps, N, 3)) if traj else None
+    tp = np.zeros((n_steps, N, 3)) if traj else None
+    r = _L().o_obabo_literal(ctypes.byref(s), ctypes.byref(pt_), ctypes.byref(prm), int(n_steps), _ptr(qq), _ptr(pp),
+                             ctypes.byref(st), _ptr(tq), _ptr(tp))
+    if r != 0:
+        raise RuntimeError("oracle literal OBABO failed (%d)" % r)
     return dict(q=qq, p=pp, step=st.value, traj_q=tq, traj_p=tp)
 
 

@@ -85,6 +85,7 @@ class Integrator:
     gamma: float
     temperature: float
     K: int
+    scheme: str = "aboba"   # "aboba" (Eq. 2) or "obabo" (the staggered frame of App. E)
 
 
 @dataclass
