@@ -204,6 +204,25 @@ LSD_API int lsd_set_draft_weights(lsd_handle *h, const float *weights, size_t n_
 /* lsd_get_draft_weights: copy the current draft weights (packed float32). */
 LSD_API int lsd_get_draft_weights(const lsd_handle *h, float *weights, size_t n_weights);
 
+/* lsd_set_integrator: the Langevin splitting of the chain.
+ *   LSD_ABOBA (default): Eq. 2; the state is (q, p) after a full ABOBA step.
+ *   LSD_OBABO: App. E.  The chain runs in the staggered frame, whose transition
+ *     is a full-step A (q += dt p/m) followed by the BOB Gaussian of Eq. 4 at
+ *     the new position, verified and transported exactly as for ABOBA.  The
+ *     OBABO output momentum of every committed step is recovered from the
+ *     staggered momenta around it and its (already verified) target force, by
+ *     drawing the first half-step noise from its conditional law (Philox
+ *     stream 3 at the step index); positions are the staggered ones.  Entering
+ *     the frame from an OBABO state (q, p) at step n applies the leading O and
+ *     B half-steps (stream 4 at n), which costs one target force evaluation.
+ * Switching to LSD_OBABO takes the current state as an OBABO state; switching
+ * back takes the current OBABO output state as the ABOBA state.  Under
+ * LSD_OBABO, lsd_get_state returns the OBABO output (q, p) and lsd_set_state
+ * takes one (and enters the frame).  Returns LSD_EINVAL for another value. */
+#define LSD_ABOBA 0
+#define LSD_OBABO 1
+LSD_API int lsd_set_integrator(lsd_handle *h, int32_t scheme);
+
 /* lsd_set_error_correction: speculative error correction (Alg. 3) on (1) or
  * off (0).  On: the draft mean uses F~ + dF, where dF = F - F~raw of the last
  * committed step; switching on clears dF. */
@@ -252,10 +271,12 @@ LSD_API int lsd_descriptors(const lsd_handle *h, int32_t n_configs, float *X, fl
 LSD_API int lsd_get_window(const lsd_handle *h, double *q_mid, double *p_draft, float *F_draft, float *F_target,
                    double *log_ratio, double *log_u, double *delta_norm, int32_t *accept);
 
-/* lsd_checkpoint: serialise the full dynamical state (positions, momenta, step,
- * seed, error-correction cache, draft weights and optimiser moments) into buf;
- * with buf == NULL only *len is set.  lsd_restore reads it back into a handle
- * built with the same system and potentials. */
+/* lsd_checkpoint: serialise the full dynamical state (positions, the chain's
+ * momenta -- staggered under LSD_OBABO -- and the OBABO output momenta, step,
+ * seed, integrator, error-correction cache, draft weights and optimiser
+ * moments) into buf; with buf == NULL only *len is set.  lsd_restore reads it
+ * back into a handle built with the same system and potentials, without
+ * re-entering the OBABO frame, so a restored run continues bit for bit. */
 LSD_API int lsd_checkpoint(const lsd_handle *h, void *buf, size_t *len);
 LSD_API int lsd_restore(lsd_handle *h, const void *buf, size_t len);
 

@@ -68,6 +68,7 @@ struct lsd_handle {
     std::vector<double> mass_h;
     Geo geo{};
     Coef coef{};
+    double *p_obabo = nullptr;   // OBABO output momenta of the current step (staggered frame: p is the staggered one)
     PotHost draft, target;
     bool learned_small = false;
     DraftPlan dplan{};
@@ -399,14 +400,14 @@ void enqueue_verify(lsd_handle *h, cudaStream_t s) {
     enqueue_eval(h, h->target, h->w_fix, h->K, h->w_Ft, nullptr, s, !h->vplan.all_pairs);
     if (h->train.capture_on) enqueue_frame_capture(h->train, h->w_qmid, h->w_Ft, h->K, h->N, h->st, s);
     launch_transport(h->K, h->geo, h->coef, h->species, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Ft, h->w_Fraw, h->ec_dF,
-                     h->ec_on, h->q, h->p, h->st, h->partials, h->logu, s);
+                     h->ec_on, h->q, h->p, h->p_obabo, h->st, h->partials, h->logu, s);
 }
 
 void enqueue_plain(lsd_handle *h, cudaStream_t s) {
     if (!h->vplan.all_pairs) launch_verlet_build(h->vplan, h->q, h->species, h->geo, h->vbufs, h->st, s);
     launch_plain_half(h->geo, h->coef, h->species, h->q, h->p, h->st, h->w_qmid, h->w_fix, s);
     enqueue_eval(h, h->target, h->w_fix, 1, h->w_Ft, nullptr, s, !h->vplan.all_pairs);
-    launch_plain_finish(h->geo, h->coef, h->species, h->w_qmid, h->w_Ft, h->q, h->p, h->st, s);
+    launch_plain_finish(h->geo, h->coef, h->species, h->w_qmid, h->w_Ft, h->q, h->p, h->p_obabo, h->st, s);
 }
 
 void destroy_graphs(lsd_handle *h) {
@@ -461,6 +462,22 @@ int check_err(const DevState &s) {
     if (s.err & 1) return LSD_EOVERFLOW;
     if (s.err & 4) return LSD_ESTATE;
     return LSD_OK;
+}
+
+// p <- OB(q, p_obabo) at step index n: target forces at q, then the leading
+// O and B half-steps of the staggered frame (App. E).
+int obabo_enter(lsd_handle *h, long long n) {
+    const size_t D = 3 * (size_t)h->N;
+    cudaStream_t s = h->stream;
+    CK(cudaMemcpyAsync(h->p, h->p_obabo, D * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    launch_fixpoint(h->q, h->species, h->N, h->geo, h->fix_eval, s);
+    enqueue_eval(h, h->target, h->fix_eval, 1, h->w_Ft, nullptr, s);
+    launch_obabo_enter(h->geo, h->coef, h->species, h->w_Ft, n, h->p, s);
+    CK(cudaGetLastError());
+    TRY(wait_stream(h));
+    DevState st;
+    TRY(read_state(h, &st));
+    return check_err(st);
 }
 
 // FP8 potentials: the activation and gradient scales, once per handle.  The
@@ -593,6 +610,18 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         c.aF_sig[s] = c.sig[s] > 0 ? c.aF / c.sig[s] : 0.0;
     }
     c.seed = h->seed;
+    // App. E: the staggered OBABO frame (used after lsd_set_integrator(h, LSD_OBABO))
+    c.obabo = 0;
+    c.ch = std::exp(-0.5 * gamma * dt);
+    c.bF = hh * kap;
+    c.ob_a = c.ch / (1.0 + c.c1);
+    c.ob_b = std::sqrt(1.0 / (1.0 + c.c1));
+    const double one_minus_half = -std::expm1(-gamma * dt);
+    for (int s = 0; s < h->S; ++s) {
+        const double m = h->mass_h[s];
+        c.hmf[s] = dt / m;
+        c.sigh[s] = std::sqrt(m * kB * T * kap * one_minus_half);
+    }
     if ((rc = pot_setup(h, h->draft, draft, true)) != LSD_OK) return fail(rc);
     if ((rc = pot_setup(h, h->target, target, false)) != LSD_OK) return fail(rc);
     h->learned_small = h->draft.dev.has_mlp;
@@ -643,7 +672,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     }
     const size_t N = h->N, D = 3 * N, KN = (size_t)K * N, KD = (size_t)K * D;
     const int dmax = std::max(h->draft.dev.d0p, h->target.dev.d0p);
-    if ((rc = dalloc(h, &h->q, D)) || (rc = dalloc(h, &h->p, D)) || (rc = dalloc(h, &h->species, N)) ||
+    if ((rc = dalloc(h, &h->q, D)) || (rc = dalloc(h, &h->p, D)) || (rc = dalloc(h, &h->p_obabo, D)) || (rc = dalloc(h, &h->species, N)) ||
         (rc = dalloc(h, &h->st, 1)) || (rc = dalloc(h, &h->w_qmid, KD)) || (rc = dalloc(h, &h->w_pdraft, KD)) ||
         (rc = dalloc(h, &h->w_Fd, KD)) || (rc = dalloc(h, &h->w_Fraw, KD)) || (rc = dalloc(h, &h->w_Ft, KD)) ||
         (rc = dalloc(h, &h->w_fix, KN)) || (rc = dalloc(h, &h->fix_eval, KN)) || (rc = dalloc(h, &h->ec_dF, D)) ||
@@ -838,7 +867,8 @@ int lsd_get_state(const lsd_handle *hc, double *pos, double *mom, int64_t *step)
     lsd_handle *h = const_cast<lsd_handle *>(hc);
     const size_t D = 3 * (size_t)h->N;
     if (pos) CK(cudaMemcpyAsync(pos, h->q, D * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    if (mom) CK(cudaMemcpyAsync(mom, h->p, D * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    const double *pm = h->coef.obabo ? h->p_obabo : h->p;   // OBABO: the recovered output momentum
+    if (mom) CK(cudaMemcpyAsync(mom, pm, D * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     long long st = 0;
     CK(cudaMemcpyAsync(&st, &h->st->step, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
     TRY(wait_stream(h));
@@ -850,11 +880,36 @@ int lsd_set_state(lsd_handle *h, const double *pos, const double *mom, int64_t s
     if (!h || step < 0) return LSD_EINVAL;
     const size_t D = 3 * (size_t)h->N;
     if (pos) CK(cudaMemcpyAsync(h->q, pos, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    if (mom) CK(cudaMemcpyAsync(h->p, mom, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (mom) CK(cudaMemcpyAsync(h->coef.obabo ? h->p_obabo : h->p, mom, D * sizeof(double), cudaMemcpyHostToDevice,
+                                h->stream));
     long long st = step;
     CK(cudaMemcpyAsync(&h->st->step, &st, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
     TRY(wait_stream(h));
     h->drafted = false;
+    if (h->coef.obabo) TRY(obabo_enter(h, step));   // the staggered momentum of the given OBABO state
+    return LSD_OK;
+}
+
+int lsd_set_integrator(lsd_handle *h, int32_t scheme) {
+    if (!h || (scheme != LSD_ABOBA && scheme != LSD_OBABO)) return LSD_EINVAL;
+    const int want = scheme == LSD_OBABO ? 1 : 0;
+    if (want == h->coef.obabo) return LSD_OK;
+    const size_t D = 3 * (size_t)h->N;
+    DevState s;
+    TRY(read_state(h, &s));
+    destroy_graphs(h);   // the kernels take the coefficients by value at capture
+    h->drafted = false;
+    if (want) {
+        // the current state is an OBABO state y; the chain continues from OB(y)
+        CK(cudaMemcpyAsync(h->p_obabo, h->p, D * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        h->coef.obabo = 1;
+        TRY(obabo_enter(h, s.step));
+    } else {
+        // the current OBABO output state becomes the ABOBA state
+        CK(cudaMemcpyAsync(h->p, h->p_obabo, D * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        h->coef.obabo = 0;
+        TRY(wait_stream(h));
+    }
     return LSD_OK;
 }
 
@@ -1007,7 +1062,7 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
     launch_transport_reduce(h->K, h->geo, h->coef, h->species, h->w_Fd, h->w_Ft, h->st, h->partials, h->logu, st);
     CK(cudaEventRecord(ev[7], st));
     launch_transport_commit(h->K, h->geo, h->coef, h->species, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Ft, h->w_Fraw,
-                            h->ec_dF, h->ec_on, h->q, h->p, h->st, h->partials, h->logu, st);
+                            h->ec_dF, h->ec_on, h->q, h->p, h->p_obabo, h->st, h->partials, h->logu, st);
     CK(cudaEventRecord(ev[8], st));
     CK(cudaGetLastError());
     TRY(wait_stream(h));
@@ -1044,11 +1099,12 @@ int lsd_query(const lsd_handle *h, int32_t *K, int32_t *n_atoms, int32_t *d_in, 
 
 // ---- checkpoint / restore -------------------------------------------------
 namespace {
-constexpr uint64_t kCkptMagic = 0x4c53444350543031ull;   // "LSDCPT01"
+constexpr uint64_t kCkptMagic = 0x4c53444350543032ull;   // "LSDCPT02"
 struct CkptHeader {
     uint64_t magic;
     int64_t n_atoms, K, step, ec_on, n_weights, n_adam;
     uint64_t seed;
+    int64_t integrator;   // LSD_ABOBA / LSD_OBABO
 };
 }  // namespace
 
@@ -1058,7 +1114,8 @@ int lsd_checkpoint(const lsd_handle *hc, void *buf, size_t *len) {
     const size_t D = 3 * (size_t)h->N;
     const size_t nw = h->draft.weights.size();
     const size_t nadam = train_adam_size(h->train);
-    const size_t need = sizeof(CkptHeader) + 2 * D * sizeof(double) + D * sizeof(float) + nw * sizeof(float) +
+    // q, p (the chain's own momentum: staggered under OBABO), EC cache, draft weights, Adam moments, OBABO output
+    const size_t need = sizeof(CkptHeader) + 3 * D * sizeof(double) + D * sizeof(float) + nw * sizeof(float) +
                         2 * nadam * sizeof(float);
     if (!buf) {
         *len = need;
@@ -1076,18 +1133,24 @@ int lsd_checkpoint(const lsd_handle *hc, void *buf, size_t *len) {
     hd.n_weights = (int64_t)nw;
     hd.n_adam = (int64_t)nadam;
     hd.seed = h->seed;
+    hd.integrator = h->coef.obabo ? LSD_OBABO : LSD_ABOBA;
     char *o = (char *)buf;
-    int64_t step = 0;
-    TRY(lsd_get_state(h, (double *)(o + sizeof(CkptHeader)), (double *)(o + sizeof(CkptHeader)) + D, &step));
-    hd.step = step;
+    DevState s;
+    TRY(read_state(h, &s));
+    hd.step = s.step;
     std::memcpy(o, &hd, sizeof(hd));
+    double *qs = (double *)(o + sizeof(CkptHeader));
+    CK(cudaMemcpyAsync(qs, h->q, D * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(qs + D, h->p, D * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     char *p = o + sizeof(CkptHeader) + 2 * D * sizeof(double);
     CK(cudaMemcpyAsync(p, h->ec_dF, D * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
-    TRY(wait_stream(h));
     p += D * sizeof(float);
     if (nw) std::memcpy(p, h->draft.weights.data(), nw * sizeof(float));
     p += nw * sizeof(float);
     TRY(train_adam_get(h->train, (float *)p, (float *)p + nadam));
+    p += 2 * nadam * sizeof(float);
+    CK(cudaMemcpyAsync(p, h->p_obabo, D * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    TRY(wait_stream(h));
     *len = need;
     return LSD_OK;
 }
@@ -1100,11 +1163,22 @@ int lsd_restore(lsd_handle *h, const void *buf, size_t len) {
     if (hd.magic != kCkptMagic || hd.n_atoms != h->N || hd.seed != h->seed ||
         hd.n_weights != (int64_t)h->draft.weights.size() || hd.n_adam != (int64_t)train_adam_size(h->train))
         return LSD_EINVAL;
-    const size_t need = sizeof(CkptHeader) + 2 * D * sizeof(double) + D * sizeof(float) +
+    const size_t need = sizeof(CkptHeader) + 3 * D * sizeof(double) + D * sizeof(float) +
                         (size_t)hd.n_weights * sizeof(float) + 2 * (size_t)hd.n_adam * sizeof(float);
-    if (len < need) return LSD_EINVAL;
+    if (len < need || (hd.integrator != LSD_ABOBA && hd.integrator != LSD_OBABO)) return LSD_EINVAL;
     const char *o = (const char *)buf + sizeof(CkptHeader);
-    TRY(lsd_set_state(h, (const double *)o, (const double *)o + D, hd.step));
+    // the chain's own state, as saved (no re-entry into the OBABO frame)
+    CK(cudaMemcpyAsync(h->q, o, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->p, (const double *)o + D, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    const long long stp = hd.step;
+    CK(cudaMemcpyAsync(&h->st->step, &stp, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+    h->drafted = false;
+    h->coef.obabo = hd.integrator == LSD_OBABO ? 1 : 0;
+    {
+        const char *po = o + 2 * D * sizeof(double) + D * sizeof(float) + (size_t)hd.n_weights * sizeof(float) +
+                         2 * (size_t)hd.n_adam * sizeof(float);
+        CK(cudaMemcpyAsync(h->p_obabo, po, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    }
     const char *p = o + 2 * D * sizeof(double);
     CK(cudaMemcpyAsync(h->ec_dF, p, D * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     TRY(wait_stream(h));

@@ -65,6 +65,13 @@ struct Coef {
     double sig[kMaxSpecies];    // sqrt(m kB T kappa (1 - exp(-2 gamma dt)))
     double aF_sig[kMaxSpecies]; // aF / sig
     uint64_t seed;
+    // OBABO through the staggered frame (App. E)
+    int obabo;                  // 0: ABOBA; 1: staggered OBABO (full-step A, no trailing A)
+    double ch;                  // exp(-gamma dt / 2)
+    double bF;                  // (dt/2) kappa: one B half-step per unit force
+    double ob_a, ob_b;          // conditional law of the first half-step noise: mean ch / (1 + c1) w, sd sqrt(1/(1+c1))
+    double hmf[kMaxSpecies];    // dt / m
+    double sigh[kMaxSpecies];   // sqrt(m kB T kappa (1 - exp(-gamma dt)))
 };
 
 // Device-resident run state.  step is the index of the base state.
@@ -151,6 +158,18 @@ __device__ __forceinline__ const float *layer_bias(const PotDev &P, int l) {
 #pragma unroll
     for (int k = 1; k < kMaxLayers; ++k) b = l == k ? P.b[k] : b;
     return b;
+}
+
+// The OBABO output momentum of one coordinate of a staggered step (App. E):
+// p_in = p_prev + (dt/2) kappa F; w = (p_new - c1 p_prev - (1 + c1)(dt/2) kappa F) / s_half;
+// xi1 = ch/(1+c1) w + sqrt(1/(1+c1)) eta; p_mid = ch p_in + s_half xi1.
+__device__ __forceinline__ double obabo_output(const Coef &cf, int sp, double pprev, double F, double pnew,
+                                              double eta) {
+    const double sh = species_pick(cf.sigh, sp);
+    const double p_in = pprev + cf.bF * F;
+    const double w = (pnew - cf.c1 * pprev - cf.aF * F) / sh;
+    const double xi1 = cf.ob_a * w + cf.ob_b * eta;
+    return cf.ch * p_in + sh * xi1;
 }
 
 __device__ __forceinline__ float dist2_rule(float dx, float dy, float dz) {

@@ -271,18 +271,19 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
             const int sp = own ? species[i] : 0;
             uint32_t u = 0u;
             if (own && x < 3) {
-                const double hm = species_pick(cf.hm, sp);
+                // ABOBA: trailing A of the previous step, then A; staggered OBABO: one full-step A
+                const double hm = cf.obabo ? species_pick(cf.hmf, sp) : species_pick(cf.hm, sp);
                 double qv, pv;
                 if (REG) {
                     pv = preg;
-                    qv = j == 0 ? qreg : __dadd_rn(qreg, __dmul_rn(pv, hm));
+                    qv = (j == 0 || cf.obabo) ? qreg : __dadd_rn(qreg, __dmul_rn(pv, hm));
                 } else if (j == 0) {
                     qv = q_base[3 * i + x];
                     pv = p_base[3 * i + x];
                 } else {
                     const size_t o = (size_t)(j - 1) * D + 3 * i + x;
                     pv = w_pdraft[o];
-                    qv = __dadd_rn(w_qmid[o], __dmul_rn(pv, hm));
+                    qv = cf.obabo ? w_qmid[o] : __dadd_rn(w_qmid[o], __dmul_rn(pv, hm));
                 }
                 const double qm = __dadd_rn(qv, __dmul_rn(pv, hm));
                 if (REG) qreg = qm;
@@ -572,7 +573,7 @@ __global__ void plain_half_kernel(Geo g, Coef cf, const int *__restrict__ specie
     if (st->step >= st->target_step || i >= g.N) return;
     if (i == 0) st->k_eff = 1;   // one step, always inside the lists' skin
     const int sp = species[i];
-    const double hm = species_pick(cf.hm, sp);
+    const double hm = cf.obabo ? species_pick(cf.hmf, sp) : species_pick(cf.hm, sp);
     uint32_t u0, u1, u2;
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
@@ -586,7 +587,7 @@ __global__ void plain_half_kernel(Geo g, Coef cf, const int *__restrict__ specie
 
 __global__ void plain_finish_kernel(Geo g, Coef cf, const int *__restrict__ species, const double *__restrict__ qmid,
                                     const float *__restrict__ F, double *__restrict__ q, double *__restrict__ p,
-                                    DevState *__restrict__ st) {
+                                    double *__restrict__ p_obabo, DevState *__restrict__ st) {
     __shared__ bool s_last;
     if (st->step >= st->target_step) return;
     const long long n0 = st->step;
@@ -598,10 +599,17 @@ __global__ void plain_finish_kernel(Geo g, Coef cf, const int *__restrict__ spec
         for (int x = 0; x < 3; ++x) {
             const int o = 3 * i + x;
             const float xx = x == 0 ? xi.x : (x == 1 ? xi.y : xi.z);
-            const double mu = __dadd_rn(__dmul_rn(cf.c1, p[o]), __dmul_rn(cf.aF, (double)F[o]));
+            const double pprev = p[o];
+            const double mu = __dadd_rn(__dmul_rn(cf.c1, pprev), __dmul_rn(cf.aF, (double)F[o]));
             const double pn = __dadd_rn(mu, __dmul_rn(species_pick(cf.sig, sp), (double)xx));
             p[o] = pn;
-            q[o] = __dadd_rn(qmid[o], __dmul_rn(pn, species_pick(cf.hm, sp)));
+            if (cf.obabo) {
+                q[o] = qmid[o];
+                const float3 eta = normals3(cf.seed, (unsigned long long)(n0 + 1), (uint32_t)i, 3u);
+                p_obabo[o] = obabo_output(cf, sp, pprev, (double)F[o], pn, x == 0 ? eta.x : (x == 1 ? eta.y : eta.z));
+            } else {
+                q[o] = __dadd_rn(qmid[o], __dmul_rn(pn, species_pick(cf.hm, sp)));
+            }
         }
     }
     __threadfence();
@@ -621,8 +629,31 @@ void launch_plain_half(const Geo &g, const Coef &cf, const int *species, const d
 }
 
 void launch_plain_finish(const Geo &g, const Coef &cf, const int *species, const double *qmid, const float *F,
-                         double *q, double *p, DevState *st, cudaStream_t s) {
-    plain_finish_kernel<<<(g.N + 255) / 256, 256, 0, s>>>(g, cf, species, qmid, F, q, p, st);
+                         double *q, double *p, double *p_obabo, DevState *st, cudaStream_t s) {
+    plain_finish_kernel<<<(g.N + 255) / 256, 256, 0, s>>>(g, cf, species, qmid, F, q, p, p_obabo, st);
+}
+
+// Enters the staggered OBABO frame from an OBABO state at step index n: the
+// leading O half-step (noise stream 4 at n) and B half-step with the target
+// force F at q, p <- (e^(-gamma dt/2) p + Sigma_1/2^1/2 xi) + (dt/2) kappa F.
+__global__ void obabo_enter_kernel(Geo g, Coef cf, const int *__restrict__ species, const float *__restrict__ F,
+                                   long long n, double *__restrict__ p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    const int sp = species[i];
+    const float3 xi = normals3(cf.seed, (unsigned long long)n, (uint32_t)i, 4u);
+    const double sh = species_pick(cf.sigh, sp);
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        const int o = 3 * i + x;
+        const double xx = x == 0 ? xi.x : (x == 1 ? xi.y : xi.z);
+        p[o] = __dadd_rn(__dadd_rn(__dmul_rn(cf.ch, p[o]), __dmul_rn(sh, xx)), __dmul_rn(cf.bF, (double)F[o]));
+    }
+}
+
+void launch_obabo_enter(const Geo &g, const Coef &cf, const int *species, const float *F, long long n, double *p,
+                        cudaStream_t s) {
+    obabo_enter_kernel<<<(g.N + 255) / 256, 256, 0, s>>>(g, cf, species, F, n, p);
 }
 
 }  // namespace lsd

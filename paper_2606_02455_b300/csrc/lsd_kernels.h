@@ -81,11 +81,12 @@ void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *spe
                              const float *Ft, const DevState *st, double2 *partials, double *logu, cudaStream_t s);
 void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                              const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
-                             int ec_on, double *q, double *p, DevState *st, const double2 *partials,
-                             const double *logu, cudaStream_t s);
+                             int ec_on, double *q, double *p, double *p_obabo, DevState *st,
+                             const double2 *partials, const double *logu, cudaStream_t s);
 void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                       const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
-                      int ec_on, double *q, double *p, DevState *st, double2 *partials, double *logu, cudaStream_t s);
+                      int ec_on, double *q, double *p, double *p_obabo, DevState *st, double2 *partials, double *logu,
+                      cudaStream_t s);
 
 // draft and plain integrator (lsd_draft.cu)
 struct DraftPlan {
@@ -108,6 +109,8 @@ cudaError_t draft_kernels_setup(int max_smem);
 void launch_plain_half(const Geo &g, const Coef &cf, const int *species, const double *q, const double *p,
                        DevState *st, double *qmid, uint4 *fix, cudaStream_t s);
 void launch_plain_finish(const Geo &g, const Coef &cf, const int *species, const double *qmid, const float *F,
-                         double *q, double *p, DevState *st, cudaStream_t s);
+                         double *q, double *p, double *p_obabo, DevState *st, cudaStream_t s);
+void launch_obabo_enter(const Geo &g, const Coef &cf, const int *species, const float *F, long long n, double *p,
+                        cudaStream_t s);
 
 }  // namespace lsd

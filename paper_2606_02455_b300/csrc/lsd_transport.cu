@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(kTransThreads)
     transport_commit_kernel(int K, Geo g, Coef cf, const int *__restrict__ species, const double *__restrict__ w_qmid,
                             const double *__restrict__ w_pdraft, const float *__restrict__ Fd,
                             const float *__restrict__ Ft, const float *__restrict__ Fraw, float *__restrict__ ec_dF,
-                            int ec_on, double *__restrict__ q, double *__restrict__ p, DevState *__restrict__ st,
+                            int ec_on, double *__restrict__ q, double *__restrict__ p,
+                            double *__restrict__ p_obabo, DevState *__restrict__ st,
                             const double2 *__restrict__ partials, const double *__restrict__ logu, int n_part,
                             int atoms_per_block) {
     __shared__ double s_s[kMaxK], s_d[kMaxK], s_lr[kMaxK], s_lu[kMaxK], s_dn[kMaxK], s_pr[kMaxK];
@@ -121,12 +122,14 @@ __global__ void __launch_bounds__(kTransThreads)
             const double hm = species_pick(cf.hm, sp);
             float3 xi = make_float3(0.f, 0.f, 0.f);
             if (s_rej) xi = normals3(cf.seed, n, (uint32_t)i, 0u);
-            const float xs[3] = {xi.x, xi.y, xi.z};
+            float3 eta = make_float3(0.f, 0.f, 0.f);
+            if (cf.obabo) eta = normals3(cf.seed, n, (uint32_t)i, 3u);
+            const float xs[3] = {xi.x, xi.y, xi.z}, es[3] = {eta.x, eta.y, eta.z};
             for (int c = 0; c < 3; ++c) {
                 const size_t o = (size_t)jj * D + (size_t)3 * i + c;
+                const double pprev = jj == 0 ? p[3 * i + c] : w_pdraft[o - D];
                 double pn;
                 if (s_rej) {
-                    const double pprev = jj == 0 ? p[3 * i + c] : w_pdraft[o - D];
                     const double mu = __dadd_rn(__dmul_rn(cf.c1, pprev), __dmul_rn(cf.aF, (double)Ft[o]));
                     const double dl = species_pick(cf.aF_sig, sp) * ((double)Fd[o] - (double)Ft[o]);
                     pn = mu + species_pick(cf.sig, sp) * ((double)xs[c] - factor * dl);
@@ -134,7 +137,13 @@ __global__ void __launch_bounds__(kTransThreads)
                     pn = w_pdraft[o];
                 }
                 p[3 * i + c] = pn;
-                q[3 * i + c] = __dadd_rn(w_qmid[o], __dmul_rn(pn, hm));
+                if (cf.obabo) {
+                    // staggered frame: no trailing A; the OBABO output of the committed step (App. E)
+                    q[3 * i + c] = w_qmid[o];
+                    p_obabo[3 * i + c] = obabo_output(cf, sp, pprev, (double)Ft[o], pn, (double)es[c]);
+                } else {
+                    q[3 * i + c] = __dadd_rn(w_qmid[o], __dmul_rn(pn, hm));
+                }
                 if (ec_on) ec_dF[3 * i + c] = Ft[o] - Fraw[o];
             }
         }
@@ -188,20 +197,21 @@ void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *spe
 
 void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                              const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
-                             int ec_on, double *q, double *p, DevState *st, const double2 *partials,
-                             const double *logu, cudaStream_t s) {
+                             int ec_on, double *q, double *p, double *p_obabo, DevState *st,
+                             const double2 *partials, const double *logu, cudaStream_t s) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
     transport_commit_kernel<<<nb, kTransThreads, 0, s>>>(K, g, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF,
-                                                         ec_on, q, p, st, partials, logu, nb, apb);
+                                                         ec_on, q, p, p_obabo, st, partials, logu, nb, apb);
 }
 
 void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                       const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
-                      int ec_on, double *q, double *p, DevState *st, double2 *partials, double *logu, cudaStream_t s) {
+                      int ec_on, double *q, double *p, double *p_obabo, DevState *st, double2 *partials, double *logu,
+                      cudaStream_t s) {
     launch_transport_reduce(K, g, cf, species, Fd, Ft, st, partials, logu, s);
-    launch_transport_commit(K, g, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, st, partials, logu,
-                            s);
+    launch_transport_commit(K, g, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, st,
+                            partials, logu, s);
 }
 
 int transport_atoms_per_block(int N) {
