@@ -288,30 +288,34 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             flush.add_(1.0)
 
+    pipelined = not args.no_pipeline
+    h.set_pipelining(pipelined)
     for _ in range(args.warmup):
         h.step(K)
         h.plain_step(1)
-    h.set_state(q_eq, p_eq, step_eq)
-    st0 = h.stats()
+
+    def timed_windows(n):
+        """n windows from the equilibrated state, each enqueue bracketed by events, L2 flushed in between."""
+        h.set_state(q_eq, p_eq, step_eq)
+        a = h.stats()
+        _barrier(world)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for k in range(n):
+            flush_l2()
+            ev[k][0].record(stream)
+            h.enqueue_windows(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        _barrier(world)
+        b = h.stats()
+        return (sum(x.elapsed_time(y) for x, y in ev) * 1e-3, b["committed"] - a["committed"],
+                b["rejected"] - a["rejected"], b["windows"] - a["windows"], a, b)
 
     clocks = Clocks(local)
     clocks.start()
-    # ---- LSD: `steps` windows, each one graph launch bracketed by events, L2 flushed in between ----
-    _barrier(world)
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for k in range(args.steps):
-        flush_l2()
-        ev[k][0].record(stream)
-        h.enqueue_windows(1)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    _barrier(world)
-    t_lsd = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
-    st1 = h.stats()
-    committed = st1["committed"] - st0["committed"]
-    rejected = st1["rejected"] - st0["rejected"]
-    windows = st1["windows"] - st0["windows"]
+    # ---- LSD: `steps` windows (pipelined: each enqueue verifies one window while drafting the next) ----
+    t_lsd, committed, rejected, windows, st0, st1 = timed_windows(args.steps)
     if args.only_lsd:
         # profiling mode: the LSD windows alone (no baseline, e2e or roofline pass)
         clocks.stop()
@@ -320,6 +324,14 @@ def run_ours(args):
                               "ms_per_step": round(t_lsd * 1e3 / args.steps, 5)}), flush=True)
         h.close()
         return
+    # ---- the same windows without the draft/verify overlap, for comparison ----
+    value_unpipelined = None
+    if pipelined:
+        h.set_pipelining(False)
+        h.step(K)
+        t_u, c_u, _, _, _, _ = timed_windows(args.steps)
+        value_unpipelined = whole_job_rate(c_u, t_u, world) * w.integ.dt * NS_PER_DAY
+        h.set_pipelining(True)
     # ---- plain target Langevin: the same number of steps as committed, one graph launch per step ----
     h.set_state(q_eq, p_eq, step_eq)
     n_plain = max(committed, 16)
@@ -359,7 +371,9 @@ def run_ours(args):
     D = 3 * s.n_atoms
 
     rl = roofline(h, w, peaks, peak_kind, pos)
-    launches_per_window = 8
+    # draft + 7 verification kernels; a pipelined round adds the window-begin, speculative-base, stale-check (2)
+    # and redraft launches (the Verlet-list kernels, when the grid has them, are not counted)
+    launches_per_window = 13 if pipelined else 8
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "ns/day", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_lsd_max * 1e3 / args.steps, 5), "higher_is_better": True,
@@ -381,6 +395,8 @@ def run_ours(args):
         "committed_per_window": round(committed / max(windows, 1), 3),
         "plain_target_ns_per_day": round(plain_value, 3),
         "speedup_vs_plain": round(value / plain_value, 3),
+        "pipelined": pipelined,
+        "value_unpipelined": None if value_unpipelined is None else round(value_unpipelined, 3),
         "plain_ms_per_step": round(t_plain * 1e3 / n_plain, 5),
         "gpu_launches": int(windows * launches_per_window + n_plain * 7),
         "e2e": {"value": round(e2e_val, 3), "unit": "ns/day", "h2d_bytes_per_step": 2 * D * 8 + 8,
@@ -468,6 +484,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-windows", type=int, default=6)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-pipeline", action="store_true", help="time the unpipelined window loop only")
     ap.add_argument("--only-lsd", action="store_true", help="time the LSD windows only (for profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3:

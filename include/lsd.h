@@ -204,6 +204,21 @@ LSD_API int lsd_set_draft_weights(lsd_handle *h, const float *weights, size_t n_
 /* lsd_get_draft_weights: copy the current draft weights (packed float32). */
 LSD_API int lsd_get_draft_weights(const lsd_handle *h, float *weights, size_t n_weights);
 
+/* lsd_set_pipelining: 1 makes lsd_step and lsd_enqueue_windows overlap the
+ * draft of window w+1 with the verification of window w (the single-GPU form
+ * of the pipelined protocol of Alg. 2): while w is verified on the handle's
+ * stream, a second, high-priority stream drafts w+1 speculatively from the
+ * last drafted state of w into a second set of window buffers.  When w is
+ * fully accepted the committed state is that speculative base bit for bit and
+ * the draft is kept; otherwise w+1 is drafted again from the committed state
+ * before it is verified.  Committed trajectories are identical to the
+ * unpipelined loop's.  Allocates the second window buffers on first use.
+ * Not with speculative error correction (the speculative draft would read the
+ * cache while the commit rewrites it): returns LSD_ESTATE if EC is on, and
+ * lsd_set_error_correction(h, 1) returns LSD_ESTATE while pipelining is on.
+ * lsd_draft_window / lsd_verify_window / lsd_profile_window stay unpipelined. */
+LSD_API int lsd_set_pipelining(lsd_handle *h, int32_t on);
+
 /* lsd_set_integrator: the Langevin splitting of the chain.
  *   LSD_ABOBA (default): Eq. 2; the state is (q, p) after a full ABOBA step.
  *   LSD_OBABO: App. E.  The chain runs in the staggered frame, whose transition

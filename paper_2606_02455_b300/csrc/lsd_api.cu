@@ -95,6 +95,22 @@ struct lsd_handle {
     // streams and graphs
     cudaStream_t own_stream = nullptr, stream = nullptr;
     cudaGraphExec_t g_window = nullptr, g_plain = nullptr;
+    // the pipelined window loop: two window buffers (buffer 0 aliases the
+    // per-window arrays above), their headers, the speculative base state, a
+    // high-priority draft stream and the fork/join events of a round
+    struct WinBufs {
+        double *qmid = nullptr, *pdraft = nullptr;
+        float *Fd = nullptr, *Fraw = nullptr;
+        uint4 *fix = nullptr;
+        VerletBufs vb;
+    } wb[2];
+    bool pipe_on = false, pipe_alloc = false, pipe_primed = false;
+    int pipe_cur = 0;
+    WinHdr *hdr = nullptr;
+    double *qb = nullptr, *pb = nullptr;
+    cudaStream_t dstream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_v = nullptr, ev_d = nullptr;
+    cudaGraphExec_t g_round[2] = {nullptr, nullptr};
     bool drafted = false;
     bool unbounded = false;   // target_step set to "no cap" by lsd_enqueue_*
     // learned-draft training
@@ -369,11 +385,12 @@ void enqueue_mlp(lsd_handle *h, const PotHost &pot, int M, cudaStream_t s) {
 // With use_list the candidates are the window's Verlet lists (the window and
 // plain-step paths); otherwise all atoms (explicit configurations).
 void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, float *F, float *E_out,
-                  cudaStream_t s, bool use_list = false) {
+                  cudaStream_t s, bool use_list = false, const VerletBufs *vb = nullptr) {
     const int M = Kc * h->N;
     const PotDev &P = pot.dev;
+    if (!vb) vb = &h->vbufs;
     if (use_list)
-        launch_neigh_list(fix, h->vbufs.vlist, h->vbufs.vcount, h->vplan.cap, M, h->geo, pot.rmax2f, pot.near2f,
+        launch_neigh_list(fix, vb->vlist, vb->vcount, h->vplan.cap, M, h->geo, pot.rmax2f, pot.near2f,
                           h->cap_near, h->cap_far, h->near_keys, h->far_keys, h->n_near, h->n_far, h->st, s);
     else
         launch_neigh_build(fix, M, h->geo, pot.rmax2f, pot.near2f, h->cap_near, h->cap_far, h->near_keys,
@@ -388,19 +405,57 @@ void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, f
                         h->E_mlp, F, E_out, h->st, s);
 }
 
-// The window's Verlet lists around the base state, then the draft.
-void enqueue_draft(lsd_handle *h, cudaStream_t s) {
-    if (!h->vplan.all_pairs) launch_verlet_build(h->vplan, h->q, h->species, h->geo, h->vbufs, h->st, s);
-    launch_draft(h->dplan, h->learned_small, h->K, h->geo, h->draft.dev, h->coef, h->vplan, h->vbufs, h->species,
-                 h->q, h->p, h->ec_dF, h->ec_on, h->st, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Fraw, h->w_fix,
-                 h->w_dEdX, s);
+// The window's Verlet lists around the base state, then the draft, into
+// window buffer b.  hdr null: from the committed state (q, p, st->step);
+// else (pipelined loop) from the base (q, p) at step hdr->base, skipped when
+// hdr->skip is set.
+void enqueue_draft_buf(lsd_handle *h, int b, cudaStream_t s, WinHdr *hdr, const double *q, const double *p) {
+    lsd_handle::WinBufs &w = h->wb[b];
+    if (!h->vplan.all_pairs)
+        launch_verlet_build(h->vplan, q, h->species, h->geo, w.vb, h->st, s, hdr ? &hdr->skip : nullptr);
+    launch_draft(h->dplan, h->learned_small, h->K, h->geo, h->draft.dev, h->coef, h->vplan, w.vb, h->species, q, p,
+                 h->ec_dF, h->ec_on, h->st, w.qmid, w.pdraft, w.Fd, w.Fraw, w.fix, h->w_dEdX, s, hdr);
 }
 
-void enqueue_verify(lsd_handle *h, cudaStream_t s) {
-    enqueue_eval(h, h->target, h->w_fix, h->K, h->w_Ft, nullptr, s, !h->vplan.all_pairs);
-    if (h->train.capture_on) enqueue_frame_capture(h->train, h->w_qmid, h->w_Ft, h->K, h->N, h->st, s);
-    launch_transport(h->K, h->geo, h->coef, h->species, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Ft, h->w_Fraw, h->ec_dF,
-                     h->ec_on, h->q, h->p, h->p_obabo, h->st, h->partials, h->logu, s);
+// Verification, frames and transport of window buffer b.
+void enqueue_verify_buf(lsd_handle *h, int b, cudaStream_t s) {
+    lsd_handle::WinBufs &w = h->wb[b];
+    enqueue_eval(h, h->target, w.fix, h->K, h->w_Ft, nullptr, s, !h->vplan.all_pairs, &w.vb);
+    if (h->train.capture_on) enqueue_frame_capture(h->train, w.qmid, h->w_Ft, h->K, h->N, h->st, s);
+    launch_transport(h->K, h->geo, h->coef, h->species, w.qmid, w.pdraft, w.Fd, h->w_Ft, w.Fraw, h->ec_dF, h->ec_on,
+                     h->q, h->p, h->p_obabo, h->st, h->partials, h->logu, s);
+}
+
+void enqueue_draft(lsd_handle *h, cudaStream_t s) { enqueue_draft_buf(h, 0, s, nullptr, h->q, h->p); }
+void enqueue_verify(lsd_handle *h, cudaStream_t s) { enqueue_verify_buf(h, 0, s); }
+
+// One round of the pipelined loop: verify window b on the main stream while
+// the draft stream drafts window b^1 speculatively; then keep or redraft b^1.
+void enqueue_round(lsd_handle *h, int b) {
+    cudaStream_t V = h->stream, D = h->dstream;
+    const int n = b ^ 1;
+    cudaEventRecord(h->ev_fork, V);
+    cudaStreamWaitEvent(D, h->ev_fork, 0);
+    launch_window_begin(&h->hdr[b], h->st, V);
+    enqueue_verify_buf(h, b, V);
+    launch_spec_base(h->geo, h->coef, h->species, h->wb[b].qmid, h->wb[b].pdraft, &h->hdr[b], &h->hdr[n], h->qb,
+                     h->pb, D);
+    enqueue_draft_buf(h, n, D, &h->hdr[n], h->qb, h->pb);
+    cudaEventRecord(h->ev_v, V);
+    cudaStreamWaitEvent(D, h->ev_v, 0);
+    launch_stale_check(h->geo, h->q, h->p, h->st, &h->hdr[n], h->qb, h->pb, D);
+    enqueue_draft_buf(h, n, D, &h->hdr[n], h->qb, h->pb);
+    cudaEventRecord(h->ev_d, D);
+    cudaStreamWaitEvent(V, h->ev_d, 0);
+}
+
+// The first window of a pipelined run: drafted from the committed state into buffer 0.
+void enqueue_prime(lsd_handle *h) {
+    launch_hdr_invalidate(&h->hdr[0], h->stream);
+    launch_stale_check(h->geo, h->q, h->p, h->st, &h->hdr[0], h->qb, h->pb, h->stream);
+    enqueue_draft_buf(h, 0, h->stream, &h->hdr[0], h->qb, h->pb);
+    h->pipe_primed = true;
+    h->pipe_cur = 0;
 }
 
 void enqueue_plain(lsd_handle *h, cudaStream_t s) {
@@ -414,6 +469,11 @@ void destroy_graphs(lsd_handle *h) {
     if (h->g_window) cudaGraphExecDestroy(h->g_window);
     if (h->g_plain) cudaGraphExecDestroy(h->g_plain);
     h->g_window = h->g_plain = nullptr;
+    for (auto &g : h->g_round) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+    h->pipe_primed = false;   // a later pipelined run drafts its first window afresh
 }
 
 int build_graph(lsd_handle *h, void (*fn)(lsd_handle *, cudaStream_t), cudaGraphExec_t *out) {
@@ -432,9 +492,39 @@ void window_fn(lsd_handle *h, cudaStream_t s) {
     enqueue_verify(h, s);
 }
 
+int build_round_graph(lsd_handle *h, int b, cudaGraphExec_t *out) {
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_round(h, b);
+    CK(cudaStreamEndCapture(h->stream, &g));
+    cudaError_t e = cudaGraphInstantiate(out, g, cudaGraphInstantiateFlagUseNodePriority);
+    cudaGraphDestroy(g);
+    CK(e);
+    return LSD_OK;
+}
+
 int ensure_graphs(lsd_handle *h) {
     if (!h->g_window) TRY(build_graph(h, window_fn, &h->g_window));
     if (!h->g_plain) TRY(build_graph(h, enqueue_plain, &h->g_plain));
+    if (h->pipe_on)
+        for (int b = 0; b < 2; ++b)
+            if (!h->g_round[b]) TRY(build_round_graph(h, b, &h->g_round[b]));
+    return LSD_OK;
+}
+
+bool pipelined(const lsd_handle *h) { return h->pipe_on && !h->ec_on; }
+
+// Launches n windows: one graph each, or (pipelined) one round each.
+int launch_windows(lsd_handle *h, long long n) {
+    if (pipelined(h)) {
+        if (!h->pipe_primed) enqueue_prime(h);
+        for (long long k = 0; k < n; ++k) {
+            CK(cudaGraphLaunch(h->g_round[h->pipe_cur], h->stream));
+            h->pipe_cur ^= 1;
+        }
+    } else {
+        for (long long k = 0; k < n; ++k) CK(cudaGraphLaunch(h->g_window, h->stream));
+    }
     return LSD_OK;
 }
 
@@ -543,7 +633,11 @@ const char *lsd_strerror(int code) {
 void lsd_destroy(lsd_handle *h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->dstream) cudaStreamSynchronize(h->dstream);
     destroy_graphs(h);
+    for (cudaEvent_t e : {h->ev_fork, h->ev_v, h->ev_d})
+        if (e) cudaEventDestroy(e);
+    if (h->dstream) cudaStreamDestroy(h->dstream);
     for (void *v : h->allocs) cudaFree(v);
     if (h->draft.tc_plan) mlp_tc_plan_free(h->draft.tc_plan);
     if (h->target.tc_plan) mlp_tc_plan_free(h->target.tc_plan);
@@ -689,6 +783,12 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         (rc = dalloc(h, &h->vbufs.cell_atoms, N)) || (rc = dalloc(h, &h->vbufs.cell_scratch, 1)) ||
         (rc = dalloc(h, &h->vbufs.vlist, N * h->vplan.cap)) || (rc = dalloc(h, &h->vbufs.vcount, N)))
         return fail(rc);
+    h->wb[0].qmid = h->w_qmid;
+    h->wb[0].pdraft = h->w_pdraft;
+    h->wb[0].Fd = h->w_Fd;
+    h->wb[0].Fraw = h->w_Fraw;
+    h->wb[0].fix = h->w_fix;
+    h->wb[0].vb = h->vbufs;
     if ((rc = pot_upload(h, h->draft)) != LSD_OK) return fail(rc);
     if ((rc = pot_upload(h, h->target)) != LSD_OK) return fail(rc);
     // MLPs on the tensor cores: BF16 as is, FP32 as three TF32 products, FP8 e4m3
@@ -771,6 +871,7 @@ int lsd_draft_window(lsd_handle *h) {
     DevState s;
     TRY(read_state(h, &s));
     TRY(set_target_step(h, s.step + h->K));
+    h->pipe_primed = false;   // the per-window calls use window buffer 0
     enqueue_draft(h, h->stream);
     CK(cudaGetLastError());
     h->drafted = true;
@@ -804,7 +905,7 @@ int lsd_step(lsd_handle *h, int64_t n_steps, lsd_stats *stats) {
         if (rate < 1.0) rate = 1.0;
         long long batch = (long long)std::ceil((double)rem / rate);
         if (batch < 1) batch = 1;
-        for (long long b = 0; b < batch; ++b) CK(cudaGraphLaunch(h->g_window, h->stream));
+        TRY(launch_windows(h, batch));
         TRY(read_state(h, &s));
         TRY(check_err(s));
         rem = target - s.step;
@@ -821,7 +922,7 @@ int lsd_enqueue_windows(lsd_handle *h, int32_t n) {
         TRY(set_target_step(h, (long long)1 << 60));
         h->unbounded = true;
     }
-    for (int32_t k = 0; k < n; ++k) CK(cudaGraphLaunch(h->g_window, h->stream));
+    TRY(launch_windows(h, n));
     h->drafted = false;
     return LSD_OK;
 }
@@ -833,6 +934,7 @@ int lsd_enqueue_plain(lsd_handle *h, int32_t n) {
         TRY(set_target_step(h, (long long)1 << 60));
         h->unbounded = true;
     }
+    h->pipe_primed = false;   // plain steps reuse window buffer 0
     for (int32_t k = 0; k < n; ++k) CK(cudaGraphLaunch(h->g_plain, h->stream));
     return LSD_OK;
 }
@@ -843,6 +945,7 @@ int lsd_plain_step(lsd_handle *h, int64_t n_steps) {
     DevState s;
     TRY(read_state(h, &s));
     TRY(set_target_step(h, s.step + n_steps));
+    h->pipe_primed = false;   // plain steps reuse window buffer 0
     for (int64_t t = 0; t < n_steps; ++t) CK(cudaGraphLaunch(h->g_plain, h->stream));
     TRY(read_state(h, &s));
     return check_err(s);
@@ -886,7 +989,38 @@ int lsd_set_state(lsd_handle *h, const double *pos, const double *mom, int64_t s
     CK(cudaMemcpyAsync(&h->st->step, &st, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
     TRY(wait_stream(h));
     h->drafted = false;
+    h->pipe_primed = false;
     if (h->coef.obabo) TRY(obabo_enter(h, step));   // the staggered momentum of the given OBABO state
+    return LSD_OK;
+}
+
+int lsd_set_pipelining(lsd_handle *h, int32_t on) {
+    if (!h) return LSD_EINVAL;
+    if (on && h->ec_on) return LSD_ESTATE;   // the speculative draft would read the cache while it is rewritten
+    TRY(wait_stream(h));
+    if (on && !h->pipe_alloc) {
+        const size_t N = h->N, D = 3 * N, KN = (size_t)h->K * N, KD = (size_t)h->K * D;
+        const size_t ncell = (size_t)h->vplan.nc[0] * h->vplan.nc[1] * h->vplan.nc[2];
+        lsd_handle::WinBufs &w = h->wb[1];
+        int rc = LSD_OK;
+        if ((rc = dalloc(h, &w.qmid, KD)) || (rc = dalloc(h, &w.pdraft, KD)) || (rc = dalloc(h, &w.Fd, KD)) ||
+            (rc = dalloc(h, &w.Fraw, KD)) || (rc = dalloc(h, &w.fix, KN)) || (rc = dalloc(h, &w.vb.fix_base, N)) ||
+            (rc = dalloc(h, &w.vb.cell_of_atom, N)) || (rc = dalloc(h, &w.vb.cell_count, ncell)) ||
+            (rc = dalloc(h, &w.vb.cell_start, ncell + 1)) || (rc = dalloc(h, &w.vb.cell_atoms, N)) ||
+            (rc = dalloc(h, &w.vb.cell_scratch, 1)) || (rc = dalloc(h, &w.vb.vlist, N * h->vplan.cap)) ||
+            (rc = dalloc(h, &w.vb.vcount, N)) || (rc = dalloc(h, &h->hdr, 2)) || (rc = dalloc(h, &h->qb, D)) ||
+            (rc = dalloc(h, &h->pb, D)))
+            return rc;
+        int lo = 0, hi = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CK(cudaStreamCreateWithPriority(&h->dstream, cudaStreamNonBlocking, hi));   // the draft is the serial chain
+        CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_v, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_d, cudaEventDisableTiming));
+        h->pipe_alloc = true;
+    }
+    h->pipe_on = on != 0;
+    destroy_graphs(h);
     return LSD_OK;
 }
 
@@ -915,6 +1049,7 @@ int lsd_set_integrator(lsd_handle *h, int32_t scheme) {
 
 int lsd_set_error_correction(lsd_handle *h, int32_t on) {
     if (!h) return LSD_EINVAL;
+    if (on && h->pipe_on) return LSD_ESTATE;   // see lsd_set_pipelining
     CK(cudaMemsetAsync(h->ec_dF, 0, 3 * (size_t)h->N * sizeof(float), h->stream));
     h->ec_on = on ? 1 : 0;
     destroy_graphs(h);
@@ -1039,6 +1174,7 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
     const int M = h->K * h->N;
     const PotDev &P = h->target.dev;
     CK(cudaEventRecord(ev[0], st));
+    h->pipe_primed = false;
     enqueue_draft(h, st);
     CK(cudaEventRecord(ev[1], st));
     if (h->vplan.all_pairs)
@@ -1172,6 +1308,7 @@ int lsd_restore(lsd_handle *h, const void *buf, size_t len) {
     CK(cudaMemcpyAsync(h->p, (const double *)o + D, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     const long long stp = hd.step;
     CK(cudaMemcpyAsync(&h->st->step, &stp, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+    h->pipe_primed = false;
     h->drafted = false;
     h->coef.obabo = hd.integrator == LSD_OBABO ? 1 : 0;
     {

@@ -74,6 +74,15 @@ struct Coef {
     double sigh[kMaxSpecies];   // sqrt(m kB T kappa (1 - exp(-gamma dt)))
 };
 
+// Header of one window buffer of the pipelined loop: the step index of the
+// state the window was drafted from, how many steps the draft reached, and
+// whether the kernels that would (re)draft it skip.
+struct WinHdr {
+    long long base;
+    int k_eff;
+    int skip;
+};
+
 // Device-resident run state.  step is the index of the base state.
 struct DevState {
     long long step;

@@ -201,7 +201,8 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                                 const double *__restrict__ q_base, const double *__restrict__ p_base,
                                 const float *__restrict__ ec_dF, int ec_on, DevState *__restrict__ st,
                                 double *__restrict__ w_qmid, double *__restrict__ w_pdraft, float *__restrict__ w_Fd,
-                                float *__restrict__ w_Fraw, uint4 *__restrict__ w_fix, float *__restrict__ w_dEdX) {
+                                float *__restrict__ w_Fraw, uint4 *__restrict__ w_fix, float *__restrict__ w_dEdX,
+                                WinHdr *__restrict__ hdr) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N;
     const int C = gridDim.x, c = blockIdx.x;
@@ -214,8 +215,15 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     uint4 *sfix = (uint4 *)(sstage + (LEARNED ? (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) : 0));  // [2][N]
     int *sflag = (int *)(sfix + (stage_fix ? 2 * (size_t)N : 0));                                        // [2]
     float *snoise = (float *)(sflag + 4);   // [K][A][3] when noise_smem: the window's xi, drawn up front
-    if (st->step >= st->target_step) return;   // uniform over the cluster
-    const long long n0 = st->step;
+    // the base step: the committed one, or (pipelined loop) the window header's; uniform over the cluster
+    long long n0;
+    if (hdr) {
+        if (hdr->skip || hdr->base >= st->target_step) return;
+        n0 = hdr->base;
+    } else {
+        if (st->step >= st->target_step) return;
+        n0 = st->step;
+    }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int grp = tid >> 2, x = tid & 3, gl = lane & ~3;
     const size_t D = (size_t)3 * N;
@@ -472,7 +480,10 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
         // its own global writes, and sF is rewritten only after the next cluster
         // barrier: no CTA barrier is needed here
     }
-    if (c == 0 && tid == 0) st->k_eff = keff;
+    if (c == 0 && tid == 0) {
+        if (hdr) hdr->k_eff = keff;
+        else st->k_eff = keff;
+    }
 }
 
 static size_t draft_smem_bytes(int N, int C, const PotDev &P, bool learned, bool stage_fix, int noise_K) {
@@ -503,7 +514,8 @@ DraftPlan draft_plan(int N, int K, const PotDev &P, bool learned, int max_cluste
 cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf,
                          const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
                          const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
-                         double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX, cudaStream_t s) {
+                         double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX, cudaStream_t s,
+                         WinHdr *hdr) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(pl.cluster, 1, 1);
     cfg.blockDim = dim3(kDraftThreads, 1, 1);
@@ -524,7 +536,7 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
                         : (pl.reg ? draft_window_cluster_kernel<false, true> : draft_window_cluster_kernel<false, false>);
     return cudaLaunchKernelEx(&cfg, kern, K, g, P, cf, vl, (const int *)vb.vcount, vp.cap, (const uint4 *)vb.fix_base,
                               vp.move2f, stage, mi, ns, species, q, p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd,
-                              w_Fraw, w_fix, w_dEdX);
+                              w_Fraw, w_fix, w_dEdX, hdr);
 }
 
 static const void *draft_kernel_ptrs[4] = {
@@ -561,6 +573,93 @@ int draft_max_cluster(size_t smem, bool learned) {
     }
     return c >= 16 ? 16 : (c >= 8 ? 8 : (c >= 4 ? 4 : (c >= 2 ? 2 : 1)));
 }
+
+// ---------------------------------------------------------------------------
+// The pipelined window loop (single-GPU form of the pipelined protocol of
+// Alg. 2): while window b is verified, window b^1 is drafted speculatively
+// from the last drafted state of b, as if all of b were accepted.  After the
+// verification the speculative draft is kept iff its base step equals the
+// committed step and b had no rejection (then every step of b was accepted and
+// the committed state is the speculative base bit for bit, so the draft is the
+// one a fresh start would make); otherwise b^1 is drafted again from the
+// committed state.
+// ---------------------------------------------------------------------------
+
+// The speculative base of window b^1: the state after the last step window b
+// drafted (ABOBA: q_mid + (dt/2) p/m with the commit's rounding; staggered
+// OBABO: q_mid), its step index, and whether there is one (k_eff > 0).
+__global__ void spec_base_kernel(Geo g, Coef cf, const int *__restrict__ species, const double *__restrict__ qmid_b,
+                                 const double *__restrict__ pdraft_b, const WinHdr *__restrict__ hb,
+                                 WinHdr *__restrict__ hn, double *__restrict__ qb, double *__restrict__ pb) {
+    const int k = hb->k_eff;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        hn->base = k > 0 ? hb->base + k : -1;
+        hn->skip = k > 0 ? 0 : 1;
+    }
+    if (k <= 0 || i >= g.N) return;
+    const size_t o = (size_t)(k - 1) * 3 * g.N + 3 * (size_t)i;
+    const double hm = species_pick(cf.hm, species[i]);
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        const double pn = pdraft_b[o + x];
+        pb[3 * i + x] = pn;
+        qb[3 * i + x] = cf.obabo ? qmid_b[o + x] : __dadd_rn(qmid_b[o + x], __dmul_rn(pn, hm));
+    }
+}
+
+// Valid iff the speculative base is the committed state: the previous window
+// committed up to the base step without a rejection (a rejection at its last
+// step also ends at that step index, but in the reflected state).
+__device__ __forceinline__ bool spec_is_valid(const WinHdr *hn, const DevState *st) {
+    return hn->skip == 0 && hn->base == st->step && st->first_reject_last == -1;
+}
+
+// Reads the header only (it is rewritten by stale_commit_kernel afterwards):
+// an invalid window's base becomes the committed state.
+__global__ void stale_check_kernel(Geo g, const double *__restrict__ q, const double *__restrict__ p,
+                                   const DevState *__restrict__ st, const WinHdr *__restrict__ hn,
+                                   double *__restrict__ qb, double *__restrict__ pb) {
+    if (spec_is_valid(hn, st)) return;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 3 * g.N; k += gridDim.x * blockDim.x) {
+        qb[k] = q[k];
+        pb[k] = p[k];
+    }
+}
+
+__global__ void stale_commit_kernel(const DevState *__restrict__ st, WinHdr *__restrict__ hn) {
+    if (spec_is_valid(hn, st)) {
+        hn->skip = 1;            // keep the speculative draft: the redraft kernels return at once
+    } else {
+        hn->base = st->step;     // draft again from the committed state
+        hn->skip = 0;
+    }
+}
+
+// The verification of window b reads its k_eff through the run state.
+__global__ void window_begin_kernel(const WinHdr *__restrict__ hb, DevState *__restrict__ st) { st->k_eff = hb->k_eff; }
+
+__global__ void hdr_invalidate_kernel(WinHdr *__restrict__ h) {
+    h->base = -1;
+    h->skip = 1;
+    h->k_eff = 0;
+}
+
+void launch_spec_base(const Geo &g, const Coef &cf, const int *species, const double *qmid_b, const double *pdraft_b,
+                      const WinHdr *hb, WinHdr *hn, double *qb, double *pb, cudaStream_t s) {
+    spec_base_kernel<<<(g.N + 255) / 256, 256, 0, s>>>(g, cf, species, qmid_b, pdraft_b, hb, hn, qb, pb);
+}
+
+void launch_stale_check(const Geo &g, const double *q, const double *p, const DevState *st, WinHdr *hn, double *qb,
+                        double *pb, cudaStream_t s) {
+    const int blocks = (3 * g.N + 255) / 256 < 296 ? (3 * g.N + 255) / 256 : 296;
+    stale_check_kernel<<<blocks, 256, 0, s>>>(g, q, p, st, hn, qb, pb);
+    stale_commit_kernel<<<1, 1, 0, s>>>(st, hn);
+}
+
+void launch_window_begin(const WinHdr *hb, DevState *st, cudaStream_t s) { window_begin_kernel<<<1, 1, 0, s>>>(hb, st); }
+
+void launch_hdr_invalidate(WinHdr *h, cudaStream_t s) { hdr_invalidate_kernel<<<1, 1, 0, s>>>(h); }
 
 // ---------------------------------------------------------------------------
 // Plain target ABOBA (the baseline): half step before the batched force

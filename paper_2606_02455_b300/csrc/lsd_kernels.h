@@ -41,7 +41,7 @@ struct VerletBufs {
     int *vcount = nullptr;       // [N]
 };
 void launch_verlet_build(const VerletPlan &vp, const double *q, const int *species, const Geo &g, VerletBufs &b,
-                         DevState *st, cudaStream_t s);
+                         DevState *st, cudaStream_t s, const int *skip = nullptr);
 cudaError_t verlet_setup(int max_smem);
 void launch_neigh_list(const uint4 *fix, const int *vlist, const int *vcount, int vcap, int M, const Geo &g,
                        float rmax2f, float near2f, int cap_near, int cap_far, int *near_keys, int *far_keys,
@@ -104,7 +104,15 @@ int draft_max_cluster(size_t smem, bool learned);
 cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf,
                          const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
                          const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
-                         double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX, cudaStream_t s);
+                         double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX, cudaStream_t s,
+                         WinHdr *hdr = nullptr);
+// the pipelined window loop (lsd_draft.cu)
+void launch_spec_base(const Geo &g, const Coef &cf, const int *species, const double *qmid_b, const double *pdraft_b,
+                      const WinHdr *hb, WinHdr *hn, double *qb, double *pb, cudaStream_t s);
+void launch_stale_check(const Geo &g, const double *q, const double *p, const DevState *st, WinHdr *hn, double *qb,
+                        double *pb, cudaStream_t s);
+void launch_window_begin(const WinHdr *hb, DevState *st, cudaStream_t s);
+void launch_hdr_invalidate(WinHdr *h, cudaStream_t s);
 cudaError_t draft_kernels_setup(int max_smem);
 void launch_plain_half(const Geo &g, const Coef &cf, const int *species, const double *q, const double *p,
                        DevState *st, double *qmid, uint4 *fix, cudaStream_t s);

@@ -29,7 +29,7 @@ PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2, "fp32-cuda-cores": 3}
 SYMBOLS = ["lsd_init", "lsd_draft_window", "lsd_verify_window", "lsd_step", "lsd_plain_step", "lsd_enqueue_windows",
            "lsd_enqueue_plain", "lsd_get_state",
            "lsd_set_state", "lsd_get_stats", "lsd_set_stream", "lsd_set_draft_weights", "lsd_get_draft_weights",
-           "lsd_set_error_correction", "lsd_set_integrator", "lsd_set_frame_capture", "lsd_frame_count", "lsd_train_draft",
+           "lsd_set_error_correction", "lsd_set_integrator", "lsd_set_pipelining", "lsd_set_frame_capture", "lsd_frame_count", "lsd_train_draft",
            "lsd_force_match_dev", "lsd_target_forces_dev", "lsd_draft_forces_dev", "lsd_neighbors",
            "lsd_descriptors", "lsd_get_window", "lsd_profile_window", "lsd_checkpoint", "lsd_restore", "lsd_query",
            "lsd_target_mlp_static_dev", "lsd_destroy",
@@ -89,6 +89,7 @@ def _lib():
             "lsd_get_draft_weights": [P, P, SZ],
             "lsd_set_error_correction": [P, I32],
             "lsd_set_integrator": [P, I32],
+            "lsd_set_pipelining": [P, I32],
             "lsd_set_frame_capture": [P, I64],
             "lsd_frame_count": [P, P],
             "lsd_train_draft": [P, I32, ctypes.c_float, I32, P],
@@ -255,6 +256,10 @@ class LSD:
     def set_stream(self, stream=None):
         ptr = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
         _check(_lib().lsd_set_stream(self.h, ptr), "lsd_set_stream")
+
+    def set_pipelining(self, on=True):
+        """Overlap the draft of window w+1 with the verification of window w (lsd_set_pipelining)."""
+        _check(_lib().lsd_set_pipelining(self.h, int(bool(on))), "lsd_set_pipelining")
 
     SCHEMES = {"aboba": 0, "obabo": 1}
 

@@ -1,0 +1,77 @@
+"""The pipelined window loop (lsd_set_pipelining: the draft of window w+1 overlaps the verification of window w,
+speculatively from w's last drafted state, and is drafted again when w had a rejection) commits exactly the
+trajectory of the unpipelined loop: same steps, same bits."""
+import numpy as np
+import pytest
+
+from paper_2606_02455_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(w, target, n, pipelined, **kw):
+    from paper_2606_02455_b300 import lsd
+    h = lsd.LSD(w.system, w.draft, target, w.integ)
+    if pipelined:
+        h.set_pipelining(True)
+    st = h.step(n)
+    q, p, step = h.get_state()
+    h.close()
+    return q, p, step, st
+
+
+@pytest.mark.parametrize("cfg,scale,n", [(1, 1.0, 96), (2, 1.5, 80), (4, None, 96)])
+def test_pipelined_equals_unpipelined_bitwise(cfg, scale, n):
+    w = W.CONFIGS[cfg]()
+    target = w.target if scale is None else W.replace(w.target, head_scale=scale)
+    qa, pa, sa, sta = _run(w, target, n, False)
+    qb, pb, sb, stb = _run(w, target, n, True)
+    assert sa == sb == n
+    assert sta["rejected"] == stb["rejected"] and sta["rejected"] > 0
+    assert np.array_equal(qa, qb) and np.array_equal(pa, pb)
+
+
+def test_pipelined_obabo_equals_unpipelined():
+    w = W.config1()
+    w = W.replace(w, integ=W.replace(w.integ, scheme="obabo"))
+    target = W.replace(w.target, head_scale=1.0)
+    qa, pa, sa, sta = _run(w, target, 64, False)
+    qb, pb, sb, stb = _run(w, target, 64, True)
+    assert sa == sb == 64 and sta["rejected"] == stb["rejected"]
+    assert np.array_equal(qa, qb) and np.array_equal(pa, pb)
+
+
+def test_pipelined_survives_state_changes_between_runs():
+    """set_state and plain steps between pipelined runs: each run starts from the state it is given."""
+    from paper_2606_02455_b300 import lsd
+    w = W.config1()
+    target = W.replace(w.target, head_scale=1.0)
+    s = w.system
+    a = lsd.LSD(s, w.draft, target, w.integ)
+    b = lsd.LSD(s, w.draft, target, w.integ)
+    b.set_pipelining(True)
+    for h in (a, b):
+        h.step(24)
+        h.plain_step(5)
+        h.step(16)
+        h.set_state(s.positions, s.momenta, 3)
+        h.step(24)
+    qa, pa, sa = a.get_state()
+    qb, pb, sb = b.get_state()
+    assert sa == sb == 27 and np.array_equal(qa, qb) and np.array_equal(pa, pb)
+    a.close()
+    b.close()
+
+
+def test_pipelining_excludes_error_correction():
+    from paper_2606_02455_b300 import lsd
+    w = W.config1()
+    h = lsd.LSD(w.system, w.draft, w.target, w.integ)
+    h.set_error_correction(True)
+    with pytest.raises(lsd.LSDError):
+        h.set_pipelining(True)
+    h.set_error_correction(False)
+    h.set_pipelining(True)
+    with pytest.raises(lsd.LSDError):
+        h.set_error_correction(True)
+    h.close()
