@@ -189,11 +189,12 @@ def _algorithmic_work(w, phase, q):
 
 def _analysis(st1, st0, rl, K, t_plain_step):
     """The paper's bounds at the measured operating point (paper_2606_02455_b300.analysis): per-step rejection
-    rate <beta> = rejections / verified steps, cost ratio c = drafted-step time / plain-step time, the pipelined
+    rate <beta> = rejections / tested steps (every committed step was tested, in order; steps after a window's
+    first rejection are flushed untested), cost ratio c = drafted-step time / plain-step time, the pipelined
     bound 1 / (c + <beta>) (Eq. 8) and the synchronous lookahead-K bound."""
     from paper_2606_02455_b300 import analysis as A
-    verified = max(st1["verified"] - st0["verified"], 1)
-    beta = (st1["rejected"] - st0["rejected"]) / verified
+    tested = max(st1["committed"] - st0["committed"], 1)
+    beta = (st1["rejected"] - st0["rejected"]) / tested
     ph = rl["phases_ms"]
     t_draft = ph["draft"] * 1e-3 / K
     c = t_draft / t_plain_step

@@ -47,7 +47,8 @@ def _measure(cfg: int, K: int, windows: int, equil: int):
     st1 = h.stats()
     committed = st1["committed"] - st0["committed"]
     verified = st1["verified"] - st0["verified"]
-    beta = (st1["rejected"] - st0["rejected"]) / max(verified, 1)
+    # per tested step: every committed step was tested in order; steps after a window's first rejection were not
+    beta = (st1["rejected"] - st0["rejected"]) / max(committed, 1)
     n_plain = 200
     e0.record(stream)
     h.plain_step(n_plain)
@@ -71,8 +72,8 @@ def main(argv=None):
     fixed, per = A.fit_verify_costs([r["K"] for r in rows], [r["t_verify"] for r in rows])
     t_draft = float(np.mean([r["t_draft"] for r in rows]))
     t_plain = float(np.mean([r["t_plain"] for r in rows]))
-    verified = sum(r["verified"] for r in rows)
-    beta = float(sum(r["beta"] * r["verified"] for r in rows) / max(verified, 1))
+    tested = sum(r["committed"] for r in rows)
+    beta = float(sum(r["beta"] * r["committed"] for r in rows) / max(tested, 1))
     costs = A.WindowCosts(t_draft=t_draft, verify_fixed=max(fixed, 0.0), verify_per_step=per, t_plain=t_plain)
     k_best, s_best = A.best_window(beta, costs, K_max=max(args.K) * 2)
     for r in rows:
