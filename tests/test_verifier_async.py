@@ -18,7 +18,7 @@ from paper_2606_02455_b300 import verifier as VF
 A, S, B_T, B_D, DIM = 0.8, 1.0, 0.0, 0.45, 24
 
 
-def _chain(seed, sleep_max=1e-3, fail_sid=None, hang_sid=None, hang=2.0):
+def _chain(seed, sleep_max=1e-3, fail_sid=None, hang_sid=None, hang=2.0, bias=B_D):
     rng_draft = np.random.default_rng(seed)
     tag = {"n": 0}
     base_of = {}
@@ -26,7 +26,7 @@ def _chain(seed, sleep_max=1e-3, fail_sid=None, hang_sid=None, hang=2.0):
 
     def draft_step(y):
         tag["n"] += 1
-        return {"v": A * y["v"] + B_D + S * rng_draft.standard_normal(DIM), "tag": ("draft", tag["n"])}
+        return {"v": A * y["v"] + bias + S * rng_draft.standard_normal(DIM), "tag": ("draft", tag["n"])}
 
     def verify_step(y, y_new, sid):
         with lock:
@@ -35,7 +35,7 @@ def _chain(seed, sleep_max=1e-3, fail_sid=None, hang_sid=None, hang=2.0):
         if sid == fail_sid:
             raise RuntimeError("injected worker failure")
         time.sleep(hang if sid == hang_sid else r.uniform(0, sleep_max))
-        mu_d = A * y["v"] + B_D
+        mu_d = A * y["v"] + bias
         mu_t = A * y["v"] + B_T
         acc, p, _ = O.transport(np.full(DIM, S), r.uniform(1e-12, 1.0), y_new["v"], mu_d, mu_t)
         if acc:
@@ -90,7 +90,8 @@ def test_worker_failure_is_detected():
 
 
 def test_worker_that_does_not_return_times_out():
-    x0, draft, verify, _ = _chain(4, hang_sid=4, hang=2.0)
+    # draft equal to target: nothing is rejected, so the hung step is never flushed and holds V back
+    x0, draft, verify, _ = _chain(4, hang_sid=4, hang=2.0, bias=B_T)
     t0 = time.monotonic()
     with pytest.raises(TimeoutError):
         VF.run_pipelined(x0, 30, draft, verify, n_workers=3, timeout=0.3)
