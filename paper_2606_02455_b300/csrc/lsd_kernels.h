@@ -78,7 +78,7 @@ int mlp_tc_static_launch(const void *plan, const float *X, int M, const PotDev &
 // transport (lsd_transport.cu)
 int transport_atoms_per_block(int N);
 void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *species, const float *Fd,
-                             const float *Ft, const DevState *st, double2 *partials, double *logu, cudaStream_t s);
+                             const float *Ft, DevState *st, double2 *partials, double *logu, cudaStream_t s);
 void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                              const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
                              int ec_on, double *q, double *p, double *p_obabo, DevState *st,

@@ -33,34 +33,182 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh) {
     return t;   // valid in thread 0
 }
 
+// Shared state of a window's decision, used by the commit (and by the fused
+// reduce-commit for windows whose atoms fit in one block).
+struct CommitShared {
+    double s[kMaxK], d[kMaxK], lr[kMaxK], lu[kMaxK], dn[kMaxK], pr[kMaxK];
+    int acc[kMaxK];
+    int nc, rej, l, bad;
+};
+
+// Sums the partials of every window step in a fixed order, forms log r and
+// the accept flags, and finds l = the first rejected step (all threads).
+__device__ void commit_decide(CommitShared &C, int K, const double2 *__restrict__ partials, int n_part,
+                              const double *__restrict__ logu, long long rem) {
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        double s = 0.0, d = 0.0;
+        for (int b = 0; b < n_part; ++b) {
+            const double2 v = __ldcg(partials + (size_t)j * n_part + b);
+            s += v.x;
+            d += v.y;
+        }
+        C.s[j] = s;
+        C.d[j] = d;
+        const double lr = -s - 0.5 * d;
+        const double lu = __ldcg(logu + j);
+        C.lr[j] = lr;
+        C.lu[j] = lu;
+        C.acc[j] = (d == 0.0) || (lu <= fmin(0.0, lr));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int l = K, rej = 0, bad = 0;
+        for (int j = 0; j < K; ++j) {
+            if (!isfinite(C.lr[j])) { bad = 1; l = j + 1; break; }
+            if (!C.acc[j]) { l = j + 1; rej = 1; break; }
+        }
+        const int nc = (long long)l < rem ? l : (int)rem;
+        C.l = l;
+        C.nc = bad ? 0 : nc;
+        C.rej = (rej && nc == l) ? 1 : 0;
+        C.bad = bad;
+    }
+    __syncthreads();
+}
+
+// Commits atoms [a0, a1): the draft's own bits for an accepted last step, the
+// reflection (Eq. 5) for a rejected one; the staggered OBABO frame keeps the
+// position and recovers the output momentum (App. E).
+__device__ void commit_atoms(const CommitShared &C, int N, const Coef &cf, const int *__restrict__ species,
+                             const double *__restrict__ w_qmid, const double *__restrict__ w_pdraft,
+                             const float *__restrict__ Fd, const float *__restrict__ Ft,
+                             const float *__restrict__ Fraw, float *__restrict__ ec_dF, int ec_on,
+                             double *__restrict__ q, double *__restrict__ p, double *__restrict__ p_obabo,
+                             long long n0, int a0, int a1) {
+    const int nc = C.nc;
+    if (nc <= 0) return;
+    const int jj = nc - 1;
+    const size_t D = (size_t)3 * N;
+    const double factor = C.rej ? 2.0 * C.s[jj] / C.d[jj] : 0.0;
+    const unsigned long long n = (unsigned long long)(n0 + jj + 1);
+    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+        const int sp = species[i];
+        const double hm = species_pick(cf.hm, sp);
+        float3 xi = make_float3(0.f, 0.f, 0.f);
+        if (C.rej) xi = normals3(cf.seed, n, (uint32_t)i, 0u);
+        float3 eta = make_float3(0.f, 0.f, 0.f);
+        if (cf.obabo) eta = normals3(cf.seed, n, (uint32_t)i, 3u);
+        const float xs[3] = {xi.x, xi.y, xi.z}, es[3] = {eta.x, eta.y, eta.z};
+        for (int c = 0; c < 3; ++c) {
+            const size_t o = (size_t)jj * D + (size_t)3 * i + c;
+            const double pprev = jj == 0 ? p[3 * i + c] : w_pdraft[o - D];
+            double pn;
+            if (C.rej) {
+                const double mu = __dadd_rn(__dmul_rn(cf.c1, pprev), __dmul_rn(cf.aF, (double)Ft[o]));
+                const double dl = species_pick(cf.aF_sig, sp) * ((double)Fd[o] - (double)Ft[o]);
+                pn = mu + species_pick(cf.sig, sp) * ((double)xs[c] - factor * dl);
+            } else {
+                pn = w_pdraft[o];
+            }
+            p[3 * i + c] = pn;
+            if (cf.obabo) {
+                // staggered frame: no trailing A; the OBABO output of the committed step (App. E)
+                q[3 * i + c] = w_qmid[o];
+                p_obabo[3 * i + c] = obabo_output(cf, sp, pprev, (double)Ft[o], pn, (double)es[c]);
+            } else {
+                q[3 * i + c] = __dadd_rn(w_qmid[o], __dmul_rn(pn, hm));
+            }
+            if (ec_on) ec_dF[3 * i + c] = Ft[o] - Fraw[o];
+        }
+    }
+}
+
+// Statistics of the window and the step advance (one block, all threads).
+__device__ void commit_stats(CommitShared &C, int K, DevState *__restrict__ st, long long n0) {
+    const int nc = C.nc;
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        const double dn = sqrt(C.d[j]);
+        C.dn[j] = dn;
+        C.pr[j] = (double)erff((float)dn * 0.35355339059327373f);   // erf(|delta| / sqrt 8), Eq. 6
+        st->accept[j] = C.acc[j];
+        st->logr[j] = C.lr[j];
+        st->logu[j] = C.lu[j];
+        st->dnorm[j] = dn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->n_commit_last = nc;
+        st->first_reject_last = C.rej || (C.l <= K && !C.acc[C.l - 1]) ? C.l : -1;
+        if (C.bad) atomicOr(&st->err, 2);
+        st->windows += 1;
+        st->verified += K;
+        st->committed += nc;
+        st->rejected += C.rej;
+        double sd = 0.0, sp = 0.0;
+        for (int j = 0; j < nc; ++j) {
+            sd += C.dn[j];
+            sp += C.pr[j];
+        }
+        st->sum_delta += sd;
+        st->sum_pred += sp;
+        st->step = n0 + nc;
+    }
+}
+
+// Per window step j (blockIdx.y) and slice of atoms (blockIdx.x): z.delta and
+// delta.delta in FP64, with delta = (1+c1)(dt/2)kappa (F~ - F) / sigma and
+// z = xi (the draft's own noise); log u of step j by block (0, j).  fused:
+// the window's atoms fit in one block, and the last block to finish decides,
+// commits every atom and updates the statistics (no second launch).
 __global__ void __launch_bounds__(kTransThreads)
     transport_reduce_kernel(int K, Geo g, Coef cf, const int *__restrict__ species, const float *__restrict__ Fd,
-                            const float *__restrict__ Ft, const DevState *__restrict__ st, double2 *__restrict__ partials,
-                            double *__restrict__ logu, int atoms_per_block) {
+                            const float *__restrict__ Ft, DevState *__restrict__ st, double2 *__restrict__ partials,
+                            double *__restrict__ logu, int atoms_per_block, int fused,
+                            const double *__restrict__ w_qmid, const double *__restrict__ w_pdraft,
+                            const float *__restrict__ Fraw, float *__restrict__ ec_dF, int ec_on,
+                            double *__restrict__ q, double *__restrict__ p, double *__restrict__ p_obabo) {
     __shared__ double sh[32];
-    if (st->step >= st->target_step) return;
-    if ((int)blockIdx.y >= st->k_eff) return;   // window step the draft did not reach
+    __shared__ CommitShared C;
+    __shared__ bool s_last;
+    if (st->step >= st->target_step) return;   // uniform over the grid
     const int N = g.N;
     const int j = blockIdx.y;
-    const unsigned long long n = (unsigned long long)(st->step + j + 1);
-    // log u of the acceptance test, one FP64 log per window step, in parallel over steps
-    if (blockIdx.x == 0 && threadIdx.x == blockDim.x - 1) logu[j] = log(uniform53(cf.seed, n));
-    const int a0 = blockIdx.x * atoms_per_block;
-    const int a1 = min(N, a0 + atoms_per_block);
-    double s = 0.0, d = 0.0;
-    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
-        const float3 xi = normals3(cf.seed, n, (uint32_t)i, 0u);
-        const double k = species_pick(cf.aF_sig, species[i]);
-        const size_t o = ((size_t)j * N + i) * 3;
-        const double d0 = k * ((double)Fd[o + 0] - (double)Ft[o + 0]);
-        const double d1 = k * ((double)Fd[o + 1] - (double)Ft[o + 1]);
-        const double d2 = k * ((double)Fd[o + 2] - (double)Ft[o + 2]);
-        s += (double)xi.x * d0 + (double)xi.y * d1 + (double)xi.z * d2;
-        d += d0 * d0 + d1 * d1 + d2 * d2;
+    const int keff = st->k_eff;
+    if (j < keff) {                            // steps the draft did not reach are skipped
+        const unsigned long long n = (unsigned long long)(st->step + j + 1);
+        // log u of the acceptance test, one FP64 log per window step, in parallel over steps
+        if (blockIdx.x == 0 && threadIdx.x == blockDim.x - 1) logu[j] = log(uniform53(cf.seed, n));
+        const int a0 = blockIdx.x * atoms_per_block;
+        const int a1 = min(N, a0 + atoms_per_block);
+        double s = 0.0, d = 0.0;
+        for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+            const float3 xi = normals3(cf.seed, n, (uint32_t)i, 0u);
+            const double k = species_pick(cf.aF_sig, species[i]);
+            const size_t o = ((size_t)j * N + i) * 3;
+            const double d0 = k * ((double)Fd[o + 0] - (double)Ft[o + 0]);
+            const double d1 = k * ((double)Fd[o + 1] - (double)Ft[o + 1]);
+            const double d2 = k * ((double)Fd[o + 2] - (double)Ft[o + 2]);
+            s += (double)xi.x * d0 + (double)xi.y * d1 + (double)xi.z * d2;
+            d += d0 * d0 + d1 * d1 + d2 * d2;
+        }
+        const double S = block_sum_d(s, sh);
+        const double D = block_sum_d(d, sh);
+        if (threadIdx.x == 0) partials[(size_t)j * gridDim.x + blockIdx.x] = make_double2(S, D);
     }
-    const double S = block_sum_d(s, sh);
-    const double D = block_sum_d(d, sh);
-    if (threadIdx.x == 0) partials[(size_t)j * gridDim.x + blockIdx.x] = make_double2(S, D);
+    if (!fused) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->blocks_done, 1u) == gridDim.x * gridDim.y - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const long long n0 = st->step;
+    const int Kw = min(K, keff);
+    commit_decide(C, Kw, partials, gridDim.x, logu, st->target_step - n0);
+    commit_atoms(C, N, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, n0, 0, N);
+    __syncthreads();
+    if (threadIdx.x == 0) st->blocks_done = 0u;
+    commit_stats(C, Kw, st, n0);
 }
 
 __global__ void __launch_bounds__(kTransThreads)
@@ -71,128 +219,32 @@ __global__ void __launch_bounds__(kTransThreads)
                             double *__restrict__ p_obabo, DevState *__restrict__ st,
                             const double2 *__restrict__ partials, const double *__restrict__ logu, int n_part,
                             int atoms_per_block) {
-    __shared__ double s_s[kMaxK], s_d[kMaxK], s_lr[kMaxK], s_lu[kMaxK], s_dn[kMaxK], s_pr[kMaxK];
-    __shared__ int s_acc[kMaxK];
-    __shared__ int s_nc, s_rej, s_l, s_bad;
+    __shared__ CommitShared C;
     __shared__ bool s_last;
     if (st->step >= st->target_step) return;
     K = min(K, st->k_eff);   // the window holds the k_eff steps the draft reached
-    const int N = g.N;
     const long long n0 = st->step;
-    const long long rem = st->target_step - n0;
-    for (int j = threadIdx.x; j < K; j += blockDim.x) {
-        double s = 0.0, d = 0.0;
-        for (int b = 0; b < n_part; ++b) {
-            const double2 v = partials[(size_t)j * n_part + b];
-            s += v.x;
-            d += v.y;
-        }
-        s_s[j] = s;
-        s_d[j] = d;
-        const double lr = -s - 0.5 * d;
-        const double lu = logu[j];
-        s_lr[j] = lr;
-        s_lu[j] = lu;
-        s_acc[j] = (d == 0.0) || (lu <= fmin(0.0, lr));
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int l = K, rej = 0, bad = 0;
-        for (int j = 0; j < K; ++j) {
-            if (!isfinite(s_lr[j])) { bad = 1; l = j + 1; break; }
-            if (!s_acc[j]) { l = j + 1; rej = 1; break; }
-        }
-        const int nc = (long long)l < rem ? l : (int)rem;
-        s_l = l;
-        s_nc = bad ? 0 : nc;
-        s_rej = (rej && nc == l) ? 1 : 0;
-        s_bad = bad;
-    }
-    __syncthreads();
-    const int nc = s_nc;
-    if (nc > 0) {
-        const int jj = nc - 1;
-        const size_t D = (size_t)3 * N;
-        const double factor = s_rej ? 2.0 * s_s[jj] / s_d[jj] : 0.0;
-        const unsigned long long n = (unsigned long long)(n0 + jj + 1);
-        const int a0 = blockIdx.x * atoms_per_block;
-        const int a1 = min(N, a0 + atoms_per_block);
-        for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
-            const int sp = species[i];
-            const double hm = species_pick(cf.hm, sp);
-            float3 xi = make_float3(0.f, 0.f, 0.f);
-            if (s_rej) xi = normals3(cf.seed, n, (uint32_t)i, 0u);
-            float3 eta = make_float3(0.f, 0.f, 0.f);
-            if (cf.obabo) eta = normals3(cf.seed, n, (uint32_t)i, 3u);
-            const float xs[3] = {xi.x, xi.y, xi.z}, es[3] = {eta.x, eta.y, eta.z};
-            for (int c = 0; c < 3; ++c) {
-                const size_t o = (size_t)jj * D + (size_t)3 * i + c;
-                const double pprev = jj == 0 ? p[3 * i + c] : w_pdraft[o - D];
-                double pn;
-                if (s_rej) {
-                    const double mu = __dadd_rn(__dmul_rn(cf.c1, pprev), __dmul_rn(cf.aF, (double)Ft[o]));
-                    const double dl = species_pick(cf.aF_sig, sp) * ((double)Fd[o] - (double)Ft[o]);
-                    pn = mu + species_pick(cf.sig, sp) * ((double)xs[c] - factor * dl);
-                } else {
-                    pn = w_pdraft[o];
-                }
-                p[3 * i + c] = pn;
-                if (cf.obabo) {
-                    // staggered frame: no trailing A; the OBABO output of the committed step (App. E)
-                    q[3 * i + c] = w_qmid[o];
-                    p_obabo[3 * i + c] = obabo_output(cf, sp, pprev, (double)Ft[o], pn, (double)es[c]);
-                } else {
-                    q[3 * i + c] = __dadd_rn(w_qmid[o], __dmul_rn(pn, hm));
-                }
-                if (ec_on) ec_dF[3 * i + c] = Ft[o] - Fraw[o];
-            }
-        }
-    }
+    commit_decide(C, K, partials, n_part, logu, st->target_step - n0);
+    const int a0 = blockIdx.x * atoms_per_block;
+    commit_atoms(C, g.N, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, n0, a0,
+                 min(g.N, a0 + atoms_per_block));
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned prev = atomicAdd(&st->blocks_done, 1u);
-        s_last = (prev == gridDim.x - 1);
-    }
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // statistics of the window, one thread per step (|delta| and the predicted rejection erf(|delta|/sqrt 8))
-    for (int j = threadIdx.x; j < K; j += blockDim.x) {
-        const double dn = sqrt(s_d[j]);
-        s_dn[j] = dn;
-        s_pr[j] = (double)erff((float)dn * 0.35355339059327373f);
-        st->accept[j] = s_acc[j];
-        st->logr[j] = s_lr[j];
-        st->logu[j] = s_lu[j];
-        st->dnorm[j] = dn;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        st->blocks_done = 0u;
-        st->n_commit_last = nc;
-        st->first_reject_last = s_rej || (s_l <= K && !s_acc[s_l - 1]) ? s_l : -1;
-        if (s_bad) atomicOr(&st->err, 2);
-        st->windows += 1;
-        st->verified += K;
-        st->committed += nc;
-        st->rejected += s_rej;
-        double sd = 0.0, sp = 0.0;
-        for (int j = 0; j < nc; ++j) {
-            sd += s_dn[j];
-            sp += s_pr[j];
-        }
-        st->sum_delta += sd;
-        st->sum_pred += sp;
-        st->step = n0 + nc;
-    }
+    if (threadIdx.x == 0) st->blocks_done = 0u;
+    commit_stats(C, K, st, n0);
 }
 
 void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *species, const float *Fd,
-                             const float *Ft, const DevState *st, double2 *partials, double *logu, cudaStream_t s) {
+                             const float *Ft, DevState *st, double2 *partials, double *logu, cudaStream_t s) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
-    transport_reduce_kernel<<<dim3(nb, K), kTransThreads, 0, s>>>(K, g, cf, species, Fd, Ft, st, partials, logu, apb);
+    transport_reduce_kernel<<<dim3(nb, K), kTransThreads, 0, s>>>(K, g, cf, species, Fd, Ft, st, partials, logu, apb,
+                                                                   0, nullptr, nullptr, nullptr, nullptr, 0, nullptr,
+                                                                   nullptr, nullptr);
 }
 
 void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
@@ -205,10 +257,19 @@ void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *spe
                                                          ec_on, q, p, p_obabo, st, partials, logu, nb, apb);
 }
 
+// Windows whose atoms fit in one block per step: one fused launch; else reduce, then commit.
 void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                       const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
                       int ec_on, double *q, double *p, double *p_obabo, DevState *st, double2 *partials, double *logu,
                       cudaStream_t s) {
+    const int apb = transport_atoms_per_block(g.N);
+    const int nb = (g.N + apb - 1) / apb;
+    if (nb == 1) {
+        transport_reduce_kernel<<<dim3(1, K), kTransThreads, 0, s>>>(K, g, cf, species, Fd, Ft, st, partials, logu,
+                                                                      apb, 1, w_qmid, w_pdraft, Fraw, ec_dF, ec_on, q,
+                                                                      p, p_obabo);
+        return;
+    }
     launch_transport_reduce(K, g, cf, species, Fd, Ft, st, partials, logu, s);
     launch_transport_commit(K, g, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, st,
                             partials, logu, s);
