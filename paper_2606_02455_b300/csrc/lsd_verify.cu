@@ -142,7 +142,7 @@ __global__ void neigh_build_kernel(const uint4 *__restrict__ fix, const int *__r
 // Per-warp staging of a row's descriptor neighbours in shared memory.
 // ---------------------------------------------------------------------------
 struct NbStage {
-    float *dx, *dy, *dz, *r, *fc, *dfc, *e1, *e2;
+    float *dx, *dy, *dz, *r, *rinv, *fc, *dfc, *e1, *e2;
     int *sp;
 };
 
@@ -152,14 +152,15 @@ __device__ __forceinline__ NbStage nb_stage_ptrs(float *base, int cap) {
     s.dy = base + cap;
     s.dz = base + 2 * cap;
     s.r = base + 3 * cap;
-    s.fc = base + 4 * cap;
-    s.dfc = base + 5 * cap;
-    s.e1 = base + 6 * cap;
-    s.e2 = base + 7 * cap;
-    s.sp = (int *)(base + 8 * cap);
+    s.rinv = base + 4 * cap;
+    s.fc = base + 5 * cap;
+    s.dfc = base + 6 * cap;
+    s.e1 = base + 7 * cap;
+    s.e2 = base + 8 * cap;
+    s.sp = (int *)(base + 9 * cap);
     return s;
 }
-constexpr int kStageFloats = 9;
+constexpr int kStageFloats = 10;
 
 __device__ __forceinline__ void nb_stage_load(const NbStage &S, const uint4 *fj, uint4 fi, const int *keys, int n,
                                               const Geo &g, float rc, int lane) {
@@ -175,6 +176,7 @@ __device__ __forceinline__ void nb_stage_load(const NbStage &S, const uint4 *fj,
         S.dy[p] = d.y;
         S.dz[p] = d.z;
         S.r[p] = r;
+        S.rinv[p] = 1.f / r;     // once per neighbour: the O(n^2) pair loops multiply
         S.fc[p] = fc;
         S.dfc[p] = dfc;
         S.e1[p] = expf(-0.005f * r2);
@@ -230,10 +232,10 @@ __global__ void desc_kernel(const uint4 *__restrict__ fix, const int *__restrict
 #pragma unroll
         for (int t = 0; t < kNAng; ++t) a[t] = 0.f;
         for (int p = 0; p < n; ++p) {
-            const float xp = S.dx[p], yp = S.dy[p], zp = S.dz[p], rp = S.r[p], fp = S.fc[p];
+            const float xp = S.dx[p], yp = S.dy[p], zp = S.dz[p], rip = S.rinv[p], fp = S.fc[p];
             const float e1p = S.e1[p], e2p = S.e2[p];
             for (int q = p + 1 + lane; q < n; q += 32) {
-                const float c = (xp * S.dx[q] + yp * S.dy[q] + zp * S.dz[q]) / (rp * S.r[q]);
+                const float c = (xp * S.dx[q] + yp * S.dy[q] + zp * S.dz[q]) * (rip * S.rinv[q]);
                 const float ff = fp * S.fc[q];
                 const float E1 = e1p * S.e1[q] * ff, E2 = e2p * S.e2[q] * ff;
                 const float bp1 = 1.f + c, bm1 = 1.f - c;
@@ -290,6 +292,7 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
         const float *wang = wbuf + g.S * nr;
         for (int p = lane; p < n; p += 32) {
             const float xp = S.dx[p], yp = S.dy[p], zp = S.dz[p], rp = S.r[p], fp = S.fc[p], dfp = S.dfc[p];
+            const float rip = S.rinv[p];
             const float e1p = S.e1[p], e2p = S.e2[p];
             // radial: c = sum_k w_k g_k'(r)
             float c = 0.f;
@@ -299,13 +302,13 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
                 const float phi = expf(-t * t * P.rbf_inv2w2);
                 c += wr[k] * phi * (-t * P.rbf_invw2 * fp + dfp);
             }
-            float gx = c * xp / rp, gy = c * yp / rp, gz = c * zp / rp;
+            float gx = c * xp * rip, gy = c * yp * rip, gz = c * zp * rip;
             if (P.n_ang) {
                 float alpha_sum_x = 0.f, alpha_sum_y = 0.f, alpha_sum_z = 0.f, beta_sum = 0.f;
                 for (int q = 0; q < n; ++q) {
                     if (q == p) continue;
-                    const float xq = S.dx[q], yq = S.dy[q], zq = S.dz[q], rq = S.r[q];
-                    const float inv_pq = 1.f / (rp * rq);
+                    const float xq = S.dx[q], yq = S.dy[q], zq = S.dz[q];
+                    const float inv_pq = rip * S.rinv[q];
                     const float cth = (xp * xq + yp * yq + zp * zq) * inv_pq;
                     const float fq = S.fc[q];
                     const float E1 = e1p * S.e1[q], E2 = e2p * S.e2[q];
@@ -333,9 +336,9 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
                     const float ffq = fp * fq;
                     // d/d(d_p): S1*E*ff*(d_q/(rp rq) - c d_p/rp^2) + S0*E*(-2 eta d_p)*ff + S0*E*dfp*fq*d_p/rp
                     const float A = (S1_1 * E1 + S1_2 * E2) * ffq * inv_pq;
-                    const float B = -(S1_1 * E1 + S1_2 * E2) * ffq * cth / (rp * rp) -
+                    const float B = -(S1_1 * E1 + S1_2 * E2) * ffq * cth * (rip * rip) -
                                     2.f * (0.005f * S0_1 * E1 + 0.05f * S0_2 * E2) * ffq +
-                                    (S0_1 * E1 + S0_2 * E2) * dfp * fq / rp;
+                                    (S0_1 * E1 + S0_2 * E2) * dfp * fq * rip;
                     alpha_sum_x += A * xq;
                     alpha_sum_y += A * yq;
                     alpha_sum_z += A * zq;
