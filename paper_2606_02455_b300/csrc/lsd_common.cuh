@@ -275,9 +275,16 @@ __device__ __forceinline__ float dsiluf_(float h) {
 // SiLU and its derivative from one exponential and one reciprocal (hardware
 // approximations, a few ulp): the tensor-core epilogues, where they are the
 // bulk of the per-element work.  h is clamped at -80 so exp(-h) stays finite.
+// rcp.approx: one special-function-unit operation, within 1 ulp (the
+// correctly rounded reciprocal takes a refinement sequence on top)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ void silu_dsilu_fast(float h, float &a, float &d) {
     const float e = __expf(-fmaxf(h, -80.f));
-    const float s = __frcp_rn(1.0f + e);
+    const float s = rcp_approx(1.0f + e);
     a = h * s;
     d = s * (1.0f + h * (1.0f - s));
 }

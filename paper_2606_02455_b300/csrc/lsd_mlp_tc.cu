@@ -11,8 +11,12 @@
 // Operand arithmetic, one template:
 //   BF16     kind::f16, K = 16 per instruction;
 //   TF32x3   FP32 targets: x = x_hi + x_lo (x_hi = tf32(x), x_lo = tf32(x - x_hi),
-//            round to nearest); lo*hi + hi*lo + hi*hi accumulate in FP32 (the
-//            dropped lo*lo is below 2^-22 of the product), K = 8;
+//            round to nearest); hi*hi + lo*hi + hi*lo in FP32 (the dropped
+//            lo*lo is below 2^-22 of the product), K = 8.  B_hi and B_lo sit
+//            one after the other in the stage, so one N = 2n instruction gives
+//            A_hi B_hi (columns [0, n)) and A_hi B_lo ([n, 2n)), and a second,
+//            N = n, adds A_lo B_hi to [0, n): two instructions per K step
+//            instead of three; the epilogue adds the two column halves;
 //   FP8      kind::f8f6f4, e4m3 with static per-tensor scales (weights: amax /
 //            448 per layer; every activation and gradient tensor: a scale
 //            calibrated once per handle), K = 32; the accumulator is rescaled
@@ -42,34 +46,37 @@ namespace lsd {
 
 constexpr int kTcRows = 128;
 constexpr int kPanelBytes = kTcRows * 128;           // one 128-byte-wide K panel of A: 16 KB
-constexpr int kStageBytes = 256 * 128;               // one B stage: 256 rows x 128 B (TF32: hi then lo, 128 rows each)
 constexpr int kEpiWarps = 16;
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kTcThreads = kEpiThreads + 32;         // + the TMA producer warp
 constexpr uint32_t kTmemCols = 512;
+constexpr int kStageBytes = 32 * 1024;               // one B stage: a 128-byte-wide K chunk of up to 256 rows
+constexpr int kMiscBytes = 2048;                     // barriers, TMEM slot, head partial sums [3][128]
 constexpr int kSmemBudget = 227 * 1024 - 1024;       // the opt-in maximum less the 1024-byte alignment slack
-constexpr int kMiscBytes = 2048;                     // barriers, TMEM slot, head partials [3][128]
 
 template <int OP> struct TcT;
+// acc: TMEM columns reserved for the accumulator
 template <> struct TcT<kTcBF16> {
-    static constexpr int elem = 2, panel = 64, mmak = 16, copies = 1, maxk = 256, maxn = 256;
+    static constexpr int elem = 2, panel = 64, mmak = 16, copies = 1, maxk = 256, maxn = 256, acc = 256;
     static constexpr uint32_t fmt = tc::kFmtBF16;
 };
 template <> struct TcT<kTcTF32x3> {
-    static constexpr int elem = 4, panel = 32, mmak = 8, copies = 2, maxk = 128, maxn = 128;
+    static constexpr int elem = 4, panel = 32, mmak = 8, copies = 2, maxk = 128, maxn = 128, acc = 256;
     static constexpr uint32_t fmt = tc::kFmtTF32;
 };
 template <> struct TcT<kTcFP8> {
-    static constexpr int elem = 1, panel = 128, mmak = 32, copies = 1, maxk = 256, maxn = 256;
+    static constexpr int elem = 1, panel = 128, mmak = 32, copies = 1, maxk = 256, maxn = 256, acc = 256;
     static constexpr uint32_t fmt = tc::kFmtE4M3;
 };
-template <int OP> constexpr int tc_a_bytes() { return TcT<OP>::maxk / TcT<OP>::panel * kPanelBytes * TcT<OP>::copies; }
-template <int OP> constexpr int tc_stages() {
+template <int OP> __host__ __device__ constexpr int tc_a_bytes() {
+    return TcT<OP>::maxk / TcT<OP>::panel * kPanelBytes * TcT<OP>::copies;
+}
+template <int OP> __host__ __device__ constexpr int tc_stages() {
     return (kSmemBudget - tc_a_bytes<OP>() - kMiscBytes) / kStageBytes > 6
                ? 6
                : (kSmemBudget - tc_a_bytes<OP>() - kMiscBytes) / kStageBytes;
 }
-template <int OP> constexpr int tc_smem_bytes() {
+template <int OP> __host__ __device__ constexpr int tc_smem_bytes() {
     return 1024 + tc_a_bytes<OP>() + tc_stages<OP>() * kStageBytes + kMiscBytes;
 }
 static_assert(tc_smem_bytes<kTcBF16>() <= 227 * 1024, "BF16 shared memory");
@@ -80,10 +87,10 @@ static_assert(tc_stages<kTcTF32x3>() >= 2, "TF32 stages");
 // Shared-memory addresses; per-stage ones are computed (a runtime-indexed
 // array would live in local memory).
 struct TcSm {
-    uint32_t a;      // A panels; TF32 lo copy at a + tc_a_bytes / 2
-    uint32_t b0;     // stage s at b0 + s kStageBytes; TF32 lo chunk kStageBytes / 2 after the hi chunk
+    uint32_t a;       // A panels; TF32 lo copy at a + tc_a_bytes / 2
+    uint32_t b0;      // stage s at b0 + s kStageBytes; TF32: the lo chunk right after the N rows of the hi chunk
     uint32_t full0, empty0, done, tslot;
-    float *ypart;    // [3][128] head partial sums of column blocks 1..3
+    float *ypart;     // [3][128] head partial sums of column blocks 1..3, then e'(y) per row
     __device__ __forceinline__ uint32_t b(int s) const { return b0 + (uint32_t)s * kStageBytes; }
     __device__ __forceinline__ uint32_t full(int s) const { return full0 + 8u * (uint32_t)s; }
     __device__ __forceinline__ uint32_t empty(int s) const { return empty0 + 8u * (uint32_t)s; }
@@ -106,48 +113,45 @@ __device__ __forceinline__ bool epi_and(bool v) {
     return r != 0;
 }
 
-// The MMAs of one GEMM (thread 0), then every epilogue thread waits for the
-// accumulator.  chunk counts B chunks over the kernel (stage = chunk % S,
-// use = chunk / S), in the producer's order; gemm counts GEMMs.
+// The MMAs of one GEMM, issued by one thread after the epilogue has published
+// A.  chunk counts B chunks over the kernel (stage = chunk % S, use = chunk /
+// S), in the producer's order.  Every chunk's stage is released to the
+// producer by a commit; the last commit arrives on `done`.
 template <int OP>
-__device__ __forceinline__ bool tc_mma(const TcSm &S, int K, int N, uint32_t tmem, uint32_t &chunk, uint32_t &gemm) {
+__device__ __forceinline__ bool tc_issue(const TcSm &S, int K, int N, uint32_t tmem, uint32_t chunk) {
     using T = TcT<OP>;
     constexpr int NS = tc_stages<OP>();
-    bool ok = true;
     const int nk = (K + T::panel - 1) / T::panel;
-    if (threadIdx.x == 0) {
-        tc::fence_after_sync();
-        const uint32_t idesc = tc::idesc_f32acc(T::fmt, kTcRows, N);
-        for (int kc = 0; kc < nk; ++kc) {
-            const uint32_t c = chunk + kc;
-            const int s = c % NS;
-            if (!tc::mbar_wait(S.full(s), (c / NS) & 1)) { ok = false; break; }
-            tc::fence_after_sync();
-            const int kend = min(T::panel, K - kc * T::panel);
-            for (int k = 0; k < kend; k += T::mmak) {
-                const uint32_t ao = S.a + kc * kPanelBytes + k * T::elem, bo = S.b(s) + k * T::elem;
-                const uint32_t acc = (kc | k) != 0;
-                if (OP == kTcTF32x3) {
-                    const uint64_t ahd = tc::sdesc_sw128(ao), ald = tc::sdesc_sw128(ao + tc_a_bytes<OP>() / 2);
-                    const uint64_t bhd = tc::sdesc_sw128(bo), bld = tc::sdesc_sw128(bo + kStageBytes / 2);
-                    tc::mma_tf32(tmem, ald, bhd, idesc, acc);
-                    tc::mma_tf32(tmem, ahd, bld, idesc, 1u);
-                    tc::mma_tf32(tmem, ahd, bhd, idesc, 1u);
-                } else if (OP == kTcFP8) {
-                    tc::mma_f8f6f4(tmem, tc::sdesc_sw128(ao), tc::sdesc_sw128(bo), idesc, acc);
-                } else {
-                    tc::mma_f16(tmem, tc::sdesc_sw128(ao), tc::sdesc_sw128(bo), idesc, acc);
-                }
-            }
-            tc::mma_commit(S.empty(s));
-        }
-        if (ok) tc::mma_commit(S.done);
-    }
-    chunk += nk;
-    if (!tc::mbar_wait(S.done, gemm & 1)) ok = false;
-    ++gemm;
     tc::fence_after_sync();
-    return ok;
+    const uint32_t idesc = tc::idesc_f32acc(T::fmt, kTcRows, N);
+    const uint32_t idesc2 = tc::idesc_f32acc(T::fmt, kTcRows, 2 * N);   // TF32: B_hi and B_lo stacked
+    for (int kc = 0; kc < nk; ++kc) {
+        const uint32_t c = chunk + kc;
+        const int s = c % NS;
+        if (!tc::mbar_wait(S.full(s), (c / NS) & 1)) return false;
+        tc::fence_after_sync();
+        const int kend = min(T::panel, K - kc * T::panel);
+        // descriptors of the chunk's first K step; a K step advances the start address by mmak * elem bytes
+        const uint64_t ad = tc::sdesc_sw128(S.a + kc * kPanelBytes), bd = tc::sdesc_sw128(S.b(s));
+#pragma unroll
+        for (int j = 0; j < T::panel / T::mmak; ++j) {
+            if (j * T::mmak >= kend) break;
+            const uint64_t step = (uint64_t)((j * T::mmak * T::elem) >> 4);
+            const uint32_t acc = (kc | j) != 0;
+            if (OP == kTcTF32x3) {
+                const uint64_t alo = tc::sdesc_sw128(S.a + tc_a_bytes<OP>() / 2 + kc * kPanelBytes) + step;
+                tc::mma_tf32(tmem, ad + step, bd + step, idesc2, acc);   // A_hi [B_hi; B_lo]
+                tc::mma_tf32(tmem, alo, bd + step, idesc, 1u);            // + A_lo B_hi
+            } else if (OP == kTcFP8) {
+                tc::mma_f8f6f4(tmem, ad + step, bd + step, idesc, acc);
+            } else {
+                tc::mma_f16(tmem, ad + step, bd + step, idesc, acc);
+            }
+        }
+        tc::mma_commit(S.empty(s));
+    }
+    tc::mma_commit(S.done);
+    return true;
 }
 
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
@@ -173,12 +177,12 @@ __device__ __forceinline__ uint32_t pack_e4m3(float a, float b, float c, float d
 template <int OP>
 __device__ __forceinline__ void store_a16(uint32_t a, int r, int c, const float (&v)[16], float qinv) {
     using T = TcT<OP>;
-    const uint32_t pbase = a + (c / T::panel) * kPanelBytes;
+    const uint32_t pofs = (c / T::panel) * kPanelBytes;
     const int e0 = c % T::panel;   // element offset inside the 128-byte row
     if (OP == kTcBF16) {
 #pragma unroll
         for (int q = 0; q < 2; ++q)
-            st_shared_v4(pbase + tc::sw128_offset(r, e0 / 8 + q), pack_bf16(v[8 * q], v[8 * q + 1]),
+            st_shared_v4(a + pofs + tc::sw128_offset(r, e0 / 8 + q), pack_bf16(v[8 * q], v[8 * q + 1]),
                          pack_bf16(v[8 * q + 2], v[8 * q + 3]), pack_bf16(v[8 * q + 4], v[8 * q + 5]),
                          pack_bf16(v[8 * q + 6], v[8 * q + 7]));
     } else if (OP == kTcTF32x3) {
@@ -190,12 +194,13 @@ __device__ __forceinline__ void store_a16(uint32_t a, int r, int c, const float 
                 h[e] = tf32_rna(v[4 * q + e]);
                 l[e] = tf32_rna(v[4 * q + e] - __uint_as_float(h[e]));
             }
-            const uint32_t off = tc::sw128_offset(r, e0 / 4 + q);
-            st_shared_v4(pbase + off, h[0], h[1], h[2], h[3]);
-            st_shared_v4(pbase + tc_a_bytes<OP>() / 2 + off, l[0], l[1], l[2], l[3]);
+            const uint32_t off = pofs + tc::sw128_offset(r, e0 / 4 + q);
+            st_shared_v4(a + off, h[0], h[1], h[2], h[3]);
+            st_shared_v4(a + tc_a_bytes<OP>() / 2 + off, l[0], l[1], l[2], l[3]);
         }
     } else {
-        st_shared_v4(pbase + tc::sw128_offset(r, e0 / 16), pack_e4m3(v[0] * qinv, v[1] * qinv, v[2] * qinv, v[3] * qinv),
+        st_shared_v4(a + pofs + tc::sw128_offset(r, e0 / 16),
+                     pack_e4m3(v[0] * qinv, v[1] * qinv, v[2] * qinv, v[3] * qinv),
                      pack_e4m3(v[4] * qinv, v[5] * qinv, v[6] * qinv, v[7] * qinv),
                      pack_e4m3(v[8] * qinv, v[9] * qinv, v[10] * qinv, v[11] * qinv),
                      pack_e4m3(v[12] * qinv, v[13] * qinv, v[14] * qinv, v[15] * qinv));
@@ -235,7 +240,7 @@ __device__ void tc_producer(const TcSm &S, const TcMaps &maps, int M, const PotD
             }
             tc::mbar_expect_tx(S.full(s), (uint32_t)T::copies * (uint32_t)N * 128u);
             tc::tma_load_2d(S.b(s), &m[0], kc * T::panel, 0, S.full(s));
-            if (OP == kTcTF32x3) tc::tma_load_2d(S.b(s) + kStageBytes / 2, &m[1], kc * T::panel, 0, S.full(s));
+            if (OP == kTcTF32x3) tc::tma_load_2d(S.b(s) + (uint32_t)N * 128u, &m[1], kc * T::panel, 0, S.full(s));
         }
     };
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
@@ -251,13 +256,19 @@ __device__ void tc_producer(const TcSm &S, const TcMaps &maps, int M, const PotD
 // scales (FP8): [l] A scale of forward GEMM l, [L + l] A scale of backward
 // GEMM l, [2L + l] weight scale of layer l.  amax (calibration, may be null):
 // |max| of the same A tensors, slots [l] and [L + l].
+//
+// The head's factor e'(y) is a per-row scalar and every backward step is
+// linear in the gradient, so the backward chain runs on u_{L-1} = w_out *
+// SiLU'(h_{L-1}) (written as the last forward epilogue's A, with no second
+// pass over the tile) and e'(y) multiplies dE/dx in the last epilogue.
+// SiLU'(h_l) is kept for l < L - 1 only.
 template <int OP>
 __global__ void __launch_bounds__(kTcThreads, 1)
     mlp_tc_kernel(const __grid_constant__ TcMaps maps, const float *__restrict__ X, int M, PotDev P,
                   float *__restrict__ E_mlp, float *__restrict__ dEdX, __nv_bfloat16 *__restrict__ scratch,
                   const float *__restrict__ scales, float *__restrict__ amax, int *__restrict__ err) {
+    constexpr int ACC = TcT<OP>::acc;   // accumulator columns reserved in TMEM
     constexpr int NS = tc_stages<OP>();
-    constexpr int ACC = TcT<OP>::maxn;   // accumulator columns
     extern __shared__ uint8_t smraw[];
     const uint32_t base = (tc::smem_u32(smraw) + 1023u) & ~1023u;
     TcSm S;
@@ -293,8 +304,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int quarter = warp & 3, cb = warp >> 2;
         const int r = 32 * quarter + lane;                               // row in the tile
         const uint32_t tacc = tmem + ((uint32_t)(32 * quarter) << 16);   // this warp's lanes, column 0
-        const bool sp_tmem = ACC + L * W <= (int)kTmemCols;              // SiLU' next to the accumulator
-        __nv_bfloat16 *my_scr = scratch ? scratch + (size_t)blockIdx.x * L * kTcRows * W : nullptr;
+        const bool sp_tmem = ACC + (L - 1) * W <= (int)kTmemCols;        // SiLU' next to the accumulator
+        __nv_bfloat16 *my_scr = scratch ? scratch + (size_t)blockIdx.x * (L - 1) * kTcRows * W : nullptr;
         auto sp_addr = [&](int l, int c) -> __nv_bfloat16 * { return my_scr + ((size_t)l * kTcRows + r) * W + c; };
         auto store_sp = [&](int l, int c, const float (&d)[16]) {
             if (sp_tmem) {
@@ -305,6 +316,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                   pack_bf16(d[6], d[7]));
                 o[1] = make_uint4(pack_bf16(d[8], d[9]), pack_bf16(d[10], d[11]), pack_bf16(d[12], d[13]),
                                   pack_bf16(d[14], d[15]));
+            }
+        };
+        // the accumulator's columns [c, c + 16) of an N-column GEMM (TF32: the sum of the two halves)
+        auto load_acc = [&](int c, int N, float (&v)[16]) {
+            tc::tmem_ld16(tacc + c, v);
+            if (OP == kTcTF32x3) {
+                float u[16];
+                tc::tmem_ld16(tacc + N + c, u);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] += u[i];
             }
         };
         auto load_sp = [&](int l, int c, float (&d)[16]) {
@@ -325,10 +346,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
             }
         };
-        const float sc_x = OP == kTcFP8 ? scales[0] : 1.f;
+        // The epilogue's A stores become visible to the tensor core, then
+        // thread 0 issues the next GEMM.  Lanes 1..31 of warp 0 wait at the
+        // warp barrier meanwhile: spinning on an mbarrier in the same warp
+        // would take issue turns from the issuing lane.
         uint32_t chunk = 0, gemm = 0;
-        const int ntiles = (M + kTcRows - 1) / kTcRows;
+        auto issue = [&](int K, int N) -> bool {
+            tc::fence_async_shared();
+            tc::fence_before_sync();
+            epi_sync();
+            bool iok = true;
+            if (warp == 0) {
+                if (lane == 0) iok = tc_issue<OP>(S, K, N, tmem, chunk);
+                __syncwarp();
+            }
+            chunk += (K + TcT<OP>::panel - 1) / TcT<OP>::panel;
+            return iok;
+        };
+        auto wait_acc = [&](bool iok) -> bool {
+            const bool w = tc::mbar_wait(S.done, gemm & 1);
+            ++gemm;
+            tc::fence_after_sync();
+            return epi_and(iok && w);
+        };
         bool ok = true;
+        const float sc_x = OP == kTcFP8 ? scales[0] : 1.f;
+        const int ntiles = (M + kTcRows - 1) / kTcRows;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const int row = tile * kTcRows + r;
             const bool live = row < M;
@@ -354,21 +397,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 store_a16<OP>(S.a, r, c, v, 1.f / sc_x);
             }
             if (amax) record_amax(amax, 0, am);
-            tc::fence_async_shared();
-            tc::fence_before_sync();
-            epi_sync();
-            // forward
-            float y = 0.f;
+            // forward; the last layer's epilogue also writes the backward chain's first A
+            float y = 0.f, dedy = 0.f;
             for (int l = 0; l < L; ++l) {
-                ok = epi_and(tc_mma<OP>(S, l == 0 ? d0p : W, W, tmem, chunk, gemm));
+                const bool last = l == L - 1;
+                ok = wait_acc(issue(l == 0 ? d0p : W, W));
                 if (!ok) break;
                 const float dq = OP == kTcFP8 ? scales[l] * scales[2 * L + l] : 1.f;
-                const float qinv = (OP == kTcFP8 && l + 1 < L) ? 1.f / scales[l + 1] : 1.f;
+                const float qinv = OP == kTcFP8 ? 1.f / scales[last ? L + L - 1 : l + 1] : 1.f;
                 const float *bl = layer_bias(P, l);
                 am = 0.f;
                 for (int c = 16 * cb; c < W; c += 64) {
                     float v[16], d[16];
-                    tc::tmem_ld16(tacc + c, v);
+                    load_acc(c, W, v);
                     const float4 *b4p = reinterpret_cast<const float4 *>(bl + c);
 #pragma unroll
                     for (int i = 0; i < 16; i += 4) {
@@ -378,66 +419,58 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         silu_dsilu_fast(v[i + 2] * dq + b4.z, v[i + 2], d[i + 2]);
                         silu_dsilu_fast(v[i + 3] * dq + b4.w, v[i + 3], d[i + 3]);
                     }
-                    store_sp(l, c, d);
-                    if (l == L - 1) {
+                    if (last) {
+                        const float4 *w4p = reinterpret_cast<const float4 *>(P.wout + c);
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) y += v[i] * P.wout[c + i];
+                        for (int i = 0; i < 16; i += 4) {
+                            const float4 w4 = __ldg(w4p + i / 4);
+                            y += v[i] * w4.x + v[i + 1] * w4.y + v[i + 2] * w4.z + v[i + 3] * w4.w;
+                            d[i] *= w4.x;
+                            d[i + 1] *= w4.y;
+                            d[i + 2] *= w4.z;
+                            d[i + 3] *= w4.w;
+                        }
+                        if (amax) am = amax16(am, d);
+                        store_a16<OP>(S.a, r, c, d, qinv);
                     } else {
+                        store_sp(l, c, d);
                         if (amax) am = amax16(am, v);
                         store_a16<OP>(S.a, r, c, v, qinv);
                     }
                 }
-                if (amax && l + 1 < L) record_amax(amax, l + 1, am);
-                if (l == L - 1 && cb > 0) S.ypart[(cb - 1) * kTcRows + r] = y;
-                tc::fence_async_shared();
-                tc::fence_before_sync();
-                epi_sync();
+                if (amax) record_amax(amax, last ? L + L - 1 : l + 1, am);
+                if (last && cb > 0) S.ypart[(cb - 1) * kTcRows + r] = y;
             }
             if (!ok) break;
-            // energy head: column block 0 adds the partial sums; e'(y) to every column block
-            if (cb == 0) {
-                for (int b = 1; b < 4 && 16 * b < W; ++b) y += S.ypart[(b - 1) * kTcRows + r];
-                y += P.bout;
-                float dedy;
-                if (P.head == LSD_HEAD_LINEAR) {
-                    if (live) E_mlp[row] = y;
-                    dedy = 1.f;
-                } else {
-                    const float t = tanhf(y);
-                    if (live) E_mlp[row] = P.head_scale * t;
-                    dedy = P.head_scale * (1.f - t * t);
-                }
-                S.ypart[r] = dedy;
-            }
-            epi_sync();
-            {
-                const float dedy = S.ypart[r];
-                const float qinv = OP == kTcFP8 ? 1.f / scales[L + L - 1] : 1.f;
-                am = 0.f;
-                for (int c = 16 * cb; c < W; c += 64) {
-                    float v[16];
-                    load_sp(L - 1, c, v);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] *= dedy * P.wout[c + i];
-                    if (amax) am = amax16(am, v);
-                    store_a16<OP>(S.a, r, c, v, qinv);
-                }
-                if (amax) record_amax(amax, L + L - 1, am);
-            }
-            tc::fence_async_shared();
-            tc::fence_before_sync();
-            epi_sync();
-            // backward
+            // backward; the head (energy, e'(y)) is finished while the first backward GEMM runs
             for (int l = L - 1; l >= 0; --l) {
                 const int dout = l == 0 ? d0p : W;
-                ok = epi_and(tc_mma<OP>(S, W, dout, tmem, chunk, gemm));
+                const bool iok = issue(W, dout);
+                if (l == L - 1) {
+                    if (cb == 0) {
+                        for (int b = 1; b < 4 && 16 * b < W; ++b) y += S.ypart[(b - 1) * kTcRows + r];
+                        y += P.bout;
+                        if (P.head == LSD_HEAD_LINEAR) {
+                            if (live) E_mlp[row] = y;
+                            dedy = 1.f;
+                        } else {
+                            const float t = tanhf(y);
+                            if (live) E_mlp[row] = P.head_scale * t;
+                            dedy = P.head_scale * (1.f - t * t);
+                        }
+                        S.ypart[r] = dedy;
+                    }
+                    epi_sync();
+                    dedy = S.ypart[r];
+                }
+                ok = wait_acc(iok);
                 if (!ok) break;
                 const float dq = OP == kTcFP8 ? scales[L + l] * scales[2 * L + l] : 1.f;
                 const float qinv = (OP == kTcFP8 && l > 0) ? 1.f / scales[L + l - 1] : 1.f;
                 am = 0.f;
                 for (int c = 16 * cb; c < dout; c += 64) {
                     float v[16];
-                    tc::tmem_ld16(tacc + c, v);
+                    load_acc(c, dout, v);
                     if (l > 0) {
                         float d[16];
                         load_sp(l - 1, c, d);
@@ -446,16 +479,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         if (amax) am = amax16(am, v);
                         store_a16<OP>(S.a, r, c, v, qinv);
                     } else if (live) {
+                        const float f = dq * dedy;
                         float4 *dst = reinterpret_cast<float4 *>(dEdX + (size_t)row * d0p + c);
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
-                            dst[i] = make_float4(v[4 * i] * dq, v[4 * i + 1] * dq, v[4 * i + 2] * dq, v[4 * i + 3] * dq);
+                            dst[i] = make_float4(v[4 * i] * f, v[4 * i + 1] * f, v[4 * i + 2] * f, v[4 * i + 3] * f);
                     }
                 }
                 if (amax && l > 0) record_amax(amax, L + l - 1, am);
-                tc::fence_async_shared();
-                tc::fence_before_sync();
-                epi_sync();
             }
         }
         if (!ok && tid == 0) atomicOr(err, 8);
@@ -506,7 +537,7 @@ static bool make_map(CUtensorMap *m, int op, const void *ptr, int rows, int cols
 
 bool mlp_tc_supported(int op, const PotDev &P) {
     if (!P.has_mlp || P.width % 32 != 0 || P.n_layers > kMaxLayers || P.n_layers < 1 || !encode_fn()) return false;
-    if (op == kTcTF32x3) return P.width <= 128 && P.d0p <= 128 && 128 + P.n_layers * P.width <= (int)kTmemCols;
+    if (op == kTcTF32x3) return P.width <= 128 && P.d0p <= 128 && 256 + (P.n_layers - 1) * P.width <= (int)kTmemCols;
     return P.width <= 256 && P.d0p <= 256;
 }
 
@@ -536,10 +567,11 @@ size_t mlp_tc_smem_bytes(int op) {
     return op == kTcBF16 ? tc_smem_bytes<kTcBF16>() : (op == kTcTF32x3 ? tc_smem_bytes<kTcTF32x3>() : tc_smem_bytes<kTcFP8>());
 }
 
+// SiLU'(h_l) of the hidden layers but the last, per CTA, when it does not fit
+// next to the accumulator in TMEM
 size_t mlp_tc_scratch_elems(int op, const PotDev &P, int n_cta) {
-    const int acc = op == kTcTF32x3 ? 128 : 256;
-    if (acc + P.n_layers * P.width <= (int)kTmemCols) return 0;
-    return (size_t)n_cta * P.n_layers * kTcRows * P.width;
+    if (256 + (P.n_layers - 1) * P.width <= (int)kTmemCols) return 0;
+    return (size_t)n_cta * (P.n_layers - 1) * kTcRows * P.width;
 }
 
 int mlp_tc_grid(int M, int n_sm) {

@@ -159,3 +159,30 @@ def test_fp8_potential_is_one_function():
     F1 = h.target_forces(q).cpu().numpy()
     assert np.array_equal(F0, F1)
     h.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("bf16", BF16_TOL)])
+def test_persistent_tiles_match_single_tile_launches(precision, tol):
+    """The grid is one CTA per SM looping over 128-row tiles: 40 configurations of 512 atoms are 160 tiles on 148
+    SMs, so some CTAs run a second tile with their barrier phases carried over.  Those configurations agree with the
+    same ones evaluated two at a time (8 tiles, one per CTA), and the FP32 form with the CUDA-core kernel."""
+    import torch
+    from paper_2606_02455_b300 import lsd
+    s, draft, tgt = _system(cells=8, precision=precision)
+    n = 40
+    integ = W.Integrator(0.5, 0.01, 350.0, n)   # a batch holds up to K configurations
+    h = lsd.LSD(s, draft, tgt, integ)
+    rng = np.random.default_rng(11)
+    qs = np.stack([s.positions + 0.05 * rng.standard_normal(s.positions.shape) for _ in range(n)])
+    big = h.target_forces(torch.tensor(qs, device="cuda")).cpu().numpy()
+    for c0 in (0, n - 2):
+        small = h.target_forces(torch.tensor(qs[c0:c0 + 2], device="cuda")).cpu().numpy()
+        for c in range(2):
+            assert _rel(small[c], big[c0 + c].astype(np.float64)) < tol
+    if precision == "fp32":
+        hc = lsd.LSD(s, draft, W.replace(tgt, precision="fp32-cuda-cores"), integ)
+        ref = hc.target_forces(torch.tensor(qs, device="cuda")).cpu().numpy()
+        for c in range(n):
+            assert _rel(big[c], ref[c].astype(np.float64)) < tol
+        hc.close()
+    h.close()
