@@ -102,6 +102,7 @@ struct lsd_handle {
         double *qmid = nullptr, *pdraft = nullptr;
         float *Fd = nullptr, *Fraw = nullptr;
         uint4 *fix = nullptr;
+        double *logu = nullptr;   // [K] log u of the acceptance test, written by the draft
         VerletBufs vb;
     } wb[2];
     bool pipe_on = false, pipe_alloc = false, pipe_primed = false;
@@ -414,7 +415,7 @@ void enqueue_draft_buf(lsd_handle *h, int b, cudaStream_t s, WinHdr *hdr, const 
     if (!h->vplan.all_pairs)
         launch_verlet_build(h->vplan, q, h->species, h->geo, w.vb, h->st, s, hdr ? &hdr->skip : nullptr);
     launch_draft(h->dplan, h->learned_small, h->K, h->geo, h->draft.dev, h->coef, h->vplan, w.vb, h->species, q, p,
-                 h->ec_dF, h->ec_on, h->st, w.qmid, w.pdraft, w.Fd, w.Fraw, w.fix, h->w_dEdX, s, hdr);
+                 h->ec_dF, h->ec_on, h->st, w.qmid, w.pdraft, w.Fd, w.Fraw, w.fix, h->w_dEdX, w.logu, s, hdr);
 }
 
 // Verification, frames and transport of window buffer b.
@@ -423,7 +424,7 @@ void enqueue_verify_buf(lsd_handle *h, int b, cudaStream_t s) {
     enqueue_eval(h, h->target, w.fix, h->K, h->w_Ft, nullptr, s, !h->vplan.all_pairs, &w.vb);
     if (h->train.capture_on) enqueue_frame_capture(h->train, w.qmid, h->w_Ft, h->K, h->N, h->st, s);
     launch_transport(h->K, h->geo, h->coef, h->species, w.qmid, w.pdraft, w.Fd, h->w_Ft, w.Fraw, h->ec_dF, h->ec_on,
-                     h->q, h->p, h->p_obabo, h->st, h->partials, h->logu, s);
+                     h->q, h->p, h->p_obabo, h->st, h->partials, w.logu, s);
 }
 
 void enqueue_draft(lsd_handle *h, cudaStream_t s) { enqueue_draft_buf(h, 0, s, nullptr, h->q, h->p); }
@@ -730,7 +731,8 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     }
     h->cap_near = std::min(nb_capacity(rho, rnear, 32), (27 * h->N + 31) / 32 * 32);
     h->cap_far = std::min(nb_capacity(rho, rfar, 32), (27 * h->N + 31) / 32 * 32);
-    if (desc_smem_bytes(8, h->cap_near) + 8 * 256 * sizeof(float) > (size_t)kMaxDynSmem) return fail(LSD_EUNSUPPORTED);
+    if (desc_smem_bytes(8, h->cap_near) + 8 * (256 + 4 * h->cap_near) * sizeof(float) > (size_t)kMaxDynSmem)
+        return fail(LSD_EUNSUPPORTED);
     if (verify_kernels_setup(kMaxDynSmem) != cudaSuccess || mlp_kernels_setup(kMaxDynSmem) != cudaSuccess ||
         mlp_tc_setup() != cudaSuccess ||
         draft_kernels_setup(kMaxDynSmem) != cudaSuccess ||
@@ -788,6 +790,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     h->wb[0].Fd = h->w_Fd;
     h->wb[0].Fraw = h->w_Fraw;
     h->wb[0].fix = h->w_fix;
+    h->wb[0].logu = h->logu;
     h->wb[0].vb = h->vbufs;
     if ((rc = pot_upload(h, h->draft)) != LSD_OK) return fail(rc);
     if ((rc = pot_upload(h, h->target)) != LSD_OK) return fail(rc);
@@ -1009,7 +1012,7 @@ int lsd_set_pipelining(lsd_handle *h, int32_t on) {
             (rc = dalloc(h, &w.vb.cell_start, ncell + 1)) || (rc = dalloc(h, &w.vb.cell_atoms, N)) ||
             (rc = dalloc(h, &w.vb.cell_scratch, 1)) || (rc = dalloc(h, &w.vb.vlist, N * h->vplan.cap)) ||
             (rc = dalloc(h, &w.vb.vcount, N)) || (rc = dalloc(h, &h->hdr, 2)) || (rc = dalloc(h, &h->qb, D)) ||
-            (rc = dalloc(h, &h->pb, D)))
+            (rc = dalloc(h, &h->pb, D)) || (rc = dalloc(h, &w.logu, (size_t)h->K)))
             return rc;
         int lo = 0, hi = 0;
         CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
@@ -1195,7 +1198,7 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
     launch_force_gather(h->near_keys, h->n_near, h->cap_near, M, h->N, P.has_mlp, h->pair_g, h->Fpart, h->E_lj,
                         h->E_mlp, h->w_Ft, nullptr, h->st, st);
     CK(cudaEventRecord(ev[6], st));
-    launch_transport_reduce(h->K, h->geo, h->coef, h->species, h->w_Fd, h->w_Ft, h->st, h->partials, h->logu, st);
+    launch_transport_reduce(h->K, h->geo, h->coef, h->species, h->w_Fd, h->w_Ft, h->st, h->partials, st);
     CK(cudaEventRecord(ev[7], st));
     launch_transport_commit(h->K, h->geo, h->coef, h->species, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Ft, h->w_Fraw,
                             h->ec_dF, h->ec_on, h->q, h->p, h->p_obabo, h->st, h->partials, h->logu, st);

@@ -293,6 +293,14 @@ __device__ __forceinline__ float d2siluf_(float h) {
     return s * (1.0f - s) * (2.0f + h * (1.0f - 2.0f * s));
 }
 
+// Programmatic dependent launch: a kernel launched with launch_dependent() may
+// start while the stream's previous kernel is still running; pdl_wait() blocks
+// until that kernel (and so every earlier one) has finished and its writes are
+// visible, and pdl_release() lets the stream's next kernel begin launching.
+// Both are no-ops in a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

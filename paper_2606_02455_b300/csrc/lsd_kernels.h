@@ -3,9 +3,30 @@
 
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "lsd_common.cuh"
 
 namespace lsd {
+
+// Launches kern as a programmatic dependent of the stream's previous kernel
+// (its launch overlaps that kernel's tail).  Only for kernels that call
+// pdl_wait() before touching memory an earlier kernel writes.
+template <typename... KArgs, typename... Args>
+inline void launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // verification (lsd_verify.cu)
 void launch_fixpoint(const double *q, const int *species, int M, const Geo &g, uint4 *fix, cudaStream_t s);
@@ -78,15 +99,15 @@ int mlp_tc_static_launch(const void *plan, const float *X, int M, const PotDev &
 // transport (lsd_transport.cu)
 int transport_atoms_per_block(int N);
 void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *species, const float *Fd,
-                             const float *Ft, DevState *st, double2 *partials, double *logu, cudaStream_t s);
+                             const float *Ft, DevState *st, double2 *partials, cudaStream_t s);
 void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                              const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
                              int ec_on, double *q, double *p, double *p_obabo, DevState *st,
                              const double2 *partials, const double *logu, cudaStream_t s);
 void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                       const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
-                      int ec_on, double *q, double *p, double *p_obabo, DevState *st, double2 *partials, double *logu,
-                      cudaStream_t s);
+                      int ec_on, double *q, double *p, double *p_obabo, DevState *st, double2 *partials,
+                      const double *logu, cudaStream_t s);
 
 // draft and plain integrator (lsd_draft.cu)
 struct DraftPlan {
@@ -104,8 +125,8 @@ int draft_max_cluster(size_t smem, bool learned);
 cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf,
                          const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
                          const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
-                         double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX, cudaStream_t s,
-                         WinHdr *hdr = nullptr);
+                         double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX, double *w_logu,
+                         cudaStream_t s, WinHdr *hdr = nullptr);
 // the pipelined window loop (lsd_draft.cu)
 void launch_spec_base(const Geo &g, const Coef &cf, const int *species, const double *qmid_b, const double *pdraft_b,
                       const WinHdr *hb, WinHdr *hn, double *qb, double *pb, cudaStream_t s);

@@ -92,6 +92,8 @@ __device__ __forceinline__ void gemm_dispatch(int ncols, const float *A, int lda
 
 __global__ void __launch_bounds__(256) mlp_fp32_kernel(const float *__restrict__ X, int M, PotDev P,
                                                        float *__restrict__ E_mlp, float *__restrict__ dEdX) {
+    pdl_wait();
+    pdl_release();
     extern __shared__ float sm[];
     const int d0p = P.d0p, W = P.width, L = P.n_layers;
     const int ld = d0p > W ? d0p : W;
@@ -173,7 +175,7 @@ size_t mlp_fp32_smem_bytes(const PotDev &P) {
 }
 
 void launch_mlp_fp32(const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX, cudaStream_t s) {
-    mlp_fp32_kernel<<<(M + kTM - 1) / kTM, 256, mlp_fp32_smem_bytes(P), s>>>(X, M, P, E_mlp, dEdX);
+    launch_dependent(mlp_fp32_kernel, (M + kTM - 1) / kTM, 256, mlp_fp32_smem_bytes(P), s, X, M, P, E_mlp, dEdX);
 }
 
 cudaError_t mlp_kernels_setup(int max_smem) {

@@ -369,6 +369,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             tc::fence_after_sync();
             return epi_and(iok && w);
         };
+        // the descriptors come from the stream's previous kernel (the producer's
+        // weight copies do not depend on it and start at once)
+        pdl_wait();
+        pdl_release();
         bool ok = true;
         const float sc_x = OP == kTcFP8 ? scales[0] : 1.f;
         const int ntiles = (M + kTcRows - 1) / kTcRows;
@@ -584,16 +588,16 @@ static void launch_grid(const TcPlanImpl *pl, int grid, const float *X, int M, c
                         cudaStream_t s) {
     switch (pl->op) {
         case kTcBF16:
-            mlp_tc_kernel<kTcBF16><<<grid, kTcThreads, tc_smem_bytes<kTcBF16>(), s>>>(pl->maps, X, M, P, E_mlp, dEdX,
-                                                                                     scratch, scales, amax, err);
+            launch_dependent(mlp_tc_kernel<kTcBF16>, grid, kTcThreads, tc_smem_bytes<kTcBF16>(), s, pl->maps, X, M, P,
+                             E_mlp, dEdX, scratch, scales, amax, err);
             break;
         case kTcTF32x3:
-            mlp_tc_kernel<kTcTF32x3><<<grid, kTcThreads, tc_smem_bytes<kTcTF32x3>(), s>>>(
-                pl->maps, X, M, P, E_mlp, dEdX, scratch, scales, amax, err);
+            launch_dependent(mlp_tc_kernel<kTcTF32x3>, grid, kTcThreads, tc_smem_bytes<kTcTF32x3>(), s, pl->maps, X, M,
+                             P, E_mlp, dEdX, scratch, scales, amax, err);
             break;
         default:
-            mlp_tc_kernel<kTcFP8><<<grid, kTcThreads, tc_smem_bytes<kTcFP8>(), s>>>(pl->maps, X, M, P, E_mlp, dEdX,
-                                                                                   scratch, scales, amax, err);
+            launch_dependent(mlp_tc_kernel<kTcFP8>, grid, kTcThreads, tc_smem_bytes<kTcFP8>(), s, pl->maps, X, M, P,
+                             E_mlp, dEdX, scratch, scales, amax, err);
             break;
     }
 }

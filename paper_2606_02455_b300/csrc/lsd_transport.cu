@@ -8,8 +8,12 @@
 // A rejected step's momentum is <p> + sigma (z - 2 (z.delta/delta.delta) delta)
 // and its position q_mid + (dt/2) p/m (the shared map g = A of Thm 3.1).
 //
-// transport_reduce_kernel: per (chunk of atoms, window step) FP64 partial sums
-//   of z.delta and delta.delta, written to a fixed slot (no atomics).
+// transport_reduce_kernel: per (chunk of atoms, window step) partial sums of
+//   z.delta and delta.delta, written to a fixed slot (no atomics).  An atom's
+//   three-term products and a warp's 32 atoms are summed in FP32 (the FP32
+//   forces bound delta's accuracy anyway); warps, chunks and the log ratio
+//   are FP64.  log u comes from the draft (one FP64 log per step, computed
+//   off this critical path).
 // transport_commit_kernel: every CTA sums the partials in the same fixed
 //   order, finds l = first rejected step, and commits its slice of atoms:
 //   the draft's own bits for an accepted step, the reflection for a rejected
@@ -21,15 +25,22 @@ namespace lsd {
 
 constexpr int kTransThreads = 256;
 
-__device__ __forceinline__ double block_sum_d(double v, double *sh) {
+// The block's sums of a and b: FP32 within a warp, FP64 over the warps (warp 0).
+__device__ __forceinline__ double2 block_sum2(float a, float b, double2 *sh) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_sum_d(v);
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) sh[w] = make_double2((double)a, (double)b);
     __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < nw; ++k) t += sh[k];
+    double2 t = make_double2(0.0, 0.0);
+    if (w == 0) {
+        if (lane < nw) t = sh[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            t.x += __shfl_down_sync(0xffffffffu, t.x, o);
+            t.y += __shfl_down_sync(0xffffffffu, t.y, o);
+        }
+    }
     return t;   // valid in thread 0
 }
 
@@ -37,8 +48,9 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh) {
 // reduce-commit for windows whose atoms fit in one block).
 struct CommitShared {
     double s[kMaxK], d[kMaxK], lr[kMaxK], lu[kMaxK], dn[kMaxK], pr[kMaxK];
-    int acc[kMaxK];
+    int acc[kMaxK], fin[kMaxK];
     int nc, rej, l, bad;
+    double factor;   // 2 z.delta / delta.delta of the committed step when it was rejected
 };
 
 // Sums the partials of every window step in a fixed order, forms log r and
@@ -59,12 +71,13 @@ __device__ void commit_decide(CommitShared &C, int K, const double2 *__restrict_
         C.lr[j] = lr;
         C.lu[j] = lu;
         C.acc[j] = (d == 0.0) || (lu <= fmin(0.0, lr));
+        C.fin[j] = isfinite(lr);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         int l = K, rej = 0, bad = 0;
         for (int j = 0; j < K; ++j) {
-            if (!isfinite(C.lr[j])) { bad = 1; l = j + 1; break; }
+            if (!C.fin[j]) { bad = 1; l = j + 1; break; }
             if (!C.acc[j]) { l = j + 1; rej = 1; break; }
         }
         const int nc = (long long)l < rem ? l : (int)rem;
@@ -72,6 +85,7 @@ __device__ void commit_decide(CommitShared &C, int K, const double2 *__restrict_
         C.nc = bad ? 0 : nc;
         C.rej = (rej && nc == l) ? 1 : 0;
         C.bad = bad;
+        C.factor = C.rej ? 2.0 * C.s[nc - 1] / C.d[nc - 1] : 0.0;
     }
     __syncthreads();
 }
@@ -89,7 +103,7 @@ __device__ void commit_atoms(const CommitShared &C, int N, const Coef &cf, const
     if (nc <= 0) return;
     const int jj = nc - 1;
     const size_t D = (size_t)3 * N;
-    const double factor = C.rej ? 2.0 * C.s[jj] / C.d[jj] : 0.0;
+    const double factor = C.factor;
     const unsigned long long n = (unsigned long long)(n0 + jj + 1);
     for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
         const int sp = species[i];
@@ -136,6 +150,15 @@ __device__ void commit_stats(CommitShared &C, int K, DevState *__restrict__ st, 
         st->dnorm[j] = dn;
     }
     __syncthreads();
+    double sd = 0.0, sp = 0.0;
+    if (threadIdx.x < 32) {
+        for (int j = threadIdx.x; j < nc; j += 32) {
+            sd += C.dn[j];
+            sp += C.pr[j];
+        }
+        sd = warp_sum_d(sd);
+        sp = warp_sum_d(sp);
+    }
     if (threadIdx.x == 0) {
         st->n_commit_last = nc;
         st->first_reject_last = C.rej || (C.l <= K && !C.acc[C.l - 1]) ? C.l : -1;
@@ -144,11 +167,6 @@ __device__ void commit_stats(CommitShared &C, int K, DevState *__restrict__ st, 
         st->verified += K;
         st->committed += nc;
         st->rejected += C.rej;
-        double sd = 0.0, sp = 0.0;
-        for (int j = 0; j < nc; ++j) {
-            sd += C.dn[j];
-            sp += C.pr[j];
-        }
         st->sum_delta += sd;
         st->sum_pred += sp;
         st->step = n0 + nc;
@@ -156,44 +174,43 @@ __device__ void commit_stats(CommitShared &C, int K, DevState *__restrict__ st, 
 }
 
 // Per window step j (blockIdx.y) and slice of atoms (blockIdx.x): z.delta and
-// delta.delta in FP64, with delta = (1+c1)(dt/2)kappa (F~ - F) / sigma and
-// z = xi (the draft's own noise); log u of step j by block (0, j).  fused:
+// delta.delta, with delta = (1+c1)(dt/2)kappa (F~ - F) / sigma and z = xi (the
+// draft's own noise).  fused:
 // the window's atoms fit in one block, and the last block to finish decides,
 // commits every atom and updates the statistics (no second launch).
 __global__ void __launch_bounds__(kTransThreads)
     transport_reduce_kernel(int K, Geo g, Coef cf, const int *__restrict__ species, const float *__restrict__ Fd,
                             const float *__restrict__ Ft, DevState *__restrict__ st, double2 *__restrict__ partials,
-                            double *__restrict__ logu, int atoms_per_block, int fused,
+                            const double *__restrict__ logu, int atoms_per_block, int fused,
                             const double *__restrict__ w_qmid, const double *__restrict__ w_pdraft,
                             const float *__restrict__ Fraw, float *__restrict__ ec_dF, int ec_on,
                             double *__restrict__ q, double *__restrict__ p, double *__restrict__ p_obabo) {
-    __shared__ double sh[32];
+    __shared__ double2 sh[32];
     __shared__ CommitShared C;
     __shared__ bool s_last;
+    pdl_wait();
+    pdl_release();
     if (st->step >= st->target_step) return;   // uniform over the grid
     const int N = g.N;
     const int j = blockIdx.y;
     const int keff = st->k_eff;
     if (j < keff) {                            // steps the draft did not reach are skipped
         const unsigned long long n = (unsigned long long)(st->step + j + 1);
-        // log u of the acceptance test, one FP64 log per window step, in parallel over steps
-        if (blockIdx.x == 0 && threadIdx.x == blockDim.x - 1) logu[j] = log(uniform53(cf.seed, n));
         const int a0 = blockIdx.x * atoms_per_block;
         const int a1 = min(N, a0 + atoms_per_block);
-        double s = 0.0, d = 0.0;
+        float s = 0.f, d = 0.f;
         for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
             const float3 xi = normals3(cf.seed, n, (uint32_t)i, 0u);
-            const double k = species_pick(cf.aF_sig, species[i]);
+            const float k = (float)species_pick(cf.aF_sig, species[i]);
             const size_t o = ((size_t)j * N + i) * 3;
-            const double d0 = k * ((double)Fd[o + 0] - (double)Ft[o + 0]);
-            const double d1 = k * ((double)Fd[o + 1] - (double)Ft[o + 1]);
-            const double d2 = k * ((double)Fd[o + 2] - (double)Ft[o + 2]);
-            s += (double)xi.x * d0 + (double)xi.y * d1 + (double)xi.z * d2;
+            const float d0 = k * (Fd[o + 0] - Ft[o + 0]);
+            const float d1 = k * (Fd[o + 1] - Ft[o + 1]);
+            const float d2 = k * (Fd[o + 2] - Ft[o + 2]);
+            s += xi.x * d0 + xi.y * d1 + xi.z * d2;
             d += d0 * d0 + d1 * d1 + d2 * d2;
         }
-        const double S = block_sum_d(s, sh);
-        const double D = block_sum_d(d, sh);
-        if (threadIdx.x == 0) partials[(size_t)j * gridDim.x + blockIdx.x] = make_double2(S, D);
+        const double2 SD = block_sum2(s, d, sh);
+        if (threadIdx.x == 0) partials[(size_t)j * gridDim.x + blockIdx.x] = SD;
     }
     if (!fused) return;
     __threadfence();
@@ -221,6 +238,8 @@ __global__ void __launch_bounds__(kTransThreads)
                             int atoms_per_block) {
     __shared__ CommitShared C;
     __shared__ bool s_last;
+    pdl_wait();
+    pdl_release();
     if (st->step >= st->target_step) return;
     K = min(K, st->k_eff);   // the window holds the k_eff steps the draft reached
     const long long n0 = st->step;
@@ -239,12 +258,12 @@ __global__ void __launch_bounds__(kTransThreads)
 }
 
 void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *species, const float *Fd,
-                             const float *Ft, DevState *st, double2 *partials, double *logu, cudaStream_t s) {
+                             const float *Ft, DevState *st, double2 *partials, cudaStream_t s) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
-    transport_reduce_kernel<<<dim3(nb, K), kTransThreads, 0, s>>>(K, g, cf, species, Fd, Ft, st, partials, logu, apb,
-                                                                   0, nullptr, nullptr, nullptr, nullptr, 0, nullptr,
-                                                                   nullptr, nullptr);
+    launch_dependent(transport_reduce_kernel, dim3(nb, K), kTransThreads, 0, s, K, g, cf, species, Fd, Ft, st, partials,
+                     (const double *)nullptr, apb, 0, (const double *)nullptr, (const double *)nullptr, (const float *)nullptr,
+                     (float *)nullptr, 0, (double *)nullptr, (double *)nullptr, (double *)nullptr);
 }
 
 void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
@@ -253,24 +272,23 @@ void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *spe
                              const double2 *partials, const double *logu, cudaStream_t s) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
-    transport_commit_kernel<<<nb, kTransThreads, 0, s>>>(K, g, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF,
-                                                         ec_on, q, p, p_obabo, st, partials, logu, nb, apb);
+    launch_dependent(transport_commit_kernel, nb, kTransThreads, 0, s, K, g, cf, species, w_qmid, w_pdraft, Fd, Ft,
+                     Fraw, ec_dF, ec_on, q, p, p_obabo, st, (const double2 *)partials, (const double *)logu, nb, apb);
 }
 
 // Windows whose atoms fit in one block per step: one fused launch; else reduce, then commit.
 void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                       const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
-                      int ec_on, double *q, double *p, double *p_obabo, DevState *st, double2 *partials, double *logu,
-                      cudaStream_t s) {
+                      int ec_on, double *q, double *p, double *p_obabo, DevState *st, double2 *partials,
+                      const double *logu, cudaStream_t s) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
     if (nb == 1) {
-        transport_reduce_kernel<<<dim3(1, K), kTransThreads, 0, s>>>(K, g, cf, species, Fd, Ft, st, partials, logu,
-                                                                      apb, 1, w_qmid, w_pdraft, Fraw, ec_dF, ec_on, q,
-                                                                      p, p_obabo);
+        launch_dependent(transport_reduce_kernel, dim3(1, K), kTransThreads, 0, s, K, g, cf, species, Fd, Ft, st,
+                         partials, logu, apb, 1, w_qmid, w_pdraft, Fraw, ec_dF, ec_on, q, p, p_obabo);
         return;
     }
-    launch_transport_reduce(K, g, cf, species, Fd, Ft, st, partials, logu, s);
+    launch_transport_reduce(K, g, cf, species, Fd, Ft, st, partials, s);
     launch_transport_commit(K, g, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, st,
                             partials, logu, s);
 }

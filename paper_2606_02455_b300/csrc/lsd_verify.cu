@@ -36,6 +36,8 @@ __global__ void neigh_build_kernel(const uint4 *__restrict__ fix, const int *__r
                                    const int *__restrict__ vcount, int vcap, int M, Geo g, float rmax2f, float near2f,
                                    int cap_near, int cap_far, int *__restrict__ near_keys, int *__restrict__ far_keys,
                                    int *__restrict__ n_near, int *__restrict__ n_far, DevState *st) {
+    pdl_wait();
+    pdl_release();
     const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= M) return;
@@ -57,13 +59,25 @@ __global__ void neigh_build_kernel(const uint4 *__restrict__ fix, const int *__r
     int cn = 0, cf = 0;
     if (MINIMG) {
         const unsigned below = (1u << lane) - 1u;
-        for (int base = 0; base < ncand; base += 32) {
-            const int t = base + lane;
-            const int k = LIST ? (t < ncand ? cand[t] : N) : t;
+        constexpr int kBatch = 8;   // candidates' positions loaded together: one memory latency per 8 passes
+        for (int base0 = 0; base0 < ncand; base0 += 32 * kBatch) {
+            int kk[kBatch];
+            uint4 ff[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int t = base0 + 32 * u + lane;
+                kk[u] = LIST ? (t < ncand ? cand[t] : N) : (t < ncand ? t : N);
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) ff[u] = kk[u] < N ? fj[kk[u]] : fi;
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+            if (base0 + 32 * u >= ncand) break;
+            const int k = kk[u];
             bool in_n = false, in_f = false;
             int key = 0;
             if (k < N && k != i) {
-                const uint4 fkk = fj[k];
+                const uint4 fkk = ff[u];
                 float dx, dy, dz;
                 int kx, ky, kz;
                 axis_min(fi.x, fkk.x, g.scale_f[0], dx, kx);
@@ -80,6 +94,7 @@ __global__ void neigh_build_kernel(const uint4 *__restrict__ fix, const int *__r
             if (in_f && wf < cap_far) fk[wf] = key;
             cn += __popc(bn);
             cf += __popc(bf);
+            }
         }
     }
     for (int base = 0; base < (MINIMG ? 0 : ncand); base += 32) {
@@ -162,6 +177,29 @@ __device__ __forceinline__ NbStage nb_stage_ptrs(float *base, int cap) {
 }
 constexpr int kStageFloats = 10;
 
+// The n (n - 1) / 2 unordered neighbour pairs of a row, flattened so that a
+// warp's lanes stay busy whatever n is: pair t is (p, (p + d) mod n) with
+// d = t / n + 1, p = t mod n (full diagonals d < n / 2, and for even n the
+// half diagonal d = n / 2 with p < n / 2).  Within one diagonal the p are
+// distinct and so are the q.  A lane starts at t = lane and advances by 32.
+struct PairIter {
+    int n, p, d;
+    __device__ __forceinline__ PairIter(int n_, int lane) : n(n_), p(lane), d(1) {
+        while (p >= n && n > 0) {
+            p -= n;
+            ++d;
+        }
+    }
+    __device__ __forceinline__ int q() const { return p + d < n ? p + d : p + d - n; }
+    __device__ __forceinline__ void next() {
+        p += 32;
+        while (p >= n) {
+            p -= n;
+            ++d;
+        }
+    }
+};
+
 __device__ __forceinline__ void nb_stage_load(const NbStage &S, const uint4 *fj, uint4 fi, const int *keys, int n,
                                               const Geo &g, float rc, int lane) {
     for (int p = lane; p < n; p += 32) {
@@ -192,6 +230,8 @@ __device__ __forceinline__ void nb_stage_load(const NbStage &S, const uint4 *fj,
 // ---------------------------------------------------------------------------
 __global__ void desc_kernel(const uint4 *__restrict__ fix, const int *__restrict__ near_keys,
                             const int *__restrict__ n_near, int cap, int M, Geo g, PotDev P, float *__restrict__ X) {
+    pdl_wait();
+    pdl_release();
     extern __shared__ float smem[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -231,13 +271,14 @@ __global__ void desc_kernel(const uint4 *__restrict__ fix, const int *__restrict
         float a[kNAng];
 #pragma unroll
         for (int t = 0; t < kNAng; ++t) a[t] = 0.f;
-        for (int p = 0; p < n; ++p) {
-            const float xp = S.dx[p], yp = S.dy[p], zp = S.dz[p], rip = S.rinv[p], fp = S.fc[p];
-            const float e1p = S.e1[p], e2p = S.e2[p];
-            for (int q = p + 1 + lane; q < n; q += 32) {
-                const float c = (xp * S.dx[q] + yp * S.dy[q] + zp * S.dz[q]) * (rip * S.rinv[q]);
-                const float ff = fp * S.fc[q];
-                const float E1 = e1p * S.e1[q] * ff, E2 = e2p * S.e2[q] * ff;
+        const int npairs = n * (n - 1) / 2;
+        PairIter it(n, lane);
+        for (int t = lane; t < npairs; t += 32, it.next()) {
+            const int p = it.p, q = it.q();
+            {
+                const float c = (S.dx[p] * S.dx[q] + S.dy[p] * S.dy[q] + S.dz[p] * S.dz[q]) * (S.rinv[p] * S.rinv[q]);
+                const float ff = S.fc[p] * S.fc[q];
+                const float E1 = S.e1[p] * S.e1[q] * ff, E2 = S.e2[p] * S.e2[q] * ff;
                 const float bp1 = 1.f + c, bm1 = 1.f - c;
                 const float bp2 = bp1 * bp1, bm2 = bm1 * bm1, bp4 = bp2 * bp2, bm4 = bm2 * bm2;
                 const float bp8 = bp4 * bp4, bm8 = bm4 * bm4;
@@ -271,6 +312,8 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
                                 const int *__restrict__ n_far, int cap, int cap_far, int M, Geo g, PotDev P,
                                 const float *__restrict__ dEdX, float4 *__restrict__ pair_g,
                                 float4 *__restrict__ Fpart, float *__restrict__ E_lj) {
+    pdl_wait();
+    pdl_release();
     extern __shared__ float smem[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -281,6 +324,7 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
     const uint4 fi = fj[i];
     const int warps = blockDim.x >> 5;
     float *wbuf = smem + (size_t)warps * kStageFloats * cap + (size_t)wib * P.d0p;
+    float *abuf = smem + (size_t)warps * (kStageFloats * cap + P.d0p) + (size_t)wib * 4 * cap;
     NbStage S = nb_stage_ptrs(smem + (size_t)wib * kStageFloats * cap, cap);
     const int n = n_near[row];
     const int *keys = near_keys + (size_t)row * cap;
@@ -290,10 +334,65 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
         nb_stage_load(S, fj, fi, keys, n, g, P.desc_rc, lane);
         const int nr = P.n_rbf;
         const float *wang = wbuf + g.S * nr;
+        // angular: every unordered pair (p, q) once; its term T(c_pq, r_p, r_q) adds
+        // dT/dd_p = A d_q + B_p d_p to neighbour p and dT/dd_q = A d_p + B_q d_q to q
+        // (warp-private accumulators ang = (alpha_x, alpha_y, alpha_z, beta) per neighbour)
+        float *ax = abuf, *ay = abuf + cap, *az = abuf + 2 * cap, *bb = abuf + 3 * cap;
+        if (P.n_ang) {
+            for (int p = lane; p < n; p += 32) ax[p] = ay[p] = az[p] = bb[p] = 0.f;
+            __syncwarp();
+            const int npairs = n * (n - 1) / 2;
+            PairIter it(n, lane);
+            for (int t = lane; t < npairs; t += 32, it.next()) {
+                const int p = it.p, q = it.q();
+                const float xp = S.dx[p], yp = S.dy[p], zp = S.dz[p], xq = S.dx[q], yq = S.dy[q], zq = S.dz[q];
+                const float rip = S.rinv[p], riq = S.rinv[q];
+                const float inv_pq = rip * riq;
+                const float cth = (xp * xq + yp * yq + zp * zq) * inv_pq;
+                const float fp = S.fc[p], fq = S.fc[q];
+                const float E1 = S.e1[p] * S.e1[q], E2 = S.e2[p] * S.e2[q];
+                // (1 + lambda c)^zeta and zeta (1 + lambda c)^(zeta - 1), lambda = +1 (p) and -1 (m)
+                const float bp1 = 1.f + cth, bm1 = 1.f - cth;
+                const float bp2 = bp1 * bp1, bm2 = bm1 * bm1, bp4 = bp2 * bp2, bm4 = bm2 * bm2;
+                const float bp8 = bp4 * bp4, bm8 = bm4 * bm4;
+                const float bp3 = bp2 * bp1, bm3 = bm2 * bm1, bp7 = bp4 * bp3, bm7 = bm4 * bm3;
+                // per eta: S0 = sum_a w_a pref pow (value weights), S1 = dS0/dc
+                float S0_1 = 0.f, S0_2 = 0.f, S1_1 = 0.f, S1_2 = 0.f;
+                // zeta 1: pref 1
+                S0_1 += wang[0] * bp1 + wang[2] * bm1;  S0_2 += wang[1] * bp1 + wang[3] * bm1;
+                S1_1 += wang[0] - wang[2];              S1_2 += wang[1] - wang[3];
+                // zeta 2: pref 1/2, zeta*pow1*pref = b
+                S0_1 += 0.5f * (wang[4] * bp2 + wang[6] * bm2);  S0_2 += 0.5f * (wang[5] * bp2 + wang[7] * bm2);
+                S1_1 += wang[4] * bp1 - wang[6] * bm1;           S1_2 += wang[5] * bp1 - wang[7] * bm1;
+                // zeta 4: pref 1/8, zeta*pow1*pref = b^3/2
+                S0_1 += 0.125f * (wang[8] * bp4 + wang[10] * bm4);  S0_2 += 0.125f * (wang[9] * bp4 + wang[11] * bm4);
+                S1_1 += 0.5f * (wang[8] * bp3 - wang[10] * bm3);    S1_2 += 0.5f * (wang[9] * bp3 - wang[11] * bm3);
+                // zeta 8: pref 1/128, zeta*pow1*pref = b^7/16
+                S0_1 += 0.0078125f * (wang[12] * bp8 + wang[14] * bm8);
+                S0_2 += 0.0078125f * (wang[13] * bp8 + wang[15] * bm8);
+                S1_1 += 0.0625f * (wang[12] * bp7 - wang[14] * bm7);
+                S1_2 += 0.0625f * (wang[13] * bp7 - wang[15] * bm7);
+                const float ffq = fp * fq;
+                const float S1E = (S1_1 * E1 + S1_2 * E2) * ffq, S0E = S0_1 * E1 + S0_2 * E2;
+                // d/dd_p: S1 E ff (d_q / (r_p r_q) - c d_p / r_p^2) - 2 eta S0 E ff d_p + S0 E dfc_p fc_q d_p / r_p
+                const float A = S1E * inv_pq;
+                const float Bc = -2.f * (0.005f * S0_1 * E1 + 0.05f * S0_2 * E2) * ffq;
+                const float Bp = Bc - S1E * cth * (rip * rip) + S0E * S.dfc[p] * fq * rip;
+                const float Bq = Bc - S1E * cth * (riq * riq) + S0E * fp * S.dfc[q] * riq;
+                atomicAdd(ax + p, A * xq);
+                atomicAdd(ay + p, A * yq);
+                atomicAdd(az + p, A * zq);
+                atomicAdd(bb + p, Bp);
+                atomicAdd(ax + q, A * xp);
+                atomicAdd(ay + q, A * yp);
+                atomicAdd(az + q, A * zp);
+                atomicAdd(bb + q, Bq);
+            }
+            __syncwarp();
+        }
         for (int p = lane; p < n; p += 32) {
             const float xp = S.dx[p], yp = S.dy[p], zp = S.dz[p], rp = S.r[p], fp = S.fc[p], dfp = S.dfc[p];
             const float rip = S.rinv[p];
-            const float e1p = S.e1[p], e2p = S.e2[p];
             // radial: c = sum_k w_k g_k'(r)
             float c = 0.f;
             const float *wr = wbuf + S.sp[p] * nr;
@@ -304,49 +403,9 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
             }
             float gx = c * xp * rip, gy = c * yp * rip, gz = c * zp * rip;
             if (P.n_ang) {
-                float alpha_sum_x = 0.f, alpha_sum_y = 0.f, alpha_sum_z = 0.f, beta_sum = 0.f;
-                for (int q = 0; q < n; ++q) {
-                    if (q == p) continue;
-                    const float xq = S.dx[q], yq = S.dy[q], zq = S.dz[q];
-                    const float inv_pq = rip * S.rinv[q];
-                    const float cth = (xp * xq + yp * yq + zp * zq) * inv_pq;
-                    const float fq = S.fc[q];
-                    const float E1 = e1p * S.e1[q], E2 = e2p * S.e2[q];
-                    // (1 + lambda c)^zeta and zeta*(1+lambda c)^(zeta-1) for lambda = +1 (p) and -1 (m)
-                    const float bp1 = 1.f + cth, bm1 = 1.f - cth;
-                    const float bp2 = bp1 * bp1, bm2 = bm1 * bm1, bp4 = bp2 * bp2, bm4 = bm2 * bm2;
-                    const float bp8 = bp4 * bp4, bm8 = bm4 * bm4;
-                    const float bp3 = bp2 * bp1, bm3 = bm2 * bm1, bp7 = bp4 * bp3, bm7 = bm4 * bm3;
-                    // per eta: S0 = sum_a w_a pref pow (value weights), S1 = sum_a w_a pref zeta lambda pow1
-                    float S0_1 = 0.f, S0_2 = 0.f, S1_1 = 0.f, S1_2 = 0.f;
-                    // zeta 1: pref 1
-                    S0_1 += wang[0] * bp1 + wang[2] * bm1;  S0_2 += wang[1] * bp1 + wang[3] * bm1;
-                    S1_1 += wang[0] - wang[2];              S1_2 += wang[1] - wang[3];
-                    // zeta 2: pref 1/2, zeta*pow1*pref = bp1
-                    S0_1 += 0.5f * (wang[4] * bp2 + wang[6] * bm2);  S0_2 += 0.5f * (wang[5] * bp2 + wang[7] * bm2);
-                    S1_1 += wang[4] * bp1 - wang[6] * bm1;           S1_2 += wang[5] * bp1 - wang[7] * bm1;
-                    // zeta 4: pref 1/8, zeta*pow1*pref = 0.5*b^3
-                    S0_1 += 0.125f * (wang[8] * bp4 + wang[10] * bm4);  S0_2 += 0.125f * (wang[9] * bp4 + wang[11] * bm4);
-                    S1_1 += 0.5f * (wang[8] * bp3 - wang[10] * bm3);    S1_2 += 0.5f * (wang[9] * bp3 - wang[11] * bm3);
-                    // zeta 8: pref 1/128, zeta*pow1*pref = b^7/16
-                    S0_1 += 0.0078125f * (wang[12] * bp8 + wang[14] * bm8);
-                    S0_2 += 0.0078125f * (wang[13] * bp8 + wang[15] * bm8);
-                    S1_1 += 0.0625f * (wang[12] * bp7 - wang[14] * bm7);
-                    S1_2 += 0.0625f * (wang[13] * bp7 - wang[15] * bm7);
-                    const float ffq = fp * fq;
-                    // d/d(d_p): S1*E*ff*(d_q/(rp rq) - c d_p/rp^2) + S0*E*(-2 eta d_p)*ff + S0*E*dfp*fq*d_p/rp
-                    const float A = (S1_1 * E1 + S1_2 * E2) * ffq * inv_pq;
-                    const float B = -(S1_1 * E1 + S1_2 * E2) * ffq * cth * (rip * rip) -
-                                    2.f * (0.005f * S0_1 * E1 + 0.05f * S0_2 * E2) * ffq +
-                                    (S0_1 * E1 + S0_2 * E2) * dfp * fq * rip;
-                    alpha_sum_x += A * xq;
-                    alpha_sum_y += A * yq;
-                    alpha_sum_z += A * zq;
-                    beta_sum += B;
-                }
-                gx += alpha_sum_x + beta_sum * xp;
-                gy += alpha_sum_y + beta_sum * yp;
-                gz += alpha_sum_z + beta_sum * zp;
+                gx += ax[p] + bb[p] * xp;
+                gy += ay[p] + bb[p] * yp;
+                gz += az[p] + bb[p] * zp;
             }
             pair_g[(size_t)row * cap + p] = make_float4(gx, gy, gz, 0.f);
             fx += gx;
@@ -393,6 +452,8 @@ __global__ void force_gather_kernel(const int *__restrict__ near_keys, const int
                                     const float4 *__restrict__ Fpart, const float *__restrict__ E_lj,
                                     const float *__restrict__ E_mlp, float *__restrict__ F_out,
                                     float *__restrict__ E_out, DevState *st) {
+    pdl_wait();
+    pdl_release();
     const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= M) return;
@@ -468,8 +529,8 @@ void launch_neigh_build(const uint4 *fix, int M, const Geo &g, float rmax2f, flo
     const int threads = 256;
     const int blocks = (int)(((size_t)M * 32 + threads - 1) / threads);
     auto k = min_image_only(g, rmax2f) ? neigh_build_kernel<false, true> : neigh_build_kernel<false, false>;
-    k<<<blocks, threads, 0, s>>>(fix, nullptr, nullptr, 0, M, g, rmax2f, near2f, cap_near, cap_far, near_keys,
-                                 far_keys, n_near, n_far, st);
+    launch_dependent(k, blocks, threads, 0, s, fix, nullptr, nullptr, 0, M, g, rmax2f, near2f, cap_near, cap_far,
+                     near_keys, far_keys, n_near, n_far, st);
 }
 
 void launch_neigh_list(const uint4 *fix, const int *vlist, const int *vcount, int vcap, int M, const Geo &g,
@@ -478,8 +539,8 @@ void launch_neigh_list(const uint4 *fix, const int *vlist, const int *vcount, in
     const int threads = 256;
     const int blocks = (int)(((size_t)M * 32 + threads - 1) / threads);
     auto k = min_image_only(g, rmax2f) ? neigh_build_kernel<true, true> : neigh_build_kernel<true, false>;
-    k<<<blocks, threads, 0, s>>>(fix, vlist, vcount, vcap, M, g, rmax2f, near2f, cap_near, cap_far, near_keys,
-                                 far_keys, n_near, n_far, st);
+    launch_dependent(k, blocks, threads, 0, s, fix, vlist, vcount, vcap, M, g, rmax2f, near2f, cap_near, cap_far,
+                     near_keys, far_keys, n_near, n_far, st);
 }
 
 size_t desc_smem_bytes(int warps, int cap) { return (size_t)warps * kStageFloats * cap * sizeof(float); }
@@ -488,16 +549,16 @@ void launch_desc(const uint4 *fix, const int *near_keys, const int *n_near, int 
                  const PotDev &P, float *X, cudaStream_t s) {
     const int warps = 8;
     const size_t sm = desc_smem_bytes(warps, cap);
-    desc_kernel<<<(M + warps - 1) / warps, warps * 32, sm, s>>>(fix, near_keys, n_near, cap, M, g, P, X);
+    launch_dependent(desc_kernel, (M + warps - 1) / warps, warps * 32, sm, s, fix, near_keys, n_near, cap, M, g, P, X);
 }
 
 void launch_pairgrad(const uint4 *fix, const int *near_keys, const int *n_near, const int *far_keys, const int *n_far,
                      int cap, int cap_far, int M, const Geo &g, const PotDev &P, const float *dEdX, float4 *pair_g,
                      float4 *Fpart, float *E_lj, cudaStream_t s) {
     const int warps = 8;
-    const size_t sm = desc_smem_bytes(warps, cap) + (size_t)warps * P.d0p * sizeof(float);
-    pairgrad_kernel<<<(M + warps - 1) / warps, warps * 32, sm, s>>>(fix, near_keys, n_near, far_keys, n_far, cap,
-                                                                     cap_far, M, g, P, dEdX, pair_g, Fpart, E_lj);
+    const size_t sm = desc_smem_bytes(warps, cap) + (size_t)warps * (P.d0p + 4 * cap) * sizeof(float);
+    launch_dependent(pairgrad_kernel, (M + warps - 1) / warps, warps * 32, sm, s, fix, near_keys, n_near, far_keys,
+                     n_far, cap, cap_far, M, g, P, dEdX, pair_g, Fpart, E_lj);
 }
 
 void launch_force_gather(const int *near_keys, const int *n_near, int cap, int M, int N, int has_mlp,
@@ -505,8 +566,8 @@ void launch_force_gather(const int *near_keys, const int *n_near, int cap, int M
                          float *E_out, DevState *st, cudaStream_t s) {
     const int threads = 256;
     const int blocks = (int)(((size_t)M * 32 + threads - 1) / threads);
-    force_gather_kernel<<<blocks, threads, 0, s>>>(near_keys, n_near, cap, M, N, has_mlp, pair_g, Fpart, E_lj, E_mlp,
-                                                   F, E_out, st);
+    launch_dependent(force_gather_kernel, blocks, threads, 0, s, near_keys, n_near, cap, M, N, has_mlp, pair_g, Fpart,
+                     E_lj, E_mlp, F, E_out, st);
 }
 
 cudaError_t verify_kernels_setup(int max_smem) {
