@@ -410,12 +410,17 @@ void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, f
 // window buffer b.  hdr null: from the committed state (q, p, st->step);
 // else (pipelined loop) from the base (q, p) at step hdr->base, skipped when
 // hdr->skip is set.
-void enqueue_draft_buf(lsd_handle *h, int b, cudaStream_t s, WinHdr *hdr, const double *q, const double *p) {
+void enqueue_draft_buf(lsd_handle *h, int b, cudaStream_t s, WinHdr *hdr, const double *q, const double *p,
+                       bool redraft = false) {
     lsd_handle::WinBufs &w = h->wb[b];
-    if (!h->vplan.all_pairs)
-        launch_verlet_build(h->vplan, q, h->species, h->geo, w.vb, h->st, s, hdr ? &hdr->skip : nullptr);
+    if (!h->vplan.all_pairs) {
+        if (redraft) launch_redraft_flag(h->st, hdr, s);
+        launch_verlet_build(h->vplan, q, h->species, h->geo, w.vb, h->st, s,
+                            hdr ? (redraft ? &hdr->keep : &hdr->skip) : nullptr);
+    }
     launch_draft(h->dplan, h->learned_small, h->K, h->geo, h->draft.dev, h->coef, h->vplan, w.vb, h->species, q, p,
-                 h->ec_dF, h->ec_on, h->st, w.qmid, w.pdraft, w.Fd, w.Fraw, w.fix, h->w_dEdX, w.logu, s, hdr);
+                 h->ec_dF, h->ec_on, h->st, w.qmid, w.pdraft, w.Fd, w.Fraw, w.fix, h->w_dEdX, w.logu, s, hdr,
+                 redraft ? 1 : 0);
 }
 
 // Verification, frames and transport of window buffer b.
@@ -444,8 +449,7 @@ void enqueue_round(lsd_handle *h, int b) {
     enqueue_draft_buf(h, n, D, &h->hdr[n], h->qb, h->pb);
     cudaEventRecord(h->ev_v, V);
     cudaStreamWaitEvent(D, h->ev_v, 0);
-    launch_stale_check(h->geo, h->q, h->p, h->st, &h->hdr[n], h->qb, h->pb, D);
-    enqueue_draft_buf(h, n, D, &h->hdr[n], h->qb, h->pb);
+    enqueue_draft_buf(h, n, D, &h->hdr[n], h->q, h->p, true);   // returns at once when the speculative draft stands
     cudaEventRecord(h->ev_d, D);
     cudaStreamWaitEvent(V, h->ev_d, 0);
 }
@@ -453,8 +457,7 @@ void enqueue_round(lsd_handle *h, int b) {
 // The first window of a pipelined run: drafted from the committed state into buffer 0.
 void enqueue_prime(lsd_handle *h) {
     launch_hdr_invalidate(&h->hdr[0], h->stream);
-    launch_stale_check(h->geo, h->q, h->p, h->st, &h->hdr[0], h->qb, h->pb, h->stream);
-    enqueue_draft_buf(h, 0, h->stream, &h->hdr[0], h->qb, h->pb);
+    enqueue_draft_buf(h, 0, h->stream, &h->hdr[0], h->q, h->p, true);
     h->pipe_primed = true;
     h->pipe_cur = 0;
 }

@@ -81,6 +81,7 @@ struct WinHdr {
     long long base;
     int k_eff;
     int skip;
+    int keep;   // the redraft's Verlet build: 1 when the speculative draft stands
 };
 
 // Device-resident run state.  step is the index of the base state.

@@ -192,6 +192,13 @@ __device__ __forceinline__ void st_cluster(const int *local, uint32_t rank, int 
 constexpr int kGroups = kDraftThreads / 4;   // four-lane groups: one atom, lanes 0..2 its coordinates
 constexpr int kRegPasses = 2;
 
+// Valid iff the speculative base is the committed state: the previous window
+// committed up to the base step without a rejection (a rejection at its last
+// step also ends at that step index, but in the reflected state).
+__device__ __forceinline__ bool spec_is_valid(const WinHdr *hn, const DevState *st) {
+    return hn->skip == 0 && hn->base == st->step && st->first_reject_last == -1;
+}
+
 template <bool LEARNED, bool REG>
 __global__ void __launch_bounds__(kDraftThreads, 1)
     draft_window_cluster_kernel(int K, Geo g, PotDev P, Coef cf, const int *__restrict__ vlist,
@@ -202,7 +209,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                                 const float *__restrict__ ec_dF, int ec_on, DevState *__restrict__ st,
                                 double *__restrict__ w_qmid, double *__restrict__ w_pdraft, float *__restrict__ w_Fd,
                                 float *__restrict__ w_Fraw, uint4 *__restrict__ w_fix, float *__restrict__ w_dEdX,
-                                WinHdr *__restrict__ hdr, double *__restrict__ w_logu) {
+                                WinHdr *__restrict__ hdr, double *__restrict__ w_logu, int redraft) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N;
     const int C = gridDim.x, c = blockIdx.x;
@@ -215,9 +222,15 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     uint4 *sfix = (uint4 *)(sstage + (LEARNED ? (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) : 0));  // [2][N]
     int *sflag = (int *)(sfix + (stage_fix ? 2 * (size_t)N : 0));                                        // [2]
     float *snoise = (float *)(sflag + 4);   // [K][A][3] when noise_smem: the window's xi, drawn up front
-    // the base step: the committed one, or (pipelined loop) the window header's; uniform over the cluster
+    // the base step: the committed one, or (pipelined loop) the window header's;
+    // a redraft runs only when the speculative draft of this window does not
+    // stand, from the committed state.  Uniform over the cluster: the header is
+    // rewritten only after the last cluster barrier.
     long long n0;
-    if (hdr) {
+    if (hdr && redraft) {
+        if (spec_is_valid(hdr, st) || st->step >= st->target_step) return;
+        n0 = st->step;
+    } else if (hdr) {
         if (hdr->skip || hdr->base >= st->target_step) return;
         n0 = hdr->base;
     } else {
@@ -485,8 +498,15 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     if (c == 0)
         for (int t = tid; t < keff; t += blockDim.x) w_logu[t] = log(uniform53(cf.seed, (unsigned long long)(n0 + t + 1)));
     if (c == 0 && tid == 0) {
-        if (hdr) hdr->k_eff = keff;
-        else st->k_eff = keff;
+        if (hdr) {
+            hdr->k_eff = keff;
+            if (redraft) {
+                hdr->base = n0;
+                hdr->skip = 0;
+            }
+        } else {
+            st->k_eff = keff;
+        }
     }
 }
 
@@ -519,7 +539,7 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
                          const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
                          const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
                          double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX, double *w_logu,
-                         cudaStream_t s, WinHdr *hdr) {
+                         cudaStream_t s, WinHdr *hdr, int redraft) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(pl.cluster, 1, 1);
     cfg.blockDim = dim3(kDraftThreads, 1, 1);
@@ -540,7 +560,7 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
                         : (pl.reg ? draft_window_cluster_kernel<false, true> : draft_window_cluster_kernel<false, false>);
     return cudaLaunchKernelEx(&cfg, kern, K, g, P, cf, vl, (const int *)vb.vcount, vp.cap, (const uint4 *)vb.fix_base,
                               vp.move2f, stage, mi, ns, species, q, p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd,
-                              w_Fraw, w_fix, w_dEdX, hdr, w_logu);
+                              w_Fraw, w_fix, w_dEdX, hdr, w_logu, redraft);
 }
 
 static const void *draft_kernel_ptrs[4] = {
@@ -612,32 +632,11 @@ __global__ void spec_base_kernel(Geo g, Coef cf, const int *__restrict__ species
     }
 }
 
-// Valid iff the speculative base is the committed state: the previous window
-// committed up to the base step without a rejection (a rejection at its last
-// step also ends at that step index, but in the reflected state).
-__device__ __forceinline__ bool spec_is_valid(const WinHdr *hn, const DevState *st) {
-    return hn->skip == 0 && hn->base == st->step && st->first_reject_last == -1;
-}
 
-// Reads the header only (it is rewritten by stale_commit_kernel afterwards):
-// an invalid window's base becomes the committed state.
-__global__ void stale_check_kernel(Geo g, const double *__restrict__ q, const double *__restrict__ p,
-                                   const DevState *__restrict__ st, const WinHdr *__restrict__ hn,
-                                   double *__restrict__ qb, double *__restrict__ pb) {
-    if (spec_is_valid(hn, st)) return;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 3 * g.N; k += gridDim.x * blockDim.x) {
-        qb[k] = q[k];
-        pb[k] = p[k];
-    }
-}
-
-__global__ void stale_commit_kernel(const DevState *__restrict__ st, WinHdr *__restrict__ hn) {
-    if (spec_is_valid(hn, st)) {
-        hn->skip = 1;            // keep the speculative draft: the redraft kernels return at once
-    } else {
-        hn->base = st->step;     // draft again from the committed state
-        hn->skip = 0;
-    }
+// The redraft's Verlet build runs only when the speculative draft does not
+// stand (the same test the redraft itself makes).
+__global__ void redraft_flag_kernel(const DevState *__restrict__ st, WinHdr *__restrict__ hn) {
+    hn->keep = spec_is_valid(hn, st) ? 1 : 0;
 }
 
 // The verification of window b reads its k_eff through the run state.
@@ -654,12 +653,7 @@ void launch_spec_base(const Geo &g, const Coef &cf, const int *species, const do
     spec_base_kernel<<<(g.N + 255) / 256, 256, 0, s>>>(g, cf, species, qmid_b, pdraft_b, hb, hn, qb, pb);
 }
 
-void launch_stale_check(const Geo &g, const double *q, const double *p, const DevState *st, WinHdr *hn, double *qb,
-                        double *pb, cudaStream_t s) {
-    const int blocks = (3 * g.N + 255) / 256 < 296 ? (3 * g.N + 255) / 256 : 296;
-    stale_check_kernel<<<blocks, 256, 0, s>>>(g, q, p, st, hn, qb, pb);
-    stale_commit_kernel<<<1, 1, 0, s>>>(st, hn);
-}
+void launch_redraft_flag(const DevState *st, WinHdr *hn, cudaStream_t s) { redraft_flag_kernel<<<1, 1, 0, s>>>(st, hn); }
 
 void launch_window_begin(const WinHdr *hb, DevState *st, cudaStream_t s) { window_begin_kernel<<<1, 1, 0, s>>>(hb, st); }
 

@@ -126,12 +126,11 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
                          const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
                          const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
                          double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX, double *w_logu,
-                         cudaStream_t s, WinHdr *hdr = nullptr);
+                         cudaStream_t s, WinHdr *hdr = nullptr, int redraft = 0);
 // the pipelined window loop (lsd_draft.cu)
 void launch_spec_base(const Geo &g, const Coef &cf, const int *species, const double *qmid_b, const double *pdraft_b,
                       const WinHdr *hb, WinHdr *hn, double *qb, double *pb, cudaStream_t s);
-void launch_stale_check(const Geo &g, const double *q, const double *p, const DevState *st, WinHdr *hn, double *qb,
-                        double *pb, cudaStream_t s);
+void launch_redraft_flag(const DevState *st, WinHdr *hn, cudaStream_t s);
 void launch_window_begin(const WinHdr *hb, DevState *st, cudaStream_t s);
 void launch_hdr_invalidate(WinHdr *h, cudaStream_t s);
 cudaError_t draft_kernels_setup(int max_smem);
