@@ -734,7 +734,9 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     }
     h->cap_near = std::min(nb_capacity(rho, rnear, 32), (27 * h->N + 31) / 32 * 32);
     h->cap_far = std::min(nb_capacity(rho, rfar, 32), (27 * h->N + 31) / 32 * 32);
-    if (desc_smem_bytes(8, h->cap_near) + 8 * (256 + 4 * h->cap_near) * sizeof(float) > (size_t)kMaxDynSmem)
+    // the pair-gradient kernel: staging, dE/dX and the q-side hand-over buffer per warp; at most 16 neighbours per lane
+    if (h->cap_near > 512 ||
+        desc_smem_bytes(8, h->cap_near) + 8 * (256 + 4 * h->cap_near) * sizeof(float) > (size_t)kMaxDynSmem)
         return fail(LSD_EUNSUPPORTED);
     if (verify_kernels_setup(kMaxDynSmem) != cudaSuccess || mlp_kernels_setup(kMaxDynSmem) != cudaSuccess ||
         mlp_tc_setup() != cudaSuccess ||

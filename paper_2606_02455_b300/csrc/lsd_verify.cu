@@ -307,6 +307,60 @@ __global__ void desc_kernel(const uint4 *__restrict__ fix, const int *__restrict
 // ---------------------------------------------------------------------------
 // Pair gradients g_p = dE_i / d(r_p) and LJ forces.
 // ---------------------------------------------------------------------------
+// The angular term T(c_pq, r_p, r_q) of one unordered pair: dT/dd_p =
+// A d_q + B_p d_p is added to p's accumulators (a*), and dT/dd_q = A d_p +
+// B_q d_q is returned for q.  wang: dE/dX of the angular features.
+__device__ __forceinline__ float4 pair_terms(const NbStage &S, const float *wang, int p, int q, float &ax, float &ay,
+                                             float &az, float &ab) {
+    const float xp = S.dx[p], yp = S.dy[p], zp = S.dz[p], xq = S.dx[q], yq = S.dy[q], zq = S.dz[q];
+    const float rip = S.rinv[p], riq = S.rinv[q];
+    const float inv_pq = rip * riq;
+    const float cth = (xp * xq + yp * yq + zp * zq) * inv_pq;
+    const float fp = S.fc[p], fq = S.fc[q];
+    const float E1 = S.e1[p] * S.e1[q], E2 = S.e2[p] * S.e2[q];
+    // (1 + lambda c)^zeta and zeta (1 + lambda c)^(zeta - 1), lambda = +1 (p) and -1 (m)
+    const float bp1 = 1.f + cth, bm1 = 1.f - cth;
+    const float bp2 = bp1 * bp1, bm2 = bm1 * bm1, bp4 = bp2 * bp2, bm4 = bm2 * bm2;
+    const float bp8 = bp4 * bp4, bm8 = bm4 * bm4;
+    const float bp3 = bp2 * bp1, bm3 = bm2 * bm1, bp7 = bp4 * bp3, bm7 = bm4 * bm3;
+    // per eta: S0 = sum_a w_a pref pow (value weights), S1 = dS0/dc
+    float S0_1 = 0.f, S0_2 = 0.f, S1_1 = 0.f, S1_2 = 0.f;
+    // zeta 1: pref 1
+    S0_1 += wang[0] * bp1 + wang[2] * bm1;  S0_2 += wang[1] * bp1 + wang[3] * bm1;
+    S1_1 += wang[0] - wang[2];              S1_2 += wang[1] - wang[3];
+    // zeta 2: pref 1/2, zeta*pow1*pref = b
+    S0_1 += 0.5f * (wang[4] * bp2 + wang[6] * bm2);  S0_2 += 0.5f * (wang[5] * bp2 + wang[7] * bm2);
+    S1_1 += wang[4] * bp1 - wang[6] * bm1;           S1_2 += wang[5] * bp1 - wang[7] * bm1;
+    // zeta 4: pref 1/8, zeta*pow1*pref = b^3/2
+    S0_1 += 0.125f * (wang[8] * bp4 + wang[10] * bm4);  S0_2 += 0.125f * (wang[9] * bp4 + wang[11] * bm4);
+    S1_1 += 0.5f * (wang[8] * bp3 - wang[10] * bm3);    S1_2 += 0.5f * (wang[9] * bp3 - wang[11] * bm3);
+    // zeta 8: pref 1/128, zeta*pow1*pref = b^7/16
+    S0_1 += 0.0078125f * (wang[12] * bp8 + wang[14] * bm8);
+    S0_2 += 0.0078125f * (wang[13] * bp8 + wang[15] * bm8);
+    S1_1 += 0.0625f * (wang[12] * bp7 - wang[14] * bm7);
+    S1_2 += 0.0625f * (wang[13] * bp7 - wang[15] * bm7);
+    const float ffq = fp * fq;
+    const float S1E = (S1_1 * E1 + S1_2 * E2) * ffq, S0E = S0_1 * E1 + S0_2 * E2;
+    // d/dd_p: S1 E ff (d_q / (r_p r_q) - c d_p / r_p^2) - 2 eta S0 E ff d_p + S0 E dfc_p fc_q d_p / r_p
+    const float A = S1E * inv_pq;
+    const float Bc = -2.f * (0.005f * S0_1 * E1 + 0.05f * S0_2 * E2) * ffq;
+    const float Bp = Bc - S1E * cth * (rip * rip) + S0E * S.dfc[p] * fq * rip;
+    const float Bq = Bc - S1E * cth * (riq * riq) + S0E * fp * S.dfc[q] * riq;
+    ax += A * xq;
+    ay += A * yq;
+    az += A * zq;
+    ab += Bp;
+    return make_float4(A * xp, A * yp, A * zp, Bq);
+}
+
+// SLOTS > 0: neighbours per lane (lane l owns p = l + 32 s); every row has at
+// most 32 SLOTS of them, and rows with more than 32 run the angular pairs by
+// diagonals: in diagonal d lane l evaluates (p, p + d mod n) for its own p,
+// keeps the p side in registers and hands the q side over through shared
+// memory to q's owner (within one diagonal the q are distinct, so no two lanes
+// write the same slot).  SLOTS = 0, and rows of at most 32: the pairs are
+// flattened over all 32 lanes and both sides go to shared accumulators.
+template <int SLOTS>
 __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__restrict__ near_keys,
                                 const int *__restrict__ n_near, const int *__restrict__ far_keys,
                                 const int *__restrict__ n_far, int cap, int cap_far, int M, Geo g, PotDev P,
@@ -324,7 +378,7 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
     const uint4 fi = fj[i];
     const int warps = blockDim.x >> 5;
     float *wbuf = smem + (size_t)warps * kStageFloats * cap + (size_t)wib * P.d0p;
-    float *abuf = smem + (size_t)warps * (kStageFloats * cap + P.d0p) + (size_t)wib * 4 * cap;
+    float4 *tb = reinterpret_cast<float4 *>(smem + (size_t)warps * (kStageFloats * cap + P.d0p)) + (size_t)wib * cap;
     NbStage S = nb_stage_ptrs(smem + (size_t)wib * kStageFloats * cap, cap);
     const int n = n_near[row];
     const int *keys = near_keys + (size_t)row * cap;
@@ -334,63 +388,61 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
         nb_stage_load(S, fj, fi, keys, n, g, P.desc_rc, lane);
         const int nr = P.n_rbf;
         const float *wang = wbuf + g.S * nr;
-        // angular: every unordered pair (p, q) once; its term T(c_pq, r_p, r_q) adds
-        // dT/dd_p = A d_q + B_p d_p to neighbour p and dT/dd_q = A d_p + B_q d_q to q
-        // (warp-private accumulators ang = (alpha_x, alpha_y, alpha_z, beta) per neighbour)
-        float *ax = abuf, *ay = abuf + cap, *az = abuf + 2 * cap, *bb = abuf + 3 * cap;
-        if (P.n_ang) {
-            for (int p = lane; p < n; p += 32) ax[p] = ay[p] = az[p] = bb[p] = 0.f;
+        constexpr int R = SLOTS > 0 ? SLOTS : 1;
+        float ax[R], ay[R], az[R], ab[R];
+#pragma unroll
+        for (int s = 0; s < R; ++s) ax[s] = ay[s] = az[s] = ab[s] = 0.f;
+        float *sx = reinterpret_cast<float *>(tb), *sy = sx + cap, *sz = sx + 2 * cap, *sb = sx + 3 * cap;
+        const bool flat = SLOTS == 0 || n <= 32;
+        if (P.n_ang && flat) {
+            // the pairs flattened over all 32 lanes, both sides added to shared accumulators
+            for (int p = lane; p < n; p += 32) sx[p] = sy[p] = sz[p] = sb[p] = 0.f;
             __syncwarp();
             const int npairs = n * (n - 1) / 2;
             PairIter it(n, lane);
             for (int t = lane; t < npairs; t += 32, it.next()) {
                 const int p = it.p, q = it.q();
-                const float xp = S.dx[p], yp = S.dy[p], zp = S.dz[p], xq = S.dx[q], yq = S.dy[q], zq = S.dz[q];
-                const float rip = S.rinv[p], riq = S.rinv[q];
-                const float inv_pq = rip * riq;
-                const float cth = (xp * xq + yp * yq + zp * zq) * inv_pq;
-                const float fp = S.fc[p], fq = S.fc[q];
-                const float E1 = S.e1[p] * S.e1[q], E2 = S.e2[p] * S.e2[q];
-                // (1 + lambda c)^zeta and zeta (1 + lambda c)^(zeta - 1), lambda = +1 (p) and -1 (m)
-                const float bp1 = 1.f + cth, bm1 = 1.f - cth;
-                const float bp2 = bp1 * bp1, bm2 = bm1 * bm1, bp4 = bp2 * bp2, bm4 = bm2 * bm2;
-                const float bp8 = bp4 * bp4, bm8 = bm4 * bm4;
-                const float bp3 = bp2 * bp1, bm3 = bm2 * bm1, bp7 = bp4 * bp3, bm7 = bm4 * bm3;
-                // per eta: S0 = sum_a w_a pref pow (value weights), S1 = dS0/dc
-                float S0_1 = 0.f, S0_2 = 0.f, S1_1 = 0.f, S1_2 = 0.f;
-                // zeta 1: pref 1
-                S0_1 += wang[0] * bp1 + wang[2] * bm1;  S0_2 += wang[1] * bp1 + wang[3] * bm1;
-                S1_1 += wang[0] - wang[2];              S1_2 += wang[1] - wang[3];
-                // zeta 2: pref 1/2, zeta*pow1*pref = b
-                S0_1 += 0.5f * (wang[4] * bp2 + wang[6] * bm2);  S0_2 += 0.5f * (wang[5] * bp2 + wang[7] * bm2);
-                S1_1 += wang[4] * bp1 - wang[6] * bm1;           S1_2 += wang[5] * bp1 - wang[7] * bm1;
-                // zeta 4: pref 1/8, zeta*pow1*pref = b^3/2
-                S0_1 += 0.125f * (wang[8] * bp4 + wang[10] * bm4);  S0_2 += 0.125f * (wang[9] * bp4 + wang[11] * bm4);
-                S1_1 += 0.5f * (wang[8] * bp3 - wang[10] * bm3);    S1_2 += 0.5f * (wang[9] * bp3 - wang[11] * bm3);
-                // zeta 8: pref 1/128, zeta*pow1*pref = b^7/16
-                S0_1 += 0.0078125f * (wang[12] * bp8 + wang[14] * bm8);
-                S0_2 += 0.0078125f * (wang[13] * bp8 + wang[15] * bm8);
-                S1_1 += 0.0625f * (wang[12] * bp7 - wang[14] * bm7);
-                S1_2 += 0.0625f * (wang[13] * bp7 - wang[15] * bm7);
-                const float ffq = fp * fq;
-                const float S1E = (S1_1 * E1 + S1_2 * E2) * ffq, S0E = S0_1 * E1 + S0_2 * E2;
-                // d/dd_p: S1 E ff (d_q / (r_p r_q) - c d_p / r_p^2) - 2 eta S0 E ff d_p + S0 E dfc_p fc_q d_p / r_p
-                const float A = S1E * inv_pq;
-                const float Bc = -2.f * (0.005f * S0_1 * E1 + 0.05f * S0_2 * E2) * ffq;
-                const float Bp = Bc - S1E * cth * (rip * rip) + S0E * S.dfc[p] * fq * rip;
-                const float Bq = Bc - S1E * cth * (riq * riq) + S0E * fp * S.dfc[q] * riq;
-                atomicAdd(ax + p, A * xq);
-                atomicAdd(ay + p, A * yq);
-                atomicAdd(az + p, A * zq);
-                atomicAdd(bb + p, Bp);
-                atomicAdd(ax + q, A * xp);
-                atomicAdd(ay + q, A * yp);
-                atomicAdd(az + q, A * zp);
-                atomicAdd(bb + q, Bq);
+                float px = 0.f, py = 0.f, pz = 0.f, pb = 0.f;
+                const float4 v = pair_terms(S, wang, p, q, px, py, pz, pb);
+                atomicAdd(sx + p, px);
+                atomicAdd(sy + p, py);
+                atomicAdd(sz + p, pz);
+                atomicAdd(sb + p, pb);
+                atomicAdd(sx + q, v.x);
+                atomicAdd(sy + q, v.y);
+                atomicAdd(sz + q, v.z);
+                atomicAdd(sb + q, v.w);
             }
             __syncwarp();
+        } else if (P.n_ang) {
+            // diagonals d = 1 .. n/2; for even n the last one holds n/2 pairs (p < d)
+            for (int d = 1; 2 * d <= n; ++d) {
+                const bool half = 2 * d == n;
+#pragma unroll
+                for (int s = 0; s < R; ++s) {
+                    const int p = lane + 32 * s;
+                    if (p < n && (!half || p < d)) {
+                        const int q = p + d < n ? p + d : p + d - n;
+                        tb[q] = pair_terms(S, wang, p, q, ax[s], ay[s], az[s], ab[s]);
+                    }
+                }
+                __syncwarp();
+#pragma unroll
+                for (int s = 0; s < R; ++s) {
+                    const int q = lane + 32 * s;
+                    if (q < n && (!half || q >= d)) {
+                        const float4 v = tb[q];
+                        ax[s] += v.x;
+                        ay[s] += v.y;
+                        az[s] += v.z;
+                        ab[s] += v.w;
+                    }
+                }
+                __syncwarp();
+            }
         }
-        for (int p = lane; p < n; p += 32) {
+        // per neighbour: the radial term, then the angular sums (registers, or the shared accumulators)
+        auto finish = [&](int p, float bx, float by, float bz, float bw) {
             const float xp = S.dx[p], yp = S.dy[p], zp = S.dz[p], rp = S.r[p], fp = S.fc[p], dfp = S.dfc[p];
             const float rip = S.rinv[p];
             // radial: c = sum_k w_k g_k'(r)
@@ -401,16 +453,22 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
                 const float phi = expf(-t * t * P.rbf_inv2w2);
                 c += wr[k] * phi * (-t * P.rbf_invw2 * fp + dfp);
             }
-            float gx = c * xp * rip, gy = c * yp * rip, gz = c * zp * rip;
-            if (P.n_ang) {
-                gx += ax[p] + bb[p] * xp;
-                gy += ay[p] + bb[p] * yp;
-                gz += az[p] + bb[p] * zp;
-            }
+            const float gx = c * xp * rip + bx + bw * xp;
+            const float gy = c * yp * rip + by + bw * yp;
+            const float gz = c * zp * rip + bz + bw * zp;
             pair_g[(size_t)row * cap + p] = make_float4(gx, gy, gz, 0.f);
             fx += gx;
             fy += gy;
             fz += gz;
+        };
+        if (flat) {
+            for (int p = lane; p < n; p += 32)
+                if (P.n_ang) finish(p, sx[p], sy[p], sz[p], sb[p]);
+                else finish(p, 0.f, 0.f, 0.f, 0.f);
+        } else {
+#pragma unroll
+            for (int s = 0; s < R; ++s)
+                if (lane + 32 * s < n) finish(lane + 32 * s, ax[s], ay[s], az[s], ab[s]);
         }
     }
     if (P.has_lj) {
@@ -557,8 +615,11 @@ void launch_pairgrad(const uint4 *fix, const int *near_keys, const int *n_near, 
                      float4 *Fpart, float *E_lj, cudaStream_t s) {
     const int warps = 8;
     const size_t sm = desc_smem_bytes(warps, cap) + (size_t)warps * (P.d0p + 4 * cap) * sizeof(float);
-    launch_dependent(pairgrad_kernel, (M + warps - 1) / warps, warps * 32, sm, s, fix, near_keys, n_near, far_keys,
-                     n_far, cap, cap_far, M, g, P, dEdX, pair_g, Fpart, E_lj);
+    // lists of at most 128 hold mostly rows of a few dozen neighbours: flattened pairs with a small register
+    // footprint; longer lists run their large rows by diagonals
+    auto k = cap <= 128 ? pairgrad_kernel<0> : (cap <= 256 ? pairgrad_kernel<8> : pairgrad_kernel<16>);
+    launch_dependent(k, (M + warps - 1) / warps, warps * 32, sm, s, fix, near_keys, n_near, far_keys, n_far, cap,
+                     cap_far, M, g, P, dEdX, pair_g, Fpart, E_lj);
 }
 
 void launch_force_gather(const int *near_keys, const int *n_near, int cap, int M, int N, int has_mlp,
@@ -573,7 +634,13 @@ void launch_force_gather(const int *near_keys, const int *n_near, int cap, int M
 cudaError_t verify_kernels_setup(int max_smem) {
     cudaError_t e = cudaFuncSetAttribute(desc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(pairgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    const void *pk[3] = {(const void *)pairgrad_kernel<0>, (const void *)pairgrad_kernel<8>,
+                         (const void *)pairgrad_kernel<16>};
+    for (const void *k : pk) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace lsd
