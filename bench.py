@@ -159,6 +159,14 @@ def _lj_pairs_per_atom(w, q):
     return tot / N
 
 
+# DRAM bytes (read + write) of one launch, from one ncu capture of the kernel as it is now (the summaries under
+# profiles/ give the command); a kernel changed since its capture has no entry here.
+NCU_TRAFFIC = {
+    ("lj_mlp_angular_256atoms_K16", "draft"): 56832,       # draft_window_cluster_kernel, K = 16
+    ("lj_mlp_angular_256atoms_K16", "mlp"): 1748224,       # mlp_tc_kernel<TF32x3>, 4096 rows
+}
+
+
 def _algorithmic_work(w, phase, q):
     """Algorithmic work of one launch of a phase, with its bound: (amount, unit, bound, detail).
 
@@ -230,10 +238,11 @@ def roofline(h, w, peaks, peak_kind, q, n_rep=20):
     amount, unit, bound, detail = work
     sec = phases[dom] * 1e-3
     out.update(detail)
+    traffic = NCU_TRAFFIC.get((w.name, dom))
     if bound == "alu":
         ach = amount / sec / 1e12
         out.update({"bound": "alu", "achieved": round(ach, 4), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
-                    "frac": round(ach / fp32_peak, 5), "traffic": None,
+                    "frac": round(ach / fp32_peak, 5), "traffic": traffic,
                     "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz" % sm_max})
         if dom == "draft":
             out["us_per_step"] = round(phases[dom] * 1e3 / w.integ.K, 3)
@@ -248,14 +257,14 @@ def roofline(h, w, peaks, peak_kind, q, n_rep=20):
             # TF32 dense = bf16 x (1.1 / 2.25), the nominal ratio
             pk, src = bf16 * 1.1 / 2.25, "%s bf16 burst x 1.1/2.25 (nominal TF32:BF16)" % peak_kind
         out.update({"bound": "tensor", "achieved": round(ach, 2), "peak": round(pk, 1), "unit": "TFLOP/s",
-                    "frac": round(ach / pk, 5), "traffic": None, "peak_source": src})
+                    "frac": round(ach / pk, 5), "traffic": traffic, "peak_source": src})
         if w.target.precision in ("fp32", "fp32-cuda-cores"):
             out["tensor_flop_executed_per_algorithmic"] = 3
     else:
         ach = amount / sec / 1e9
         pk = peaks["hbm_gbs"]
         out.update({"bound": "hbm", "achieved": round(ach, 1), "peak": pk, "unit": "GB/s", "frac": round(ach / pk, 4),
-                    "traffic": None, "peak_source": peak_kind})
+                    "traffic": traffic, "peak_source": peak_kind})
     return out
 
 
@@ -372,9 +381,9 @@ def run_ours(args):
     D = 3 * s.n_atoms
 
     rl = roofline(h, w, peaks, peak_kind, pos)
-    # draft + 7 verification kernels; a pipelined round adds the window-begin, speculative-base, stale-check (2)
-    # and redraft launches (the Verlet-list kernels, when the grid has them, are not counted)
-    launches_per_window = 13 if pipelined else 8
+    # this library's kernels per window / pipelined round / plain step, for the handle's configuration
+    lc = h.launch_counts()
+    launches_per_window = lc["round"] if pipelined else lc["window"]
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "ns/day", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_lsd_max * 1e3 / args.steps, 5), "higher_is_better": True,
@@ -399,7 +408,7 @@ def run_ours(args):
         "pipelined": pipelined,
         "value_unpipelined": None if value_unpipelined is None else round(value_unpipelined, 3),
         "plain_ms_per_step": round(t_plain * 1e3 / n_plain, 5),
-        "gpu_launches": int(windows * launches_per_window + n_plain * 7),
+        "gpu_launches": int(windows * launches_per_window + n_plain * lc["plain"]),
         "e2e": {"value": round(e2e_val, 3), "unit": "ns/day", "h2d_bytes_per_step": 2 * D * 8 + 8,
                 "d2h_bytes_per_step": 2 * D * 8 + 8 + 8, "calls": "lsd_set_state, lsd_draft_window, "
                                                                   "lsd_verify_window, lsd_get_state"},

@@ -308,6 +308,14 @@ LSD_API int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases);
 /* lsd_query: K, N, input dimension of the target MLP, neighbour capacities. */
 LSD_API int lsd_query(const lsd_handle *h, int32_t *K, int32_t *n_atoms, int32_t *target_d_in, int32_t *nb_cap);
 
+/* lsd_launch_counts: how many kernels of this library one window launches
+ * (lsd_draft_window + lsd_verify_window, or one window of lsd_step), one round
+ * of the pipelined loop (lsd_set_pipelining), and one plain step, for the
+ * handle's current configuration (neighbour-list mode, transport form, MLP,
+ * frame capture).  Memory-set nodes are not kernels and are not counted.
+ * Any pointer may be null.  No GPU work. */
+LSD_API int lsd_launch_counts(const lsd_handle *h, int32_t *per_window, int32_t *per_round, int32_t *per_plain);
+
 /* lsd_target_mlp_static_dev: the target potential's per-atom MLP (energies
  * and dE/dX, the tensor-core BF16 path of a handle whose target precision is
  * LSD_BF16) for callers that cannot allocate device memory: code running

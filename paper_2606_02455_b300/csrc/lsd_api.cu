@@ -1241,6 +1241,25 @@ int lsd_query(const lsd_handle *h, int32_t *K, int32_t *n_atoms, int32_t *d_in, 
     return LSD_OK;
 }
 
+// The launch sequences of enqueue_draft_buf, enqueue_verify_buf, enqueue_round
+// and enqueue_plain, counted.
+int lsd_launch_counts(const lsd_handle *h, int32_t *per_window, int32_t *per_round, int32_t *per_plain) {
+    if (!h) return LSD_EINVAL;
+    const bool lists = !h->vplan.all_pairs;
+    const bool one_cell = h->vplan.nc[0] < 3 || h->vplan.nc[1] < 3 || h->vplan.nc[2] < 3;
+    const int verlet = lists ? (one_cell ? 2 : 4) : 0;
+    const int eval = 3 + (h->target.dev.has_mlp ? 2 : 0);   // neighbours, [descriptors, MLP,] pair gradients, gather
+    const int nb = (h->N + transport_atoms_per_block(h->N) - 1) / transport_atoms_per_block(h->N);
+    const int transport = nb == 1 ? 1 : 2;
+    const int verify = eval + (h->train.capture_on ? 1 : 0) + transport;
+    const int draft = verlet + 1;
+    if (per_window) *per_window = draft + verify;
+    // window_begin; verify; spec_base; speculative draft; redraft (with its flag kernel in list mode)
+    if (per_round) *per_round = 1 + verify + 1 + draft + (lists ? 1 : 0) + draft;
+    if (per_plain) *per_plain = verlet + 1 + eval + 1;
+    return LSD_OK;
+}
+
 // ---- checkpoint / restore -------------------------------------------------
 namespace {
 constexpr uint64_t kCkptMagic = 0x4c53444350543032ull;   // "LSDCPT02"

@@ -33,7 +33,7 @@ SYMBOLS = ["lsd_init", "lsd_draft_window", "lsd_verify_window", "lsd_step", "lsd
            "lsd_force_match_dev", "lsd_target_forces_dev", "lsd_draft_forces_dev", "lsd_neighbors",
            "lsd_descriptors", "lsd_get_window", "lsd_profile_window", "lsd_checkpoint", "lsd_restore", "lsd_query",
            "lsd_target_mlp_static_dev", "lsd_destroy",
-           "lsd_strerror"]
+           "lsd_strerror", "lsd_launch_counts"]
 
 
 class LSDError(RuntimeError):
@@ -102,6 +102,7 @@ def _lib():
             "lsd_checkpoint": [P, P, P],
             "lsd_restore": [P, P, SZ],
             "lsd_query": [P, P, P, P, P],
+            "lsd_launch_counts": [P, P, P, P],
             "lsd_target_mlp_static_dev": [P, P, I32, P, P],
             "lsd_profile_window": [P, P, I32],
         }
@@ -326,6 +327,13 @@ class LSD:
         return self._forces(_lib().lsd_draft_forces_dev, q, energies)
 
     # -- inspection (parity tests) -------------------------------------------------------------------------
+    def launch_counts(self):
+        """Kernels of this library per window, per pipelined round and per plain step."""
+        w, r, p = (ctypes.c_int32() for _ in range(3))
+        _check(_lib().lsd_launch_counts(self.h, ctypes.byref(w), ctypes.byref(r), ctypes.byref(p)),
+               "lsd_launch_counts")
+        return dict(window=w.value, round=r.value, plain=p.value)
+
     def query(self):
         K, N, d, cap = (ctypes.c_int32() for _ in range(4))
         _check(_lib().lsd_query(self.h, ctypes.byref(K), ctypes.byref(N), ctypes.byref(d), ctypes.byref(cap)))
