@@ -154,11 +154,11 @@ __device__ __forceinline__ bool tc_issue(const TcSm &S, int K, int N, uint32_t t
     return true;
 }
 
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
+// TF32 of x rounded to nearest, ties away from zero (the rounding of
+// cvt.rna.tf32.f32) for finite x: half a TF32 ulp added to the magnitude bits,
+// then the 13 bits below the TF32 mantissa cleared (a carry into the exponent
+// is the correct rounding up).  Integer ALU work instead of a conversion.
+__device__ __forceinline__ uint32_t tf32_rna(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }

@@ -518,33 +518,10 @@ __global__ void force_gather_kernel(const int *__restrict__ near_keys, const int
     const int j = row / N, i = row - j * N;
     float ax = 0.f, ay = 0.f, az = 0.f;
     if (has_mlp) {
-        const int n = n_near[row];
-        const int *keys = near_keys + (size_t)row * cap;
-        for (int p = lane; p < n; p += 32) {
-            const int key = keys[p];
-            const int rk = j * N + (key >> 5);
-            const int want = (i << 5) | (26 - (key & 31));
-            const int *kk = near_keys + (size_t)rk * cap;
-            int lo = 0, hi = n_near[rk] - 1, found = -1;
-            while (lo <= hi) {
-                const int mid = (lo + hi) >> 1;
-                const int v = kk[mid];
-                if (v == want) { found = mid; break; }
-                if (v < want) lo = mid + 1;
-                else hi = mid - 1;
-            }
-            if (found < 0) {
-                atomicOr(&st->err, 4);
-                continue;
-            }
-            const float4 gv = pair_g[(size_t)rk * cap + found];
-            ax += gv.x;
-            ay += gv.y;
-            az += gv.z;
-        }
-        ax = warp_sum(ax);
-        ay = warp_sum(ay);
-        az = warp_sum(az);
+        const float3 r = gather_reverse(near_keys, n_near, pair_g, cap, N, j, i, lane, &st->err);
+        ax = r.x;
+        ay = r.y;
+        az = r.z;
     }
     if (lane == 0) {
         const float4 fp = Fpart[row];
