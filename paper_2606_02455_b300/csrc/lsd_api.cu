@@ -555,6 +555,7 @@ int check_err(const DevState &s) {
     if (s.err & 2) return LSD_ENONFINITE;
     if (s.err & 1) return LSD_EOVERFLOW;
     if (s.err & 4) return LSD_ESTATE;
+    if (s.err & (8 | 16)) return LSD_ETIMEOUT;   // a bounded device wait gave up (MLP pipeline, transport barrier)
     return LSD_OK;
 }
 
@@ -740,7 +741,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         return fail(LSD_EUNSUPPORTED);
     if (verify_kernels_setup(kMaxDynSmem) != cudaSuccess || mlp_kernels_setup(kMaxDynSmem) != cudaSuccess ||
         mlp_tc_setup() != cudaSuccess ||
-        draft_kernels_setup(kMaxDynSmem) != cudaSuccess ||
+        draft_kernels_setup(kMaxDynSmem) != cudaSuccess || transport_setup() != cudaSuccess ||
         verlet_setup(kMaxDynSmem) != cudaSuccess)
         return fail(LSD_ECUDA);
     {

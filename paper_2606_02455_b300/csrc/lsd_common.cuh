@@ -93,6 +93,7 @@ struct DevState {
     int k_eff;                   // window steps drafted (the draft stops early if an atom left the list's skin)
     int err;                     // bit flags: 1 neighbour overflow, 2 non-finite
     unsigned int blocks_done;    // last-block counter of the commit kernel
+    unsigned long long grid_arrive;   // arrivals at the transport's grid barrier (generations of nb*K)
     long long windows, committed, rejected, verified;
     double sum_delta, sum_pred;
     int accept[kMaxK];

@@ -98,6 +98,7 @@ int mlp_tc_static_launch(const void *plan, const float *X, int M, const PotDev &
 
 // transport (lsd_transport.cu)
 int transport_atoms_per_block(int N);
+cudaError_t transport_setup();
 void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *species, const float *Fd,
                              const float *Ft, DevState *st, double2 *partials, cudaStream_t s);
 void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,

@@ -228,6 +228,88 @@ __global__ void __launch_bounds__(kTransThreads)
     commit_stats(C, Kw, st, n0);
 }
 
+// A barrier over the whole grid of a cooperative launch (every block resident):
+// each block's thread 0 arrives on a 64-bit counter and waits for the end of
+// its generation of `total` arrivals, giving up after about two seconds.
+__device__ bool grid_sync_bounded(unsigned long long *ctr, unsigned total) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long arrive = atomicAdd(ctr, 1ull);
+        const unsigned long long target = (arrive / total + 1ull) * total;
+        int ok = 1;
+        const long long t0 = clock64();
+        for (;;) {
+            unsigned long long v;
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+            if (v >= target) break;
+            if (clock64() - t0 > 4000000000ll) {
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// The whole transport in one cooperative launch: block (b, j) sums chunk b of
+// window step j; after a grid barrier every block takes the decision (the same
+// partials in the same order, so the same result) and commits its own slice of
+// atoms, and block 0 updates the statistics.  The commit's FP64 work is spread
+// over all nb*K SMs instead of one.
+__global__ void __launch_bounds__(kTransThreads)
+    transport_coop_kernel(int K, Geo g, Coef cf, const int *__restrict__ species, const float *__restrict__ Fd,
+                          const float *__restrict__ Ft, DevState *__restrict__ st, double2 *__restrict__ partials,
+                          const double *__restrict__ logu, int atoms_per_block, const double *__restrict__ w_qmid,
+                          const double *__restrict__ w_pdraft, const float *__restrict__ Fraw,
+                          float *__restrict__ ec_dF, int ec_on, double *__restrict__ q, double *__restrict__ p,
+                          double *__restrict__ p_obabo) {
+    __shared__ double2 sh[32];
+    __shared__ CommitShared C;
+    pdl_wait();
+    pdl_release();
+    // read before the barrier: block 0 rewrites the run state after it
+    const volatile DevState *vs = st;
+    const long long n0 = vs->step, tgt = vs->target_step;
+    const int keff = vs->k_eff;
+    if (n0 >= tgt) return;   // uniform over the grid
+    const int N = g.N;
+    const int j = blockIdx.y, nb = gridDim.x;
+    float s = 0.f, d = 0.f;
+    if (j < keff) {
+        const unsigned long long n = (unsigned long long)(n0 + j + 1);
+        const int a0 = blockIdx.x * atoms_per_block;
+        const int a1 = min(N, a0 + atoms_per_block);
+        for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+            const float3 xi = normals3(cf.seed, n, (uint32_t)i, 0u);
+            const float k = (float)species_pick(cf.aF_sig, species[i]);
+            const size_t o = ((size_t)j * N + i) * 3;
+            const float d0 = k * (Fd[o + 0] - Ft[o + 0]);
+            const float d1 = k * (Fd[o + 1] - Ft[o + 1]);
+            const float d2 = k * (Fd[o + 2] - Ft[o + 2]);
+            s += xi.x * d0 + xi.y * d1 + xi.z * d2;
+            d += d0 * d0 + d1 * d1 + d2 * d2;
+        }
+    }
+    const double2 SD = block_sum2(s, d, sh);
+    if (threadIdx.x == 0 && j < keff) partials[(size_t)j * nb + blockIdx.x] = SD;
+    if (!grid_sync_bounded(&st->grid_arrive, (unsigned)(nb * gridDim.y))) {
+        if (threadIdx.x == 0) atomicOr(&st->err, 16);
+        return;
+    }
+    const int Kw = min(K, keff);
+    commit_decide(C, Kw, partials, nb, logu, tgt - n0);
+    const int nblk = nb * gridDim.y, blk = blockIdx.y * nb + blockIdx.x;
+    const int A = (N + nblk - 1) / nblk;
+    commit_atoms(C, N, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, n0, blk * A,
+                 min(N, blk * A + A));
+    if (blk == 0) commit_stats(C, Kw, st, n0);
+}
+
 __global__ void __launch_bounds__(kTransThreads)
     transport_commit_kernel(int K, Geo g, Coef cf, const int *__restrict__ species, const double *__restrict__ w_qmid,
                             const double *__restrict__ w_pdraft, const float *__restrict__ Fd,
@@ -276,13 +358,41 @@ void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *spe
                      Fraw, ec_dF, ec_on, q, p, p_obabo, st, (const double2 *)partials, (const double *)logu, nb, apb);
 }
 
-// Windows whose atoms fit in one block per step: one fused launch; else reduce, then commit.
+static int g_coop_blocks = -1;   // blocks of transport_coop_kernel the device keeps resident at once
+
+cudaError_t transport_setup() {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, transport_coop_kernel, kTransThreads, 0);
+    g_coop_blocks = e == cudaSuccess ? sms * per_sm : 0;
+    return e;
+}
+
+// One cooperative launch when the grid fits on the device at once; else the
+// one-block-per-step fused launch, or reduce then commit.
 void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                       const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
                       int ec_on, double *q, double *p, double *p_obabo, DevState *st, double2 *partials,
                       const double *logu, cudaStream_t s) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
+    if (nb * K <= g_coop_blocks) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(nb, K);
+        cfg.blockDim = dim3(kTransThreads);
+        cfg.stream = s;
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        at[1].id = cudaLaunchAttributeCooperative;
+        at[1].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 2;
+        cudaLaunchKernelEx(&cfg, transport_coop_kernel, K, g, cf, species, Fd, Ft, st, partials, logu, apb, w_qmid,
+                           w_pdraft, Fraw, ec_dF, ec_on, q, p, p_obabo);
+        return;
+    }
     if (nb == 1) {
         launch_dependent(transport_reduce_kernel, dim3(1, K), kTransThreads, 0, s, K, g, cf, species, Fd, Ft, st,
                          partials, logu, apb, 1, w_qmid, w_pdraft, Fraw, ec_dF, ec_on, q, p, p_obabo);
