@@ -314,40 +314,25 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-// sum over the descriptor neighbours p of row (j, i) of the pair gradient of
-// the reverse entry (k_p, i, -s_p), found by binary search in k_p's sorted
-// list; warp-collective, every lane returns the sum.  A missing reverse entry
-// sets error bit 4.
-__device__ __forceinline__ float3 gather_reverse(const int *__restrict__ near_keys, const int *__restrict__ n_near,
-                                                 const float4 *__restrict__ pair_g, int cap, int N, int j, int i,
-                                                 int lane, int *err) {
-    const int row = j * N + i;
-    const int n = n_near[row];
-    const int *keys = near_keys + (size_t)row * cap;
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    for (int p = lane; p < n; p += 32) {
-        const int key = keys[p];
-        const int rk = j * N + (key >> 5);
-        const int want = (i << 5) | (26 - (key & 31));
-        const int *kk = near_keys + (size_t)rk * cap;
-        int lo = 0, hi = n_near[rk] - 1, found = -1;
-        while (lo <= hi) {
-            const int mid = (lo + hi) >> 1;
-            const int v = kk[mid];
-            if (v == want) { found = mid; break; }
-            if (v < want) lo = mid + 1;
-            else hi = mid - 1;
-        }
-        if (found < 0) {
-            atomicOr(err, 4);
-            continue;
-        }
-        const float4 gv = pair_g[(size_t)rk * cap + found];
-        ax += gv.x;
-        ay += gv.y;
-        az += gv.z;
+// The pair-gradient slot of the reverse entry (k_p, i, -s_p) of neighbour p
+// of row (j, i), found by binary search in k_p's sorted list; -1 (and error
+// bit 4) when it is missing.
+__device__ __forceinline__ int find_reverse(const int *__restrict__ near_keys, const int *__restrict__ n_near,
+                                            int cap, int N, int j, int i, int p, int *err) {
+    const int key = near_keys[((size_t)j * N + i) * cap + p];
+    const int rk = j * N + (key >> 5);
+    const int want = (i << 5) | (26 - (key & 31));
+    const int *kk = near_keys + (size_t)rk * cap;
+    int lo = 0, hi = n_near[rk] - 1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int v = kk[mid];
+        if (v == want) return rk * cap + mid;
+        if (v < want) lo = mid + 1;
+        else hi = mid - 1;
     }
-    return make_float3(warp_sum(ax), warp_sum(ay), warp_sum(az));
+    atomicOr(err, 4);
+    return -1;
 }
 
 // Cosine cutoff and its derivative.

@@ -270,28 +270,44 @@ __global__ void __launch_bounds__(kTransThreads)
                           double *__restrict__ p_obabo) {
     __shared__ double2 sh[32];
     __shared__ CommitShared C;
-    pdl_wait();
+    // The run state, log u and the draft's forces and noise come from kernels
+    // that finished before the force gather began: read and drawn before the
+    // wait (block 0 rewrites the run state only after the grid barrier).
     pdl_release();
-    // read before the barrier: block 0 rewrites the run state after it
     const volatile DevState *vs = st;
     const long long n0 = vs->step, tgt = vs->target_step;
     const int keff = vs->k_eff;
     if (n0 >= tgt) return;   // uniform over the grid
     const int N = g.N;
     const int j = blockIdx.y, nb = gridDim.x;
-    float s = 0.f, d = 0.f;
-    if (j < keff) {
-        const unsigned long long n = (unsigned long long)(n0 + j + 1);
-        const int a0 = blockIdx.x * atoms_per_block;
-        const int a1 = min(N, a0 + atoms_per_block);
-        for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
-            const float3 xi = normals3(cf.seed, n, (uint32_t)i, 0u);
-            const float k = (float)species_pick(cf.aF_sig, species[i]);
+    const int a0 = blockIdx.x * atoms_per_block, a1 = min(N, a0 + atoms_per_block);
+    constexpr int kPer = 4;   // atoms per thread held across the wait (chunks of up to 1024 atoms)
+    float3 xi[kPer], fd[kPer];
+    float kk[kPer];
+    const unsigned long long n = (unsigned long long)(n0 + j + 1);
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int i = a0 + threadIdx.x + u * (int)blockDim.x;
+        xi[u] = fd[u] = make_float3(0.f, 0.f, 0.f);
+        kk[u] = 0.f;
+        if (j < keff && i < a1) {
+            xi[u] = normals3(cf.seed, n, (uint32_t)i, 0u);
+            kk[u] = (float)species_pick(cf.aF_sig, species[i]);
             const size_t o = ((size_t)j * N + i) * 3;
-            const float d0 = k * (Fd[o + 0] - Ft[o + 0]);
-            const float d1 = k * (Fd[o + 1] - Ft[o + 1]);
-            const float d2 = k * (Fd[o + 2] - Ft[o + 2]);
-            s += xi.x * d0 + xi.y * d1 + xi.z * d2;
+            fd[u] = make_float3(Fd[o + 0], Fd[o + 1], Fd[o + 2]);
+        }
+    }
+    pdl_wait();   // the target forces
+    float s = 0.f, d = 0.f;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int i = a0 + threadIdx.x + u * (int)blockDim.x;
+        if (j < keff && i < a1) {
+            const size_t o = ((size_t)j * N + i) * 3;
+            const float d0 = kk[u] * (fd[u].x - Ft[o + 0]);
+            const float d1 = kk[u] * (fd[u].y - Ft[o + 1]);
+            const float d2 = kk[u] * (fd[u].z - Ft[o + 2]);
+            s += xi[u].x * d0 + xi[u].y * d1 + xi[u].z * d2;
             d += d0 * d0 + d1 * d1 + d2 * d2;
         }
     }
@@ -377,7 +393,7 @@ void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, c
                       const double *logu, cudaStream_t s) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
-    if (nb * K <= g_coop_blocks) {
+    if (apb <= 4 * kTransThreads && nb * K <= g_coop_blocks) {   // four atoms per thread at most
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(nb, K);
         cfg.blockDim = dim3(kTransThreads);

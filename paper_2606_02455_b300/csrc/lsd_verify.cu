@@ -366,7 +366,12 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
                                 const int *__restrict__ n_far, int cap, int cap_far, int M, Geo g, PotDev P,
                                 const float *__restrict__ dEdX, float4 *__restrict__ pair_g,
                                 float4 *__restrict__ Fpart, float *__restrict__ E_lj) {
-    pdl_wait();
+    // MLP potentials: the previous kernel is the MLP, and the neighbour lists
+    // and positions come from kernels that finished before it began, so the
+    // geometry staging and the LJ part run before the wait, while the MLP still
+    // runs; only dE/dX needs it.  Otherwise the lists come from the previous
+    // kernel itself.
+    if (!P.has_mlp) pdl_wait();
     pdl_release();
     extern __shared__ float smem[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -383,9 +388,31 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
     const int n = n_near[row];
     const int *keys = near_keys + (size_t)row * cap;
     float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+    if (P.has_mlp) nb_stage_load(S, fj, fi, keys, n, g, P.desc_rc, lane);
+    if (P.has_lj) {
+        const int si = (int)fi.w;
+        const int nf = n_far[row];
+        const int *fkeys = far_keys + (size_t)row * cap_far;
+        for (int t = lane; t < n + nf; t += 32) {
+            const int key = t < n ? keys[t] : fkeys[t - n];
+            const uint4 fk = fj[key >> 5];
+            const float3 d = entry_disp(fi, fk, key & 31, g);
+            const float d2 = dist2_rule(d.x, d.y, d.z);
+            if (!(d2 < P.lj_rc2f)) continue;
+            const int pr = si * g.S + (int)fk.w;
+            const float s2 = P.lj_sig2[pr] / d2;
+            const float s6 = s2 * s2 * s2, s12 = s6 * s6;
+            const float fr = -P.lj_eps24[pr] * (2.f * s12 - s6) / d2;   // (dU/dr)/r
+            fx += fr * d.x;
+            fy += fr * d.y;
+            fz += fr * d.z;
+            e += 0.5f * (P.lj_eps4[pr] * (s12 - s6) - P.lj_shift[pr]);
+        }
+    }
     if (P.has_mlp) {
+        pdl_wait();
         for (int f = lane; f < P.d0p; f += 32) wbuf[f] = dEdX[(size_t)row * P.d0p + f];
-        nb_stage_load(S, fj, fi, keys, n, g, P.desc_rc, lane);
+        __syncwarp();
         const int nr = P.n_rbf;
         const float *wang = wbuf + g.S * nr;
         constexpr int R = SLOTS > 0 ? SLOTS : 1;
@@ -471,26 +498,6 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
                 if (lane + 32 * s < n) finish(lane + 32 * s, ax[s], ay[s], az[s], ab[s]);
         }
     }
-    if (P.has_lj) {
-        const int si = (int)fi.w;
-        const int nf = n_far[row];
-        const int *fkeys = far_keys + (size_t)row * cap_far;
-        for (int t = lane; t < n + nf; t += 32) {
-            const int key = t < n ? keys[t] : fkeys[t - n];
-            const uint4 fk = fj[key >> 5];
-            const float3 d = entry_disp(fi, fk, key & 31, g);
-            const float d2 = dist2_rule(d.x, d.y, d.z);
-            if (!(d2 < P.lj_rc2f)) continue;
-            const int pr = si * g.S + (int)fk.w;
-            const float s2 = P.lj_sig2[pr] / d2;
-            const float s6 = s2 * s2 * s2, s12 = s6 * s6;
-            const float fr = -P.lj_eps24[pr] * (2.f * s12 - s6) / d2;   // (dU/dr)/r
-            fx += fr * d.x;
-            fy += fr * d.y;
-            fz += fr * d.z;
-            e += 0.5f * (P.lj_eps4[pr] * (s12 - s6) - P.lj_shift[pr]);
-        }
-    }
     fx = warp_sum(fx);
     fy = warp_sum(fy);
     fz = warp_sum(fz);
@@ -510,18 +517,44 @@ __global__ void force_gather_kernel(const int *__restrict__ near_keys, const int
                                     const float4 *__restrict__ Fpart, const float *__restrict__ E_lj,
                                     const float *__restrict__ E_mlp, float *__restrict__ F_out,
                                     float *__restrict__ E_out, DevState *st) {
-    pdl_wait();
+    // the lists come from a kernel that finished before the pair gradients
+    // released this launch: the reverse entries are found before the wait
     pdl_release();
     const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= M) return;
     const int j = row / N, i = row - j * N;
+    constexpr int kSlots = 8;   // reverse entries held per lane across the wait (lists of up to 256)
+    int at[kSlots];
+    const int n = has_mlp ? n_near[row] : 0;
+#pragma unroll
+    for (int u = 0; u < kSlots; ++u) {
+        const int p = lane + 32 * u;
+        at[u] = p < n ? find_reverse(near_keys, n_near, cap, N, j, i, p, &st->err) : -1;
+    }
+    pdl_wait();
     float ax = 0.f, ay = 0.f, az = 0.f;
     if (has_mlp) {
-        const float3 r = gather_reverse(near_keys, n_near, pair_g, cap, N, j, i, lane, &st->err);
-        ax = r.x;
-        ay = r.y;
-        az = r.z;
+#pragma unroll
+        for (int u = 0; u < kSlots; ++u)
+            if (at[u] >= 0) {
+                const float4 gv = pair_g[at[u]];
+                ax += gv.x;
+                ay += gv.y;
+                az += gv.z;
+            }
+        for (int p = lane + 32 * kSlots; p < n; p += 32) {
+            const int a = find_reverse(near_keys, n_near, cap, N, j, i, p, &st->err);
+            if (a >= 0) {
+                const float4 gv = pair_g[a];
+                ax += gv.x;
+                ay += gv.y;
+                az += gv.z;
+            }
+        }
+        ax = warp_sum(ax);
+        ay = warp_sum(ay);
+        az = warp_sum(az);
     }
     if (lane == 0) {
         const float4 fp = Fpart[row];
