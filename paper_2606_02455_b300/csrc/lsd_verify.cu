@@ -310,8 +310,8 @@ __global__ void desc_kernel(const uint4 *__restrict__ fix, const int *__restrict
 // The angular term T(c_pq, r_p, r_q) of one unordered pair: dT/dd_p =
 // A d_q + B_p d_p is added to p's accumulators (a*), and dT/dd_q = A d_p +
 // B_q d_q is returned for q.  wang: dE/dX of the angular features.
-__device__ __forceinline__ float4 pair_terms(const NbStage &S, const float *wang, int p, int q, float &ax, float &ay,
-                                             float &az, float &ab) {
+__device__ __forceinline__ float4 pair_terms(const NbStage &S, const float (&wang)[kNAng], int p, int q, float &ax,
+                                             float &ay, float &az, float &ab) {
     const float xp = S.dx[p], yp = S.dy[p], zp = S.dz[p], xq = S.dx[q], yq = S.dy[q], zq = S.dz[q];
     const float rip = S.rinv[p], riq = S.rinv[q];
     const float inv_pq = rip * riq;
@@ -414,7 +414,9 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
         for (int f = lane; f < P.d0p; f += 32) wbuf[f] = dEdX[(size_t)row * P.d0p + f];
         __syncwarp();
         const int nr = P.n_rbf;
-        const float *wang = wbuf + g.S * nr;
+        float wang[kNAng];   // dE/dX of the angular features, in registers across the pair loop
+#pragma unroll
+        for (int t = 0; t < kNAng; ++t) wang[t] = wbuf[g.S * nr + t];
         constexpr int R = SLOTS > 0 ? SLOTS : 1;
         float ax[R], ay[R], az[R], ab[R];
 #pragma unroll
