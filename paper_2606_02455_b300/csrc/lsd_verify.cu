@@ -157,21 +157,17 @@ __global__ void neigh_build_kernel(const uint4 *__restrict__ fix, const int *__r
 // Per-warp staging of a row's descriptor neighbours in shared memory.
 // ---------------------------------------------------------------------------
 struct NbStage {
-    float *dx, *dy, *dz, *r, *rinv, *fc, *dfc, *e1, *e2;
+    float4 *g;   // (dx, dy, dz, 1/r): one 16-byte load per neighbour in the pair loops
+    float4 *c;   // (fc, dfc, e1, e2)
+    float *r;
     int *sp;
 };
 
 __device__ __forceinline__ NbStage nb_stage_ptrs(float *base, int cap) {
-    NbStage s;
-    s.dx = base;
-    s.dy = base + cap;
-    s.dz = base + 2 * cap;
-    s.r = base + 3 * cap;
-    s.rinv = base + 4 * cap;
-    s.fc = base + 5 * cap;
-    s.dfc = base + 6 * cap;
-    s.e1 = base + 7 * cap;
-    s.e2 = base + 8 * cap;
+    NbStage s;   // cap is a multiple of 32: the float4 arrays stay 16-byte aligned
+    s.g = reinterpret_cast<float4 *>(base);
+    s.c = reinterpret_cast<float4 *>(base + 4 * cap);
+    s.r = base + 8 * cap;
     s.sp = (int *)(base + 9 * cap);
     return s;
 }
@@ -210,15 +206,9 @@ __device__ __forceinline__ void nb_stage_load(const NbStage &S, const uint4 *fj,
         const float r = sqrtf(r2);
         float fc, dfc;
         cutoff_fn(r, rc, fc, dfc);
-        S.dx[p] = d.x;
-        S.dy[p] = d.y;
-        S.dz[p] = d.z;
+        S.g[p] = make_float4(d.x, d.y, d.z, 1.f / r);   // 1/r once per neighbour: the O(n^2) pair loops multiply
+        S.c[p] = make_float4(fc, dfc, expf(-0.005f * r2), expf(-0.05f * r2));
         S.r[p] = r;
-        S.rinv[p] = 1.f / r;     // once per neighbour: the O(n^2) pair loops multiply
-        S.fc[p] = fc;
-        S.dfc[p] = dfc;
-        S.e1[p] = expf(-0.005f * r2);
-        S.e2[p] = expf(-0.05f * r2);
         S.sp[p] = (int)fk.w;
     }
     __syncwarp();
@@ -232,7 +222,7 @@ __global__ void desc_kernel(const uint4 *__restrict__ fix, const int *__restrict
                             const int *__restrict__ n_near, int cap, int M, Geo g, PotDev P, float *__restrict__ X) {
     pdl_wait();
     pdl_release();
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) float smem[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + wib;
     if (row >= M) return;
@@ -255,7 +245,7 @@ __global__ void desc_kernel(const uint4 *__restrict__ fix, const int *__restrict
             const float mu = (float)kb * P.rbf_w;
             for (int p = lane >> 4; p < n; p += 2) {
                 const float t = S.r[p] - mu;
-                const float v = expf(-t * t * P.rbf_inv2w2) * S.fc[p];
+                const float v = expf(-t * t * P.rbf_inv2w2) * S.c[p].x;
                 const int sp = S.sp[p];
 #pragma unroll
                 for (int s = 0; s < kMaxSpecies; ++s) acc[s] += (sp == s) ? v : 0.f;
@@ -276,9 +266,10 @@ __global__ void desc_kernel(const uint4 *__restrict__ fix, const int *__restrict
         for (int t = lane; t < npairs; t += 32, it.next()) {
             const int p = it.p, q = it.q();
             {
-                const float c = (S.dx[p] * S.dx[q] + S.dy[p] * S.dy[q] + S.dz[p] * S.dz[q]) * (S.rinv[p] * S.rinv[q]);
-                const float ff = S.fc[p] * S.fc[q];
-                const float E1 = S.e1[p] * S.e1[q] * ff, E2 = S.e2[p] * S.e2[q] * ff;
+                const float4 gp = S.g[p], gq = S.g[q], cp = S.c[p], cq = S.c[q];
+                const float c = (gp.x * gq.x + gp.y * gq.y + gp.z * gq.z) * (gp.w * gq.w);
+                const float ff = cp.x * cq.x;
+                const float E1 = cp.z * cq.z * ff, E2 = cp.w * cq.w * ff;
                 const float bp1 = 1.f + c, bm1 = 1.f - c;
                 const float bp2 = bp1 * bp1, bm2 = bm1 * bm1, bp4 = bp2 * bp2, bm4 = bm2 * bm2;
                 const float bp8 = bp4 * bp4, bm8 = bm4 * bm4;
@@ -312,12 +303,13 @@ __global__ void desc_kernel(const uint4 *__restrict__ fix, const int *__restrict
 // B_q d_q is returned for q.  wang: dE/dX of the angular features.
 __device__ __forceinline__ float4 pair_terms(const NbStage &S, const float (&wang)[kNAng], int p, int q, float &ax,
                                              float &ay, float &az, float &ab) {
-    const float xp = S.dx[p], yp = S.dy[p], zp = S.dz[p], xq = S.dx[q], yq = S.dy[q], zq = S.dz[q];
-    const float rip = S.rinv[p], riq = S.rinv[q];
+    const float4 gp = S.g[p], gq = S.g[q], cp = S.c[p], cq = S.c[q];
+    const float xp = gp.x, yp = gp.y, zp = gp.z, xq = gq.x, yq = gq.y, zq = gq.z;
+    const float rip = gp.w, riq = gq.w;
     const float inv_pq = rip * riq;
     const float cth = (xp * xq + yp * yq + zp * zq) * inv_pq;
-    const float fp = S.fc[p], fq = S.fc[q];
-    const float E1 = S.e1[p] * S.e1[q], E2 = S.e2[p] * S.e2[q];
+    const float fp = cp.x, fq = cq.x;
+    const float E1 = cp.z * cq.z, E2 = cp.w * cq.w;
     // (1 + lambda c)^zeta and zeta (1 + lambda c)^(zeta - 1), lambda = +1 (p) and -1 (m)
     const float bp1 = 1.f + cth, bm1 = 1.f - cth;
     const float bp2 = bp1 * bp1, bm2 = bm1 * bm1, bp4 = bp2 * bp2, bm4 = bm2 * bm2;
@@ -344,8 +336,8 @@ __device__ __forceinline__ float4 pair_terms(const NbStage &S, const float (&wan
     // d/dd_p: S1 E ff (d_q / (r_p r_q) - c d_p / r_p^2) - 2 eta S0 E ff d_p + S0 E dfc_p fc_q d_p / r_p
     const float A = S1E * inv_pq;
     const float Bc = -2.f * (0.005f * S0_1 * E1 + 0.05f * S0_2 * E2) * ffq;
-    const float Bp = Bc - S1E * cth * (rip * rip) + S0E * S.dfc[p] * fq * rip;
-    const float Bq = Bc - S1E * cth * (riq * riq) + S0E * fp * S.dfc[q] * riq;
+    const float Bp = Bc - S1E * cth * (rip * rip) + S0E * cp.y * fq * rip;
+    const float Bq = Bc - S1E * cth * (riq * riq) + S0E * fp * cq.y * riq;
     ax += A * xq;
     ay += A * yq;
     az += A * zq;
@@ -373,7 +365,7 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
     // kernel itself.
     if (!P.has_mlp) pdl_wait();
     pdl_release();
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) float smem[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + wib;
     if (row >= M) return;
@@ -472,8 +464,9 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
         }
         // per neighbour: the radial term, then the angular sums (registers, or the shared accumulators)
         auto finish = [&](int p, float bx, float by, float bz, float bw) {
-            const float xp = S.dx[p], yp = S.dy[p], zp = S.dz[p], rp = S.r[p], fp = S.fc[p], dfp = S.dfc[p];
-            const float rip = S.rinv[p];
+            const float4 gp = S.g[p], cp = S.c[p];
+            const float xp = gp.x, yp = gp.y, zp = gp.z, rp = S.r[p], fp = cp.x, dfp = cp.y;
+            const float rip = gp.w;
             // radial: c = sum_k w_k g_k'(r)
             float c = 0.f;
             const float *wr = wbuf + S.sp[p] * nr;
