@@ -251,14 +251,15 @@ def roofline(h, w, peaks, peak_kind, q, n_rep=20):
     elif bound == "tensor":
         ach = amount / sec / 1e12
         bf16 = peaks["bf16_tflops"]
-        if w.target.precision == "bf16":
-            pk, src = bf16, "%s bf16 burst" % peak_kind
+        if w.target.precision in ("bf16", "fp32"):
+            # BF16 and the FP16 split of FP32 targets: the FP16 dense rate equals the BF16 one
+            pk, src = bf16, "%s bf16 burst (FP16 dense = BF16 dense)" % peak_kind
         else:
             # TF32 dense = bf16 x (1.1 / 2.25), the nominal ratio
             pk, src = bf16 * 1.1 / 2.25, "%s bf16 burst x 1.1/2.25 (nominal TF32:BF16)" % peak_kind
         out.update({"bound": "tensor", "achieved": round(ach, 2), "peak": round(pk, 1), "unit": "TFLOP/s",
                     "frac": round(ach / pk, 5), "traffic": traffic, "peak_source": src})
-        if w.target.precision in ("fp32", "fp32-cuda-cores"):
+        if w.target.precision in ("fp32", "fp32-tf32"):
             out["tensor_flop_executed_per_algorithmic"] = 3
     else:
         ach = amount / sec / 1e9
@@ -389,7 +390,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(t_lsd_max * 1e3 / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "dtype_detail": ("FP32 forces and descriptors; MLP %s; FP64 integrator state, z.delta, delta.delta and "
-                         "log ratio" % {"fp32": "at FP32 accuracy as three TF32 tensor-core products per term",
+                         "log ratio" % {"fp32": "at FP32 accuracy as three FP16 tensor-core products per term "
+                                                "(exact power-of-two scales)",
+                                        "fp32-tf32": "at FP32 accuracy as three TF32 tensor-core products per term",
                                         "bf16": "in BF16 on the tensor cores with FP32 accumulation",
                                         "fp8": "in FP32 on the CUDA cores (FP8 not built)",
                                         "fp32-cuda-cores": "in FP32 on the CUDA cores"}[w.target.precision]),

@@ -96,15 +96,21 @@ extern "C" {
 #define LSD_HEAD_TANH 0
 #define LSD_HEAD_LINEAR 1
 
-/* MLP arithmetic.  LSD_FP32 runs on the tensor cores as three TF32 products
- * per term (x = x_hi + x_lo, x_hi = tf32(x), x_lo = tf32(x - x_hi); the terms
- * lo*hi + hi*lo + hi*hi accumulate in FP32), which keeps FP32 accuracy, when
- * width <= 128 and the padded input dimension <= 128; otherwise, and always
- * for LSD_FP32_CUDA_CORES, it runs in plain FP32 on the CUDA cores. */
-#define LSD_FP32 0            /* MLP in FP32 (tensor cores, 3 x TF32)               */
+/* MLP arithmetic.  LSD_FP32 keeps FP32 accuracy on the tensor cores by
+ * splitting every operand x = x_hi + x_lo and accumulating hi*hi + hi*lo +
+ * lo*hi in FP32 (the dropped lo*lo term is below 2^-21 of the product).  The
+ * split is in FP16 (11 significant bits each) after an exact power-of-two
+ * scale: weights per layer with max|W| near 2^14, each activation and gradient
+ * tensor with its |max| on the initial configuration near 2^6 (calibrated once
+ * per handle, 1024x headroom to the FP16 limit).  LSD_FP32_TF32 splits in
+ * TF32 instead (no scales, twice the tensor-core instructions).  Both need
+ * width <= 128 and a padded input dimension <= 128; otherwise, and always for
+ * LSD_FP32_CUDA_CORES, the MLP runs in plain FP32 on the CUDA cores. */
+#define LSD_FP32 0            /* MLP in FP32 (tensor cores, 3 x FP16, scaled)        */
 #define LSD_BF16 1            /* MLP in BF16 with FP32 accumulation                  */
 #define LSD_FP8 2             /* MLP in FP8 e4m3, per-tensor scales, FP32 accumulate */
 #define LSD_FP32_CUDA_CORES 3 /* MLP in FP32 on the CUDA cores                       */
+#define LSD_FP32_TF32 4       /* MLP in FP32 (tensor cores, 3 x TF32)                */
 
 typedef struct {
     int32_t n_atoms;
@@ -119,7 +125,7 @@ typedef struct {
 
 typedef struct {
     int32_t kind;               /* LSD_POT_*                                                */
-    int32_t precision;          /* LSD_FP32 | LSD_BF16 | LSD_FP8 | LSD_FP32_CUDA_CORES      */
+    int32_t precision;          /* LSD_FP32 | LSD_BF16 | LSD_FP8 | LSD_FP32_CUDA_CORES | LSD_FP32_TF32 */
     const double *lj_eps;       /* [n_species] eV                                           */
     const double *lj_sigma;     /* [n_species] Angstrom                                     */
     double lj_cutoff;           /* Angstrom; LJ term present when > 0                       */

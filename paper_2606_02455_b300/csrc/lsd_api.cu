@@ -50,9 +50,10 @@ struct PotHost {
     __nv_bfloat16 *tc_scratch = nullptr;  // per-CTA SiLU' slots of the tensor-core MLP (when not in TMEM)
     size_t n_dbuf = 0;                    // floats in dbuf
     float *dbuf_tf = nullptr;             // TF32 hi parts of the FP32 layouts, then the lo parts
+    __half *dbuf_h = nullptr;             // scaled FP16 hi parts of the FP32 layouts, then the lo parts
     uint8_t *dbuf_f8 = nullptr;           // e4m3 copies of the FP32 layouts (per-layer scales)
-    float *tc_scales = nullptr;           // FP8 [3L]: forward A scales, backward A scales, weight scales
-    float *tc_amax = nullptr;             // FP8 calibration [2L]
+    float *tc_scales = nullptr;           // FP8, F16x3 [3L]: forward A, backward A, weight dequantisation factors
+    float *tc_amax = nullptr;             // calibration [2L]
 };
 
 }  // namespace
@@ -174,7 +175,7 @@ int pot_setup(lsd_handle *h, PotHost &ph, const lsd_potential *lp, bool is_draft
     P.head = lp->head;
     P.head_scale = (float)lp->head_scale;
     if (lp->kind < LSD_POT_LJ || lp->kind > LSD_POT_LEARNED) return LSD_EINVAL;
-    if (lp->precision < LSD_FP32 || lp->precision > LSD_FP32_CUDA_CORES) return LSD_EINVAL;
+    if (lp->precision < LSD_FP32 || lp->precision > LSD_FP32_TF32) return LSD_EINVAL;
     P.has_lj = lp->lj_cutoff > 0.0;
     P.has_mlp = lp->kind != LSD_POT_LJ && lp->n_layers > 0;
     if (P.has_lj) {
@@ -234,7 +235,12 @@ int pot_setup(lsd_handle *h, PotHost &ph, const lsd_potential *lp, bool is_draft
         ph.n_dbuf = total;
         TRY(dalloc(h, &ph.dbuf, total));
         TRY(dalloc(h, &ph.dbuf_bf, total));
-        if (lp->precision == LSD_FP32) TRY(dalloc(h, &ph.dbuf_tf, 2 * total));
+        if (lp->precision == LSD_FP32 || lp->precision == LSD_FP32_TF32) TRY(dalloc(h, &ph.dbuf_tf, 2 * total));
+        if (lp->precision == LSD_FP32) {
+            TRY(dalloc(h, &ph.dbuf_h, 2 * total));
+            TRY(dalloc(h, &ph.tc_scales, 3 * (size_t)L));
+            TRY(dalloc(h, &ph.tc_amax, 2 * (size_t)L));
+        }
         if (lp->precision == LSD_FP8) {
             TRY(dalloc(h, &ph.dbuf_f8, total));
             TRY(dalloc(h, &ph.tc_scales, 3 * (size_t)L));
@@ -312,6 +318,29 @@ int pot_upload(lsd_handle *h, PotHost &ph) {
             tf[total + k] = tf32(buf[k] - tf[k]);
         }
         CK(cudaMemcpyAsync(ph.dbuf_tf, tf.data(), 2 * total * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    }
+    std::vector<__half> hh;
+    std::vector<float> hsc;
+    if (ph.dbuf_h) {
+        // FP16 split of W s_l, s_l = 2^(14 - ceil log2 max|W_l|) (exact): hi = fp16(W s), lo = fp16(W s - hi)
+        hh.resize(2 * total);
+        hsc.assign(L, 1.f);
+        for (int l = 0; l < L; ++l) {
+            const int dinp = l == 0 ? P.d0p : W;
+            float m = 0.f;
+            for (size_t k = 0; k < (size_t)dinp * W; ++k) m = std::max(m, std::fabs(buf[offWn[l] + k]));
+            const float sc = m > 0.f ? std::ldexp(1.f, 14 - (int)std::ceil(std::log2(m))) : 1.f;
+            hsc[l] = 1.f / sc;
+            for (const size_t off : {offWn[l], offWt[l]})
+                for (size_t k = 0; k < (size_t)dinp * W; ++k) {
+                    const float x = buf[off + k] * sc;
+                    const __half hi = __float2half_rn(x);
+                    hh[off + k] = hi;
+                    hh[total + off + k] = __float2half_rn(x - __half2float(hi));
+                }
+        }
+        CK(cudaMemcpyAsync(ph.dbuf_h, hh.data(), 2 * total * sizeof(__half), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(ph.tc_scales + 2 * L, hsc.data(), L * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     }
     std::vector<uint8_t> f8;
     std::vector<float> wsc;
@@ -575,13 +604,16 @@ int obabo_enter(lsd_handle *h, long long n) {
     return check_err(st);
 }
 
-// FP8 potentials: the activation and gradient scales, once per handle.  The
-// BF16 kernel runs the potential's MLP on the initial configuration (N rows)
-// and records |max| of every A operand tensor; each scale is 2 |max| / 448, so
-// values up to twice the calibration range are represented and larger ones
-// saturate.  The scales then stay fixed, which keeps the FP8 potential one
-// function of the configuration for the handle's lifetime.
-int calibrate_fp8(lsd_handle *h, PotHost &ph) {
+// The activation and gradient scales of FP8 and F16x3 potentials, once per
+// handle.  A calibration kernel (BF16 for FP8, the unscaled TF32 split for
+// F16x3) runs the potential's MLP on the initial configuration (N rows) and
+// records |max| of every A operand tensor.  FP8: the scale is 2 |max| / 448,
+// so values up to twice the calibration range are represented and larger ones
+// saturate; the fixed scales keep the FP8 potential one function of the
+// configuration for the handle's lifetime.  F16x3: the power of two that puts
+// |max| in (2^5, 2^6]; scaling is exact, so the result does not depend on it
+// as long as values stay below 2^16 (1024x the calibration range).
+int calibrate_scales(lsd_handle *h, PotHost &ph) {
     const PotDev &P = ph.dev;
     const int L = P.n_layers, N = h->N;
     cudaStream_t s = h->stream;
@@ -596,7 +628,12 @@ int calibrate_fp8(lsd_handle *h, PotHost &ph) {
     std::vector<float> am(2 * L), sc(2 * L);
     CK(cudaMemcpyAsync(am.data(), ph.tc_amax, 2 * L * sizeof(float), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    for (int k = 0; k < 2 * L; ++k) sc[k] = am[k] > 0.f ? 2.f * am[k] / 448.f : 1.f;
+    const bool f8 = mlp_tc_plan_op(ph.tc_plan) == kTcFP8;
+    for (int k = 0; k < 2 * L; ++k) {
+        if (!(am[k] > 0.f)) sc[k] = 1.f;
+        else if (f8) sc[k] = 2.f * am[k] / 448.f;                                // e4m3: 2 |max| at the top
+        else sc[k] = std::ldexp(1.f, (int)std::ceil(std::log2(am[k])) - 6);   // F16x3: |max| at 2^6, exact
+    }
     CK(cudaMemcpyAsync(ph.tc_scales, sc.data(), 2 * L * sizeof(float), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     DevState st;
@@ -806,16 +843,28 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         if (!P.has_mlp) continue;
         int op = -1;
         if (P.precision == LSD_BF16) op = kTcBF16;
-        if (P.precision == LSD_FP32 && ph->dbuf_tf && mlp_tc_supported(kTcTF32x3, P)) op = kTcTF32x3;
+        if (P.precision == LSD_FP32_TF32 && mlp_tc_supported(kTcTF32x3, P)) op = kTcTF32x3;
+        if (P.precision == LSD_FP32 && mlp_tc_supported(kTcF16x3, P)) op = kTcF16x3;
         if (P.precision == LSD_FP8) op = kTcFP8;
-        if (op < 0) continue;   // FP32 beyond the TF32 kernel's shapes, or LSD_FP32_CUDA_CORES: CUDA cores
+        if (op < 0) continue;   // FP32 beyond the split kernels' shapes, or LSD_FP32_CUDA_CORES: CUDA cores
         if (!mlp_tc_supported(op, P)) return fail(LSD_EUNSUPPORTED);
-        TcWeights w{}, wb{};
+        TcWeights w{}, wb{}, wtf{};
         for (int l = 0; l < P.n_layers; ++l) {
             const size_t on = P.Wn[l] - ph->dbuf, ot = P.Wt[l] - ph->dbuf;
             wb.wn[l][0] = P.Wn_bf[l];
             wb.wt[l][0] = P.Wt_bf[l];
-            if (op == kTcTF32x3) {
+            if (ph->dbuf_tf) {
+                wtf.wn[l][0] = ph->dbuf_tf + on;
+                wtf.wn[l][1] = ph->dbuf_tf + ph->n_dbuf + on;
+                wtf.wt[l][0] = ph->dbuf_tf + ot;
+                wtf.wt[l][1] = ph->dbuf_tf + ph->n_dbuf + ot;
+            }
+            if (op == kTcF16x3) {
+                w.wn[l][0] = ph->dbuf_h + on;
+                w.wn[l][1] = ph->dbuf_h + ph->n_dbuf + on;
+                w.wt[l][0] = ph->dbuf_h + ot;
+                w.wt[l][1] = ph->dbuf_h + ph->n_dbuf + ot;
+            } else if (op == kTcTF32x3) {
                 w.wn[l][0] = ph->dbuf_tf + on;
                 w.wn[l][1] = ph->dbuf_tf + ph->n_dbuf + on;
                 w.wt[l][0] = ph->dbuf_tf + ot;
@@ -829,8 +878,9 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         }
         ph->tc_plan = mlp_tc_plan(op, P, w);
         if (!ph->tc_plan) return fail(LSD_ECUDA);
-        if (op == kTcFP8) {
-            ph->cal_plan = mlp_tc_plan(kTcBF16, P, wb);
+        if (op == kTcFP8 || op == kTcF16x3) {
+            // the calibration run: BF16 for FP8, the unscaled TF32 split for F16x3
+            ph->cal_plan = op == kTcFP8 ? mlp_tc_plan(kTcBF16, P, wb) : mlp_tc_plan(kTcTF32x3, P, wtf);
             if (!ph->cal_plan) return fail(LSD_ECUDA);
         }
         const int grid = mlp_tc_grid(h->K * h->N, h->n_sm);
@@ -861,7 +911,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     h->train.st = h->st;
     h->train.K = K;
     for (PotHost *ph : {&h->draft, &h->target})
-        if (ph->cal_plan && (rc = calibrate_fp8(h, *ph)) != LSD_OK) return fail(rc);
+        if (ph->cal_plan && (rc = calibrate_scales(h, *ph)) != LSD_OK) return fail(rc);
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(LSD_ECUDA);
     *out = h;
     return LSD_OK;

@@ -30,7 +30,7 @@ struct Geo {
 
 struct PotDev {
     int kind;              // LSD_POT_*
-    int precision;         // LSD_FP32 | LSD_BF16 | LSD_FP8
+    int precision;         // LSD_FP32 | LSD_BF16 | LSD_FP8 | LSD_FP32_CUDA_CORES | LSD_FP32_TF32
     int head;              // LSD_HEAD_*
     float head_scale;
     int has_lj, has_mlp;

@@ -75,7 +75,7 @@ cudaError_t mlp_kernels_setup(int max_smem);
 
 // MLP on the tcgen05 tensor cores (lsd_mlp_tc.cu): BF16, FP32 as three TF32
 // products per term, FP8 e4m3 with static per-tensor scales
-enum { kTcBF16 = 0, kTcTF32x3 = 1, kTcFP8 = 2 };
+enum { kTcBF16 = 0, kTcTF32x3 = 1, kTcFP8 = 2, kTcF16x3 = 3 };
 struct TcWeights {
     const void *wn[kMaxLayers][2];   // W_l   [W][din_p] in the operand type; [1] = TF32 lo part
     const void *wt[kMaxLayers][2];   // W_l^T [din_p][W]

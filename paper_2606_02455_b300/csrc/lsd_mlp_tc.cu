@@ -17,6 +17,11 @@
 //            A_hi B_hi (columns [0, n)) and A_hi B_lo ([n, 2n)), and a second,
 //            N = n, adds A_lo B_hi to [0, n): two instructions per K step
 //            instead of three; the epilogue adds the two column halves;
+//   F16x3    FP32 targets, same split in FP16 (11 significant bits each) with
+//            exact power-of-two scales (weights: max|W_l| near 2^14; every A
+//            tensor: its calibrated |max| near 2^6, 1024x headroom below the
+//            FP16 limit), K = 16: half the instructions of TF32x3 at the same
+//            accuracy; the epilogue divides by the scales;
 //   FP8      kind::f8f6f4, e4m3 with static per-tensor scales (weights: amax /
 //            448 per layer; every activation and gradient tensor: a scale
 //            calibrated once per handle), K = 32; the accumulator is rescaled
@@ -35,6 +40,7 @@
 // after a bounded time and records an error.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
 #include "lsd.h"
@@ -64,6 +70,10 @@ template <> struct TcT<kTcTF32x3> {
     static constexpr int elem = 4, panel = 32, mmak = 8, copies = 2, maxk = 128, maxn = 128, acc = 256;
     static constexpr uint32_t fmt = tc::kFmtTF32;
 };
+template <> struct TcT<kTcF16x3> {
+    static constexpr int elem = 2, panel = 64, mmak = 16, copies = 2, maxk = 128, maxn = 128, acc = 256;
+    static constexpr uint32_t fmt = tc::kFmtF16;
+};
 template <> struct TcT<kTcFP8> {
     static constexpr int elem = 1, panel = 128, mmak = 32, copies = 1, maxk = 256, maxn = 256, acc = 256;
     static constexpr uint32_t fmt = tc::kFmtE4M3;
@@ -82,6 +92,7 @@ template <int OP> __host__ __device__ constexpr int tc_smem_bytes() {
 static_assert(tc_smem_bytes<kTcBF16>() <= 227 * 1024, "BF16 shared memory");
 static_assert(tc_smem_bytes<kTcTF32x3>() <= 227 * 1024, "TF32 shared memory");
 static_assert(tc_smem_bytes<kTcFP8>() <= 227 * 1024, "FP8 shared memory");
+static_assert(tc_smem_bytes<kTcF16x3>() <= 227 * 1024, "F16x3 shared memory");
 static_assert(tc_stages<kTcTF32x3>() >= 2, "TF32 stages");
 
 // Shared-memory addresses; per-stage ones are computed (a runtime-indexed
@@ -142,6 +153,10 @@ __device__ __forceinline__ bool tc_issue(const TcSm &S, int K, int N, uint32_t t
                 const uint64_t alo = tc::sdesc_sw128(S.a + tc_a_bytes<OP>() / 2 + kc * kPanelBytes) + step;
                 tc::mma_tf32(tmem, ad + step, bd + step, idesc2, acc);   // A_hi [B_hi; B_lo]
                 tc::mma_tf32(tmem, alo, bd + step, idesc, 1u);            // + A_lo B_hi
+            } else if (OP == kTcF16x3) {
+                const uint64_t alo = tc::sdesc_sw128(S.a + tc_a_bytes<OP>() / 2 + kc * kPanelBytes) + step;
+                tc::mma_f16(tmem, ad + step, bd + step, idesc2, acc);
+                tc::mma_f16(tmem, alo, bd + step, idesc, 1u);
             } else if (OP == kTcFP8) {
                 tc::mma_f8f6f4(tmem, ad + step, bd + step, idesc, acc);
             } else {
@@ -164,6 +179,10 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 }
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+__device__ __forceinline__ uint32_t pack_f16(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 __device__ __forceinline__ uint32_t pack_e4m3(float a, float b, float c, float d) {
@@ -195,6 +214,23 @@ __device__ __forceinline__ void store_a16(uint32_t a, int r, int c, const float 
                 l[e] = tf32_rna(v[4 * q + e] - __uint_as_float(h[e]));
             }
             const uint32_t off = pofs + tc::sw128_offset(r, e0 / 4 + q);
+            st_shared_v4(a + off, h[0], h[1], h[2], h[3]);
+            st_shared_v4(a + tc_a_bytes<OP>() / 2 + off, l[0], l[1], l[2], l[3]);
+        }
+    } else if (OP == kTcF16x3) {
+        // scaled by qinv (a power of two); hi = x rounded to 11 significant bits
+        // (exact in FP16 in its normal range), lo = FP16 of the exact remainder
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float x0 = v[8 * q + 2 * e] * qinv, x1 = v[8 * q + 2 * e + 1] * qinv;
+                const float h0 = __uint_as_float(tf32_rna(x0)), h1 = __uint_as_float(tf32_rna(x1));
+                h[e] = pack_f16(h0, h1);
+                l[e] = pack_f16(x0 - h0, x1 - h1);
+            }
+            const uint32_t off = pofs + tc::sw128_offset(r, e0 / 8 + q);
             st_shared_v4(a + off, h[0], h[1], h[2], h[3]);
             st_shared_v4(a + tc_a_bytes<OP>() / 2 + off, l[0], l[1], l[2], l[3]);
         }
@@ -240,7 +276,7 @@ __device__ void tc_producer(const TcSm &S, const TcMaps &maps, int M, const PotD
             }
             tc::mbar_expect_tx(S.full(s), (uint32_t)T::copies * (uint32_t)N * 128u);
             tc::tma_load_2d(S.b(s), &m[0], kc * T::panel, 0, S.full(s));
-            if (OP == kTcTF32x3) tc::tma_load_2d(S.b(s) + (uint32_t)N * 128u, &m[1], kc * T::panel, 0, S.full(s));
+            if (T::copies == 2) tc::tma_load_2d(S.b(s) + (uint32_t)N * 128u, &m[1], kc * T::panel, 0, S.full(s));
         }
     };
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
@@ -321,7 +357,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // the accumulator's columns [c, c + 16) of an N-column GEMM (TF32: the sum of the two halves)
         auto load_acc = [&](int c, int N, float (&v)[16]) {
             tc::tmem_ld16(tacc + c, v);
-            if (OP == kTcTF32x3) {
+            if (OP == kTcTF32x3 || OP == kTcF16x3) {
                 float u[16];
                 tc::tmem_ld16(tacc + N + c, u);
 #pragma unroll
@@ -374,7 +410,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         pdl_wait();
         pdl_release();
         bool ok = true;
-        const float sc_x = OP == kTcFP8 ? scales[0] : 1.f;
+        constexpr bool kScaled = OP == kTcFP8 || OP == kTcF16x3;   // static per-tensor scales
+        const float sc_x = kScaled ? scales[0] : 1.f;
         const int ntiles = (M + kTcRows - 1) / kTcRows;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const int row = tile * kTcRows + r;
@@ -407,8 +444,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const bool last = l == L - 1;
                 ok = wait_acc(issue(l == 0 ? d0p : W, W));
                 if (!ok) break;
-                const float dq = OP == kTcFP8 ? scales[l] * scales[2 * L + l] : 1.f;
-                const float qinv = OP == kTcFP8 ? 1.f / scales[last ? L + L - 1 : l + 1] : 1.f;
+                const float dq = kScaled ? scales[l] * scales[2 * L + l] : 1.f;
+                const float qinv = kScaled ? 1.f / scales[last ? L + L - 1 : l + 1] : 1.f;
                 const float *bl = layer_bias(P, l);
                 am = 0.f;
                 for (int c = 16 * cb; c < W; c += 64) {
@@ -469,8 +506,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 ok = wait_acc(iok);
                 if (!ok) break;
-                const float dq = OP == kTcFP8 ? scales[L + l] * scales[2 * L + l] : 1.f;
-                const float qinv = (OP == kTcFP8 && l > 0) ? 1.f / scales[L + l - 1] : 1.f;
+                const float dq = kScaled ? scales[L + l] * scales[2 * L + l] : 1.f;
+                const float qinv = (kScaled && l > 0) ? 1.f / scales[L + l - 1] : 1.f;
                 am = 0.f;
                 for (int c = 16 * cb; c < dout; c += 64) {
                     float v[16];
@@ -526,8 +563,9 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 static bool make_map(CUtensorMap *m, int op, const void *ptr, int rows, int cols, int box_rows) {
     auto fn = encode_fn();
     if (!fn) return false;
-    const int elem = op == kTcBF16 ? 2 : (op == kTcTF32x3 ? 4 : 1);
-    const CUtensorMapDataType dt = op == kTcBF16   ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+    const int elem = (op == kTcBF16 || op == kTcF16x3) ? 2 : (op == kTcTF32x3 ? 4 : 1);
+    const CUtensorMapDataType dt = op == kTcBF16     ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                   : op == kTcF16x3  ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                    : op == kTcTF32x3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                      : CU_TENSOR_MAP_DATA_TYPE_UINT8;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
@@ -541,7 +579,8 @@ static bool make_map(CUtensorMap *m, int op, const void *ptr, int rows, int cols
 
 bool mlp_tc_supported(int op, const PotDev &P) {
     if (!P.has_mlp || P.width % 32 != 0 || P.n_layers > kMaxLayers || P.n_layers < 1 || !encode_fn()) return false;
-    if (op == kTcTF32x3) return P.width <= 128 && P.d0p <= 128 && 256 + (P.n_layers - 1) * P.width <= (int)kTmemCols;
+    if (op == kTcTF32x3 || op == kTcF16x3)
+        return P.width <= 128 && P.d0p <= 128 && 256 + (P.n_layers - 1) * P.width <= (int)kTmemCols;
     return P.width <= 256 && P.d0p <= 256;
 }
 
@@ -549,7 +588,7 @@ void *mlp_tc_plan(int op, const PotDev &P, const TcWeights &w) {
     TcPlanImpl *pl = new TcPlanImpl();
     pl->op = op;
     bool ok = true;
-    const int ncopy = op == kTcTF32x3 ? 2 : 1;
+    const int ncopy = (op == kTcTF32x3 || op == kTcF16x3) ? 2 : 1;
     for (int l = 0; l < P.n_layers && ok; ++l) {
         const int dinp = l == 0 ? P.d0p : P.width;
         for (int k = 0; k < ncopy && ok; ++k)
@@ -568,7 +607,10 @@ void mlp_tc_plan_free(void *plan) { delete (TcPlanImpl *)plan; }
 int mlp_tc_plan_op(const void *plan) { return ((const TcPlanImpl *)plan)->op; }
 
 size_t mlp_tc_smem_bytes(int op) {
-    return op == kTcBF16 ? tc_smem_bytes<kTcBF16>() : (op == kTcTF32x3 ? tc_smem_bytes<kTcTF32x3>() : tc_smem_bytes<kTcFP8>());
+    return op == kTcBF16     ? tc_smem_bytes<kTcBF16>()
+           : op == kTcTF32x3 ? tc_smem_bytes<kTcTF32x3>()
+           : op == kTcF16x3  ? tc_smem_bytes<kTcF16x3>()
+                             : tc_smem_bytes<kTcFP8>();
 }
 
 // SiLU'(h_l) of the hidden layers but the last, per CTA, when it does not fit
@@ -595,6 +637,10 @@ static void launch_grid(const TcPlanImpl *pl, int grid, const float *X, int M, c
             launch_dependent(mlp_tc_kernel<kTcTF32x3>, grid, kTcThreads, tc_smem_bytes<kTcTF32x3>(), s, pl->maps, X, M,
                              P, E_mlp, dEdX, scratch, scales, amax, err);
             break;
+        case kTcF16x3:
+            launch_dependent(mlp_tc_kernel<kTcF16x3>, grid, kTcThreads, tc_smem_bytes<kTcF16x3>(), s, pl->maps, X, M,
+                             P, E_mlp, dEdX, scratch, scales, amax, err);
+            break;
         default:
             launch_dependent(mlp_tc_kernel<kTcFP8>, grid, kTcThreads, tc_smem_bytes<kTcFP8>(), s, pl->maps, X, M, P,
                              E_mlp, dEdX, scratch, scales, amax, err);
@@ -616,6 +662,9 @@ cudaError_t mlp_tc_setup() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(mlp_tc_kernel<kTcFP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  tc_smem_bytes<kTcFP8>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(mlp_tc_kernel<kTcF16x3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc_smem_bytes<kTcF16x3>());
     return e;
 }
 

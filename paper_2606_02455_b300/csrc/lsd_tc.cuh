@@ -141,7 +141,7 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
 __host__ __device__ constexpr uint32_t idesc_f32acc(uint32_t ab_format, int M, int N) {
     return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-constexpr uint32_t kFmtBF16 = 1, kFmtTF32 = 2;
+constexpr uint32_t kFmtF16 = 0, kFmtBF16 = 1, kFmtTF32 = 2;
 constexpr uint32_t kFmtE4M3 = 0;   // kind::f8f6f4 operand format
 
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,

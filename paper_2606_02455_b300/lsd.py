@@ -23,7 +23,7 @@ ERRORS = {-1: "LSD_EINVAL", -2: "LSD_ENOMEM", -3: "LSD_ECUDA", -4: "LSD_ETIMEOUT
           -6: "LSD_ESTATE", -7: "LSD_EOVERFLOW", -8: "LSD_EUNSUPPORTED"}
 POT_LJ, POT_LJ_MLP, POT_LEARNED = 0, 1, 2
 HEAD_TANH, HEAD_LINEAR = 0, 1
-PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2, "fp32-cuda-cores": 3}
+PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2, "fp32-cuda-cores": 3, "fp32-tf32": 4}
 
 # every symbol declared in include/lsd.h
 SYMBOLS = ["lsd_init", "lsd_draft_window", "lsd_verify_window", "lsd_step", "lsd_plain_step", "lsd_enqueue_windows",

@@ -88,10 +88,12 @@ def test_tensor_core_window_runs_and_commits():
 
 
 @pytest.mark.parametrize("cfg", [1, 2])
-def test_fp32_tensor_core_mlp_matches_oracle(cfg):
-    """FP32 targets run their MLP on the tensor cores as three TF32 products per term: descriptors, dE/dX and forces
-    on perturbed configurations stay within the FP32 bar (1e-5 relative) of the FP64 oracle, and agree with the
-    plain FP32 CUDA-core kernel to the same bar."""
+@pytest.mark.parametrize("precision", ["fp32", "fp32-tf32"])
+def test_fp32_tensor_core_mlp_matches_oracle(cfg, precision):
+    """FP32 targets run their MLP on the tensor cores as three products per term, split in FP16 with exact
+    power-of-two scales (fp32) or in TF32 (fp32-tf32): descriptors, dE/dX and forces on perturbed configurations
+    stay within the FP32 bar (1e-5 relative) of the FP64 oracle, and agree with the plain FP32 CUDA-core kernel to
+    the same bar."""
     import torch
     from paper_2606_02455_b300 import lsd
     w = W.CONFIGS[cfg]()
@@ -99,7 +101,7 @@ def test_fp32_tensor_core_mlp_matches_oracle(cfg):
     integ = W.replace(w.integ, K=4)
     rng = np.random.default_rng(cfg)
     qs = np.stack([s.positions + 0.05 * rng.standard_normal(s.positions.shape) for _ in range(4)])
-    h = lsd.LSD(s, w.draft, w.target, integ)
+    h = lsd.LSD(s, w.draft, W.replace(w.target, precision=precision), integ)
     hc = lsd.LSD(s, w.draft, W.replace(w.target, precision="fp32-cuda-cores"), integ)
     F = h.target_forces(torch.tensor(qs, device="cuda")).cpu().numpy()
     Fc = hc.target_forces(torch.tensor(qs, device="cuda")).cpu().numpy()
@@ -161,7 +163,7 @@ def test_fp8_potential_is_one_function():
     h.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("bf16", BF16_TOL)])
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp32-tf32", 1e-5), ("bf16", BF16_TOL)])
 def test_persistent_tiles_match_single_tile_launches(precision, tol):
     """The grid is one CTA per SM looping over 128-row tiles: 40 configurations of 512 atoms are 160 tiles on 148
     SMs, so some CTAs run a second tile with their barrier phases carried over.  Those configurations agree with the
@@ -179,7 +181,7 @@ def test_persistent_tiles_match_single_tile_launches(precision, tol):
         small = h.target_forces(torch.tensor(qs[c0:c0 + 2], device="cuda")).cpu().numpy()
         for c in range(2):
             assert _rel(small[c], big[c0 + c].astype(np.float64)) < tol
-    if precision == "fp32":
+    if precision.startswith("fp32"):
         hc = lsd.LSD(s, draft, W.replace(tgt, precision="fp32-cuda-cores"), integ)
         ref = hc.target_forces(torch.tensor(qs, device="cuda")).cpu().numpy()
         for c in range(n):
