@@ -163,7 +163,7 @@ def _lj_pairs_per_atom(w, q):
 # profiles/ give the command); a kernel changed since its capture has no entry here.
 NCU_TRAFFIC = {
     ("lj_mlp_angular_256atoms_K16", "draft"): 56832,       # draft_window_cluster_kernel, K = 16
-    ("lj_mlp_angular_256atoms_K16", "mlp"): 1748224,       # mlp_tc_kernel<TF32x3>, 4096 rows
+    ("lj_mlp_angular_256atoms_K16", "mlp"): 1419520,       # mlp_tc_kernel<F16x3>, 4096 rows
 }
 
 
