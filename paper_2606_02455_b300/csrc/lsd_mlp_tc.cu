@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         auto sp_addr = [&](int l, int c) -> __nv_bfloat16 * { return my_scr + ((size_t)l * kTcRows + r) * W + c; };
         auto store_sp = [&](int l, int c, const float (&d)[16]) {
             if (sp_tmem) {
-                tc::tmem_st16(tacc + ACC + l * W + c, d);
+                tc::tmem_st16_async(tacc + ACC + l * W + c, d);   // completes by the wait at the epilogue's end
             } else {
                 uint4 *o = reinterpret_cast<uint4 *>(sp_addr(l, c));
                 o[0] = make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]),
@@ -356,12 +356,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         };
         // the accumulator's columns [c, c + 16) of an N-column GEMM (TF32: the sum of the two halves)
         auto load_acc = [&](int c, int N, float (&v)[16]) {
-            tc::tmem_ld16(tacc + c, v);
             if (OP == kTcTF32x3 || OP == kTcF16x3) {
-                float u[16];
-                tc::tmem_ld16(tacc + N + c, u);
+                uint32_t a[16], b[16];   // both halves in flight, one wait
+                tc::tmem_ld16_issue(tacc + c, a);
+                tc::tmem_ld16_issue(tacc + N + c, b);
+                tc::tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] += u[i];
+                for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(a[i]) + __uint_as_float(b[i]);
+            } else {
+                tc::tmem_ld16(tacc + c, v);
             }
         };
         auto load_sp = [&](int l, int c, float (&d)[16]) {
@@ -388,6 +391,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // would take issue turns from the issuing lane.
         uint32_t chunk = 0, gemm = 0;
         auto issue = [&](int K, int N) -> bool {
+            tc::tmem_wait_st();   // this epilogue's SiLU' stores
             tc::fence_async_shared();
             tc::fence_before_sync();
             epi_sync();
