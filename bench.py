@@ -5,7 +5,7 @@
 A step is one LSD window: K drafted steps (persistent draft kernel), one batched target evaluation on all K*N
 atoms (neighbours, descriptors, MLP, adjoint), transport and commit; the window runs as one CUDA graph.
 `value` = committed steps x dt / device time, in ns/day, with the state resident in HBM.  L2 is flushed
-between timed windows.  `e2e` is the same metric through the public per-window C-ABI calls with the state
+between timed windows.  `e2e` is the same metric through the public one-call window (lsd_window_host) with the state
 copied host->device before and device->host after every window.  The plain-target baseline (the same
 kernels, one ABOBA step per graph launch) is timed the same way in the same process.  `roofline` is the
 dominant kernel, timed live with CUDA events on the library's stream.  `cpu_baseline` is the FP64 oracle on a
@@ -361,20 +361,20 @@ def run_ours(args):
     value = whole_job_rate(committed, t_lsd, world) * w.integ.dt * NS_PER_DAY
     plain_value = whole_job_rate(n_plain, t_plain, world) * w.integ.dt * NS_PER_DAY
 
-    # ---- e2e: public per-window calls with host buffers ----
+    # ---- e2e: the public one-call window with host buffers (pinned): every window uploads its state, runs,
+    # and reads the committed state back ----
     h.set_state(q_eq, p_eq, step_eq)
-    pos = np.ascontiguousarray(q_eq.copy())
-    mom = np.ascontiguousarray(p_eq.copy())
+    pos = torch.empty((s.n_atoms, 3), dtype=torch.float64, pin_memory=True).numpy()
+    mom = torch.empty((s.n_atoms, 3), dtype=torch.float64, pin_memory=True).numpy()
+    pos[:] = q_eq
+    mom[:] = p_eq
     n_e2e = args.steps
     stats_a = h.stats()
     step = step_eq
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(n_e2e):
-        h.set_state(pos, mom, step)
-        h.draft_window()
-        nc, _ = h.verify_window()
-        pos, mom, step = h.get_state(pos, mom)
+        step, nc = h.window_host(pos, mom, step)
     t_e2e = time.perf_counter() - t0
     stats_b = h.stats()
     e2e_committed = stats_b["committed"] - stats_a["committed"]
@@ -412,9 +412,8 @@ def run_ours(args):
         "value_unpipelined": None if value_unpipelined is None else round(value_unpipelined, 3),
         "plain_ms_per_step": round(t_plain * 1e3 / n_plain, 5),
         "gpu_launches": int(windows * launches_per_window + n_plain * lc["plain"]),
-        "e2e": {"value": round(e2e_val, 3), "unit": "ns/day", "h2d_bytes_per_step": 2 * D * 8 + 8,
-                "d2h_bytes_per_step": 2 * D * 8 + 8 + 8, "calls": "lsd_set_state, lsd_draft_window, "
-                                                                  "lsd_verify_window, lsd_get_state"},
+        "e2e": {"value": round(e2e_val, 3), "unit": "ns/day", "h2d_bytes_per_step": 2 * D * 8 + 16,
+                "d2h_bytes_per_step": 2 * D * 8 + 32, "calls": "lsd_window_host (pinned host state in and out)"},
         "roofline": rl,
         "clocks": clk,
     }

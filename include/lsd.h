@@ -196,6 +196,17 @@ LSD_API int lsd_enqueue_plain(lsd_handle *h, int32_t n_steps);
 LSD_API int lsd_get_state(const lsd_handle *h, double *pos, double *mom, int64_t *step);
 LSD_API int lsd_set_state(lsd_handle *h, const double *pos, const double *mom, int64_t step);
 
+/* lsd_window_host: one window (Alg. 1, lsd_draft_window + lsd_verify_window)
+ * from a host state, with the new state returned to the host, in one call:
+ * the state (pos, mom [N][3], step) is copied to the device, the window runs
+ * as one graph launch, and the committed state is copied back into pos_out,
+ * mom_out (may alias pos, mom) with its step index and the committed count;
+ * one stream synchronisation.  Pinned host buffers make the copies
+ * asynchronous.  Staggered OBABO states are entered as by lsd_set_state.
+ * Returns the window's error status as lsd_verify_window does. */
+LSD_API int lsd_window_host(lsd_handle *h, const double *pos, const double *mom, int64_t step, double *pos_out,
+                            double *mom_out, int64_t *step_out, int32_t *n_committed);
+
 /* lsd_get_stats: cumulative counters (see lsd_stats). */
 LSD_API int lsd_get_stats(const lsd_handle *h, lsd_stats *out);
 

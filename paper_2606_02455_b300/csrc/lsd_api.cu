@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -1022,6 +1023,40 @@ int lsd_get_stats(const lsd_handle *h, lsd_stats *out) {
     out->sum_pred_reject = s.sum_pred;
     out->step = s.step;
     return LSD_OK;
+}
+
+int lsd_window_host(lsd_handle *h, const double *pos, const double *mom, int64_t step, double *pos_out,
+                    double *mom_out, int64_t *step_out, int32_t *n_committed) {
+    if (!h || !pos || !mom || !pos_out || !mom_out || step < 0) return LSD_EINVAL;
+    TRY(ensure_graphs(h));
+    const size_t D = 3 * (size_t)h->N;
+    double *pm = h->coef.obabo ? h->p_obabo : h->p;
+    CK(cudaMemcpyAsync(h->q, pos, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(pm, mom, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    // step and stop step of the run state, adjacent: one copy
+    static_assert(offsetof(DevState, target_step) == offsetof(DevState, step) + sizeof(long long), "layout");
+    long long head[2] = {step, step + h->K};
+    CK(cudaMemcpyAsync(&h->st->step, head, sizeof(head), cudaMemcpyHostToDevice, h->stream));
+    h->unbounded = false;
+    h->drafted = false;
+    h->pipe_primed = false;
+    if (h->coef.obabo) TRY(obabo_enter(h, step));
+    CK(cudaGraphLaunch(h->g_window, h->stream));
+    CK(cudaMemcpyAsync(pos_out, h->q, D * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(mom_out, pm, D * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    // step, stop step, committed count, first rejection, k_eff, error flags: the first 32 bytes
+    struct Head {
+        long long step, target;
+        int n_commit, first_reject, k_eff, err;
+    } out{};
+    static_assert(offsetof(DevState, err) + sizeof(int) == sizeof(Head), "layout");
+    CK(cudaMemcpyAsync(&out, h->st, sizeof(Head), cudaMemcpyDeviceToHost, h->stream));
+    TRY(wait_stream(h));
+    if (step_out) *step_out = out.step;
+    if (n_committed) *n_committed = out.n_commit;
+    DevState s{};
+    s.err = out.err;
+    return check_err(s);
 }
 
 int lsd_get_state(const lsd_handle *hc, double *pos, double *mom, int64_t *step) {

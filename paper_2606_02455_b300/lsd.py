@@ -33,7 +33,7 @@ SYMBOLS = ["lsd_init", "lsd_draft_window", "lsd_verify_window", "lsd_step", "lsd
            "lsd_force_match_dev", "lsd_target_forces_dev", "lsd_draft_forces_dev", "lsd_neighbors",
            "lsd_descriptors", "lsd_get_window", "lsd_profile_window", "lsd_checkpoint", "lsd_restore", "lsd_query",
            "lsd_target_mlp_static_dev", "lsd_destroy",
-           "lsd_strerror", "lsd_launch_counts"]
+           "lsd_strerror", "lsd_launch_counts", "lsd_window_host"]
 
 
 class LSDError(RuntimeError):
@@ -103,6 +103,7 @@ def _lib():
             "lsd_restore": [P, P, SZ],
             "lsd_query": [P, P, P, P, P],
             "lsd_launch_counts": [P, P, P, P],
+            "lsd_window_host": [P, P, P, ctypes.c_int64, P, P, P, P],
             "lsd_target_mlp_static_dev": [P, P, I32, P, P],
             "lsd_profile_window": [P, P, I32],
         }
@@ -253,6 +254,19 @@ class LSD:
         pos = np.ascontiguousarray(pos, dtype=np.float64)
         mom = np.ascontiguousarray(mom, dtype=np.float64)
         _check(_lib().lsd_set_state(self.h, _p(pos), _p(mom), int(step)), "lsd_set_state")
+
+    def window_host(self, pos, mom, step, pos_out=None, mom_out=None):
+        """One window from a host state (lsd_window_host): numpy float64 [N, 3] arrays (pinned memory makes the
+        copies asynchronous); pos_out / mom_out default to pos / mom.  Returns (new step, committed count)."""
+        pos_out = pos if pos_out is None else pos_out
+        mom_out = mom if mom_out is None else mom_out
+        for a in (pos, mom, pos_out, mom_out):
+            assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"] and a.shape == (self.N, 3)
+        st = ctypes.c_int64()
+        nc = ctypes.c_int32()
+        _check(_lib().lsd_window_host(self.h, _p(pos), _p(mom), int(step), _p(pos_out), _p(mom_out),
+                                      ctypes.byref(st), ctypes.byref(nc)), "lsd_window_host")
+        return st.value, nc.value
 
     def set_stream(self, stream=None):
         ptr = None if stream is None else ctypes.c_void_p(stream.cuda_stream)

@@ -90,3 +90,34 @@ def test_launch_counts_follow_the_configuration():
     h = lsd.LSD(w.system, w.draft, w.target, w.integ)
     assert h.launch_counts() == dict(window=12, round=20, plain=11)
     h.close()
+
+
+def test_window_host_equals_the_per_window_calls():
+    """lsd_window_host (state in, one window, state out, one synchronisation) commits bit for bit what
+    lsd_set_state + lsd_draft_window + lsd_verify_window + lsd_get_state commit, over windows with and without
+    rejections, with the output buffers aliasing the inputs."""
+    import torch
+    from paper_2606_02455_b300 import lsd
+    w = W.config2()
+    s = w.system
+    a = lsd.LSD(s, w.draft, w.target, w.integ)
+    b = lsd.LSD(s, w.draft, w.target, w.integ)
+    pos = torch.empty((s.n_atoms, 3), dtype=torch.float64, pin_memory=True).numpy()
+    mom = torch.empty((s.n_atoms, 3), dtype=torch.float64, pin_memory=True).numpy()
+    pos[:] = s.positions
+    mom[:] = s.momenta
+    q, p, step = s.positions.copy(), s.momenta.copy(), 0
+    rejected = 0
+    for _ in range(12):
+        b.set_state(q, p, step)
+        b.draft_window()
+        nc_b, first = b.verify_window()
+        q, p, step_b = b.get_state()
+        step_a, nc_a = a.window_host(pos, mom, step)
+        assert (step_a, nc_a) == (step_b, nc_b)
+        assert np.array_equal(pos, q) and np.array_equal(mom, p)
+        rejected += first != -1
+        step = step_b
+    assert rejected > 0
+    a.close()
+    b.close()
