@@ -113,6 +113,7 @@ struct lsd_handle {
     double *qb = nullptr, *pb = nullptr;
     cudaStream_t dstream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_v = nullptr, ev_d = nullptr;
+    cudaEvent_t ev_sync = nullptr;   // wait_stream's event, created once
     cudaGraphExec_t g_round[2] = {nullptr, nullptr};
     bool drafted = false;
     bool unbounded = false;   // target_step set to "no cap" by lsd_enqueue_*
@@ -373,30 +374,23 @@ int nb_capacity(double density, double rc, int extra) {
 }
 
 int wait_stream(lsd_handle *h) {
-    cudaEvent_t ev;
-    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    cudaError_t e = cudaEventRecord(ev, h->stream);
+    if (!h->ev_sync) CK(cudaEventCreateWithFlags(&h->ev_sync, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(h->ev_sync, h->stream);
     if (e != cudaSuccess) {
-        cudaEventDestroy(ev);
         g_last_cuda = e;
         return LSD_ECUDA;
     }
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
-        e = cudaEventQuery(ev);
+        e = cudaEventQuery(h->ev_sync);
         if (e == cudaSuccess) break;
         if (e != cudaErrorNotReady) {
-            cudaEventDestroy(ev);
             g_last_cuda = e;
             return LSD_ECUDA;
         }
         const double dtw = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        if (dtw > kWaitLimitSeconds) {
-            cudaEventDestroy(ev);
-            return LSD_ETIMEOUT;
-        }
+        if (dtw > kWaitLimitSeconds) return LSD_ETIMEOUT;
     }
-    cudaEventDestroy(ev);
     return LSD_OK;
 }
 
@@ -678,7 +672,7 @@ void lsd_destroy(lsd_handle *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->dstream) cudaStreamSynchronize(h->dstream);
     destroy_graphs(h);
-    for (cudaEvent_t e : {h->ev_fork, h->ev_v, h->ev_d})
+    for (cudaEvent_t e : {h->ev_fork, h->ev_v, h->ev_d, h->ev_sync})
         if (e) cudaEventDestroy(e);
     if (h->dstream) cudaStreamDestroy(h->dstream);
     for (void *v : h->allocs) cudaFree(v);
