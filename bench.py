@@ -364,8 +364,8 @@ def run_ours(args):
     # ---- e2e: the public one-call window with host buffers (pinned): every window uploads its state, runs,
     # and reads the committed state back ----
     h.set_state(q_eq, p_eq, step_eq)
-    pos = torch.empty((s.n_atoms, 3), dtype=torch.float64, pin_memory=True).numpy()
-    mom = torch.empty((s.n_atoms, 3), dtype=torch.float64, pin_memory=True).numpy()
+    state = torch.empty((2, s.n_atoms, 3), dtype=torch.float64, pin_memory=True).numpy()
+    pos, mom = state[0], state[1]   # adjacent, as on the device: one copy each way
     pos[:] = q_eq
     mom[:] = p_eq
     n_e2e = args.steps

@@ -806,7 +806,8 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     }
     const size_t N = h->N, D = 3 * N, KN = (size_t)K * N, KD = (size_t)K * D;
     const int dmax = std::max(h->draft.dev.d0p, h->target.dev.d0p);
-    if ((rc = dalloc(h, &h->q, D)) || (rc = dalloc(h, &h->p, D)) || (rc = dalloc(h, &h->p_obabo, D)) || (rc = dalloc(h, &h->species, N)) ||
+    // q and p in one allocation, p right after q: a host state laid out the same way moves in one copy
+    if ((rc = dalloc(h, &h->q, 2 * D)) || (rc = dalloc(h, &h->p_obabo, D)) || (rc = dalloc(h, &h->species, N)) ||
         (rc = dalloc(h, &h->st, 1)) || (rc = dalloc(h, &h->w_qmid, KD)) || (rc = dalloc(h, &h->w_pdraft, KD)) ||
         (rc = dalloc(h, &h->w_Fd, KD)) || (rc = dalloc(h, &h->w_Fraw, KD)) || (rc = dalloc(h, &h->w_Ft, KD)) ||
         (rc = dalloc(h, &h->w_fix, KN)) || (rc = dalloc(h, &h->fix_eval, KN)) || (rc = dalloc(h, &h->ec_dF, D)) ||
@@ -823,6 +824,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         (rc = dalloc(h, &h->vbufs.cell_atoms, N)) || (rc = dalloc(h, &h->vbufs.cell_scratch, 1)) ||
         (rc = dalloc(h, &h->vbufs.vlist, N * h->vplan.cap)) || (rc = dalloc(h, &h->vbufs.vcount, N)))
         return fail(rc);
+    h->p = h->q + D;
     h->wb[0].qmid = h->w_qmid;
     h->wb[0].pdraft = h->w_pdraft;
     h->wb[0].Fd = h->w_Fd;
@@ -1025,8 +1027,12 @@ int lsd_window_host(lsd_handle *h, const double *pos, const double *mom, int64_t
     TRY(ensure_graphs(h));
     const size_t D = 3 * (size_t)h->N;
     double *pm = h->coef.obabo ? h->p_obabo : h->p;
-    CK(cudaMemcpyAsync(h->q, pos, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(pm, mom, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (pm == h->q + D && mom == pos + D) {   // [pos; mom] adjacent on both sides
+        CK(cudaMemcpyAsync(h->q, pos, 2 * D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    } else {
+        CK(cudaMemcpyAsync(h->q, pos, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(pm, mom, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    }
     // step and stop step of the run state, adjacent: one copy
     static_assert(offsetof(DevState, target_step) == offsetof(DevState, step) + sizeof(long long), "layout");
     long long head[2] = {step, step + h->K};
@@ -1036,8 +1042,12 @@ int lsd_window_host(lsd_handle *h, const double *pos, const double *mom, int64_t
     h->pipe_primed = false;
     if (h->coef.obabo) TRY(obabo_enter(h, step));
     CK(cudaGraphLaunch(h->g_window, h->stream));
-    CK(cudaMemcpyAsync(pos_out, h->q, D * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaMemcpyAsync(mom_out, pm, D * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (pm == h->q + D && mom_out == pos_out + D) {
+        CK(cudaMemcpyAsync(pos_out, h->q, 2 * D * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    } else {
+        CK(cudaMemcpyAsync(pos_out, h->q, D * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(mom_out, pm, D * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
     // step, stop step, committed count, first rejection, k_eff, error flags: the first 32 bytes
     struct Head {
         long long step, target;

@@ -92,18 +92,24 @@ def test_launch_counts_follow_the_configuration():
     h.close()
 
 
-def test_window_host_equals_the_per_window_calls():
+@pytest.mark.parametrize("joint", [True, False])
+def test_window_host_equals_the_per_window_calls(joint):
     """lsd_window_host (state in, one window, state out, one synchronisation) commits bit for bit what
     lsd_set_state + lsd_draft_window + lsd_verify_window + lsd_get_state commit, over windows with and without
-    rejections, with the output buffers aliasing the inputs."""
+    rejections, with the output buffers aliasing the inputs; positions and momenta in one pinned buffer (one copy
+    each way) or in two."""
     import torch
     from paper_2606_02455_b300 import lsd
     w = W.config2()
     s = w.system
     a = lsd.LSD(s, w.draft, w.target, w.integ)
     b = lsd.LSD(s, w.draft, w.target, w.integ)
-    pos = torch.empty((s.n_atoms, 3), dtype=torch.float64, pin_memory=True).numpy()
-    mom = torch.empty((s.n_atoms, 3), dtype=torch.float64, pin_memory=True).numpy()
+    if joint:
+        buf = torch.empty((2, s.n_atoms, 3), dtype=torch.float64, pin_memory=True).numpy()
+        pos, mom = buf[0], buf[1]
+    else:
+        pos = torch.empty((s.n_atoms, 3), dtype=torch.float64, pin_memory=True).numpy()
+        mom = torch.empty((s.n_atoms, 3), dtype=torch.float64, pin_memory=True).numpy()
     pos[:] = s.positions
     mom[:] = s.momenta
     q, p, step = s.positions.copy(), s.momenta.copy(), 0

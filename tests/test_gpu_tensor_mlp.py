@@ -188,3 +188,23 @@ def test_persistent_tiles_match_single_tile_launches(precision, tol):
             assert _rel(big[c], ref[c].astype(np.float64)) < tol
         hc.close()
     h.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32-tf32"])
+def test_fp32_split_ragged_rows_match_oracle(precision):
+    """216 atoms x 3 configurations = 648 rows: five full 128-row tiles and a ragged one of 8 rows, through the
+    FP16 and TF32 splits of a 67 -> 128 x 3 -> 1 FP32 target: forces within the FP32 bar of the FP64 oracle."""
+    import torch
+    from paper_2606_02455_b300 import lsd
+    s, draft, tgt = _system(cells=6, precision=precision, width=128, layers=3)
+    integ = W.Integrator(0.5, 0.01, 350.0, 4)
+    h = lsd.LSD(s, draft, tgt, integ)
+    rng = np.random.default_rng(17)
+    qs = np.stack([s.positions + 0.05 * rng.standard_normal(s.positions.shape) for _ in range(3)])
+    F = h.target_forces(torch.tensor(qs, device="cuda")).cpu().numpy()
+    _, G = h.descriptors(3)
+    for c in range(3):
+        ref = O.energy_forces(s, tgt, qs[c], want=("F", "dEdX"))
+        assert _rel(G[c], ref["dEdX"]) < 1e-5, _rel(G[c], ref["dEdX"])
+        assert _rel(F[c], ref["F"]) < 1e-5, _rel(F[c], ref["F"])
+    h.close()
