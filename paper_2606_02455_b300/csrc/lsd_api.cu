@@ -793,9 +793,10 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         while (vp.cap_pow2 < vp.cap) vp.cap_pow2 *= 2;
         if ((size_t)8 * vp.cap_pow2 * sizeof(int) > (size_t)kMaxDynSmem) return fail(LSD_EUNSUPPORTED);
         // the largest cluster the hardware co-schedules with the plan's shared memory
-        h->dplan = draft_plan(h->N, K, h->draft.dev, h->learned_small, 16, kMaxDynSmem);
+        h->dplan = draft_plan(h->N, K, h->draft.dev, h->learned_small, vp.cap, vp.all_pairs, 16, kMaxDynSmem);
         const int maxc = draft_max_cluster(h->dplan.smem, h->learned_small);
-        if (maxc < h->dplan.cluster) h->dplan = draft_plan(h->N, K, h->draft.dev, h->learned_small, maxc, kMaxDynSmem);
+        if (maxc < h->dplan.cluster)
+            h->dplan = draft_plan(h->N, K, h->draft.dev, h->learned_small, vp.cap, vp.all_pairs, maxc, kMaxDynSmem);
         {
             double rcd = h->draft.p.lj_cutoff;
             if (h->learned_small) rcd = std::max(rcd, h->draft.p.desc_cutoff);

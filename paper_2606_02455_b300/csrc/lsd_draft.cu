@@ -25,12 +25,14 @@
 // so the half-step positions are reproducible bit for bit.
 #include "lsd_common.cuh"
 #include "lsd_kernels.h"
+#include "lsd_tc.cuh"
 
 namespace lsd {
 
 constexpr int kDraftThreads = 512;
 constexpr int kDraftWarps = kDraftThreads / 32;
 constexpr int kLearnCap = 96;      // staged descriptor neighbours per warp (learned draft)
+constexpr int kMaxCluster = 16;    // largest draft cluster
 
 __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
@@ -43,6 +45,14 @@ struct FixView {
     const uint4 *smem;
     const uint4 *glob;
     __device__ __forceinline__ uint4 operator[](int k) const { return smem ? smem[k] : __ldcg(glob + k); }
+};
+
+// The candidate list of an owned atom: its copy in shared memory (staged once
+// per launch) or the global Verlet list.
+struct ListView {
+    const int *p;
+    bool smem;
+    __device__ __forceinline__ int operator[](int t) const { return smem ? p[t] : __ldg(p + t); }
 };
 
 // Every image of atom k that passes the per-axis bound around atom i, as
@@ -74,7 +84,7 @@ __device__ __forceinline__ void for_images(const Geo &g, uint4 fi, uint4 fk, flo
 
 // Learned draft, first phase: radial descriptors of atom i from its candidate
 // list (all atoms when cand is null), the MLP (BF16 operands, FP32 accumulation), dE/dx written to g_out[d0p].
-__device__ void learned_atom_grad(const PotDev &P, const Geo &g, const FixView &fx, int i, const int *cand, int nc,
+__device__ void learned_atom_grad(const PotDev &P, const Geo &g, const FixView &fx, int i, const ListView cand, int nc,
                                   bool minimg, float *stage, float *xbuf, float *g_out) {
     const int lane = threadIdx.x & 31;
     const uint4 fi = fx[i];
@@ -86,7 +96,7 @@ __device__ void learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
         // the (at most 8) images of k within the descriptor cutoff, in enumeration order
         float rs[8];
         int nm = 0, sk = 0;
-        const int k = t < nc ? (cand ? __ldg(cand + t) : t) : i;
+        const int k = t < nc ? (cand.p ? cand[t] : t) : i;
         if (k != i) {
             const uint4 fk = fx[k];
             sk = (int)fk.w;
@@ -179,11 +189,16 @@ __device__ __forceinline__ void st_cluster(const int *local, uint32_t rank, int 
 //   A  half-step positions of owned atoms (FP64, one lane per coordinate, four
 //      lanes per atom), their fixed point written to global memory for the
 //      verification and, when the positions fit in shared memory, stored
-//      directly into every CTA's copy (distributed shared memory,
-//      double-buffered by step parity, so one cluster barrier per step orders
-//      both the writes of step j and the reads of step j-1); with Verlet lists,
-//      the displacement check, whose flag is stored the same way
-//   B  cluster barrier; stop when any CTA flagged a displacement
+//      directly into every CTA's copy (asynchronous distributed-shared-memory
+//      stores, double-buffered by step parity, each completing bytes on the
+//      receiving CTA's mbarrier of that parity); with Verlet lists, each CTA's
+//      displacement flag, stored into its own slot in every CTA the same way
+//   B  wait until all N positions (and C flags) of the step have landed in this
+//      CTA -- no cluster-wide barrier, so no fence waits for this step's global
+//      stores; a CTA reaches step j+2 (which rewrites the buffers of step j)
+//      only after every CTA sent step j+1, which each does after reading step
+//      j.  Without staged positions: a cluster barrier, positions from global
+//      memory.  Stop when any CTA flagged a displacement
 //   C  forces on owned atoms (one warp per atom, lanes over the candidates:
 //      the atom's Verlet list, or all atoms when vlist is null)
 //   D  BOB + A, one lane per coordinate
@@ -203,7 +218,8 @@ template <bool LEARNED, bool REG>
 __global__ void __launch_bounds__(kDraftThreads, 1)
     draft_window_cluster_kernel(int K, Geo g, PotDev P, Coef cf, const int *__restrict__ vlist,
                                 const int *__restrict__ vcount, int vcap, const uint4 *__restrict__ fix_base,
-                                float move2f, int stage_fix, int minimg, int noise_smem,
+                                float move2f, float rlist2f, int stage_fix, int minimg, int noise_smem,
+                                int stage_list, int self_list,
                                 const int *__restrict__ species,
                                 const double *__restrict__ q_base, const double *__restrict__ p_base,
                                 const float *__restrict__ ec_dF, int ec_on, DevState *__restrict__ st,
@@ -216,12 +232,22 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     const int A = (N + C - 1) / C;           // owned atoms per CTA
     const int a0 = c * A, a1 = min(N, a0 + A);
     const int nown = a1 > a0 ? a1 - a0 : 0;
+    const bool use_list = vlist != nullptr || self_list;
     float4 *sF = (float4 *)smraw;                               // [A]
-    float *slj = (float *)(sF + A);                             // sig2, eps24 tables
+    uint4 *sbase = (uint4 *)(sF + A);                           // [A] list base positions of owned atoms (lists)
+    float *slj = (float *)(sbase + (use_list ? A : 0));         // sig2, eps24 tables
     float *sstage = slj + 2 * kMaxSpecies * kMaxSpecies;        // learned: per warp 3*cap + d0p
     uint4 *sfix = (uint4 *)(sstage + (LEARNED ? (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) : 0));  // [2][N]
-    int *sflag = (int *)(sfix + (stage_fix ? 2 * (size_t)N : 0));                                        // [2]
-    float *snoise = (float *)(sflag + 4);   // [K][A][3] when noise_smem: the window's xi, drawn up front
+    // displacement flags: [2] (cluster-barrier exchange) or [2][kMaxCluster], one slot per sending CTA
+    int *sflag = (int *)(sfix + (stage_fix ? 2 * (size_t)N : 0));
+    uint64_t *sbar = (uint64_t *)(sflag + 2 * kMaxCluster);   // [2] exchange mbarriers (staged positions)
+    float *snoise = (float *)(sbar + 2);   // [K][A][3] when noise_smem: the window's xi, drawn up front
+    // Read-only per-atom data of owned atoms, staged once: a cluster barrier's
+    // acquire leaves no global line in L1, so a per-step global read is an L2
+    // round trip on the step's critical path.
+    int *sspec = (int *)(snoise + (noise_smem ? (size_t)K * A * 3 : 0));   // [A] species
+    int *svc = sspec + A;                                                  // [A] list lengths (stage_list)
+    int *svl = svc + A;                                                    // [A][vcap] lists (stage_list)
     // the base step: the committed one, or (pipelined loop) the window header's;
     // a redraft runs only when the speculative draft of this window does not
     // stand, from the committed state.  Uniform over the cluster: the header is
@@ -240,7 +266,6 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int grp = tid >> 2, x = tid & 3, gl = lane & ~3;
     const size_t D = (size_t)3 * N;
-    const bool use_list = vlist != nullptr;
     const int passes = (nown + kGroups - 1) / kGroups;
     constexpr int kP = REG ? kRegPasses : 1;
     const float rc2_all = LEARNED ? fmaxf(P.lj_rc2f, P.desc_rc2f) : P.lj_rc2f;
@@ -249,7 +274,77 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
         slj[t] = P.lj_sig2[t];
         slj[kMaxSpecies * kMaxSpecies + t] = P.lj_eps24[t];
     }
-    if (tid < 2) sflag[tid] = 0;
+    if (tid < 2 * kMaxCluster) sflag[tid] = 0;
+    const uint32_t bar0 = tc::smem_u32(sbar);
+    if (stage_fix && tid == 0) {
+        tc::mbar_init(bar0, 1);
+        tc::mbar_init(bar0 + 8, 1);
+        tc::mbar_fence_init();
+    }
+    // bytes that land in this CTA per step: every atom's position, every CTA's flag
+    const uint32_t step_bytes = (uint32_t)(N * sizeof(uint4) + (use_list ? C * sizeof(int) : 0));
+    // remote bases of the CTAs this lane sends positions to (ranks x, x+4, x+8, x+12)
+    uint32_t rfix[4], rbar[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int r = x + 4 * m;
+        rfix[m] = rbar[m] = 0u;
+        if (stage_fix && r < C) {
+            rfix[m] = tc::cluster_map(tc::smem_u32(sfix), (uint32_t)r);
+            rbar[m] = tc::cluster_map(bar0, (uint32_t)r);
+        }
+    }
+    for (int ii = tid; ii < nown; ii += blockDim.x) {
+        sspec[ii] = species[a0 + ii];
+        if (vlist) sbase[ii] = fix_base[a0 + ii];
+        if (vlist && stage_list) svc[ii] = vcount[a0 + ii];
+    }
+    if (vlist && stage_list)
+        for (int e = tid; e < nown * vcap; e += blockDim.x) {
+            const int ii = e / vcap, t = e - ii * vcap;
+            if (t < vcount[a0 + ii]) svl[e] = vlist[(size_t)(a0 + ii) * vcap + t];
+        }
+    if (self_list) {
+        // No cell grid (box narrower than three list radii): each CTA lists its
+        // own atoms' candidates itself, by one scan over every atom's base
+        // position (minimum images: if any image of k lies within the list
+        // radius, the minimum one does), in index order.  The base positions
+        // of all atoms go to the step-1 position buffer, which other CTAs
+        // first write after this CTA has sent its step-0 positions.
+        uint4 *sb_all = sfix + N;
+        for (int k = tid; k < N; k += blockDim.x)
+            sb_all[k] = make_uint4(fixpoint(q_base[3 * k], g.scale[0]), fixpoint(q_base[3 * k + 1], g.scale[1]),
+                                   fixpoint(q_base[3 * k + 2], g.scale[2]), (unsigned)species[k]);
+        __syncthreads();
+        for (int ii = warp; ii < nown; ii += kDraftWarps) {
+            const int i = a0 + ii;
+            const uint4 fi = sb_all[i];
+            int cnt = 0;
+            for (int b0 = 0; b0 < N; b0 += 32) {
+                const int k = b0 + lane;
+                bool in = false;
+                if (k < N && k != i) {
+                    const uint4 fk = sb_all[k];
+                    float dx, dy, dz;
+                    int kk;
+                    axis_min(fi.x, fk.x, g.scale_f[0], dx, kk);
+                    axis_min(fi.y, fk.y, g.scale_f[1], dy, kk);
+                    axis_min(fi.z, fk.z, g.scale_f[2], dz, kk);
+                    in = dist2_rule(dx, dy, dz) < rlist2f;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, in);
+                const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+                if (in && pos < vcap) svl[(size_t)ii * vcap + pos] = k;
+                cnt += __popc(bal);
+            }
+            if (lane == 0) {
+                sbase[ii] = fi;
+                svc[ii] = cnt < vcap ? cnt : vcap;
+                if (cnt > vcap) atomicOr(&st->err, 1);
+            }
+        }
+        __syncthreads();
+    }
     // REG: coordinate x of owned atoms grp + p * kGroups
     double qr[kP], pr[kP];
     float dfr[kP], xr[kP];
@@ -276,20 +371,21 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
             o[2] = xi.z;
         }
     }
-    // every CTA has started and zeroed its flags before the first remote store
+    // every CTA has started, zeroed its flags and initialised its mbarriers before the first remote store
     if (stage_fix || use_list) cluster_barrier();
     __syncthreads();
     int keff = K;
     for (int j = 0; j < K; ++j) {
         const int par = j & 1;
         const unsigned long long n = (unsigned long long)(n0 + j + 1);
+        if (stage_fix && tid == 0) tc::mbar_expect_tx(bar0 + 8 * par, step_bytes);
         // A: half-step positions, fixed point, broadcast, displacement from the list's base
         int moved = 0;
         auto step_a = [&](int p, double &qreg, double &preg) {
             const int ii = grp + p * kGroups;
             const bool own = ii < nown;
             const int i = a0 + (own ? ii : 0);
-            const int sp = own ? species[i] : 0;
+            const int sp = own ? sspec[ii] : 0;
             uint32_t u = 0u;
             if (own && x < 3) {
                 // ABOBA: trailing A of the previous step, then A; staggered OBABO: one full-step A
@@ -316,10 +412,14 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
             if (own) {
                 const uint4 fv = make_uint4(ux, uy, uz, (unsigned)sp);
                 if (x == 0) w_fix[(size_t)j * N + i] = fv;
-                if (stage_fix)
-                    for (int r = x; r < C; r += 4) st_cluster(sfix + (size_t)par * N + i, (uint32_t)r, fv);
+                if (stage_fix) {
+                    const uint32_t off = (uint32_t)(((size_t)par * N + i) * sizeof(uint4));
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        if (x + 4 * m < C) tc::st_async(rfix[m] + off, fv, rbar[m] + 8 * par);
+                }
                 if (use_list && x == 0) {
-                    const uint4 b = fix_base[i];
+                    const uint4 b = sbase[ii];
                     float dmin, d2;
                     int kk;
                     axis_min(b.x, ux, g.scale_f[0], dmin, kk);
@@ -342,7 +442,13 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
         }
         if (use_list) {
             moved = __syncthreads_or(moved);
-            if (moved && tid < C) st_cluster(sflag + par, (uint32_t)tid, 1);
+            if (stage_fix) {
+                if (tid < C)
+                    tc::st_async(tc::cluster_map(tc::smem_u32(sflag + par * kMaxCluster + c), (uint32_t)tid),
+                                 moved ? 1u : 0u, tc::cluster_map(bar0 + 8 * par, (uint32_t)tid));
+            } else if (moved && tid < C) {
+                st_cluster(sflag + par, (uint32_t)tid, 1);
+            }
         }
         // noise of this step's B, independent of the positions: drawn while the barrier completes
         if (REG && !noise_smem) {
@@ -355,20 +461,34 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                 }
             }
         }
-        cluster_barrier();
-        // B: stop drafting when any atom left the skin (same flags in every CTA)
-        if (use_list && sflag[par]) {
-            keff = j;
-            break;
+        // B: this step's positions and flags in this CTA; stop drafting when any
+        // atom left the skin (the same flags in every CTA)
+        if (stage_fix) {
+            const bool ok = tc::mbar_wait_cluster(bar0 + 8 * par, (uint32_t)((j >> 1) & 1));
+            const int f = (use_list && lane < C) ? sflag[par * kMaxCluster + lane] : 0;
+            const int code = __syncthreads_or((ok ? 0 : 2) | (f ? 1 : 0));
+            if (code) {
+                if ((code & 2) && tid == 0) atomicOr(&st->err, 8);
+                keff = j;
+                break;
+            }
+        } else {
+            cluster_barrier();
+            if (use_list && sflag[par]) {
+                keff = j;
+                break;
+            }
         }
         FixView fx{stage_fix ? sfix + (size_t)par * N : nullptr, w_fix + (size_t)j * N};
         if (LEARNED) {
             float *stage = sstage + (size_t)warp * (3 * kLearnCap + P.d0p);
             for (int ii = warp; ii < nown; ii += kDraftWarps) {
                 const int i = a0 + ii;
-                learned_atom_grad(P, g, fx, i, use_list ? vlist + (size_t)i * vcap : nullptr,
-                                  use_list ? vcount[i] : N, minimg != 0, stage, stage + 3 * kLearnCap,
-                                  w_dEdX + (size_t)i * P.d0p);
+                const ListView cand{use_list ? (stage_list ? svl + (size_t)ii * vcap : vlist + (size_t)i * vcap)
+                                             : nullptr,
+                                    stage_list != 0};
+                learned_atom_grad(P, g, fx, i, cand, use_list ? (stage_list ? svc[ii] : vcount[i]) : N,
+                                  minimg != 0, stage, stage + 3 * kLearnCap, w_dEdX + (size_t)i * P.d0p);
             }
             cluster_barrier();   // dE/dx of every atom visible to every CTA
         }
@@ -377,8 +497,9 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
             const int i = a0 + ii;
             const uint4 fi = fx[i];
             const int si = (int)fi.w;
-            const int *lst = use_list ? vlist + (size_t)i * vcap : nullptr;
-            const int nl = use_list ? vcount[i] : N;
+            const ListView lst{use_list ? (stage_list ? svl + (size_t)ii * vcap : vlist + (size_t)i * vcap) : nullptr,
+                               stage_list != 0};
+            const int nl = use_list ? (stage_list ? svc[ii] : vcount[i]) : N;
             float fxx = 0.f, fyy = 0.f, fzz = 0.f;
             if (!LEARNED && minimg) {
                 // pair-only draft, minimum images: four independent candidates per
@@ -389,7 +510,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int t = t0 + 32 * u;
-                        kk[u] = t < nl ? (use_list ? __ldg(lst + t) : t) : i;
+                        kk[u] = t < nl ? (use_list ? lst[t] : t) : i;
                         fk[u] = fx[kk[u]];
                     }
 #pragma unroll
@@ -414,7 +535,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                 }
             }
             for (int t = lane; t < ((!LEARNED && minimg) ? 0 : nl); t += 32) {
-                const int k = use_list ? __ldg(lst + t) : t;
+                const int k = use_list ? lst[t] : t;
                 if (k == i) continue;
                 const uint4 fk = fx[k];
                 const int pr2 = si * g.S + (int)fk.w;
@@ -455,13 +576,13 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
         }
         __syncthreads();
         // the flag of this parity is next written (by any CTA) after the next barrier
-        if (use_list && tid == 0) sflag[par] = 0;
+        if (use_list && !stage_fix && tid == 0) sflag[par] = 0;
         // D: BOB + A, one lane per coordinate
         auto step_d = [&](int p, double &preg, float dfreg, float xreg) {
             const int ii = grp + p * kGroups;
             if (ii >= nown || x >= 3) return;
             const int i = a0 + ii;
-            const int sp = species[i];
+            const int sp = sspec[ii];
             const float4 F = sF[ii];
             const float fr = x == 0 ? F.x : (x == 1 ? F.y : F.z);
             float xx = xreg;
@@ -510,26 +631,42 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     }
 }
 
-static size_t draft_smem_bytes(int N, int C, const PotDev &P, bool learned, bool stage_fix, int noise_K) {
+static size_t draft_smem_bytes(int N, int C, const PotDev &P, bool learned, bool stage_fix, int noise_K, int vcap,
+                               bool stage_list) {
+    // vcap > 0: lists (global or built in the kernel), each CTA's list bases staged
     const int A = (N + C - 1) / C;
     size_t b = (size_t)A * sizeof(float4) + 2 * kMaxSpecies * kMaxSpecies * sizeof(float);
+    if (vcap > 0) b += (size_t)A * sizeof(uint4);
+    b += (size_t)A * sizeof(int);
+    if (stage_list) b += (size_t)A * (vcap + 1) * sizeof(int);
     if (learned) b += (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) * sizeof(float);
     if (stage_fix) b += 2 * (size_t)N * sizeof(uint4);
-    return b + 4 * sizeof(int) + (size_t)noise_K * A * 3 * sizeof(float);
+    return b + 2 * kMaxCluster * sizeof(int) + 2 * sizeof(uint64_t) + (size_t)noise_K * A * 3 * sizeof(float);
 }
 
 constexpr size_t kNoiseSmemMax = 32 * 1024;   // the window's noise is staged up front when it fits
+constexpr size_t kListSmemMax = 64 * 1024;    // owned atoms' Verlet lists are staged when they fit
 
-DraftPlan draft_plan(int N, int K, const PotDev &P, bool learned, int max_cluster, size_t max_smem) {
+DraftPlan draft_plan(int N, int K, const PotDev &P, bool learned, int vcap, bool all_pairs, int max_cluster,
+                     size_t max_smem) {
     DraftPlan pl{};
     int C = 1;
+    max_cluster = max_cluster < kMaxCluster ? max_cluster : kMaxCluster;
     while (C < max_cluster && (N + C - 1) / C > 16) C *= 2;
     pl.cluster = C;
     pl.stage_fix = 2 * (size_t)N * sizeof(uint4) <= 128 * 1024;
     const size_t noise = (size_t)K * ((N + C - 1) / C) * 3 * sizeof(float);
     pl.noise_smem = noise <= kNoiseSmemMax;
     pl.K = K;
-    pl.smem = draft_smem_bytes(N, C, P, learned, pl.stage_fix, pl.noise_smem ? K : 0);
+    pl.stage_list = vcap > 0 && (size_t)((N + C - 1) / C) * (vcap + 1) * sizeof(int) <= kListSmemMax;
+    // without a cell grid the kernel lists candidates itself when the lists fit
+    // (and the base positions fit in the staged position buffers)
+    pl.self_list = all_pairs && pl.stage_list && pl.stage_fix;
+    if (all_pairs && !pl.self_list) {
+        vcap = 0;   // every atom is a candidate; no lists at all
+        pl.stage_list = false;
+    }
+    pl.smem = draft_smem_bytes(N, C, P, learned, pl.stage_fix, pl.noise_smem ? K : 0, vcap, pl.stage_list);
     pl.reg = (N + C - 1) / C <= kRegPasses * kGroups;
     pl.ok = pl.smem <= max_smem;
     return pl;
@@ -556,10 +693,12 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
     const int *vl = vp.all_pairs ? nullptr : (const int *)vb.vlist;
     const int mi = pl.minimg ? 1 : 0;
     const int ns = (pl.noise_smem && K <= pl.K) ? 1 : 0;
+    const int self = (pl.self_list && vp.all_pairs) ? 1 : 0;
+    const int sl = (pl.stage_list && (vl || self)) ? 1 : 0;
     auto kern = learned ? (pl.reg ? draft_window_cluster_kernel<true, true> : draft_window_cluster_kernel<true, false>)
                         : (pl.reg ? draft_window_cluster_kernel<false, true> : draft_window_cluster_kernel<false, false>);
     return cudaLaunchKernelEx(&cfg, kern, K, g, P, cf, vl, (const int *)vb.vcount, vp.cap, (const uint4 *)vb.fix_base,
-                              vp.move2f, stage, mi, ns, species, q, p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd,
+                              vp.move2f, vp.rlist2f, stage, mi, ns, sl, self, species, q, p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd,
                               w_Fraw, w_fix, w_dEdX, hdr, w_logu, redraft);
 }
 

@@ -118,10 +118,13 @@ struct DraftPlan {
     bool reg;         // owned atoms' FP64 state in registers
     bool minimg;      // every draft cutoff below 0.499 of every box side: minimum images only
     bool noise_smem;  // the window's noise drawn up front into shared memory
+    bool stage_list;  // owned atoms' Verlet lists copied to shared memory once per launch
+    bool self_list;   // no cell grid: the kernel lists its atoms' candidates itself (in shared memory)
     int K;            // window length the plan was made for
     bool ok;
 };
-DraftPlan draft_plan(int N, int K, const PotDev &P, bool learned, int max_cluster, size_t max_smem);
+DraftPlan draft_plan(int N, int K, const PotDev &P, bool learned, int vcap, bool all_pairs, int max_cluster,
+                     size_t max_smem);
 int draft_max_cluster(size_t smem, bool learned);
 cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf,
                          const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
