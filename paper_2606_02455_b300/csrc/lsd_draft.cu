@@ -461,6 +461,19 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                 }
             }
         }
+        // the force-independent products of this step's BOB, c1 p and sigma xi,
+        // formed while the positions travel (the same roundings as in D)
+        double c1p[kP], sxi[kP];
+#pragma unroll
+        for (int p = 0; p < kP; ++p) {
+            c1p[p] = sxi[p] = 0.0;
+            const int ii = grp + p * kGroups;
+            if (REG && p < passes && ii < nown && x < 3) {
+                const float xx = noise_smem ? snoise[((size_t)j * A + ii) * 3 + x] : xr[p];
+                c1p[p] = __dmul_rn(cf.c1, pr[p]);
+                sxi[p] = __dmul_rn(species_pick(cf.sig, sspec[ii]), (double)xx);
+            }
+        }
         // B: this step's positions and flags in this CTA; stop drafting when any
         // atom left the skin (the same flags in every CTA)
         if (stage_fix) {
@@ -578,7 +591,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
         // the flag of this parity is next written (by any CTA) after the next barrier
         if (use_list && !stage_fix && tid == 0) sflag[par] = 0;
         // D: BOB + A, one lane per coordinate
-        auto step_d = [&](int p, double &preg, float dfreg, float xreg) {
+        auto step_d = [&](int p, double &preg, float dfreg, float xreg, double c1p_r, double sxi_r) {
             const int ii = grp + p * kGroups;
             if (ii >= nown || x >= 3) return;
             const int i = a0 + ii;
@@ -595,8 +608,8 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
             const size_t o = (size_t)j * D + 3 * i + x;
             const double pv = REG ? preg : ((j == 0) ? p_base[3 * i + x] : w_pdraft[o - D]);
             const float fu = ec_on ? fr + (REG ? dfreg : ec_dF[3 * i + x]) : fr;
-            const double mu = __dadd_rn(__dmul_rn(cf.c1, pv), __dmul_rn(cf.aF, (double)fu));
-            const double pn = __dadd_rn(mu, __dmul_rn(species_pick(cf.sig, sp), (double)xx));
+            const double mu = __dadd_rn(REG ? c1p_r : __dmul_rn(cf.c1, pv), __dmul_rn(cf.aF, (double)fu));
+            const double pn = __dadd_rn(mu, REG ? sxi_r : __dmul_rn(species_pick(cf.sig, sp), (double)xx));
             if (REG) preg = pn;
             w_pdraft[o] = pn;
             w_Fd[o] = fu;
@@ -605,10 +618,10 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
         if (REG) {
 #pragma unroll
             for (int p = 0; p < kP; ++p)
-                if (p < passes) step_d(p, pr[p], dfr[p], xr[p]);
+                if (p < passes) step_d(p, pr[p], dfr[p], xr[p], c1p[p], sxi[p]);
         } else {
             double dp;
-            for (int p = 0; p < passes; ++p) step_d(p, dp, 0.f, 0.f);
+            for (int p = 0; p < passes; ++p) step_d(p, dp, 0.f, 0.f, 0.0, 0.0);
         }
         // the next step reads owned atoms' state from this thread's registers or
         // its own global writes, and sF is rewritten only after the next cluster
