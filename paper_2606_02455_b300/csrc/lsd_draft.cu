@@ -516,35 +516,49 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
             float fxx = 0.f, fyy = 0.f, fzz = 0.f;
             if (!LEARNED && minimg) {
                 // pair-only draft, minimum images: four independent candidates per
-                // lane in flight (loads first, then arithmetic), LJ by predication
-                for (int t0 = lane; t0 < nl; t0 += 128) {
-                    uint4 fk[4];
-                    int kk[4];
+                // lane in flight (loads first, then arithmetic), LJ by predication;
+                // compiled once per way of reaching positions and candidates, so the
+                // staged case reads shared memory with no per-load selection
+                auto gather = [&](auto pos_at, auto cand_at) {
+                    for (int t0 = lane; t0 < nl; t0 += 128) {
+                        uint4 fk[4];
+                        int kk[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int t = t0 + 32 * u;
-                        kk[u] = t < nl ? (use_list ? lst[t] : t) : i;
-                        fk[u] = fx[kk[u]];
-                    }
+                        for (int u = 0; u < 4; ++u) {
+                            const int t = t0 + 32 * u;
+                            kk[u] = t < nl ? cand_at(t) : i;
+                            fk[u] = pos_at(kk[u]);
+                        }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        float dx, dy, dz;
-                        int kx;
-                        axis_min(fi.x, fk[u].x, g.scale_f[0], dx, kx);
-                        axis_min(fi.y, fk[u].y, g.scale_f[1], dy, kx);
-                        axis_min(fi.z, fk[u].z, g.scale_f[2], dz, kx);
-                        const float d2 = dist2_rule(dx, dy, dz);
-                        const bool in = kk[u] != i && d2 < P.lj_rc2f;
-                        const int pr2 = si * g.S + (int)fk[u].w;
-                        const float sig2 = slj[pr2], eps24 = slj[kMaxSpecies * kMaxSpecies + pr2];
-                        const float inv = __fdividef(1.f, in ? d2 : 1.f);
-                        const float s2 = sig2 * inv;
-                        const float s6 = s2 * s2 * s2, s12 = s6 * s6;
-                        const float fr = in ? -eps24 * (2.f * s12 - s6) * inv : 0.f;
-                        fxx += fr * dx;
-                        fyy += fr * dy;
-                        fzz += fr * dz;
+                        for (int u = 0; u < 4; ++u) {
+                            float dx, dy, dz;
+                            int kx;
+                            axis_min(fi.x, fk[u].x, g.scale_f[0], dx, kx);
+                            axis_min(fi.y, fk[u].y, g.scale_f[1], dy, kx);
+                            axis_min(fi.z, fk[u].z, g.scale_f[2], dz, kx);
+                            const float d2 = dist2_rule(dx, dy, dz);
+                            const bool in = kk[u] != i && d2 < P.lj_rc2f;
+                            const int pr2 = si * g.S + (int)fk[u].w;
+                            const float sig2 = slj[pr2], eps24 = slj[kMaxSpecies * kMaxSpecies + pr2];
+                            const float inv = __fdividef(1.f, in ? d2 : 1.f);
+                            const float s2 = sig2 * inv;
+                            const float s6 = s2 * s2 * s2, s12 = s6 * s6;
+                            const float fr = in ? -eps24 * (2.f * s12 - s6) * inv : 0.f;
+                            fxx += fr * dx;
+                            fyy += fr * dy;
+                            fzz += fr * dz;
+                        }
                     }
+                };
+                if (stage_fix && use_list && stage_list) {
+                    const uint4 *sp = sfix + (size_t)par * N;
+                    const int *sl = svl + (size_t)ii * vcap;
+                    gather([&](int k) { return sp[k]; }, [&](int t) { return sl[t]; });
+                } else if (stage_fix && !use_list) {
+                    const uint4 *sp = sfix + (size_t)par * N;
+                    gather([&](int k) { return sp[k]; }, [&](int t) { return t; });
+                } else {
+                    gather([&](int k) { return fx[k]; }, [&](int t) { return use_list ? lst[t] : t; });
                 }
             }
             for (int t = lane; t < ((!LEARNED && minimg) ? 0 : nl); t += 32) {
@@ -582,10 +596,23 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                     }
                 });
             }
-            fxx = warp_sum(fxx);
-            fyy = warp_sum(fyy);
-            fzz = warp_sum(fzz);
-            if (lane == 0) sF[ii] = make_float4(fxx, fyy, fzz, 0.f);
+            // the three warp sums in six shuffles: halves exchange pairs of
+            // components, quarters single ones, then an ordinary butterfly;
+            // lanes 0, 8 and 16 end with the x, y and z totals
+            {
+                const bool lo = lane < 16;
+                float k0 = lo ? fxx : fzz, k1 = lo ? fyy : 0.f;
+                const float s0 = lo ? fzz : fxx, s1 = lo ? 0.f : fyy;
+                k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+                k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+                const bool q = (lane & 8) != 0;
+                float v = q ? k1 : k0;
+                v += __shfl_xor_sync(0xffffffffu, q ? k0 : k1, 8);
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                if ((lane & 7) == 0 && lane < 24) (&sF[ii].x)[lane >> 3] = v;
+            }
         }
         __syncthreads();
         // the flag of this parity is next written (by any CTA) after the next barrier
