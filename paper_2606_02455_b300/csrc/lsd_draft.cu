@@ -346,20 +346,27 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
         __syncthreads();
     }
     // REG: coordinate x of owned atoms grp + p * kGroups
-    double qr[kP], pr[kP];
+    // (and the atom's per-species constants: the half-step drift factor and sigma)
+    double qr[kP], pr[kP], hmr[kP], sgr[kP];
     float dfr[kP], xr[kP];
 #pragma unroll
     for (int p = 0; p < kP; ++p) {
-        qr[p] = pr[p] = 0.0;
+        qr[p] = pr[p] = hmr[p] = sgr[p] = 0.0;
         dfr[p] = xr[p] = 0.f;
         const int ii = grp + p * kGroups;
         if (REG && ii < nown && x < 3) {
             const int i = a0 + ii;
+            const int sp = species[i];
             qr[p] = q_base[3 * i + x];
             pr[p] = p_base[3 * i + x];
             dfr[p] = ec_on ? ec_dF[3 * i + x] : 0.f;
+            hmr[p] = cf.obabo ? species_pick(cf.hmf, sp) : species_pick(cf.hm, sp);
+            sgr[p] = species_pick(cf.sig, sp);
         }
     }
+    // threads of the last warp (idle while warps 0-1 run the FP64 updates) post
+    // each step's expected bytes and send this CTA's displacement flag
+    const int side = tid - (int)(blockDim.x - 32);
     // the noise of every step of the window, when it fits: off the per-step critical path
     if (noise_smem) {
         for (int idx = tid; idx < K * nown; idx += blockDim.x) {
@@ -378,9 +385,14 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     for (int j = 0; j < K; ++j) {
         const int par = j & 1;
         const unsigned long long n = (unsigned long long)(n0 + j + 1);
-        if (stage_fix && tid == 0) tc::mbar_expect_tx(bar0 + 8 * par, step_bytes);
+        if (stage_fix && side == 31) tc::mbar_expect_tx(bar0 + 8 * par, step_bytes);
         // A: half-step positions, fixed point, broadcast, displacement from the list's base
         int moved = 0;
+        // c1 p and sigma xi of this step's BOB (force-independent, the same roundings as in D):
+        // with the noise staged, formed in A right after the drift, under its latency
+        double c1p[kP], sxi[kP];
+#pragma unroll
+        for (int p = 0; p < kP; ++p) c1p[p] = sxi[p] = 0.0;
         auto step_a = [&](int p, double &qreg, double &preg) {
             const int ii = grp + p * kGroups;
             const bool own = ii < nown;
@@ -389,7 +401,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
             uint32_t u = 0u;
             if (own && x < 3) {
                 // ABOBA: trailing A of the previous step, then A; staggered OBABO: one full-step A
-                const double hm = cf.obabo ? species_pick(cf.hmf, sp) : species_pick(cf.hm, sp);
+                const double hm = REG ? hmr[p] : (cf.obabo ? species_pick(cf.hmf, sp) : species_pick(cf.hm, sp));
                 double qv, pv;
                 if (REG) {
                     pv = preg;
@@ -406,6 +418,11 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                 if (REG) qreg = qm;
                 w_qmid[(size_t)j * D + 3 * i + x] = qm;
                 u = fixpoint(qm, scale_x);
+                // after the conversion the exchange waits for, so they queue behind it on the FP64 pipe
+                if (REG && noise_smem) {
+                    c1p[p] = __dmul_rn(cf.c1, pv);
+                    sxi[p] = __dmul_rn(sgr[p], (double)snoise[((size_t)j * A + ii) * 3 + x]);
+                }
             }
             const uint32_t ux = __shfl_sync(0xffffffffu, u, gl), uy = __shfl_sync(0xffffffffu, u, gl + 1),
                            uz = __shfl_sync(0xffffffffu, u, gl + 2);
@@ -443,9 +460,9 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
         if (use_list) {
             moved = __syncthreads_or(moved);
             if (stage_fix) {
-                if (tid < C)
-                    tc::st_async(tc::cluster_map(tc::smem_u32(sflag + par * kMaxCluster + c), (uint32_t)tid),
-                                 moved ? 1u : 0u, tc::cluster_map(bar0 + 8 * par, (uint32_t)tid));
+                if (side >= 0 && side < C)
+                    tc::st_async(tc::cluster_map(tc::smem_u32(sflag + par * kMaxCluster + c), (uint32_t)side),
+                                 moved ? 1u : 0u, tc::cluster_map(bar0 + 8 * par, (uint32_t)side));
             } else if (moved && tid < C) {
                 st_cluster(sflag + par, (uint32_t)tid, 1);
             }
@@ -461,17 +478,15 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                 }
             }
         }
-        // the force-independent products of this step's BOB, c1 p and sigma xi,
-        // formed while the positions travel (the same roundings as in D)
-        double c1p[kP], sxi[kP];
+        // without staged noise, the products are formed here, once xi is drawn
+        if (REG && !noise_smem) {
 #pragma unroll
-        for (int p = 0; p < kP; ++p) {
-            c1p[p] = sxi[p] = 0.0;
-            const int ii = grp + p * kGroups;
-            if (REG && p < passes && ii < nown && x < 3) {
-                const float xx = noise_smem ? snoise[((size_t)j * A + ii) * 3 + x] : xr[p];
-                c1p[p] = __dmul_rn(cf.c1, pr[p]);
-                sxi[p] = __dmul_rn(species_pick(cf.sig, sspec[ii]), (double)xx);
+            for (int p = 0; p < kP; ++p) {
+                const int ii = grp + p * kGroups;
+                if (p < passes && ii < nown && x < 3) {
+                    c1p[p] = __dmul_rn(cf.c1, pr[p]);
+                    sxi[p] = __dmul_rn(sgr[p], (double)xr[p]);
+                }
             }
         }
         // B: this step's positions and flags in this CTA; stop drafting when any
