@@ -43,7 +43,25 @@ def _small_ragged():
     return W.Workload("ragged27", s, W.Potential(**lj), target, W.Integrator(1.0, 0.01, 300.0, 8), 100)
 
 
-WORKLOADS = {"c1": lambda: W.config1(), "c2": lambda: W.config2(), "ragged27": _small_ragged}
+def _dilute_lists():
+    """512 atoms of two species, simple cubic 8^3 at 4 A in a 32 A box: with a 6 A list radius the cell grid has
+    five cells per axis, so the window's Verlet lists come from their own kernels (cell count, scan, fill, list)
+    and, short enough to fit, are copied into the draft CTAs' shared memory (the config-2 box has no cell grid:
+    there the draft lists its own atoms' candidates)."""
+    pos = W.jitter(W.simple_cubic(8, 4.0), 4.0, seed=13)
+    sp = (np.arange(512) % 3 == 0).astype(np.int32)
+    masses = np.array([12.0, 16.0])
+    s = W.System(positions=pos, momenta=W.mb_momenta(masses[sp], 300.0, 17), species=sp, masses=masses,
+                 box=np.array([32.0] * 3), seed=23)
+    lj = dict(lj_eps=np.array([0.0104, 0.0067]), lj_sigma=np.array([3.0, 2.8]), lj_cutoff=5.0)
+    d0 = W.input_dim(2, 8, 0)
+    target = W.Potential(**lj, n_rbf=8, n_ang=0, n_layers=1, width=32, desc_cutoff=4.0, head="tanh",
+                         head_scale=0.3, weights=W.mlp_weights(d0, 1, 32, 29))
+    return W.Workload("dilute512_lists", s, W.Potential(**lj), target, W.Integrator(1.0, 0.01, 300.0, 8), 100)
+
+
+WORKLOADS = {"c1": lambda: W.config1(), "c2": lambda: W.config2(), "ragged27": _small_ragged,
+             "dilute512": _dilute_lists}
 
 
 @pytest.fixture(scope="module", params=list(WORKLOADS))

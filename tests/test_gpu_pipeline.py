@@ -31,6 +31,19 @@ def test_pipelined_equals_unpipelined_bitwise(cfg, scale, n):
     assert np.array_equal(qa, qb) and np.array_equal(pa, pb)
 
 
+def test_pipelined_equals_unpipelined_bitwise_cell_grid_lists():
+    """The same on a box with a cell grid: each window's Verlet lists come from their own kernels (the redraft
+    rebuilds them only when the speculative draft does not stand) and are staged in the draft's shared memory."""
+    from test_gpu_parity import _dilute_lists
+    w = _dilute_lists()
+    target = W.replace(w.target, head_scale=1.5)
+    qa, pa, sa, sta = _run(w, target, 64, False)
+    qb, pb, sb, stb = _run(w, target, 64, True)
+    assert sa == sb == 64
+    assert sta["rejected"] == stb["rejected"] and sta["rejected"] > 0
+    assert np.array_equal(qa, qb) and np.array_equal(pa, pb)
+
+
 def test_pipelined_obabo_equals_unpipelined():
     w = W.config1()
     w = W.replace(w, integ=W.replace(w.integ, scheme="obabo"))
