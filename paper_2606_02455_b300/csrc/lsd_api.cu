@@ -93,7 +93,6 @@ struct lsd_handle {
     float *X = nullptr, *dEdX = nullptr, *E_mlp = nullptr, *E_lj = nullptr, *E_atom = nullptr;
     float4 *pair_g = nullptr, *Fpart = nullptr;
     double2 *partials = nullptr;
-    double *logu = nullptr;
     // streams and graphs
     cudaStream_t own_stream = nullptr, stream = nullptr;
     cudaGraphExec_t g_window = nullptr, g_plain = nullptr;
@@ -104,7 +103,6 @@ struct lsd_handle {
         double *qmid = nullptr, *pdraft = nullptr;
         float *Fd = nullptr, *Fraw = nullptr;
         uint4 *fix = nullptr;
-        double *logu = nullptr;   // [K] log u of the acceptance test, written by the draft
         VerletBufs vb;
     } wb[2];
     bool pipe_on = false, pipe_alloc = false, pipe_primed = false;
@@ -443,7 +441,7 @@ void enqueue_draft_buf(lsd_handle *h, int b, cudaStream_t s, WinHdr *hdr, const 
                             hdr ? (redraft ? &hdr->keep : &hdr->skip) : nullptr);
     }
     launch_draft(h->dplan, h->learned_small, h->K, h->geo, h->draft.dev, h->coef, h->vplan, w.vb, h->species, q, p,
-                 h->ec_dF, h->ec_on, h->st, w.qmid, w.pdraft, w.Fd, w.Fraw, w.fix, h->w_dEdX, w.logu, s, hdr,
+                 h->ec_dF, h->ec_on, h->st, w.qmid, w.pdraft, w.Fd, w.Fraw, w.fix, h->w_dEdX, s, hdr,
                  redraft ? 1 : 0);
 }
 
@@ -453,7 +451,7 @@ void enqueue_verify_buf(lsd_handle *h, int b, cudaStream_t s) {
     enqueue_eval(h, h->target, w.fix, h->K, h->w_Ft, nullptr, s, !h->vplan.all_pairs, &w.vb);
     if (h->train.capture_on) enqueue_frame_capture(h->train, w.qmid, h->w_Ft, h->K, h->N, h->st, s);
     launch_transport(h->K, h->geo, h->coef, h->species, w.qmid, w.pdraft, w.Fd, h->w_Ft, w.Fraw, h->ec_dF, h->ec_on,
-                     h->q, h->p, h->p_obabo, h->st, h->partials, w.logu, s);
+                     h->q, h->p, h->p_obabo, h->st, h->partials, s);
 }
 
 void enqueue_draft(lsd_handle *h, cudaStream_t s) { enqueue_draft_buf(h, 0, s, nullptr, h->q, h->p); }
@@ -818,7 +816,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         (rc = dalloc(h, &h->E_mlp, KN)) || (rc = dalloc(h, &h->E_lj, KN)) || (rc = dalloc(h, &h->E_atom, KN)) ||
         (rc = dalloc(h, &h->pair_g, KN * h->cap_near)) || (rc = dalloc(h, &h->Fpart, KN)) ||
         (rc = dalloc(h, &h->partials, (size_t)K * ((h->N + 1023) / 1024 + 600))) ||
-        (rc = dalloc(h, &h->logu, (size_t)K)) ||         (rc = dalloc(h, &h->w_dEdX, N * std::max(h->draft.dev.d0p, 32))) ||
+        (rc = dalloc(h, &h->w_dEdX, N * std::max(h->draft.dev.d0p, 32))) ||
         (rc = dalloc(h, &h->vbufs.fix_base, N)) || (rc = dalloc(h, &h->vbufs.cell_of_atom, N)) ||
         (rc = dalloc(h, &h->vbufs.cell_count, (size_t)h->vplan.nc[0] * h->vplan.nc[1] * h->vplan.nc[2])) ||
         (rc = dalloc(h, &h->vbufs.cell_start, (size_t)h->vplan.nc[0] * h->vplan.nc[1] * h->vplan.nc[2] + 1)) ||
@@ -831,7 +829,6 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     h->wb[0].Fd = h->w_Fd;
     h->wb[0].Fraw = h->w_Fraw;
     h->wb[0].fix = h->w_fix;
-    h->wb[0].logu = h->logu;
     h->wb[0].vb = h->vbufs;
     if ((rc = pot_upload(h, h->draft)) != LSD_OK) return fail(rc);
     if ((rc = pot_upload(h, h->target)) != LSD_OK) return fail(rc);
@@ -1108,7 +1105,7 @@ int lsd_set_pipelining(lsd_handle *h, int32_t on) {
             (rc = dalloc(h, &w.vb.cell_start, ncell + 1)) || (rc = dalloc(h, &w.vb.cell_atoms, N)) ||
             (rc = dalloc(h, &w.vb.cell_scratch, 1)) || (rc = dalloc(h, &w.vb.vlist, N * h->vplan.cap)) ||
             (rc = dalloc(h, &w.vb.vcount, N)) || (rc = dalloc(h, &h->hdr, 2)) || (rc = dalloc(h, &h->qb, D)) ||
-            (rc = dalloc(h, &h->pb, D)) || (rc = dalloc(h, &w.logu, (size_t)h->K)))
+            (rc = dalloc(h, &h->pb, D)))
             return rc;
         int lo = 0, hi = 0;
         CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
@@ -1297,7 +1294,7 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
     launch_transport_reduce(h->K, h->geo, h->coef, h->species, h->w_Fd, h->w_Ft, h->st, h->partials, st);
     CK(cudaEventRecord(ev[7], st));
     launch_transport_commit(h->K, h->geo, h->coef, h->species, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Ft, h->w_Fraw,
-                            h->ec_dF, h->ec_on, h->q, h->p, h->p_obabo, h->st, h->partials, h->logu, st);
+                            h->ec_dF, h->ec_on, h->q, h->p, h->p_obabo, h->st, h->partials, st);
     CK(cudaEventRecord(ev[8], st));
     CK(cudaGetLastError());
     TRY(wait_stream(h));

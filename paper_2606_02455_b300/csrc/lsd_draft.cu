@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                                 const float *__restrict__ ec_dF, int ec_on, DevState *__restrict__ st,
                                 double *__restrict__ w_qmid, double *__restrict__ w_pdraft, float *__restrict__ w_Fd,
                                 float *__restrict__ w_Fraw, uint4 *__restrict__ w_fix, float *__restrict__ w_dEdX,
-                                WinHdr *__restrict__ hdr, double *__restrict__ w_logu, int redraft) {
+                                WinHdr *__restrict__ hdr, int redraft) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N;
     const int C = gridDim.x, c = blockIdx.x;
@@ -669,10 +669,6 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
         // its own global writes, and sF is rewritten only after the next cluster
         // barrier: no CTA barrier is needed here
     }
-    // log u of the acceptance test of every drafted step (one FP64 log each),
-    // here rather than on the verification's critical path
-    if (c == 0)
-        for (int t = tid; t < keff; t += blockDim.x) w_logu[t] = log(uniform53(cf.seed, (unsigned long long)(n0 + t + 1)));
     if (c == 0 && tid == 0) {
         if (hdr) {
             hdr->k_eff = keff;
@@ -730,7 +726,7 @@ DraftPlan draft_plan(int N, int K, const PotDev &P, bool learned, int vcap, bool
 cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf,
                          const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
                          const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
-                         double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX, double *w_logu,
+                         double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX,
                          cudaStream_t s, WinHdr *hdr, int redraft) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(pl.cluster, 1, 1);
@@ -754,7 +750,7 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
                         : (pl.reg ? draft_window_cluster_kernel<false, true> : draft_window_cluster_kernel<false, false>);
     return cudaLaunchKernelEx(&cfg, kern, K, g, P, cf, vl, (const int *)vb.vcount, vp.cap, (const uint4 *)vb.fix_base,
                               vp.move2f, vp.rlist2f, stage, mi, ns, sl, self, species, q, p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd,
-                              w_Fraw, w_fix, w_dEdX, hdr, w_logu, redraft);
+                              w_Fraw, w_fix, w_dEdX, hdr, redraft);
 }
 
 static const void *draft_kernel_ptrs[4] = {

@@ -104,11 +104,11 @@ void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *spe
 void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                              const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
                              int ec_on, double *q, double *p, double *p_obabo, DevState *st,
-                             const double2 *partials, const double *logu, cudaStream_t s);
+                             const double2 *partials, cudaStream_t s);
 void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                       const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
                       int ec_on, double *q, double *p, double *p_obabo, DevState *st, double2 *partials,
-                      const double *logu, cudaStream_t s);
+                      cudaStream_t s);
 
 // draft and plain integrator (lsd_draft.cu)
 struct DraftPlan {
@@ -129,7 +129,7 @@ int draft_max_cluster(size_t smem, bool learned);
 cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf,
                          const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
                          const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
-                         double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX, double *w_logu,
+                         double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX,
                          cudaStream_t s, WinHdr *hdr = nullptr, int redraft = 0);
 // the pipelined window loop (lsd_draft.cu)
 void launch_spec_base(const Geo &g, const Coef &cf, const int *species, const double *qmid_b, const double *pdraft_b,

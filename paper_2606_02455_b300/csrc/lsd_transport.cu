@@ -12,8 +12,9 @@
 //   z.delta and delta.delta, written to a fixed slot (no atomics).  An atom's
 //   three-term products and a warp's 32 atoms are summed in FP32 (the FP32
 //   forces bound delta's accuracy anyway); warps, chunks and the log ratio
-//   are FP64.  log u comes from the draft (one FP64 log per step, computed
-//   off this critical path).
+//   are FP64.  log u (one FP64 log per step) is formed by the deciding
+//   kernel itself; the cooperative form does it before its wait on the force
+//   gather, so it overlaps the gather.
 // transport_commit_kernel: every CTA sums the partials in the same fixed
 //   order, finds l = first rejected step, and commits its slice of atoms:
 //   the draft's own bits for an accepted step, the reflection for a rejected
@@ -53,10 +54,18 @@ struct CommitShared {
     double factor;   // 2 z.delta / delta.delta of the committed step when it was rejected
 };
 
+// log u of the acceptance test of window steps 0..K-1 (one FP64 log each),
+// into C.lu, by thread j % blockDim.x -- the thread that reads it in
+// commit_decide, so no barrier is needed in between.
+__device__ __forceinline__ void logu_fill(CommitShared &C, const Coef &cf, long long n0, int K) {
+    for (int j = threadIdx.x; j < K; j += blockDim.x) C.lu[j] = log(uniform53(cf.seed, (unsigned long long)(n0 + j + 1)));
+}
+
 // Sums the partials of every window step in a fixed order, forms log r and
-// the accept flags, and finds l = the first rejected step (all threads).
+// the accept flags (against C.lu, filled by logu_fill), and finds l = the
+// first rejected step (all threads).
 __device__ void commit_decide(CommitShared &C, int K, const double2 *__restrict__ partials, int n_part,
-                              const double *__restrict__ logu, long long rem) {
+                              long long rem) {
     for (int j = threadIdx.x; j < K; j += blockDim.x) {
         double s = 0.0, d = 0.0;
         for (int b = 0; b < n_part; ++b) {
@@ -67,9 +76,8 @@ __device__ void commit_decide(CommitShared &C, int K, const double2 *__restrict_
         C.s[j] = s;
         C.d[j] = d;
         const double lr = -s - 0.5 * d;
-        const double lu = __ldcg(logu + j);
+        const double lu = C.lu[j];
         C.lr[j] = lr;
-        C.lu[j] = lu;
         C.acc[j] = (d == 0.0) || (lu <= fmin(0.0, lr));
         C.fin[j] = isfinite(lr);
     }
@@ -181,7 +189,7 @@ __device__ void commit_stats(CommitShared &C, int K, DevState *__restrict__ st, 
 __global__ void __launch_bounds__(kTransThreads)
     transport_reduce_kernel(int K, Geo g, Coef cf, const int *__restrict__ species, const float *__restrict__ Fd,
                             const float *__restrict__ Ft, DevState *__restrict__ st, double2 *__restrict__ partials,
-                            const double *__restrict__ logu, int atoms_per_block, int fused,
+                            int atoms_per_block, int fused,
                             const double *__restrict__ w_qmid, const double *__restrict__ w_pdraft,
                             const float *__restrict__ Fraw, float *__restrict__ ec_dF, int ec_on,
                             double *__restrict__ q, double *__restrict__ p, double *__restrict__ p_obabo) {
@@ -221,7 +229,8 @@ __global__ void __launch_bounds__(kTransThreads)
     __threadfence();
     const long long n0 = st->step;
     const int Kw = min(K, keff);
-    commit_decide(C, Kw, partials, gridDim.x, logu, st->target_step - n0);
+    logu_fill(C, cf, n0, Kw);
+    commit_decide(C, Kw, partials, gridDim.x, st->target_step - n0);
     commit_atoms(C, N, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, n0, 0, N);
     __syncthreads();
     if (threadIdx.x == 0) st->blocks_done = 0u;
@@ -264,15 +273,16 @@ __device__ bool grid_sync_bounded(unsigned long long *ctr, unsigned total) {
 __global__ void __launch_bounds__(kTransThreads)
     transport_coop_kernel(int K, Geo g, Coef cf, const int *__restrict__ species, const float *__restrict__ Fd,
                           const float *__restrict__ Ft, DevState *__restrict__ st, double2 *__restrict__ partials,
-                          const double *__restrict__ logu, int atoms_per_block, const double *__restrict__ w_qmid,
+                          int atoms_per_block, const double *__restrict__ w_qmid,
                           const double *__restrict__ w_pdraft, const float *__restrict__ Fraw,
                           float *__restrict__ ec_dF, int ec_on, double *__restrict__ q, double *__restrict__ p,
                           double *__restrict__ p_obabo) {
     __shared__ double2 sh[32];
     __shared__ CommitShared C;
-    // The run state, log u and the draft's forces and noise come from kernels
-    // that finished before the force gather began: read and drawn before the
-    // wait (block 0 rewrites the run state only after the grid barrier).
+    // The run state and the draft's forces and noise come from kernels that
+    // finished before the force gather began: read and drawn (with log u)
+    // before the wait (block 0 rewrites the run state only after the grid
+    // barrier).
     pdl_release();
     const volatile DevState *vs = st;
     const long long n0 = vs->step, tgt = vs->target_step;
@@ -297,6 +307,8 @@ __global__ void __launch_bounds__(kTransThreads)
             fd[u] = make_float3(Fd[o + 0], Fd[o + 1], Fd[o + 2]);
         }
     }
+    // log u of every step (a long FP64 chain per thread), while the force gather finishes
+    logu_fill(C, cf, n0, min(K, keff));
     pdl_wait();   // the target forces
     float s = 0.f, d = 0.f;
 #pragma unroll
@@ -318,7 +330,7 @@ __global__ void __launch_bounds__(kTransThreads)
         return;
     }
     const int Kw = min(K, keff);
-    commit_decide(C, Kw, partials, nb, logu, tgt - n0);
+    commit_decide(C, Kw, partials, nb, tgt - n0);
     const int nblk = nb * gridDim.y, blk = blockIdx.y * nb + blockIdx.x;
     const int A = (N + nblk - 1) / nblk;
     commit_atoms(C, N, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, n0, blk * A,
@@ -332,7 +344,7 @@ __global__ void __launch_bounds__(kTransThreads)
                             const float *__restrict__ Ft, const float *__restrict__ Fraw, float *__restrict__ ec_dF,
                             int ec_on, double *__restrict__ q, double *__restrict__ p,
                             double *__restrict__ p_obabo, DevState *__restrict__ st,
-                            const double2 *__restrict__ partials, const double *__restrict__ logu, int n_part,
+                            const double2 *__restrict__ partials, int n_part,
                             int atoms_per_block) {
     __shared__ CommitShared C;
     __shared__ bool s_last;
@@ -341,7 +353,8 @@ __global__ void __launch_bounds__(kTransThreads)
     if (st->step >= st->target_step) return;
     K = min(K, st->k_eff);   // the window holds the k_eff steps the draft reached
     const long long n0 = st->step;
-    commit_decide(C, K, partials, n_part, logu, st->target_step - n0);
+    logu_fill(C, cf, n0, K);
+    commit_decide(C, K, partials, n_part, st->target_step - n0);
     const int a0 = blockIdx.x * atoms_per_block;
     commit_atoms(C, g.N, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, n0, a0,
                  min(g.N, a0 + atoms_per_block));
@@ -360,18 +373,18 @@ void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *spe
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
     launch_dependent(transport_reduce_kernel, dim3(nb, K), kTransThreads, 0, s, K, g, cf, species, Fd, Ft, st, partials,
-                     (const double *)nullptr, apb, 0, (const double *)nullptr, (const double *)nullptr, (const float *)nullptr,
+                     apb, 0, (const double *)nullptr, (const double *)nullptr, (const float *)nullptr,
                      (float *)nullptr, 0, (double *)nullptr, (double *)nullptr, (double *)nullptr);
 }
 
 void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                              const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
                              int ec_on, double *q, double *p, double *p_obabo, DevState *st,
-                             const double2 *partials, const double *logu, cudaStream_t s) {
+                             const double2 *partials, cudaStream_t s) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
     launch_dependent(transport_commit_kernel, nb, kTransThreads, 0, s, K, g, cf, species, w_qmid, w_pdraft, Fd, Ft,
-                     Fraw, ec_dF, ec_on, q, p, p_obabo, st, (const double2 *)partials, (const double *)logu, nb, apb);
+                     Fraw, ec_dF, ec_on, q, p, p_obabo, st, (const double2 *)partials, nb, apb);
 }
 
 static int g_coop_blocks = -1;   // blocks of transport_coop_kernel the device keeps resident at once
@@ -390,7 +403,7 @@ cudaError_t transport_setup() {
 void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                       const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
                       int ec_on, double *q, double *p, double *p_obabo, DevState *st, double2 *partials,
-                      const double *logu, cudaStream_t s) {
+                      cudaStream_t s) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
     if (apb <= 4 * kTransThreads && nb * K <= g_coop_blocks) {   // four atoms per thread at most
@@ -405,18 +418,18 @@ void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, c
         at[1].val.cooperative = 1;
         cfg.attrs = at;
         cfg.numAttrs = 2;
-        cudaLaunchKernelEx(&cfg, transport_coop_kernel, K, g, cf, species, Fd, Ft, st, partials, logu, apb, w_qmid,
+        cudaLaunchKernelEx(&cfg, transport_coop_kernel, K, g, cf, species, Fd, Ft, st, partials, apb, w_qmid,
                            w_pdraft, Fraw, ec_dF, ec_on, q, p, p_obabo);
         return;
     }
     if (nb == 1) {
         launch_dependent(transport_reduce_kernel, dim3(1, K), kTransThreads, 0, s, K, g, cf, species, Fd, Ft, st,
-                         partials, logu, apb, 1, w_qmid, w_pdraft, Fraw, ec_dF, ec_on, q, p, p_obabo);
+                         partials, apb, 1, w_qmid, w_pdraft, Fraw, ec_dF, ec_on, q, p, p_obabo);
         return;
     }
     launch_transport_reduce(K, g, cf, species, Fd, Ft, st, partials, s);
     launch_transport_commit(K, g, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, st,
-                            partials, logu, s);
+                            partials, s);
 }
 
 int transport_atoms_per_block(int N) {
