@@ -281,14 +281,23 @@ __global__ void desc_kernel(const uint4 *__restrict__ fix, const int *__restrict
                 a[14] += 0.0078125f * bm8 * E1; a[15] += 0.0078125f * bm8 * E2;
             }
         }
+        // the sixteen warp sums as one reduce-scatter: at offsets 16, 8, 4, 2
+        // each lane keeps the half of its partial sums its offset bit selects
+        // and adds the partner's partials of that half; lanes 2f and 2f+1 end
+        // with the total of feature f (62 shuffles and adds instead of 160)
+        static_assert(kNAng == 16, "the reduce-scatter is laid out for 16 features");
 #pragma unroll
-        for (int t = 0; t < kNAng; ++t) a[t] = warp_sum(a[t]);
-        if (lane < kNAng) {
-            float v = 0.f;
+        for (int m = kNAng; m > 1; m >>= 1) {
+            const bool up = (lane & (m == 16 ? 16 : m == 8 ? 8 : m == 4 ? 4 : 2)) != 0;
+            const int o = m == 16 ? 16 : m == 8 ? 8 : m == 4 ? 4 : 2;
 #pragma unroll
-            for (int t = 0; t < kNAng; ++t) v = (lane == t) ? a[t] : v;
-            x[g.S * nr + lane] = v;
+            for (int t = 0; t < m / 2; ++t) {
+                const float keep = up ? a[t + m / 2] : a[t], send = up ? a[t] : a[t + m / 2];
+                a[t] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
         }
+        a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+        if ((lane & 1) == 0) x[g.S * nr + (lane >> 1)] = a[0];
     }
     // one-hot and padding
     const int off = g.S * nr + P.n_ang;
