@@ -7,19 +7,23 @@
 // The K steps are inherently serial; within a step the force evaluation is
 // parallel over atoms.  The whole window therefore runs in ONE launch of a
 // thread-block cluster (up to 16 CTAs, one per SM): each CTA owns a slice of
-// the atoms, writes their half-step fixed-point positions to global memory,
-// and a hardware cluster barrier (release/acquire at cluster scope, no spin
-// loop) makes every CTA see all positions before forces are evaluated.
+// the atoms and writes their half-step fixed-point positions to global memory
+// (for the verification) and, when all N fit, into every CTA's shared memory
+// by asynchronous stores that complete bytes on the receiving CTA's mbarrier;
+// each CTA waits until the step's N positions have landed (bounded wait).
+// Larger systems use a cluster barrier and read the positions through L2.
 //
-// Candidates come from the window's Verlet lists (lsd_verlet.cu: cutoff +
-// skin around the base positions).  At every step each CTA checks its atoms'
+// Candidates come from Verlet lists (cutoff + skin around a base): the
+// window's lists from lsd_verlet.cu on a cell grid of three or more cells per
+// axis, else lists each CTA builds for its own atoms at launch from one scan
+// over all atoms (no cell grid).  At every step each CTA checks its atoms'
 // displacement from the base; if any atom moved more than 0.45 skin the whole
 // cluster stops drafting at that step (k_eff < K, decided identically in every
-// CTA from flags read after the barrier), because the lists are no longer
-// guaranteed complete.  Each list entry is tested with the exact membership
-// rule, so the interacting set is the rule's set, not an approximation.  When
-// the cell grid is narrower than three cells every atom is a candidate: no
-// lists, no displacement check, k_eff = K.
+// CTA from the exchanged flags), because the lists are no longer guaranteed
+// complete.  Each list entry is tested with the exact membership rule, so the
+// interacting set is the rule's set, not an approximation.  When neither kind
+// of list fits in shared memory every atom is a candidate: no lists, no
+// displacement check, k_eff = K.
 //
 // FP64 only for the state updates, with explicit round-to-nearest intrinsics
 // so the half-step positions are reproducible bit for bit.
