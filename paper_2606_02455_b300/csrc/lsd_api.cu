@@ -408,13 +408,14 @@ void enqueue_mlp(lsd_handle *h, const PotHost &pot, int M, cudaStream_t s) {
 // With use_list the candidates are the window's Verlet lists (the window and
 // plain-step paths); otherwise all atoms (explicit configurations).
 void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, float *F, float *E_out,
-                  cudaStream_t s, bool use_list = false, const VerletBufs *vb = nullptr) {
+                  cudaStream_t s, bool use_list = false, const VerletBufs *vb = nullptr, const int *keff = nullptr) {
     const int M = Kc * h->N;
     const PotDev &P = pot.dev;
     if (!vb) vb = &h->vbufs;
+    if (!keff) keff = &h->st->k_eff;
     if (use_list)
         launch_neigh_list(fix, vb->vlist, vb->vcount, h->vplan.cap, M, h->geo, pot.rmax2f, pot.near2f,
-                          h->cap_near, h->cap_far, h->near_keys, h->far_keys, h->n_near, h->n_far, h->st, s);
+                          h->cap_near, h->cap_far, h->near_keys, h->far_keys, h->n_near, h->n_far, h->st, keff, s);
     else
         launch_neigh_build(fix, M, h->geo, pot.rmax2f, pot.near2f, h->cap_near, h->cap_far, h->near_keys,
                            h->far_keys, h->n_near, h->n_far, h->st, s);
@@ -445,17 +446,18 @@ void enqueue_draft_buf(lsd_handle *h, int b, cudaStream_t s, WinHdr *hdr, const 
                  redraft ? 1 : 0);
 }
 
-// Verification, frames and transport of window buffer b.
-void enqueue_verify_buf(lsd_handle *h, int b, cudaStream_t s) {
+// Verification, frames and transport of window buffer b; keff: the window's
+// drafted step count (its header in a pipelined round, else the run state's).
+void enqueue_verify_buf(lsd_handle *h, int b, cudaStream_t s, const int *keff) {
     lsd_handle::WinBufs &w = h->wb[b];
-    enqueue_eval(h, h->target, w.fix, h->K, h->w_Ft, nullptr, s, !h->vplan.all_pairs, &w.vb);
-    if (h->train.capture_on) enqueue_frame_capture(h->train, w.qmid, h->w_Ft, h->K, h->N, h->st, s);
+    enqueue_eval(h, h->target, w.fix, h->K, h->w_Ft, nullptr, s, !h->vplan.all_pairs, &w.vb, keff);
+    if (h->train.capture_on) enqueue_frame_capture(h->train, w.qmid, h->w_Ft, h->K, h->N, h->st, keff, s);
     launch_transport(h->K, h->geo, h->coef, h->species, w.qmid, w.pdraft, w.Fd, h->w_Ft, w.Fraw, h->ec_dF, h->ec_on,
-                     h->q, h->p, h->p_obabo, h->st, h->partials, s);
+                     h->q, h->p, h->p_obabo, h->st, h->partials, keff, s);
 }
 
 void enqueue_draft(lsd_handle *h, cudaStream_t s) { enqueue_draft_buf(h, 0, s, nullptr, h->q, h->p); }
-void enqueue_verify(lsd_handle *h, cudaStream_t s) { enqueue_verify_buf(h, 0, s); }
+void enqueue_verify(lsd_handle *h, cudaStream_t s) { enqueue_verify_buf(h, 0, s, &h->st->k_eff); }
 
 // One round of the pipelined loop: verify window b on the main stream while
 // the draft stream drafts window b^1 speculatively; then keep or redraft b^1.
@@ -464,8 +466,7 @@ void enqueue_round(lsd_handle *h, int b) {
     const int n = b ^ 1;
     cudaEventRecord(h->ev_fork, V);
     cudaStreamWaitEvent(D, h->ev_fork, 0);
-    launch_window_begin(&h->hdr[b], h->st, V);
-    enqueue_verify_buf(h, b, V);
+    enqueue_verify_buf(h, b, V, &h->hdr[b].k_eff);
     launch_spec_base(h->geo, h->coef, h->species, h->wb[b].qmid, h->wb[b].pdraft, &h->hdr[b], &h->hdr[n], h->qb,
                      h->pb, D);
     enqueue_draft_buf(h, n, D, &h->hdr[n], h->qb, h->pb);
@@ -1279,7 +1280,7 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
     else
         launch_neigh_list(h->w_fix, h->vbufs.vlist, h->vbufs.vcount, h->vplan.cap, M, h->geo, h->target.rmax2f,
                           h->target.near2f, h->cap_near, h->cap_far, h->near_keys, h->far_keys, h->n_near, h->n_far,
-                          h->st, st);
+                          h->st, &h->st->k_eff, st);
     CK(cudaEventRecord(ev[2], st));
     if (P.has_mlp) launch_desc(h->w_fix, h->near_keys, h->n_near, h->cap_near, M, h->geo, P, h->X, st);
     CK(cudaEventRecord(ev[3], st));
@@ -1291,10 +1292,10 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
     launch_force_gather(h->near_keys, h->n_near, h->cap_near, M, h->N, P.has_mlp, h->pair_g, h->Fpart, h->E_lj,
                         h->E_mlp, h->w_Ft, nullptr, h->st, st);
     CK(cudaEventRecord(ev[6], st));
-    launch_transport_reduce(h->K, h->geo, h->coef, h->species, h->w_Fd, h->w_Ft, h->st, h->partials, st);
+    launch_transport_reduce(h->K, h->geo, h->coef, h->species, h->w_Fd, h->w_Ft, h->st, h->partials, &h->st->k_eff, st);
     CK(cudaEventRecord(ev[7], st));
     launch_transport_commit(h->K, h->geo, h->coef, h->species, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Ft, h->w_Fraw,
-                            h->ec_dF, h->ec_on, h->q, h->p, h->p_obabo, h->st, h->partials, st);
+                            h->ec_dF, h->ec_on, h->q, h->p, h->p_obabo, h->st, h->partials, &h->st->k_eff, st);
     CK(cudaEventRecord(ev[8], st));
     CK(cudaGetLastError());
     TRY(wait_stream(h));
@@ -1342,8 +1343,8 @@ int lsd_launch_counts(const lsd_handle *h, int32_t *per_window, int32_t *per_rou
     const int verify = eval + (h->train.capture_on ? 1 : 0) + transport;
     const int draft = verlet + 1;
     if (per_window) *per_window = draft + verify;
-    // window_begin; verify; spec_base; speculative draft; redraft (with its flag kernel in list mode)
-    if (per_round) *per_round = 1 + verify + 1 + draft + (lists ? 1 : 0) + draft;
+    // verify; spec_base; speculative draft; redraft (with its flag kernel in list mode)
+    if (per_round) *per_round = verify + 1 + draft + (lists ? 1 : 0) + draft;
     if (per_plain) *per_plain = verlet + 1 + eval + 1;
     return LSD_OK;
 }

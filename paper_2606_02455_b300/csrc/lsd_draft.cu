@@ -833,9 +833,6 @@ __global__ void redraft_flag_kernel(const DevState *__restrict__ st, WinHdr *__r
     hn->keep = spec_is_valid(hn, st) ? 1 : 0;
 }
 
-// The verification of window b reads its k_eff through the run state.
-__global__ void window_begin_kernel(const WinHdr *__restrict__ hb, DevState *__restrict__ st) { st->k_eff = hb->k_eff; }
-
 __global__ void hdr_invalidate_kernel(WinHdr *__restrict__ h) {
     h->base = -1;
     h->skip = 1;
@@ -849,7 +846,6 @@ void launch_spec_base(const Geo &g, const Coef &cf, const int *species, const do
 
 void launch_redraft_flag(const DevState *st, WinHdr *hn, cudaStream_t s) { redraft_flag_kernel<<<1, 1, 0, s>>>(st, hn); }
 
-void launch_window_begin(const WinHdr *hb, DevState *st, cudaStream_t s) { window_begin_kernel<<<1, 1, 0, s>>>(hb, st); }
 
 void launch_hdr_invalidate(WinHdr *h, cudaStream_t s) { hdr_invalidate_kernel<<<1, 1, 0, s>>>(h); }
 

@@ -66,7 +66,7 @@ void launch_verlet_build(const VerletPlan &vp, const double *q, const int *speci
 cudaError_t verlet_setup(int max_smem);
 void launch_neigh_list(const uint4 *fix, const int *vlist, const int *vcount, int vcap, int M, const Geo &g,
                        float rmax2f, float near2f, int cap_near, int cap_far, int *near_keys, int *far_keys,
-                       int *n_near, int *n_far, DevState *st, cudaStream_t s);
+                       int *n_near, int *n_far, DevState *st, const int *keff, cudaStream_t s);
 
 // MLP (lsd_mlp.cu)
 void launch_mlp_fp32(const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX, cudaStream_t s);
@@ -99,16 +99,18 @@ int mlp_tc_static_launch(const void *plan, const float *X, int M, const PotDev &
 // transport (lsd_transport.cu)
 int transport_atoms_per_block(int N);
 cudaError_t transport_setup();
+// keff: the window's drafted step count (the run state's, or the window
+// header's in a pipelined round).
 void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *species, const float *Fd,
-                             const float *Ft, DevState *st, double2 *partials, cudaStream_t s);
+                             const float *Ft, DevState *st, double2 *partials, const int *keff, cudaStream_t s);
 void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                              const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
                              int ec_on, double *q, double *p, double *p_obabo, DevState *st,
-                             const double2 *partials, cudaStream_t s);
+                             const double2 *partials, const int *keff, cudaStream_t s);
 void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                       const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
                       int ec_on, double *q, double *p, double *p_obabo, DevState *st, double2 *partials,
-                      cudaStream_t s);
+                      const int *keff, cudaStream_t s);
 
 // draft and plain integrator (lsd_draft.cu)
 struct DraftPlan {
@@ -135,7 +137,6 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
 void launch_spec_base(const Geo &g, const Coef &cf, const int *species, const double *qmid_b, const double *pdraft_b,
                       const WinHdr *hb, WinHdr *hn, double *qb, double *pb, cudaStream_t s);
 void launch_redraft_flag(const DevState *st, WinHdr *hn, cudaStream_t s);
-void launch_window_begin(const WinHdr *hb, DevState *st, cudaStream_t s);
 void launch_hdr_invalidate(WinHdr *h, cudaStream_t s);
 cudaError_t draft_kernels_setup(int max_smem);
 void launch_plain_half(const Geo &g, const Coef &cf, const int *species, const double *q, const double *p,

@@ -310,10 +310,10 @@ __global__ void adam_kernel(float *__restrict__ w, float *__restrict__ m, float 
 
 __global__ void frame_capture_kernel(const double *__restrict__ w_qmid, const float *__restrict__ w_Ft, int K, int N,
                                      long long cap, long long start_verified, const DevState *__restrict__ st,
-                                     double *__restrict__ fq, float *__restrict__ fF) {
+                                     const int *__restrict__ keff, double *__restrict__ fq, float *__restrict__ fF) {
     if (st->step >= st->target_step) return;
     const int j = blockIdx.y;
-    if (j >= st->k_eff) return;   // steps the draft did not reach carry no target label
+    if (j >= *keff) return;   // steps the draft did not reach carry no target label
     // frames are numbered by verified window steps (the commit kernel adds k_eff afterwards)
     const long long slot = (st->verified - start_verified + j) % cap;
     const int D = 3 * N;
@@ -426,12 +426,13 @@ int train_frame_count(TrainState &t, int64_t *n, cudaStream_t s) {
 }
 
 void enqueue_frame_capture(TrainState &t, const double *w_qmid, const float *w_Ft, int K, int N, DevState *st,
-                           cudaStream_t s) {
+                           const int *keff, cudaStream_t s) {
     t.K = K;
     t.st = st;
     const int D = 3 * N;
     const int bx = (D + 255) / 256 < 64 ? (D + 255) / 256 : 64;
-    frame_capture_kernel<<<dim3(bx, K), 256, 0, s>>>(w_qmid, w_Ft, K, N, t.capacity, t.start_verified, st, t.fq, t.fF);
+    frame_capture_kernel<<<dim3(bx, K), 256, 0, s>>>(w_qmid, w_Ft, K, N, t.capacity, t.start_verified, st, keff, t.fq,
+                                                     t.fF);
 }
 
 size_t train_adam_size(const TrainState &t) { return t.enabled ? t.n_weights : 0; }

@@ -39,7 +39,7 @@ int train_get_weights(TrainState &t, std::vector<float> &w, cudaStream_t s);
 int train_set_capture(TrainState &t, long long capacity, int N);
 int train_frame_count(TrainState &t, int64_t *n, cudaStream_t s);
 void enqueue_frame_capture(TrainState &t, const double *w_qmid, const float *w_Ft, int K, int N, DevState *st,
-                           cudaStream_t s);
+                           const int *keff, cudaStream_t s);
 size_t train_adam_size(const TrainState &t);
 int train_adam_get(TrainState &t, float *m, float *v);
 int train_adam_set(TrainState &t, const float *m, const float *v);

@@ -169,6 +169,7 @@ __device__ void commit_stats(CommitShared &C, int K, DevState *__restrict__ st, 
     }
     if (threadIdx.x == 0) {
         st->n_commit_last = nc;
+        st->k_eff = K;   // the window's drafted steps (a pipelined round reads them from its header)
         st->first_reject_last = C.rej || (C.l <= K && !C.acc[C.l - 1]) ? C.l : -1;
         if (C.bad) atomicOr(&st->err, 2);
         st->windows += 1;
@@ -189,7 +190,7 @@ __device__ void commit_stats(CommitShared &C, int K, DevState *__restrict__ st, 
 __global__ void __launch_bounds__(kTransThreads)
     transport_reduce_kernel(int K, Geo g, Coef cf, const int *__restrict__ species, const float *__restrict__ Fd,
                             const float *__restrict__ Ft, DevState *__restrict__ st, double2 *__restrict__ partials,
-                            int atoms_per_block, int fused,
+                            const int *__restrict__ keff_p, int atoms_per_block, int fused,
                             const double *__restrict__ w_qmid, const double *__restrict__ w_pdraft,
                             const float *__restrict__ Fraw, float *__restrict__ ec_dF, int ec_on,
                             double *__restrict__ q, double *__restrict__ p, double *__restrict__ p_obabo) {
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(kTransThreads)
     if (st->step >= st->target_step) return;   // uniform over the grid
     const int N = g.N;
     const int j = blockIdx.y;
-    const int keff = st->k_eff;
+    const int keff = *keff_p;
     if (j < keff) {                            // steps the draft did not reach are skipped
         const unsigned long long n = (unsigned long long)(st->step + j + 1);
         const int a0 = blockIdx.x * atoms_per_block;
@@ -273,7 +274,7 @@ __device__ bool grid_sync_bounded(unsigned long long *ctr, unsigned total) {
 __global__ void __launch_bounds__(kTransThreads)
     transport_coop_kernel(int K, Geo g, Coef cf, const int *__restrict__ species, const float *__restrict__ Fd,
                           const float *__restrict__ Ft, DevState *__restrict__ st, double2 *__restrict__ partials,
-                          int atoms_per_block, const double *__restrict__ w_qmid,
+                          const int *__restrict__ keff_p, int atoms_per_block, const double *__restrict__ w_qmid,
                           const double *__restrict__ w_pdraft, const float *__restrict__ Fraw,
                           float *__restrict__ ec_dF, int ec_on, double *__restrict__ q, double *__restrict__ p,
                           double *__restrict__ p_obabo) {
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(kTransThreads)
     pdl_release();
     const volatile DevState *vs = st;
     const long long n0 = vs->step, tgt = vs->target_step;
-    const int keff = vs->k_eff;
+    const int keff = *(const volatile int *)keff_p;
     if (n0 >= tgt) return;   // uniform over the grid
     const int N = g.N;
     const int j = blockIdx.y, nb = gridDim.x;
@@ -344,14 +345,14 @@ __global__ void __launch_bounds__(kTransThreads)
                             const float *__restrict__ Ft, const float *__restrict__ Fraw, float *__restrict__ ec_dF,
                             int ec_on, double *__restrict__ q, double *__restrict__ p,
                             double *__restrict__ p_obabo, DevState *__restrict__ st,
-                            const double2 *__restrict__ partials, int n_part,
+                            const double2 *__restrict__ partials, const int *__restrict__ keff_p, int n_part,
                             int atoms_per_block) {
     __shared__ CommitShared C;
     __shared__ bool s_last;
     pdl_wait();
     pdl_release();
     if (st->step >= st->target_step) return;
-    K = min(K, st->k_eff);   // the window holds the k_eff steps the draft reached
+    K = min(K, *keff_p);   // the window holds the k_eff steps the draft reached
     const long long n0 = st->step;
     logu_fill(C, cf, n0, K);
     commit_decide(C, K, partials, n_part, st->target_step - n0);
@@ -369,22 +370,22 @@ __global__ void __launch_bounds__(kTransThreads)
 }
 
 void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *species, const float *Fd,
-                             const float *Ft, DevState *st, double2 *partials, cudaStream_t s) {
+                             const float *Ft, DevState *st, double2 *partials, const int *keff, cudaStream_t s) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
     launch_dependent(transport_reduce_kernel, dim3(nb, K), kTransThreads, 0, s, K, g, cf, species, Fd, Ft, st, partials,
-                     apb, 0, (const double *)nullptr, (const double *)nullptr, (const float *)nullptr,
+                     keff, apb, 0, (const double *)nullptr, (const double *)nullptr, (const float *)nullptr,
                      (float *)nullptr, 0, (double *)nullptr, (double *)nullptr, (double *)nullptr);
 }
 
 void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                              const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
                              int ec_on, double *q, double *p, double *p_obabo, DevState *st,
-                             const double2 *partials, cudaStream_t s) {
+                             const double2 *partials, const int *keff, cudaStream_t s) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
     launch_dependent(transport_commit_kernel, nb, kTransThreads, 0, s, K, g, cf, species, w_qmid, w_pdraft, Fd, Ft,
-                     Fraw, ec_dF, ec_on, q, p, p_obabo, st, (const double2 *)partials, nb, apb);
+                     Fraw, ec_dF, ec_on, q, p, p_obabo, st, (const double2 *)partials, keff, nb, apb);
 }
 
 static int g_coop_blocks = -1;   // blocks of transport_coop_kernel the device keeps resident at once
@@ -403,7 +404,7 @@ cudaError_t transport_setup() {
 void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                       const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
                       int ec_on, double *q, double *p, double *p_obabo, DevState *st, double2 *partials,
-                      cudaStream_t s) {
+                      const int *keff, cudaStream_t s) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
     if (apb <= 4 * kTransThreads && nb * K <= g_coop_blocks) {   // four atoms per thread at most
@@ -418,18 +419,18 @@ void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, c
         at[1].val.cooperative = 1;
         cfg.attrs = at;
         cfg.numAttrs = 2;
-        cudaLaunchKernelEx(&cfg, transport_coop_kernel, K, g, cf, species, Fd, Ft, st, partials, apb, w_qmid,
+        cudaLaunchKernelEx(&cfg, transport_coop_kernel, K, g, cf, species, Fd, Ft, st, partials, keff, apb, w_qmid,
                            w_pdraft, Fraw, ec_dF, ec_on, q, p, p_obabo);
         return;
     }
     if (nb == 1) {
         launch_dependent(transport_reduce_kernel, dim3(1, K), kTransThreads, 0, s, K, g, cf, species, Fd, Ft, st,
-                         partials, apb, 1, w_qmid, w_pdraft, Fraw, ec_dF, ec_on, q, p, p_obabo);
+                         partials, keff, apb, 1, w_qmid, w_pdraft, Fraw, ec_dF, ec_on, q, p, p_obabo);
         return;
     }
-    launch_transport_reduce(K, g, cf, species, Fd, Ft, st, partials, s);
+    launch_transport_reduce(K, g, cf, species, Fd, Ft, st, partials, keff, s);
     launch_transport_commit(K, g, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, st,
-                            partials, s);
+                            partials, keff, s);
 }
 
 int transport_atoms_per_block(int N) {

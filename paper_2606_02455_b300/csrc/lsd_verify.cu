@@ -35,7 +35,8 @@ template <bool LIST, bool MINIMG>
 __global__ void neigh_build_kernel(const uint4 *__restrict__ fix, const int *__restrict__ vlist,
                                    const int *__restrict__ vcount, int vcap, int M, Geo g, float rmax2f, float near2f,
                                    int cap_near, int cap_far, int *__restrict__ near_keys, int *__restrict__ far_keys,
-                                   int *__restrict__ n_near, int *__restrict__ n_far, DevState *st) {
+                                   int *__restrict__ n_near, int *__restrict__ n_far, DevState *st,
+                                   const int *__restrict__ keff) {
     pdl_wait();
     pdl_release();
     const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
@@ -43,7 +44,7 @@ __global__ void neigh_build_kernel(const uint4 *__restrict__ fix, const int *__r
     if (row >= M) return;
     const int N = g.N;
     const int j = row / N, i = row - j * N;
-    if (LIST && j >= st->k_eff) {
+    if (LIST && j >= *keff) {
         if (lane == 0) {
             n_near[row] = 0;
             n_far[row] = 0;
@@ -602,17 +603,17 @@ void launch_neigh_build(const uint4 *fix, int M, const Geo &g, float rmax2f, flo
     const int blocks = (int)(((size_t)M * 32 + threads - 1) / threads);
     auto k = min_image_only(g, rmax2f) ? neigh_build_kernel<false, true> : neigh_build_kernel<false, false>;
     launch_dependent(k, blocks, threads, 0, s, fix, nullptr, nullptr, 0, M, g, rmax2f, near2f, cap_near, cap_far,
-                     near_keys, far_keys, n_near, n_far, st);
+                     near_keys, far_keys, n_near, n_far, st, (const int *)nullptr);
 }
 
 void launch_neigh_list(const uint4 *fix, const int *vlist, const int *vcount, int vcap, int M, const Geo &g,
                        float rmax2f, float near2f, int cap_near, int cap_far, int *near_keys, int *far_keys,
-                       int *n_near, int *n_far, DevState *st, cudaStream_t s) {
+                       int *n_near, int *n_far, DevState *st, const int *keff, cudaStream_t s) {
     const int threads = 256;
     const int blocks = (int)(((size_t)M * 32 + threads - 1) / threads);
     auto k = min_image_only(g, rmax2f) ? neigh_build_kernel<true, true> : neigh_build_kernel<true, false>;
     launch_dependent(k, blocks, threads, 0, s, fix, vlist, vcount, vcap, M, g, rmax2f, near2f, cap_near, cap_far,
-                     near_keys, far_keys, n_near, n_far, st);
+                     near_keys, far_keys, n_near, n_far, st, keff);
 }
 
 size_t desc_smem_bytes(int warps, int cap) { return (size_t)warps * kStageFloats * cap * sizeof(float); }

@@ -97,11 +97,11 @@ def test_launch_counts_follow_the_configuration():
     from paper_2606_02455_b300 import lsd
     w = W.config2()
     h = lsd.LSD(w.system, w.draft, w.target, w.integ)
-    assert h.launch_counts() == dict(window=7, round=10, plain=7)
+    assert h.launch_counts() == dict(window=7, round=9, plain=7)
     h.close()
     w = W.config4()
     h = lsd.LSD(w.system, w.draft, w.target, w.integ)
-    assert h.launch_counts() == dict(window=12, round=20, plain=11)
+    assert h.launch_counts() == dict(window=12, round=19, plain=11)
     h.close()
 
 
