@@ -174,6 +174,27 @@ LSD_API int lsd_draft_window(lsd_handle *h);
  * -1.  Synchronises the stream.  LSD_ESTATE without a preceding draft. */
 LSD_API int lsd_verify_window(lsd_handle *h, int32_t *n_committed, int32_t *first_reject);
 
+/* lsd_transport_window: reflectionVerify (Eq. 5) and the commit of Alg. 1 on
+ * a window given as arrays, with no draft and no target evaluation: the
+ * transport step of Alg. 2 verify_step on its own.  From the current state
+ * (q, p, step n0) and k <= K window steps (host buffers, [k][N][3]):
+ *   q_mid    double  half-step positions A(q) of each drafted step
+ *   p_draft  double  drafted momenta p'_j (p'_{j-1} is step j's input momentum)
+ *   F_draft  float   draft forces F~_j at q_mid_j (eV/A; also the raw forces
+ *                    of the error-correction cache)
+ *   F_target float   target forces F_j at q_mid_j (eV/A)
+ * z_j is the draft noise xi_{n0+j} regenerated from its counter; delta_j =
+ * (1+c1)(dt/2) kappa (F~_j - F_j)/sigma; log r_j = -z.delta - |delta|^2/2 in
+ * FP64; step j is accepted iff log u_{n0+j} <= min(0, log r_j).  Steps up to
+ * and including the first rejected one are committed (the rejected one as
+ * the reflection <p> + sigma (z - 2 (z.delta/delta.delta) delta), position
+ * q_mid + (dt/2) p/m).  lsd_get_window then returns the arrays, log ratios,
+ * log u and flags.  Outputs as lsd_verify_window.  Copies the inputs;
+ * synchronises the stream.  LSD_EINVAL for NULL arrays or k outside
+ * [1, K]. */
+LSD_API int lsd_transport_window(lsd_handle *h, const double *q_mid, const double *p_draft, const float *F_draft,
+                                 const float *F_target, int32_t k, int32_t *n_committed, int32_t *first_reject);
+
 /* lsd_step: runs windows (draft + verify + commit, captured as one CUDA graph)
  * until n_steps more steps are committed; the final window commits only what
  * is needed.  stats (may be NULL) receives the cumulative counters. */
@@ -255,6 +276,16 @@ LSD_API int lsd_set_pipelining(lsd_handle *h, int32_t on);
 #define LSD_OBABO 1
 LSD_API int lsd_set_integrator(lsd_handle *h, int32_t scheme);
 
+/* lsd_set_max_displacement: the draft stops a window early, at the first
+ * step at which some atom lies more than d_max Angstrom from the position its
+ * candidate lists were built around (a stopping time: the decision depends
+ * only on noise already drawn, so committed steps keep the target law).  The
+ * window then verifies k_eff < K steps.  The library's own bound is 0.45
+ * times the list skin (beyond it the lists could miss a pair); d_max is
+ * clamped to it, and d_max = 0 restores it.  LSD_EUNSUPPORTED when the draft
+ * uses no candidate lists (every atom a candidate: no displacement check). */
+LSD_API int lsd_set_max_displacement(lsd_handle *h, double d_max);
+
 /* lsd_set_error_correction: speculative error correction (Alg. 3) on (1) or
  * off (0).  On: the draft mean uses F~ + dF, where dF = F - F~raw of the last
  * committed step; switching on clears dF. */
@@ -265,6 +296,14 @@ LSD_API int lsd_set_error_correction(lsd_handle *h, int32_t on);
  * lsd_train_draft; capacity 0 turns capture off. */
 LSD_API int lsd_set_frame_capture(lsd_handle *h, int64_t capacity);
 LSD_API int lsd_frame_count(const lsd_handle *h, int64_t *n_frames);
+
+/* lsd_get_frames: host copies of captured frames first .. first+count-1,
+ * numbered in capture order from 0 (a window's verified steps in step order):
+ * q [count][N][3] double half-step positions q_mid_j, F [count][N][3] float
+ * target forces at them (either pointer may be NULL).  Only the most recent
+ * `capacity` frames are held: LSD_EINVAL for a range outside them,
+ * LSD_ESTATE when capture is off.  Synchronises the stream. */
+LSD_API int lsd_get_frames(lsd_handle *h, int64_t first, int64_t count, double *q, float *F);
 
 /* lsd_train_draft: n_iters Adam steps (learning rate lr) of force matching of a
  * LSD_POT_LEARNED draft on the captured frames: loss = mean over frames and

@@ -776,8 +776,18 @@ static o_verdict o_reflection_verify(const o_system *sys, const o_coef *c, doubl
 
 /* Exported 1-D/generic transport for tests: given the draft momentum, both
  * means, per-component sigma and u, returns the accept flag and writes p. */
+int o_transport_terms(int32_t D, const double *sig, double u, const double *p_draft, const double *mu_draft,
+                      const double *mu_target, double *p_out, double *log_ratio, double *zdelta, double *deltadelta);
+
 int o_transport(int32_t D, const double *sig, double u, const double *p_draft, const double *mu_draft,
                 const double *mu_target, double *p_out, double *log_ratio) {
+    return o_transport_terms(D, sig, u, p_draft, mu_draft, mu_target, p_out, log_ratio, NULL, NULL);
+}
+
+/* reflectionVerify as above; also returns z.delta and delta.delta (either
+ * pointer may be NULL), the two sums Eq. 5 and Eq. 6 are built from. */
+int o_transport_terms(int32_t D, const double *sig, double u, const double *p_draft, const double *mu_draft,
+                      const double *mu_target, double *p_out, double *log_ratio, double *zdelta, double *deltadelta) {
     double lr = 0.0, zd = 0.0, dd = 0.0;
     for (int k = 0; k < D; ++k) {
         double z = (p_draft[k] - mu_draft[k]) / sig[k];
@@ -797,6 +807,8 @@ int o_transport(int32_t D, const double *sig, double u, const double *p_draft, c
         }
     }
     if (log_ratio) *log_ratio = lr;
+    if (zdelta) *zdelta = zd;
+    if (deltadelta) *deltadelta = dd;
     return acc;
 }
 

@@ -81,6 +81,7 @@ def _L():
                 "o_coefficients": (None, [P, P, P, P, P, P]),
                 "o_mb_momenta": (None, [P, P, P]),
                 "o_transport": (ctypes.c_int, [I32, P, D, P, P, P, P, P]),
+                "o_transport_terms": (ctypes.c_int, [I32, P, D, P, P, P, P, P, P, P]),
                 "o_lsd_window": (ctypes.c_int, [P, P, P, P, I64, I32, I32, P, P, P, P, P, P, P, P, P, P, P, P, P]),
                 "o_lsd_run": (ctypes.c_int, [P, P, P, P, I64, I32, I32, P, P, P, P, P, P, P]),
                 "o_plain_run": (ctypes.c_int, [P, P, P, I64, P, P, P, P, P, P]),
@@ -293,6 +294,19 @@ def transport(sig, u, p_draft, mu_draft, mu_target):
     acc = _L().o_transport(int(pd.size), _ptr(sig), float(u), _ptr(pd), _ptr(md), _ptr(mt), _ptr(out),
                            ctypes.byref(lr))
     return bool(acc), out, lr.value
+
+
+def transport_terms(sig, u, p_draft, mu_draft, mu_target):
+    """reflectionVerify (Eq. 5) on flat vectors; returns (accept, p, log_ratio, z.delta, delta.delta)."""
+    sig = np.ascontiguousarray(sig, dtype=np.float64)
+    pd = np.ascontiguousarray(p_draft, dtype=np.float64)
+    md = np.ascontiguousarray(mu_draft, dtype=np.float64)
+    mt = np.ascontiguousarray(mu_target, dtype=np.float64)
+    out = np.zeros_like(pd)
+    lr, zd, dd = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    acc = _L().o_transport_terms(int(pd.size), _ptr(sig), float(u), _ptr(pd), _ptr(md), _ptr(mt), _ptr(out),
+                                 ctypes.byref(lr), ctypes.byref(zd), ctypes.byref(dd))
+    return bool(acc), out, lr.value, zd.value, dd.value
 
 
 def lsd_window(system, draft, target, integ, seed, n0, K, q, p, ec_dF=None, max_commit=None):

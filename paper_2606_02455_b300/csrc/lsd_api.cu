@@ -113,6 +113,7 @@ struct lsd_handle {
     cudaEvent_t ev_fork = nullptr, ev_v = nullptr, ev_d = nullptr;
     cudaEvent_t ev_sync = nullptr;   // wait_stream's event, created once
     cudaGraphExec_t g_round[2] = {nullptr, nullptr};
+    float move2f_list = 0.f;   // (0.45 skin)^2: the largest displacement the lists stay complete for
     bool drafted = false;
     bool unbounded = false;   // target_step set to "no cap" by lsd_enqueue_*
     // learned-draft training
@@ -787,6 +788,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         vp.all_pairs = vp.nc[0] < 3 || vp.nc[1] < 3 || vp.nc[2] < 3;
         vp.rlist2f = (float)(rlist * rlist);
         vp.move2f = (float)((0.45 * skin) * (0.45 * skin));
+        h->move2f_list = vp.move2f;
         vp.cap = std::min(nb_capacity(rho, rlist, 32), (h->N + 31) / 32 * 32);
         vp.cap_pow2 = 32;
         while (vp.cap_pow2 < vp.cap) vp.cap_pow2 *= 2;
@@ -944,6 +946,33 @@ int lsd_verify_window(lsd_handle *h, int32_t *n_committed, int32_t *first_reject
     if (n_committed) *n_committed = s.n_commit_last;
     if (first_reject) *first_reject = s.first_reject_last;
     return check_err(s);
+}
+
+int lsd_transport_window(lsd_handle *h, const double *q_mid, const double *p_draft, const float *F_draft,
+                         const float *F_target, int32_t k, int32_t *n_committed, int32_t *first_reject) {
+    if (!h || !q_mid || !p_draft || !F_draft || !F_target || k < 1 || k > h->K) return LSD_EINVAL;
+    TRY(wait_stream(h));
+    const size_t bytes_d = (size_t)k * 3 * h->N * sizeof(double), bytes_f = (size_t)k * 3 * h->N * sizeof(float);
+    cudaStream_t s = h->stream;
+    CK(cudaMemcpyAsync(h->w_qmid, q_mid, bytes_d, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->w_pdraft, p_draft, bytes_d, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->w_Fd, F_draft, bytes_f, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->w_Fraw, F_draft, bytes_f, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->w_Ft, F_target, bytes_f, cudaMemcpyHostToDevice, s));
+    const int keff = k;
+    CK(cudaMemcpyAsync(&h->st->k_eff, &keff, sizeof(int), cudaMemcpyHostToDevice, s));
+    DevState st;
+    TRY(read_state(h, &st));
+    TRY(set_target_step(h, st.step + k));
+    h->drafted = false;
+    h->pipe_primed = false;   // window buffer 0 now holds the given window
+    launch_transport(h->K, h->geo, h->coef, h->species, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Ft, h->w_Fraw,
+                     h->ec_dF, h->ec_on, h->q, h->p, h->p_obabo, h->st, h->partials, &h->st->k_eff, s);
+    CK(cudaGetLastError());
+    TRY(read_state(h, &st));
+    if (n_committed) *n_committed = st.n_commit_last;
+    if (first_reject) *first_reject = st.first_reject_last;
+    return check_err(st);
 }
 
 int lsd_step(lsd_handle *h, int64_t n_steps, lsd_stats *stats) {
@@ -1141,6 +1170,16 @@ int lsd_set_integrator(lsd_handle *h, int32_t scheme) {
         h->coef.obabo = 0;
         TRY(wait_stream(h));
     }
+    return LSD_OK;
+}
+
+int lsd_set_max_displacement(lsd_handle *h, double d_max) {
+    if (!h || !(d_max >= 0.0)) return LSD_EINVAL;
+    if (h->vplan.all_pairs && !h->dplan.self_list) return LSD_EUNSUPPORTED;   // no lists: no displacement check
+    TRY(wait_stream(h));
+    const float m2 = d_max == 0.0 ? h->move2f_list : (float)(d_max * d_max);
+    h->vplan.move2f = std::min(m2, h->move2f_list);
+    destroy_graphs(h);   // the bound is a launch argument of the draft
     return LSD_OK;
 }
 
@@ -1458,6 +1497,11 @@ int lsd_set_frame_capture(lsd_handle *h, int64_t capacity) {
 int lsd_frame_count(const lsd_handle *h, int64_t *n) {
     if (!h || !n) return LSD_EINVAL;
     return train_frame_count(const_cast<lsd_handle *>(h)->train, n, h->stream);
+}
+
+int lsd_get_frames(lsd_handle *h, int64_t first, int64_t count, double *q, float *F) {
+    if (!h || first < 0 || count < 0) return LSD_EINVAL;
+    return train_get_frames(h->train, first, count, q, F, h->stream);
 }
 
 int lsd_train_draft(lsd_handle *h, int32_t n_iters, float lr, int32_t frames_per_iter, float *loss_out) {

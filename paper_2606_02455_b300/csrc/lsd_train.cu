@@ -425,6 +425,29 @@ int train_frame_count(TrainState &t, int64_t *n, cudaStream_t s) {
     return LSD_OK;
 }
 
+// Host copies of frames first .. first+count-1 (numbered from the start of
+// capture); only the last `capacity` frames are still in the ring.
+int train_get_frames(TrainState &t, long long first, long long count, double *q, float *F, cudaStream_t s) {
+    if (!t.capture_on || !t.st) return LSD_ESTATE;
+    DevState ds;
+    if (cudaMemcpyAsync(&ds, t.st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LSD_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LSD_ECUDA;
+    const long long total = ds.verified - t.start_verified;
+    const long long oldest = total > t.capacity ? total - t.capacity : 0;
+    if (first < oldest || first + count > total) return LSD_EINVAL;
+    const size_t D = (size_t)3 * t.N;
+    for (long long f = first; f < first + count; ++f) {
+        const size_t slot = (size_t)(f % t.capacity), r = (size_t)(f - first);
+        if (q && cudaMemcpyAsync(q + r * D, t.fq + slot * D, D * sizeof(double), cudaMemcpyDeviceToHost, s) !=
+                     cudaSuccess)
+            return LSD_ECUDA;
+        if (F && cudaMemcpyAsync(F + r * D, t.fF + slot * D, D * sizeof(float), cudaMemcpyDeviceToHost, s) !=
+                     cudaSuccess)
+            return LSD_ECUDA;
+    }
+    return cudaStreamSynchronize(s) == cudaSuccess ? LSD_OK : LSD_ECUDA;
+}
+
 void enqueue_frame_capture(TrainState &t, const double *w_qmid, const float *w_Ft, int K, int N, DevState *st,
                            const int *keff, cudaStream_t s) {
     t.K = K;

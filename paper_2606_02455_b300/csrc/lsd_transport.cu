@@ -9,11 +9,13 @@
 // and its position q_mid + (dt/2) p/m (the shared map g = A of Thm 3.1).
 //
 // transport_reduce_kernel: per (chunk of atoms, window step) partial sums of
-//   z.delta and delta.delta, written to a fixed slot (no atomics).  An atom's
-//   three-term products and a warp's 32 atoms are summed in FP32 (the FP32
-//   forces bound delta's accuracy anyway); warps, chunks and the log ratio
-//   are FP64.  log u (one FP64 log per step) is formed by the deciding
-//   kernel itself; the cooperative form does it before its wait on the force
+//   z.delta and delta.delta, written to a fixed slot (no atomics).  Everything
+//   from the first product up is FP64: delta's components are FP64 products of
+//   the exact FP64 difference of the two FP32 forces, z is the FP32 normal
+//   widened exactly, and the sums over an atom's three components, a warp's
+//   32 atoms, the warps, the chunks and the log ratio are FP64 in a fixed
+//   order.  log u (one FP64 log per step) is formed by the deciding kernel
+//   itself; the cooperative form does it before its wait on the force
 //   gather, so it overlaps the gather.
 // transport_commit_kernel: every CTA sums the partials in the same fixed
 //   order, finds l = first rejected step, and commits its slice of atoms:
@@ -26,12 +28,13 @@ namespace lsd {
 
 constexpr int kTransThreads = 256;
 
-// The block's sums of a and b: FP32 within a warp, FP64 over the warps (warp 0).
-__device__ __forceinline__ double2 block_sum2(float a, float b, double2 *sh) {
+// The block's FP64 sums of a and b in a fixed order: a butterfly within each
+// warp, then warp 0 over the warps' results.
+__device__ __forceinline__ double2 block_sum2(double a, double b, double2 *sh) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    a = warp_sum(a);
-    b = warp_sum(b);
-    if (lane == 0) sh[w] = make_double2((double)a, (double)b);
+    a = warp_sum_d(a);
+    b = warp_sum_d(b);
+    if (lane == 0) sh[w] = make_double2(a, b);
     __syncthreads();
     double2 t = make_double2(0.0, 0.0);
     if (w == 0) {
@@ -43,6 +46,18 @@ __device__ __forceinline__ double2 block_sum2(float a, float b, double2 *sh) {
         }
     }
     return t;   // valid in thread 0
+}
+
+// One atom's terms of z.delta and delta.delta, added to s and d, all in FP64:
+// delta_c = k (F~_c - F_c) with k = (1+c1)(dt/2) kappa / sigma of its species
+// (the FP64 difference of two FP32 values is exact), z_c = xi_c.
+__device__ __forceinline__ void atom_terms(double k, float3 xi, float3 fd, const float *__restrict__ ft, double &s,
+                                           double &d) {
+    const double d0 = k * ((double)fd.x - (double)ft[0]);
+    const double d1 = k * ((double)fd.y - (double)ft[1]);
+    const double d2 = k * ((double)fd.z - (double)ft[2]);
+    s += ((double)xi.x * d0 + (double)xi.y * d1) + (double)xi.z * d2;
+    d += (d0 * d0 + d1 * d1) + d2 * d2;
 }
 
 // Shared state of a window's decision, used by the commit (and by the fused
@@ -207,16 +222,12 @@ __global__ void __launch_bounds__(kTransThreads)
         const unsigned long long n = (unsigned long long)(st->step + j + 1);
         const int a0 = blockIdx.x * atoms_per_block;
         const int a1 = min(N, a0 + atoms_per_block);
-        float s = 0.f, d = 0.f;
+        double s = 0.0, d = 0.0;
         for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
             const float3 xi = normals3(cf.seed, n, (uint32_t)i, 0u);
-            const float k = (float)species_pick(cf.aF_sig, species[i]);
+            const double k = species_pick(cf.aF_sig, species[i]);
             const size_t o = ((size_t)j * N + i) * 3;
-            const float d0 = k * (Fd[o + 0] - Ft[o + 0]);
-            const float d1 = k * (Fd[o + 1] - Ft[o + 1]);
-            const float d2 = k * (Fd[o + 2] - Ft[o + 2]);
-            s += xi.x * d0 + xi.y * d1 + xi.z * d2;
-            d += d0 * d0 + d1 * d1 + d2 * d2;
+            atom_terms(k, xi, make_float3(Fd[o + 0], Fd[o + 1], Fd[o + 2]), Ft + o, s, d);
         }
         const double2 SD = block_sum2(s, d, sh);
         if (threadIdx.x == 0) partials[(size_t)j * gridDim.x + blockIdx.x] = SD;
@@ -294,16 +305,16 @@ __global__ void __launch_bounds__(kTransThreads)
     const int a0 = blockIdx.x * atoms_per_block, a1 = min(N, a0 + atoms_per_block);
     constexpr int kPer = 4;   // atoms per thread held across the wait (chunks of up to 1024 atoms)
     float3 xi[kPer], fd[kPer];
-    float kk[kPer];
+    double kk[kPer];
     const unsigned long long n = (unsigned long long)(n0 + j + 1);
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
         const int i = a0 + threadIdx.x + u * (int)blockDim.x;
         xi[u] = fd[u] = make_float3(0.f, 0.f, 0.f);
-        kk[u] = 0.f;
+        kk[u] = 0.0;
         if (j < keff && i < a1) {
             xi[u] = normals3(cf.seed, n, (uint32_t)i, 0u);
-            kk[u] = (float)species_pick(cf.aF_sig, species[i]);
+            kk[u] = species_pick(cf.aF_sig, species[i]);
             const size_t o = ((size_t)j * N + i) * 3;
             fd[u] = make_float3(Fd[o + 0], Fd[o + 1], Fd[o + 2]);
         }
@@ -311,18 +322,11 @@ __global__ void __launch_bounds__(kTransThreads)
     // log u of every step (a long FP64 chain per thread), while the force gather finishes
     logu_fill(C, cf, n0, min(K, keff));
     pdl_wait();   // the target forces
-    float s = 0.f, d = 0.f;
+    double s = 0.0, d = 0.0;
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
         const int i = a0 + threadIdx.x + u * (int)blockDim.x;
-        if (j < keff && i < a1) {
-            const size_t o = ((size_t)j * N + i) * 3;
-            const float d0 = kk[u] * (fd[u].x - Ft[o + 0]);
-            const float d1 = kk[u] * (fd[u].y - Ft[o + 1]);
-            const float d2 = kk[u] * (fd[u].z - Ft[o + 2]);
-            s += xi[u].x * d0 + xi[u].y * d1 + xi[u].z * d2;
-            d += d0 * d0 + d1 * d1 + d2 * d2;
-        }
+        if (j < keff && i < a1) atom_terms(kk[u], xi[u], fd[u], Ft + ((size_t)j * N + i) * 3, s, d);
     }
     const double2 SD = block_sum2(s, d, sh);
     if (threadIdx.x == 0 && j < keff) partials[(size_t)j * nb + blockIdx.x] = SD;

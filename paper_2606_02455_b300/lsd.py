@@ -33,7 +33,8 @@ SYMBOLS = ["lsd_init", "lsd_draft_window", "lsd_verify_window", "lsd_step", "lsd
            "lsd_force_match_dev", "lsd_target_forces_dev", "lsd_draft_forces_dev", "lsd_neighbors",
            "lsd_descriptors", "lsd_get_window", "lsd_profile_window", "lsd_checkpoint", "lsd_restore", "lsd_query",
            "lsd_target_mlp_static_dev", "lsd_destroy",
-           "lsd_strerror", "lsd_launch_counts", "lsd_window_host"]
+           "lsd_strerror", "lsd_launch_counts", "lsd_window_host", "lsd_transport_window", "lsd_get_frames",
+           "lsd_set_max_displacement"]
 
 
 class LSDError(RuntimeError):
@@ -106,6 +107,9 @@ def _lib():
             "lsd_window_host": [P, P, P, ctypes.c_int64, P, P, P, P],
             "lsd_target_mlp_static_dev": [P, P, I32, P, P],
             "lsd_profile_window": [P, P, I32],
+            "lsd_transport_window": [P, P, P, P, P, I32, P, P],
+            "lsd_get_frames": [P, I64, I64, P, P],
+            "lsd_set_max_displacement": [P, D],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -222,6 +226,19 @@ class LSD:
         _check(_lib().lsd_verify_window(self.h, ctypes.byref(nc), ctypes.byref(fr)), "lsd_verify_window")
         return nc.value, fr.value
 
+    def transport_window(self, q_mid, p_draft, F_draft, F_target):
+        """reflectionVerify and commit on a given window (lsd_transport_window): [k, N, 3] arrays, float64 for
+        q_mid and p_draft, float32 forces.  Returns (committed count, first rejected step or -1)."""
+        k = int(np.asarray(q_mid).shape[0])
+        arrs = [np.ascontiguousarray(q_mid, dtype=np.float64), np.ascontiguousarray(p_draft, dtype=np.float64),
+                np.ascontiguousarray(F_draft, dtype=np.float32), np.ascontiguousarray(F_target, dtype=np.float32)]
+        for a in arrs:
+            assert a.shape == (k, self.N, 3)
+        nc, fr = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib().lsd_transport_window(self.h, *[_p(a) for a in arrs], k, ctypes.byref(nc), ctypes.byref(fr)),
+               "lsd_transport_window")
+        return nc.value, fr.value
+
     def step(self, n_steps):
         st = lsd_stats()
         _check(_lib().lsd_step(self.h, int(n_steps), ctypes.byref(st)), "lsd_step")
@@ -282,6 +299,10 @@ class LSD:
         """"aboba" (Eq. 2) or "obabo" (the staggered frame of App. E; entering it evaluates the target once)."""
         _check(_lib().lsd_set_integrator(self.h, self.SCHEMES[scheme]), "lsd_set_integrator")
 
+    def set_max_displacement(self, d_max):
+        """End windows early once an atom moves d_max Angstrom from its lists' base (0 restores the default)."""
+        _check(_lib().lsd_set_max_displacement(self.h, float(d_max)), "lsd_set_max_displacement")
+
     def set_error_correction(self, on=True):
         _check(_lib().lsd_set_error_correction(self.h, int(bool(on))), "lsd_set_error_correction")
 
@@ -302,6 +323,13 @@ class LSD:
         n = ctypes.c_int64()
         _check(_lib().lsd_frame_count(self.h, ctypes.byref(n)), "lsd_frame_count")
         return n.value
+
+    def get_frames(self, first, count):
+        """Captured frames first .. first+count-1 (lsd_get_frames): q_mid [count, N, 3] float64, F_target float32."""
+        q = np.zeros((count, self.N, 3))
+        F = np.zeros((count, self.N, 3), np.float32)
+        _check(_lib().lsd_get_frames(self.h, int(first), int(count), _p(q), _p(F)), "lsd_get_frames")
+        return q, F
 
     def train_draft(self, n_iters, lr, frames_per_iter=0):
         loss = ctypes.c_float()

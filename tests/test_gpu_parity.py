@@ -1,28 +1,26 @@
 """GPU parity: the CUDA library (through the C ABI) against the FP64 oracle on the same seeded inputs.
 
-Tolerances (each per result against FP64): neighbour lists and accept/reject decisions identical (decisions
-whose margin |log u - min(0, log r)| is below 1e-6 are near-ties, reported and excluded); FP32 forces,
-descriptors and dE/dX within 1e-5 relative (norm over a configuration); BF16 paths within 2e-2 relative."""
+Tolerances (each per result against FP64, derived in tests/parity_bounds.py): neighbour lists and accept/reject
+decisions identical; FP32 forces, descriptors and dE/dX within 1e-5 relative, as a norm ratio per configuration
+and per element (relative to the configuration's largest |value|); BF16 paths within 2e-2.  The end-to-end log
+ratio is within 1e-4 max(1, |log r|), and decisions are compared outside exactly that band (a decision inside it
+would be a near-tie; none occurs at the test seeds).  States after a window or a free run are within the
+momentum and position bounds of parity_bounds.state_tols."""
 import numpy as np
 import pytest
 
 import oracle.oracle as O
 from paper_2606_02455_b300 import workloads as W
+from parity_bounds import BF16_TOL, FORCE_TOL, elem, logr_tol, rel as _rel, state_tols
 
 pytestmark = pytest.mark.gpu
 
-FORCE_TOL = 1e-5
-BF16_TOL = 2e-2
-TIE = 1e-6
+LOGR_DN = 1e-4   # |delta|: the FP32 force error relative to the force difference it is built from
 
 
 def _lsd():
     from paper_2606_02455_b300 import lsd
     return lsd
-
-
-def _rel(a, b):
-    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
 
 
 def _configs(system, n, scale, seed):
@@ -89,38 +87,32 @@ def test_target_neighbors_descriptors_forces(wl):
         for i in range(s.n_atoms):
             assert np.array_equal(desc[i], od[i]), ("desc list", c, i)
             assert np.array_equal(ljl[i], ol[i]), ("lj list", c, i)
-        assert _rel(X[c], ref["X"]) < FORCE_TOL
-        assert _rel(G[c], ref["dEdX"]) < FORCE_TOL
+        assert _rel(X[c], ref["X"]) < FORCE_TOL and elem(X[c], ref["X"]) < FORCE_TOL
+        assert _rel(G[c], ref["dEdX"]) < FORCE_TOL and elem(G[c], ref["dEdX"]) < FORCE_TOL
         assert _rel(F[c], ref["F"]) < FORCE_TOL, (c, _rel(F[c], ref["F"]))
+        assert elem(F[c], ref["F"]) < FORCE_TOL, (c, elem(F[c], ref["F"]))
         assert abs(E[c].astype(np.float64).sum() - ref["E"]) < FORCE_TOL * np.abs(ref["E_atom"]).sum()
     h.close()
 
 
-def _p_tol(wl, n_steps):
-    """Momentum tolerance after n_steps draft steps.  Per step the GPU differs from FP64 by its FP32 Box-Muller
-    noise (|dxi| <= 1e-6 for |xi| < 6, a few ulp of logf/sqrtf/sincospif) times sigma, and by the FP32 force
-    error (<= 1e-5 of |F|) times (1+c1)(dt/2)kappa; errors add up over steps (c1 ~ 1)."""
-    c1, aF, hm, sg = O.coefficients(wl.system, wl.integ)
-    fmax = np.abs(O.forces(wl.system, wl.target, wl.system.positions)).max() + \
-        np.abs(O.forces(wl.system, wl.draft, wl.system.positions)).max()
-    return n_steps * (sg.max() * 1e-6 + aF * 1e-5 * 10 * fmax), hm.max()
-
-
-def _window_compare(win, ref, K, wl):
+def _window_compare(win, ref, K, wl, target):
     assert np.array_equal(win["q_mid"][0], ref["qmid"][0]), "first half step is not bit-identical"
     for j in range(K):
-        ptol, hm = _p_tol(wl, j + 1)
+        ptol, qtol = state_tols(wl, target, j + 1)
         assert np.abs(win["p_draft"][j] - ref["pdraft"][j]).max() < ptol, ("p_draft", j)
-        assert np.abs(win["q_mid"][j] - ref["qmid"][j]).max() < 2 * hm * ptol + 1e-12, ("q_mid", j)
+        # q_mid_j = q'_{j-1} + (dt/2) p'_{j-1}/m: within the position bound of step j
+        assert np.abs(win["q_mid"][j] - ref["qmid"][j]).max() < qtol, ("q_mid", j)
     for j in range(K):
-        assert _rel(win["F_draft"][j], ref["Fdraft"][j]) < FORCE_TOL, ("F_draft", j)
-        assert _rel(win["F_target"][j], ref["Ftarget"][j]) < FORCE_TOL, ("F_target", j)
-    assert np.allclose(win["delta_norm"], ref["delta_norm"], rtol=1e-4, atol=1e-7)
-    assert np.allclose(win["log_ratio"], ref["logr"], rtol=1e-4, atol=1e-7)
-    assert np.array_equal(win["log_u"], ref["logu"]) or np.allclose(win["log_u"], ref["logu"], rtol=1e-15, atol=0)
+        for key_g, key_o in (("F_draft", "Fdraft"), ("F_target", "Ftarget")):
+            assert _rel(win[key_g][j], ref[key_o][j]) < FORCE_TOL, (key_g, j)
+            assert elem(win[key_g][j], ref[key_o][j]) < FORCE_TOL, (key_g, j, elem(win[key_g][j], ref[key_o][j]))
+    tol = logr_tol(ref["logr"])
+    assert (np.abs(win["log_ratio"] - ref["logr"]) <= tol).all(), np.abs(win["log_ratio"] - ref["logr"]) / tol
+    assert np.allclose(win["delta_norm"], ref["delta_norm"], rtol=LOGR_DN, atol=1e-7)
+    assert np.allclose(win["log_u"], ref["logu"], rtol=1e-15, atol=0)
     margin = np.abs(ref["logu"] - np.minimum(ref["logr"], 0.0))
-    ties = margin < TIE
-    assert not ties.any(), "near-tie decisions at the test seed: %s" % np.nonzero(ties)
+    ties = margin <= tol
+    assert not ties.any(), "decisions within the log-ratio tolerance at the test seed: %s" % np.nonzero(ties)
     assert np.array_equal(win["accept"], ref["accept"])
 
 
@@ -136,16 +128,14 @@ def test_window_matches_oracle(wl, head_scale):
     nc, first = h.verify_window()
     win = h.get_window()
     ref = O.lsd_window(s, wl.draft, target, wl.integ, s.seed, 0, wl.integ.K, s.positions, s.momenta)
-    _window_compare(win, ref, wl.integ.K, wl)
+    _window_compare(win, ref, wl.integ.K, wl, target)
     assert nc == ref["n_committed"]
     assert first == (-1 if ref["accept"].all() else int(np.argmin(ref["accept"])) + 1)
     q, p, step = h.get_state()
     assert step == nc
-    ptol, hm = _p_tol(wl, nc)
-    c1, aF, _, sg = O.coefficients(s, wl.integ)
-    ptol += 1e-4 * sg.max()       # a reflection amplifies the FP32 error of delta by 2|z.delta|/|delta|
+    ptol, qtol = state_tols(wl, target, nc, 0 if ref["accept"][:nc].all() else 1)
     assert np.abs(p - ref["p"]).max() < ptol
-    assert np.abs(q - ref["q"]).max() < 3 * hm * ptol + 1e-12
+    assert np.abs(q - ref["q"]).max() < qtol
     h.close()
 
 
@@ -161,18 +151,17 @@ def test_free_running_matches_oracle_20_steps(wl):
     ref = O.lsd_run(s, wl.draft, target, wl.integ, s.seed, 20, wl.integ.K, s.positions, s.momenta)
     assert step == 20 == st["committed"]
     assert st["rejected"] == ref["stats"]["rejected"]
-    ptol, hm = _p_tol(wl, 20)
-    ptol = 10 * ptol + 1e-4 * O.coefficients(s, wl.integ)[3].max() * ref["stats"]["rejected"]
+    ptol, qtol = state_tols(wl, target, 20, int(ref["stats"]["rejected"]))
     assert np.abs(p - ref["p"]).max() < ptol
-    assert np.abs(q - ref["q"]).max() < 40 * hm * ptol
+    assert np.abs(q - ref["q"]).max() < qtol
     h.set_state(s.positions, s.momenta, 0)
     h.plain_step(20)
     q, p, step = h.get_state()
     refp = O.plain_run(s, target, wl.integ, s.seed, 20, s.positions, s.momenta)
     assert step == 20
-    ptol, hm = _p_tol(wl, 20)
-    assert np.abs(p - refp["p"]).max() < 10 * ptol
-    assert np.abs(q - refp["q"]).max() < 400 * hm * ptol
+    ptol, qtol = state_tols(wl, target, 20)
+    assert np.abs(p - refp["p"]).max() < ptol
+    assert np.abs(q - refp["q"]).max() < qtol
     h.close()
 
 
@@ -196,9 +185,8 @@ def test_error_correction_window_matches_oracle():
         q, p, dF = ref["q"], ref["p"], ref["ec_dF"]
         step += nc
         assert gstep == step
-        ptol, hm = _p_tol(w, nc)
-        ptol += 1e-4 * O.coefficients(s, w.integ)[3].max()
-        assert np.abs(gp - p).max() < ptol and np.abs(gq - q).max() < 3 * hm * ptol
+        ptol, qtol = state_tols(w, target, nc, 0 if ref["accept"][:nc].all() else 1)
+        assert np.abs(gp - p).max() < ptol and np.abs(gq - q).max() < qtol
         h.set_state(q, p, step)    # keep both sides on the oracle's state
     h.close()
 
@@ -216,8 +204,10 @@ def test_draft_equal_target_accepts_everything():
     h.set_state(s.positions, s.momenta, 0)
     h.plain_step(64)
     q2, p2, _ = h.get_state()
-    ptol, hm = _p_tol(w, 64)
-    assert np.abs(p1 - p2).max() < 10 * ptol and np.abs(q1 - q2).max() < 640 * hm * ptol
+    # both runs use the same FP32 forces of the same potential: only the summation of the draft kernel and of the
+    # verification kernels differs (~1e-6 of |F| per element), far inside the oracle bound used here
+    ptol, qtol = state_tols(w, w.draft, 64, draft=w.draft)
+    assert np.abs(p1 - p2).max() < ptol and np.abs(q1 - q2).max() < qtol
     h.close()
 
 

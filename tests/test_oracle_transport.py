@@ -101,3 +101,22 @@ def test_rejected_sample_is_householder_reflection():
         assert np.linalg.norm(zr) == pytest.approx(np.linalg.norm(z), rel=1e-12)
         assert zr @ dl == pytest.approx(-(z @ dl), rel=1e-10, abs=1e-12)
     assert found > 20
+
+
+def test_transport_terms_give_the_log_ratio_in_closed_form():
+    """Eq. 5: with z = S^-1/2 (p~ - <p~>) and delta = S^-1/2 (<p~> - <p>), the log density ratio of the two
+    Gaussians at p~ is -z.delta - |delta|^2/2.  The oracle forms log r from the two Gaussian exponents and the
+    sums z.delta, delta.delta separately; scipy's densities fix both."""
+    rng = np.random.default_rng(4)
+    for D in (1, 3, 12, 96):
+        sig = rng.uniform(0.5, 2.0, D)
+        mu_d, mu_t = rng.standard_normal(D), rng.standard_normal(D)
+        pd = mu_d + sig * rng.standard_normal(D)
+        acc, p, lr, zd, dd = O.transport_terms(sig, 0.5, pd, mu_d, mu_t)
+        logpdf = stats.norm.logpdf(pd, mu_t, sig).sum() - stats.norm.logpdf(pd, mu_d, sig).sum()
+        assert lr == pytest.approx(logpdf, rel=1e-12, abs=1e-12)
+        assert -zd - 0.5 * dd == pytest.approx(logpdf, rel=1e-12, abs=1e-12)
+        # |delta|^2 is the squared Mahalanobis distance of the two means; z.delta its projection
+        assert dd == pytest.approx(float(np.sum(((mu_d - mu_t) / sig) ** 2)), rel=1e-13)
+        assert acc == (np.log(0.5) <= min(0.0, logpdf))
+        assert np.array_equal(p, O.transport(sig, 0.5, pd, mu_d, mu_t)[1])
