@@ -162,20 +162,36 @@ def _lj_pairs_per_atom(w, q):
 # DRAM bytes (read + write) of one launch, from one ncu capture of the kernel as it is now (the summaries under
 # profiles/ give the command); a kernel changed since its capture has no entry here.
 NCU_TRAFFIC = {
-    ("lj_mlp_angular_256atoms_K16", "draft"): 70144,       # draft_window_cluster_kernel, K = 16
-    ("lj_mlp_angular_256atoms_K16", "mlp"): 1419520,       # mlp_tc_kernel<F16x3>, 4096 rows
 }
+
+
+# FP32 operations of one unordered angular neighbour pair (all 16 terms): the descriptor's forward (cosine, the
+# powers (1 +- c)^zeta, 16 weighted accumulations) and the pair gradient's backward (the same powers, the value and
+# derivative sums S0, S1 per eta, and the two displacement gradients), counted from the formulas each kernel
+# evaluates; and per (neighbour, radial basis function): exp argument, exp, cutoff product, accumulation.
+FLOP_ANG_DESC = 64
+FLOP_ANG_GRAD = 132
+FLOP_RAD_DESC = 8
+FLOP_RAD_GRAD = 12
+FLOP_LJ_PAIR = 23
+
+
+def _neighbours_per_atom(w, rc):
+    s = w.system
+    return s.n_atoms / float(np.prod(s.box)) * 4.0 / 3.0 * np.pi * rc ** 3
 
 
 def _algorithmic_work(w, phase, q):
     """Algorithmic work of one launch of a phase, with its bound: (amount, unit, bound, detail).
 
     mlp:   2 FLOP per multiply-add of the forward chain plus the input-gradient chain (no weight gradient):
-           2 * M * sum(d_in * d_out) * 2, M = K N rows.  FP32 targets run it as three TF32 tensor-core
-           products per term (3x the algorithmic MACs executed); BF16 targets as one BF16 product.
+           2 * M * sum(d_in * d_out) * 2, M = K N rows.  FP32 targets run it as three FP16 tensor-core
+           products per term (3x the algorithmic MACs executed); BF16 and FP8 targets as one product.
     draft: per drafted step, every LJ pair within the cutoff costs 8 FLOP of distance and 15 of force
            (gather form: each ordered pair once), plus 24 FP64 FLOP per atom of BOB + A;
            K steps per launch, serial.
+    descriptors / pair_grad: FP32 ALU work per row, from the mean neighbour count nb within the descriptor cutoff:
+           nb (nb - 1) / 2 angular pairs x FLOP_ANG_* + nb x n_rbf x FLOP_RAD_* (+ LJ pairs for pair_grad).
     transport: bytes that must cross HBM once per window."""
     s, t, K = w.system, w.target, w.integ.K
     N = s.n_atoms
@@ -186,8 +202,18 @@ def _algorithmic_work(w, phase, q):
         return 2.0 * 2.0 * M * macs, "FLOP", "tensor", {"precision": t.precision, "rows": M}
     if phase == "draft":
         nb = _lj_pairs_per_atom(w, q)
-        flop = K * (N * nb * (8 + 15) + N * 24)
+        flop = K * (N * nb * FLOP_LJ_PAIR + N * 24)
         return flop, "FLOP", "alu", {"lj_pairs_per_atom": round(nb, 1), "steps_per_launch": K}
+    if phase in ("descriptors", "pair_grad") and t.n_layers:
+        nb = _neighbours_per_atom(w, t.desc_cutoff)
+        ang = nb * (nb - 1) / 2 if t.n_ang else 0.0
+        if phase == "descriptors":
+            per_row = ang * FLOP_ANG_DESC + nb * t.n_rbf * FLOP_RAD_DESC
+        else:
+            nlj = _neighbours_per_atom(w, t.lj_cutoff) if t.lj_cutoff else 0.0
+            per_row = ang * FLOP_ANG_GRAD + nb * t.n_rbf * FLOP_RAD_GRAD + nlj * FLOP_LJ_PAIR
+        return M * per_row, "FLOP", "alu", {"neighbours_per_atom": round(nb, 1), "rows": M,
+                                            "flop_per_row": round(per_row)}
     if phase in ("transport_reduce",):
         return M * 3 * (4 + 4), "B", "hbm", {}
     if phase in ("transport_commit",):
@@ -248,12 +274,19 @@ def roofline(h, w, peaks, peak_kind, q, n_rep=20):
             out["us_per_step"] = round(phases[dom] * 1e3 / w.integ.K, 3)
             out["note"] = ("serial chain of K drafted steps in one thread-block cluster (at most 16 SMs); "
                            "latency-bound: the per-step time, not FLOP/s, is the figure of merit")
+        else:
+            out["note"] = ("FP32 operations counted from the kernel's formulas (angular pair %d / %d FLOP, radial "
+                           "term %d / %d FLOP for descriptors / pair gradients) over the derived FP32 FMA peak" % (
+                               FLOP_ANG_DESC, FLOP_ANG_GRAD, FLOP_RAD_DESC, FLOP_RAD_GRAD))
     elif bound == "tensor":
         ach = amount / sec / 1e12
         bf16 = peaks["bf16_tflops"]
         if w.target.precision in ("bf16", "fp32"):
             # BF16 and the FP16 split of FP32 targets: the FP16 dense rate equals the BF16 one
             pk, src = bf16, "%s bf16 burst (FP16 dense = BF16 dense)" % peak_kind
+        elif w.target.precision == "fp8":
+            # FP8 dense = bf16 x (4.5 / 2.25), the nominal ratio
+            pk, src = bf16 * 2.0, "%s bf16 burst x 4.5/2.25 (nominal FP8:BF16)" % peak_kind
         else:
             # TF32 dense = bf16 x (1.1 / 2.25), the nominal ratio
             pk, src = bf16 * 1.1 / 2.25, "%s bf16 burst x 1.1/2.25 (nominal TF32:BF16)" % peak_kind
@@ -273,31 +306,42 @@ def roofline(h, w, peaks, peak_kind, q, n_rep=20):
 # our implementation
 # ------------------------------------------------------------------------------------------------------------------
 
-def run_ours(args):
+L2_BYTES = 126 * 2 ** 20
+
+
+def _working_set_bytes(w):
+    """Device bytes one window's verification touches (neighbour keys and pair gradients at ~2x the mean count,
+    descriptors and dE/dX, window arrays): decides whether L2 must be flushed between timed windows."""
+    s, t, K = w.system, w.target, w.integ.K
+    N = s.n_atoms
+    rc = max(t.desc_cutoff or 0.0, t.lj_cutoff or 0.0)
+    nb = 2.0 * N / float(np.prod(s.box)) * 4.0 / 3.0 * np.pi * rc ** 3 + 32
+    d0p = ((s.n_species * t.n_rbf + t.n_ang + s.n_species) + 31) // 32 * 32
+    return K * N * (nb * (4 + 16) + 2 * 4 * d0p + 3 * (8 + 8 + 4 + 4 + 4))
+
+
+def measure_workload(w, args, world, rank, full):
+    """LSD windows and plain target steps of one workload on this rank's GPU.  `full`: also the unpipelined
+    comparison, e2e through the public one-call window, the live per-phase roofline and the clocks."""
     import torch
     from paper_2606_02455_b300 import lsd
 
-    world, rank, local = _dist()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    w = _workload(args.config)
     s = w.system
     s.seed = replica_seed(s.seed, rank)   # independent replicas
     K = w.integ.K
-    peaks, peak_kind = _peaks()
     h = lsd.LSD(s, w.draft, w.target, w.integ)
     stream = torch.cuda.Stream()
     h.set_stream(stream)
-    # equilibrate with plain target dynamics, then warm up both graphs
+    # equilibrate with plain target dynamics
     h.plain_step(args.equil)
     q_eq, p_eq, step_eq = h.get_state()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush_needed = _working_set_bytes(w) < 4 * L2_BYTES
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda") if flush_needed else None
 
     def flush_l2():
-        with torch.cuda.stream(stream):
-            flush.add_(1.0)
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.add_(1.0)
 
     pipelined = not args.no_pipeline
     h.set_pipelining(pipelined)
@@ -306,151 +350,267 @@ def run_ours(args):
         h.plain_step(1)
 
     def timed_windows(n):
-        """n windows from the equilibrated state, each enqueue bracketed by events, L2 flushed in between."""
+        """n windows from the equilibrated state on the library's stream.  Small working sets: each window
+        bracketed by its own events, L2 flushed before it; otherwise (inputs larger than L2) one event pair."""
         h.set_state(q_eq, p_eq, step_eq)
         a = h.stats()
         _barrier(world)
         torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
-        for k in range(n):
-            flush_l2()
-            ev[k][0].record(stream)
-            h.enqueue_windows(1)
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
+        if flush is not None:
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+            for k in range(n):
+                flush_l2()
+                ev[k][0].record(stream)
+                h.enqueue_windows(1)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            t = sum(x.elapsed_time(y) for x, y in ev) * 1e-3
+        else:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.enqueue_windows(n)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) * 1e-3
         _barrier(world)
         b = h.stats()
-        return (sum(x.elapsed_time(y) for x, y in ev) * 1e-3, b["committed"] - a["committed"],
-                b["rejected"] - a["rejected"], b["windows"] - a["windows"], a, b)
+        return (t, b["committed"] - a["committed"], b["rejected"] - a["rejected"], b["windows"] - a["windows"], a, b)
 
-    clocks = Clocks(local)
-    clocks.start()
-    # ---- LSD: `steps` windows (pipelined: each enqueue verifies one window while drafting the next) ----
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0"))) if full else None
+    if clocks:
+        clocks.start()
     t_lsd, committed, rejected, windows, st0, st1 = timed_windows(args.steps)
-    if args.only_lsd:
-        # profiling mode: the LSD windows alone (no baseline, e2e or roofline pass)
-        clocks.stop()
-        if rank == 0:
-            print(json.dumps({"metric": METRIC, "mode": "only-lsd", "windows": windows, "committed": committed,
-                              "ms_per_step": round(t_lsd * 1e3 / args.steps, 5)}), flush=True)
-        h.close()
-        return
-    # ---- the same windows without the draft/verify overlap, for comparison ----
     value_unpipelined = None
-    if pipelined:
+    if pipelined and full:
         h.set_pipelining(False)
         h.step(K)
         t_u, c_u, _, _, _, _ = timed_windows(args.steps)
         value_unpipelined = whole_job_rate(c_u, t_u, world) * w.integ.dt * NS_PER_DAY
         h.set_pipelining(True)
-    # ---- plain target Langevin: the same number of steps as committed, one graph launch per step ----
+    # plain target Langevin: the same number of steps as committed, back to back (one graph launch per step)
     h.set_state(q_eq, p_eq, step_eq)
-    n_plain = max(committed, 16)
-    evp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_plain)]
+    n_plain = max(committed, 32)
+    h.plain_step(2)
+    h.set_state(q_eq, p_eq, step_eq)
     torch.cuda.synchronize()
-    for k in range(n_plain):
-        flush_l2()
-        evp[k][0].record(stream)
-        h.enqueue_plain(1)
-        evp[k][1].record(stream)
+    flush_l2()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h.enqueue_plain(n_plain)
+    e1.record(stream)
     torch.cuda.synchronize()
-    t_plain = sum(a.elapsed_time(b) for a, b in evp) * 1e-3
-    clk = clocks.stop()
+    t_plain = e0.elapsed_time(e1) * 1e-3
+    clk = clocks.stop() if clocks else None
 
-    t_lsd_max = _max_over_ranks(t_lsd, world)
     value = whole_job_rate(committed, t_lsd, world) * w.integ.dt * NS_PER_DAY
     plain_value = whole_job_rate(n_plain, t_plain, world) * w.integ.dt * NS_PER_DAY
-
-    # ---- e2e: the public one-call window with host buffers (pinned): every window uploads its state, runs,
-    # and reads the committed state back ----
+    lc = h.launch_counts()
+    out = {
+        "workload": w.name, "value": round(value, 4), "ms_per_window": round(t_lsd * 1e3 / args.steps, 5),
+        "acceptance_rate": round(1.0 - rejected / max(committed, 1), 5),
+        "committed_per_window": round(committed / max(windows, 1), 3),
+        "plain_target_ns_per_day": round(plain_value, 4), "plain_ms_per_step": round(t_plain * 1e3 / n_plain, 5),
+        "speedup_vs_plain": round(value / plain_value, 4),
+        "l2": "flushed (256 MB write) before every timed window and once before the plain steps" if flush is not None
+        else "not flushed: the window's working set (%.2f GB) is larger than L2" % (_working_set_bytes(w) / 1e9),
+    }
+    if not full:
+        h.close()
+        return out
+    out.update({
+        "t_lsd": t_lsd, "committed": committed, "windows": windows, "n_plain": n_plain, "st0": st0, "st1": st1,
+        "t_plain": t_plain, "pipelined": pipelined,
+        "value_unpipelined": None if value_unpipelined is None else round(value_unpipelined, 4),
+        "gpu_launches": int(windows * (lc["round"] if pipelined else lc["window"]) + n_plain * lc["plain"]),
+        "clocks": clk,
+    })
+    # ---- e2e: the public one-call window with host buffers (pinned): every window uploads its state, runs, and
+    # reads the committed state back ----
     h.set_state(q_eq, p_eq, step_eq)
     state = torch.empty((2, s.n_atoms, 3), dtype=torch.float64, pin_memory=True).numpy()
     pos, mom = state[0], state[1]   # adjacent, as on the device: one copy each way
     pos[:] = q_eq
     mom[:] = p_eq
-    n_e2e = args.steps
     step = step_eq
     for _ in range(max(args.warmup, 3)):   # untimed: first-call costs of the one-call path
         step, nc = h.window_host(pos, mom, step)
     stats_a = h.stats()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(n_e2e):
+    for _ in range(args.steps):
         step, nc = h.window_host(pos, mom, step)
     t_e2e = time.perf_counter() - t0
     stats_b = h.stats()
     e2e_committed = stats_b["committed"] - stats_a["committed"]
-    e2e_val = whole_job_rate(e2e_committed, t_e2e, world) * w.integ.dt * NS_PER_DAY
     D = 3 * s.n_atoms
+    out["e2e"] = {"value": round(whole_job_rate(e2e_committed, t_e2e, world) * w.integ.dt * NS_PER_DAY, 4),
+                  "unit": "ns/day", "h2d_bytes_per_step": 2 * D * 8 + 16, "d2h_bytes_per_step": 2 * D * 8 + 32,
+                  "calls": "lsd_window_host (pinned host state in and out)"}
+    out["roofline"] = roofline(h, w, _peaks()[0], _peaks()[1], pos)
+    h.close()
+    return out
 
-    rl = roofline(h, w, peaks, peak_kind, pos)
-    # this library's kernels per window / pipelined round / plain step, for the handle's configuration
-    lc = h.launch_counts()
-    launches_per_window = lc["round"] if pipelined else lc["window"]
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    w = _workload(args.config)
+    K = w.integ.K
+    m = measure_workload(w, args, world, rank, full=True)
+    st0, st1 = m["st0"], m["st1"]
+    extra = {}
+    for cfg in args.extra:
+        if cfg == args.config:
+            continue
+        extra["config%d" % cfg] = measure_workload(_workload(cfg), args, world, rank, full=False)
+    t = w.target
     line = {
-        "metric": METRIC, "value": round(value, 3), "unit": "ns/day", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(t_lsd_max * 1e3 / args.steps, 5), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "metric": METRIC, "value": m["value"], "unit": "ns/day", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(_max_over_ranks(m["t_lsd"], world) * 1e3 / args.steps, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "dtype_detail": ("FP32 forces and descriptors; MLP %s; FP64 integrator state, z.delta, delta.delta and "
                          "log ratio" % {"fp32": "at FP32 accuracy as three FP16 tensor-core products per term "
                                                 "(exact power-of-two scales)",
                                         "fp32-tf32": "at FP32 accuracy as three TF32 tensor-core products per term",
                                         "bf16": "in BF16 on the tensor cores with FP32 accumulation",
-                                        "fp8": "in FP32 on the CUDA cores (FP8 not built)",
-                                        "fp32-cuda-cores": "in FP32 on the CUDA cores"}[w.target.precision]),
+                                        "fp8": "in FP8 e4m3 on the tensor cores (per-tensor scales) with FP32 "
+                                               "accumulation",
+                                        "fp32-cuda-cores": "in FP32 on the CUDA cores"}[t.precision]),
         "data": "synthetic",
-        "config": {"workload": w.name, "n_atoms": s.n_atoms, "K": K, "dt_fs": w.integ.dt, "T_K": w.integ.temperature,
-                   "gamma_per_fs": w.integ.gamma, "target": "LJ + 0.05 eV tanh(MLP %d->%dx%d->1)" % (
-                       s.n_species * w.target.n_rbf + w.target.n_ang + s.n_species, w.target.width,
-                       w.target.n_layers),
-                   "draft": "LJ", "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "flushed (256 MB write) between timed windows"},
-        "acceptance_rate": round(1.0 - rejected / max(committed, 1), 5),
-        "analysis": _analysis(st1, st0, rl, K, t_plain / n_plain),
-        "committed_per_window": round(committed / max(windows, 1), 3),
-        "plain_target_ns_per_day": round(plain_value, 3),
-        "speedup_vs_plain": round(value / plain_value, 3),
-        "pipelined": pipelined,
-        "value_unpipelined": None if value_unpipelined is None else round(value_unpipelined, 3),
-        "plain_ms_per_step": round(t_plain * 1e3 / n_plain, 5),
-        "gpu_launches": int(windows * launches_per_window + n_plain * lc["plain"]),
-        "e2e": {"value": round(e2e_val, 3), "unit": "ns/day", "h2d_bytes_per_step": 2 * D * 8 + 16,
-                "d2h_bytes_per_step": 2 * D * 8 + 32, "calls": "lsd_window_host (pinned host state in and out)"},
-        "roofline": rl,
-        "clocks": clk,
+        "config": {"workload": w.name, "n_atoms": w.system.n_atoms, "K": K, "dt_fs": w.integ.dt,
+                   "T_K": w.integ.temperature, "gamma_per_fs": w.integ.gamma,
+                   "target": "LJ + 0.05 eV tanh(MLP %d->%dx%d->1, %s)" % (
+                       w.system.n_species * t.n_rbf + t.n_ang + w.system.n_species, t.width, t.n_layers,
+                       t.precision),
+                   "draft": _draft_label(w), "parallelism": "replicas" if world > 1 else "single",
+                   "l2": m["l2"]},
+        "acceptance_rate": m["acceptance_rate"],
+        "analysis": _analysis(st1, st0, m["roofline"], K, m["t_plain"] / m["n_plain"]),
+        "committed_per_window": m["committed_per_window"],
+        "plain_target_ns_per_day": m["plain_target_ns_per_day"],
+        "speedup_vs_plain": m["speedup_vs_plain"],
+        "pipelined": m["pipelined"],
+        "value_unpipelined": m["value_unpipelined"],
+        "plain_ms_per_step": m["plain_ms_per_step"],
+        "gpu_launches": m["gpu_launches"],
+        "e2e": m["e2e"],
+        "roofline": m["roofline"],
+        "clocks": m["clocks"],
+        "workloads": extra,
     }
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    h.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _draft_label(w):
+    d = w.draft
+    if not d.n_layers:
+        return "LJ"
+    d0 = w.system.n_species * d.n_rbf + d.n_ang + w.system.n_species
+    return "LJ + learned MLP %d->%s->1 (%s, linear head)" % (d0, "x".join([str(d.width)] * d.n_layers), d.precision)
 
 
 # ------------------------------------------------------------------------------------------------------------------
 # the oracle on the host (CPU baseline and the reference arm)
 # ------------------------------------------------------------------------------------------------------------------
 
-def cpu_baseline(w, seconds):
+def _oracle_threads():
+    return os.cpu_count() or 1
+
+
+def oracle_window_rate(w, seconds, threads):
+    """Whole oracle windows (Alg. 1, the window-parallel variant: a window's K target evaluations on `threads`
+    threads) from the workload's initial state for about `seconds`: (ns/day, sample description)."""
     from oracle import oracle as O
     s = w.system
     K = w.integ.K
+    O.set_threads(threads)
     q, p, step = s.positions.copy(), s.momenta.copy(), 0
     t0 = time.perf_counter()
-    committed = 0
-    windows = 0
-    while time.perf_counter() - t0 < seconds:
+    committed = windows = 0
+    while time.perf_counter() - t0 < seconds or windows == 0:
         out = O.lsd_window(s, w.draft, w.target, w.integ, s.seed, step, K, q, p)
         q, p = out["q"], out["p"]
         step += out["n_committed"]
         committed += out["n_committed"]
         windows += 1
     dt = time.perf_counter() - t0
-    return {"value": round(committed * w.integ.dt * NS_PER_DAY / dt, 6), "unit": "ns/day", "cores": 1,
-            "kind": "oracle", "sample": "%d windows (%d committed steps) of %s, single-threaded FP64 C" % (
-                windows, committed, w.name)}
+    O.set_threads(1)
+    return committed * w.integ.dt * NS_PER_DAY / dt, "%d windows (%d committed steps) of %s" % (
+        windows, committed, w.name)
+
+
+def oracle_slice_rate(w, threads, rows_target, rows_draft, seed=0):
+    """A bounded slice of one oracle window when whole windows take hours: the target's energy and forces of
+    centre atoms [0, rows_target) in all K window configurations (one configuration per thread, as in the
+    window-parallel verification) and the draft's of centre atoms [0, rows_draft) of one configuration; one window
+    is extrapolated as (N / rows) times each, the draft K times, and every drafted step is counted as committed (an
+    upper bound on the oracle's LSD rate).  The K configurations are the initial state with a seeded 0.01 A jitter
+    standing in for the drafted half-step positions.  Returns (ns/day, seconds spent, sample description)."""
+    from oracle import oracle as O
+    s = w.system
+    K, N = w.integ.K, s.n_atoms
+    rng = np.random.default_rng(seed)
+    qs = s.positions[None] + 0.01 * rng.standard_normal((K, N, 3))
+    O.set_threads(threads)
+    t0 = time.perf_counter()
+    O.eval_range(s, w.target, qs, 0, rows_target)
+    t_v = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    O.eval_range(s, w.draft, qs[:1], 0, rows_draft)
+    t_d = time.perf_counter() - t1
+    O.set_threads(1)
+    window = t_v * N / rows_target + K * t_d * N / rows_draft
+    rate = K * w.integ.dt * NS_PER_DAY / window
+    desc = ("slice of one window of %s: target energy/forces of centre atoms [0, %d) of %d in all %d configurations "
+            "(%.2f s on %d threads) and LJ draft of centre atoms [0, %d) of one configuration (%.2f s); one window "
+            "extrapolated to %.0f s (verification x %.0f, draft x %d x %.0f), every drafted step counted as committed "
+            "(upper bound)" % (w.name, rows_target, N, K, t_v, threads, rows_draft, t_d, window, N / rows_target, K,
+                               N / rows_draft))
+    return rate, t_v + t_d, desc
+
+
+def _slice_rows(w, seconds, threads):
+    """Centre-atom rows of the slice sized so that it takes about `seconds` (about 2/3 target, 1/3 draft),
+    from a small timed calibration slice of each."""
+    from oracle import oracle as O
+    s = w.system
+    K, N = w.integ.K, s.n_atoms
+    qs = np.repeat(s.positions[None], K, axis=0)
+    O.set_threads(threads)
+    r0 = min(N, 2)
+    t0 = time.perf_counter()
+    O.eval_range(s, w.target, qs, 0, r0)
+    per_t = (time.perf_counter() - t0) / r0
+    r1 = min(N, 32)
+    t0 = time.perf_counter()
+    O.eval_range(s, w.draft, qs[:1], 0, r1)
+    per_d = (time.perf_counter() - t0) / r1
+    O.set_threads(1)
+    rows_t = int(max(1, min(N, 0.65 * seconds / max(per_t, 1e-9))))
+    rows_d = int(max(1, min(N, 0.35 * seconds / max(per_d, 1e-9))))
+    return rows_t, rows_d
+
+
+def cpu_baseline(w, seconds):
+    threads = _oracle_threads()
+    if w.system.n_atoms <= 256:
+        val, sample = oracle_window_rate(w, seconds, threads)
+        sample += ", window-parallel FP64 C oracle on %d threads" % threads
+    else:
+        rt, rd = _slice_rows(w, seconds, threads)
+        val, _, sample = oracle_slice_rate(w, threads, rt, rd)
+    return {"value": val, "unit": "ns/day", "cores": threads, "kind": "oracle", "sample": sample}
 
 
 def run_reference(args):
@@ -460,46 +620,47 @@ def run_reference(args):
     w = _workload(args.config)
     from oracle import oracle as O
     O.build()
-    s = w.system
+    threads = _oracle_threads()
     K = w.integ.K
-    q, p, step = s.positions.copy(), s.momenta.copy(), 0
-    for _ in range(max(1, min(args.warmup, 1))):
-        out = O.lsd_window(s, w.draft, w.target, w.integ, s.seed, step, K, q, p)
-    times, committed = [], 0
-    n = max(1, min(args.steps, args.ref_windows))
-    for _ in range(n):
-        t0 = time.perf_counter()
-        out = O.lsd_window(s, w.draft, w.target, w.integ, s.seed, step, K, q, p)
-        times.append(time.perf_counter() - t0)
-        q, p = out["q"], out["p"]
-        step += out["n_committed"]
-        committed += out["n_committed"]
-    tot = sum(times)
-    val = committed * w.integ.dt * NS_PER_DAY / tot
-    sample = "%d windows (%d committed steps) of %s, single-threaded FP64 C oracle" % (n, committed, w.name)
+    small = w.system.n_atoms <= 256
+    rt, rd = (None, None) if small else _slice_rows(w, args.ref_seconds, threads)
+    vals, times, desc = [], [], ""
+    for k in range(args.warmup + args.steps):
+        if small:
+            t0 = time.perf_counter()
+            v, desc = oracle_window_rate(w, args.ref_seconds, threads)
+            dt = time.perf_counter() - t0
+        else:
+            v, dt, desc = oracle_slice_rate(w, threads, rt, rd, seed=k)
+        if k >= args.warmup:
+            vals.append(v)
+            times.append(dt)
+    val = float(np.mean(vals))
+    sample = "each step: " + desc + (", window-parallel FP64 C oracle on %d threads" % threads if small else "")
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": "ns/day", "n_gpus": world,
-        "steps": n, "warmup": args.warmup, "ms_per_step": round(tot * 1e3 / n, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "n_atoms": s.n_atoms, "K": K, "dt_fs": w.integ.dt},
-        "cpu_baseline": {"value": round(val, 6), "unit": "ns/day", "cores": 1, "kind": "oracle", "sample": sample},
-        "e2e": {"value": round(val, 6), "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "ns/day", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(float(np.mean(times)) * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n_atoms": w.system.n_atoms, "K": K, "dt_fs": w.integ.dt},
+        "cpu_baseline": {"value": val, "unit": "ns/day", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--config", type=int, default=5)
+    ap.add_argument("--extra", type=int, nargs="*", default=[2, 4],
+                    help="configurations measured as well (value, plain, acceptance) under `workloads`")
     ap.add_argument("--equil", type=int, default=1000)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--ref-windows", type=int, default=6)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-pipeline", action="store_true", help="time the unpipelined window loop only")
-    ap.add_argument("--only-lsd", action="store_true", help="time the LSD windows only (for profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -373,27 +373,35 @@ LSD_API int lsd_query(const lsd_handle *h, int32_t *K, int32_t *n_atoms, int32_t
 LSD_API int lsd_launch_counts(const lsd_handle *h, int32_t *per_window, int32_t *per_round, int32_t *per_plain);
 
 /* lsd_target_mlp_static_dev: the target potential's per-atom MLP (energies
- * and dE/dX, the tensor-core BF16 path of a handle whose target precision is
- * LSD_BF16) for callers that cannot allocate device memory: code running
+ * and dE/dX) on the tensor cores, in the target's own operand arithmetic
+ * (BF16, FP8 e4m3 with the handle's scales, or FP32 as three FP16 or TF32
+ * products), for callers that cannot allocate device memory: code running
  * inside a host application whose own allocator owns all device memory, or a
  * latency-critical loop that must not stall on cudaMalloc's implicit device
- * synchronisation.  It allocates nothing: the kernel's per-CTA SiLU' scratch
- * is a fixed 4 MiB array inside the library (held by every device that loads
- * the library until the process exits).  This entry point has no counterpart
- * in the paper; it is the same computation as the MLP step of
- * lsd_target_forces_dev.
+ * synchronisation.  It allocates nothing: when the kernel needs per-CTA
+ * scratch for SiLU' (layers x 128 x width x 2 bytes per CTA, when it does not
+ * fit in tensor memory), that scratch is a fixed 4 MiB array inside the
+ * library (held by every device that loads the library until the process
+ * exits), and the kernel runs as many CTAs as the array has slots for (21 at
+ * width 256 with 4 layers), each looping over its share of the 128-row tiles.
+ * This entry point has no counterpart in the paper; it is the same
+ * computation as the MLP step of lsd_target_forces_dev, bit for bit.
  *   X_dev     [M][d_pad] float descriptors, d_pad = target_d_in rounded up to
  *             a multiple of 32, padding columns zero (device pointer, read)
- *   E_dev     [M] float per-atom MLP energies (device pointer, written)
+ *   E_dev     [M] float per-atom MLP energies, head included (device pointer,
+ *             written)
  *   dEdX_dev  [M][d_pad] float dE/dX (device pointer, written)
- * Asynchronous on the handle's stream; the caller synchronises.  The first
- * call on a device looks up the array's device address (a one-time set-up per
- * device); make that first call before any stream capture.  Every call shares
- * the array, so calls that overlap on the GPU race; nothing in it needs to
- * start at zero.  Errors: LSD_EINVAL for NULL pointers, M < 1, or a network
- * whose SiLU' for one 128-row tile (layers x 128 x width x 2 bytes) exceeds
- * the 4 MiB array; LSD_EUNSUPPORTED when the target is not a BF16 MLP;
- * LSD_ECUDA if the launch or the address look-up fails. */
+ * Asynchronous on the handle's stream; the caller synchronises.  A bounded
+ * wait inside the kernel that gives up sets the handle's error state, which
+ * the next call that reads the handle's state reports (LSD_ETIMEOUT).  The
+ * first call on a device looks up the array's device address (a one-time
+ * set-up per device); make that first call before any stream capture.  Every
+ * call shares the array, so calls that overlap on the GPU race; nothing in it
+ * needs to start at zero.  Errors: LSD_EINVAL for NULL pointers, M < 1, or a
+ * network whose SiLU' for one 128-row tile exceeds the 4 MiB array;
+ * LSD_EUNSUPPORTED when the target has no MLP or its MLP runs on the CUDA
+ * cores (LSD_FP32_CUDA_CORES, or FP32 wider than 128); LSD_ECUDA if the
+ * launch or the address look-up fails. */
 LSD_API int lsd_target_mlp_static_dev(lsd_handle *h, const float *X_dev, int32_t M, float *E_dev, float *dEdX_dev);
 
 LSD_API void lsd_destroy(lsd_handle *h);

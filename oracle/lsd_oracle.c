@@ -434,6 +434,14 @@ static void o_mlp_backward(const o_potential *pot, int d0, const double *h, doub
 /* Potential energy and forces                                                */
 /* ------------------------------------------------------------------------- */
 
+/* Threads of the loops over independent configurations (a window's K target
+ * evaluations; o_eval_range); 1 (the default) runs them serially. */
+static int o_threads = 1;
+
+void o_set_threads(int32_t n) { o_threads = n > 0 ? n : 1; }
+
+int o_get_threads(void) { return o_threads; }
+
 #define O_NB_CAP 4096
 
 static void o_lj_pair(double eps, double sig, double rc, double r, double *U, double *dU) {
@@ -443,23 +451,21 @@ static void o_lj_pair(double eps, double sig, double rc, double r, double *U, do
     *dU = -24.0 * eps / r * (2.0 * sr12 - sr6);
 }
 
-/* E = sum of LJ (shifted, all periodic images within cutoff) + sum_i e(x_i)
- * + harmonic tether.  F = -dE/dq (+ the optional non-conservative shear field).
- * Optional outputs: per-atom energies, descriptors X [N][d0], dE/dX [N][d0].
- * Returns the total energy, or NAN when a neighbour list overflows. */
-double o_energy_forces(const o_system *sys, const o_potential *pot, const double *q, double *F, double *E_atom,
-                       double *X, double *dEdX) {
+/* The terms of the energy whose centre atom i lies in [i0, i1): the LJ pairs
+ * (i, j) (half of each pair's energy, the force on i) and e(x_i) with the
+ * forces of its descriptor terms on i and its neighbours; F and E_atom are
+ * accumulated, not cleared.  Over i in [0, N) this is every term of E. */
+static double o_energy_forces_range(const o_system *sys, const o_potential *pot, const double *q, int i0, int i1,
+                                    double *F, double *E_atom, double *X, double *dEdX) {
     int N = sys->n_atoms, ns = sys->n_species;
     double E = 0.0;
     o_fix *fx = (o_fix *)malloc(sizeof(o_fix) * (size_t)N);
     o_nb *nb = (o_nb *)malloc(sizeof(o_nb) * O_NB_CAP);
     o_fixpoint(sys, q, fx);
-    if (F) for (int k = 0; k < 3 * N; ++k) F[k] = 0.0;
-    if (E_atom) for (int i = 0; i < N; ++i) E_atom[i] = 0.0;
     int bad = 0;
 
     if (pot->lj_cutoff > 0.0) {
-        for (int i = 0; i < N; ++i) {
+        for (int i = i0; i < i1; ++i) {
             int n = o_list(sys, q, fx, i, pot->lj_cutoff, nb, O_NB_CAP);
             if (n < 0) { bad = 1; break; }
             int si = sys->species[i];
@@ -481,7 +487,7 @@ double o_energy_forces(const o_system *sys, const o_potential *pot, const double
         double *x = (double *)malloc(sizeof(double) * (size_t)d0);
         double *gx = (double *)malloc(sizeof(double) * (size_t)d0);
         double *h = (double *)malloc(sizeof(double) * (size_t)pot->n_layers * pot->width);
-        for (int i = 0; i < N && !bad; ++i) {
+        for (int i = i0; i < i1 && !bad; ++i) {
             int n = o_list(sys, q, fx, i, pot->desc_cutoff, nb, O_NB_CAP);
             if (n < 0) { bad = 1; break; }
             o_descriptor(sys, pot, i, nb, n, x);
@@ -531,6 +537,22 @@ double o_energy_forces(const o_system *sys, const o_potential *pot, const double
         free(gx);
         free(h);
     }
+    free(nb);
+    free(fx);
+    return bad ? NAN : E;
+}
+
+/* E = sum of LJ (shifted, all periodic images within cutoff) + sum_i e(x_i)
+ * + harmonic tether.  F = -dE/dq (+ the optional non-conservative shear field).
+ * Optional outputs: per-atom energies, descriptors X [N][d0], dE/dX [N][d0].
+ * Returns the total energy, or NAN when a neighbour list overflows. */
+double o_energy_forces(const o_system *sys, const o_potential *pot, const double *q, double *F, double *E_atom,
+                       double *X, double *dEdX) {
+    int N = sys->n_atoms;
+    if (F) for (int k = 0; k < 3 * N; ++k) F[k] = 0.0;
+    if (E_atom) for (int i = 0; i < N; ++i) E_atom[i] = 0.0;
+    double E = o_energy_forces_range(sys, pot, q, 0, N, F, E_atom, X, dEdX);
+    int bad = isnan(E);
 
     if (!bad && pot->k_harm > 0.0) {
         for (int k = 0; k < 3 * N; ++k) {
@@ -543,9 +565,29 @@ double o_energy_forces(const o_system *sys, const o_potential *pot, const double
     if (!bad && pot->shear != 0.0 && F) {
         for (int i = 0; i < N; ++i) F[3 * i + 0] += pot->shear * sin(2.0 * O_PI * q[3 * i + 1] / sys->box[1]);
     }
-    free(nb);
-    free(fx);
     return bad ? NAN : E;
+}
+
+/* The centre-atom terms [i0, i1) of the energy and forces (LJ + MLP
+ * potentials; no tether or shear field) of C configurations q [C][N][3]: F
+ * [C][N][3] and E [C] are cleared, then receive those terms.  The C
+ * configurations run on o_set_threads() threads, one configuration each, as
+ * in the window's verification loop.  Summed over the ranges of a partition
+ * of [0, N), this is o_energy_forces.  Used to time a bounded slice of an
+ * evaluation too large to run whole.  Returns 0, or -1 on a list overflow. */
+int o_eval_range(const o_system *sys, const o_potential *pot, int32_t C, const double *q, int32_t i0, int32_t i1,
+                 double *F, double *E) {
+    int N = sys->n_atoms;
+    if (i0 < 0 || i1 > N || i0 > i1 || C < 1) return -2;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(o_threads) if (o_threads > 1) reduction(| : bad)
+    for (int c = 0; c < C; ++c) {
+        double *Fc = F + (size_t)c * 3 * N;
+        for (int k = 0; k < 3 * N; ++k) Fc[k] = 0.0;
+        E[c] = o_energy_forces_range(sys, pot, q + (size_t)c * 3 * N, i0, i1, Fc, NULL, NULL, NULL);
+        bad |= isnan(E[c]);
+    }
+    return bad ? -1 : 0;
 }
 
 /* Forces on selected atoms only, one atom at a time, for systems too large
@@ -958,11 +1000,18 @@ int o_lsd_window(const o_system *sys, const o_potential *draft, const o_potentia
                     Fd + (size_t)j * D, mud + (size_t)j * D, qd + (size_t)j * D, pd + (size_t)j * D) != 0)
             ret = -1;
     }
-    /* verify every window step (Alg. 1 parallel loop) */
+    /* verify every window step (Alg. 1 parallel loop): the K target evaluations
+     * are independent, so with o_set_threads(n > 1) they run on n threads, each
+     * step's arithmetic unchanged (same result as one thread, bit for bit) */
+    double *Et = (double *)malloc(sizeof(double) * (size_t)K);
+    if (ret == 0) {
+#pragma omp parallel for schedule(dynamic, 1) num_threads(o_threads) if (o_threads > 1)
+        for (int j = 0; j < K; ++j)
+            Et[j] = o_energy_forces(sys, target, qmid + (size_t)j * D, Ft + (size_t)j * D, NULL, NULL, NULL);
+    }
     for (int j = 0; j < K && ret == 0; ++j) {
         const double *pin = (j == 0) ? p : pd + (size_t)(j - 1) * D;
-        double E = o_energy_forces(sys, target, qmid + (size_t)j * D, Ft + (size_t)j * D, NULL, NULL, NULL);
-        if (isnan(E)) { ret = -1; break; }
+        if (isnan(Et[j])) { ret = -1; break; }
         for (int k = 0; k < D; ++k) mut[k] = c.c1 * pin[k] + c.aF * Ft[(size_t)j * D + k];   /* <p>, Eq. 4 */
         double u = o_uniform(prm->seed, (uint64_t)(n0 + j + 1));
         o_verdict v = o_reflection_verify(sys, &c, u, pd + (size_t)j * D, mud + (size_t)j * D, mut,
@@ -996,7 +1045,7 @@ int o_lsd_window(const o_system *sys, const o_potential *draft, const o_potentia
         if (w_Fdraft) memcpy(w_Fdraft, Fd, sizeof(double) * KD);
         if (w_Ftarget) memcpy(w_Ftarget, Ft, sizeof(double) * KD);
     }
-    free(qmid); free(pd); free(qd); free(mud); free(Fd); free(Ft); free(mut); free(qx); free(px); free(acc);
+    free(qmid); free(pd); free(qd); free(mud); free(Fd); free(Ft); free(mut); free(qx); free(px); free(acc); free(Et);
     o_coef_free(&c);
     return ret == 0 ? n_commit : ret;
 }

@@ -31,7 +31,7 @@ _LIB_PATH = os.path.join(_HERE, "liblsd_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-fopenmp"]
 
 
 def build(force: bool = False) -> str:
@@ -82,6 +82,9 @@ def _L():
                 "o_mb_momenta": (None, [P, P, P]),
                 "o_transport": (ctypes.c_int, [I32, P, D, P, P, P, P, P]),
                 "o_transport_terms": (ctypes.c_int, [I32, P, D, P, P, P, P, P, P, P]),
+                "o_set_threads": (None, [I32]),
+                "o_eval_range": (ctypes.c_int, [P, P, I32, P, I32, I32, P, P]),
+                "o_get_threads": (ctypes.c_int, []),
                 "o_lsd_window": (ctypes.c_int, [P, P, P, P, I64, I32, I32, P, P, P, P, P, P, P, P, P, P, P, P, P]),
                 "o_lsd_run": (ctypes.c_int, [P, P, P, P, I64, I32, I32, P, P, P, P, P, P, P]),
                 "o_plain_run": (ctypes.c_int, [P, P, P, I64, P, P, P, P, P, P]),
@@ -283,6 +286,16 @@ def forces(system, pot, q):
 # transport, windows and trajectories
 # ----------------------------------------------------------------------------------------------
 
+def set_threads(n: int) -> None:
+    """Threads of a window's verification loop (its K target evaluations, one per thread); 1 runs it serially.
+    The results do not depend on the thread count."""
+    _L().o_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(_L().o_get_threads())
+
+
 def transport(sig, u, p_draft, mu_draft, mu_target):
     """reflectionVerify (Eq. 5) on flat vectors; returns (accept, p, log_ratio)."""
     sig = np.ascontiguousarray(sig, dtype=np.float64)
@@ -438,6 +451,25 @@ def force_match(system, draft, frames_q, frames_F, grad=True):
     g = np.zeros(len(draft.weights)) if grad else None
     loss = _L().o_force_match(ctypes.byref(s), ctypes.byref(pd_), int(nf), _ptr(fq), _ptr(fF), _ptr(g))
     return loss, g
+
+
+def eval_range(system, pot, qs, i0, i1):
+    """Centre-atom terms [i0, i1) of the energy and forces of configurations qs [C, N, 3] (run on set_threads()
+    threads, one configuration each): (F [C, N, 3], E [C]).  Summed over a partition of the atoms it is
+    energy_forces."""
+    keep = _Keep()
+    s = _csys(system, keep)
+    p = _cpot(pot, keep)
+    qq = keep.arr(qs, np.float64).reshape(-1, system.n_atoms, 3)
+    C = qq.shape[0]
+    F = np.zeros((C, system.n_atoms, 3))
+    E = np.zeros(C)
+    r = _L().o_eval_range(ctypes.byref(s), ctypes.byref(p), int(C), _ptr(qq), int(i0), int(i1), _ptr(F), _ptr(E))
+    if r == -2:
+        raise IndexError("atom range out of bounds")
+    if r != 0:
+        raise RuntimeError("oracle neighbour list overflow")
+    return F, E
 
 
 def forces_subset(system, pot, q, atoms):

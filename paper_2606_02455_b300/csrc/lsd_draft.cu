@@ -244,8 +244,10 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     uint4 *sfix = (uint4 *)(sstage + (LEARNED ? (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) : 0));  // [2][N]
     // displacement flags: [2] (cluster-barrier exchange) or [2][kMaxCluster], one slot per sending CTA
     int *sflag = (int *)(sfix + (stage_fix ? 2 * (size_t)N : 0));
-    uint64_t *sbar = (uint64_t *)(sflag + 2 * kMaxCluster);   // [2] exchange mbarriers (staged positions)
-    float *snoise = (float *)(sbar + 2);   // [K][A][3] when noise_smem: the window's xi, drawn up front
+    // [3] mbarriers: the two exchange barriers (staged positions, by step parity) and the exit barrier of a
+    // window that gave up waiting
+    uint64_t *sbar = (uint64_t *)(sflag + 2 * kMaxCluster);
+    float *snoise = (float *)(sbar + 3);   // [K][A][3] when noise_smem: the window's xi, drawn up front
     // Read-only per-atom data of owned atoms, staged once: a cluster barrier's
     // acquire leaves no global line in L1, so a per-step global read is an L2
     // round trip on the step's critical path.
@@ -283,6 +285,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     if (stage_fix && tid == 0) {
         tc::mbar_init(bar0, 1);
         tc::mbar_init(bar0 + 8, 1);
+        tc::mbar_init(bar0 + 16, C);
         tc::mbar_fence_init();
     }
     // bytes that land in this CTA per step: every atom's position, every CTA's flag
@@ -386,6 +389,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     if (stage_fix || use_list) cluster_barrier();
     __syncthreads();
     int keff = K;
+    bool gave_up = false;   // this CTA's wait for a step's positions ran out of time
     for (int j = 0; j < K; ++j) {
         const int par = j & 1;
         const unsigned long long n = (unsigned long long)(n0 + j + 1);
@@ -501,6 +505,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
             const int code = __syncthreads_or((ok ? 0 : 2) | (f ? 1 : 0));
             if (code) {
                 if ((code & 2) && tid == 0) atomicOr(&st->err, 8);
+                gave_up = (code & 2) != 0;
                 keff = j;
                 break;
             }
@@ -673,6 +678,26 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
         // its own global writes, and sF is rewritten only after the next cluster
         // barrier: no CTA barrier is needed here
     }
+    if (gave_up) {
+        // A CTA that gave up may still be the target of its peers' stores of the
+        // next step (they received this step's positions and went on).  Those
+        // peers then give up on that step themselves, two seconds later, and
+        // come here too: each CTA that gave up arrives on every CTA's exit
+        // barrier and waits, three times as long, for all C arrivals before it
+        // exits, so no peer that is still sending finds it gone.  Peers that
+        // stopped normally at this step send nothing more; the wait then runs
+        // out and the CTA exits (the window already carries the error bit).
+        if (tid < C)
+            asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(
+                             tc::cluster_map(bar0 + 16, (uint32_t)tid))
+                         : "memory");
+        if (tid == 0) {
+            const long long t0 = clock64();
+            while (!tc::mbar_try_wait_cluster(bar0 + 16, 0u) && clock64() - t0 < 12000000000ll) {
+            }
+        }
+        __syncthreads();
+    }
     if (c == 0 && tid == 0) {
         if (hdr) {
             hdr->k_eff = keff;
@@ -696,7 +721,7 @@ static size_t draft_smem_bytes(int N, int C, const PotDev &P, bool learned, bool
     if (stage_list) b += (size_t)A * (vcap + 1) * sizeof(int);
     if (learned) b += (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) * sizeof(float);
     if (stage_fix) b += 2 * (size_t)N * sizeof(uint4);
-    return b + 2 * kMaxCluster * sizeof(int) + 2 * sizeof(uint64_t) + (size_t)noise_K * A * 3 * sizeof(float);
+    return b + 2 * kMaxCluster * sizeof(int) + 3 * sizeof(uint64_t) + (size_t)noise_K * A * 3 * sizeof(float);
 }
 
 constexpr size_t kNoiseSmemMax = 32 * 1024;   // the window's noise is staged up front when it fits

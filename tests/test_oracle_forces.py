@@ -93,8 +93,40 @@ def test_bcc_lattice_sum_sees_every_image():
     assert np.allclose(res["F"], 0.0, atol=1e-14)
     nb = O.neighbors(s, s.positions, rc)
     assert len(nb[0]) == 8 and len(nb[1]) == 8
-    assert sorted(int(k) & 31 for k in nb[0]) == [c for c in range(27) if all(
-        d != 1 for d in (c % 3, (c // 3) % 3, c // 9))] or len(set(int(k) & 31 for k in nb[0])) == 8
+    # atom 1 sits at +L/2 of atom 0 on every axis: atom 0 sees atom 1 at shifts {0, -1} per axis, atom 1 sees
+    # atom 0 at shifts {0, +1}; code = (sx+1) + 3(sy+1) + 9(sz+1)
+    code = lambda sx, sy, sz: (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1)
+    r01 = sorted(code(a, b, c) for a in (-1, 0) for b in (-1, 0) for c in (-1, 0))
+    r10 = sorted(code(a, b, c) for a in (0, 1) for b in (0, 1) for c in (0, 1))
+    assert sorted(int(k) & 31 for k in nb[0]) == r01 and all(int(k) >> 5 == 1 for k in nb[0])
+    assert sorted(int(k) & 31 for k in nb[1]) == r10 and all(int(k) >> 5 == 0 for k in nb[1])
+
+
+def test_simple_cubic_lattice_sees_eighteen_image_neighbours():
+    """A simple cubic lattice of 2^3 atoms (spacing a) in a periodic box of side 2a, cutoff between sqrt(2) a and
+    sqrt(3) a: every atom sees its 6 first and 12 second neighbours, which are images of only 6 distinct atoms (the
+    two face neighbours along an axis are one atom at two shifts, each face-diagonal atom appears at four shifts).  The expected (atom, shift) set is the set
+    of lattice points within the cutoff; E = 8/2 (6 U(a) + 12 U(sqrt2 a)); F = 0 by symmetry."""
+    a, rc = 3.0, 4.6
+    L = 2 * a
+    g = np.array([[i, j, k] for i in range(2) for j in range(2) for k in range(2)], float)
+    pos = g * a + 0.25
+    s = W.System(positions=pos, momenta=np.zeros((8, 3)), species=np.zeros(8, np.int32), masses=np.array([40.0]),
+                 box=np.array([L] * 3))
+    pot = W.Potential(lj_eps=np.array([0.0104]), lj_sigma=np.array([3.4]), lj_cutoff=rc)
+    nb = O.neighbors(s, pos, rc)
+    code = lambda sh: (sh[0] + 1) + 3 * (sh[1] + 1) + 9 * (sh[2] + 1)
+    for i in range(8):
+        expect = sorted((j, code(sh)) for j in range(8) for sh in np.ndindex(3, 3, 3)
+                        if 0 < np.linalg.norm(pos[j] + (np.array(sh) - 1) * L - pos[i]) < rc
+                        for sh in [tuple(np.array(sh) - 1)])
+        got = sorted((int(k) >> 5, int(k) & 31) for k in nb[i])
+        assert len(got) == 18 and got == expect, i
+        assert len({j for j, _ in got}) == 6
+    res = O.energy_forces(s, pot, pos)
+    assert res["E"] == pytest.approx(4 * (6 * _lj(0.0104, 3.4, rc, a) + 12 * _lj(0.0104, 3.4, rc, np.sqrt(2) * a)),
+                                     rel=1e-12)
+    assert np.allclose(res["F"], 0.0, atol=1e-13)
 
 
 def test_radial_descriptor_two_atoms():
@@ -231,3 +263,24 @@ def test_forces_on_selected_atoms_with_images():
     F = O.forces(s, pot, s.positions)
     Fs = O.forces_subset(s, pot, s.positions, [0, 1, 2, 3])
     assert np.allclose(Fs, F, rtol=1e-11, atol=1e-14)
+
+
+def test_centre_atom_ranges_partition_the_evaluation():
+    """The centre-atom ranges of o_eval_range sum to the full energy and forces (every LJ pair and every e(x_i)
+    term has exactly one centre atom), on several configurations at once and on several threads."""
+    w = W.config2()
+    s = w.system
+    rng = np.random.default_rng(3)
+    qs = np.stack([s.positions + 0.05 * rng.standard_normal(s.positions.shape) for _ in range(3)])
+    cuts = [0, 37, 128, 200, 256]
+    O.set_threads(3)
+    try:
+        parts = [O.eval_range(s, w.target, qs, a, b) for a, b in zip(cuts[:-1], cuts[1:])]
+    finally:
+        O.set_threads(1)
+    for c in range(3):
+        ref = O.energy_forces(s, w.target, qs[c], want=("F",))
+        F = sum(p[0][c] for p in parts)
+        E = sum(p[1][c] for p in parts)
+        assert E == pytest.approx(ref["E"], rel=1e-12, abs=1e-12)
+        assert np.allclose(F, ref["F"], rtol=1e-11, atol=1e-12)

@@ -164,3 +164,21 @@ def test_predicted_rejections_match_observed():
     mean = st["pred_rejected"]
     var = mean * (1 - mean / st["committed"])
     assert abs(st["rejected"] - mean) < 4 * np.sqrt(var) + 1
+
+
+def test_window_parallel_verification_equals_serial():
+    """The oracle's window-parallel variant (the K target evaluations of a window on several threads, the CPU
+    analogue of the batched verification) gives the serial result bit for bit."""
+    w = W.config1()
+    s = w.system
+    target = W.replace(w.target, head_scale=1.5)
+    O.set_threads(1)
+    a = O.lsd_window(s, w.draft, target, w.integ, s.seed, 0, w.integ.K, s.positions, s.momenta)
+    O.set_threads(4)
+    try:
+        b = O.lsd_window(s, w.draft, target, w.integ, s.seed, 0, w.integ.K, s.positions, s.momenta)
+    finally:
+        O.set_threads(1)
+    for k in ("qmid", "pdraft", "Ftarget", "logr", "accept", "q", "p"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["n_committed"] == b["n_committed"]

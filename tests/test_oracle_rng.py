@@ -50,3 +50,23 @@ def test_streams_and_keys_differ():
     assert not np.array_equal(a, O.normals(1, 6, 3, 0))
     assert not np.array_equal(a, O.normals(1, 5, 4, 0))
     assert not np.array_equal(a, O.normals(1, 5, 3, 2))
+
+
+def test_uniform_and_normals_bit_layout():
+    """The acceptance uniform of step n is ((w0 >> 5) 2^26 + (w1 >> 6) + 1) / 2^53 of the Philox words of counter
+    (n_lo, n_hi, 0, 1) under key (seed_lo, seed_hi); the normals of (n, atom, stream) are Box-Muller on
+    u1 = ((w0 >> 9) + 1/2) / 2^23, u2 = (w1 >> 9) / 2^23 (x, y) and on words 2, 3 (z).  The words come from the
+    Philox implementation pinned by the published known-answer vectors above."""
+    import math
+    for seed, n in ((12345, 1), (12345, 7), (2 ** 40 + 17, 2 ** 33 + 5), (0, 1)):
+        w = [int(x) for x in O.philox4x32_10([n & 0xFFFFFFFF, n >> 32, 0, 1], [seed & 0xFFFFFFFF, seed >> 32])]
+        m = (w[0] >> 5) * 2 ** 26 + (w[1] >> 6) + 1
+        assert O.uniform(seed, n) == m / 2.0 ** 53
+        for atom, stream in ((0, 0), (5, 0), (3, 2)):
+            w = [int(x) for x in O.philox4x32_10([n & 0xFFFFFFFF, n >> 32, atom, stream],
+                                                 [seed & 0xFFFFFFFF, seed >> 32])]
+            u1, u2 = ((w[0] >> 9) + 0.5) / 2 ** 23, (w[1] >> 9) / 2 ** 23
+            u3, u4 = ((w[2] >> 9) + 0.5) / 2 ** 23, (w[3] >> 9) / 2 ** 23
+            r1, r2 = math.sqrt(-2 * math.log(u1)), math.sqrt(-2 * math.log(u3))
+            expect = [r1 * math.cos(2 * math.pi * u2), r1 * math.sin(2 * math.pi * u2), r2 * math.cos(2 * math.pi * u4)]
+            assert np.allclose(O.normals(seed, n, atom, stream), expect, rtol=1e-14, atol=1e-15)
