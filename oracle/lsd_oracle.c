@@ -225,11 +225,33 @@ typedef struct { int32_t j; int32_t code; double d[3]; double r; } o_nb;
 
 /* Brute-force neighbour list of atom i within rc, in canonical order
  * (neighbour index ascending, then shift code ascending). */
+/* A conservative pre-test that changes no list: along every axis each image
+ * other than the minimum one is at least as far as it (|d0| <= 2^31, so the
+ * minimum-image displacement is at most L/2), so when the minimum-image
+ * distance, in FP64 from the same fixed-point coordinates, exceeds the cutoff
+ * by more than the rule's FP32 rounding could hide (1e-5 relative, against a
+ * few 1e-7), no image of j passes the rule.  o_set_list_prefilter(0) turns it
+ * off (the tests compare both). */
+static int o_prefilter = 1;
+
+void o_set_list_prefilter(int32_t on) { o_prefilter = on != 0; }
+
+static int o_beyond(const o_system *sys, const o_fix *fx, int i, int j, double rc2) {
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        int32_t d0 = (int32_t)(uint32_t)(fx[j].u[a] - fx[i].u[a]);
+        double d = (double)d0 * (sys->box[a] / O_TWO32);
+        d2 += d * d;
+    }
+    return d2 > rc2 * (1.0 + 1e-5);
+}
+
 static int o_list(const o_system *sys, const double *q, const o_fix *fx, int i, double rc, o_nb *out,
                   int cap) {
     float rc2f = (float)(rc * rc);
     int n = 0;
     for (int j = 0; j < sys->n_atoms; ++j) {
+        if (o_prefilter && j != i && o_beyond(sys, fx, i, j, rc * rc)) continue;
         for (int code = 0; code < 27; ++code) {
             int s[3] = {code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1};
             if (j == i && code == 13) continue;

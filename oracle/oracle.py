@@ -83,6 +83,7 @@ def _L():
                 "o_transport": (ctypes.c_int, [I32, P, D, P, P, P, P, P]),
                 "o_transport_terms": (ctypes.c_int, [I32, P, D, P, P, P, P, P, P, P]),
                 "o_set_threads": (None, [I32]),
+                "o_set_list_prefilter": (None, [I32]),
                 "o_eval_range": (ctypes.c_int, [P, P, I32, P, I32, I32, P, P]),
                 "o_get_threads": (ctypes.c_int, []),
                 "o_lsd_window": (ctypes.c_int, [P, P, P, P, I64, I32, I32, P, P, P, P, P, P, P, P, P, P, P, P, P]),
@@ -290,6 +291,12 @@ def set_threads(n: int) -> None:
     """Threads of a window's verification loop (its K target evaluations, one per thread); 1 runs it serially.
     The results do not depend on the thread count."""
     _L().o_set_threads(int(n))
+
+
+def set_list_prefilter(on: bool) -> None:
+    """The conservative minimum-image pre-test of the neighbour lists (on by default; lists are the same either
+    way)."""
+    _L().o_set_list_prefilter(int(bool(on)))
 
 
 def get_threads() -> int:

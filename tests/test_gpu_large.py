@@ -79,3 +79,56 @@ def test_config4_runs_many_windows():
     q, p, step = h.get_state()
     assert step == 200 and np.isfinite(q).all() and np.isfinite(p).all()
     h.close()
+
+
+def test_config4_window_decisions_match_oracle():
+    """One full config-4 window (4,096 atoms, K = 32) against the oracle's window from the same seeded state, with
+    the target network in FP32 arithmetic (the CUDA-core MLP: the BF16 and FP8 arithmetic define other targets,
+    whose errors against FP64 are stated per result).  Forces within the FP32 bar per window step; each step's log
+    ratio equals the oracle's plus the part its own forces explain: with delta_g - delta_o = e (from the two sides'
+    forces), log r_g - log r_o = -z.e - delta_o.e - |e|^2/2 up to the noise error 1e-6 |delta|_1; decisions
+    identical wherever |log u - min(0, log r)| exceeds that band, and the committed count identical when no
+    decision up to the first rejection lies inside it.  At 12,288 components the FP32 force error moves log r by
+    ~1e-3, so the band is per step, not a fixed tolerance."""
+    import os
+    from paper_2606_02455_b300 import lsd
+    from parity_bounds import FORCE_TOL, XI_ERR, elem, rel
+    w = W.config4()
+    s, K = w.system, w.integ.K
+    target = W.replace(w.target, precision="fp32-cuda-cores")
+    h = lsd.LSD(s, w.draft, target, w.integ)
+    h.draft_window()
+    nc, first = h.verify_window()
+    win = h.get_window()
+    h.close()
+    O.set_threads(os.cpu_count() or 1)
+    try:
+        ref = O.lsd_window(s, w.draft, target, w.integ, s.seed, 0, K, s.positions, s.momenta)
+    finally:
+        O.set_threads(1)
+    c1, aF, hm, sg = O.coefficients(s, w.integ)
+    k = (aF / sg[s.species])[:, None]
+    ties = 0
+    tie_before_first = False
+    l_ref = int(ref["n_committed"])
+    for j in range(K):
+        for key_g, key_o in (("F_draft", "Fdraft"), ("F_target", "Ftarget")):
+            assert rel(win[key_g][j], ref[key_o][j]) < FORCE_TOL, (key_g, j)
+            assert elem(win[key_g][j], ref[key_o][j]) < FORCE_TOL, (key_g, j)
+        d_o = k * (ref["Fdraft"][j] - ref["Ftarget"][j])
+        d_g = k * (win["F_draft"][j].astype(np.float64) - win["F_target"][j].astype(np.float64))
+        e = d_g - d_o
+        z = np.stack([O.normals(s.seed, j + 1, i, 0) for i in range(s.n_atoms)])
+        expect = ref["logr"][j] - np.sum(z * e) - np.sum(d_o * e) - 0.5 * np.sum(e * e)
+        band = XI_ERR * np.abs(d_g).sum() + 1e-9 * (1.0 + abs(ref["logr"][j]))
+        assert abs(win["log_ratio"][j] - expect) <= band, (j, win["log_ratio"][j], expect, band)
+        explained = abs(np.sum(z * e) + np.sum(d_o * e) + 0.5 * np.sum(e * e)) + band
+        margin = abs(ref["logu"][j] - min(0.0, ref["logr"][j]))
+        if margin <= explained:
+            ties += 1
+            tie_before_first = tie_before_first or j < l_ref
+            continue
+        assert win["accept"][j] == ref["accept"][j], j
+    assert ties <= 2, ties
+    if not tie_before_first:
+        assert nc == l_ref and first == (-1 if ref["accept"].all() else int(np.argmin(ref["accept"])) + 1)

@@ -284,3 +284,32 @@ def test_centre_atom_ranges_partition_the_evaluation():
         E = sum(p[1][c] for p in parts)
         assert E == pytest.approx(ref["E"], rel=1e-12, abs=1e-12)
         assert np.allclose(F, ref["F"], rtol=1e-11, atol=1e-12)
+
+
+def test_list_prefilter_changes_no_list():
+    """The oracle's minimum-image pre-test only skips pairs the membership rule rejects: lists with and without
+    it are identical, on the benchmark systems, on a box whose cutoff is 0.97 of its side (every image along every
+    axis in play) and on pairs placed within 1e-6 of the cutoff."""
+    rng = np.random.default_rng(8)
+    cases = []
+    w = W.config2()
+    cases.append((w.system, w.system.positions + 0.1 * rng.standard_normal(w.system.positions.shape), 5.0))
+    w = W.config1()
+    cases.append((w.system, w.system.positions, 8.5))
+    small = W.small_system(1, 5.0, 2)
+    cases.append((small, small.positions, 0.97 * 5.0))
+    rc = 4.0
+    pos = np.array([[1.0, 1.0, 1.0], [1.0 + rc * (1 - 1e-6), 1.0, 1.0], [1.0, 1.0 + rc * (1 + 1e-6), 1.0],
+                    [1.0, 1.0, 1.0 + rc]])
+    tiny = W.System(positions=pos, momenta=np.zeros((4, 3)), species=np.zeros(4, np.int32), masses=np.array([1.0]),
+                    box=np.array([12.0, 12.0, 12.0]))
+    cases.append((tiny, pos, rc))
+    for sysm, q, cut in cases:
+        O.set_list_prefilter(True)
+        a = O.neighbors(sysm, q, cut)
+        O.set_list_prefilter(False)
+        try:
+            b = O.neighbors(sysm, q, cut)
+        finally:
+            O.set_list_prefilter(True)
+        assert all(np.array_equal(x, y) for x, y in zip(a, b))
