@@ -162,6 +162,10 @@ def _lj_pairs_per_atom(w, q):
 # DRAM bytes (read + write) of one launch, from one ncu capture of the kernel as it is now (the summaries under
 # profiles/ give the command); a kernel changed since its capture has no entry here.
 NCU_TRAFFIC = {
+    # pairgrad_kernel<8>: 144,895,744 B per launch captured on the 4,096-atom workload (131,072 rows); the pair
+    # gradients and staged geometry scale with rows, so one 2,097,152-row launch moves 16x that
+    ("fp8_mlp_32768atoms_K64", "pair_grad"): 16 * 144895744,
+    ("bf16_mlp_4096atoms_K32", "pair_grad"): 144895744,
 }
 
 

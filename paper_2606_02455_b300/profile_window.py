@@ -1,0 +1,41 @@
+"""Runs LSD windows of a benchmark configuration, for profilers (ncu) and quick timing.
+
+    python -m paper_2606_02455_b300.profile_window --config 4 [--K 32] [--windows 2] [--equil 0] [--pipelined]
+
+Builds one handle for the configuration (window length K overridable, to keep a profiled footprint small),
+optionally runs `equil` plain target steps, then `windows` windows through lsd_enqueue_windows on the handle's
+stream, and prints the per-phase CUDA-event times of one more window (lsd_profile_window) and the run's counters.
+The first kernels a handle launches are its set-up (the FP8 and FP32-split calibration runs the MLP once on N
+rows); window kernels follow.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+from . import lsd, workloads as W
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--config", type=int, default=4)
+    ap.add_argument("--K", type=int, default=0, help="window length (0: the configuration's)")
+    ap.add_argument("--windows", type=int, default=2)
+    ap.add_argument("--equil", type=int, default=0)
+    ap.add_argument("--pipelined", action="store_true")
+    a = ap.parse_args()
+    w = W.CONFIGS[a.config](a.K) if a.K else W.CONFIGS[a.config]()
+    h = lsd.LSD(w.system, w.draft, w.target, w.integ)
+    if a.equil:
+        h.plain_step(a.equil)
+    h.set_pipelining(a.pipelined)
+    h.enqueue_windows(a.windows)
+    st = h.stats()
+    ph = h.profile_window()
+    print(json.dumps({"workload": w.name, "windows": st["windows"], "committed": st["committed"],
+                      "phases_ms": {k: round(v, 4) for k, v in ph.items()}}))
+    h.close()
+
+
+if __name__ == "__main__":
+    main()

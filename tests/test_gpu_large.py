@@ -88,7 +88,8 @@ def test_config4_window_decisions_match_oracle():
     ratio equals the oracle's plus the part its own forces explain: with delta_g - delta_o = e (from the two sides'
     forces), log r_g - log r_o = -z.e - delta_o.e - |e|^2/2 up to the noise error 1e-6 |delta|_1; decisions
     identical wherever |log u - min(0, log r)| exceeds that band, and the committed count identical when no
-    decision up to the first rejection lies inside it.  At 12,288 components the FP32 force error moves log r by
+    decision up to the first rejection lies inside it.  The GPU's window may end early (k_eff < K, when an atom
+    leaves its lists' skin); the oracle's steps past k_eff are not compared.  At 12,288 components the FP32 force error moves log r by
     ~1e-3, so the band is per step, not a fixed tolerance."""
     import os
     from paper_2606_02455_b300 import lsd
@@ -100,7 +101,11 @@ def test_config4_window_decisions_match_oracle():
     h.draft_window()
     nc, first = h.verify_window()
     win = h.get_window()
+    # the draft ends the window early once an atom has moved 0.45 skin from its lists' base (a stopping time):
+    # the light atoms of this system often do; steps past k_eff were not drafted
+    k_eff = h.stats()["verified"]
     h.close()
+    assert 1 <= k_eff <= K
     O.set_threads(os.cpu_count() or 1)
     try:
         ref = O.lsd_window(s, w.draft, target, w.integ, s.seed, 0, K, s.positions, s.momenta)
@@ -110,8 +115,8 @@ def test_config4_window_decisions_match_oracle():
     k = (aF / sg[s.species])[:, None]
     ties = 0
     tie_before_first = False
-    l_ref = int(ref["n_committed"])
-    for j in range(K):
+    l_ref = min(int(ref["n_committed"]), k_eff)
+    for j in range(k_eff):
         for key_g, key_o in (("F_draft", "Fdraft"), ("F_target", "Ftarget")):
             assert rel(win[key_g][j], ref[key_o][j]) < FORCE_TOL, (key_g, j)
             assert elem(win[key_g][j], ref[key_o][j]) < FORCE_TOL, (key_g, j)
@@ -131,4 +136,5 @@ def test_config4_window_decisions_match_oracle():
         assert win["accept"][j] == ref["accept"][j], j
     assert ties <= 2, ties
     if not tie_before_first:
-        assert nc == l_ref and first == (-1 if ref["accept"].all() else int(np.argmin(ref["accept"])) + 1)
+        acc = ref["accept"][:k_eff]
+        assert nc == l_ref and first == (-1 if acc.all() else int(np.argmin(acc)) + 1)
