@@ -413,13 +413,14 @@ void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, f
     const int M = Kc * h->N;
     const PotDev &P = pot.dev;
     if (!vb) vb = &h->vbufs;
+    const int *keff_rows = keff;   // window paths: rows past the draft's k_eff stay empty (null: every row)
     if (!keff) keff = &h->st->k_eff;
     if (use_list)
         launch_neigh_list(fix, vb->vlist, vb->vcount, h->vplan.cap, M, h->geo, pot.rmax2f, pot.near2f,
                           h->cap_near, h->cap_far, h->near_keys, h->far_keys, h->n_near, h->n_far, h->st, keff, s);
     else
         launch_neigh_build(fix, M, h->geo, pot.rmax2f, pot.near2f, h->cap_near, h->cap_far, h->near_keys,
-                           h->far_keys, h->n_near, h->n_far, h->st, s);
+                           h->far_keys, h->n_near, h->n_far, h->st, s, keff_rows);
     if (P.has_mlp) {
         launch_desc(fix, h->near_keys, h->n_near, h->cap_near, M, h->geo, P, h->X, s);
         enqueue_mlp(h, pot, M, s);
@@ -1315,7 +1316,7 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
     CK(cudaEventRecord(ev[1], st));
     if (h->vplan.all_pairs)
         launch_neigh_build(h->w_fix, M, h->geo, h->target.rmax2f, h->target.near2f, h->cap_near, h->cap_far,
-                           h->near_keys, h->far_keys, h->n_near, h->n_far, h->st, st);
+                           h->near_keys, h->far_keys, h->n_near, h->n_far, h->st, st, &h->st->k_eff);
     else
         launch_neigh_list(h->w_fix, h->vbufs.vlist, h->vbufs.vcount, h->vplan.cap, M, h->geo, h->target.rmax2f,
                           h->target.near2f, h->cap_near, h->cap_far, h->near_keys, h->far_keys, h->n_near, h->n_far,

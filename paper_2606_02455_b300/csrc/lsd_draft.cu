@@ -165,10 +165,15 @@ __device__ void learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
         gh = __bfloat162float(P.wout_bf[lane]) * dsiluf_(h);   // linear head: dE/dy = 1
     }
     __syncwarp();
-    for (int f = 0; f < P.d0p; ++f) {
-        float v = (lane < W && f < P.d0) ? __bfloat162float(P.Wn_bf[0][(size_t)lane * P.d0p + f]) * gh : 0.f;
-        v = warp_sum(v);
-        if (lane == 0) g_out[f] = v;
+    // dE/dx_f = sum_u W[u][f] gh_u: lane f over the hidden units, gh_u handed round by shuffles
+    for (int f0 = 0; f0 < P.d0p; f0 += 32) {
+        const int f = f0 + lane;
+        float v = 0.f;
+        for (int u = 0; u < W; ++u) {
+            const float gu = __shfl_sync(0xffffffffu, gh, u);
+            if (f < P.d0) v = fmaf(__bfloat162float(P.Wn_bf[0][(size_t)u * P.d0p + f]), gu, v);
+        }
+        if (f < P.d0p) g_out[f] = v;
     }
     __syncwarp();
 }
@@ -223,7 +228,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     draft_window_cluster_kernel(int K, Geo g, PotDev P, Coef cf, const int *__restrict__ vlist,
                                 const int *__restrict__ vcount, int vcap, const uint4 *__restrict__ fix_base,
                                 float move2f, float rlist2f, int stage_fix, int minimg, int noise_smem,
-                                int stage_list, int self_list,
+                                int stage_list, int self_list, int stage_dedx,
                                 const int *__restrict__ species,
                                 const double *__restrict__ q_base, const double *__restrict__ p_base,
                                 const float *__restrict__ ec_dF, int ec_on, DevState *__restrict__ st,
@@ -254,6 +259,8 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     int *sspec = (int *)(snoise + (noise_smem ? (size_t)K * A * 3 : 0));   // [A] species
     int *svc = sspec + A;                                                  // [A] list lengths (stage_list)
     int *svl = svc + A;                                                    // [A][vcap] lists (stage_list)
+    // learned draft, small systems: the radial dE/dX of every atom, [N][S n_rbf], staged once per step
+    float *sdedx = (float *)(sspec + A + (stage_list ? (size_t)A * (vcap + 1) : 0));
     // the base step: the committed one, or (pipelined loop) the window header's;
     // a redraft runs only when the speculative draft of this window does not
     // stand, from the committed state.  Uniform over the cluster: the header is
@@ -528,6 +535,14 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                                   minimg != 0, stage, stage + 3 * kLearnCap, w_dEdX + (size_t)i * P.d0p);
             }
             cluster_barrier();   // dE/dx of every atom visible to every CTA
+            if (stage_dedx) {
+                // the radial block of every atom's dE/dX into shared memory: one coalesced pass
+                // instead of two L2 round trips per neighbour pair and basis function
+                const int SR = g.S * P.n_rbf;
+                for (int e = tid; e < N * SR; e += blockDim.x)
+                    sdedx[e] = __ldcg(w_dEdX + (size_t)(e / SR) * P.d0p + (e % SR));
+                __syncthreads();
+            }
         }
         // C: forces on owned atoms, one warp per atom, lanes over its candidates
         for (int ii = warp; ii < nown; ii += kDraftWarps) {
@@ -606,13 +621,24 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                         const float r = sqrtf(d2);
                         float fc, dfc;
                         cutoff_fn(r, P.desc_rc, fc, dfc);
-                        const float *gi = w_dEdX + (size_t)i * P.d0p + (int)fk.w * P.n_rbf;
-                        const float *gk = w_dEdX + (size_t)k * P.d0p + si * P.n_rbf;
                         float cc = 0.f;
-                        for (int b = 0; b < P.n_rbf; ++b) {
-                            const float tt = r - (float)b * P.rbf_w;
-                            const float dg = expf(-tt * tt * P.rbf_inv2w2) * (-tt * P.rbf_invw2 * fc + dfc);
-                            cc += (__ldcg(gi + b) + __ldcg(gk + b)) * dg;
+                        if (stage_dedx) {
+                            const int SR = g.S * P.n_rbf;
+                            const float *gi = sdedx + (size_t)i * SR + (int)fk.w * P.n_rbf;
+                            const float *gk = sdedx + (size_t)k * SR + si * P.n_rbf;
+                            for (int b = 0; b < P.n_rbf; ++b) {
+                                const float tt = r - (float)b * P.rbf_w;
+                                const float dg = expf(-tt * tt * P.rbf_inv2w2) * (-tt * P.rbf_invw2 * fc + dfc);
+                                cc += (gi[b] + gk[b]) * dg;
+                            }
+                        } else {
+                            const float *gi = w_dEdX + (size_t)i * P.d0p + (int)fk.w * P.n_rbf;
+                            const float *gk = w_dEdX + (size_t)k * P.d0p + si * P.n_rbf;
+                            for (int b = 0; b < P.n_rbf; ++b) {
+                                const float tt = r - (float)b * P.rbf_w;
+                                const float dg = expf(-tt * tt * P.rbf_inv2w2) * (-tt * P.rbf_invw2 * fc + dfc);
+                                cc += (__ldcg(gi + b) + __ldcg(gk + b)) * dg;
+                            }
                         }
                         fxx += cc * dx / r;
                         fyy += cc * dy / r;
@@ -712,7 +738,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
 }
 
 static size_t draft_smem_bytes(int N, int C, const PotDev &P, bool learned, bool stage_fix, int noise_K, int vcap,
-                               bool stage_list) {
+                               bool stage_list, size_t dedx_floats) {
     // vcap > 0: lists (global or built in the kernel), each CTA's list bases staged
     const int A = (N + C - 1) / C;
     size_t b = (size_t)A * sizeof(float4) + 2 * kMaxSpecies * kMaxSpecies * sizeof(float);
@@ -721,11 +747,13 @@ static size_t draft_smem_bytes(int N, int C, const PotDev &P, bool learned, bool
     if (stage_list) b += (size_t)A * (vcap + 1) * sizeof(int);
     if (learned) b += (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) * sizeof(float);
     if (stage_fix) b += 2 * (size_t)N * sizeof(uint4);
-    return b + 2 * kMaxCluster * sizeof(int) + 3 * sizeof(uint64_t) + (size_t)noise_K * A * 3 * sizeof(float);
+    return b + 2 * kMaxCluster * sizeof(int) + 3 * sizeof(uint64_t) + (size_t)noise_K * A * 3 * sizeof(float) +
+           dedx_floats * sizeof(float);
 }
 
 constexpr size_t kNoiseSmemMax = 32 * 1024;   // the window's noise is staged up front when it fits
 constexpr size_t kListSmemMax = 64 * 1024;    // owned atoms' Verlet lists are staged when they fit
+constexpr size_t kDedxSmemMax = 48 * 1024;    // the learned draft's radial dE/dX of all atoms, staged when it fits
 
 DraftPlan draft_plan(int N, int K, const PotDev &P, bool learned, int vcap, bool all_pairs, int max_cluster,
                      size_t max_smem) {
@@ -746,7 +774,12 @@ DraftPlan draft_plan(int N, int K, const PotDev &P, bool learned, int vcap, bool
         vcap = 0;   // every atom is a candidate; no lists at all
         pl.stage_list = false;
     }
-    pl.smem = draft_smem_bytes(N, C, P, learned, pl.stage_fix, pl.noise_smem ? K : 0, vcap, pl.stage_list);
+    // the learned draft's radial dE/dX of every atom, staged per step when it is small
+    const int S = P.n_rbf > 0 ? (P.d0 - P.n_ang) / (P.n_rbf + 1) : 0;
+    const size_t dedx = (size_t)N * S * P.n_rbf;
+    pl.stage_dedx = learned && dedx > 0 && dedx * sizeof(float) <= kDedxSmemMax;
+    pl.smem = draft_smem_bytes(N, C, P, learned, pl.stage_fix, pl.noise_smem ? K : 0, vcap, pl.stage_list,
+                               pl.stage_dedx ? dedx : 0);
     pl.reg = (N + C - 1) / C <= kRegPasses * kGroups;
     pl.ok = pl.smem <= max_smem;
     return pl;
@@ -775,10 +808,11 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
     const int ns = (pl.noise_smem && K <= pl.K) ? 1 : 0;
     const int self = (pl.self_list && vp.all_pairs) ? 1 : 0;
     const int sl = (pl.stage_list && (vl || self)) ? 1 : 0;
+    const int sd = (learned && pl.stage_dedx) ? 1 : 0;
     auto kern = learned ? (pl.reg ? draft_window_cluster_kernel<true, true> : draft_window_cluster_kernel<true, false>)
                         : (pl.reg ? draft_window_cluster_kernel<false, true> : draft_window_cluster_kernel<false, false>);
     return cudaLaunchKernelEx(&cfg, kern, K, g, P, cf, vl, (const int *)vb.vcount, vp.cap, (const uint4 *)vb.fix_base,
-                              vp.move2f, vp.rlist2f, stage, mi, ns, sl, self, species, q, p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd,
+                              vp.move2f, vp.rlist2f, stage, mi, ns, sl, self, sd, species, q, p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd,
                               w_Fraw, w_fix, w_dEdX, hdr, redraft);
 }
 

@@ -31,7 +31,8 @@ inline void launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block, size
 // verification (lsd_verify.cu)
 void launch_fixpoint(const double *q, const int *species, int M, const Geo &g, uint4 *fix, cudaStream_t s);
 void launch_neigh_build(const uint4 *fix, int M, const Geo &g, float rmax2f, float near2f, int cap_near, int cap_far,
-                        int *near_keys, int *far_keys, int *n_near, int *n_far, DevState *st, cudaStream_t s);
+                        int *near_keys, int *far_keys, int *n_near, int *n_far, DevState *st, cudaStream_t s,
+                        const int *keff = nullptr);
 void launch_desc(const uint4 *fix, const int *near_keys, const int *n_near, int cap, int M, const Geo &g,
                  const PotDev &P, float *X, cudaStream_t s);
 void launch_pairgrad(const uint4 *fix, const int *near_keys, const int *n_near, const int *far_keys, const int *n_far,
@@ -122,6 +123,7 @@ struct DraftPlan {
     bool noise_smem;  // the window's noise drawn up front into shared memory
     bool stage_list;  // owned atoms' Verlet lists copied to shared memory once per launch
     bool self_list;   // no cell grid: the kernel lists its atoms' candidates itself (in shared memory)
+    bool stage_dedx;  // learned draft: every atom's radial dE/dX staged in shared memory each step
     int K;            // window length the plan was made for
     bool ok;
 };

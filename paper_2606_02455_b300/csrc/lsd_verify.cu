@@ -25,8 +25,9 @@ namespace lsd {
 // by (k, code) without a sort.
 // ---------------------------------------------------------------------------
 // LIST = false: candidates are all atoms of the window step (any configuration);
-// LIST = true: candidates are the atom's sorted Verlet list, and rows of window
-// steps the draft did not reach (j >= k_eff) are left empty.
+// LIST = true: candidates are the atom's sorted Verlet list.  With keff (the
+// window paths) rows of window steps the draft did not reach (j >= k_eff) are
+// left empty; without it (explicit configurations) every row is built.
 // MINIMG (the cutoff below 0.499 of every box side): only the minimum image
 // of a candidate can pass the rule (any other image along an axis is at least
 // L/2, less rounding, away), and an atom's own images are beyond the cutoff, so
@@ -44,7 +45,7 @@ __global__ void neigh_build_kernel(const uint4 *__restrict__ fix, const int *__r
     if (row >= M) return;
     const int N = g.N;
     const int j = row / N, i = row - j * N;
-    if (LIST && j >= *keff) {
+    if (keff && j >= *keff) {
         if (lane == 0) {
             n_near[row] = 0;
             n_far[row] = 0;
@@ -598,12 +599,13 @@ static bool min_image_only(const Geo &g, float rmax2f) {
 }
 
 void launch_neigh_build(const uint4 *fix, int M, const Geo &g, float rmax2f, float near2f, int cap_near, int cap_far,
-                        int *near_keys, int *far_keys, int *n_near, int *n_far, DevState *st, cudaStream_t s) {
+                        int *near_keys, int *far_keys, int *n_near, int *n_far, DevState *st, cudaStream_t s,
+                        const int *keff) {
     const int threads = 256;
     const int blocks = (int)(((size_t)M * 32 + threads - 1) / threads);
     auto k = min_image_only(g, rmax2f) ? neigh_build_kernel<false, true> : neigh_build_kernel<false, false>;
     launch_dependent(k, blocks, threads, 0, s, fix, nullptr, nullptr, 0, M, g, rmax2f, near2f, cap_near, cap_far,
-                     near_keys, far_keys, n_near, n_far, st, (const int *)nullptr);
+                     near_keys, far_keys, n_near, n_far, st, keff);
 }
 
 void launch_neigh_list(const uint4 *fix, const int *vlist, const int *vcount, int vcap, int M, const Geo &g,

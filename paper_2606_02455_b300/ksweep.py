@@ -25,6 +25,10 @@ def _measure(cfg: int, K: int, windows: int, equil: int):
     from . import lsd
     w = W.CONFIGS[cfg](K)
     h = lsd.LSD(w.system, w.draft, w.target, w.integ)
+    # a stream of its own (set before the warm-up: a new stream rebuilds the graphs): the legacy default stream
+    # would hand the library its own non-blocking stream, which the events below would not see
+    stream = torch.cuda.Stream()
+    h.set_stream(stream)
     h.plain_step(equil)
     for _ in range(3):
         h.profile_window()
@@ -34,10 +38,9 @@ def _measure(cfg: int, K: int, windows: int, equil: int):
             ph[k] = ph.get(k, 0.0) + v / 10
     t_draft = ph["draft"] * 1e-3 / K
     t_verify = sum(v for k, v in ph.items() if k != "draft") * 1e-3
-    st0 = h.stats()
-    stream = torch.cuda.current_stream()
-    h.set_stream(stream)
+    h.enqueue_windows(2)   # graphs of the window loop built before the timed region
     torch.cuda.synchronize()
+    st0 = h.stats()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     h.enqueue_windows(windows)
@@ -51,7 +54,7 @@ def _measure(cfg: int, K: int, windows: int, equil: int):
     beta = (st1["rejected"] - st0["rejected"]) / max(committed, 1)
     n_plain = 200
     e0.record(stream)
-    h.plain_step(n_plain)
+    h.enqueue_plain(n_plain)
     e1.record(stream)
     torch.cuda.synchronize()
     t_plain = e0.elapsed_time(e1) * 1e-3 / n_plain
@@ -68,7 +71,15 @@ def main(argv=None):
     ap.add_argument("--windows", type=int, default=60)
     ap.add_argument("--equil", type=int, default=300)
     args = ap.parse_args(argv)
-    rows = [_measure(args.config, K, args.windows, args.equil) for K in args.K]
+    rows, failed = [], {}
+    for K in args.K:
+        try:
+            rows.append(_measure(args.config, K, args.windows, args.equil))
+        except RuntimeError as e:   # reported, not fatal: the other window lengths still run
+            failed[K] = str(e)
+    if len(rows) < 2:
+        print(json.dumps({"config": args.config, "failed": failed}))
+        return
     fixed, per = A.fit_verify_costs([r["K"] for r in rows], [r["t_verify"] for r in rows])
     t_draft = float(np.mean([r["t_draft"] for r in rows]))
     t_plain = float(np.mean([r["t_plain"] for r in rows]))
@@ -85,7 +96,8 @@ def main(argv=None):
                                           "beta": beta, "c": costs.c},
            "bounds": A.summarize(beta, costs, int(np.median(args.K))),
            "best_K_predicted": k_best, "speedup_predicted_at_best": s_best, "best_K_measured": measured_best,
-           "rows": [{k: (round(v, 6) if isinstance(v, float) else v) for k, v in r.items()} for r in rows]}
+           "rows": [{k: (round(v, 6) if isinstance(v, float) else v) for k, v in r.items()} for r in rows],
+           "failed": failed}
     print(json.dumps(out))
 
 
