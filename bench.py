@@ -425,7 +425,9 @@ def measure_workload(w, args, world, rank, full):
         "t_lsd": t_lsd, "committed": committed, "windows": windows, "n_plain": n_plain, "st0": st0, "st1": st1,
         "t_plain": t_plain, "pipelined": pipelined,
         "value_unpipelined": None if value_unpipelined is None else round(value_unpipelined, 4),
-        "gpu_launches": int(windows * (lc["round"] if pipelined else lc["window"]) + n_plain * lc["plain"]),
+        # the fused plain step (lc["plain"] == 0) is one launch for all n_plain steps
+        "gpu_launches": int(windows * (lc["round"] if pipelined else lc["window"]) +
+                            (1 if lc["plain"] == 0 else n_plain * lc["plain"])),
         "clocks": clk,
     })
     # ---- e2e: the public one-call window with host buffers (pinned): every window uploads its state, runs, and

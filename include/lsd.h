@@ -204,6 +204,19 @@ LSD_API int lsd_step(lsd_handle *h, int64_t n_steps, lsd_stats *stats);
  * state with the same noise keys (the baseline the metric compares against). */
 LSD_API int lsd_plain_step(lsd_handle *h, int64_t n_steps);
 
+/* lsd_set_plain_fused: plain target steps (lsd_plain_step, lsd_enqueue_plain)
+ * in one cooperative launch of a fused kernel (one block per eight or four
+ * atoms, the network resident in shared memory, two bounded grid barriers per
+ * step) that runs every step of the call (on, the
+ * default where available: ABOBA, at most 512 atoms, an
+ * FP32 target network of width 32, 64 or 128 with up to 4 layers and a
+ * padded input width of 32, 64 or 128, neighbour lists of capacity <= 128),
+ * or as one CUDA graph of separate kernels per step (off).  The fused kernel
+ * evaluates the same FP32 network on the CUDA cores (results agree with the
+ * graph path to FP32 rounding).  LSD_EUNSUPPORTED when on is requested and
+ * the handle's configuration has no fused plan. */
+LSD_API int lsd_set_plain_fused(lsd_handle *h, int32_t on);
+
 /* lsd_enqueue_windows / lsd_enqueue_plain: enqueue n window graphs (or n
  * plain target steps) on the handle's stream and return without waiting;
  * windows run until the caller synchronises the stream (e.g. with CUDA events
@@ -368,8 +381,10 @@ LSD_API int lsd_query(const lsd_handle *h, int32_t *K, int32_t *n_atoms, int32_t
  * (lsd_draft_window + lsd_verify_window, or one window of lsd_step), one round
  * of the pipelined loop (lsd_set_pipelining), and one plain step, for the
  * handle's current configuration (neighbour-list mode, transport form, MLP,
- * frame capture).  Memory-set nodes are not kernels and are not counted.
- * Any pointer may be null.  No GPU work. */
+ * frame capture).  per_plain is 0 when plain steps run in the fused kernel
+ * (lsd_set_plain_fused): one launch per lsd_plain_step / lsd_enqueue_plain
+ * call, whatever its step count.  Memory-set nodes are not kernels and are not
+ * counted.  Any pointer may be null.  No GPU work. */
 LSD_API int lsd_launch_counts(const lsd_handle *h, int32_t *per_window, int32_t *per_round, int32_t *per_plain);
 
 /* lsd_target_mlp_static_dev: the target potential's per-atom MLP (energies

@@ -114,6 +114,13 @@ struct lsd_handle {
     cudaEvent_t ev_sync = nullptr;   // wait_stream's event, created once
     cudaGraphExec_t g_round[2] = {nullptr, nullptr};
     float move2f_list = 0.f;   // (0.45 skin)^2: the largest displacement the lists stay complete for
+    // the fused plain-target step (small FP32 targets): plan, whether it is in use, exchange buffers
+    PlainPlan pplan{};
+    bool plain_fused = false;
+    uint4 *pf_fix = nullptr;
+    int *pf_keys = nullptr, *pf_cnt = nullptr;
+    float4 *pf_pg = nullptr;
+    unsigned long long *pf_bar = nullptr;   // its grid-barrier counter
     bool drafted = false;
     bool unbounded = false;   // target_step set to "no cap" by lsd_enqueue_*
     // learned-draft training
@@ -261,6 +268,7 @@ int pot_setup(lsd_handle *h, PotHost &ph, const lsd_potential *lp, bool is_draft
         }
     }
     ph.rmax2f = std::max(P.lj_rc2f, P.desc_rc2f);
+    P.rmax2f = ph.rmax2f;   // the fused plain step reads it from the potential block
     ph.near2f = P.has_mlp ? P.desc_rc2f : 0.f;
     return LSD_OK;
 }
@@ -492,6 +500,19 @@ void enqueue_plain(lsd_handle *h, cudaStream_t s) {
     launch_plain_half(h->geo, h->coef, h->species, h->q, h->p, h->st, h->w_qmid, h->w_fix, s);
     enqueue_eval(h, h->target, h->w_fix, 1, h->w_Ft, nullptr, s, !h->vplan.all_pairs);
     launch_plain_finish(h->geo, h->coef, h->species, h->w_qmid, h->w_Ft, h->q, h->p, h->p_obabo, h->st, s);
+}
+
+// n plain target steps in one launch of the fused kernel (ABOBA only).
+bool use_plain_fused(const lsd_handle *h) { return h->plain_fused && !h->coef.obabo; }
+
+int launch_plain_steps_fused(lsd_handle *h, long long n) {
+    while (n > 0) {
+        const int chunk = n > (1 << 30) ? (1 << 30) : (int)n;
+        CK(launch_plain_fused(h->pplan, chunk, h->geo, h->target.dev, h->coef, h->species, h->q, h->p, h->pf_fix,
+                              h->pf_keys, h->pf_cnt, h->pf_pg, h->pf_bar, h->st, h->stream));
+        n -= chunk;
+    }
+    return LSD_OK;
 }
 
 void destroy_graphs(lsd_handle *h) {
@@ -909,6 +930,21 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     if ((rc = train_init(h->train, h->draft.dev, h->draft.weights, h->N)) != LSD_OK) return fail(rc);
     h->train.st = h->st;
     h->train.K = K;
+    {
+        // plain target steps in one fused cooperative launch when the system is small and the target's network FP32
+        const int tp = h->target.p.precision;
+        const bool fp32 = tp == LSD_FP32 || tp == LSD_FP32_TF32 || tp == LSD_FP32_CUDA_CORES;
+        h->pplan = plain_plan(h->N, h->target.dev, fp32, false, h->cap_near, h->geo, kMaxDynSmem);
+        if (h->pplan.ok && plain_setup(h->pplan) != cudaSuccess) h->pplan.ok = false;
+        cudaGetLastError();   // a configuration the device cannot co-schedule only disables the fused step
+        if (h->pplan.ok) {
+            if ((rc = dalloc(h, &h->pf_fix, N)) || (rc = dalloc(h, &h->pf_keys, N * h->pplan.cap)) ||
+                (rc = dalloc(h, &h->pf_cnt, N)) || (rc = dalloc(h, &h->pf_pg, N * h->pplan.cap)) ||
+                (rc = dalloc(h, &h->pf_bar, 1)))
+                return fail(rc);
+            h->plain_fused = true;
+        }
+    }
     for (PotHost *ph : {&h->draft, &h->target})
         if (ph->cal_plan && (rc = calibrate_scales(h, *ph)) != LSD_OK) return fail(rc);
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(LSD_ECUDA);
@@ -1020,6 +1056,7 @@ int lsd_enqueue_plain(lsd_handle *h, int32_t n) {
         h->unbounded = true;
     }
     h->pipe_primed = false;   // plain steps reuse window buffer 0
+    if (use_plain_fused(h)) return launch_plain_steps_fused(h, n);
     for (int32_t k = 0; k < n; ++k) CK(cudaGraphLaunch(h->g_plain, h->stream));
     return LSD_OK;
 }
@@ -1031,7 +1068,11 @@ int lsd_plain_step(lsd_handle *h, int64_t n_steps) {
     TRY(read_state(h, &s));
     TRY(set_target_step(h, s.step + n_steps));
     h->pipe_primed = false;   // plain steps reuse window buffer 0
-    for (int64_t t = 0; t < n_steps; ++t) CK(cudaGraphLaunch(h->g_plain, h->stream));
+    if (use_plain_fused(h)) {
+        TRY(launch_plain_steps_fused(h, n_steps));
+    } else {
+        for (int64_t t = 0; t < n_steps; ++t) CK(cudaGraphLaunch(h->g_plain, h->stream));
+    }
     TRY(read_state(h, &s));
     return check_err(s);
 }
@@ -1385,7 +1426,15 @@ int lsd_launch_counts(const lsd_handle *h, int32_t *per_window, int32_t *per_rou
     if (per_window) *per_window = draft + verify;
     // verify; spec_base; speculative draft; redraft (with its flag kernel in list mode)
     if (per_round) *per_round = verify + 1 + draft + (lists ? 1 : 0) + draft;
-    if (per_plain) *per_plain = verlet + 1 + eval + 1;
+    if (per_plain) *per_plain = use_plain_fused(h) ? 0 : verlet + 1 + eval + 1;
+    return LSD_OK;
+}
+
+int lsd_set_plain_fused(lsd_handle *h, int32_t on) {
+    if (!h) return LSD_EINVAL;
+    if (on && !h->pplan.ok) return LSD_EUNSUPPORTED;
+    TRY(wait_stream(h));
+    h->plain_fused = on != 0;
     return LSD_OK;
 }
 

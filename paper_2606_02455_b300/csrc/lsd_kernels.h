@@ -135,6 +135,22 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
                          const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
                          double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX,
                          cudaStream_t s, WinHdr *hdr = nullptr, int redraft = 0);
+// the fused plain-target step (lsd_plain.cu)
+constexpr int kPlainMaxN = 512;
+struct PlainPlan {
+    bool ok;
+    bool minimg;      // every cutoff below 0.499 of every box side
+    int atoms;        // owned atoms per block (one warp each)
+    int blocks;       // cooperative grid: one block per `atoms` atoms
+    size_t smem;      // dynamic shared memory per block
+    int cap;          // descriptor list capacity (multiple of 32, <= 128)
+    int R;            // cap / 32
+};
+PlainPlan plain_plan(int N, const PotDev &P, bool fp32_target, bool obabo, int cap, const Geo &g, size_t max_smem);
+cudaError_t plain_setup(const PlainPlan &pl);
+cudaError_t launch_plain_fused(const PlainPlan &pl, int n_steps, const Geo &g, const PotDev &P, const Coef &cf,
+                               const int *species, double *q, double *p, uint4 *gfix, int *gkeys, int *gcnt,
+                               float4 *gpg, unsigned long long *bar, DevState *st, cudaStream_t s);
 // the pipelined window loop (lsd_draft.cu)
 void launch_spec_base(const Geo &g, const Coef &cf, const int *species, const double *qmid_b, const double *pdraft_b,
                       const WinHdr *hb, WinHdr *hn, double *qb, double *pb, cudaStream_t s);

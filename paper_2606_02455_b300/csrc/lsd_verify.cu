@@ -15,6 +15,7 @@
 
 #include "lsd_common.cuh"
 #include "lsd_kernels.h"
+#include "lsd_pairs.cuh"
 
 namespace lsd {
 
@@ -156,67 +157,6 @@ __global__ void neigh_build_kernel(const uint4 *__restrict__ fix, const int *__r
 }
 
 // ---------------------------------------------------------------------------
-// Per-warp staging of a row's descriptor neighbours in shared memory.
-// ---------------------------------------------------------------------------
-struct NbStage {
-    float4 *g;   // (dx, dy, dz, 1/r): one 16-byte load per neighbour in the pair loops
-    float4 *c;   // (fc, dfc, e1, e2)
-    float *r;
-    int *sp;
-};
-
-__device__ __forceinline__ NbStage nb_stage_ptrs(float *base, int cap) {
-    NbStage s;   // cap is a multiple of 32: the float4 arrays stay 16-byte aligned
-    s.g = reinterpret_cast<float4 *>(base);
-    s.c = reinterpret_cast<float4 *>(base + 4 * cap);
-    s.r = base + 8 * cap;
-    s.sp = (int *)(base + 9 * cap);
-    return s;
-}
-constexpr int kStageFloats = 10;
-
-// The n (n - 1) / 2 unordered neighbour pairs of a row, flattened so that a
-// warp's lanes stay busy whatever n is: pair t is (p, (p + d) mod n) with
-// d = t / n + 1, p = t mod n (full diagonals d < n / 2, and for even n the
-// half diagonal d = n / 2 with p < n / 2).  Within one diagonal the p are
-// distinct and so are the q.  A lane starts at t = lane and advances by 32.
-struct PairIter {
-    int n, p, d;
-    __device__ __forceinline__ PairIter(int n_, int lane) : n(n_), p(lane), d(1) {
-        while (p >= n && n > 0) {
-            p -= n;
-            ++d;
-        }
-    }
-    __device__ __forceinline__ int q() const { return p + d < n ? p + d : p + d - n; }
-    __device__ __forceinline__ void next() {
-        p += 32;
-        while (p >= n) {
-            p -= n;
-            ++d;
-        }
-    }
-};
-
-__device__ __forceinline__ void nb_stage_load(const NbStage &S, const uint4 *fj, uint4 fi, const int *keys, int n,
-                                              const Geo &g, float rc, int lane) {
-    for (int p = lane; p < n; p += 32) {
-        const int key = keys[p];
-        const uint4 fk = fj[key >> 5];
-        const float3 d = entry_disp(fi, fk, key & 31, g);
-        const float r2 = dist2_rule(d.x, d.y, d.z);
-        const float r = sqrtf(r2);
-        float fc, dfc;
-        cutoff_fn(r, rc, fc, dfc);
-        S.g[p] = make_float4(d.x, d.y, d.z, 1.f / r);   // 1/r once per neighbour: the O(n^2) pair loops multiply
-        S.c[p] = make_float4(fc, dfc, expf(-0.005f * r2), expf(-0.05f * r2));
-        S.r[p] = r;
-        S.sp[p] = (int)fk.w;
-    }
-    __syncwarp();
-}
-
-// ---------------------------------------------------------------------------
 // Descriptors: radial by lanes over basis functions (two halves over
 // neighbours), angular by lanes over neighbour pairs, warp reductions.
 // ---------------------------------------------------------------------------
@@ -232,137 +172,20 @@ __global__ void desc_kernel(const uint4 *__restrict__ fix, const int *__restrict
     const int j = row / N, i = row - j * N;
     const uint4 *fj = fix + (size_t)j * N;
     const uint4 fi = fj[i];
-    NbStage S = nb_stage_ptrs(smem + (size_t)wib * kStageFloats * cap, cap);
+    NbStage S = nb_stage_ptrs(smem + (size_t)wib * kNbStageFloats * cap, cap);
     const int n = n_near[row];
     nb_stage_load(S, fj, fi, near_keys + (size_t)row * cap, n, g, P.desc_rc, lane);
-    float *x = X + (size_t)row * P.d0p;
-    const int nr = P.n_rbf;
-    // radial
-    {
-        float acc[kMaxSpecies];
-#pragma unroll
-        for (int s = 0; s < kMaxSpecies; ++s) acc[s] = 0.f;
-        const int kb = lane & 15;
-        if (kb < nr) {
-            const float mu = (float)kb * P.rbf_w;
-            for (int p = lane >> 4; p < n; p += 2) {
-                const float t = S.r[p] - mu;
-                const float v = expf(-t * t * P.rbf_inv2w2) * S.c[p].x;
-                const int sp = S.sp[p];
-#pragma unroll
-                for (int s = 0; s < kMaxSpecies; ++s) acc[s] += (sp == s) ? v : 0.f;
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < kMaxSpecies; ++s) acc[s] += __shfl_down_sync(0xffffffffu, acc[s], 16);
-        if (lane < nr)
-            for (int s = 0; s < g.S; ++s) x[s * nr + lane] = acc[s];
-    }
-    // angular
-    if (P.n_ang) {
-        float a[kNAng];
-#pragma unroll
-        for (int t = 0; t < kNAng; ++t) a[t] = 0.f;
-        const int npairs = n * (n - 1) / 2;
-        PairIter it(n, lane);
-        for (int t = lane; t < npairs; t += 32, it.next()) {
-            const int p = it.p, q = it.q();
-            {
-                const float4 gp = S.g[p], gq = S.g[q], cp = S.c[p], cq = S.c[q];
-                const float c = (gp.x * gq.x + gp.y * gq.y + gp.z * gq.z) * (gp.w * gq.w);
-                const float ff = cp.x * cq.x;
-                const float E1 = cp.z * cq.z * ff, E2 = cp.w * cq.w * ff;
-                const float bp1 = 1.f + c, bm1 = 1.f - c;
-                const float bp2 = bp1 * bp1, bm2 = bm1 * bm1, bp4 = bp2 * bp2, bm4 = bm2 * bm2;
-                const float bp8 = bp4 * bp4, bm8 = bm4 * bm4;
-                // zeta = 1 (2^0), 2 (2^-1), 4 (2^-3), 8 (2^-7)
-                a[0] += bp1 * E1; a[1] += bp1 * E2; a[2] += bm1 * E1; a[3] += bm1 * E2;
-                a[4] += 0.5f * bp2 * E1; a[5] += 0.5f * bp2 * E2; a[6] += 0.5f * bm2 * E1; a[7] += 0.5f * bm2 * E2;
-                a[8] += 0.125f * bp4 * E1; a[9] += 0.125f * bp4 * E2; a[10] += 0.125f * bm4 * E1; a[11] += 0.125f * bm4 * E2;
-                a[12] += 0.0078125f * bp8 * E1; a[13] += 0.0078125f * bp8 * E2;
-                a[14] += 0.0078125f * bm8 * E1; a[15] += 0.0078125f * bm8 * E2;
-            }
-        }
-        // the sixteen warp sums as one reduce-scatter: at offsets 16, 8, 4, 2
-        // each lane keeps the half of its partial sums its offset bit selects
-        // and adds the partner's partials of that half; lanes 2f and 2f+1 end
-        // with the total of feature f (62 shuffles and adds instead of 160)
-        static_assert(kNAng == 16, "the reduce-scatter is laid out for 16 features");
-#pragma unroll
-        for (int m = kNAng; m > 1; m >>= 1) {
-            const bool up = (lane & (m == 16 ? 16 : m == 8 ? 8 : m == 4 ? 4 : 2)) != 0;
-            const int o = m == 16 ? 16 : m == 8 ? 8 : m == 4 ? 4 : 2;
-#pragma unroll
-            for (int t = 0; t < m / 2; ++t) {
-                const float keep = up ? a[t + m / 2] : a[t], send = up ? a[t] : a[t + m / 2];
-                a[t] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-            }
-        }
-        a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
-        if ((lane & 1) == 0) x[g.S * nr + (lane >> 1)] = a[0];
-    }
-    // one-hot and padding
-    const int off = g.S * nr + P.n_ang;
-    for (int f = off + lane; f < P.d0p; f += 32) x[f] = (f == off + (int)fi.w) ? 1.f : 0.f;
+    desc_row(S, n, P, g.S, (int)fi.w, X + (size_t)row * P.d0p, lane);
 }
 
 // ---------------------------------------------------------------------------
 // Pair gradients g_p = dE_i / d(r_p) and LJ forces.
 // ---------------------------------------------------------------------------
-// The angular term T(c_pq, r_p, r_q) of one unordered pair: dT/dd_p =
-// A d_q + B_p d_p is added to p's accumulators (a*), and dT/dd_q = A d_p +
-// B_q d_q is returned for q.  wang: dE/dX of the angular features.
-__device__ __forceinline__ float4 pair_terms(const NbStage &S, const float (&wang)[kNAng], int p, int q, float &ax,
-                                             float &ay, float &az, float &ab) {
-    const float4 gp = S.g[p], gq = S.g[q], cp = S.c[p], cq = S.c[q];
-    const float xp = gp.x, yp = gp.y, zp = gp.z, xq = gq.x, yq = gq.y, zq = gq.z;
-    const float rip = gp.w, riq = gq.w;
-    const float inv_pq = rip * riq;
-    const float cth = (xp * xq + yp * yq + zp * zq) * inv_pq;
-    const float fp = cp.x, fq = cq.x;
-    const float E1 = cp.z * cq.z, E2 = cp.w * cq.w;
-    // (1 + lambda c)^zeta and zeta (1 + lambda c)^(zeta - 1), lambda = +1 (p) and -1 (m)
-    const float bp1 = 1.f + cth, bm1 = 1.f - cth;
-    const float bp2 = bp1 * bp1, bm2 = bm1 * bm1, bp4 = bp2 * bp2, bm4 = bm2 * bm2;
-    const float bp8 = bp4 * bp4, bm8 = bm4 * bm4;
-    const float bp3 = bp2 * bp1, bm3 = bm2 * bm1, bp7 = bp4 * bp3, bm7 = bm4 * bm3;
-    // per eta: S0 = sum_a w_a pref pow (value weights), S1 = dS0/dc
-    float S0_1 = 0.f, S0_2 = 0.f, S1_1 = 0.f, S1_2 = 0.f;
-    // zeta 1: pref 1
-    S0_1 += wang[0] * bp1 + wang[2] * bm1;  S0_2 += wang[1] * bp1 + wang[3] * bm1;
-    S1_1 += wang[0] - wang[2];              S1_2 += wang[1] - wang[3];
-    // zeta 2: pref 1/2, zeta*pow1*pref = b
-    S0_1 += 0.5f * (wang[4] * bp2 + wang[6] * bm2);  S0_2 += 0.5f * (wang[5] * bp2 + wang[7] * bm2);
-    S1_1 += wang[4] * bp1 - wang[6] * bm1;           S1_2 += wang[5] * bp1 - wang[7] * bm1;
-    // zeta 4: pref 1/8, zeta*pow1*pref = b^3/2
-    S0_1 += 0.125f * (wang[8] * bp4 + wang[10] * bm4);  S0_2 += 0.125f * (wang[9] * bp4 + wang[11] * bm4);
-    S1_1 += 0.5f * (wang[8] * bp3 - wang[10] * bm3);    S1_2 += 0.5f * (wang[9] * bp3 - wang[11] * bm3);
-    // zeta 8: pref 1/128, zeta*pow1*pref = b^7/16
-    S0_1 += 0.0078125f * (wang[12] * bp8 + wang[14] * bm8);
-    S0_2 += 0.0078125f * (wang[13] * bp8 + wang[15] * bm8);
-    S1_1 += 0.0625f * (wang[12] * bp7 - wang[14] * bm7);
-    S1_2 += 0.0625f * (wang[13] * bp7 - wang[15] * bm7);
-    const float ffq = fp * fq;
-    const float S1E = (S1_1 * E1 + S1_2 * E2) * ffq, S0E = S0_1 * E1 + S0_2 * E2;
-    // d/dd_p: S1 E ff (d_q / (r_p r_q) - c d_p / r_p^2) - 2 eta S0 E ff d_p + S0 E dfc_p fc_q d_p / r_p
-    const float A = S1E * inv_pq;
-    const float Bc = -2.f * (0.005f * S0_1 * E1 + 0.05f * S0_2 * E2) * ffq;
-    const float Bp = Bc - S1E * cth * (rip * rip) + S0E * cp.y * fq * rip;
-    const float Bq = Bc - S1E * cth * (riq * riq) + S0E * fp * cq.y * riq;
-    ax += A * xq;
-    ay += A * yq;
-    az += A * zq;
-    ab += Bp;
-    return make_float4(A * xp, A * yp, A * zp, Bq);
-}
 
-// SLOTS > 0: neighbours per lane (lane l owns p = l + 32 s); every row has at
-// most 32 SLOTS of them, and rows with more than 32 run the angular pairs by
-// diagonals: in diagonal d lane l evaluates (p, p + d mod n) for its own p,
-// keeps the p side in registers and hands the q side over through shared
-// memory to q's owner (within one diagonal the q are distinct, so no two lanes
-// write the same slot).  SLOTS = 0, and rows of at most 32: the pairs are
-// flattened over all 32 lanes and both sides go to shared accumulators.
+// SLOTS: neighbours per lane (lane l owns p = l + 32 s); every row has at most
+// 32 SLOTS of them.  The angular pairs run by diagonals (row_pair_grads): a
+// fixed order of summation with no atomics, so the forces do not depend on the
+// launch shape.
 template <int SLOTS>
 __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__restrict__ near_keys,
                                 const int *__restrict__ n_near, const int *__restrict__ far_keys,
@@ -385,9 +208,9 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
     const uint4 *fj = fix + (size_t)j * N;
     const uint4 fi = fj[i];
     const int warps = blockDim.x >> 5;
-    float *wbuf = smem + (size_t)warps * kStageFloats * cap + (size_t)wib * P.d0p;
-    float4 *tb = reinterpret_cast<float4 *>(smem + (size_t)warps * (kStageFloats * cap + P.d0p)) + (size_t)wib * cap;
-    NbStage S = nb_stage_ptrs(smem + (size_t)wib * kStageFloats * cap, cap);
+    float *wbuf = smem + (size_t)warps * kNbStageFloats * cap + (size_t)wib * P.d0p;
+    float4 *tb = reinterpret_cast<float4 *>(smem + (size_t)warps * (kNbStageFloats * cap + P.d0p)) + (size_t)wib * cap;
+    NbStage S = nb_stage_ptrs(smem + (size_t)wib * kNbStageFloats * cap, cap);
     const int n = n_near[row];
     const int *keys = near_keys + (size_t)row * cap;
     float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
@@ -416,93 +239,7 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
         pdl_wait();
         for (int f = lane; f < P.d0p; f += 32) wbuf[f] = dEdX[(size_t)row * P.d0p + f];
         __syncwarp();
-        const int nr = P.n_rbf;
-        float wang[kNAng];   // dE/dX of the angular features, in registers across the pair loop
-#pragma unroll
-        for (int t = 0; t < kNAng; ++t) wang[t] = wbuf[g.S * nr + t];
-        constexpr int R = SLOTS > 0 ? SLOTS : 1;
-        float ax[R], ay[R], az[R], ab[R];
-#pragma unroll
-        for (int s = 0; s < R; ++s) ax[s] = ay[s] = az[s] = ab[s] = 0.f;
-        float *sx = reinterpret_cast<float *>(tb), *sy = sx + cap, *sz = sx + 2 * cap, *sb = sx + 3 * cap;
-        const bool flat = SLOTS == 0 || n <= 32;
-        if (P.n_ang && flat) {
-            // the pairs flattened over all 32 lanes, both sides added to shared accumulators
-            for (int p = lane; p < n; p += 32) sx[p] = sy[p] = sz[p] = sb[p] = 0.f;
-            __syncwarp();
-            const int npairs = n * (n - 1) / 2;
-            PairIter it(n, lane);
-            for (int t = lane; t < npairs; t += 32, it.next()) {
-                const int p = it.p, q = it.q();
-                float px = 0.f, py = 0.f, pz = 0.f, pb = 0.f;
-                const float4 v = pair_terms(S, wang, p, q, px, py, pz, pb);
-                atomicAdd(sx + p, px);
-                atomicAdd(sy + p, py);
-                atomicAdd(sz + p, pz);
-                atomicAdd(sb + p, pb);
-                atomicAdd(sx + q, v.x);
-                atomicAdd(sy + q, v.y);
-                atomicAdd(sz + q, v.z);
-                atomicAdd(sb + q, v.w);
-            }
-            __syncwarp();
-        } else if (P.n_ang) {
-            // diagonals d = 1 .. n/2; for even n the last one holds n/2 pairs (p < d)
-            for (int d = 1; 2 * d <= n; ++d) {
-                const bool half = 2 * d == n;
-#pragma unroll
-                for (int s = 0; s < R; ++s) {
-                    const int p = lane + 32 * s;
-                    if (p < n && (!half || p < d)) {
-                        const int q = p + d < n ? p + d : p + d - n;
-                        tb[q] = pair_terms(S, wang, p, q, ax[s], ay[s], az[s], ab[s]);
-                    }
-                }
-                __syncwarp();
-#pragma unroll
-                for (int s = 0; s < R; ++s) {
-                    const int q = lane + 32 * s;
-                    if (q < n && (!half || q >= d)) {
-                        const float4 v = tb[q];
-                        ax[s] += v.x;
-                        ay[s] += v.y;
-                        az[s] += v.z;
-                        ab[s] += v.w;
-                    }
-                }
-                __syncwarp();
-            }
-        }
-        // per neighbour: the radial term, then the angular sums (registers, or the shared accumulators)
-        auto finish = [&](int p, float bx, float by, float bz, float bw) {
-            const float4 gp = S.g[p], cp = S.c[p];
-            const float xp = gp.x, yp = gp.y, zp = gp.z, rp = S.r[p], fp = cp.x, dfp = cp.y;
-            const float rip = gp.w;
-            // radial: c = sum_k w_k g_k'(r)
-            float c = 0.f;
-            const float *wr = wbuf + S.sp[p] * nr;
-            for (int k = 0; k < nr; ++k) {
-                const float t = rp - (float)k * P.rbf_w;
-                const float phi = expf(-t * t * P.rbf_inv2w2);
-                c += wr[k] * phi * (-t * P.rbf_invw2 * fp + dfp);
-            }
-            const float gx = c * xp * rip + bx + bw * xp;
-            const float gy = c * yp * rip + by + bw * yp;
-            const float gz = c * zp * rip + bz + bw * zp;
-            pair_g[(size_t)row * cap + p] = make_float4(gx, gy, gz, 0.f);
-            fx += gx;
-            fy += gy;
-            fz += gz;
-        };
-        if (flat) {
-            for (int p = lane; p < n; p += 32)
-                if (P.n_ang) finish(p, sx[p], sy[p], sz[p], sb[p]);
-                else finish(p, 0.f, 0.f, 0.f, 0.f);
-        } else {
-#pragma unroll
-            for (int s = 0; s < R; ++s)
-                if (lane + 32 * s < n) finish(lane + 32 * s, ax[s], ay[s], az[s], ab[s]);
-        }
+        row_pair_grads<SLOTS>(S, n, P, g.S, wbuf, tb, pair_g + (size_t)row * cap, lane, fx, fy, fz);
     }
     fx = warp_sum(fx);
     fy = warp_sum(fy);
@@ -618,7 +355,7 @@ void launch_neigh_list(const uint4 *fix, const int *vlist, const int *vcount, in
                      near_keys, far_keys, n_near, n_far, st, keff);
 }
 
-size_t desc_smem_bytes(int warps, int cap) { return (size_t)warps * kStageFloats * cap * sizeof(float); }
+size_t desc_smem_bytes(int warps, int cap) { return (size_t)warps * kNbStageFloats * cap * sizeof(float); }
 
 void launch_desc(const uint4 *fix, const int *near_keys, const int *n_near, int cap, int M, const Geo &g,
                  const PotDev &P, float *X, cudaStream_t s) {
@@ -634,7 +371,7 @@ void launch_pairgrad(const uint4 *fix, const int *near_keys, const int *n_near, 
     const size_t sm = desc_smem_bytes(warps, cap) + (size_t)warps * (P.d0p + 4 * cap) * sizeof(float);
     // lists of at most 128 hold mostly rows of a few dozen neighbours: flattened pairs with a small register
     // footprint; longer lists run their large rows by diagonals
-    auto k = cap <= 128 ? pairgrad_kernel<0> : (cap <= 256 ? pairgrad_kernel<8> : pairgrad_kernel<16>);
+    auto k = cap <= 128 ? pairgrad_kernel<4> : (cap <= 256 ? pairgrad_kernel<8> : pairgrad_kernel<16>);
     launch_dependent(k, (M + warps - 1) / warps, warps * 32, sm, s, fix, near_keys, n_near, far_keys, n_far, cap,
                      cap_far, M, g, P, dEdX, pair_g, Fpart, E_lj);
 }
@@ -651,7 +388,7 @@ void launch_force_gather(const int *near_keys, const int *n_near, int cap, int M
 cudaError_t verify_kernels_setup(int max_smem) {
     cudaError_t e = cudaFuncSetAttribute(desc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e != cudaSuccess) return e;
-    const void *pk[3] = {(const void *)pairgrad_kernel<0>, (const void *)pairgrad_kernel<8>,
+    const void *pk[3] = {(const void *)pairgrad_kernel<4>, (const void *)pairgrad_kernel<8>,
                          (const void *)pairgrad_kernel<16>};
     for (const void *k : pk) {
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);

@@ -34,7 +34,7 @@ SYMBOLS = ["lsd_init", "lsd_draft_window", "lsd_verify_window", "lsd_step", "lsd
            "lsd_descriptors", "lsd_get_window", "lsd_profile_window", "lsd_checkpoint", "lsd_restore", "lsd_query",
            "lsd_target_mlp_static_dev", "lsd_destroy",
            "lsd_strerror", "lsd_launch_counts", "lsd_window_host", "lsd_transport_window", "lsd_get_frames",
-           "lsd_set_max_displacement"]
+           "lsd_set_max_displacement", "lsd_set_plain_fused"]
 
 
 class LSDError(RuntimeError):
@@ -110,6 +110,7 @@ def _lib():
             "lsd_transport_window": [P, P, P, P, P, I32, P, P],
             "lsd_get_frames": [P, I64, I64, P, P],
             "lsd_set_max_displacement": [P, D],
+            "lsd_set_plain_fused": [P, I32],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -298,6 +299,10 @@ class LSD:
     def set_integrator(self, scheme):
         """"aboba" (Eq. 2) or "obabo" (the staggered frame of App. E; entering it evaluates the target once)."""
         _check(_lib().lsd_set_integrator(self.h, self.SCHEMES[scheme]), "lsd_set_integrator")
+
+    def set_plain_fused(self, on=True):
+        """Plain target steps in one fused cluster launch per call (on) or one graph of kernels per step (off)."""
+        _check(_lib().lsd_set_plain_fused(self.h, int(bool(on))), "lsd_set_plain_fused")
 
     def set_max_displacement(self, d_max):
         """End windows early once an atom moves d_max Angstrom from its lists' base (0 restores the default)."""

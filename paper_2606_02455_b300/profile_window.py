@@ -1,10 +1,12 @@
 """Runs LSD windows of a benchmark configuration, for profilers (ncu) and quick timing.
 
     python -m paper_2606_02455_b300.profile_window --config 4 [--K 32] [--windows 2] [--equil 0] [--pipelined]
+                                                   [--plain 0]
 
 Builds one handle for the configuration (window length K overridable, to keep a profiled footprint small),
 optionally runs `equil` plain target steps, then `windows` windows through lsd_enqueue_windows on the handle's
-stream, and prints the per-phase CUDA-event times of one more window (lsd_profile_window) and the run's counters.
+stream, prints the per-phase CUDA-event times of one more window (lsd_profile_window) and the run's counters, and
+then runs `plain` plain target steps in one call.
 The first kernels a handle launches are its set-up (the FP8 and FP32-split calibration runs the MLP once on N
 rows); window kernels follow.
 """
@@ -23,6 +25,7 @@ def main() -> None:
     ap.add_argument("--windows", type=int, default=2)
     ap.add_argument("--equil", type=int, default=0)
     ap.add_argument("--pipelined", action="store_true")
+    ap.add_argument("--plain", type=int, default=0, help="plain target steps after the windows (one call)")
     a = ap.parse_args()
     w = W.CONFIGS[a.config](a.K) if a.K else W.CONFIGS[a.config]()
     h = lsd.LSD(w.system, w.draft, w.target, w.integ)
@@ -32,8 +35,10 @@ def main() -> None:
     h.enqueue_windows(a.windows)
     st = h.stats()
     ph = h.profile_window()
+    if a.plain:
+        h.plain_step(a.plain)
     print(json.dumps({"workload": w.name, "windows": st["windows"], "committed": st["committed"],
-                      "phases_ms": {k: round(v, 4) for k, v in ph.items()}}))
+                      "phases_ms": {k: round(v, 4) for k, v in ph.items()}, "plain_steps": a.plain}))
     h.close()
 
 

@@ -92,11 +92,14 @@ def test_pipelining_excludes_error_correction():
 
 def test_launch_counts_follow_the_configuration():
     """The kernels a window, a pipelined round and a plain step launch: all-pairs candidates and a one-launch
-    transport for the 256-atom workload; Verlet-list builds (four kernels on a grid of cells) and a two-launch
-    transport for 4096 atoms."""
+    transport for the 256-atom workload, whose plain steps run in the fused kernel (0 per step: one launch per call;
+    7 per step on the graph path); Verlet-list builds (four kernels on a grid of cells) and a two-launch transport
+    for 4096 atoms."""
     from paper_2606_02455_b300 import lsd
     w = W.config2()
     h = lsd.LSD(w.system, w.draft, w.target, w.integ)
+    assert h.launch_counts() == dict(window=7, round=9, plain=0)
+    h.set_plain_fused(False)
     assert h.launch_counts() == dict(window=7, round=9, plain=7)
     h.close()
     w = W.config4()
