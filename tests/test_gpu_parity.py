@@ -332,3 +332,29 @@ def test_learned_draft_training_reduces_rejections():
     after = (st1["sum_delta"] - st0["sum_delta"]) / (st1["committed"] - st0["committed"])
     assert after < 0.8 * before, (before, after)
     h.close()
+
+
+@pytest.mark.parametrize("name", ["c2", "dilute512"])
+def test_forces_do_not_depend_on_batch_or_launch_shape(name):
+    """The adjoint is a fixed-order gather (pair gradients by diagonals, no atomics): a configuration's forces and
+    energies are bit-identical whether it is evaluated alone or as one row block of a K-configuration batch (other
+    grids, other tiles of the MLP), and the window's target forces equal the explicit entry point's on the window's
+    own half-step positions."""
+    import torch
+    lsd = _lsd()
+    w = WORKLOADS[name]()
+    s = w.system
+    K = w.integ.K
+    h = lsd.LSD(s, w.draft, w.target, w.integ)
+    qs = torch.tensor(_configs(s, K, 0.08, seed=321), device="cuda")
+    F_all, E_all = h.target_forces(qs, energies=True)
+    for c in (0, K // 2, K - 1):
+        F_one, E_one = h.target_forces(qs[c:c + 1], energies=True)
+        assert torch.equal(F_one[0], F_all[c]) and torch.equal(E_one[0], E_all[c]), c
+    h.draft_window()
+    h.verify_window()
+    win = h.get_window()
+    k_eff = h.stats()["verified"]
+    F_win = h.target_forces(torch.tensor(win["q_mid"][:k_eff], device="cuda")).cpu().numpy()
+    assert np.array_equal(F_win, win["F_target"][:k_eff])
+    h.close()
