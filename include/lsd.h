@@ -321,9 +321,28 @@ LSD_API int lsd_get_frames(lsd_handle *h, int64_t first, int64_t count, double *
 /* lsd_train_draft: n_iters Adam steps (learning rate lr) of force matching of a
  * LSD_POT_LEARNED draft on the captured frames: loss = mean over frames and
  * components of |F~ - F_target|^2, gradient by the double backward through
- * the MLP and the descriptors.  loss_out (may be NULL) receives the loss of
+ * the MLP and the descriptors.  Frames of up to 256 atoms are evaluated one
+ * per block; larger ones with the frame's atoms as rows of the batched
+ * neighbour, descriptor and force kernels (any size; it rebuilds the
+ * window's neighbour lists, so call it between windows).  loss_out (may be NULL) receives the loss of
  * the last iteration.  frames_per_iter <= 0 uses all frames. */
 LSD_API int lsd_train_draft(lsd_handle *h, int32_t n_iters, float lr, int32_t frames_per_iter, float *loss_out);
+
+/* lsd_set_online_training: retrain a LSD_POT_LEARNED draft during lsd_step
+ * every `every_accepted` accepted steps (0 turns it off): between windows,
+ * n_iters Adam steps (learning rate lr, frames_per_iter frames each, as
+ * lsd_train_draft) on the captured target-verified frames; the next window
+ * drafts with the new network (each step is still verified against the
+ * target with the draft that proposed it, so the committed chain keeps the
+ * target law).  lsd_step checks after each batch of windows and shortens its
+ * batches to stop near the next retraining point.  Needs frame capture on
+ * (LSD_ESTATE otherwise); LSD_EINVAL for a draft that is not learned. */
+LSD_API int lsd_set_online_training(lsd_handle *h, int64_t every_accepted, int32_t n_iters, float lr,
+                                    int32_t frames_per_iter);
+
+/* lsd_online_status: retrainings done so far and the force-matching loss of
+ * the last one ((eV/A)^2); either pointer may be NULL. */
+LSD_API int lsd_online_status(const lsd_handle *h, int64_t *retrains, float *last_loss);
 
 /* lsd_force_match_dev: loss and gradient (packed like the weights, float32) of
  * the learned draft on n_frames given frames (device pointers, positions

@@ -114,6 +114,13 @@ struct lsd_handle {
     cudaEvent_t ev_sync = nullptr;   // wait_stream's event, created once
     cudaGraphExec_t g_round[2] = {nullptr, nullptr};
     float move2f_list = 0.f;   // (0.45 skin)^2: the largest displacement the lists stay complete for
+    // online retraining of a learned draft (lsd_set_online_training)
+    long long online_every = 0;        // accepted steps between retrainings (0: off)
+    int online_iters = 0, online_fpi = 0;
+    float online_lr = 0.f;
+    long long online_base = 0;         // accepted-step count at the last retraining
+    long long online_count = 0;
+    float online_loss = 0.f;
     // the fused plain-target step (small FP32 targets): plan, whether it is in use, exchange buffers
     PlainPlan pplan{};
     bool plain_fused = false;
@@ -659,6 +666,52 @@ int calibrate_scales(lsd_handle *h, PotHost &ph) {
 }
 
 
+// The force-matching gradient of n_frames frames (slots frame0.. mod n_avail
+// of fq [.][N][3] / fF) of a learned draft whose frames exceed one block:
+// per frame, the frame's neighbour lists (the window's Verlet machinery, or
+// all atoms without a cell grid), the draft's descriptors, the trainer's MLP
+// with its pre-activations, the draft forces by the pair-gradient and gather
+// kernels, then the residual, the descriptor JVP and the per-weight sums.  The
+// sum over frames, and Adam when asked, follow.
+int train_large_pass(lsd_handle *h, const double *fq, const float *fF, long long frame0, long long n_avail,
+                     int n_frames, bool adam, float lr) {
+    TrainState &t = h->train;
+    TRY(train_large_bufs(t, n_frames));
+    const int N = h->N;
+    const PotHost &ph = h->draft;
+    const PotDev &P = ph.dev;
+    cudaStream_t s = h->stream;
+    const float scale = -2.0f / ((float)n_frames * 3.0f * (float)N);
+    const size_t D = 3 * (size_t)N;
+    for (int f = 0; f < n_frames; ++f) {
+        const long long slot = (frame0 + f) % n_avail;
+        const double *q = fq + (size_t)slot * D;
+        const float *Fs = fF + (size_t)slot * D;
+        launch_fixpoint(q, h->species, N, h->geo, h->fix_eval, s);
+        if (!h->vplan.all_pairs) {
+            launch_verlet_build(h->vplan, q, h->species, h->geo, h->vbufs, h->st, s);
+            launch_neigh_list(h->fix_eval, h->vbufs.vlist, h->vbufs.vcount, h->vplan.cap, N, h->geo, ph.rmax2f,
+                              ph.near2f, h->cap_near, h->cap_far, h->near_keys, h->far_keys, h->n_near, h->n_far,
+                              h->st, nullptr, s);
+        } else {
+            launch_neigh_build(h->fix_eval, N, h->geo, ph.rmax2f, ph.near2f, h->cap_near, h->cap_far, h->near_keys,
+                               h->far_keys, h->n_near, h->n_far, h->st, s);
+        }
+        launch_desc(h->fix_eval, h->near_keys, h->n_near, h->cap_near, N, h->geo, P, h->X, s);
+        launch_fm_mlp(t, h->X, P.d0p, h->dEdX, s);
+        launch_pairgrad(h->fix_eval, h->near_keys, h->n_near, h->far_keys, h->n_far, h->cap_near, h->cap_far, N,
+                        h->geo, P, h->dEdX, h->pair_g, h->Fpart, h->E_lj, s);
+        launch_force_gather(h->near_keys, h->n_near, h->cap_near, N, N, 1, h->pair_g, h->Fpart, h->E_lj, h->E_mlp,
+                            t.lFd, nullptr, h->st, s);
+        launch_fm_frame_grad(t, h->fix_eval, h->near_keys, h->n_near, h->cap_near, h->geo, P, h->X, P.d0p, Fs, scale,
+                             f, s);
+    }
+    launch_fm_reduce_adam(t, n_frames, adam, lr, s);
+    CK(cudaGetLastError());
+    h->pipe_primed = false;   // the window's Verlet lists were rebuilt for the frames
+    return LSD_OK;
+}
+
 __global__ void mb_init_kernel(int N, Coef cf, const int *species, const double *mass, double T, double kT_kappa,
                                double *p) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -673,6 +726,8 @@ __global__ void mb_init_kernel(int N, Coef cf, const int *species, const double 
 }  // namespace
 
 extern "C" {
+
+int lsd_train_draft(lsd_handle *h, int32_t n_iters, float lr, int32_t frames_per_iter, float *loss_out);
 
 const char *lsd_strerror(int code) {
     switch (code) {
@@ -1025,11 +1080,26 @@ int lsd_step(lsd_handle *h, int64_t n_steps, lsd_stats *stats) {
         double rate = (s.windows > w0) ? (double)(s.committed - c0) / (double)(s.windows - w0) : (double)h->K;
         if (rate < 1.0) rate = 1.0;
         long long batch = (long long)std::ceil((double)rem / rate);
+        if (h->online_every > 0) {
+            // stop the batch near the next retraining point
+            const long long left = h->online_every - ((s.committed - s.rejected) - h->online_base);
+            const long long b2 = (long long)std::ceil((double)std::max(left, 1ll) / rate);
+            batch = std::min(batch, b2);
+        }
         if (batch < 1) batch = 1;
         TRY(launch_windows(h, batch));
         TRY(read_state(h, &s));
         TRY(check_err(s));
         rem = target - s.step;
+        if (h->online_every > 0 && (s.committed - s.rejected) - h->online_base >= h->online_every) {
+            // retrain the learned draft on the captured target-verified frames, between windows
+            float loss = 0.f;
+            TRY(lsd_train_draft(h, h->online_iters, h->online_lr, h->online_fpi, &loss));
+            h->online_loss = loss;
+            h->online_count += 1;
+            h->online_base = s.committed - s.rejected;
+            TRY(ensure_graphs(h));
+        }
     }
     h->drafted = false;
     if (stats) TRY(lsd_get_stats(h, stats));
@@ -1549,6 +1619,29 @@ int lsd_frame_count(const lsd_handle *h, int64_t *n) {
     return train_frame_count(const_cast<lsd_handle *>(h)->train, n, h->stream);
 }
 
+int lsd_set_online_training(lsd_handle *h, int64_t every_accepted, int32_t n_iters, float lr, int32_t frames_per_iter) {
+    if (!h || every_accepted < 0 || n_iters < 0) return LSD_EINVAL;
+    if (every_accepted > 0) {
+        if (h->draft.p.kind != LSD_POT_LEARNED) return LSD_EINVAL;
+        if (!h->train.capture_on) return LSD_ESTATE;   // frames are the training labels
+    }
+    DevState st;
+    TRY(read_state(h, &st));
+    h->online_every = every_accepted;
+    h->online_iters = n_iters;
+    h->online_lr = lr;
+    h->online_fpi = frames_per_iter;
+    h->online_base = st.committed - st.rejected;
+    return LSD_OK;
+}
+
+int lsd_online_status(const lsd_handle *h, int64_t *retrains, float *last_loss) {
+    if (!h) return LSD_EINVAL;
+    if (retrains) *retrains = h->online_count;
+    if (last_loss) *last_loss = h->online_loss;
+    return LSD_OK;
+}
+
 int lsd_get_frames(lsd_handle *h, int64_t first, int64_t count, double *q, float *F) {
     if (!h || first < 0 || count < 0) return LSD_EINVAL;
     return train_get_frames(h->train, first, count, q, F, h->stream);
@@ -1558,7 +1651,22 @@ int lsd_train_draft(lsd_handle *h, int32_t n_iters, float lr, int32_t frames_per
     if (!h || n_iters < 0) return LSD_EINVAL;
     if (h->draft.p.kind != LSD_POT_LEARNED) return LSD_EINVAL;
     TRY(wait_stream(h));
-    TRY(train_run(h->train, h->geo, h->draft.dev, h->species, n_iters, lr, frames_per_iter, loss_out, h->stream));
+    if (train_frame_fits(h->train)) {
+        TRY(train_run(h->train, h->geo, h->draft.dev, h->species, n_iters, lr, frames_per_iter, loss_out, h->stream));
+    } else {
+        int64_t avail = 0;
+        TRY(train_frame_count(h->train, &avail, h->stream));
+        if (avail < 1) return LSD_ESTATE;
+        const int fpi = (frames_per_iter <= 0 || frames_per_iter > avail) ? (int)avail : frames_per_iter;
+        for (int it = 0; it < n_iters; ++it) {
+            const long long frame0 = (h->train.iter * (long long)fpi) % avail;
+            TRY(train_large_pass(h, h->train.fq, h->train.fF, frame0, avail, fpi, true, lr));
+        }
+        if (loss_out) {
+            CK(cudaMemcpyAsync(loss_out, h->train.loss, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+        }
+    }
     // new weights -> draft MLP (FP32 master in the trainer)
     TRY(train_get_weights(h->train, h->draft.weights, h->stream));
     TRY(pot_upload(h, h->draft));
@@ -1571,8 +1679,20 @@ int lsd_force_match_dev(lsd_handle *h, const double *frames_q_dev, const float *
     if (!h || !frames_q_dev || !frames_F_dev || n_frames < 1) return LSD_EINVAL;
     if (h->draft.p.kind != LSD_POT_LEARNED) return LSD_EINVAL;
     TRY(wait_stream(h));
-    return train_force_match(h->train, h->geo, h->draft.dev, h->species, frames_q_dev, frames_F_dev, n_frames, loss_out,
-                             grad_dev, h->stream);
+    if (train_frame_fits(h->train))
+        return train_force_match(h->train, h->geo, h->draft.dev, h->species, frames_q_dev, frames_F_dev, n_frames,
+                                 loss_out, grad_dev, h->stream);
+    TRY(train_large_pass(h, frames_q_dev, frames_F_dev, 0, n_frames, n_frames, false, 0.f));
+    if (grad_dev)
+        CK(cudaMemcpyAsync(grad_dev, h->train.grad, h->train.n_weights * sizeof(float), cudaMemcpyDeviceToDevice,
+                           h->stream));
+    float l = 0.f;
+    CK(cudaMemcpyAsync(&l, h->train.loss, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    TRY(wait_stream(h));
+    if (loss_out) *loss_out = l;
+    DevState st;
+    TRY(read_state(h, &st));
+    return check_err(st);
 }
 
 }  // extern "C"

@@ -373,7 +373,8 @@ int train_init(TrainState &t, const PotDev &P, const std::vector<float> &weights
 
 void train_free(TrainState &t) {
     for (void *p : {(void *)t.w, (void *)t.m, (void *)t.v, (void *)t.grad, (void *)t.loss, (void *)t.fq, (void *)t.fF,
-                    (void *)t.grad_frames, (void *)t.loss_frames})
+                    (void *)t.grad_frames, (void *)t.loss_frames, (void *)t.lH, (void *)t.lT, (void *)t.lV,
+                    (void *)t.lres, (void *)t.lFd, (void *)t.lloss, (void *)t.lpart})
         if (p) cudaFree(p);
     t = TrainState{};
 }
@@ -456,6 +457,213 @@ void enqueue_frame_capture(TrainState &t, const double *w_qmid, const float *w_F
     const int bx = (D + 255) / 256 < 64 ? (D + 255) / 256 : 64;
     frame_capture_kernel<<<dim3(bx, K), 256, 0, s>>>(w_qmid, w_Ft, K, N, t.capacity, t.start_verified, st, keff, t.fq,
                                                      t.fF);
+}
+
+// ---------------------------------------------------------------------------
+// Frames larger than one block's shared memory: the same gradient with the
+// frame's atoms as rows of the library's batched kernels (neighbour lists,
+// descriptors, pair gradients and the force gather, run by the caller with
+// the draft's parameters) and four kernels of its own:
+//   fm_mlp_kernel       h = W1 x + b1 and dE/dx = W1^T (w_out SiLU'(h)) per row
+//                       (FP32 master weights; the draft forces then come from
+//                       the pair-gradient and gather kernels);
+//   fm_residual_kernel  r_i = F~_i - F*_i and |r_i|^2 per row;
+//   fm_jvp_kernel       v_i = sum_p phi_k'(r_ip) dhat_ip . (r_{k_p} - r_i) per
+//                       species block, and t_i = W1 v_i;
+//   fm_wgrad_kernel     the per-weight sums of the double backward over rows,
+//                       per block of rows in order, then the blocks in order.
+// Deterministic: no atomics, fixed summation orders.
+// ---------------------------------------------------------------------------
+constexpr int kFmRowsPerBlock = 256;
+
+static int ensure_frame_bufs(TrainState &t, int n_frames);
+
+__global__ void fm_mlp_kernel(int M, int d0, int d0p, int W, const float *__restrict__ w, const float *__restrict__ X,
+                              float *__restrict__ H, float *__restrict__ G) {
+    const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= M) return;
+    const float *W1 = w, *b1 = w + (size_t)W * d0, *wo = b1 + W;
+    const float x = lane < d0 ? X[(size_t)row * d0p + lane] : 0.f;
+    float h = 0.f, gu = 0.f;
+    if (lane < W) h = b1[lane];
+    for (int f = 0; f < d0; ++f) {
+        const float xf = __shfl_sync(0xffffffffu, x, f);
+        if (lane < W) h = fmaf(W1[(size_t)lane * d0 + f], xf, h);
+    }
+    if (lane < W) {
+        H[(size_t)row * W + lane] = h;
+        gu = wo[lane] * dsiluf_(h);   // linear head: dE/dy = 1
+    }
+    float g = 0.f;
+    for (int u = 0; u < W; ++u) {
+        const float gv = __shfl_sync(0xffffffffu, gu, u);
+        if (lane < d0) g = fmaf(W1[(size_t)u * d0 + lane], gv, g);
+    }
+    if (lane < d0p) G[(size_t)row * d0p + lane] = g;
+}
+
+__global__ void fm_residual_kernel(int M, const float *__restrict__ Fd, const float *__restrict__ Fs,
+                                   float4 *__restrict__ res, float *__restrict__ loss_rows) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const float rx = Fd[3 * (size_t)i] - Fs[3 * (size_t)i], ry = Fd[3 * (size_t)i + 1] - Fs[3 * (size_t)i + 1],
+                rz = Fd[3 * (size_t)i + 2] - Fs[3 * (size_t)i + 2];
+    res[i] = make_float4(rx, ry, rz, 0.f);
+    loss_rows[i] = rx * rx + ry * ry + rz * rz;
+}
+
+__global__ void fm_jvp_kernel(int M, int d0, int d0p, int W, const float *__restrict__ w, const uint4 *__restrict__ fix,
+                              const int *__restrict__ near_keys, const int *__restrict__ n_near, int cap, Geo g,
+                              PotDev P, const float4 *__restrict__ res, float *__restrict__ V,
+                              float *__restrict__ T) {
+    extern __shared__ __align__(16) float fsm[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (row >= M) return;
+    float *sr = fsm + (size_t)wib * (3 * cap + 32), *sa = sr + cap;
+    int *ssp = (int *)(sa + cap);
+    float *sv = (float *)(ssp + cap);   // [32] v of this row
+    const uint4 fi = fix[row];
+    const float4 ri = res[row];
+    const int n = min(n_near[row], cap);
+    const int *keys = near_keys + (size_t)row * cap;
+    for (int p = lane; p < n; p += 32) {
+        const int key = keys[p];
+        const int k = key >> 5;
+        const uint4 fk = fix[k];
+        const float3 d = entry_disp(fi, fk, key & 31, g);
+        const float r = sqrtf(dist2_rule(d.x, d.y, d.z));
+        const float4 rk = res[k];
+        sr[p] = r;
+        sa[p] = (d.x * (rk.x - ri.x) + d.y * (rk.y - ri.y) + d.z * (rk.z - ri.z)) / r;
+        ssp[p] = (int)fk.w;
+    }
+    __syncwarp();
+    float acc[kMaxSpecies];
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s) acc[s] = 0.f;
+    const int kb = lane & 15;
+    if (kb < P.n_rbf) {
+        const float mu = (float)kb * P.rbf_w;
+        for (int p = lane >> 4; p < n; p += 2) {
+            float fc, dfc;
+            cutoff_fn(sr[p], P.desc_rc, fc, dfc);
+            const float t = sr[p] - mu;
+            const float dg = expf(-t * t * P.rbf_inv2w2) * (-t * P.rbf_invw2 * fc + dfc);
+#pragma unroll
+            for (int s = 0; s < kMaxSpecies; ++s) acc[s] += (ssp[p] == s) ? dg * sa[p] : 0.f;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s) acc[s] += __shfl_down_sync(0xffffffffu, acc[s], 16);
+    sv[lane] = 0.f;
+    __syncwarp();
+    if (lane < P.n_rbf)
+        for (int s = 0; s < g.S; ++s) sv[s * P.n_rbf + lane] = acc[s];
+    __syncwarp();
+    if (lane < d0p) V[(size_t)row * d0p + lane] = lane < d0 ? sv[lane] : 0.f;
+    if (lane < W) {
+        float t = 0.f;
+        for (int f = 0; f < d0; ++f) t = fmaf(w[(size_t)lane * d0 + f], sv[f], t);
+        T[(size_t)row * W + lane] = t;
+    }
+}
+
+// Per block of kFmRowsPerBlock rows, every weight's sum over the rows in order;
+// partials [blocks][nw].
+__global__ void fm_wgrad_kernel(int M, int d0, int d0p, int W, const float *__restrict__ w,
+                                const float *__restrict__ X, const float *__restrict__ H, const float *__restrict__ V,
+                                const float *__restrict__ T, float *__restrict__ partials) {
+    const int nw = W * d0 + 2 * W + 1;
+    const float *wo = w + (size_t)W * d0 + W;
+    const int r0 = blockIdx.x * kFmRowsPerBlock, r1 = min(M, r0 + kFmRowsPerBlock);
+    for (int e = threadIdx.x; e < nw; e += blockDim.x) {
+        float acc = 0.f;
+        if (e < W * d0) {
+            const int u = e / d0, f = e - u * d0;
+            for (int i = r0; i < r1; ++i) {
+                const float h = H[(size_t)i * W + u];
+                acc += wo[u] * (V[(size_t)i * d0p + f] * dsiluf_(h) + T[(size_t)i * W + u] * d2siluf_(h) *
+                                                                          X[(size_t)i * d0p + f]);
+            }
+        } else if (e < W * d0 + W) {
+            const int u = e - W * d0;
+            for (int i = r0; i < r1; ++i) acc += wo[u] * T[(size_t)i * W + u] * d2siluf_(H[(size_t)i * W + u]);
+        } else if (e < W * d0 + 2 * W) {
+            const int u = e - W * d0 - W;
+            for (int i = r0; i < r1; ++i) acc += T[(size_t)i * W + u] * dsiluf_(H[(size_t)i * W + u]);
+        }
+        partials[(size_t)blockIdx.x * nw + e] = acc;
+    }
+}
+
+// One frame's gradient and loss from the row-block partials, in block order.
+__global__ void fm_frame_sum_kernel(const float *__restrict__ partials, int n_blocks, int nw,
+                                    const float *__restrict__ loss_rows, int M, float scale,
+                                    float *__restrict__ grad_frame, float *__restrict__ loss_frame) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nw) {
+        float s = 0.f;
+        for (int b = 0; b < n_blocks; ++b) s += partials[(size_t)b * nw + e];
+        grad_frame[e] = scale * s;
+    }
+    if (e == 0) {
+        float l = 0.f;
+        for (int i = 0; i < M; ++i) l += loss_rows[i];
+        *loss_frame = -0.5f * scale * l;   // scale = -2/(F*3N)
+    }
+}
+
+bool train_frame_fits(const TrainState &t) { return t.N <= kTrainMaxN; }
+
+int train_large_bufs(TrainState &t, int n_frames) {
+    const int M = t.N, d0p = (t.d0 + 31) / 32 * 32;
+    if (!t.lH) {
+        const size_t nb = (size_t)(M + kFmRowsPerBlock - 1) / kFmRowsPerBlock;
+        if (cudaMalloc(&t.lH, (size_t)M * t.W * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&t.lT, (size_t)M * t.W * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&t.lV, (size_t)M * d0p * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&t.lres, (size_t)M * sizeof(float4)) != cudaSuccess ||
+            cudaMalloc(&t.lFd, (size_t)M * 3 * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&t.lloss, (size_t)M * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&t.lpart, nb * t.n_weights * sizeof(float)) != cudaSuccess)
+            return LSD_ENOMEM;
+    }
+    return ensure_frame_bufs(t, n_frames);
+}
+
+void launch_fm_mlp(const TrainState &t, const float *X, int d0p, float *G, cudaStream_t s) {
+    const int M = t.N;
+    fm_mlp_kernel<<<(M * 32 + 255) / 256, 256, 0, s>>>(M, t.d0, d0p, t.W, t.w, X, t.lH, G);
+}
+
+void launch_fm_frame_grad(const TrainState &t, const uint4 *fix, const int *near_keys, const int *n_near, int cap,
+                          const Geo &g, const PotDev &P, const float *X, int d0p, const float *Fstar, float scale,
+                          int frame_index, cudaStream_t s) {
+    const int M = t.N;
+    fm_residual_kernel<<<(M + 255) / 256, 256, 0, s>>>(M, t.lFd, Fstar, t.lres, t.lloss);
+    const int warps = 8;
+    const size_t sm = (size_t)warps * (3 * cap + 32) * sizeof(float);
+    fm_jvp_kernel<<<(M + warps - 1) / warps, warps * 32, sm, s>>>(M, t.d0, d0p, t.W, t.w, fix, near_keys, n_near, cap, g,
+                                                                  P, t.lres, t.lV, t.lT);
+    const int nb = (M + kFmRowsPerBlock - 1) / kFmRowsPerBlock;
+    fm_wgrad_kernel<<<nb, 256, 0, s>>>(M, t.d0, d0p, t.W, t.w, X, t.lH, t.lV, t.lT, t.lpart);
+    const int nw = (int)t.n_weights;
+    fm_frame_sum_kernel<<<(nw + 255) / 256, 256, 0, s>>>(t.lpart, nb, nw, t.lloss, M, scale,
+                                                         t.grad_frames + (size_t)frame_index * nw,
+                                                         t.loss_frames + frame_index);
+}
+
+void launch_fm_reduce_adam(TrainState &t, int n_frames, bool adam, float lr, cudaStream_t s) {
+    const int nw = (int)t.n_weights;
+    fm_reduce_kernel<<<(nw + 255) / 256, 256, 0, s>>>(t.grad_frames, t.loss_frames, n_frames, nw, t.grad, t.loss);
+    if (!adam) return;
+    ++t.adam_t;
+    ++t.iter;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)t.adam_t), c2 = 1.f - powf(b2, (float)t.adam_t);
+    adam_kernel<<<(nw + 255) / 256, 256, 0, s>>>(t.w, t.m, t.v, t.grad, nw, lr, b1, b2, 1e-8f, c1, c2);
 }
 
 size_t train_adam_size(const TrainState &t) { return t.enabled ? t.n_weights : 0; }

@@ -27,6 +27,9 @@ struct TrainState {
     float *grad = nullptr;          // [n_weights]
     float *loss = nullptr;          // [1]
     int max_frames = 0;
+    // frames larger than one block: per-row workspace of one frame
+    float *lH = nullptr, *lT = nullptr, *lV = nullptr, *lFd = nullptr, *lloss = nullptr, *lpart = nullptr;
+    float4 *lres = nullptr;
     long long adam_t = 0;
     long long iter = 0;
     DevState *st = nullptr;
@@ -46,6 +49,14 @@ int train_adam_get(TrainState &t, float *m, float *v);
 int train_adam_set(TrainState &t, const float *m, const float *v);
 int train_run(TrainState &t, const Geo &g, const PotDev &P, const int *species, int n_iters, float lr,
               int frames_per_iter, float *loss_out, cudaStream_t s);
+// frames larger than one block (the caller runs lists, descriptors, pair gradients and the gather)
+bool train_frame_fits(const TrainState &t);
+int train_large_bufs(TrainState &t, int n_frames);
+void launch_fm_mlp(const TrainState &t, const float *X, int d0p, float *G, cudaStream_t s);
+void launch_fm_frame_grad(const TrainState &t, const uint4 *fix, const int *near_keys, const int *n_near, int cap,
+                          const Geo &g, const PotDev &P, const float *X, int d0p, const float *Fstar, float scale,
+                          int frame_index, cudaStream_t s);
+void launch_fm_reduce_adam(TrainState &t, int n_frames, bool adam, float lr, cudaStream_t s);
 int train_force_match(TrainState &t, const Geo &g, const PotDev &P, const int *species, const double *fq,
                       const float *fF, int n_frames, float *loss_out, float *grad_dev, cudaStream_t s);
 

@@ -34,7 +34,7 @@ SYMBOLS = ["lsd_init", "lsd_draft_window", "lsd_verify_window", "lsd_step", "lsd
            "lsd_descriptors", "lsd_get_window", "lsd_profile_window", "lsd_checkpoint", "lsd_restore", "lsd_query",
            "lsd_target_mlp_static_dev", "lsd_destroy",
            "lsd_strerror", "lsd_launch_counts", "lsd_window_host", "lsd_transport_window", "lsd_get_frames",
-           "lsd_set_max_displacement", "lsd_set_plain_fused"]
+           "lsd_set_max_displacement", "lsd_set_plain_fused", "lsd_set_online_training", "lsd_online_status"]
 
 
 class LSDError(RuntimeError):
@@ -111,6 +111,8 @@ def _lib():
             "lsd_get_frames": [P, I64, I64, P, P],
             "lsd_set_max_displacement": [P, D],
             "lsd_set_plain_fused": [P, I32],
+            "lsd_set_online_training": [P, I64, I32, ctypes.c_float, I32],
+            "lsd_online_status": [P, P, P],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -335,6 +337,16 @@ class LSD:
         F = np.zeros((count, self.N, 3), np.float32)
         _check(_lib().lsd_get_frames(self.h, int(first), int(count), _p(q), _p(F)), "lsd_get_frames")
         return q, F
+
+    def set_online_training(self, every_accepted, n_iters=100, lr=3e-3, frames_per_iter=0):
+        """Retrain the learned draft during step() every `every_accepted` accepted steps (0: off)."""
+        _check(_lib().lsd_set_online_training(self.h, int(every_accepted), int(n_iters), float(lr),
+                                              int(frames_per_iter)), "lsd_set_online_training")
+
+    def online_status(self):
+        n, l = ctypes.c_int64(), ctypes.c_float()
+        _check(_lib().lsd_online_status(self.h, ctypes.byref(n), ctypes.byref(l)), "lsd_online_status")
+        return n.value, l.value
 
     def train_draft(self, n_iters, lr, frames_per_iter=0):
         loss = ctypes.c_float()
