@@ -217,6 +217,21 @@ LSD_API int lsd_plain_step(lsd_handle *h, int64_t n_steps);
  * the handle's configuration has no fused plan. */
 LSD_API int lsd_set_plain_fused(lsd_handle *h, int32_t on);
 
+/* lsd_set_grid_draft: the form of the draft (Alg. 2, draft_step K times) for
+ * systems of at least 2048 atoms with a cell grid.  on (the default where
+ * available): every draft that has the GPU to itself (lsd_draft_window, the
+ * unpipelined window, the pipelined loop's first draft and redraft) runs as
+ * one cooperative launch of one 512-thread CTA per SM with a bounded
+ * grid-wide barrier per step (two with a learned draft); the pipelined loop's
+ * speculative draft, which overlaps a verification, stays in the cluster form
+ * (at most 16 SMs).  off: every draft in the cluster form.  Both forms compute
+ * each atom's force in the same order and give the same bits.  A grid barrier
+ * that waits more than about two seconds ends the window early and sets
+ * LSD_ETIMEOUT.  LSD_EUNSUPPORTED when on is requested and the handle has no
+ * grid form (fewer atoms, no cell grid, or a device that cannot co-schedule
+ * the grid). */
+LSD_API int lsd_set_grid_draft(lsd_handle *h, int32_t on);
+
 /* lsd_enqueue_windows / lsd_enqueue_plain: enqueue n window graphs (or n
  * plain target steps) on the handle's stream and return without waiting;
  * windows run until the caller synchronises the stream (e.g. with CUDA events

@@ -74,6 +74,9 @@ struct lsd_handle {
     PotHost draft, target;
     bool learned_small = false;
     DraftPlan dplan{};
+    DraftPlan gplan{};              // the grid form of the draft (large systems), when the device co-schedules it
+    bool grid_draft = false;        // windows and redrafts draft in the grid form
+    DraftSync *dsync = nullptr;     // its barrier and flag words
     VerletPlan vplan{};
     VerletBufs vbufs{};
     float *w_dEdX = nullptr;
@@ -458,9 +461,11 @@ void enqueue_draft_buf(lsd_handle *h, int b, cudaStream_t s, WinHdr *hdr, const 
         launch_verlet_build(h->vplan, q, h->species, h->geo, w.vb, h->st, s,
                             hdr ? (redraft ? &hdr->keep : &hdr->skip) : nullptr);
     }
-    launch_draft(h->dplan, h->learned_small, h->K, h->geo, h->draft.dev, h->coef, h->vplan, w.vb, h->species, q, p,
-                 h->ec_dF, h->ec_on, h->st, w.qmid, w.pdraft, w.Fd, w.Fraw, w.fix, h->w_dEdX, s, hdr,
-                 redraft ? 1 : 0);
+    // the speculative draft of the pipelined loop overlaps a verification: the cluster form, on a few SMs
+    const bool grid = h->grid_draft && (!hdr || redraft);
+    launch_draft(grid ? h->gplan : h->dplan, h->learned_small, h->K, h->geo, h->draft.dev, h->coef, h->vplan, w.vb,
+                 h->species, q, p, h->ec_dF, h->ec_on, h->st, w.qmid, w.pdraft, w.Fd, w.Fraw, w.fix, h->w_dEdX, s, hdr,
+                 redraft ? 1 : 0, h->dsync);
 }
 
 // Verification, frames and transport of window buffer b; keff: the window's
@@ -882,6 +887,17 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
             h->dplan.minimg = rcd < 0.499 * lmin;
         }
         if (!h->dplan.ok) return fail(LSD_EUNSUPPORTED);
+        // large systems: the grid form for every draft that has the GPU to itself
+        if (h->N >= kGridDraftMinAtoms) {
+            DraftPlan gp = draft_grid_plan(h->N, K, h->draft.dev, h->learned_small, vp.cap, vp.all_pairs, h->n_sm,
+                                           kMaxDynSmem);
+            gp.minimg = h->dplan.minimg;
+            if (gp.ok && draft_grid_fits(gp, h->learned_small, h->n_sm)) {
+                h->gplan = gp;
+                h->grid_draft = true;
+            }
+            cudaGetLastError();
+        }
     }
     const size_t N = h->N, D = 3 * N, KN = (size_t)K * N, KD = (size_t)K * D;
     const int dmax = std::max(h->draft.dev.d0p, h->target.dev.d0p);
@@ -897,6 +913,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         (rc = dalloc(h, &h->pair_g, KN * h->cap_near)) || (rc = dalloc(h, &h->Fpart, KN)) ||
         (rc = dalloc(h, &h->partials, (size_t)K * ((h->N + 1023) / 1024 + 600))) ||
         (rc = dalloc(h, &h->w_dEdX, N * std::max(h->draft.dev.d0p, 32))) ||
+        (rc = dalloc(h, &h->dsync, 1)) ||
         (rc = dalloc(h, &h->vbufs.fix_base, N)) || (rc = dalloc(h, &h->vbufs.cell_of_atom, N)) ||
         (rc = dalloc(h, &h->vbufs.cell_count, (size_t)h->vplan.nc[0] * h->vplan.nc[1] * h->vplan.nc[2])) ||
         (rc = dalloc(h, &h->vbufs.cell_start, (size_t)h->vplan.nc[0] * h->vplan.nc[1] * h->vplan.nc[2] + 1)) ||
@@ -1497,6 +1514,15 @@ int lsd_launch_counts(const lsd_handle *h, int32_t *per_window, int32_t *per_rou
     // verify; spec_base; speculative draft; redraft (with its flag kernel in list mode)
     if (per_round) *per_round = verify + 1 + draft + (lists ? 1 : 0) + draft;
     if (per_plain) *per_plain = use_plain_fused(h) ? 0 : verlet + 1 + eval + 1;
+    return LSD_OK;
+}
+
+int lsd_set_grid_draft(lsd_handle *h, int32_t on) {
+    if (!h) return LSD_EINVAL;
+    if (on && !h->gplan.ok) return LSD_EUNSUPPORTED;
+    TRY(wait_stream(h));
+    if (h->grid_draft != (on != 0)) destroy_graphs(h);   // the draft launch is part of the captured graphs
+    h->grid_draft = on != 0;
     return LSD_OK;
 }
 

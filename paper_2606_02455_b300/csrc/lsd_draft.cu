@@ -12,6 +12,13 @@
 // by asynchronous stores that complete bytes on the receiving CTA's mbarrier;
 // each CTA waits until the step's N positions have landed (bounded wait).
 // Larger systems use a cluster barrier and read the positions through L2.
+// Large systems also have a grid form of the same kernel: one CTA per SM in a
+// cooperative launch, a bounded grid-wide barrier per step in place of the
+// cluster barrier, and the displacement flags in global memory.  The per-atom
+// arithmetic (and its order) is the cluster form's, so both give the same
+// bits; the window loop runs the grid form when nothing else needs the SMs
+// (an unpipelined window, a redraft) and the cluster form for the speculative
+// draft that overlaps a verification.
 //
 // Candidates come from Verlet lists (cutoff + skin around a base): the
 // window's lists from lsd_verlet.cu on a cell grid of three or more cells per
@@ -40,6 +47,36 @@ constexpr int kMaxCluster = 16;    // largest draft cluster
 
 __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// A barrier over every CTA of a cooperative launch (one CTA per SM, all
+// resident).  Bounded: it gives up after about two seconds, or at once when
+// another CTA has given up (sync->abort), so a stalled grid ends within one
+// time-out instead of one per remaining step.
+// (No static shared memory: the kernels' dynamic allowance is the device's maximum.)
+__device__ bool draft_grid_barrier(DraftSync *sync, unsigned total) {
+    int ok = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long arrive = atomicAdd(&sync->bar, 1ull);
+        const unsigned long long target = (arrive / total + 1ull) * total;
+        const long long t0 = clock64();
+        for (;;) {
+            unsigned long long v;
+            unsigned ab;
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(&sync->bar) : "memory");
+            if (v >= target) break;
+            asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(ab) : "l"(&sync->abort) : "memory");
+            if (ab != 0u || clock64() - t0 > 4000000000ll) {
+                ok = 0;
+                atomicExch(&sync->abort, 1u);
+                break;
+            }
+        }
+        __threadfence();
+    }
+    return __syncthreads_and(ok) != 0;   // thread 0's verdict, for every thread
 }
 
 
@@ -223,7 +260,9 @@ __device__ __forceinline__ bool spec_is_valid(const WinHdr *hn, const DevState *
     return hn->skip == 0 && hn->base == st->step && st->first_reject_last == -1;
 }
 
-template <bool LEARNED, bool REG>
+// GRID: the grid form (gridDim.x CTAs of a cooperative launch; stage_fix and
+// self_list are 0; sync zeroed before the launch).
+template <bool LEARNED, bool REG, bool GRID>
 __global__ void __launch_bounds__(kDraftThreads, 1)
     draft_window_cluster_kernel(int K, Geo g, PotDev P, Coef cf, const int *__restrict__ vlist,
                                 const int *__restrict__ vcount, int vcap, const uint4 *__restrict__ fix_base,
@@ -234,7 +273,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                                 const float *__restrict__ ec_dF, int ec_on, DevState *__restrict__ st,
                                 double *__restrict__ w_qmid, double *__restrict__ w_pdraft, float *__restrict__ w_Fd,
                                 float *__restrict__ w_Fraw, uint4 *__restrict__ w_fix, float *__restrict__ w_dEdX,
-                                WinHdr *__restrict__ hdr, int redraft) {
+                                WinHdr *__restrict__ hdr, int redraft, DraftSync *__restrict__ sync) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N;
     const int C = gridDim.x, c = blockIdx.x;
@@ -393,7 +432,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
         }
     }
     // every CTA has started, zeroed its flags and initialised its mbarriers before the first remote store
-    if (stage_fix || use_list) cluster_barrier();
+    if (!GRID && (stage_fix || use_list)) cluster_barrier();
     __syncthreads();
     int keff = K;
     bool gave_up = false;   // this CTA's wait for a step's positions ran out of time
@@ -474,7 +513,10 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
         }
         if (use_list) {
             moved = __syncthreads_or(moved);
-            if (stage_fix) {
+            if (GRID) {
+                // K - j: the largest value marks the earliest step at which an atom left the skin
+                if (moved && tid == 0) atomicMax(&sync->moved, (unsigned)(K - j));
+            } else if (stage_fix) {
                 if (side >= 0 && side < C)
                     tc::st_async(tc::cluster_map(tc::smem_u32(sflag + par * kMaxCluster + c), (uint32_t)side),
                                  moved ? 1u : 0u, tc::cluster_map(bar0 + 8 * par, (uint32_t)side));
@@ -516,6 +558,17 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                 keff = j;
                 break;
             }
+        } else if (GRID) {
+            if (!draft_grid_barrier(sync, (unsigned)C)) {
+                if (tid == 0) atomicOr(&st->err, 8);
+                keff = j;
+                break;
+            }
+            // every flag of steps <= j was raised before this barrier; later steps' flags are smaller
+            if (use_list && *(volatile unsigned *)&sync->moved >= (unsigned)(K - j)) {
+                keff = j;
+                break;
+            }
         } else {
             cluster_barrier();
             if (use_list && sflag[par]) {
@@ -534,7 +587,16 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                 learned_atom_grad(P, g, fx, i, cand, use_list ? (stage_list ? svc[ii] : vcount[i]) : N,
                                   minimg != 0, stage, stage + 3 * kLearnCap, w_dEdX + (size_t)i * P.d0p);
             }
-            cluster_barrier();   // dE/dx of every atom visible to every CTA
+            // dE/dx of every atom visible to every CTA
+            if (GRID) {
+                if (!draft_grid_barrier(sync, (unsigned)C)) {
+                    if (tid == 0) atomicOr(&st->err, 8);
+                    keff = j;
+                    break;
+                }
+            } else {
+                cluster_barrier();
+            }
             if (stage_dedx) {
                 // the radial block of every atom's dE/dX into shared memory: one coalesced pass
                 // instead of two L2 round trips per neighbour pair and basis function
@@ -666,7 +728,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
         }
         __syncthreads();
         // the flag of this parity is next written (by any CTA) after the next barrier
-        if (use_list && !stage_fix && tid == 0) sflag[par] = 0;
+        if (!GRID && use_list && !stage_fix && tid == 0) sflag[par] = 0;
         // D: BOB + A, one lane per coordinate
         auto step_d = [&](int p, double &preg, float dfreg, float xreg, double c1p_r, double sxi_r) {
             const int ii = grp + p * kGroups;
@@ -785,21 +847,55 @@ DraftPlan draft_plan(int N, int K, const PotDev &P, bool learned, int vcap, bool
     return pl;
 }
 
+// The grid form: one CTA per SM, positions through L2, the window's Verlet
+// lists (a cell grid is required: without one every atom would be every
+// CTA's candidate).
+DraftPlan draft_grid_plan(int N, int K, const PotDev &P, bool learned, int vcap, bool all_pairs, int n_sm,
+                          size_t max_smem) {
+    DraftPlan pl{};
+    if (all_pairs || vcap <= 0 || n_sm <= 0) return pl;
+    const int C = n_sm < N ? n_sm : N;
+    const int A = (N + C - 1) / C;
+    pl.cluster = C;
+    pl.grid = true;
+    pl.stage_fix = false;
+    pl.self_list = false;
+    pl.K = K;
+    pl.noise_smem = (size_t)K * A * 3 * sizeof(float) <= kNoiseSmemMax;
+    pl.stage_list = (size_t)A * (vcap + 1) * sizeof(int) <= kListSmemMax;
+    const int S = P.n_rbf > 0 ? (P.d0 - P.n_ang) / (P.n_rbf + 1) : 0;
+    const size_t dedx = (size_t)N * S * P.n_rbf;
+    pl.stage_dedx = learned && dedx > 0 && dedx * sizeof(float) <= kDedxSmemMax;
+    pl.smem = draft_smem_bytes(N, C, P, learned, false, pl.noise_smem ? K : 0, vcap, pl.stage_list,
+                               pl.stage_dedx ? dedx : 0);
+    pl.reg = A <= kRegPasses * kGroups;
+    pl.ok = pl.smem <= max_smem;
+    return pl;
+}
+
 cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf,
                          const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
                          const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
                          double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX,
-                         cudaStream_t s, WinHdr *hdr, int redraft) {
+                         cudaStream_t s, WinHdr *hdr, int redraft, DraftSync *sync) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(pl.cluster, 1, 1);
     cfg.blockDim = dim3(kDraftThreads, 1, 1);
     cfg.dynamicSmemBytes = pl.smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = pl.cluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
+    if (pl.grid) {
+        if (!sync) return cudaErrorInvalidValue;
+        const cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(DraftSync), s);
+        if (e != cudaSuccess) return e;
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+    } else {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = pl.cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+    }
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const int stage = pl.stage_fix ? 1 : 0;
@@ -809,16 +905,27 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
     const int self = (pl.self_list && vp.all_pairs) ? 1 : 0;
     const int sl = (pl.stage_list && (vl || self)) ? 1 : 0;
     const int sd = (learned && pl.stage_dedx) ? 1 : 0;
-    auto kern = learned ? (pl.reg ? draft_window_cluster_kernel<true, true> : draft_window_cluster_kernel<true, false>)
-                        : (pl.reg ? draft_window_cluster_kernel<false, true> : draft_window_cluster_kernel<false, false>);
+    using Kern = decltype(&draft_window_cluster_kernel<false, false, false>);
+    static const Kern kerns[8] = {
+        draft_window_cluster_kernel<false, false, false>, draft_window_cluster_kernel<false, true, false>,
+        draft_window_cluster_kernel<true, false, false>,  draft_window_cluster_kernel<true, true, false>,
+        draft_window_cluster_kernel<false, false, true>,  draft_window_cluster_kernel<false, true, true>,
+        draft_window_cluster_kernel<true, false, true>,   draft_window_cluster_kernel<true, true, true>};
+    const Kern kern = kerns[(pl.grid ? 4 : 0) + (learned ? 2 : 0) + (pl.reg ? 1 : 0)];
     return cudaLaunchKernelEx(&cfg, kern, K, g, P, cf, vl, (const int *)vb.vcount, vp.cap, (const uint4 *)vb.fix_base,
                               vp.move2f, vp.rlist2f, stage, mi, ns, sl, self, sd, species, q, p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd,
-                              w_Fraw, w_fix, w_dEdX, hdr, redraft);
+                              w_Fraw, w_fix, w_dEdX, hdr, redraft, sync);
 }
 
-static const void *draft_kernel_ptrs[4] = {
-    (const void *)draft_window_cluster_kernel<false, false>, (const void *)draft_window_cluster_kernel<false, true>,
-    (const void *)draft_window_cluster_kernel<true, false>, (const void *)draft_window_cluster_kernel<true, true>};
+static const void *draft_kernel_ptrs[8] = {
+    (const void *)draft_window_cluster_kernel<false, false, false>,
+    (const void *)draft_window_cluster_kernel<false, true, false>,
+    (const void *)draft_window_cluster_kernel<true, false, false>,
+    (const void *)draft_window_cluster_kernel<true, true, false>,
+    (const void *)draft_window_cluster_kernel<false, false, true>,
+    (const void *)draft_window_cluster_kernel<false, true, true>,
+    (const void *)draft_window_cluster_kernel<true, false, true>,
+    (const void *)draft_window_cluster_kernel<true, true, true>};
 
 cudaError_t draft_kernels_setup(int max_smem) {
     for (const void *k : draft_kernel_ptrs) {
@@ -828,6 +935,17 @@ cudaError_t draft_kernels_setup(int max_smem) {
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// Every CTA of the grid form resident at once (the cooperative launch's condition).
+bool draft_grid_fits(const DraftPlan &pl, bool learned, int n_sm) {
+    int per_sm = 0;
+    const void *k = draft_kernel_ptrs[4 + (learned ? 2 : 0) + (pl.reg ? 1 : 0)];
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kDraftThreads, pl.smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return per_sm * n_sm >= pl.cluster;
 }
 
 int draft_max_cluster(size_t smem, bool learned) {

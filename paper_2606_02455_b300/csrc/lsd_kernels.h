@@ -114,8 +114,15 @@ void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, c
                       const int *keff, cudaStream_t s);
 
 // draft and plain integrator (lsd_draft.cu)
+// The grid-form draft's synchronisation words, zeroed before each launch.
+struct DraftSync {
+    unsigned long long bar;   // grid-barrier arrivals
+    unsigned moved;           // K - j of the earliest step j at which an atom left the lists' skin (0: none)
+    unsigned abort;           // a CTA's barrier wait ran out of time
+};
 struct DraftPlan {
-    int cluster;      // CTAs in the draft cluster (one per SM)
+    int cluster;      // CTAs in the draft cluster (one per SM); the grid form: CTAs of the cooperative grid
+    bool grid;        // the grid form (cooperative launch, grid-wide barriers)
     bool stage_fix;   // positions of a step staged in shared memory
     size_t smem;      // dynamic shared memory per CTA
     bool reg;         // owned atoms' FP64 state in registers
@@ -129,12 +136,16 @@ struct DraftPlan {
 };
 DraftPlan draft_plan(int N, int K, const PotDev &P, bool learned, int vcap, bool all_pairs, int max_cluster,
                      size_t max_smem);
+constexpr int kGridDraftMinAtoms = 2048;   // smaller systems draft in one cluster only
+bool draft_grid_fits(const DraftPlan &pl, bool learned, int n_sm);
+DraftPlan draft_grid_plan(int N, int K, const PotDev &P, bool learned, int vcap, bool all_pairs, int n_sm,
+                          size_t max_smem);
 int draft_max_cluster(size_t smem, bool learned);
 cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf,
                          const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
                          const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
                          double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX,
-                         cudaStream_t s, WinHdr *hdr = nullptr, int redraft = 0);
+                         cudaStream_t s, WinHdr *hdr = nullptr, int redraft = 0, DraftSync *sync = nullptr);
 // the fused plain-target step (lsd_plain.cu)
 constexpr int kPlainMaxN = 512;
 struct PlainPlan {

@@ -71,39 +71,67 @@ __device__ __forceinline__ void nb_stage_load(const NbStage &S, const uint4 *fj,
 }
 
 
+// The angular weights of one row in the packed form of the pair loop.  The
+// sixteen angular features are T[z][l][e] = 2^(1 - zeta) sum_{p<q} (1 + lambda
+// c)^zeta E_e fc_p fc_q (zeta = 1, 2, 4, 8 for z = 0..3, lambda = +1, -1 for
+// l = 0, 1, eta = 0.005, 0.05 for e = 0, 1), feature index 4 z + 2 l + e.  With
+// w = dE/dX of those features, the pair loop needs, per eta,
+//   S0_e = sum_z pref_z (w[z][0][e] b+^zeta + w[z][1][e] b-^zeta)
+//   S1_e = dS0_e/dc = sum_z zeta pref_z (w[z][0][e] b+^(zeta-1) - w[z][1][e] b-^(zeta-1))
+// with b+- = 1 +- c.  Both are dot products over (z, lambda); packed over lambda
+// they are fused multiply-adds of float pairs (two lanes of FP32 work per
+// instruction) with the (b+^k, b-^k) pairs.
+struct AngW {
+    float2 w0[4][2];   // [z][e]: pref_z (w[z][0][e], w[z][1][e])
+    float2 w1[3][2];   // [z - 1][e], zeta 2, 4, 8: zeta pref_z (w[z][0][e], -w[z][1][e])
+    float c1[2];       // [e]: the zeta = 1 term of S1_e, w[0][0][e] - w[0][1][e]
+};
+
+__device__ __forceinline__ AngW ang_weights(const float (&w)[kNAng]) {
+    constexpr float pref[4] = {1.f, 0.5f, 0.125f, 0.0078125f};   // 2^(1 - zeta)
+    constexpr float zpref[4] = {1.f, 1.f, 0.5f, 0.0625f};         // zeta 2^(1 - zeta)
+    AngW a;
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            a.w0[z][e] = make_float2(pref[z] * w[4 * z + e], pref[z] * w[4 * z + 2 + e]);
+            if (z > 0) a.w1[z - 1][e] = make_float2(zpref[z] * w[4 * z + e], -zpref[z] * w[4 * z + 2 + e]);
+        }
+    a.c1[0] = w[0] - w[2];
+    a.c1[1] = w[1] - w[3];
+    return a;
+}
+
 // The angular term T(c_pq, r_p, r_q) of one unordered pair: dT/dd_p =
 // A d_q + B_p d_p is added to p's accumulators (a*), and dT/dd_q = A d_p +
-// B_q d_q is returned for q.  wang: dE/dX of the angular features.
-__device__ __forceinline__ float4 pair_terms(const NbStage &S, const float (&wang)[kNAng], int p, int q, float &ax,
-                                             float &ay, float &az, float &ab) {
+// B_q d_q is returned for q.
+__device__ __forceinline__ float4 pair_terms(const NbStage &S, const AngW &W, int p, int q, float &ax, float &ay,
+                                             float &az, float &ab) {
     const float4 gp = S.g[p], gq = S.g[q], cp = S.c[p], cq = S.c[q];
     const float xp = gp.x, yp = gp.y, zp = gp.z, xq = gq.x, yq = gq.y, zq = gq.z;
     const float rip = gp.w, riq = gq.w;
     const float inv_pq = rip * riq;
     const float cth = (xp * xq + yp * yq + zp * zq) * inv_pq;
     const float fp = cp.x, fq = cq.x;
+    // (b+^k, b-^k) for k = 1, 2, 3, 4, 7, 8
+    const float2 b1 = make_float2(1.f + cth, 1.f - cth);
+    const float2 b2 = __fmul2_rn(b1, b1), b4 = __fmul2_rn(b2, b2);
+    const float2 b3 = __fmul2_rn(b2, b1), b8 = __fmul2_rn(b4, b4), b7 = __fmul2_rn(b4, b3);
+    float2 t0[2], t1[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        t0[e] = __fmul2_rn(W.w0[0][e], b1);
+        t0[e] = __ffma2_rn(W.w0[1][e], b2, t0[e]);
+        t0[e] = __ffma2_rn(W.w0[2][e], b4, t0[e]);
+        t0[e] = __ffma2_rn(W.w0[3][e], b8, t0[e]);
+        t1[e] = __ffma2_rn(W.w1[0][e], b1, make_float2(W.c1[e], 0.f));
+        t1[e] = __ffma2_rn(W.w1[1][e], b3, t1[e]);
+        t1[e] = __ffma2_rn(W.w1[2][e], b7, t1[e]);
+    }
+    const float S0_1 = t0[0].x + t0[0].y, S0_2 = t0[1].x + t0[1].y;
+    const float S1_1 = t1[0].x + t1[0].y, S1_2 = t1[1].x + t1[1].y;
     const float E1 = cp.z * cq.z, E2 = cp.w * cq.w;
-    // (1 + lambda c)^zeta and zeta (1 + lambda c)^(zeta - 1), lambda = +1 (p) and -1 (m)
-    const float bp1 = 1.f + cth, bm1 = 1.f - cth;
-    const float bp2 = bp1 * bp1, bm2 = bm1 * bm1, bp4 = bp2 * bp2, bm4 = bm2 * bm2;
-    const float bp8 = bp4 * bp4, bm8 = bm4 * bm4;
-    const float bp3 = bp2 * bp1, bm3 = bm2 * bm1, bp7 = bp4 * bp3, bm7 = bm4 * bm3;
-    // per eta: S0 = sum_a w_a pref pow (value weights), S1 = dS0/dc
-    float S0_1 = 0.f, S0_2 = 0.f, S1_1 = 0.f, S1_2 = 0.f;
-    // zeta 1: pref 1
-    S0_1 += wang[0] * bp1 + wang[2] * bm1;  S0_2 += wang[1] * bp1 + wang[3] * bm1;
-    S1_1 += wang[0] - wang[2];              S1_2 += wang[1] - wang[3];
-    // zeta 2: pref 1/2, zeta*pow1*pref = b
-    S0_1 += 0.5f * (wang[4] * bp2 + wang[6] * bm2);  S0_2 += 0.5f * (wang[5] * bp2 + wang[7] * bm2);
-    S1_1 += wang[4] * bp1 - wang[6] * bm1;           S1_2 += wang[5] * bp1 - wang[7] * bm1;
-    // zeta 4: pref 1/8, zeta*pow1*pref = b^3/2
-    S0_1 += 0.125f * (wang[8] * bp4 + wang[10] * bm4);  S0_2 += 0.125f * (wang[9] * bp4 + wang[11] * bm4);
-    S1_1 += 0.5f * (wang[8] * bp3 - wang[10] * bm3);    S1_2 += 0.5f * (wang[9] * bp3 - wang[11] * bm3);
-    // zeta 8: pref 1/128, zeta*pow1*pref = b^7/16
-    S0_1 += 0.0078125f * (wang[12] * bp8 + wang[14] * bm8);
-    S0_2 += 0.0078125f * (wang[13] * bp8 + wang[15] * bm8);
-    S1_1 += 0.0625f * (wang[12] * bp7 - wang[14] * bm7);
-    S1_2 += 0.0625f * (wang[13] * bp7 - wang[15] * bm7);
     const float ffq = fp * fq;
     const float S1E = (S1_1 * E1 + S1_2 * E2) * ffq, S0E = S0_1 * E1 + S0_2 * E2;
     // d/dd_p: S1 E ff (d_q / (r_p r_q) - c d_p / r_p^2) - 2 eta S0 E ff d_p + S0 E dfc_p fc_q d_p / r_p
@@ -148,28 +176,40 @@ __device__ __forceinline__ void desc_row(const NbStage &S, int n, const PotDev &
     }
     // angular
     if (P.n_ang) {
-        float a[kNAng];
+        // per (zeta, eta) the pair (lambda = +1, lambda = -1) of sums of b^zeta E_eta fc_p fc_q, packed: one fused
+        // multiply-add of a float pair per (zeta, eta); the prefactors 2^(1 - zeta) (powers of two) are applied
+        // to the warp totals
+        float2 acc[4][2];
 #pragma unroll
-        for (int t = 0; t < kNAng; ++t) a[t] = 0.f;
+        for (int z = 0; z < 4; ++z) acc[z][0] = acc[z][1] = make_float2(0.f, 0.f);
         const int npairs = n * (n - 1) / 2;
         PairIter it(n, lane);
         for (int t = lane; t < npairs; t += 32, it.next()) {
             const int p = it.p, q = it.q();
-            {
-                const float4 gp = S.g[p], gq = S.g[q], cp = S.c[p], cq = S.c[q];
-                const float c = (gp.x * gq.x + gp.y * gq.y + gp.z * gq.z) * (gp.w * gq.w);
-                const float ff = cp.x * cq.x;
-                const float E1 = cp.z * cq.z * ff, E2 = cp.w * cq.w * ff;
-                const float bp1 = 1.f + c, bm1 = 1.f - c;
-                const float bp2 = bp1 * bp1, bm2 = bm1 * bm1, bp4 = bp2 * bp2, bm4 = bm2 * bm2;
-                const float bp8 = bp4 * bp4, bm8 = bm4 * bm4;
-                // zeta = 1 (2^0), 2 (2^-1), 4 (2^-3), 8 (2^-7)
-                a[0] += bp1 * E1; a[1] += bp1 * E2; a[2] += bm1 * E1; a[3] += bm1 * E2;
-                a[4] += 0.5f * bp2 * E1; a[5] += 0.5f * bp2 * E2; a[6] += 0.5f * bm2 * E1; a[7] += 0.5f * bm2 * E2;
-                a[8] += 0.125f * bp4 * E1; a[9] += 0.125f * bp4 * E2; a[10] += 0.125f * bm4 * E1; a[11] += 0.125f * bm4 * E2;
-                a[12] += 0.0078125f * bp8 * E1; a[13] += 0.0078125f * bp8 * E2;
-                a[14] += 0.0078125f * bm8 * E1; a[15] += 0.0078125f * bm8 * E2;
-            }
+            const float4 gp = S.g[p], gq = S.g[q], cp = S.c[p], cq = S.c[q];
+            const float c = (gp.x * gq.x + gp.y * gq.y + gp.z * gq.z) * (gp.w * gq.w);
+            const float ff = cp.x * cq.x;
+            const float E1 = cp.z * cq.z * ff, E2 = cp.w * cq.w * ff;
+            const float2 e1 = make_float2(E1, E1), e2 = make_float2(E2, E2);
+            const float2 b1 = make_float2(1.f + c, 1.f - c);
+            const float2 b2 = __fmul2_rn(b1, b1), b4 = __fmul2_rn(b2, b2), b8 = __fmul2_rn(b4, b4);
+            acc[0][0] = __ffma2_rn(b1, e1, acc[0][0]);
+            acc[0][1] = __ffma2_rn(b1, e2, acc[0][1]);
+            acc[1][0] = __ffma2_rn(b2, e1, acc[1][0]);
+            acc[1][1] = __ffma2_rn(b2, e2, acc[1][1]);
+            acc[2][0] = __ffma2_rn(b4, e1, acc[2][0]);
+            acc[2][1] = __ffma2_rn(b4, e2, acc[2][1]);
+            acc[3][0] = __ffma2_rn(b8, e1, acc[3][0]);
+            acc[3][1] = __ffma2_rn(b8, e2, acc[3][1]);
+        }
+        // back to the feature order 4 z + 2 lambda + eta
+        float a[kNAng];
+#pragma unroll
+        for (int z = 0; z < 4; ++z) {
+            a[4 * z] = acc[z][0].x;
+            a[4 * z + 1] = acc[z][1].x;
+            a[4 * z + 2] = acc[z][0].y;
+            a[4 * z + 3] = acc[z][1].y;
         }
         // the sixteen warp sums as one reduce-scatter: at offsets 16, 8, 4, 2
         // each lane keeps the half of its partial sums its offset bit selects
@@ -187,7 +227,10 @@ __device__ __forceinline__ void desc_row(const NbStage &S, int n, const PotDev &
             }
         }
         a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
-        if ((lane & 1) == 0) x[S_ * nr + (lane >> 1)] = a[0];
+        // feature f = lane / 2 has zeta index f / 4: prefactor 2^(1 - zeta)
+        const int zf = lane >> 3;
+        const float pref = zf == 0 ? 1.f : (zf == 1 ? 0.5f : (zf == 2 ? 0.125f : 0.0078125f));
+        if ((lane & 1) == 0) x[S_ * nr + (lane >> 1)] = a[0] * pref;
     }
     // one-hot and padding
     const int off = S_ * nr + P.n_ang;
@@ -208,9 +251,10 @@ __device__ __forceinline__ void row_pair_grads(const NbStage &S, int n, const Po
                                                float4 *tb, float4 *__restrict__ pg, int lane, float &fx, float &fy,
                                                float &fz) {
     const int nr = P.n_rbf;
-    float wang[kNAng];   // dE/dX of the angular features, in registers across the pair loop
+    float wang[kNAng];   // dE/dX of the angular features
 #pragma unroll
     for (int t = 0; t < kNAng; ++t) wang[t] = P.n_ang ? wbuf[S_ * nr + t] : 0.f;
+    const AngW aw = ang_weights(wang);   // in registers across the pair loop
     float ax[R], ay[R], az[R], ab[R];
 #pragma unroll
     for (int s = 0; s < R; ++s) ax[s] = ay[s] = az[s] = ab[s] = 0.f;
@@ -222,7 +266,7 @@ __device__ __forceinline__ void row_pair_grads(const NbStage &S, int n, const Po
                 const int p = lane + 32 * s;
                 if (p < n && (!half || p < d)) {
                     const int q = p + d < n ? p + d : p + d - n;
-                    tb[q] = pair_terms(S, wang, p, q, ax[s], ay[s], az[s], ab[s]);
+                    tb[q] = pair_terms(S, aw, p, q, ax[s], ay[s], az[s], ab[s]);
                 }
             }
             __syncwarp();
