@@ -489,8 +489,8 @@ void enqueue_round(lsd_handle *h, int b) {
     cudaEventRecord(h->ev_fork, V);
     cudaStreamWaitEvent(D, h->ev_fork, 0);
     enqueue_verify_buf(h, b, V, &h->hdr[b].k_eff);
-    launch_spec_base(h->geo, h->coef, h->species, h->wb[b].qmid, h->wb[b].pdraft, &h->hdr[b], &h->hdr[n], h->qb,
-                     h->pb, D);
+    launch_spec_base(h->geo, h->coef, h->species, h->wb[b].qmid, h->wb[b].pdraft, &h->hdr[b], &h->hdr[n], h->st,
+                     h->qb, h->pb, D);
     enqueue_draft_buf(h, n, D, &h->hdr[n], h->qb, h->pb);
     cudaEventRecord(h->ev_v, V);
     cudaStreamWaitEvent(D, h->ev_v, 0);
@@ -986,6 +986,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     s0.step = 0;
     s0.target_step = 0;
     s0.first_reject_last = -1;
+    s0.spec_ema = 1.f;
     if (cudaMemcpy(h->st, &s0, sizeof(DevState), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSD_ECUDA);
     if (sys->mom) {
         if (cudaMemcpy(h->p, sys->mom, D * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)

@@ -96,6 +96,10 @@ struct DevState {
     unsigned long long grid_arrive;   // arrivals at the transport's grid barrier (generations of nb*K)
     long long windows, committed, rejected, verified;
     double sum_delta, sum_pred;
+    // the pipelined loop's speculation policy (lsd_draft.cu; results do not depend on it): a running mean of
+    // "the last committed window had no rejection", and whether the next round skips its speculative draft
+    float spec_ema;
+    int spec_hint;
     int accept[kMaxK];
     double logr[kMaxK], logu[kMaxK], dnorm[kMaxK];
 };

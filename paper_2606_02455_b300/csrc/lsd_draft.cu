@@ -982,15 +982,19 @@ int draft_max_cluster(size_t smem, bool learned) {
 
 // The speculative base of window b^1: the state after the last step window b
 // drafted (ABOBA: q_mid + (dt/2) p/m with the commit's rounding; staggered
-// OBABO: q_mid), its step index, and whether there is one (k_eff > 0).
+// OBABO: q_mid), its step index, and whether there is one (k_eff > 0).  The
+// speculative draft is skipped (it would not stand: every recent window had a
+// rejection) when the policy of the previous round says so (st->spec_hint,
+// written by this stream's redraft test after the previous commit).
 __global__ void spec_base_kernel(Geo g, Coef cf, const int *__restrict__ species, const double *__restrict__ qmid_b,
                                  const double *__restrict__ pdraft_b, const WinHdr *__restrict__ hb,
-                                 WinHdr *__restrict__ hn, double *__restrict__ qb, double *__restrict__ pb) {
+                                 WinHdr *__restrict__ hn, const DevState *__restrict__ st, double *__restrict__ qb,
+                                 double *__restrict__ pb) {
     const int k = hb->k_eff;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         hn->base = k > 0 ? hb->base + k : -1;
-        hn->skip = k > 0 ? 0 : 1;
+        hn->skip = (k > 0 && st->spec_hint == 0) ? 0 : 1;
     }
     if (k <= 0 || i >= g.N) return;
     const size_t o = (size_t)(k - 1) * 3 * g.N + 3 * (size_t)i;
@@ -1005,9 +1009,19 @@ __global__ void spec_base_kernel(Geo g, Coef cf, const int *__restrict__ species
 
 
 // The redraft's Verlet build runs only when the speculative draft does not
-// stand (the same test the redraft itself makes).
-__global__ void redraft_flag_kernel(const DevState *__restrict__ st, WinHdr *__restrict__ hn) {
+// stand (the same test the redraft itself makes).  Then the speculation
+// policy of the next round: a speculative draft stands only after a window
+// with no rejection, so the next round drafts speculatively while the running
+// mean of that event (weight 1/4 for the window just committed) is at least
+// 0.2.  The policy changes only which work runs, never the result: a skipped
+// speculation is a redraft from the committed state, the unpipelined loop's
+// draft.  Only kernels of the draft stream read or write spec_ema and
+// spec_hint.
+__global__ void redraft_flag_kernel(DevState *__restrict__ st, WinHdr *__restrict__ hn) {
     hn->keep = spec_is_valid(hn, st) ? 1 : 0;
+    const float e = 0.75f * st->spec_ema + (st->first_reject_last == -1 ? 0.25f : 0.f);
+    st->spec_ema = e;
+    st->spec_hint = e < 0.2f ? 1 : 0;
 }
 
 __global__ void hdr_invalidate_kernel(WinHdr *__restrict__ h) {
@@ -1017,11 +1031,11 @@ __global__ void hdr_invalidate_kernel(WinHdr *__restrict__ h) {
 }
 
 void launch_spec_base(const Geo &g, const Coef &cf, const int *species, const double *qmid_b, const double *pdraft_b,
-                      const WinHdr *hb, WinHdr *hn, double *qb, double *pb, cudaStream_t s) {
-    spec_base_kernel<<<(g.N + 255) / 256, 256, 0, s>>>(g, cf, species, qmid_b, pdraft_b, hb, hn, qb, pb);
+                      const WinHdr *hb, WinHdr *hn, const DevState *st, double *qb, double *pb, cudaStream_t s) {
+    spec_base_kernel<<<(g.N + 255) / 256, 256, 0, s>>>(g, cf, species, qmid_b, pdraft_b, hb, hn, st, qb, pb);
 }
 
-void launch_redraft_flag(const DevState *st, WinHdr *hn, cudaStream_t s) { redraft_flag_kernel<<<1, 1, 0, s>>>(st, hn); }
+void launch_redraft_flag(DevState *st, WinHdr *hn, cudaStream_t s) { redraft_flag_kernel<<<1, 1, 0, s>>>(st, hn); }
 
 
 void launch_hdr_invalidate(WinHdr *h, cudaStream_t s) { hdr_invalidate_kernel<<<1, 1, 0, s>>>(h); }

@@ -164,8 +164,8 @@ cudaError_t launch_plain_fused(const PlainPlan &pl, int n_steps, const Geo &g, c
                                float4 *gpg, unsigned long long *bar, DevState *st, cudaStream_t s);
 // the pipelined window loop (lsd_draft.cu)
 void launch_spec_base(const Geo &g, const Coef &cf, const int *species, const double *qmid_b, const double *pdraft_b,
-                      const WinHdr *hb, WinHdr *hn, double *qb, double *pb, cudaStream_t s);
-void launch_redraft_flag(const DevState *st, WinHdr *hn, cudaStream_t s);
+                      const WinHdr *hb, WinHdr *hn, const DevState *st, double *qb, double *pb, cudaStream_t s);
+void launch_redraft_flag(DevState *st, WinHdr *hn, cudaStream_t s);
 void launch_hdr_invalidate(WinHdr *h, cudaStream_t s);
 cudaError_t draft_kernels_setup(int max_smem);
 void launch_plain_half(const Geo &g, const Coef &cf, const int *species, const double *q, const double *p,

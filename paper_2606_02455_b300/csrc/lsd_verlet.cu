@@ -15,7 +15,8 @@
 //                     not matter: lists are sorted afterwards)
 // verlet_list_kernel  one warp per atom: 27 neighbouring cells (or all atoms
 //                     for a grid narrower than 3 cells), minimum-image test,
-//                     bitonic sort in shared memory, sorted list out
+//                     compaction in shared memory, a bitonic sort in registers
+//                     (up to 512 candidates) and the sorted list out
 #include "lsd_common.cuh"
 #include "lsd_kernels.h"
 
@@ -85,6 +86,49 @@ __global__ void cell_fill_kernel(int N, const int *__restrict__ cell_of_atom, co
     cell_atoms[cell_start[c] + atomicAdd(&cursor[c], 1)] = i;
 }
 
+// Sorts 32 E keys held E per lane (key e = r * 32 + lane in v[r]) in
+// ascending order with a bitonic network: partners 32 or more apart are in the
+// same lane (register compare-exchange), nearer ones one shuffle away.
+template <int E>
+__device__ __forceinline__ void warp_bitonic_sort(int (&v)[E], int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int jj = j >> 5;
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    if (r & jj) continue;
+                    const bool up = ((r * 32) & k) == 0;
+                    const int a = v[r], b = v[r | jj];
+                    v[r] = up ? min(a, b) : max(a, b);
+                    v[r | jj] = up ? max(a, b) : min(a, b);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const bool up = ((r * 32 + lane) & k) == 0;
+                    const int o = __shfl_xor_sync(0xffffffffu, v[r], j);
+                    v[r] = (((lane & j) == 0) == up) ? min(v[r], o) : max(v[r], o);
+                }
+            }
+        }
+    }
+}
+
+// The n compacted candidates of buf, sorted, to out (coalesced).
+template <int E>
+__device__ __forceinline__ void sort_out(const int *buf, int n, int *out, int lane) {
+    int v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) v[r] = r * 32 + lane < n ? buf[r * 32 + lane] : 0x7fffffff;
+    warp_bitonic_sort<E>(v, lane);
+#pragma unroll
+    for (int r = 0; r < E; ++r)
+        if (r * 32 + lane < n) out[r * 32 + lane] = v[r];
+}
+
 __global__ void verlet_list_kernel(const uint4 *__restrict__ fix_base, const int *__restrict__ cell_of_atom,
                                    const int *__restrict__ cell_start, const int *__restrict__ cell_atoms, Geo g,
                                    int3 nc, float rlist2f, int cap, int cap_pow2, int *__restrict__ vlist,
@@ -100,6 +144,7 @@ __global__ void verlet_list_kernel(const uint4 *__restrict__ fix_base, const int
     const int cx = ci % nc.x, cy = (ci / nc.x) % nc.y, cz = ci / (nc.x * nc.y);
     int cnt = 0;
     const int ncell_scan = one_cell ? 1 : 27;
+    const unsigned below = (1u << lane) - 1u;
     for (int t = 0; t < ncell_scan; ++t) {
         int s0, s1;
         if (one_cell) {
@@ -111,51 +156,76 @@ __global__ void verlet_list_kernel(const uint4 *__restrict__ fix_base, const int
             s0 = cell_start[c];
             s1 = cell_start[c + 1];
         }
-        for (int base = s0; base < s1; base += 32) {
-            const int p = base + lane;
-            int k = -1;
-            bool in = false;
-            if (p < s1) {
-                k = one_cell ? p : cell_atoms[p];
-                if (k != i) {
-                    const uint4 fk = fix_base[k];
+        // four candidates per lane in flight: their loads first, then the tests
+        constexpr int kB = 4;
+        for (int base = s0; base < s1; base += 32 * kB) {
+            int kk[kB];
+            uint4 fk[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int p = base + 32 * u + lane;
+                kk[u] = p < s1 ? (one_cell ? p : cell_atoms[p]) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kB; ++u) fk[u] = kk[u] >= 0 ? fix_base[kk[u]] : fi;
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                if (base + 32 * u >= s1) break;
+                bool in = false;
+                if (kk[u] >= 0 && kk[u] != i) {
                     float dx, dy, dz;
-                    int kk;
-                    axis_min(fi.x, fk.x, g.scale_f[0], dx, kk);
-                    axis_min(fi.y, fk.y, g.scale_f[1], dy, kk);
-                    axis_min(fi.z, fk.z, g.scale_f[2], dz, kk);
+                    int kx;
+                    axis_min(fi.x, fk[u].x, g.scale_f[0], dx, kx);
+                    axis_min(fi.y, fk[u].y, g.scale_f[1], dy, kx);
+                    axis_min(fi.z, fk[u].z, g.scale_f[2], dz, kx);
                     in = dist2_rule(dx, dy, dz) < rlist2f;
                 }
+                const unsigned bal = __ballot_sync(0xffffffffu, in);
+                const int pos = cnt + __popc(bal & below);
+                if (in && pos < cap_pow2) buf[pos] = kk[u];
+                cnt += __popc(bal);
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, in);
-            const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-            if (in && pos < cap_pow2) buf[pos] = k;
-            cnt += __popc(bal);
         }
     }
     // (an atom's own images lie at least one box length away, beyond any cutoff rc < L)
     const int n = cnt < cap ? cnt : cap;
-    for (int p = n + lane; p < cap_pow2; p += 32) buf[p] = 0x7fffffff;
     __syncwarp();
-    // bitonic sort of cap_pow2 entries by atom index (a single-cell scan is already in index order)
-    for (int k2 = 2; k2 <= (one_cell ? 1 : cap_pow2); k2 <<= 1) {
-        for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
-            for (int a = lane; a < cap_pow2; a += 32) {
-                const int b = a ^ j2;
-                if (b > a) {
-                    const int x = buf[a], y = buf[b];
-                    const bool up = (a & k2) == 0;
-                    if (up ? x > y : x < y) {
-                        buf[a] = y;
-                        buf[b] = x;
+    int *out = vlist + (size_t)i * cap;
+    if (one_cell) {
+        // a single-cell scan runs in index order: already sorted
+        for (int p = lane; p < n; p += 32) out[p] = buf[p];
+    } else if (n <= 32) {
+        sort_out<1>(buf, n, out, lane);
+    } else if (n <= 64) {
+        sort_out<2>(buf, n, out, lane);
+    } else if (n <= 128) {
+        sort_out<4>(buf, n, out, lane);
+    } else if (n <= 256) {
+        sort_out<8>(buf, n, out, lane);
+    } else if (n <= 512) {
+        sort_out<16>(buf, n, out, lane);
+    } else {
+        // longer lists: a bitonic sort of cap_pow2 entries in shared memory
+        for (int p = n + lane; p < cap_pow2; p += 32) buf[p] = 0x7fffffff;
+        __syncwarp();
+        for (int k2 = 2; k2 <= cap_pow2; k2 <<= 1) {
+            for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
+                for (int a = lane; a < cap_pow2; a += 32) {
+                    const int b = a ^ j2;
+                    if (b > a) {
+                        const int x = buf[a], y = buf[b];
+                        const bool up = (a & k2) == 0;
+                        if (up ? x > y : x < y) {
+                            buf[a] = y;
+                            buf[b] = x;
+                        }
                     }
                 }
+                __syncwarp();
             }
-            __syncwarp();
         }
+        for (int p = lane; p < n; p += 32) out[p] = buf[p];
     }
-    int *out = vlist + (size_t)i * cap;
-    for (int p = lane; p < n; p += 32) out[p] = buf[p];
     if (lane == 0) {
         vcount[i] = n;
         if (cnt > cap) atomicOr(&st->err, 1);
