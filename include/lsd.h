@@ -217,6 +217,20 @@ LSD_API int lsd_plain_step(lsd_handle *h, int64_t n_steps);
  * the handle's configuration has no fused plan. */
 LSD_API int lsd_set_plain_fused(lsd_handle *h, int32_t on);
 
+/* lsd_set_angular_moments: how the target's sixteen angular descriptors
+ * (triplet sums over neighbour pairs, 2^(1-zeta) sum_{p<q} (1 + lambda
+ * cos theta_pq)^zeta exp(-eta (r_p^2 + r_q^2)) fc_p fc_q) and their adjoint are
+ * evaluated.  on: through the Cartesian moments Phi_alpha = sum_p w_p u_p^alpha
+ * of the neighbour directions (the 165 monomials of degree <= 8; the pair sum
+ * is (1/2)(sum_{p,q} - diagonal) of a polynomial in u_p.u_q), O(n) work per atom
+ * and 1,344 bytes of moments per row (K N rows) kept from the descriptors for
+ * the pair gradients.  off: the pair sums themselves, O(n^2).  Both give the
+ * same functions up to FP32 rounding.  The default is on when the system's mean
+ * density puts 40 or more neighbours inside the descriptor cutoff.
+ * LSD_EUNSUPPORTED when the target has no angular descriptors; LSD_ENOMEM when
+ * the moments cannot be allocated. */
+LSD_API int lsd_set_angular_moments(lsd_handle *h, int32_t on);
+
 /* lsd_set_grid_draft: the form of the draft (Alg. 2, draft_step K times) for
  * systems of at least 2048 atoms with a cell grid.  on (the default where
  * available): every draft that has the GPU to itself (lsd_draft_window, the

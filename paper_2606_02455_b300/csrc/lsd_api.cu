@@ -33,6 +33,7 @@ namespace {
 constexpr double kTwo32 = 4294967296.0;
 constexpr int kMaxDynSmem = 227 * 1024;
 constexpr double kWaitLimitSeconds = 600.0;
+constexpr double kMomMinNeighbours = 40.0;   // expected descriptor neighbours per atom from which moments are used
 
 double kappa_conv() { return (1.602176634e-19 / 1e-10) / (1.66053906660e-27 * 1e-10 / 1e-30); }
 double kboltz_ev() { return 1.380649e-23 / 1.602176634e-19; }
@@ -74,6 +75,8 @@ struct lsd_handle {
     PotHost draft, target;
     bool learned_small = false;
     DraftPlan dplan{};
+    bool mom_on = false;            // the target's angular features and adjoint by moments
+    float *mom = nullptr;           // their per-row moments [K N][kMomRowFloats]
     DraftPlan gplan{};              // the grid form of the draft (large systems), when the device co-schedules it
     bool grid_draft = false;        // windows and redrafts draft in the grid form
     DraftSync *dsync = nullptr;     // its barrier and flag words
@@ -422,6 +425,12 @@ void enqueue_mlp(lsd_handle *h, const PotHost &pot, int M, cudaStream_t s) {
         launch_mlp_fp32(h->X, M, P, h->E_mlp, h->dEdX, s);
 }
 
+// The moment buffer when pot's angular block runs by moments (the target, with
+// rows dense enough), else null.
+float *mom_for(const lsd_handle *h, const PotHost &pot) {
+    return (h->mom_on && &pot == &h->target && pot.dev.n_ang) ? h->mom : nullptr;
+}
+
 // Batched force evaluation of `pot` on Kc configurations whose fixed-point
 // coordinates are in fix ([Kc][N]); forces to F ([Kc][N][3]).
 // With use_list the candidates are the window's Verlet lists (the window and
@@ -440,11 +449,11 @@ void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, f
         launch_neigh_build(fix, M, h->geo, pot.rmax2f, pot.near2f, h->cap_near, h->cap_far, h->near_keys,
                            h->far_keys, h->n_near, h->n_far, h->st, s, keff_rows);
     if (P.has_mlp) {
-        launch_desc(fix, h->near_keys, h->n_near, h->cap_near, M, h->geo, P, h->X, s);
+        launch_desc(fix, h->near_keys, h->n_near, h->cap_near, M, h->geo, P, h->X, s, mom_for(h, pot));
         enqueue_mlp(h, pot, M, s);
     }
     launch_pairgrad(fix, h->near_keys, h->n_near, h->far_keys, h->n_far, h->cap_near, h->cap_far, M, h->geo, P, h->dEdX,
-                    h->pair_g, h->Fpart, h->E_lj, s);
+                    h->pair_g, h->Fpart, h->E_lj, s, mom_for(h, pot));
     launch_force_gather(h->near_keys, h->n_near, h->cap_near, M, h->N, P.has_mlp, h->pair_g, h->Fpart, h->E_lj,
                         h->E_mlp, F, E_out, h->st, s);
 }
@@ -649,7 +658,7 @@ int calibrate_scales(lsd_handle *h, PotHost &ph) {
     launch_fixpoint(h->q, h->species, N, h->geo, h->fix_eval, s);
     launch_neigh_build(h->fix_eval, N, h->geo, ph.rmax2f, ph.near2f, h->cap_near, h->cap_far, h->near_keys,
                        h->far_keys, h->n_near, h->n_far, h->st, s);
-    launch_desc(h->fix_eval, h->near_keys, h->n_near, h->cap_near, N, h->geo, P, h->X, s);
+    launch_desc(h->fix_eval, h->near_keys, h->n_near, h->cap_near, N, h->geo, P, h->X, s, mom_for(h, ph));
     CK(cudaMemsetAsync(ph.tc_amax, 0, 2 * L * sizeof(float), s));
     launch_mlp_tc(ph.cal_plan, h->X, N, P, h->E_mlp, h->dEdX, ph.tc_scratch, nullptr, ph.tc_amax, h->n_sm,
                   &h->st->err, s);
@@ -849,6 +858,12 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     }
     h->cap_near = std::min(nb_capacity(rho, rnear, 32), (27 * h->N + 31) / 32 * 32);
     h->cap_far = std::min(nb_capacity(rho, rfar, 32), (27 * h->N + 31) / 32 * 32);
+    // the target's angular block by moments when rows hold many neighbours: 165 monomials per neighbour instead
+    // of n / 2 pair terms pay from about 40 neighbours on
+    if (h->target.dev.has_mlp && h->target.dev.n_ang) {
+        const double rd = h->target.p.desc_cutoff;
+        h->mom_on = rho * 4.0 / 3.0 * M_PI * rd * rd * rd >= kMomMinNeighbours;
+    }
     // the pair-gradient kernel: staging, dE/dX and the q-side hand-over buffer per warp; at most 16 neighbours per lane
     if (h->cap_near > 512 ||
         desc_smem_bytes(8, h->cap_near) + 8 * (256 + 4 * h->cap_near) * sizeof(float) > (size_t)kMaxDynSmem)
@@ -913,7 +928,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         (rc = dalloc(h, &h->pair_g, KN * h->cap_near)) || (rc = dalloc(h, &h->Fpart, KN)) ||
         (rc = dalloc(h, &h->partials, (size_t)K * ((h->N + 1023) / 1024 + 600))) ||
         (rc = dalloc(h, &h->w_dEdX, N * std::max(h->draft.dev.d0p, 32))) ||
-        (rc = dalloc(h, &h->dsync, 1)) ||
+        (rc = dalloc(h, &h->dsync, 1)) || (rc = dalloc(h, &h->mom, h->mom_on ? KN * kMomRowFloats : 1)) ||
         (rc = dalloc(h, &h->vbufs.fix_base, N)) || (rc = dalloc(h, &h->vbufs.cell_of_atom, N)) ||
         (rc = dalloc(h, &h->vbufs.cell_count, (size_t)h->vplan.nc[0] * h->vplan.nc[1] * h->vplan.nc[2])) ||
         (rc = dalloc(h, &h->vbufs.cell_start, (size_t)h->vplan.nc[0] * h->vplan.nc[1] * h->vplan.nc[2] + 1)) ||
@@ -1451,12 +1466,12 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
                           h->target.near2f, h->cap_near, h->cap_far, h->near_keys, h->far_keys, h->n_near, h->n_far,
                           h->st, &h->st->k_eff, st);
     CK(cudaEventRecord(ev[2], st));
-    if (P.has_mlp) launch_desc(h->w_fix, h->near_keys, h->n_near, h->cap_near, M, h->geo, P, h->X, st);
+    if (P.has_mlp) launch_desc(h->w_fix, h->near_keys, h->n_near, h->cap_near, M, h->geo, P, h->X, st, mom_for(h, h->target));
     CK(cudaEventRecord(ev[3], st));
     if (P.has_mlp) enqueue_mlp(h, h->target, M, st);
     CK(cudaEventRecord(ev[4], st));
     launch_pairgrad(h->w_fix, h->near_keys, h->n_near, h->far_keys, h->n_far, h->cap_near, h->cap_far, M, h->geo, P,
-                    h->dEdX, h->pair_g, h->Fpart, h->E_lj, st);
+                    h->dEdX, h->pair_g, h->Fpart, h->E_lj, st, mom_for(h, h->target));
     CK(cudaEventRecord(ev[5], st));
     launch_force_gather(h->near_keys, h->n_near, h->cap_near, M, h->N, P.has_mlp, h->pair_g, h->Fpart, h->E_lj,
                         h->E_mlp, h->w_Ft, nullptr, h->st, st);
@@ -1515,6 +1530,21 @@ int lsd_launch_counts(const lsd_handle *h, int32_t *per_window, int32_t *per_rou
     // verify; spec_base; speculative draft; redraft (with its flag kernel in list mode)
     if (per_round) *per_round = verify + 1 + draft + (lists ? 1 : 0) + draft;
     if (per_plain) *per_plain = use_plain_fused(h) ? 0 : verlet + 1 + eval + 1;
+    return LSD_OK;
+}
+
+int lsd_set_angular_moments(lsd_handle *h, int32_t on) {
+    if (!h) return LSD_EINVAL;
+    if (on && !(h->target.dev.has_mlp && h->target.dev.n_ang)) return LSD_EUNSUPPORTED;
+    TRY(wait_stream(h));
+    if (on && !h->mom_on) {
+        // the buffer was sized for one row when the handle chose the pair sums
+        float *m = nullptr;
+        TRY(dalloc(h, &m, (size_t)h->K * h->N * kMomRowFloats));
+        h->mom = m;
+    }
+    if (h->mom_on != (on != 0)) destroy_graphs(h);   // the descriptor and pair-gradient launches are in the graphs
+    h->mom_on = on != 0;
     return LSD_OK;
 }
 

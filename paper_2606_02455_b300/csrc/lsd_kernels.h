@@ -33,11 +33,15 @@ void launch_fixpoint(const double *q, const int *species, int M, const Geo &g, u
 void launch_neigh_build(const uint4 *fix, int M, const Geo &g, float rmax2f, float near2f, int cap_near, int cap_far,
                         int *near_keys, int *far_keys, int *n_near, int *n_far, DevState *st, cudaStream_t s,
                         const int *keff = nullptr);
+// mom (may be null): [M][kMomFloats] moments of the rows; non-null selects the
+// moment form of the angular features and their adjoint (the same rows of
+// moments for both calls)
+constexpr int kMomRowFloats = 336;
 void launch_desc(const uint4 *fix, const int *near_keys, const int *n_near, int cap, int M, const Geo &g,
-                 const PotDev &P, float *X, cudaStream_t s);
+                 const PotDev &P, float *X, cudaStream_t s, float *mom = nullptr);
 void launch_pairgrad(const uint4 *fix, const int *near_keys, const int *n_near, const int *far_keys, const int *n_far,
                      int cap, int cap_far, int M, const Geo &g, const PotDev &P, const float *dEdX, float4 *pair_g,
-                     float4 *Fpart, float *E_lj, cudaStream_t s);
+                     float4 *Fpart, float *E_lj, cudaStream_t s, const float *mom = nullptr);
 void launch_force_gather(const int *near_keys, const int *n_near, int cap, int M, int N, int has_mlp,
                          const float4 *pair_g, const float4 *Fpart, const float *E_lj, const float *E_mlp, float *F,
                          float *E_out, DevState *st, cudaStream_t s);

@@ -146,34 +146,43 @@ __device__ __forceinline__ float4 pair_terms(const NbStage &S, const AngW &W, in
     return make_float4(A * xp, A * yp, A * zp, Bq);
 }
 
-// One row's descriptors into x [d0p]: radial blocks by lanes over basis
-// functions (two halves over neighbours), the 16 angular terms by lanes over
-// the flattened neighbour pairs with one reduce-scatter, the one-hot of the
-// centre species si and zero padding.  S_ species; the row's n neighbours are
-// staged in S.
+// The radial blocks of one row's descriptors into x: lanes over basis
+// functions (two halves over neighbours), one shuffle between the halves.
+__device__ __forceinline__ void desc_radial(const NbStage &S, int n, const PotDev &P, int S_, float *x, int lane) {
+    const int nr = P.n_rbf;
+    float acc[kMaxSpecies];
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s) acc[s] = 0.f;
+    const int kb = lane & 15;
+    if (kb < nr) {
+        const float mu = (float)kb * P.rbf_w;
+        for (int p = lane >> 4; p < n; p += 2) {
+            const float t = S.r[p] - mu;
+            const float v = expf(-t * t * P.rbf_inv2w2) * S.c[p].x;
+            const int sp = S.sp[p];
+#pragma unroll
+            for (int s = 0; s < kMaxSpecies; ++s) acc[s] += (sp == s) ? v : 0.f;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s) acc[s] += __shfl_down_sync(0xffffffffu, acc[s], 16);
+    if (lane < nr)
+        for (int s = 0; s < S_; ++s) x[s * nr + lane] = acc[s];
+}
+
+// The one-hot of the centre species si and the zero padding of a descriptor row.
+__device__ __forceinline__ void desc_onehot(const PotDev &P, int S_, int si, float *x, int lane) {
+    const int off = S_ * P.n_rbf + P.n_ang;
+    for (int f = off + lane; f < P.d0p; f += 32) x[f] = (f == off + si) ? 1.f : 0.f;
+}
+
+// One row's descriptors into x [d0p]: the radial blocks, the 16 angular terms
+// by lanes over the flattened neighbour pairs with one reduce-scatter, the
+// one-hot of the centre species si and zero padding.  S_ species; the row's n
+// neighbours are staged in S.
 __device__ __forceinline__ void desc_row(const NbStage &S, int n, const PotDev &P, int S_, int si, float *x, int lane) {
     const int nr = P.n_rbf;
-    // radial
-    {
-        float acc[kMaxSpecies];
-#pragma unroll
-        for (int s = 0; s < kMaxSpecies; ++s) acc[s] = 0.f;
-        const int kb = lane & 15;
-        if (kb < nr) {
-            const float mu = (float)kb * P.rbf_w;
-            for (int p = lane >> 4; p < n; p += 2) {
-                const float t = S.r[p] - mu;
-                const float v = expf(-t * t * P.rbf_inv2w2) * S.c[p].x;
-                const int sp = S.sp[p];
-#pragma unroll
-                for (int s = 0; s < kMaxSpecies; ++s) acc[s] += (sp == s) ? v : 0.f;
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < kMaxSpecies; ++s) acc[s] += __shfl_down_sync(0xffffffffu, acc[s], 16);
-        if (lane < nr)
-            for (int s = 0; s < S_; ++s) x[s * nr + lane] = acc[s];
-    }
+    desc_radial(S, n, P, S_, x, lane);
     // angular
     if (P.n_ang) {
         // per (zeta, eta) the pair (lambda = +1, lambda = -1) of sums of b^zeta E_eta fc_p fc_q, packed: one fused
@@ -232,9 +241,22 @@ __device__ __forceinline__ void desc_row(const NbStage &S, int n, const PotDev &
         const float pref = zf == 0 ? 1.f : (zf == 1 ? 0.5f : (zf == 2 ? 0.125f : 0.0078125f));
         if ((lane & 1) == 0) x[S_ * nr + (lane >> 1)] = a[0] * pref;
     }
-    // one-hot and padding
-    const int off = S_ * nr + P.n_ang;
-    for (int f = off + lane; f < P.d0p; f += 32) x[f] = (f == off + si) ? 1.f : 0.f;
+    desc_onehot(P, S_, si, x, lane);
+}
+
+// The radial part of dE_i/dr_p: c = sum_k w_k g_k'(r_p), w = dE/dX of the
+// radial block of neighbour p's species (the pair gradient is c d_p / r_p).
+__device__ __forceinline__ float radial_dcoef(const NbStage &S, int p, const PotDev &P, const float *wbuf) {
+    const int nr = P.n_rbf;
+    const float rp = S.r[p], fp = S.c[p].x, dfp = S.c[p].y;
+    float c = 0.f;
+    const float *wr = wbuf + S.sp[p] * nr;
+    for (int k = 0; k < nr; ++k) {
+        const float t = rp - (float)k * P.rbf_w;
+        const float phi = expf(-t * t * P.rbf_inv2w2);
+        c += wr[k] * phi * (-t * P.rbf_invw2 * fp + dfp);
+    }
+    return c;
 }
 
 // The pair gradients g_p = dE_i/d(r_p) of one row from its staged neighbours
@@ -288,17 +310,10 @@ __device__ __forceinline__ void row_pair_grads(const NbStage &S, int n, const Po
     for (int s = 0; s < R; ++s) {
         const int p = lane + 32 * s;
         if (p >= n) continue;
-        const float4 gp = S.g[p], cp = S.c[p];
-        const float xp = gp.x, yp = gp.y, zp = gp.z, rp = S.r[p], fp = cp.x, dfp = cp.y;
+        const float4 gp = S.g[p];
+        const float xp = gp.x, yp = gp.y, zp = gp.z;
         const float rip = gp.w;
-        // radial: c = sum_k w_k g_k'(r)
-        float c = 0.f;
-        const float *wr = wbuf + S.sp[p] * nr;
-        for (int k = 0; k < nr; ++k) {
-            const float t = rp - (float)k * P.rbf_w;
-            const float phi = expf(-t * t * P.rbf_inv2w2);
-            c += wr[k] * phi * (-t * P.rbf_invw2 * fp + dfp);
-        }
+        const float c = radial_dcoef(S, p, P, wbuf);
         const float gx = c * xp * rip + ax[s] + ab[s] * xp;
         const float gy = c * yp * rip + ay[s] + ab[s] * yp;
         const float gz = c * zp * rip + az[s] + ab[s] * zp;

@@ -15,6 +15,7 @@
 
 #include "lsd_common.cuh"
 #include "lsd_kernels.h"
+#include "lsd_moments.cuh"
 #include "lsd_pairs.cuh"
 
 namespace lsd {
@@ -178,6 +179,32 @@ __global__ void desc_kernel(const uint4 *__restrict__ fix, const int *__restrict
     desc_row(S, n, P, g.S, (int)fi.w, X + (size_t)row * P.d0p, lane);
 }
 
+// The same descriptors with the angular block by moments (lsd_moments.cuh),
+// the row's moments to mom [row][kMomFloats] for the adjoint.  Shared memory
+// per warp: the staged neighbours, then 32 neighbours' staged powers.
+__global__ void desc_mom_kernel(const uint4 *__restrict__ fix, const int *__restrict__ near_keys,
+                                const int *__restrict__ n_near, int cap, int M, Geo g, PotDev P, float *__restrict__ X,
+                                float *__restrict__ mom) {
+    pdl_wait();
+    pdl_release();
+    extern __shared__ __align__(16) float smem[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (row >= M) return;
+    const int N = g.N;
+    const int j = row / N, i = row - j * N;
+    const uint4 *fj = fix + (size_t)j * N;
+    const uint4 fi = fj[i];
+    float *base = smem + (size_t)wib * (kNbStageFloats * cap + 32 * kMomTab);
+    NbStage S = nb_stage_ptrs(base, cap);
+    const int n = n_near[row];
+    nb_stage_load(S, fj, fi, near_keys + (size_t)row * cap, n, g, P.desc_rc, lane);
+    float *x = X + (size_t)row * P.d0p;
+    desc_radial(S, n, P, g.S, x, lane);
+    mom_forward(S, n, base + kNbStageFloats * cap, mom + (size_t)row * kMomFloats, x + g.S * P.n_rbf, lane);
+    desc_onehot(P, g.S, (int)fi.w, x, lane);
+}
+
 // ---------------------------------------------------------------------------
 // Pair gradients g_p = dE_i / d(r_p) and LJ forces.
 // ---------------------------------------------------------------------------
@@ -185,13 +212,14 @@ __global__ void desc_kernel(const uint4 *__restrict__ fix, const int *__restrict
 // SLOTS: neighbours per lane (lane l owns p = l + 32 s); every row has at most
 // 32 SLOTS of them.  The angular pairs run by diagonals (row_pair_grads): a
 // fixed order of summation with no atomics, so the forces do not depend on the
-// launch shape.
+// launch shape.  SLOTS = 0: the angular adjoint by moments (mom: the rows'
+// moments from desc_mom_kernel), lanes over neighbours.
 template <int SLOTS>
-__global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__restrict__ near_keys,
+__global__ void __launch_bounds__(256, SLOTS == 0 ? 2 : 1) pairgrad_kernel(const uint4 *__restrict__ fix, const int *__restrict__ near_keys,
                                 const int *__restrict__ n_near, const int *__restrict__ far_keys,
                                 const int *__restrict__ n_far, int cap, int cap_far, int M, Geo g, PotDev P,
                                 const float *__restrict__ dEdX, float4 *__restrict__ pair_g,
-                                float4 *__restrict__ Fpart, float *__restrict__ E_lj) {
+                                float4 *__restrict__ Fpart, float *__restrict__ E_lj, const float *__restrict__ mom) {
     // MLP potentials: the previous kernel is the MLP, and the neighbour lists
     // and positions come from kernels that finished before it began, so the
     // geometry staging and the LJ part run before the wait, while the MLP still
@@ -209,7 +237,11 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
     const uint4 fi = fj[i];
     const int warps = blockDim.x >> 5;
     float *wbuf = smem + (size_t)warps * kNbStageFloats * cap + (size_t)wib * P.d0p;
-    float4 *tb = reinterpret_cast<float4 *>(smem + (size_t)warps * (kNbStageFloats * cap + P.d0p)) + (size_t)wib * cap;
+    // after every warp's staging and dE/dX: the pair hand-over [cap] (pairs), or psi [kMomLd] and gamma, kappa [32]
+    float *tail = smem + (size_t)warps * (kNbStageFloats * cap + P.d0p);
+    float4 *tb = reinterpret_cast<float4 *>(tail) + (size_t)wib * cap;
+    float2 *psi = reinterpret_cast<float2 *>(tail + (size_t)wib * (2 * kMomLd + 32));
+    float *gk = tail + (size_t)wib * (2 * kMomLd + 32) + 2 * kMomLd;
     NbStage S = nb_stage_ptrs(smem + (size_t)wib * kNbStageFloats * cap, cap);
     const int n = n_near[row];
     const int *keys = near_keys + (size_t)row * cap;
@@ -239,7 +271,12 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
         pdl_wait();
         for (int f = lane; f < P.d0p; f += 32) wbuf[f] = dEdX[(size_t)row * P.d0p + f];
         __syncwarp();
-        row_pair_grads<SLOTS>(S, n, P, g.S, wbuf, tb, pair_g + (size_t)row * cap, lane, fx, fy, fz);
+        if (SLOTS == 0)
+            mom_pair_grads(S, n, P, g.S, wbuf, mom + (size_t)row * kMomFloats, psi, gk, pair_g + (size_t)row * cap,
+                           lane, fx, fy, fz);
+        else
+            row_pair_grads<SLOTS == 0 ? 1 : SLOTS>(S, n, P, g.S, wbuf, tb, pair_g + (size_t)row * cap, lane, fx, fy,
+                                                   fz);
     }
     fx = warp_sum(fx);
     fy = warp_sum(fy);
@@ -358,22 +395,31 @@ void launch_neigh_list(const uint4 *fix, const int *vlist, const int *vcount, in
 size_t desc_smem_bytes(int warps, int cap) { return (size_t)warps * kNbStageFloats * cap * sizeof(float); }
 
 void launch_desc(const uint4 *fix, const int *near_keys, const int *n_near, int cap, int M, const Geo &g,
-                 const PotDev &P, float *X, cudaStream_t s) {
+                 const PotDev &P, float *X, cudaStream_t s, float *mom) {
     const int warps = 8;
+    if (mom && P.n_ang) {
+        const size_t sm = (size_t)warps * (kNbStageFloats * cap + 32 * kMomTab) * sizeof(float);
+        launch_dependent(desc_mom_kernel, (M + warps - 1) / warps, warps * 32, sm, s, fix, near_keys, n_near, cap, M,
+                         g, P, X, mom);
+        return;
+    }
     const size_t sm = desc_smem_bytes(warps, cap);
     launch_dependent(desc_kernel, (M + warps - 1) / warps, warps * 32, sm, s, fix, near_keys, n_near, cap, M, g, P, X);
 }
 
 void launch_pairgrad(const uint4 *fix, const int *near_keys, const int *n_near, const int *far_keys, const int *n_far,
                      int cap, int cap_far, int M, const Geo &g, const PotDev &P, const float *dEdX, float4 *pair_g,
-                     float4 *Fpart, float *E_lj, cudaStream_t s) {
+                     float4 *Fpart, float *E_lj, cudaStream_t s, const float *mom) {
     const int warps = 8;
-    const size_t sm = desc_smem_bytes(warps, cap) + (size_t)warps * (P.d0p + 4 * cap) * sizeof(float);
+    const bool by_mom = mom && P.n_ang && P.has_mlp;
+    const size_t tail = by_mom ? (size_t)(2 * kMomLd + 32) : (size_t)4 * cap;
+    const size_t sm = desc_smem_bytes(warps, cap) + (size_t)warps * (P.d0p + tail) * sizeof(float);
     // lists of at most 128 hold mostly rows of a few dozen neighbours: flattened pairs with a small register
     // footprint; longer lists run their large rows by diagonals
-    auto k = cap <= 128 ? pairgrad_kernel<4> : (cap <= 256 ? pairgrad_kernel<8> : pairgrad_kernel<16>);
+    auto k = by_mom ? pairgrad_kernel<0>
+                    : (cap <= 128 ? pairgrad_kernel<4> : (cap <= 256 ? pairgrad_kernel<8> : pairgrad_kernel<16>));
     launch_dependent(k, (M + warps - 1) / warps, warps * 32, sm, s, fix, near_keys, n_near, far_keys, n_far, cap,
-                     cap_far, M, g, P, dEdX, pair_g, Fpart, E_lj);
+                     cap_far, M, g, P, dEdX, pair_g, Fpart, E_lj, mom);
 }
 
 void launch_force_gather(const int *near_keys, const int *n_near, int cap, int M, int N, int has_mlp,
@@ -386,10 +432,13 @@ void launch_force_gather(const int *near_keys, const int *n_near, int cap, int M
 }
 
 cudaError_t verify_kernels_setup(int max_smem) {
+    static_assert(kMomRowFloats == kMomFloats, "moment row size");
     cudaError_t e = cudaFuncSetAttribute(desc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e != cudaSuccess) return e;
-    const void *pk[3] = {(const void *)pairgrad_kernel<4>, (const void *)pairgrad_kernel<8>,
-                         (const void *)pairgrad_kernel<16>};
+    e = cudaFuncSetAttribute(desc_mom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e != cudaSuccess) return e;
+    const void *pk[4] = {(const void *)pairgrad_kernel<4>, (const void *)pairgrad_kernel<8>,
+                         (const void *)pairgrad_kernel<16>, (const void *)pairgrad_kernel<0>};
     for (const void *k : pk) {
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
         if (e != cudaSuccess) return e;
