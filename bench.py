@@ -162,10 +162,6 @@ def _lj_pairs_per_atom(w, q):
 # DRAM bytes (read + write) of one launch, from one ncu capture of the kernel as it is now (the summaries under
 # profiles/ give the command); a kernel changed since its capture has no entry here.
 NCU_TRAFFIC = {
-    # pairgrad_kernel<8>: 144,895,744 B per launch captured on the 4,096-atom workload (131,072 rows); the pair
-    # gradients and staged geometry scale with rows, so one 2,097,152-row launch moves 16x that
-    ("fp8_mlp_32768atoms_K64", "pair_grad"): 16 * 144895744,
-    ("bf16_mlp_4096atoms_K32", "pair_grad"): 144895744,
 }
 
 
@@ -180,12 +176,40 @@ FLOP_RAD_GRAD = 12
 FLOP_LJ_PAIR = 23
 
 
+def _mom_horner_fma():
+    """Fused multiply-adds of one eta's nested Horner evaluation of the moment adjoint (value and gradient of a
+    degree-8 polynomial in three variables, 165 coefficients), counted from its loops: per x-power 2 (value and
+    x-derivative; the first derivative step is a copy), per further y-power 3, per further z-power 4."""
+    n = 0
+    for c in range(8, -1, -1):
+        cols = 9 - c
+        for bi in range(cols):
+            L = 9 - (8 - c - bi) - c
+            n += 2 * (L - 1) - (1 if L >= 2 else 0)
+            if bi > 0:
+                n += 3 - (1 if bi == 1 else 0)
+        if c < 8:
+            n += 4 - (1 if c == 7 else 0)
+    return n
+
+
+# The angular block by moments (165 monomials x^a y^b z^c of degree <= 8 per neighbour): per neighbour, the
+# descriptor pass forms 24 powers, the unit vector and two weights (5), the monomials (165) and two weighted
+# accumulations per monomial (660); per row it squares and scales the 330 moments (990) and forms 16 features
+# from 9 sums each (288).  The pair-gradient pass runs the Horner evaluation for both etas (2 FLOP per FMA) and
+# its per-neighbour epilogue (42); per row it scales the 330 moments (990) and forms 20 adjoint scalars (960).
+FLOP_MOM_DESC_NB = 24 + 5 + 165 + 660
+FLOP_MOM_DESC_ROW = 990 + 288
+FLOP_MOM_GRAD_NB = 2 * 2 * _mom_horner_fma() + 42
+FLOP_MOM_GRAD_ROW = 990 + 960
+
+
 def _neighbours_per_atom(w, rc):
     s = w.system
     return s.n_atoms / float(np.prod(s.box)) * 4.0 / 3.0 * np.pi * rc ** 3
 
 
-def _algorithmic_work(w, phase, q):
+def _algorithmic_work(w, phase, q, moments=False):
     """Algorithmic work of one launch of a phase, with its bound: (amount, unit, bound, detail).
 
     mlp:   2 FLOP per multiply-add of the forward chain plus the input-gradient chain (no weight gradient):
@@ -195,7 +219,8 @@ def _algorithmic_work(w, phase, q):
            (gather form: each ordered pair once), plus 24 FP64 FLOP per atom of BOB + A;
            K steps per launch, serial.
     descriptors / pair_grad: FP32 ALU work per row, from the mean neighbour count nb within the descriptor cutoff:
-           nb (nb - 1) / 2 angular pairs x FLOP_ANG_* + nb x n_rbf x FLOP_RAD_* (+ LJ pairs for pair_grad).
+           nb (nb - 1) / 2 angular pairs x FLOP_ANG_* (pair sums) or nb x FLOP_MOM_*_NB + FLOP_MOM_*_ROW
+           (moments), + nb x n_rbf x FLOP_RAD_* (+ LJ pairs for pair_grad).
     transport: bytes that must cross HBM once per window."""
     s, t, K = w.system, w.target, w.integ.K
     N = s.n_atoms
@@ -212,12 +237,15 @@ def _algorithmic_work(w, phase, q):
         nb = _neighbours_per_atom(w, t.desc_cutoff)
         ang = nb * (nb - 1) / 2 if t.n_ang else 0.0
         if phase == "descriptors":
-            per_row = ang * FLOP_ANG_DESC + nb * t.n_rbf * FLOP_RAD_DESC
+            ang_f = (nb * FLOP_MOM_DESC_NB + FLOP_MOM_DESC_ROW) if moments else ang * FLOP_ANG_DESC
+            per_row = (ang_f if t.n_ang else 0.0) + nb * t.n_rbf * FLOP_RAD_DESC
         else:
             nlj = _neighbours_per_atom(w, t.lj_cutoff) if t.lj_cutoff else 0.0
-            per_row = ang * FLOP_ANG_GRAD + nb * t.n_rbf * FLOP_RAD_GRAD + nlj * FLOP_LJ_PAIR
+            ang_f = (nb * FLOP_MOM_GRAD_NB + FLOP_MOM_GRAD_ROW) if moments else ang * FLOP_ANG_GRAD
+            per_row = (ang_f if t.n_ang else 0.0) + nb * t.n_rbf * FLOP_RAD_GRAD + nlj * FLOP_LJ_PAIR
         return M * per_row, "FLOP", "alu", {"neighbours_per_atom": round(nb, 1), "rows": M,
-                                            "flop_per_row": round(per_row)}
+                                            "flop_per_row": round(per_row),
+                                            "angular": "moments" if moments else "pair sums"}
     if phase in ("transport_reduce",):
         return M * 3 * (4 + 4), "B", "hbm", {}
     if phase in ("transport_commit",):
@@ -256,7 +284,7 @@ def roofline(h, w, peaks, peak_kind, q, n_rep=20):
     phases = acc
     dom = max(phases, key=lambda k: phases[k])
     share = phases[dom] / sum(phases.values())
-    work = _algorithmic_work(w, dom, q)
+    work = _algorithmic_work(w, dom, q, h.angular_moments())
     sm_max = peaks.get("sm_max_mhz", 2032.0)
     fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s: 148 SMs x 128 FP32 lanes x FMA
     out = {"kernel": dom, "share": round(share, 3), "ms": round(phases[dom], 5),
@@ -276,8 +304,15 @@ def roofline(h, w, peaks, peak_kind, q, n_rep=20):
                     "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz" % sm_max})
         if dom == "draft":
             out["us_per_step"] = round(phases[dom] * 1e3 / w.integ.K, 3)
-            out["note"] = ("serial chain of K drafted steps in one thread-block cluster (at most 16 SMs); "
-                           "latency-bound: the per-step time, not FLOP/s, is the figure of merit")
+            out["note"] = ("serial chain of K drafted steps (one cooperative grid with a barrier per step for systems of "
+                           "2048 atoms or more, else one thread-block cluster of at most 16 SMs); latency-bound: the "
+                           "per-step time, not FLOP/s, is the figure of merit")
+        elif h.angular_moments():
+            out["note"] = ("FP32 operations counted from the kernel's formulas (angular block by moments: %d / %d "
+                           "FLOP per neighbour and %d / %d per row; radial term %d / %d FLOP; for descriptors / pair "
+                           "gradients) over the derived FP32 FMA peak" % (
+                               FLOP_MOM_DESC_NB, FLOP_MOM_GRAD_NB, FLOP_MOM_DESC_ROW, FLOP_MOM_GRAD_ROW,
+                               FLOP_RAD_DESC, FLOP_RAD_GRAD))
         else:
             out["note"] = ("FP32 operations counted from the kernel's formulas (angular pair %d / %d FLOP, radial "
                            "term %d / %d FLOP for descriptors / pair gradients) over the derived FP32 FMA peak" % (

@@ -230,6 +230,9 @@ LSD_API int lsd_set_plain_fused(lsd_handle *h, int32_t on);
  * LSD_EUNSUPPORTED when the target has no angular descriptors; LSD_ENOMEM when
  * the moments cannot be allocated. */
 LSD_API int lsd_set_angular_moments(lsd_handle *h, int32_t on);
+/* lsd_get_angular_moments: *on = 1 when the target's angular block runs by
+ * moments, else 0.  LSD_EINVAL for a null argument. */
+LSD_API int lsd_get_angular_moments(const lsd_handle *h, int32_t *on);
 
 /* lsd_set_grid_draft: the form of the draft (Alg. 2, draft_step K times) for
  * systems of at least 2048 atoms with a cell grid.  on (the default where

@@ -1548,6 +1548,12 @@ int lsd_set_angular_moments(lsd_handle *h, int32_t on) {
     return LSD_OK;
 }
 
+int lsd_get_angular_moments(const lsd_handle *h, int32_t *on) {
+    if (!h || !on) return LSD_EINVAL;
+    *on = (h->mom_on && h->target.dev.n_ang) ? 1 : 0;
+    return LSD_OK;
+}
+
 int lsd_set_grid_draft(lsd_handle *h, int32_t on) {
     if (!h) return LSD_EINVAL;
     if (on && !h->gplan.ok) return LSD_EUNSUPPORTED;

@@ -34,7 +34,7 @@ SYMBOLS = ["lsd_init", "lsd_draft_window", "lsd_verify_window", "lsd_step", "lsd
            "lsd_descriptors", "lsd_get_window", "lsd_profile_window", "lsd_checkpoint", "lsd_restore", "lsd_query",
            "lsd_target_mlp_static_dev", "lsd_destroy",
            "lsd_strerror", "lsd_launch_counts", "lsd_window_host", "lsd_transport_window", "lsd_get_frames",
-           "lsd_set_max_displacement", "lsd_set_plain_fused", "lsd_set_grid_draft", "lsd_set_angular_moments", "lsd_set_online_training", "lsd_online_status"]
+           "lsd_set_max_displacement", "lsd_set_plain_fused", "lsd_set_grid_draft", "lsd_set_angular_moments", "lsd_get_angular_moments", "lsd_set_online_training", "lsd_online_status"]
 
 
 class LSDError(RuntimeError):
@@ -113,6 +113,7 @@ def _lib():
             "lsd_set_plain_fused": [P, I32],
             "lsd_set_grid_draft": [P, I32],
             "lsd_set_angular_moments": [P, I32],
+            "lsd_get_angular_moments": [P, ctypes.POINTER(ctypes.c_int32)],
             "lsd_set_online_training": [P, I64, I32, ctypes.c_float, I32],
             "lsd_online_status": [P, P, P],
         }
@@ -311,6 +312,12 @@ class LSD:
     def set_angular_moments(self, on=True):
         """The target's angular descriptors and adjoint through Cartesian moments (O(n)) or the pair sums (O(n^2))."""
         _check(_lib().lsd_set_angular_moments(self.h, int(bool(on))), "lsd_set_angular_moments")
+
+    def angular_moments(self):
+        """Whether the target's angular block runs by moments."""
+        v = ctypes.c_int32()
+        _check(_lib().lsd_get_angular_moments(self.h, ctypes.byref(v)), "lsd_get_angular_moments")
+        return bool(v.value)
 
     def set_grid_draft(self, on=True):
         """Drafts in the grid form (one CTA per SM, grid-wide barriers; large systems) or in one cluster (off)."""
