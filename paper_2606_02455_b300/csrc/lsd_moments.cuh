@@ -34,13 +34,12 @@ constexpr int kMomFloats = 2 * kMomLd;      // one row: [eta][alpha]
 constexpr int kMomRuns = 64;                // two runs of up to four monomials per lane
 constexpr int kMomTab = 33;                 // floats per staged neighbour in the forward pass (odd: no bank conflicts)
 
-// index of the monomial (0, b, c), the first of its column
+// index of the monomial (0, b, c), the first of its column: the planes c' < c
+// (plane c' holds (D - c')(D - c' + 1) / 2 monomials, D = kMomDeg + 1), then
+// the columns b' < b of plane c (column b' holds D - c - b')
 __host__ __device__ constexpr int mom_col(int b, int c) {
-    int k = 0;
-    for (int cc = 0; cc < c; ++cc)
-        for (int bb = 0; bb <= kMomDeg - cc; ++bb) k += kMomDeg + 1 - bb - cc;
-    for (int bb = 0; bb < b; ++bb) k += kMomDeg + 1 - bb - c;
-    return k;
+    constexpr int D = kMomDeg + 1;
+    return D * (D + 1) * (D + 2) / 6 - (D - c) * (D - c + 1) * (D - c + 2) / 6 + b * (D - c) - b * (b - 1) / 2;
 }
 
 __host__ __device__ constexpr float mom_fact(int m) {
@@ -221,12 +220,10 @@ __device__ __forceinline__ void mom_forward(const NbStage &S, int n, float *tab,
     }
 }
 
-// The adjoint coefficients of one row into psi[k] = (Psi_k^1, Psi_k^2) (shared
-// memory, this warp's) and kappa (both etas): from dE/dX of the angular
-// features (wang, in shared memory) and the row's moments (global).
-__device__ __forceinline__ void mom_adjoint_coefs(const float *wang, const float *__restrict__ mom_row, float2 *psi,
-                                                  float *gk, int lane) {
-    // gk [2][9] gamma_m^e, then [18], [19] kappa^e: one per lane
+// The adjoint scalars of one row, gk[e * 9 + m] = gamma_m^e = dE/dM_m^e and
+// gk[18 + e] = kappa^e = dE/dQ^e, one per lane, from dE/dX of the sixteen
+// angular features (wang, shared memory); gk is this warp's (shared memory).
+__device__ __forceinline__ void mom_gamma_kappa(const float *wang, float *gk, int lane) {
     if (lane < 2 * (kMomDeg + 1) + 2) {
         float v = 0.f;
         if (lane < 2 * (kMomDeg + 1)) {
@@ -238,7 +235,7 @@ __device__ __forceinline__ void mom_adjoint_coefs(const float *wang, const float
 #pragma unroll
                 for (int mm = 0; mm <= kMomDeg; ++mm)
                     if (mm == m) bz = mom_binom(z, mm);
-                const float sg = (m & 1) ? -bz : bz;
+                const float sg = (m & 1) ? -bz : bz;   // lambda = -1
                 v += 0.5f * pref * (wang[4 * z + e] * bz + wang[4 * z + 2 + e] * sg);
             }
         } else {
@@ -250,13 +247,6 @@ __device__ __forceinline__ void mom_adjoint_coefs(const float *wang, const float
             }
         }
         gk[lane] = v;
-    }
-    __syncwarp();
-    for (int k = lane; k < kMomAlpha; k += 32) {
-        const float2 dm = kMomCoefTab.dm[k];
-        const int m = (int)dm.x;
-        const float f = 2.f * dm.y;
-        psi[k] = make_float2(f * gk[m] * __ldg(mom_row + k), f * gk[kMomDeg + 1 + m] * __ldg(mom_row + kMomLd + k));
     }
     __syncwarp();
 }
@@ -313,39 +303,6 @@ __device__ __forceinline__ void mom_eval(const float2 *psi, float ux, float uy, 
                 G[e][1] = fmaf(G[e][1], uz, Hy[e]);
             }
         }
-    }
-}
-
-// The pair gradients of one row by the moment adjoint: lanes over neighbours,
-// radial and angular parts of g_p together, g_p to pg[p] and summed into fx,
-// fy, fz (lane partials).  wbuf: the row's dE/dX (shared memory); psi, gk: this
-// warp's adjoint buffers.
-__device__ __forceinline__ void mom_pair_grads(const NbStage &S, int n, const PotDev &P, int S_, const float *wbuf,
-                                               const float *__restrict__ mom_row, float2 *psi, float *gk,
-                                               float4 *__restrict__ pg, int lane, float &fx, float &fy, float &fz) {
-    mom_adjoint_coefs(wbuf + S_ * P.n_rbf, mom_row, psi, gk, lane);
-    const float k1 = gk[2 * (kMomDeg + 1)], k2 = gk[2 * (kMomDeg + 1) + 1];
-    for (int p = lane; p < n; p += 32) {
-        const float4 gp = S.g[p], cp = S.c[p];
-        const float ri = gp.w, r = S.r[p];
-        const float ux = gp.x * ri, uy = gp.y * ri, uz = gp.z * ri;
-        float F[2], G[2][3];
-        mom_eval(psi, ux, uy, uz, F, G);
-        const float fc = cp.x, dfc = cp.y;
-        const float w1 = fc * cp.z, w2 = fc * cp.w;
-        const float wp1 = (dfc - 2.f * 0.005f * r * fc) * cp.z, wp2 = (dfc - 2.f * 0.05f * r * fc) * cp.w;
-        const float A = (F[0] + 2.f * k1 * w1) * wp1 + (F[1] + 2.f * k2 * w2) * wp2;
-        const float bx = w1 * G[0][0] + w2 * G[1][0], by = w1 * G[0][1] + w2 * G[1][1],
-                    bz = w1 * G[0][2] + w2 * G[1][2];
-        const float ub = ux * bx + uy * by + uz * bz;
-        const float cr = radial_dcoef(S, p, P, wbuf) + A;   // along u: radial and the w' terms
-        const float gx = cr * ux + (bx - ub * ux) * ri;
-        const float gy = cr * uy + (by - ub * uy) * ri;
-        const float gz = cr * uz + (bz - ub * uz) * ri;
-        pg[p] = make_float4(gx, gy, gz, 0.f);
-        fx += gx;
-        fy += gy;
-        fz += gz;
     }
 }
 

@@ -212,14 +212,13 @@ __global__ void desc_mom_kernel(const uint4 *__restrict__ fix, const int *__rest
 // SLOTS: neighbours per lane (lane l owns p = l + 32 s); every row has at most
 // 32 SLOTS of them.  The angular pairs run by diagonals (row_pair_grads): a
 // fixed order of summation with no atomics, so the forces do not depend on the
-// launch shape.  SLOTS = 0: the angular adjoint by moments (mom: the rows'
-// moments from desc_mom_kernel), lanes over neighbours.
+// launch shape.
 template <int SLOTS>
-__global__ void __launch_bounds__(256, SLOTS == 0 ? 2 : 1) pairgrad_kernel(const uint4 *__restrict__ fix, const int *__restrict__ near_keys,
+__global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__restrict__ near_keys,
                                 const int *__restrict__ n_near, const int *__restrict__ far_keys,
                                 const int *__restrict__ n_far, int cap, int cap_far, int M, Geo g, PotDev P,
                                 const float *__restrict__ dEdX, float4 *__restrict__ pair_g,
-                                float4 *__restrict__ Fpart, float *__restrict__ E_lj, const float *__restrict__ mom) {
+                                float4 *__restrict__ Fpart, float *__restrict__ E_lj) {
     // MLP potentials: the previous kernel is the MLP, and the neighbour lists
     // and positions come from kernels that finished before it began, so the
     // geometry staging and the LJ part run before the wait, while the MLP still
@@ -237,11 +236,7 @@ __global__ void __launch_bounds__(256, SLOTS == 0 ? 2 : 1) pairgrad_kernel(const
     const uint4 fi = fj[i];
     const int warps = blockDim.x >> 5;
     float *wbuf = smem + (size_t)warps * kNbStageFloats * cap + (size_t)wib * P.d0p;
-    // after every warp's staging and dE/dX: the pair hand-over [cap] (pairs), or psi [kMomLd] and gamma, kappa [32]
-    float *tail = smem + (size_t)warps * (kNbStageFloats * cap + P.d0p);
-    float4 *tb = reinterpret_cast<float4 *>(tail) + (size_t)wib * cap;
-    float2 *psi = reinterpret_cast<float2 *>(tail + (size_t)wib * (2 * kMomLd + 32));
-    float *gk = tail + (size_t)wib * (2 * kMomLd + 32) + 2 * kMomLd;
+    float4 *tb = reinterpret_cast<float4 *>(smem + (size_t)warps * (kNbStageFloats * cap + P.d0p)) + (size_t)wib * cap;
     NbStage S = nb_stage_ptrs(smem + (size_t)wib * kNbStageFloats * cap, cap);
     const int n = n_near[row];
     const int *keys = near_keys + (size_t)row * cap;
@@ -271,12 +266,127 @@ __global__ void __launch_bounds__(256, SLOTS == 0 ? 2 : 1) pairgrad_kernel(const
         pdl_wait();
         for (int f = lane; f < P.d0p; f += 32) wbuf[f] = dEdX[(size_t)row * P.d0p + f];
         __syncwarp();
-        if (SLOTS == 0)
-            mom_pair_grads(S, n, P, g.S, wbuf, mom + (size_t)row * kMomFloats, psi, gk, pair_g + (size_t)row * cap,
-                           lane, fx, fy, fz);
-        else
-            row_pair_grads<SLOTS == 0 ? 1 : SLOTS>(S, n, P, g.S, wbuf, tb, pair_g + (size_t)row * cap, lane, fx, fy,
-                                                   fz);
+        row_pair_grads<SLOTS>(S, n, P, g.S, wbuf, tb, pair_g + (size_t)row * cap, lane, fx, fy, fz);
+    }
+    fx = warp_sum(fx);
+    fy = warp_sum(fy);
+    fz = warp_sum(fz);
+    e = warp_sum(e);
+    if (lane == 0) {
+        Fpart[row] = make_float4(fx, fy, fz, 0.f);
+        E_lj[row] = e;
+    }
+}
+
+// The pair gradients with the angular adjoint by moments (lsd_moments.cuh):
+// lanes over neighbours throughout, each lane forming its neighbour's
+// geometry in registers (the same operations as the descriptor staging), so
+// only dE/dX and the adjoint coefficients live in shared memory.  LJ pairs of
+// the descriptor list are taken in the same pass.
+__global__ void __launch_bounds__(256, 3)
+    pairgrad_mom_kernel(const uint4 *__restrict__ fix, const int *__restrict__ near_keys,
+                        const int *__restrict__ n_near, const int *__restrict__ far_keys,
+                        const int *__restrict__ n_far, int cap, int cap_far, int M, Geo g, PotDev P,
+                        const float *__restrict__ dEdX, float4 *__restrict__ pair_g, float4 *__restrict__ Fpart,
+                        float *__restrict__ E_lj, const float *__restrict__ mom) {
+    pdl_release();
+    extern __shared__ __align__(16) float smem[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (row >= M) return;
+    const int N = g.N;
+    const int j = row / N, i = row - j * N;
+    const uint4 *fj = fix + (size_t)j * N;
+    const uint4 fi = fj[i];
+    const int si = (int)fi.w;
+    float *wbuf = smem + (size_t)wib * (P.d0p + 2 * kMomLd + 32);
+    float2 *psi = reinterpret_cast<float2 *>(wbuf + P.d0p);
+    float *gk = wbuf + P.d0p + 2 * kMomLd;
+    const int n = n_near[row];
+    const int *keys = near_keys + (size_t)row * cap;
+    float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+    auto lj_pair = [&](const float3 &d, float d2, int sk) {
+        if (!(P.has_lj && d2 < P.lj_rc2f)) return;
+        const int pr = si * g.S + sk;
+        const float s2 = P.lj_sig2[pr] / d2;
+        const float s6 = s2 * s2 * s2, s12 = s6 * s6;
+        const float fr = -P.lj_eps24[pr] * (2.f * s12 - s6) / d2;   // (dU/dr)/r
+        fx += fr * d.x;
+        fy += fr * d.y;
+        fz += fr * d.z;
+        e += 0.5f * (P.lj_eps4[pr] * (s12 - s6) - P.lj_shift[pr]);
+    };
+    {
+        // LJ partners beyond the descriptor cutoff, while the network still runs
+        const int nf = n_far[row];
+        const int *fkeys = far_keys + (size_t)row * cap_far;
+        for (int t = lane; t < nf; t += 32) {
+            const int key = fkeys[t];
+            const uint4 fk = fj[key >> 5];
+            const float3 d = entry_disp(fi, fk, key & 31, g);
+            lj_pair(d, dist2_rule(d.x, d.y, d.z), (int)fk.w);
+        }
+    }
+    pdl_wait();
+    // the row's moments, loads issued before the coefficients they scale are formed
+    constexpr int kPhiPerLane = (kMomFloats + 31) / 32;
+    const float *mrow = mom + (size_t)row * kMomFloats;
+    float phi[kPhiPerLane];
+#pragma unroll
+    for (int u = 0; u < kPhiPerLane; ++u) phi[u] = lane + 32 * u < kMomFloats ? __ldg(mrow + lane + 32 * u) : 0.f;
+    for (int f = lane; f < P.d0p; f += 32) wbuf[f] = dEdX[(size_t)row * P.d0p + f];
+    __syncwarp();
+    mom_gamma_kappa(wbuf + g.S * P.n_rbf, gk, lane);
+    float *psf = reinterpret_cast<float *>(psi);
+#pragma unroll
+    for (int u = 0; u < kPhiPerLane; ++u) {
+        const int k = lane + 32 * u;
+        const int et = k >= kMomLd ? 1 : 0, kk = k - et * kMomLd;
+        if (k < kMomFloats && kk < kMomAlpha) {
+            const float2 dm = kMomCoefTab.dm[kk];
+            psf[2 * kk + et] = 2.f * dm.y * gk[et * (kMomDeg + 1) + (int)dm.x] * phi[u];
+        }
+    }
+    __syncwarp();
+    const float k1 = gk[2 * (kMomDeg + 1)], k2 = gk[2 * (kMomDeg + 1) + 1];
+    const int nr = P.n_rbf;
+    float4 *pg = pair_g + (size_t)row * cap;
+    for (int p = lane; p < n; p += 32) {
+        const int key = keys[p];
+        const uint4 fk = fj[key >> 5];
+        const float3 d = entry_disp(fi, fk, key & 31, g);
+        const float r2 = dist2_rule(d.x, d.y, d.z);
+        lj_pair(d, r2, (int)fk.w);
+        if (!P.has_mlp) continue;
+        const float r = sqrtf(r2);
+        float fc, dfc;
+        cutoff_fn(r, P.desc_rc, fc, dfc);
+        const float ri = 1.f / r;
+        const float e1 = expf(-0.005f * r2), e2 = expf(-0.05f * r2);
+        // radial: c = sum_k w_k g_k'(r)
+        float cr = 0.f;
+        const float *wr = wbuf + (int)fk.w * nr;
+        for (int k = 0; k < nr; ++k) {
+            const float t = r - (float)k * P.rbf_w;
+            const float ph = expf(-t * t * P.rbf_inv2w2);
+            cr += wr[k] * ph * (-t * P.rbf_invw2 * fc + dfc);
+        }
+        const float ux = d.x * ri, uy = d.y * ri, uz = d.z * ri;
+        float F[2], G[2][3];
+        mom_eval(psi, ux, uy, uz, F, G);
+        const float w1 = fc * e1, w2 = fc * e2;
+        const float wp1 = (dfc - 2.f * 0.005f * r * fc) * e1, wp2 = (dfc - 2.f * 0.05f * r * fc) * e2;
+        cr += (F[0] + 2.f * k1 * w1) * wp1 + (F[1] + 2.f * k2 * w2) * wp2;
+        const float bx = w1 * G[0][0] + w2 * G[1][0], by = w1 * G[0][1] + w2 * G[1][1],
+                    bz = w1 * G[0][2] + w2 * G[1][2];
+        const float ub = ux * bx + uy * by + uz * bz;
+        const float gx = cr * ux + (bx - ub * ux) * ri;
+        const float gy = cr * uy + (by - ub * uy) * ri;
+        const float gz = cr * uz + (bz - ub * uz) * ri;
+        pg[p] = make_float4(gx, gy, gz, 0.f);
+        fx += gx;
+        fy += gy;
+        fz += gz;
     }
     fx = warp_sum(fx);
     fy = warp_sum(fy);
@@ -411,15 +521,18 @@ void launch_pairgrad(const uint4 *fix, const int *near_keys, const int *n_near, 
                      int cap, int cap_far, int M, const Geo &g, const PotDev &P, const float *dEdX, float4 *pair_g,
                      float4 *Fpart, float *E_lj, cudaStream_t s, const float *mom) {
     const int warps = 8;
-    const bool by_mom = mom && P.n_ang && P.has_mlp;
-    const size_t tail = by_mom ? (size_t)(2 * kMomLd + 32) : (size_t)4 * cap;
-    const size_t sm = desc_smem_bytes(warps, cap) + (size_t)warps * (P.d0p + tail) * sizeof(float);
+    if (mom && P.n_ang && P.has_mlp) {
+        const size_t sm = (size_t)warps * (P.d0p + 2 * kMomLd + 32) * sizeof(float);
+        launch_dependent(pairgrad_mom_kernel, (M + warps - 1) / warps, warps * 32, sm, s, fix, near_keys, n_near,
+                         far_keys, n_far, cap, cap_far, M, g, P, dEdX, pair_g, Fpart, E_lj, mom);
+        return;
+    }
+    const size_t sm = desc_smem_bytes(warps, cap) + (size_t)warps * (P.d0p + 4 * cap) * sizeof(float);
     // lists of at most 128 hold mostly rows of a few dozen neighbours: flattened pairs with a small register
     // footprint; longer lists run their large rows by diagonals
-    auto k = by_mom ? pairgrad_kernel<0>
-                    : (cap <= 128 ? pairgrad_kernel<4> : (cap <= 256 ? pairgrad_kernel<8> : pairgrad_kernel<16>));
+    auto k = cap <= 128 ? pairgrad_kernel<4> : (cap <= 256 ? pairgrad_kernel<8> : pairgrad_kernel<16>);
     launch_dependent(k, (M + warps - 1) / warps, warps * 32, sm, s, fix, near_keys, n_near, far_keys, n_far, cap,
-                     cap_far, M, g, P, dEdX, pair_g, Fpart, E_lj, mom);
+                     cap_far, M, g, P, dEdX, pair_g, Fpart, E_lj);
 }
 
 void launch_force_gather(const int *near_keys, const int *n_near, int cap, int M, int N, int has_mlp,
@@ -438,7 +551,7 @@ cudaError_t verify_kernels_setup(int max_smem) {
     e = cudaFuncSetAttribute(desc_mom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e != cudaSuccess) return e;
     const void *pk[4] = {(const void *)pairgrad_kernel<4>, (const void *)pairgrad_kernel<8>,
-                         (const void *)pairgrad_kernel<16>, (const void *)pairgrad_kernel<0>};
+                         (const void *)pairgrad_kernel<16>, (const void *)pairgrad_mom_kernel};
     for (const void *k : pk) {
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
         if (e != cudaSuccess) return e;
