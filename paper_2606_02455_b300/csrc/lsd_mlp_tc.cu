@@ -367,21 +367,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 tc::tmem_ld16(tacc + c, v);
             }
         };
-        auto load_sp = [&](int l, int c, float (&d)[16]) {
-            if (sp_tmem) {
-                tc::tmem_ld16(tacc + ACC + l * W + c, d);
-            } else {
-                const uint4 *o = reinterpret_cast<const uint4 *>(sp_addr(l, c));
+        // SiLU' of 16 columns from the scratch: the raw bf16 words (fetched ahead of use), then unpacked
+        auto fetch_sp = [&](int l, int c, uint4 (&u)[2]) {
+            const uint4 *o = reinterpret_cast<const uint4 *>(sp_addr(l, c));
+            u[0] = o[0];
+            u[1] = o[1];
+        };
+        auto unpack_sp = [&](const uint4 (&u)[2], float (&d)[16]) {
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const uint4 u = o[q];
-                    const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+            for (int q = 0; q < 2; ++q) {
+                const uint32_t w4[4] = {u[q].x, u[q].y, u[q].z, u[q].w};
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162 *>(&w4[e]);
-                        d[8 * q + 2 * e] = __low2float(h2);
-                        d[8 * q + 2 * e + 1] = __high2float(h2);
-                    }
+                for (int e = 0; e < 4; ++e) {
+                    const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162 *>(&w4[e]);
+                    d[8 * q + 2 * e] = __low2float(h2);
+                    d[8 * q + 2 * e + 1] = __high2float(h2);
                 }
             }
         };
@@ -491,6 +491,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (int l = L - 1; l >= 0; --l) {
                 const int dout = l == 0 ? d0p : W;
                 const bool iok = issue(W, dout);
+                // the scratch's SiLU'(h_{l-1}) of this thread's first chunk, fetched while the GEMM runs; each
+                // later chunk's is fetched while the previous one is processed (L2 latency off the chain)
+                const bool sp_glob = l > 0 && !sp_tmem;
+                uint4 spn[2] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
+                if (sp_glob && 16 * cb < dout) fetch_sp(l - 1, 16 * cb, spn);
                 if (l == L - 1) {
                     if (cb == 0) {
                         for (int b = 1; b < 4 && 16 * b < W; ++b) y += S.ypart[(b - 1) * kTcRows + r];
@@ -515,10 +520,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 am = 0.f;
                 for (int c = 16 * cb; c < dout; c += 64) {
                     float v[16];
+                    uint4 spc[2] = {spn[0], spn[1]};
+                    if (sp_glob && c + 64 < dout) fetch_sp(l - 1, c + 64, spn);
                     load_acc(c, dout, v);
                     if (l > 0) {
                         float d[16];
-                        load_sp(l - 1, c, d);
+                        if (sp_tmem)
+                            tc::tmem_ld16(tacc + ACC + (l - 1) * W + c, d);
+                        else
+                            unpack_sp(spc, d);
 #pragma unroll
                         for (int i = 0; i < 16; ++i) v[i] *= dq * d[i];
                         if (amax) am = amax16(am, v);
