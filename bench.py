@@ -162,6 +162,15 @@ def _lj_pairs_per_atom(w, q):
 # DRAM bytes (read + write) of one launch, from one ncu capture of the kernel as it is now (the summaries under
 # profiles/ give the command); a kernel changed since its capture has no entry here.
 NCU_TRAFFIC = {
+    # desc_mom_kernel: 501,708,288 B per launch on the 32,768-atom workload shortened to K = 8 (262,144 rows; the
+    # moments written, 1,344 B per row, and the staged geometry scale with rows: a K = 64 launch moves 8x that);
+    # 199,167,744 B on the 4,096-atom workload (131,072 rows)
+    ("fp8_mlp_32768atoms_K64", "descriptors"): 8 * 501708288,
+    ("bf16_mlp_4096atoms_K32", "descriptors"): 199167744,
+    # pairgrad_mom_kernel: 873,477,120 B per launch at K = 8 (the moments read back, the pair gradients written),
+    # 8x for K = 64; 368,440,576 B on the 4,096-atom workload
+    ("fp8_mlp_32768atoms_K64", "pair_grad"): 8 * 873477120,
+    ("bf16_mlp_4096atoms_K32", "pair_grad"): 368440576,
 }
 
 
