@@ -31,8 +31,10 @@ constexpr int kMomDeg = 8;
 constexpr int kMomAlpha = 165;              // (kMomDeg + 1)(kMomDeg + 2)(kMomDeg + 3) / 6
 constexpr int kMomLd = 168;                 // one eta's moments, padded to a multiple of 4
 constexpr int kMomFloats = 2 * kMomLd;      // one row: [eta][alpha]
-constexpr int kMomRuns = 64;                // two runs of up to four monomials per lane
+constexpr int kMomRuns = 64;                // two runs of one or two monomials per lane
 constexpr int kMomTab = 33;                 // floats per staged neighbour in the forward pass (odd: no bank conflicts)
+// per warp: the powers [32][kMomTab], padding to 16 bytes, 32 float4 (x, w1, w2, species), 32 float2 (r, fc)
+constexpr int kMomTabFloats = 32 * kMomTab + 4 + 128 + 64;
 
 // index of the monomial (0, b, c), the first of its column: the planes c' < c
 // (plane c' holds (D - c')(D - c' + 1) / 2 monomials, D = kMomDeg + 1), then
@@ -48,42 +50,76 @@ __host__ __device__ constexpr float mom_fact(int m) {
     return f;
 }
 
-// The forward pass: each lane owns two runs of up to four monomials
-// x^a y^b z^c, a = a0 .. a0 + 3, of one column.  A run is (a0, 9 + b, 18 + c)
-// (offsets into a neighbour's staged powers), its first index k0 and length,
-// and the multinomials m! / alpha! of its four members.
+// The forward pass accumulates only the moments of degree 8 and 7 (45 + 36 =
+// 81 monomials): since |u| = 1, every lower degree follows exactly from the
+// traces Phi_beta = Phi_{beta + 2 e_x} + Phi_{beta + 2 e_y} + Phi_{beta + 2 e_z}
+// (u^beta (x^2 + y^2 + z^2) = u^beta), degree m - 2 from degree m.  Each lane
+// owns two runs: a degree-7 monomial x^a y^b z^c with its degree-8 neighbour
+// x^(a+1) y^b z^c (36 pairs), or a degree-8 monomial y^b z^(8-b) alone (9).  A
+// run is (a, 9 + b, 18 + c) (offsets into a neighbour's staged powers) and its
+// first index k0 and length.
 struct MomRunTable {
-    int4 run[kMomRuns];      // (a0, 9 + b, 18 + c, k0 << 8 | len)
-    float4 mult[kMomRuns];
+    int4 run[kMomRuns];   // (a, 9 + b, 18 + c, k0 << 8 | len)
 };
 __host__ __device__ constexpr MomRunTable mom_run_table() {
     MomRunTable t{};
     int r = 0;
-    for (int c = 0; c <= kMomDeg; ++c)
-        for (int b = 0; b <= kMomDeg - c; ++b) {
-            const int L = kMomDeg + 1 - b - c;
-            for (int a0 = 0; a0 < L; a0 += 4) {
-                const int len = L - a0 < 4 ? L - a0 : 4;
-                t.run[r] = int4{a0, 9 + b, 18 + c, ((mom_col(b, c) + a0) << 8) | len};
-                float m4[4] = {0.f, 0.f, 0.f, 0.f};
-                for (int s = 0; s < len; ++s) {
-                    const int a = a0 + s;
-                    m4[s] = mom_fact(a + b + c) / (mom_fact(a) * mom_fact(b) * mom_fact(c));
-                }
-                t.mult[r] = float4{m4[0], m4[1], m4[2], m4[3]};
-                ++r;
-            }
+    for (int c = 0; c < kMomDeg; ++c)
+        for (int b = 0; b < kMomDeg - c; ++b) {
+            const int a = kMomDeg - 1 - b - c;
+            t.run[r++] = int4{a, 9 + b, 18 + c, ((mom_col(b, c) + a) << 8) | 2};
         }
-    for (; r < kMomRuns; ++r) {
-        t.run[r] = int4{0, 9, 18, 0};   // empty run
-        t.mult[r] = float4{0.f, 0.f, 0.f, 0.f};
-    }
+    for (int b = 0; b <= kMomDeg; ++b) t.run[r++] = int4{0, 9 + b, 18 + kMomDeg - b, (mom_col(b, kMomDeg - b) << 8) | 1};
+    for (; r < kMomRuns; ++r) t.run[r] = int4{0, 9, 18, 0};   // empty run
     return t;
 }
 static_assert(mom_col(0, kMomDeg + 1) == kMomAlpha, "monomial count");
 
 // (global memory, not constant: lanes read different entries, which the constant cache would serialise)
 static __device__ const MomRunTable kMomRunTab = mom_run_table();
+
+// The trace rounds: round q forms degrees 6 - 2q and 5 - 2q from degrees 8 - 2q
+// and 7 - 2q; entry (dst, src1, src2, src3) of a degree-d monomial beta, the
+// sources beta + 2 e_x, beta + 2 e_y, beta + 2 e_z.
+constexpr int kMomTrace = kMomAlpha - 81;   // 84 monomials of degree <= 6
+struct MomTraceTable {
+    int4 e[kMomTrace];
+    int start[5];   // round q: entries start[q] .. start[q + 1]
+};
+__host__ __device__ constexpr MomTraceTable mom_trace_table() {
+    MomTraceTable t{};
+    int i = 0, q = 0;
+    for (int m = kMomDeg - 2; m >= 0; m -= 2, ++q) {
+        t.start[q] = i;
+        for (int d = m; d >= m - 1 && d >= 0; --d)
+            for (int c = 0; c <= d; ++c)
+                for (int b = 0; b <= d - c; ++b) {
+                    const int a = d - b - c;
+                    t.e[i++] = int4{mom_col(b, c) + a, mom_col(b, c) + a + 2, mom_col(b + 2, c) + a,
+                                    mom_col(b, c + 2) + a};
+                }
+    }
+    t.start[q] = i;
+    return t;
+}
+static_assert(mom_trace_table().start[4] == kMomTrace, "trace entries");
+static __device__ const MomTraceTable kMomTraceTab = mom_trace_table();
+
+// Monomial indices by degree: degree m's (m + 1)(m + 2) / 2 indices from
+// kMomDegStart[m] (the features need M_m = sum over one degree).
+struct MomDegTable {
+    int k[kMomAlpha];
+};
+__host__ __device__ constexpr MomDegTable mom_deg_table() {
+    MomDegTable t{};
+    int i = 0;
+    for (int m = 0; m <= kMomDeg; ++m)
+        for (int c = 0; c <= m; ++c)
+            for (int b = 0; b <= m - c; ++b) t.k[i++] = mom_col(b, c) + m - b - c;
+    return t;
+}
+static __device__ const MomDegTable kMomDegTab = mom_deg_table();
+__host__ __device__ constexpr int mom_deg_start(int m) { return m * (m + 1) * (m + 2) / 6; }
 
 // Per monomial: its degree and multinomial m! / alpha! (the adjoint's scaling).
 struct MomCoefTable {
@@ -109,28 +145,52 @@ __host__ __device__ constexpr float mom_binom(int z, int m) {
     return v;
 }
 
-// The angular features of one row (x[0 .. 15]) and its moments
-// (mom_out[e * kMomLd + k], global) from the n staged neighbours of S.  tab:
-// this warp's staging buffer of 32 neighbours x kMomTab floats (x^0..8,
-// y^0..8, z^0..8 at 0, 9, 18; x, w1, w2 at 27, 28, 29; the odd row length
-// puts the 32 lanes' rows, and one row's entries, in distinct banks).  The sums run over
-// neighbours in list order for every lane: the result does not depend on the
-// launch shape.
-__device__ __forceinline__ void mom_forward(const NbStage &S, int n, float *tab, float *__restrict__ mom_out,
-                                            float *x, int lane) {
+// One row's descriptors without a full staging of its neighbours: in chunks
+// of 32, lane q forms neighbour q's geometry in registers (the operations of
+// nb_stage_load) and stages its powers x^0..8, y^0..8, z^0..8 (rows of kMomTab
+// floats: the odd length puts the 32 lanes' rows, and one row's entries, in
+// distinct banks), (x, w1, w2, species) and (r, fc); then the radial blocks
+// accumulate with lanes over basis functions (two halves over the chunk's
+// neighbours, the order of desc_radial) and the top moments with lanes over
+// runs.  x: the row's descriptors (radial blocks at 0, the sixteen angular
+// features at S_ n_rbf); mom_out: the row's moments [e * kMomLd + k] (global);
+// tab: this warp's kMomTabFloats floats, afterwards holding the moments.  The
+// sums run over neighbours in list order and the traces in a fixed order: the
+// result does not depend on the launch shape.
+__device__ __forceinline__ void mom_row_descriptors(const uint4 *__restrict__ fj, uint4 fi,
+                                                    const int *__restrict__ keys, int n, const Geo &g,
+                                                    const PotDev &P, int S_, float *tab,
+                                                    float *__restrict__ mom_out, float *x, int lane) {
+    static_assert(32 * kMomTab >= kMomFloats, "the staging buffer holds the moments afterwards");
+    float *phs = tab;
+    float4 *xw = reinterpret_cast<float4 *>(tab + 32 * kMomTab + 4);
+    float2 *rf = reinterpret_cast<float2 *>(tab + 32 * kMomTab + 4 + 128);
     const int4 r0 = kMomRunTab.run[lane], r1 = kMomRunTab.run[lane + 32];
-    float acc[2][4][2];
+    const int nr = P.n_rbf, kb = lane & 15, half = lane >> 4;
+    const float mu = (float)kb * P.rbf_w;
+    float racc[kMaxSpecies];
+#pragma unroll
+    for (int sp = 0; sp < kMaxSpecies; ++sp) racc[sp] = 0.f;
+    float acc[2][2][2];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
-        for (int s = 0; s < 4; ++s) acc[r][s][0] = acc[r][s][1] = 0.f;
+        for (int s = 0; s < 2; ++s) acc[r][s][0] = acc[r][s][1] = 0.f;
     float q1 = 0.f, q2 = 0.f;
     for (int base = 0; base < n; base += 32) {
         const int p = base + lane;
         if (p < n) {
-            const float4 gp = S.g[p], cp = S.c[p];
-            const float ux = gp.x * gp.w, uy = gp.y * gp.w, uz = gp.z * gp.w;
-            const float w1 = cp.x * cp.z, w2 = cp.x * cp.w;
+            const int key = keys[p];
+            const uint4 fk = fj[key >> 5];
+            const float3 d = entry_disp(fi, fk, key & 31, g);
+            const float r2 = dist2_rule(d.x, d.y, d.z);
+            const float r = sqrtf(r2);
+            float fc, dfc;
+            cutoff_fn(r, P.desc_rc, fc, dfc);
+            const float ri = 1.f / r;
+            const float e1 = expf(-0.005f * r2), e2 = expf(-0.05f * r2);
+            const float ux = d.x * ri, uy = d.y * ri, uz = d.z * ri;
+            const float w1 = fc * e1, w2 = fc * e2;
             q1 += w1 * w1;
             q2 += w2 * w2;
             float *t = tab + lane * kMomTab;
@@ -144,62 +204,90 @@ __device__ __forceinline__ void mom_forward(const NbStage &S, int n, float *tab,
                 py *= uy;
                 pz *= uz;
             }
-            t[27] = ux;
-            t[28] = w1;
-            t[29] = w2;
+            xw[lane] = make_float4(ux, w1, w2, __int_as_float((int)fk.w));
+            rf[lane] = make_float2(r, fc);
         }
         __syncwarp();
         const int cnt = n - base < 32 ? n - base : 32;
+        if (kb < nr)
+            for (int q = half; q < cnt; q += 2) {
+                const float2 v = rf[q];
+                const int sp = __float_as_int(xw[q].w);
+                const float t = v.x - mu;
+                const float b = __expf(-t * t * P.rbf_inv2w2) * v.y;
+#pragma unroll
+                for (int s2 = 0; s2 < kMaxSpecies; ++s2) racc[s2] += (sp == s2) ? b : 0.f;
+            }
         for (int q = 0; q < cnt; ++q) {
             const float *t = tab + q * kMomTab;
-            const float vx = t[27], w1 = t[28], w2 = t[29];
-            float m0 = t[r0.x] * t[r0.y] * t[r0.z];
-            float m1 = t[r1.x] * t[r1.y] * t[r1.z];
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                acc[0][s][0] = fmaf(w1, m0, acc[0][s][0]);
-                acc[0][s][1] = fmaf(w2, m0, acc[0][s][1]);
-                acc[1][s][0] = fmaf(w1, m1, acc[1][s][0]);
-                acc[1][s][1] = fmaf(w2, m1, acc[1][s][1]);
-                m0 *= vx;
-                m1 *= vx;
-            }
+            const float4 v = xw[q];
+            const float vx = v.x, w1 = v.y, w2 = v.z;
+            const float m0 = t[r0.x] * t[r0.y] * t[r0.z];
+            const float m1 = t[r1.x] * t[r1.y] * t[r1.z];
+            const float m0x = m0 * vx, m1x = m1 * vx;
+            acc[0][0][0] = fmaf(w1, m0, acc[0][0][0]);
+            acc[0][0][1] = fmaf(w2, m0, acc[0][0][1]);
+            acc[0][1][0] = fmaf(w1, m0x, acc[0][1][0]);
+            acc[0][1][1] = fmaf(w2, m0x, acc[0][1][1]);
+            acc[1][0][0] = fmaf(w1, m1, acc[1][0][0]);
+            acc[1][0][1] = fmaf(w2, m1, acc[1][0][1]);
+            acc[1][1][0] = fmaf(w1, m1x, acc[1][1][0]);
+            acc[1][1][1] = fmaf(w2, m1x, acc[1][1][1]);
         }
         __syncwarp();
     }
-    // the moments out; each lane's contributions to M_m^e by degree
-    float Mp[2][kMomDeg + 1];
+    // the radial blocks: the two halves' sums
 #pragma unroll
-    for (int m = 0; m <= kMomDeg; ++m) Mp[0][m] = Mp[1][m] = 0.f;
+    for (int sp = 0; sp < kMaxSpecies; ++sp) racc[sp] += __shfl_down_sync(0xffffffffu, racc[sp], 16);
+    if (lane < nr) {
+#pragma unroll
+        for (int sp = 0; sp < kMaxSpecies; ++sp)
+            if (sp < S_) x[sp * nr + lane] = racc[sp];
+    }
+    x += S_ * nr;   // the angular features follow
+    // the top degrees into phs, then the lower degrees by traces
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int4 ru = r ? r1 : r0;
-        const float4 mu = r ? kMomRunTab.mult[lane + 32] : kMomRunTab.mult[lane];
         const int k0 = ru.w >> 8, len = ru.w & 255;
-        const int d0 = ru.x + (ru.y - 9) + (ru.z - 18);   // degree of the run's first member
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
+        for (int s = 0; s < 2; ++s)
             if (s < len) {
-                mom_out[k0 + s] = acc[r][s][0];
-                mom_out[kMomLd + k0 + s] = acc[r][s][1];
+                phs[k0 + s] = acc[r][s][0];
+                phs[kMomLd + k0 + s] = acc[r][s][1];
             }
-            const float ms = s == 0 ? mu.x : (s == 1 ? mu.y : (s == 2 ? mu.z : mu.w));   // 0 past len
-            const float v0 = ms * acc[r][s][0] * acc[r][s][0], v1 = ms * acc[r][s][1] * acc[r][s][1];
+    }
+    __syncwarp();
 #pragma unroll
-            for (int m = 0; m <= kMomDeg; ++m) {
-                Mp[0][m] += (d0 + s == m) ? v0 : 0.f;
-                Mp[1][m] += (d0 + s == m) ? v1 : 0.f;
-            }
+    for (int q = 0; q < 4; ++q) {
+        const int e0 = kMomTraceTab.start[q], cntq = kMomTraceTab.start[q + 1] - e0;
+        for (int t = lane; t < 2 * cntq; t += 32) {
+            const int4 d = kMomTraceTab.e[e0 + (t >> 1)];
+            float *ph = phs + (t & 1) * kMomLd;
+            ph[d.x] = (ph[d.y] + ph[d.z]) + ph[d.w];
         }
+        __syncwarp();
     }
-    if (lane < kMomLd - kMomAlpha) {
-        mom_out[kMomAlpha + lane] = 0.f;
-        mom_out[kMomLd + kMomAlpha + lane] = 0.f;
+    // moments out (coalesced), and the sums M_m^e degree by degree
+    for (int k = lane; k < kMomLd; k += 32) {
+        mom_out[k] = k < kMomAlpha ? phs[k] : 0.f;
+        mom_out[kMomLd + k] = k < kMomAlpha ? phs[kMomLd + k] : 0.f;
     }
+    float M0[kMomDeg + 1], M1[kMomDeg + 1];
 #pragma unroll
     for (int m = 0; m <= kMomDeg; ++m) {
-        Mp[0][m] = warp_sum(Mp[0][m]);
-        Mp[1][m] = warp_sum(Mp[1][m]);
+        float v0 = 0.f, v1 = 0.f;
+        const int cm = (m + 1) * (m + 2) / 2;
+#pragma unroll
+        for (int j0 = 0; j0 < cm; j0 += 32)
+            if (j0 + lane < cm) {
+                const int k = kMomDegTab.k[mom_deg_start(m) + j0 + lane];
+                const float mu = kMomCoefTab.dm[k].y, a0 = phs[k], a1 = phs[kMomLd + k];
+                v0 = fmaf(mu * a0, a0, v0);
+                v1 = fmaf(mu * a1, a1, v1);
+            }
+        M0[m] = warp_sum(v0);
+        M1[m] = warp_sum(v1);
     }
     q1 = warp_sum(q1);
     q2 = warp_sum(q2);
@@ -211,7 +299,7 @@ __device__ __forceinline__ void mom_forward(const NbStage &S, int n, float *tab,
         for (int m = 0; m <= kMomDeg; ++m) {
             const float bz = z == 0 ? mom_binom(0, m) : (z == 1 ? mom_binom(1, m) : (z == 2 ? mom_binom(2, m) : mom_binom(3, m)));
             const float sg = (l && (m & 1)) ? -bz : bz;
-            acc_f = fmaf(sg, e ? Mp[1][m] : Mp[0][m], acc_f);
+            acc_f = fmaf(sg, e ? M1[m] : M0[m], acc_f);
         }
         const int zeta = 1 << z;
         const float diag = l ? 0.f : (float)(1 << zeta);   // (1 + lambda)^zeta

@@ -148,6 +148,10 @@ __device__ __forceinline__ float4 pair_terms(const NbStage &S, const AngW &W, in
 
 // The radial blocks of one row's descriptors into x: lanes over basis
 // functions (two halves over neighbours), one shuffle between the halves.
+// The Gaussian basis values use the hardware exponential (__expf: relative
+// error within about 1e-6 for the arguments of the terms that matter, |x| < 10;
+// the tiny far terms carry a few ulp more): the basis is the bulk of the
+// radial work, and FP32 accuracy of the descriptors needs no more.
 __device__ __forceinline__ void desc_radial(const NbStage &S, int n, const PotDev &P, int S_, float *x, int lane) {
     const int nr = P.n_rbf;
     float acc[kMaxSpecies];
@@ -158,7 +162,7 @@ __device__ __forceinline__ void desc_radial(const NbStage &S, int n, const PotDe
         const float mu = (float)kb * P.rbf_w;
         for (int p = lane >> 4; p < n; p += 2) {
             const float t = S.r[p] - mu;
-            const float v = expf(-t * t * P.rbf_inv2w2) * S.c[p].x;
+            const float v = __expf(-t * t * P.rbf_inv2w2) * S.c[p].x;
             const int sp = S.sp[p];
 #pragma unroll
             for (int s = 0; s < kMaxSpecies; ++s) acc[s] += (sp == s) ? v : 0.f;
@@ -253,7 +257,7 @@ __device__ __forceinline__ float radial_dcoef(const NbStage &S, int p, const Pot
     const float *wr = wbuf + S.sp[p] * nr;
     for (int k = 0; k < nr; ++k) {
         const float t = rp - (float)k * P.rbf_w;
-        const float phi = expf(-t * t * P.rbf_inv2w2);
+        const float phi = __expf(-t * t * P.rbf_inv2w2);
         c += wr[k] * phi * (-t * P.rbf_invw2 * fp + dfp);
     }
     return c;

@@ -181,8 +181,9 @@ __global__ void desc_kernel(const uint4 *__restrict__ fix, const int *__restrict
 
 // The same descriptors with the angular block by moments (lsd_moments.cuh),
 // the row's moments to mom [row][kMomFloats] for the adjoint.  Shared memory
-// per warp: the staged neighbours, then 32 neighbours' staged powers.
-__global__ void desc_mom_kernel(const uint4 *__restrict__ fix, const int *__restrict__ near_keys,
+// per warp: one chunk of 32 neighbours' staged powers and geometry (later the
+// row's moments), 5 KB: four blocks of eight warps per SM.
+__global__ void __launch_bounds__(256, 4) desc_mom_kernel(const uint4 *__restrict__ fix, const int *__restrict__ near_keys,
                                 const int *__restrict__ n_near, int cap, int M, Geo g, PotDev P, float *__restrict__ X,
                                 float *__restrict__ mom) {
     pdl_wait();
@@ -195,13 +196,11 @@ __global__ void desc_mom_kernel(const uint4 *__restrict__ fix, const int *__rest
     const int j = row / N, i = row - j * N;
     const uint4 *fj = fix + (size_t)j * N;
     const uint4 fi = fj[i];
-    float *base = smem + (size_t)wib * (kNbStageFloats * cap + 32 * kMomTab);
-    NbStage S = nb_stage_ptrs(base, cap);
+    float *tab = smem + (size_t)wib * kMomTabFloats;
     const int n = n_near[row];
-    nb_stage_load(S, fj, fi, near_keys + (size_t)row * cap, n, g, P.desc_rc, lane);
     float *x = X + (size_t)row * P.d0p;
-    desc_radial(S, n, P, g.S, x, lane);
-    mom_forward(S, n, base + kNbStageFloats * cap, mom + (size_t)row * kMomFloats, x + g.S * P.n_rbf, lane);
+    mom_row_descriptors(fj, fi, near_keys + (size_t)row * cap, n, g, P, g.S, tab, mom + (size_t)row * kMomFloats, x,
+                        lane);
     desc_onehot(P, g.S, (int)fi.w, x, lane);
 }
 
@@ -368,7 +367,7 @@ __global__ void __launch_bounds__(256, 3)
         const float *wr = wbuf + (int)fk.w * nr;
         for (int k = 0; k < nr; ++k) {
             const float t = r - (float)k * P.rbf_w;
-            const float ph = expf(-t * t * P.rbf_inv2w2);
+            const float ph = __expf(-t * t * P.rbf_inv2w2);   // as in desc_radial
             cr += wr[k] * ph * (-t * P.rbf_invw2 * fc + dfc);
         }
         const float ux = d.x * ri, uy = d.y * ri, uz = d.z * ri;
@@ -508,7 +507,7 @@ void launch_desc(const uint4 *fix, const int *near_keys, const int *n_near, int 
                  const PotDev &P, float *X, cudaStream_t s, float *mom) {
     const int warps = 8;
     if (mom && P.n_ang) {
-        const size_t sm = (size_t)warps * (kNbStageFloats * cap + 32 * kMomTab) * sizeof(float);
+        const size_t sm = (size_t)warps * kMomTabFloats * sizeof(float);
         launch_dependent(desc_mom_kernel, (M + warps - 1) / warps, warps * 32, sm, s, fix, near_keys, n_near, cap, M,
                          g, P, X, mom);
         return;
