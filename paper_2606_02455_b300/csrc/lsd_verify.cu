@@ -282,7 +282,7 @@ __global__ void pairgrad_kernel(const uint4 *__restrict__ fix, const int *__rest
 // geometry in registers (the same operations as the descriptor staging), so
 // only dE/dX and the adjoint coefficients live in shared memory.  LJ pairs of
 // the descriptor list are taken in the same pass.
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
     pairgrad_mom_kernel(const uint4 *__restrict__ fix, const int *__restrict__ near_keys,
                         const int *__restrict__ n_near, const int *__restrict__ far_keys,
                         const int *__restrict__ n_far, int cap, int cap_far, int M, Geo g, PotDev P,
