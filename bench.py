@@ -43,9 +43,21 @@ def _peaks():
             "fallback"
 
 
-def _workload(cfg):
+# The dense configurations draft with a learned draft (the 4,096-atom one: "learned BF16 draft"; the 32,768-atom
+# one: "learned draft retrained online every 10,000 accepted steps"): LJ + a per-atom MLP on 8 radial basis
+# functions per species in BF16, trained during the untimed set-up by the library's online force matching on the
+# target-verified frames of its own LSD run (`train_rounds` retrainings, one every `train_every` accepted steps),
+# then timed with the trained draft; online retraining stays on at the configuration's cadence where it has one.
+LEARNED_ONLINE = {4: 0, 5: 10000}   # configuration -> retraining cadence (accepted steps) during the timed run
+
+
+def _workload(cfg, pair_draft=False):
     from paper_2606_02455_b300 import workloads as W
-    return W.CONFIGS[cfg]()
+    w = W.CONFIGS[cfg]()
+    if cfg in LEARNED_ONLINE and not pair_draft:
+        w.draft = W.learned_draft(w.target, w.system.n_species)
+    w.cfg = cfg
+    return w
 
 
 class Clocks:
@@ -241,7 +253,16 @@ def _algorithmic_work(w, phase, q, moments=False):
     if phase == "draft":
         nb = _lj_pairs_per_atom(w, q)
         flop = K * (N * nb * FLOP_LJ_PAIR + N * 24)
-        return flop, "FLOP", "alu", {"lj_pairs_per_atom": round(nb, 1), "steps_per_launch": K}
+        detail = {"lj_pairs_per_atom": round(nb, 1), "steps_per_launch": K}
+        d = w.draft
+        if d.n_layers:
+            # the learned draft per atom and step: the radial basis of every descriptor neighbour (forward 8 FLOP,
+            # adjoint 12 per basis function), the MLP forward and its input gradient (4 d_in W)
+            nbd = _neighbours_per_atom(w, d.desc_cutoff)
+            d0 = w.system.n_species * d.n_rbf + d.n_ang + w.system.n_species
+            flop += K * N * (nbd * d.n_rbf * (FLOP_RAD_DESC + FLOP_RAD_GRAD) + 4 * d0 * d.width)
+            detail["descriptor_neighbours_per_atom"] = round(nbd, 1)
+        return flop, "FLOP", "alu", detail
     if phase in ("descriptors", "pair_grad") and t.n_layers:
         nb = _neighbours_per_atom(w, t.desc_cutoff)
         ang = nb * (nb - 1) / 2 if t.n_ang else 0.0
@@ -382,6 +403,30 @@ def measure_workload(w, args, world, rank, full):
     h.set_stream(stream)
     # equilibrate with plain target dynamics
     h.plain_step(args.equil)
+    train = None
+    cfg = getattr(w, "cfg", None)
+    if cfg in LEARNED_ONLINE and w.draft.n_layers:
+        # the learned draft, trained online on the run's own frames (untimed set-up)
+        t0 = time.perf_counter()
+        a = h.stats()
+        h.set_pipelining(not args.no_pipeline)
+        h.set_frame_capture(args.train_frames)
+        h.set_online_training(args.train_every, n_iters=args.train_iters, lr=3e-3, frames_per_iter=args.train_fpi)
+        while h.online_status()[0] < args.train_rounds:
+            h.step(max(args.train_every // 4, 8))
+        n_rt, loss = h.online_status()
+        b = h.stats()
+        cad = LEARNED_ONLINE[cfg]
+        if cad:
+            h.set_online_training(cad, n_iters=args.train_iters, lr=3e-3, frames_per_iter=args.train_fpi)
+        else:
+            h.set_online_training(0)
+            h.set_frame_capture(0)
+        train = {"retrainings": n_rt, "last_loss": loss, "accepted_steps": b["committed"] - a["committed"],
+                 "beta_while_training": round((b["rejected"] - a["rejected"]) / max(b["committed"] - a["committed"], 1), 4),
+                 "wall_s": round(time.perf_counter() - t0, 2), "every_accepted": args.train_every,
+                 "iters": args.train_iters, "frames": args.train_frames, "frames_per_iter": args.train_fpi,
+                 "timed_run_cadence": cad or None}
     q_eq, p_eq, step_eq = h.get_state()
     flush_needed = _working_set_bytes(w) < 4 * L2_BYTES
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda") if flush_needed else None
@@ -461,7 +506,10 @@ def measure_workload(w, args, world, rank, full):
         "speedup_vs_plain": round(value / plain_value, 4),
         "l2": "flushed (256 MB write) before every timed window and once before the plain steps" if flush is not None
         else "not flushed: the window's working set (%.2f GB) is larger than L2" % (_working_set_bytes(w) / 1e9),
+        "draft": _draft_label(w) + (" trained online before timing" if train else ""),
     }
+    if train:
+        out["draft_training"] = train
     if not full:
         h.close()
         return out
@@ -509,7 +557,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    w = _workload(args.config)
+    w = _workload(args.config, getattr(args, "pair_draft", False))
     K = w.integ.K
     m = measure_workload(w, args, world, rank, full=True)
     st0, st1 = m["st0"], m["st1"]
@@ -517,7 +565,7 @@ def run_ours(args):
     for cfg in args.extra:
         if cfg == args.config:
             continue
-        extra["config%d" % cfg] = measure_workload(_workload(cfg), args, world, rank, full=False)
+        extra["config%d" % cfg] = measure_workload(_workload(cfg, args.pair_draft), args, world, rank, full=False)
     t = w.target
     line = {
         "metric": METRIC, "value": m["value"], "unit": "ns/day", "n_gpus": world, "steps": args.steps,
@@ -537,7 +585,7 @@ def run_ours(args):
                    "target": "LJ + 0.05 eV tanh(MLP %d->%dx%d->1, %s)" % (
                        w.system.n_species * t.n_rbf + t.n_ang + w.system.n_species, t.width, t.n_layers,
                        t.precision),
-                   "draft": _draft_label(w), "parallelism": "replicas" if world > 1 else "single",
+                   "draft": m["draft"], "parallelism": "replicas" if world > 1 else "single",
                    "l2": m["l2"]},
         "acceptance_rate": m["acceptance_rate"],
         "analysis": _analysis(st1, st0, m["roofline"], K, m["t_plain"] / m["n_plain"]),
@@ -553,6 +601,8 @@ def run_ours(args):
         "clocks": m["clocks"],
         "workloads": extra,
     }
+    if "draft_training" in m:
+        line["draft_training"] = m["draft_training"]
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     if rank == 0:
@@ -667,7 +717,7 @@ def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
         return
-    w = _workload(args.config)
+    w = _workload(args.config, getattr(args, "pair_draft", False))
     from oracle import oracle as O
     O.build()
     threads = _oracle_threads()
@@ -711,6 +761,12 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-pipeline", action="store_true", help="time the unpipelined window loop only")
+    ap.add_argument("--pair-draft", action="store_true", help="the dense configurations with the bare LJ draft")
+    ap.add_argument("--train-rounds", type=int, default=3, help="online retrainings of the learned draft before timing")
+    ap.add_argument("--train-every", type=int, default=200, help="accepted steps between retrainings before timing")
+    ap.add_argument("--train-iters", type=int, default=40)
+    ap.add_argument("--train-frames", type=int, default=128)
+    ap.add_argument("--train-fpi", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -132,39 +132,53 @@ __device__ void learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
     float *sr = stage, *sfc = stage + kLearnCap;
     int *ssp = (int *)(stage + 2 * kLearnCap);
     int cnt = 0;
-    for (int base = 0; base < nc; base += 32) {
-        const int t = base + lane;
-        // the (at most 8) images of k within the descriptor cutoff, in enumeration order
-        float rs[8];
-        int nm = 0, sk = 0;
-        const int k = t < nc ? (cand.p ? cand[t] : t) : i;
-        if (k != i) {
-            const uint4 fk = fx[k];
-            sk = (int)fk.w;
-            for_images(g, fi, fk, P.desc_rc2f, minimg, [&](float, float, float, float d2) {
-                if (d2 < P.desc_rc2f && nm < 8) rs[nm++] = sqrtf(d2);
-            });
-        }
-        int sc = nm;
+    // candidates four per lane in flight: their list entries and positions are loaded before any is tested
+    constexpr int kB = 4;
+    for (int base0 = 0; base0 < nc; base0 += 32 * kB) {
+        int kq[kB];
+        uint4 fq[kB];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, sc, o);
-            if (lane >= o) sc += v;
+        for (int u = 0; u < kB; ++u) {
+            const int t = base0 + 32 * u + lane;
+            kq[u] = t < nc ? (cand.p ? cand[t] : t) : i;
         }
-        const int tot = __shfl_sync(0xffffffffu, sc, 31);
-        int w = cnt + sc - nm;
-        for (int c = 0; c < nm; ++c) {
-            if (w < kLearnCap) {
-                const float r = rs[c];
-                float fc, dfc;
-                cutoff_fn(r, P.desc_rc, fc, dfc);
-                sr[w] = r;
-                sfc[w] = fc;
-                ssp[w] = sk;
+#pragma unroll
+        for (int u = 0; u < kB; ++u) fq[u] = kq[u] != i ? fx[kq[u]] : fi;
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            if (base0 + 32 * u >= nc) break;   // uniform over the warp
+            // the (at most 8) images of k within the descriptor cutoff, in enumeration order
+            float rs[8];
+            int nm = 0, sk = 0;
+            const int k = kq[u];
+            if (k != i) {
+                const uint4 fk = fq[u];
+                sk = (int)fk.w;
+                for_images(g, fi, fk, P.desc_rc2f, minimg, [&](float, float, float, float d2) {
+                    if (d2 < P.desc_rc2f && nm < 8) rs[nm++] = sqrtf(d2);
+                });
             }
-            ++w;
+            int sc = nm;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, sc, o);
+                if (lane >= o) sc += v;
+            }
+            const int tot = __shfl_sync(0xffffffffu, sc, 31);
+            int w = cnt + sc - nm;
+            for (int c = 0; c < nm; ++c) {
+                if (w < kLearnCap) {
+                    const float r = rs[c];
+                    float fc, dfc;
+                    cutoff_fn(r, P.desc_rc, fc, dfc);
+                    sr[w] = r;
+                    sfc[w] = fc;
+                    ssp[w] = sk;
+                }
+                ++w;
+            }
+            cnt += tot;
         }
-        cnt += tot;
     }
     __syncwarp();
     const int n = cnt < kLearnCap ? cnt : kLearnCap;
@@ -173,18 +187,22 @@ __device__ void learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
         float acc[kMaxSpecies];
 #pragma unroll
         for (int s = 0; s < kMaxSpecies; ++s) acc[s] = 0.f;
-        const int kb = lane & 15;
+        // lanes over basis functions (8 or 16 wide), the groups of lanes over neighbours, then a reduction over
+        // the groups: every lane busy for n_rbf <= 8 as for 16
+        const int nb = nr <= 8 ? 8 : 16;
+        const int kb = lane & (nb - 1), ng = 32 / nb;
         if (kb < nr) {
             const float mu = (float)kb * P.rbf_w;
-            for (int p = lane >> 4; p < n; p += 2) {
+            for (int p = lane / nb; p < n; p += ng) {
                 const float t = sr[p] - mu;
-                const float v = expf(-t * t * P.rbf_inv2w2) * sfc[p];
+                const float v = __expf(-t * t * P.rbf_inv2w2) * sfc[p];   // the hardware exponential, as the target's basis
 #pragma unroll
                 for (int s = 0; s < kMaxSpecies; ++s) acc[s] += (ssp[p] == s) ? v : 0.f;
             }
         }
+        for (int o = 16; o >= nb; o >>= 1)
 #pragma unroll
-        for (int s = 0; s < kMaxSpecies; ++s) acc[s] += __shfl_down_sync(0xffffffffu, acc[s], 16);
+            for (int s = 0; s < kMaxSpecies; ++s) acc[s] += __shfl_down_sync(0xffffffffu, acc[s], o);
         for (int f = lane; f < P.d0p; f += 32) xbuf[f] = 0.f;
         __syncwarp();
         if (lane < nr)
@@ -662,51 +680,81 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                     gather([&](int k) { return fx[k]; }, [&](int t) { return use_list ? lst[t] : t; });
                 }
             }
-            for (int t = lane; t < ((!LEARNED && minimg) ? 0 : nl); t += 32) {
-                const int k = use_list ? lst[t] : t;
-                if (k == i) continue;
-                const uint4 fk = fx[k];
-                const int pr2 = si * g.S + (int)fk.w;
-                const float sig2 = slj[pr2], eps24 = slj[kMaxSpecies * kMaxSpecies + pr2];
-                for_images(g, fi, fk, rc2_all, minimg != 0, [&](float dx, float dy, float dz, float d2) {
-                    if (P.has_lj && d2 < P.lj_rc2f) {
-                        const float inv = 1.f / d2;
-                        const float s2 = sig2 * inv;
-                        const float s6 = s2 * s2 * s2, s12 = s6 * s6;
-                        const float fr = -eps24 * (2.f * s12 - s6) * inv;
-                        fxx += fr * dx;
-                        fyy += fr * dy;
-                        fzz += fr * dz;
-                    }
-                    if (LEARNED && d2 < P.desc_rc2f) {
-                        // radial adjoint in gather form: (c_ik + c_ki) d/r
-                        const float r = sqrtf(d2);
-                        float fc, dfc;
-                        cutoff_fn(r, P.desc_rc, fc, dfc);
-                        float cc = 0.f;
-                        if (stage_dedx) {
-                            const int SR = g.S * P.n_rbf;
-                            const float *gi = sdedx + (size_t)i * SR + (int)fk.w * P.n_rbf;
-                            const float *gk = sdedx + (size_t)k * SR + si * P.n_rbf;
-                            for (int b = 0; b < P.n_rbf; ++b) {
-                                const float tt = r - (float)b * P.rbf_w;
-                                const float dg = expf(-tt * tt * P.rbf_inv2w2) * (-tt * P.rbf_invw2 * fc + dfc);
-                                cc += (gi[b] + gk[b]) * dg;
-                            }
-                        } else {
-                            const float *gi = w_dEdX + (size_t)i * P.d0p + (int)fk.w * P.n_rbf;
-                            const float *gk = w_dEdX + (size_t)k * P.d0p + si * P.n_rbf;
-                            for (int b = 0; b < P.n_rbf; ++b) {
-                                const float tt = r - (float)b * P.rbf_w;
-                                const float dg = expf(-tt * tt * P.rbf_inv2w2) * (-tt * P.rbf_invw2 * fc + dfc);
-                                cc += (__ldcg(gi + b) + __ldcg(gk + b)) * dg;
-                            }
+            // (the learned draft, or general images) candidates four per lane in flight, each lane's in list order
+            for (int t0 = lane; t0 < ((!LEARNED && minimg) ? 0 : nl); t0 += 128) {
+                int kq[4];
+                uint4 fq[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int t = t0 + 32 * u;
+                    kq[u] = t < nl ? (use_list ? lst[t] : t) : i;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) fq[u] = kq[u] != i ? fx[kq[u]] : fi;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (t0 + 32 * u >= nl) break;
+                    const int k = kq[u];
+                    if (k == i) continue;
+                    const uint4 fk = fq[u];
+                    const int pr2 = si * g.S + (int)fk.w;
+                    const float sig2 = slj[pr2], eps24 = slj[kMaxSpecies * kMaxSpecies + pr2];
+                    for_images(g, fi, fk, rc2_all, minimg != 0, [&](float dx, float dy, float dz, float d2) {
+                        if (P.has_lj && d2 < P.lj_rc2f) {
+                            const float inv = 1.f / d2;
+                            const float s2 = sig2 * inv;
+                            const float s6 = s2 * s2 * s2, s12 = s6 * s6;
+                            const float fr = -eps24 * (2.f * s12 - s6) * inv;
+                            fxx += fr * dx;
+                            fyy += fr * dy;
+                            fzz += fr * dz;
                         }
-                        fxx += cc * dx / r;
-                        fyy += cc * dy / r;
-                        fzz += cc * dz / r;
-                    }
-                });
+                        if (LEARNED && d2 < P.desc_rc2f) {
+                            // radial adjoint in gather form: (c_ik + c_ki) d/r
+                            const float r = sqrtf(d2);
+                            float fc, dfc;
+                            cutoff_fn(r, P.desc_rc, fc, dfc);
+                            float cc = 0.f;
+                            if (stage_dedx) {
+                                const int SR = g.S * P.n_rbf;
+                                const float *gi = sdedx + (size_t)i * SR + (int)fk.w * P.n_rbf;
+                                const float *gk = sdedx + (size_t)k * SR + si * P.n_rbf;
+                                for (int b = 0; b < P.n_rbf; ++b) {
+                                    const float tt = r - (float)b * P.rbf_w;
+                                    const float dg = __expf(-tt * tt * P.rbf_inv2w2) * (-tt * P.rbf_invw2 * fc + dfc);
+                                    cc += (gi[b] + gk[b]) * dg;
+                                }
+                            } else if ((P.n_rbf & 3) == 0 && (P.d0p & 3) == 0) {
+                                // both atoms' blocks of dE/dX through L2, four basis functions per 16-byte load
+                                const float4 *gi = reinterpret_cast<const float4 *>(w_dEdX + (size_t)i * P.d0p +
+                                                                                    (int)fk.w * P.n_rbf);
+                                const float4 *gk = reinterpret_cast<const float4 *>(w_dEdX + (size_t)k * P.d0p +
+                                                                                    si * P.n_rbf);
+                                for (int b4 = 0; b4 < P.n_rbf / 4; ++b4) {
+                                    const float4 a = __ldcg(gi + b4), c = __ldcg(gk + b4);
+                                    const float gs[4] = {a.x + c.x, a.y + c.y, a.z + c.z, a.w + c.w};
+#pragma unroll
+                                    for (int e = 0; e < 4; ++e) {
+                                        const float tt = r - (float)(4 * b4 + e) * P.rbf_w;
+                                        const float dg = __expf(-tt * tt * P.rbf_inv2w2) * (-tt * P.rbf_invw2 * fc + dfc);
+                                        cc += gs[e] * dg;
+                                    }
+                                }
+                            } else {
+                                const float *gi = w_dEdX + (size_t)i * P.d0p + (int)fk.w * P.n_rbf;
+                                const float *gk = w_dEdX + (size_t)k * P.d0p + si * P.n_rbf;
+                                for (int b = 0; b < P.n_rbf; ++b) {
+                                    const float tt = r - (float)b * P.rbf_w;
+                                    const float dg = __expf(-tt * tt * P.rbf_inv2w2) * (-tt * P.rbf_invw2 * fc + dfc);
+                                    cc += (__ldcg(gi + b) + __ldcg(gk + b)) * dg;
+                                }
+                            }
+                            fxx += cc * dx / r;
+                            fyy += cc * dy / r;
+                            fzz += cc * dz / r;
+                        }
+                    });
+                }
             }
             // the three warp sums in six shuffles: halves exchange pairs of
             // components, quarters single ones, then an ordinary butterfly;
