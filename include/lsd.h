@@ -141,10 +141,12 @@ typedef struct {
     int64_t windows;            /* windows run                                              */
     int64_t committed;          /* steps committed                                          */
     int64_t rejected;           /* committed steps that were reflected (at most 1 per window)*/
-    int64_t verified;           /* window steps verified (K per window)                     */
+    int64_t verified;           /* window steps verified (k_eff per window; staged windows:
+                                   the steps up to the end of the last stage run)           */
     double sum_delta;           /* sum of |delta| (Mahalanobis, Eq. 6) over committed steps  */
     double sum_pred_reject;     /* sum of erf(|delta|/sqrt 8) over committed steps (Eq. 6)   */
     int64_t step;               /* index of the current state                               */
+    int64_t stages;             /* verification passes: one per window, or per stage run     */
 } lsd_stats;
 
 typedef struct lsd_handle lsd_handle;
@@ -302,6 +304,25 @@ LSD_API int lsd_get_draft_weights(const lsd_handle *h, float *weights, size_t n_
  * lsd_draft_window / lsd_verify_window / lsd_profile_window stay unpipelined. */
 LSD_API int lsd_set_pipelining(lsd_handle *h, int32_t on);
 
+/* lsd_set_window_stages: verify each window of lsd_step / lsd_enqueue_windows /
+ * lsd_window_host in stages of S steps (0 < S < K; 0 or S >= K: one pass, the
+ * default).  Stage s drafts steps sS .. min(K, sS + S) - 1, continuing from
+ * the last drafted state, verifies them (the target forces and the transport
+ * reductions of Alg. 1), and decides over every step drafted so far.  When
+ * all of them are accepted, the draft reached the stage's end and the step
+ * cap lies beyond it, the next stage runs: a conditional node of the window's
+ * graph, set on the device, so the host does not wait.  Otherwise the window
+ * commits exactly what a one-pass window commits (the first rejection and the
+ * steps before it), and the steps past that stage are neither drafted nor
+ * verified.  Committed trajectories and every statistic but `verified` and
+ * `stages` are bit-identical to one-pass windows; per-step window arrays
+ * (lsd_get_window) hold the drafted steps only.  Frames captured
+ * (lsd_set_frame_capture) are the verified steps, fewer than one pass
+ * verifies.  Not with pipelining: LSD_ESTATE when pipelining is on, and
+ * lsd_set_pipelining(h, 1) returns LSD_ESTATE while stages are set.
+ * LSD_EINVAL for S < 0. */
+LSD_API int lsd_set_window_stages(lsd_handle *h, int32_t steps_per_stage);
+
 /* lsd_set_integrator: the Langevin splitting of the chain.
  *   LSD_ABOBA (default): Eq. 2; the state is (q, p) after a full ABOBA step.
  *   LSD_OBABO: App. E.  The chain runs in the staggered frame, whose transition
@@ -437,6 +458,14 @@ LSD_API int lsd_query(const lsd_handle *h, int32_t *K, int32_t *n_atoms, int32_t
  * call, whatever its step count.  Memory-set nodes are not kernels and are not
  * counted.  Any pointer may be null.  No GPU work. */
 LSD_API int lsd_launch_counts(const lsd_handle *h, int32_t *per_window, int32_t *per_round, int32_t *per_plain);
+
+/* lsd_stage_launch_counts: with windows verified in stages
+ * (lsd_set_window_stages), the kernels of a window's first stage (its Verlet
+ * lists included) and of each later stage; a window launches
+ * first + (stages run - 1) * later (lsd_stats.stages counts the stages run).
+ * Without stages, first = per_window of lsd_launch_counts and later = 0.  Any
+ * pointer may be null.  No GPU work. */
+LSD_API int lsd_stage_launch_counts(const lsd_handle *h, int32_t *first, int32_t *later);
 
 /* lsd_target_mlp_static_dev: the target potential's per-atom MLP (energies
  * and dE/dX) on the tensor cores, in the target's own operand arithmetic

@@ -134,6 +134,7 @@ struct lsd_handle {
     int *pf_keys = nullptr, *pf_cnt = nullptr;
     float4 *pf_pg = nullptr;
     unsigned long long *pf_bar = nullptr;   // its grid-barrier counter
+    int stage_len = 0;        // windows verified in stages of this many steps (0: in one pass)
     bool drafted = false;
     bool unbounded = false;   // target_step set to "no cap" by lsd_enqueue_*
     // learned-draft training
@@ -435,8 +436,11 @@ float *mom_for(const lsd_handle *h, const PotHost &pot) {
 // coordinates are in fix ([Kc][N]); forces to F ([Kc][N][3]).
 // With use_list the candidates are the window's Verlet lists (the window and
 // plain-step paths); otherwise all atoms (explicit configurations).
+// j_off: the window step of row block 0 (one stage of a window verified in
+// stages), against which keff is compared.
 void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, float *F, float *E_out,
-                  cudaStream_t s, bool use_list = false, const VerletBufs *vb = nullptr, const int *keff = nullptr) {
+                  cudaStream_t s, bool use_list = false, const VerletBufs *vb = nullptr, const int *keff = nullptr,
+                  int j_off = 0) {
     const int M = Kc * h->N;
     const PotDev &P = pot.dev;
     if (!vb) vb = &h->vbufs;
@@ -444,10 +448,11 @@ void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, f
     if (!keff) keff = &h->st->k_eff;
     if (use_list)
         launch_neigh_list(fix, vb->vlist, vb->vcount, h->vplan.cap, M, h->geo, pot.rmax2f, pot.near2f,
-                          h->cap_near, h->cap_far, h->near_keys, h->far_keys, h->n_near, h->n_far, h->st, keff, s);
+                          h->cap_near, h->cap_far, h->near_keys, h->far_keys, h->n_near, h->n_far, h->st, keff, s,
+                          j_off);
     else
         launch_neigh_build(fix, M, h->geo, pot.rmax2f, pot.near2f, h->cap_near, h->cap_far, h->near_keys,
-                           h->far_keys, h->n_near, h->n_far, h->st, s, keff_rows);
+                           h->far_keys, h->n_near, h->n_far, h->st, s, keff_rows, j_off);
     if (P.has_mlp) {
         launch_desc(fix, h->near_keys, h->n_near, h->cap_near, M, h->geo, P, h->X, s, mom_for(h, pot));
         enqueue_mlp(h, pot, M, s);
@@ -485,6 +490,27 @@ void enqueue_verify_buf(lsd_handle *h, int b, cudaStream_t s, const int *keff) {
     if (h->train.capture_on) enqueue_frame_capture(h->train, w.qmid, h->w_Ft, h->K, h->N, h->st, keff, s);
     launch_transport(h->K, h->geo, h->coef, h->species, w.qmid, w.pdraft, w.Fd, h->w_Ft, w.Fraw, h->ec_dF, h->ec_on,
                      h->q, h->p, h->p_obabo, h->st, h->partials, keff, s);
+}
+
+// Stage [j0, j1) of a window verified in stages: the Verlet lists (first
+// stage), the draft of steps j0 .. j1 - 1 continued from step j0 - 1, their
+// verification in rows 0 .. j1 - j0 - 1 of the workspace, and the transport's
+// decision over steps 0 .. j1 - 1.  next: the conditional handle of the next
+// stage's node (0 for the last stage), set by the transport when the window
+// goes on.
+void enqueue_stage(lsd_handle *h, int j0, int j1, cudaGraphConditionalHandle next, cudaStream_t s) {
+    lsd_handle::WinBufs &w = h->wb[0];
+    const size_t N = h->N;
+    const int *keff = &h->st->k_eff;
+    if (j0 == 0 && !h->vplan.all_pairs) launch_verlet_build(h->vplan, h->q, h->species, h->geo, w.vb, h->st, s);
+    launch_draft(h->grid_draft ? h->gplan : h->dplan, h->learned_small, j1, h->geo, h->draft.dev, h->coef, h->vplan,
+                 w.vb, h->species, h->q, h->p, h->ec_dF, h->ec_on, h->st, w.qmid, w.pdraft, w.Fd, w.Fraw, w.fix,
+                 h->w_dEdX, s, nullptr, 0, h->dsync, j0);
+    enqueue_eval(h, h->target, w.fix + (size_t)j0 * N, j1 - j0, h->w_Ft + (size_t)j0 * 3 * N, nullptr, s,
+                 !h->vplan.all_pairs, &w.vb, keff, j0);
+    if (h->train.capture_on) enqueue_frame_capture(h->train, w.qmid, h->w_Ft, j1, h->N, h->st, keff, s, j0);
+    launch_transport(j1, h->geo, h->coef, h->species, w.qmid, w.pdraft, w.Fd, h->w_Ft, w.Fraw, h->ec_dF, h->ec_on,
+                     h->q, h->p, h->p_obabo, h->st, h->partials, keff, s, j0, next ? 1 : 0, next);
 }
 
 void enqueue_draft(lsd_handle *h, cudaStream_t s) { enqueue_draft_buf(h, 0, s, nullptr, h->q, h->p); }
@@ -574,8 +600,61 @@ int build_round_graph(lsd_handle *h, int b, cudaGraphExec_t *out) {
     return LSD_OK;
 }
 
+// A window verified in stages of stage_len steps: stage 0 in the top graph,
+// then stage s in the body of an IF node that follows stage s - 1's transport
+// (nested: each handle belongs to the graph whose kernel sets it).
+int build_staged_graph(lsd_handle *h, cudaGraphExec_t *out) {
+    const int K = h->K, S = h->stage_len, n_stages = (K + S - 1) / S;
+    cudaGraph_t top = nullptr;
+    CK(cudaGraphCreate(&top, 0));
+    cudaGraph_t cur = top;
+    cudaError_t e = cudaSuccess;
+    for (int st = 0; st < n_stages && e == cudaSuccess; ++st) {
+        const int j0 = st * S, j1 = j0 + S < K ? j0 + S : K;
+        const bool more = st + 1 < n_stages;
+        cudaGraphConditionalHandle next = 0;
+        if (more && (e = cudaGraphConditionalHandleCreate(&next, cur, 0u, cudaGraphCondAssignDefault)) != cudaSuccess)
+            break;
+        if ((e = cudaStreamBeginCaptureToGraph(h->stream, cur, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            break;
+        enqueue_stage(h, j0, j1, next, h->stream);
+        cudaGraph_t body = nullptr;
+        if (more) {
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t cg = nullptr;
+            const cudaGraphNode_t *deps = nullptr;
+            const cudaGraphEdgeData *edges = nullptr;
+            size_t n_deps = 0;
+            e = cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &cg, &deps, &edges, &n_deps);
+            edges = nullptr;   // the IF node follows its predecessors with full serialisation
+            if (e == cudaSuccess) {
+                cudaGraphNodeParams np = {};
+                np.type = cudaGraphNodeTypeConditional;
+                np.conditional.handle = next;
+                np.conditional.type = cudaGraphCondTypeIf;
+                np.conditional.size = 1;
+                cudaGraphNode_t node;
+                e = cudaGraphAddNode(&node, cg, deps, edges, n_deps, &np);
+                if (e == cudaSuccess) {
+                    body = np.conditional.phGraph_out[0];
+                    e = cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+                }
+            }
+        }
+        cudaGraph_t g_end = nullptr;
+        const cudaError_t e_end = cudaStreamEndCapture(h->stream, &g_end);
+        if (e == cudaSuccess) e = e_end;
+        cur = body;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, top, 0);
+    cudaGraphDestroy(top);
+    CK(e);
+    return LSD_OK;
+}
+
 int ensure_graphs(lsd_handle *h) {
-    if (!h->g_window) TRY(build_graph(h, window_fn, &h->g_window));
+    if (!h->g_window) TRY(h->stage_len ? build_staged_graph(h, &h->g_window) : build_graph(h, window_fn, &h->g_window));
     if (!h->g_plain) TRY(build_graph(h, enqueue_plain, &h->g_plain));
     if (h->pipe_on)
         for (int b = 0; b < 2; ++b)
@@ -1191,6 +1270,7 @@ int lsd_get_stats(const lsd_handle *h, lsd_stats *out) {
     out->sum_delta = s.sum_delta;
     out->sum_pred_reject = s.sum_pred;
     out->step = s.step;
+    out->stages = s.stages;
     return LSD_OK;
 }
 
@@ -1268,6 +1348,7 @@ int lsd_set_state(lsd_handle *h, const double *pos, const double *mom, int64_t s
 int lsd_set_pipelining(lsd_handle *h, int32_t on) {
     if (!h) return LSD_EINVAL;
     if (on && h->ec_on) return LSD_ESTATE;   // the speculative draft would read the cache while it is rewritten
+    if (on && h->stage_len) return LSD_ESTATE;   // staged windows end on the device; a round drafts past them
     TRY(wait_stream(h));
     if (on && !h->pipe_alloc) {
         const size_t N = h->N, D = 3 * N, KN = (size_t)h->K * N, KD = (size_t)h->K * D;
@@ -1530,6 +1611,28 @@ int lsd_launch_counts(const lsd_handle *h, int32_t *per_window, int32_t *per_rou
     // verify; spec_base; speculative draft; redraft (with its flag kernel in list mode)
     if (per_round) *per_round = verify + 1 + draft + (lists ? 1 : 0) + draft;
     if (per_plain) *per_plain = use_plain_fused(h) ? 0 : verlet + 1 + eval + 1;
+    return LSD_OK;
+}
+
+int lsd_stage_launch_counts(const lsd_handle *h, int32_t *first, int32_t *later) {
+    if (!h) return LSD_EINVAL;
+    int32_t w = 0;
+    TRY(lsd_launch_counts(h, &w, nullptr, nullptr));
+    const bool lists = !h->vplan.all_pairs;
+    const bool one_cell = h->vplan.nc[0] < 3 || h->vplan.nc[1] < 3 || h->vplan.nc[2] < 3;
+    const int verlet = lists ? (one_cell ? 2 : 4) : 0;
+    if (first) *first = w;
+    if (later) *later = h->stage_len ? w - verlet : 0;   // a stage past the first rebuilds no lists
+    return LSD_OK;
+}
+
+int lsd_set_window_stages(lsd_handle *h, int32_t steps_per_stage) {
+    if (!h || steps_per_stage < 0) return LSD_EINVAL;
+    const int S = steps_per_stage < h->K ? steps_per_stage : 0;
+    if (S && h->pipe_on) return LSD_ESTATE;
+    TRY(wait_stream(h));
+    if (S != h->stage_len) destroy_graphs(h);
+    h->stage_len = S;
     return LSD_OK;
 }
 

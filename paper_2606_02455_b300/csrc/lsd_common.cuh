@@ -93,8 +93,9 @@ struct DevState {
     int k_eff;                   // window steps drafted (the draft stops early if an atom left the list's skin)
     int err;                     // bit flags: 1 neighbour overflow, 2 non-finite
     unsigned int blocks_done;    // last-block counter of the commit kernel
-    unsigned long long grid_arrive;   // arrivals at the transport's grid barrier (generations of nb*K)
+    unsigned grid_count, grid_gen;   // the transport's grid barrier: arrivals of this generation, generation
     long long windows, committed, rejected, verified;
+    long long stages;                // verification passes (one per window, or one per stage run)
     double sum_delta, sum_pred;
     // the pipelined loop's speculation policy (lsd_draft.cu; results do not depend on it): a running mean of
     // "the last committed window had no rejection", and whether the next round skips its speculative draft

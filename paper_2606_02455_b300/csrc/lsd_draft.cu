@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                                 const float *__restrict__ ec_dF, int ec_on, DevState *__restrict__ st,
                                 double *__restrict__ w_qmid, double *__restrict__ w_pdraft, float *__restrict__ w_Fd,
                                 float *__restrict__ w_Fraw, uint4 *__restrict__ w_fix, float *__restrict__ w_dEdX,
-                                WinHdr *__restrict__ hdr, int redraft, DraftSync *__restrict__ sync) {
+                                WinHdr *__restrict__ hdr, int redraft, DraftSync *__restrict__ sync, int j0) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N;
     const int C = gridDim.x, c = blockIdx.x;
@@ -428,8 +428,9 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
         if (REG && ii < nown && x < 3) {
             const int i = a0 + ii;
             const int sp = species[i];
-            qr[p] = q_base[3 * i + x];
-            pr[p] = p_base[3 * i + x];
+            // a launch that continues a window (j0 > 0) starts from the last drafted step's state
+            qr[p] = j0 == 0 ? q_base[3 * i + x] : w_qmid[(size_t)(j0 - 1) * D + 3 * i + x];
+            pr[p] = j0 == 0 ? p_base[3 * i + x] : w_pdraft[(size_t)(j0 - 1) * D + 3 * i + x];
             dfr[p] = ec_on ? ec_dF[3 * i + x] : 0.f;
             hmr[p] = cf.obabo ? species_pick(cf.hmf, sp) : species_pick(cf.hm, sp);
             sgr[p] = species_pick(cf.sig, sp);
@@ -440,10 +441,10 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     const int side = tid - (int)(blockDim.x - 32);
     // the noise of every step of the window, when it fits: off the per-step critical path
     if (noise_smem) {
-        for (int idx = tid; idx < K * nown; idx += blockDim.x) {
-            const int j = idx / nown, ii = idx - j * nown;
-            const float3 xi = normals3(cf.seed, (unsigned long long)(n0 + j + 1), (uint32_t)(a0 + ii), 0u);
-            float *o = snoise + ((size_t)j * A + ii) * 3;
+        for (int idx = tid; idx < (K - j0) * nown; idx += blockDim.x) {
+            const int jl = idx / nown, ii = idx - jl * nown;
+            const float3 xi = normals3(cf.seed, (unsigned long long)(n0 + j0 + jl + 1), (uint32_t)(a0 + ii), 0u);
+            float *o = snoise + ((size_t)jl * A + ii) * 3;
             o[0] = xi.x;
             o[1] = xi.y;
             o[2] = xi.z;
@@ -454,8 +455,9 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     __syncthreads();
     int keff = K;
     bool gave_up = false;   // this CTA's wait for a step's positions ran out of time
-    for (int j = 0; j < K; ++j) {
-        const int par = j & 1;
+    for (int j = j0; j < K; ++j) {
+        const int jl = j - j0;   // the launch's own step count: buffer parity, barrier phases, staged noise
+        const int par = jl & 1;
         const unsigned long long n = (unsigned long long)(n0 + j + 1);
         if (stage_fix && side == 31) tc::mbar_expect_tx(bar0 + 8 * par, step_bytes);
         // A: half-step positions, fixed point, broadcast, displacement from the list's base
@@ -493,7 +495,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                 // after the conversion the exchange waits for, so they queue behind it on the FP64 pipe
                 if (REG && noise_smem) {
                     c1p[p] = __dmul_rn(cf.c1, pv);
-                    sxi[p] = __dmul_rn(sgr[p], (double)snoise[((size_t)j * A + ii) * 3 + x]);
+                    sxi[p] = __dmul_rn(sgr[p], (double)snoise[((size_t)jl * A + ii) * 3 + x]);
                 }
             }
             const uint32_t ux = __shfl_sync(0xffffffffu, u, gl), uy = __shfl_sync(0xffffffffu, u, gl + 1),
@@ -567,7 +569,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
         // B: this step's positions and flags in this CTA; stop drafting when any
         // atom left the skin (the same flags in every CTA)
         if (stage_fix) {
-            const bool ok = tc::mbar_wait_cluster(bar0 + 8 * par, (uint32_t)((j >> 1) & 1));
+            const bool ok = tc::mbar_wait_cluster(bar0 + 8 * par, (uint32_t)((jl >> 1) & 1));
             const int f = (use_list && lane < C) ? sflag[par * kMaxCluster + lane] : 0;
             const int code = __syncthreads_or((ok ? 0 : 2) | (f ? 1 : 0));
             if (code) {
@@ -787,7 +789,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
             const float fr = x == 0 ? F.x : (x == 1 ? F.y : F.z);
             float xx = xreg;
             if (noise_smem) {
-                xx = snoise[((size_t)j * A + ii) * 3 + x];
+                xx = snoise[((size_t)jl * A + ii) * 3 + x];
             } else if (!REG) {
                 const float3 xi = normals3(cf.seed, n, (uint32_t)i, 0u);
                 xx = x == 0 ? xi.x : (x == 1 ? xi.y : xi.z);
@@ -925,7 +927,7 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
                          const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
                          const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
                          double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX,
-                         cudaStream_t s, WinHdr *hdr, int redraft, DraftSync *sync) {
+                         cudaStream_t s, WinHdr *hdr, int redraft, DraftSync *sync, int j0) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(pl.cluster, 1, 1);
     cfg.blockDim = dim3(kDraftThreads, 1, 1);
@@ -962,7 +964,7 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
     const Kern kern = kerns[(pl.grid ? 4 : 0) + (learned ? 2 : 0) + (pl.reg ? 1 : 0)];
     return cudaLaunchKernelEx(&cfg, kern, K, g, P, cf, vl, (const int *)vb.vcount, vp.cap, (const uint4 *)vb.fix_base,
                               vp.move2f, vp.rlist2f, stage, mi, ns, sl, self, sd, species, q, p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd,
-                              w_Fraw, w_fix, w_dEdX, hdr, redraft, sync);
+                              w_Fraw, w_fix, w_dEdX, hdr, redraft, sync, j0);
 }
 
 static const void *draft_kernel_ptrs[8] = {

@@ -32,7 +32,7 @@ inline void launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block, size
 void launch_fixpoint(const double *q, const int *species, int M, const Geo &g, uint4 *fix, cudaStream_t s);
 void launch_neigh_build(const uint4 *fix, int M, const Geo &g, float rmax2f, float near2f, int cap_near, int cap_far,
                         int *near_keys, int *far_keys, int *n_near, int *n_far, DevState *st, cudaStream_t s,
-                        const int *keff = nullptr);
+                        const int *keff = nullptr, int j_off = 0);
 // mom (may be null): [M][kMomFloats] moments of the rows; non-null selects the
 // moment form of the angular features and their adjoint (the same rows of
 // moments for both calls)
@@ -71,7 +71,7 @@ void launch_verlet_build(const VerletPlan &vp, const double *q, const int *speci
 cudaError_t verlet_setup(int max_smem);
 void launch_neigh_list(const uint4 *fix, const int *vlist, const int *vcount, int vcap, int M, const Geo &g,
                        float rmax2f, float near2f, int cap_near, int cap_far, int *near_keys, int *far_keys,
-                       int *n_near, int *n_far, DevState *st, const int *keff, cudaStream_t s);
+                       int *n_near, int *n_far, DevState *st, const int *keff, cudaStream_t s, int j_off = 0);
 
 // MLP (lsd_mlp.cu)
 void launch_mlp_fp32(const float *X, int M, const PotDev &P, float *E_mlp, float *dEdX, cudaStream_t s);
@@ -105,17 +105,24 @@ int mlp_tc_static_launch(const void *plan, const float *X, int M, const PotDev &
 int transport_atoms_per_block(int N);
 cudaError_t transport_setup();
 // keff: the window's drafted step count (the run state's, or the window
-// header's in a pipelined round).
+// header's in a pipelined round).  A window verified in stages: K is the end
+// of the stage (the decision covers steps 0 .. min(K, k_eff) - 1), j0 its first
+// step (steps before it were reduced by earlier stages), staged = 1 for every
+// stage but the last, and next the conditional handle of the next stage's
+// graph node, set when the window goes on (nothing is committed then).
 void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *species, const float *Fd,
-                             const float *Ft, DevState *st, double2 *partials, const int *keff, cudaStream_t s);
+                             const float *Ft, DevState *st, double2 *partials, const int *keff, cudaStream_t s,
+                             int j0 = 0);
 void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                              const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
                              int ec_on, double *q, double *p, double *p_obabo, DevState *st,
-                             const double2 *partials, const int *keff, cudaStream_t s);
+                             const double2 *partials, const int *keff, cudaStream_t s, int staged = 0,
+                             cudaGraphConditionalHandle next = 0);
 void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                       const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
                       int ec_on, double *q, double *p, double *p_obabo, DevState *st, double2 *partials,
-                      const int *keff, cudaStream_t s);
+                      const int *keff, cudaStream_t s, int j0 = 0, int staged = 0,
+                      cudaGraphConditionalHandle next = 0);
 
 // draft and plain integrator (lsd_draft.cu)
 // The grid-form draft's synchronisation words, zeroed before each launch.
@@ -149,7 +156,8 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
                          const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
                          const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
                          double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX,
-                         cudaStream_t s, WinHdr *hdr = nullptr, int redraft = 0, DraftSync *sync = nullptr);
+                         cudaStream_t s, WinHdr *hdr = nullptr, int redraft = 0, DraftSync *sync = nullptr,
+                         int j0 = 0);   // K: the last step + 1 of this launch; j0 > 0 continues a window from step j0
 // the fused plain-target step (lsd_plain.cu)
 constexpr int kPlainMaxN = 512;
 struct PlainPlan {

@@ -310,9 +310,10 @@ __global__ void adam_kernel(float *__restrict__ w, float *__restrict__ m, float 
 
 __global__ void frame_capture_kernel(const double *__restrict__ w_qmid, const float *__restrict__ w_Ft, int K, int N,
                                      long long cap, long long start_verified, const DevState *__restrict__ st,
-                                     const int *__restrict__ keff, double *__restrict__ fq, float *__restrict__ fF) {
+                                     const int *__restrict__ keff, double *__restrict__ fq, float *__restrict__ fF,
+                                     int j0) {
     if (st->step >= st->target_step) return;
-    const int j = blockIdx.y;
+    const int j = j0 + blockIdx.y;   // window steps j0 .. K - 1 (a window verified in stages: one stage's)
     if (j >= *keff) return;   // steps the draft did not reach carry no target label
     // frames are numbered by verified window steps (the commit kernel adds k_eff afterwards)
     const long long slot = (st->verified - start_verified + j) % cap;
@@ -450,13 +451,12 @@ int train_get_frames(TrainState &t, long long first, long long count, double *q,
 }
 
 void enqueue_frame_capture(TrainState &t, const double *w_qmid, const float *w_Ft, int K, int N, DevState *st,
-                           const int *keff, cudaStream_t s) {
-    t.K = K;
+                           const int *keff, cudaStream_t s, int j0) {
     t.st = st;
     const int D = 3 * N;
     const int bx = (D + 255) / 256 < 64 ? (D + 255) / 256 : 64;
-    frame_capture_kernel<<<dim3(bx, K), 256, 0, s>>>(w_qmid, w_Ft, K, N, t.capacity, t.start_verified, st, keff, t.fq,
-                                                     t.fF);
+    frame_capture_kernel<<<dim3(bx, K - j0), 256, 0, s>>>(w_qmid, w_Ft, K, N, t.capacity, t.start_verified, st, keff,
+                                                          t.fq, t.fF, j0);
 }
 
 // ---------------------------------------------------------------------------

@@ -43,7 +43,7 @@ int train_set_capture(TrainState &t, long long capacity, int N);
 int train_frame_count(TrainState &t, int64_t *n, cudaStream_t s);
 int train_get_frames(TrainState &t, long long first, long long count, double *q, float *F, cudaStream_t s);
 void enqueue_frame_capture(TrainState &t, const double *w_qmid, const float *w_Ft, int K, int N, DevState *st,
-                           const int *keff, cudaStream_t s);
+                           const int *keff, cudaStream_t s, int j0 = 0);   // window steps j0 .. K - 1
 size_t train_adam_size(const TrainState &t);
 int train_adam_get(TrainState &t, float *m, float *v);
 int train_adam_set(TrainState &t, const float *m, const float *v);

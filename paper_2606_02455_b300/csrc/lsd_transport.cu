@@ -113,6 +113,17 @@ __device__ void commit_decide(CommitShared &C, int K, const double2 *__restrict_
     __syncthreads();
 }
 
+// A window verified in stages (lsd_set_window_stages): after stage s the
+// window goes on to stage s + 1 (a conditional graph node, `next`) only when
+// every step so far was accepted, the draft reached the stage's end and the
+// stop step lies beyond it; then nothing is committed yet.  Otherwise the
+// window ends here with the commit an unstaged window would make: the first
+// rejection decides, and the steps past it are never verified.
+__device__ __forceinline__ bool stage_continues(const CommitShared &C, int Kw, int K, int staged, long long rem) {
+    return staged && !C.bad && !C.rej && Kw == K && (long long)Kw < rem;
+}
+__device__ __forceinline__ void stage_signal(cudaGraphConditionalHandle next) { cudaGraphSetConditional(next, 1u); }
+
 // Commits atoms [a0, a1): the draft's own bits for an accepted last step, the
 // reflection (Eq. 5) for a rejected one; the staggered OBABO frame keeps the
 // position and recovers the output momentum (App. E).
@@ -189,6 +200,7 @@ __device__ void commit_stats(CommitShared &C, int K, DevState *__restrict__ st, 
         if (C.bad) atomicOr(&st->err, 2);
         st->windows += 1;
         st->verified += K;
+        st->stages += 1;
         st->committed += nc;
         st->rejected += C.rej;
         st->sum_delta += sd;
@@ -208,7 +220,8 @@ __global__ void __launch_bounds__(kTransThreads)
                             const int *__restrict__ keff_p, int atoms_per_block, int fused,
                             const double *__restrict__ w_qmid, const double *__restrict__ w_pdraft,
                             const float *__restrict__ Fraw, float *__restrict__ ec_dF, int ec_on,
-                            double *__restrict__ q, double *__restrict__ p, double *__restrict__ p_obabo) {
+                            double *__restrict__ q, double *__restrict__ p, double *__restrict__ p_obabo, int j0,
+                            int staged, cudaGraphConditionalHandle next) {
     __shared__ double2 sh[32];
     __shared__ CommitShared C;
     __shared__ bool s_last;
@@ -216,7 +229,7 @@ __global__ void __launch_bounds__(kTransThreads)
     pdl_release();
     if (st->step >= st->target_step) return;   // uniform over the grid
     const int N = g.N;
-    const int j = blockIdx.y;
+    const int j = j0 + blockIdx.y;             // window steps j0 .. K - 1 (earlier stages reduced the others)
     const int keff = *keff_p;
     if (j < keff) {                            // steps the draft did not reach are skipped
         const unsigned long long n = (unsigned long long)(st->step + j + 1);
@@ -243,6 +256,14 @@ __global__ void __launch_bounds__(kTransThreads)
     const int Kw = min(K, keff);
     logu_fill(C, cf, n0, Kw);
     commit_decide(C, Kw, partials, gridDim.x, st->target_step - n0);
+    if (stage_continues(C, Kw, K, staged, st->target_step - n0)) {
+        if (threadIdx.x == 0) {
+            st->blocks_done = 0u;
+            st->stages += 1;
+            stage_signal(next);
+        }
+        return;
+    }
     commit_atoms(C, N, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, n0, 0, N);
     __syncthreads();
     if (threadIdx.x == 0) st->blocks_done = 0u;
@@ -250,24 +271,32 @@ __global__ void __launch_bounds__(kTransThreads)
 }
 
 // A barrier over the whole grid of a cooperative launch (every block resident):
-// each block's thread 0 arrives on a 64-bit counter and waits for the end of
-// its generation of `total` arrivals, giving up after about two seconds.
-__device__ bool grid_sync_bounded(unsigned long long *ctr, unsigned total) {
+// each block's thread 0 arrives on the barrier's counter; the last arrival
+// resets it and opens the next generation, for which the others wait (giving
+// up after about two seconds).  Any grid size, launch after launch: a window
+// verified in stages reduces a different number of steps per stage.
+__device__ bool grid_sync_bounded(unsigned *cnt, unsigned *gen, unsigned total) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
+        unsigned g0;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g0) : "l"(gen) : "memory");
         __threadfence();
-        const unsigned long long arrive = atomicAdd(ctr, 1ull);
-        const unsigned long long target = (arrive / total + 1ull) * total;
         int ok = 1;
-        const long long t0 = clock64();
-        for (;;) {
-            unsigned long long v;
-            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
-            if (v >= target) break;
-            if (clock64() - t0 > 4000000000ll) {
-                ok = 0;
-                break;
+        if (atomicAdd(cnt, 1u) == total - 1u) {
+            atomicExch(cnt, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            for (;;) {
+                unsigned v;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(gen) : "memory");
+                if (v != g0) break;
+                if (clock64() - t0 > 4000000000ll) {
+                    ok = 0;
+                    break;
+                }
             }
         }
         __threadfence();
@@ -288,7 +317,7 @@ __global__ void __launch_bounds__(kTransThreads)
                           const int *__restrict__ keff_p, int atoms_per_block, const double *__restrict__ w_qmid,
                           const double *__restrict__ w_pdraft, const float *__restrict__ Fraw,
                           float *__restrict__ ec_dF, int ec_on, double *__restrict__ q, double *__restrict__ p,
-                          double *__restrict__ p_obabo) {
+                          double *__restrict__ p_obabo, int j0, int staged, cudaGraphConditionalHandle next) {
     __shared__ double2 sh[32];
     __shared__ CommitShared C;
     // The run state and the draft's forces and noise come from kernels that
@@ -301,7 +330,7 @@ __global__ void __launch_bounds__(kTransThreads)
     const int keff = *(const volatile int *)keff_p;
     if (n0 >= tgt) return;   // uniform over the grid
     const int N = g.N;
-    const int j = blockIdx.y, nb = gridDim.x;
+    const int j = j0 + blockIdx.y, nb = gridDim.x;   // window steps j0 .. K - 1
     const int a0 = blockIdx.x * atoms_per_block, a1 = min(N, a0 + atoms_per_block);
     constexpr int kPer = 4;   // atoms per thread held across the wait (chunks of up to 1024 atoms)
     float3 xi[kPer], fd[kPer];
@@ -330,13 +359,20 @@ __global__ void __launch_bounds__(kTransThreads)
     }
     const double2 SD = block_sum2(s, d, sh);
     if (threadIdx.x == 0 && j < keff) partials[(size_t)j * nb + blockIdx.x] = SD;
-    if (!grid_sync_bounded(&st->grid_arrive, (unsigned)(nb * gridDim.y))) {
+    if (!grid_sync_bounded(&st->grid_count, &st->grid_gen, (unsigned)(nb * gridDim.y))) {
         if (threadIdx.x == 0) atomicOr(&st->err, 16);
         return;
     }
     const int Kw = min(K, keff);
     commit_decide(C, Kw, partials, nb, tgt - n0);
     const int nblk = nb * gridDim.y, blk = blockIdx.y * nb + blockIdx.x;
+    if (stage_continues(C, Kw, K, staged, tgt - n0)) {   // the same decision in every block
+        if (blk == 0 && threadIdx.x == 0) {
+            st->stages += 1;
+            stage_signal(next);
+        }
+        return;
+    }
     const int A = (N + nblk - 1) / nblk;
     commit_atoms(C, N, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, n0, blk * A,
                  min(N, blk * A + A));
@@ -350,16 +386,24 @@ __global__ void __launch_bounds__(kTransThreads)
                             int ec_on, double *__restrict__ q, double *__restrict__ p,
                             double *__restrict__ p_obabo, DevState *__restrict__ st,
                             const double2 *__restrict__ partials, const int *__restrict__ keff_p, int n_part,
-                            int atoms_per_block) {
+                            int atoms_per_block, int staged, cudaGraphConditionalHandle next) {
     __shared__ CommitShared C;
     __shared__ bool s_last;
     pdl_wait();
     pdl_release();
     if (st->step >= st->target_step) return;
+    const int Kstage = K;
     K = min(K, *keff_p);   // the window holds the k_eff steps the draft reached
     const long long n0 = st->step;
     logu_fill(C, cf, n0, K);
     commit_decide(C, K, partials, n_part, st->target_step - n0);
+    if (stage_continues(C, K, Kstage, staged, st->target_step - n0)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->stages += 1;
+            stage_signal(next);
+        }
+        return;
+    }
     const int a0 = blockIdx.x * atoms_per_block;
     commit_atoms(C, g.N, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, n0, a0,
                  min(g.N, a0 + atoms_per_block));
@@ -374,22 +418,25 @@ __global__ void __launch_bounds__(kTransThreads)
 }
 
 void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *species, const float *Fd,
-                             const float *Ft, DevState *st, double2 *partials, const int *keff, cudaStream_t s) {
+                             const float *Ft, DevState *st, double2 *partials, const int *keff, cudaStream_t s,
+                             int j0) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
-    launch_dependent(transport_reduce_kernel, dim3(nb, K), kTransThreads, 0, s, K, g, cf, species, Fd, Ft, st, partials,
-                     keff, apb, 0, (const double *)nullptr, (const double *)nullptr, (const float *)nullptr,
-                     (float *)nullptr, 0, (double *)nullptr, (double *)nullptr, (double *)nullptr);
+    launch_dependent(transport_reduce_kernel, dim3(nb, K - j0), kTransThreads, 0, s, K, g, cf, species, Fd, Ft, st,
+                     partials, keff, apb, 0, (const double *)nullptr, (const double *)nullptr, (const float *)nullptr,
+                     (float *)nullptr, 0, (double *)nullptr, (double *)nullptr, (double *)nullptr, j0, 0,
+                     (cudaGraphConditionalHandle)0);
 }
 
 void launch_transport_commit(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                              const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
                              int ec_on, double *q, double *p, double *p_obabo, DevState *st,
-                             const double2 *partials, const int *keff, cudaStream_t s) {
+                             const double2 *partials, const int *keff, cudaStream_t s, int staged,
+                             cudaGraphConditionalHandle next) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
     launch_dependent(transport_commit_kernel, nb, kTransThreads, 0, s, K, g, cf, species, w_qmid, w_pdraft, Fd, Ft,
-                     Fraw, ec_dF, ec_on, q, p, p_obabo, st, (const double2 *)partials, keff, nb, apb);
+                     Fraw, ec_dF, ec_on, q, p, p_obabo, st, (const double2 *)partials, keff, nb, apb, staged, next);
 }
 
 static int g_coop_blocks = -1;   // blocks of transport_coop_kernel the device keeps resident at once
@@ -408,12 +455,13 @@ cudaError_t transport_setup() {
 void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, const double *w_qmid,
                       const double *w_pdraft, const float *Fd, const float *Ft, const float *Fraw, float *ec_dF,
                       int ec_on, double *q, double *p, double *p_obabo, DevState *st, double2 *partials,
-                      const int *keff, cudaStream_t s) {
+                      const int *keff, cudaStream_t s, int j0, int staged, cudaGraphConditionalHandle next) {
     const int apb = transport_atoms_per_block(g.N);
     const int nb = (g.N + apb - 1) / apb;
-    if (apb <= 4 * kTransThreads && nb * K <= g_coop_blocks) {   // four atoms per thread at most
+    const int rows = K - j0;   // window steps reduced by this launch
+    if (apb <= 4 * kTransThreads && nb * rows <= g_coop_blocks) {   // four atoms per thread at most
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(nb, K);
+        cfg.gridDim = dim3(nb, rows);
         cfg.blockDim = dim3(kTransThreads);
         cfg.stream = s;
         cudaLaunchAttribute at[2];
@@ -424,17 +472,18 @@ void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, c
         cfg.attrs = at;
         cfg.numAttrs = 2;
         cudaLaunchKernelEx(&cfg, transport_coop_kernel, K, g, cf, species, Fd, Ft, st, partials, keff, apb, w_qmid,
-                           w_pdraft, Fraw, ec_dF, ec_on, q, p, p_obabo);
+                           w_pdraft, Fraw, ec_dF, ec_on, q, p, p_obabo, j0, staged, next);
         return;
     }
     if (nb == 1) {
-        launch_dependent(transport_reduce_kernel, dim3(1, K), kTransThreads, 0, s, K, g, cf, species, Fd, Ft, st,
-                         partials, keff, apb, 1, w_qmid, w_pdraft, Fraw, ec_dF, ec_on, q, p, p_obabo);
+        launch_dependent(transport_reduce_kernel, dim3(1, rows), kTransThreads, 0, s, K, g, cf, species, Fd, Ft, st,
+                         partials, keff, apb, 1, w_qmid, w_pdraft, Fraw, ec_dF, ec_on, q, p, p_obabo, j0, staged,
+                         next);
         return;
     }
-    launch_transport_reduce(K, g, cf, species, Fd, Ft, st, partials, keff, s);
+    launch_transport_reduce(K, g, cf, species, Fd, Ft, st, partials, keff, s, j0);
     launch_transport_commit(K, g, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, st,
-                            partials, keff, s);
+                            partials, keff, s, staged, next);
 }
 
 int transport_atoms_per_block(int N) {

@@ -39,7 +39,7 @@ __global__ void neigh_build_kernel(const uint4 *__restrict__ fix, const int *__r
                                    const int *__restrict__ vcount, int vcap, int M, Geo g, float rmax2f, float near2f,
                                    int cap_near, int cap_far, int *__restrict__ near_keys, int *__restrict__ far_keys,
                                    int *__restrict__ n_near, int *__restrict__ n_far, DevState *st,
-                                   const int *__restrict__ keff) {
+                                   const int *__restrict__ keff, int j_off) {
     pdl_wait();
     pdl_release();
     const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
@@ -47,7 +47,7 @@ __global__ void neigh_build_kernel(const uint4 *__restrict__ fix, const int *__r
     if (row >= M) return;
     const int N = g.N;
     const int j = row / N, i = row - j * N;
-    if (keff && j >= *keff) {
+    if (keff && j + j_off >= *keff) {   // j_off: the window step of row block 0 (a window verified in stages)
         if (lane == 0) {
             n_near[row] = 0;
             n_far[row] = 0;
@@ -483,22 +483,22 @@ static bool min_image_only(const Geo &g, float rmax2f) {
 
 void launch_neigh_build(const uint4 *fix, int M, const Geo &g, float rmax2f, float near2f, int cap_near, int cap_far,
                         int *near_keys, int *far_keys, int *n_near, int *n_far, DevState *st, cudaStream_t s,
-                        const int *keff) {
+                        const int *keff, int j_off) {
     const int threads = 256;
     const int blocks = (int)(((size_t)M * 32 + threads - 1) / threads);
     auto k = min_image_only(g, rmax2f) ? neigh_build_kernel<false, true> : neigh_build_kernel<false, false>;
     launch_dependent(k, blocks, threads, 0, s, fix, nullptr, nullptr, 0, M, g, rmax2f, near2f, cap_near, cap_far,
-                     near_keys, far_keys, n_near, n_far, st, keff);
+                     near_keys, far_keys, n_near, n_far, st, keff, j_off);
 }
 
 void launch_neigh_list(const uint4 *fix, const int *vlist, const int *vcount, int vcap, int M, const Geo &g,
                        float rmax2f, float near2f, int cap_near, int cap_far, int *near_keys, int *far_keys,
-                       int *n_near, int *n_far, DevState *st, const int *keff, cudaStream_t s) {
+                       int *n_near, int *n_far, DevState *st, const int *keff, cudaStream_t s, int j_off) {
     const int threads = 256;
     const int blocks = (int)(((size_t)M * 32 + threads - 1) / threads);
     auto k = min_image_only(g, rmax2f) ? neigh_build_kernel<true, true> : neigh_build_kernel<true, false>;
     launch_dependent(k, blocks, threads, 0, s, fix, vlist, vcount, vcap, M, g, rmax2f, near2f, cap_near, cap_far,
-                     near_keys, far_keys, n_near, n_far, st, keff);
+                     near_keys, far_keys, n_near, n_far, st, keff, j_off);
 }
 
 size_t desc_smem_bytes(int warps, int cap) { return (size_t)warps * kNbStageFloats * cap * sizeof(float); }

@@ -34,7 +34,8 @@ SYMBOLS = ["lsd_init", "lsd_draft_window", "lsd_verify_window", "lsd_step", "lsd
            "lsd_descriptors", "lsd_get_window", "lsd_profile_window", "lsd_checkpoint", "lsd_restore", "lsd_query",
            "lsd_target_mlp_static_dev", "lsd_destroy",
            "lsd_strerror", "lsd_launch_counts", "lsd_window_host", "lsd_transport_window", "lsd_get_frames",
-           "lsd_set_max_displacement", "lsd_set_plain_fused", "lsd_set_grid_draft", "lsd_set_angular_moments", "lsd_get_angular_moments", "lsd_set_online_training", "lsd_online_status"]
+           "lsd_set_max_displacement", "lsd_set_plain_fused", "lsd_set_grid_draft", "lsd_set_angular_moments", "lsd_get_angular_moments", "lsd_set_online_training", "lsd_online_status",
+           "lsd_set_window_stages", "lsd_stage_launch_counts"]
 
 
 class LSDError(RuntimeError):
@@ -61,7 +62,7 @@ class lsd_potential(ctypes.Structure):
 class lsd_stats(ctypes.Structure):
     _fields_ = [("windows", ctypes.c_int64), ("committed", ctypes.c_int64), ("rejected", ctypes.c_int64),
                 ("verified", ctypes.c_int64), ("sum_delta", ctypes.c_double), ("sum_pred_reject", ctypes.c_double),
-                ("step", ctypes.c_int64)]
+                ("step", ctypes.c_int64), ("stages", ctypes.c_int64)]
 
 
 _L = None
@@ -299,6 +300,10 @@ class LSD:
         """Overlap the draft of window w+1 with the verification of window w (lsd_set_pipelining)."""
         _check(_lib().lsd_set_pipelining(self.h, int(bool(on))), "lsd_set_pipelining")
 
+    def set_window_stages(self, steps_per_stage):
+        """Verify each window in stages of this many steps, stopping at the first rejection (0: one pass)."""
+        _check(_lib().lsd_set_window_stages(self.h, int(steps_per_stage)), "lsd_set_window_stages")
+
     SCHEMES = {"aboba": 0, "obabo": 1}
 
     def set_integrator(self, scheme):
@@ -410,6 +415,12 @@ class LSD:
                "lsd_launch_counts")
         return dict(window=w.value, round=r.value, plain=p.value)
 
+    def stage_launch_counts(self):
+        """Kernels of a staged window's first stage and of each later stage (lsd_stage_launch_counts)."""
+        f, l = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib().lsd_stage_launch_counts(self.h, ctypes.byref(f), ctypes.byref(l)), "lsd_stage_launch_counts")
+        return dict(first=f.value, later=l.value)
+
     def query(self):
         K, N, d, cap = (ctypes.c_int32() for _ in range(4))
         _check(_lib().lsd_query(self.h, ctypes.byref(K), ctypes.byref(N), ctypes.byref(d), ctypes.byref(cap)))
@@ -465,7 +476,7 @@ class LSD:
 
 def _stats_dict(st):
     return dict(windows=st.windows, committed=st.committed, rejected=st.rejected, verified=st.verified,
-                sum_delta=st.sum_delta, pred_rejected=st.sum_pred_reject, step=st.step)
+                sum_delta=st.sum_delta, pred_rejected=st.sum_pred_reject, step=st.step, stages=st.stages)
 
 
 def _make_target_energy():
