@@ -49,6 +49,10 @@ def _peaks():
 # target-verified frames of its own LSD run (`train_rounds` retrainings, one every `train_every` accepted steps),
 # then timed with the trained draft; online retraining stays on at the configuration's cadence where it has one.
 LEARNED_ONLINE = {4: 0, 5: 10000}   # configuration -> retraining cadence (accepted steps) during the timed run
+# configuration -> steps per verification stage of the timed windows (lsd_set_window_stages: the next stage runs
+# only while every step so far was accepted), from a sweep of S on a B300; the other configurations verify their
+# windows in one pass, pipelined
+WINDOW_STAGES = {4: 4, 5: 2}
 
 
 def _workload(cfg, pair_draft=False):
@@ -230,7 +234,7 @@ def _neighbours_per_atom(w, rc):
     return s.n_atoms / float(np.prod(s.box)) * 4.0 / 3.0 * np.pi * rc ** 3
 
 
-def _algorithmic_work(w, phase, q, moments=False):
+def _algorithmic_work(w, phase, q, moments=False, K=None):
     """Algorithmic work of one launch of a phase, with its bound: (amount, unit, bound, detail).
 
     mlp:   2 FLOP per multiply-add of the forward chain plus the input-gradient chain (no weight gradient):
@@ -243,7 +247,7 @@ def _algorithmic_work(w, phase, q, moments=False):
            nb (nb - 1) / 2 angular pairs x FLOP_ANG_* (pair sums) or nb x FLOP_MOM_*_NB + FLOP_MOM_*_ROW
            (moments), + nb x n_rbf x FLOP_RAD_* (+ LJ pairs for pair_grad).
     transport: bytes that must cross HBM once per window."""
-    s, t, K = w.system, w.target, w.integ.K
+    s, t, K = w.system, w.target, K or w.integ.K
     N = s.n_atoms
     M = K * N
     if phase == "mlp":
@@ -283,7 +287,7 @@ def _algorithmic_work(w, phase, q, moments=False):
     return None
 
 
-def _analysis(st1, st0, rl, K, t_plain_step):
+def _analysis(st1, st0, rl, K, t_plain_step, Kp=None):
     """The paper's bounds at the measured operating point (paper_2606_02455_b300.analysis): per-step rejection
     rate <beta> = rejections / tested steps (every committed step was tested, in order; steps after a window's
     first rejection are flushed untested), cost ratio c = drafted-step time / plain-step time, the pipelined
@@ -292,7 +296,7 @@ def _analysis(st1, st0, rl, K, t_plain_step):
     tested = max(st1["committed"] - st0["committed"], 1)
     beta = (st1["rejected"] - st0["rejected"]) / tested
     ph = rl["phases_ms"]
-    t_draft = ph["draft"] * 1e-3 / K
+    t_draft = ph["draft"] * 1e-3 / (Kp or K)   # the profiled window drafts Kp steps (a stage of a staged window)
     c = t_draft / t_plain_step
     return {"beta": round(beta, 5), "c": round(c, 5),
             "speedup_async_bound": round(float(A.speedup_async(beta, c)), 3),
@@ -300,7 +304,7 @@ def _analysis(st1, st0, rl, K, t_plain_step):
             "expected_committed_per_window": round(float(A.expected_committed(beta, K)), 3)}
 
 
-def roofline(h, w, peaks, peak_kind, q, n_rep=20):
+def roofline(h, w, peaks, peak_kind, q, n_rep=20, Kp=None):
     """Per-phase CUDA-event times of the window (live, on the library's stream), the dominant phase, and its
     achieved rate against the peak that bounds it."""
     phases = None
@@ -314,10 +318,11 @@ def roofline(h, w, peaks, peak_kind, q, n_rep=20):
     phases = acc
     dom = max(phases, key=lambda k: phases[k])
     share = phases[dom] / sum(phases.values())
-    work = _algorithmic_work(w, dom, q, h.angular_moments())
+    Kp = Kp or w.integ.K   # steps of the profiled window: K, or the stage length of staged windows
+    work = _algorithmic_work(w, dom, q, h.angular_moments(), K=Kp)
     sm_max = peaks.get("sm_max_mhz", 2032.0)
     fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s: 148 SMs x 128 FP32 lanes x FMA
-    out = {"kernel": dom, "share": round(share, 3), "ms": round(phases[dom], 5),
+    out = {"kernel": dom, "share": round(share, 3), "ms": round(phases[dom], 5), "window_steps_profiled": Kp,
            "phases_ms": {k: round(v, 5) for k, v in phases.items()}}
     if work is None:
         out.update({"bound": "alu", "achieved": None, "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": None,
@@ -333,7 +338,7 @@ def roofline(h, w, peaks, peak_kind, q, n_rep=20):
                     "frac": round(ach / fp32_peak, 5), "traffic": traffic,
                     "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz" % sm_max})
         if dom == "draft":
-            out["us_per_step"] = round(phases[dom] * 1e3 / w.integ.K, 3)
+            out["us_per_step"] = round(phases[dom] * 1e3 / Kp, 3)
             out["note"] = ("serial chain of K drafted steps (one cooperative grid with a barrier per step for systems of "
                            "2048 atoms or more, else one thread-block cluster of at most 16 SMs); latency-bound: the "
                            "per-step time, not FLOP/s, is the figure of merit")
@@ -378,10 +383,11 @@ def roofline(h, w, peaks, peak_kind, q, n_rep=20):
 L2_BYTES = 126 * 2 ** 20
 
 
-def _working_set_bytes(w):
+def _working_set_bytes(w, K=None):
     """Device bytes one window's verification touches (neighbour keys and pair gradients at ~2x the mean count,
-    descriptors and dE/dX, window arrays): decides whether L2 must be flushed between timed windows."""
-    s, t, K = w.system, w.target, w.integ.K
+    descriptors and dE/dX, window arrays) for K verified steps (a stage of a staged window; default the window's
+    K): decides whether L2 must be flushed between timed windows."""
+    s, t, K = w.system, w.target, K or w.integ.K
     N = s.n_atoms
     rc = max(t.desc_cutoff or 0.0, t.lj_cutoff or 0.0)
     nb = 2.0 * N / float(np.prod(s.box)) * 4.0 / 3.0 * np.pi * rc ** 3 + 32
@@ -398,18 +404,26 @@ def measure_workload(w, args, world, rank, full):
     s = w.system
     s.seed = replica_seed(s.seed, rank)   # independent replicas
     K = w.integ.K
+    cfg = getattr(w, "cfg", None)
+    S = args.stages if args.stages >= 0 else WINDOW_STAGES.get(cfg, 0)
+    S = S if S < K else 0
     h = lsd.LSD(s, w.draft, w.target, w.integ)
+
+    def set_mode(stages, pipe):
+        h.set_window_stages(0)   # pipelining and stages exclude each other
+        h.set_pipelining(pipe)
+        h.set_window_stages(stages)
     stream = torch.cuda.Stream()
     h.set_stream(stream)
     # equilibrate with plain target dynamics
     h.plain_step(args.equil)
     train = None
-    cfg = getattr(w, "cfg", None)
+    pipelined = not args.no_pipeline and S == 0
     if cfg in LEARNED_ONLINE and w.draft.n_layers:
         # the learned draft, trained online on the run's own frames (untimed set-up)
         t0 = time.perf_counter()
         a = h.stats()
-        h.set_pipelining(not args.no_pipeline)
+        set_mode(S, pipelined)
         h.set_frame_capture(args.train_frames)
         h.set_online_training(args.train_every, n_iters=args.train_iters, lr=3e-3, frames_per_iter=args.train_fpi)
         while h.online_status()[0] < args.train_rounds:
@@ -428,7 +442,7 @@ def measure_workload(w, args, world, rank, full):
                  "iters": args.train_iters, "frames": args.train_frames, "frames_per_iter": args.train_fpi,
                  "timed_run_cadence": cad or None}
     q_eq, p_eq, step_eq = h.get_state()
-    flush_needed = _working_set_bytes(w) < 4 * L2_BYTES
+    flush_needed = _working_set_bytes(w, S or K) < 4 * L2_BYTES
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda") if flush_needed else None
 
     def flush_l2():
@@ -436,8 +450,7 @@ def measure_workload(w, args, world, rank, full):
             with torch.cuda.stream(stream):
                 flush.add_(1.0)
 
-    pipelined = not args.no_pipeline
-    h.set_pipelining(pipelined)
+    set_mode(S, pipelined)
     for _ in range(args.warmup):
         h.step(K)
         h.plain_step(1)
@@ -473,13 +486,20 @@ def measure_workload(w, args, world, rank, full):
     if clocks:
         clocks.start()
     t_lsd, committed, rejected, windows, st0, st1 = timed_windows(args.steps)
-    value_unpipelined = None
+    value_unpipelined = value_one_pass = None
     if pipelined and full:
-        h.set_pipelining(False)
+        set_mode(0, False)
         h.step(K)
         t_u, c_u, _, _, _, _ = timed_windows(args.steps)
         value_unpipelined = whole_job_rate(c_u, t_u, world) * w.integ.dt * NS_PER_DAY
-        h.set_pipelining(True)
+        set_mode(0, True)
+    if S and full:
+        # the same windows verified in one pass (pipelined unless --no-pipeline), for comparison
+        set_mode(0, not args.no_pipeline)
+        h.step(K)
+        t_o, c_o, _, _, _, _ = timed_windows(args.steps)
+        value_one_pass = whole_job_rate(c_o, t_o, world) * w.integ.dt * NS_PER_DAY
+        set_mode(S, False)
     # plain target Langevin: the same number of steps as committed, back to back (one graph launch per step)
     h.set_state(q_eq, p_eq, step_eq)
     n_plain = max(committed, 32)
@@ -505,7 +525,7 @@ def measure_workload(w, args, world, rank, full):
         "plain_target_ns_per_day": round(plain_value, 4), "plain_ms_per_step": round(t_plain * 1e3 / n_plain, 5),
         "speedup_vs_plain": round(value / plain_value, 4),
         "l2": "flushed (256 MB write) before every timed window and once before the plain steps" if flush is not None
-        else "not flushed: the window's working set (%.2f GB) is larger than L2" % (_working_set_bytes(w) / 1e9),
+        else "not flushed: the window's working set (%.2f GB) is larger than L2" % (_working_set_bytes(w, S or K) / 1e9),
         "draft": _draft_label(w) + (" trained online before timing" if train else ""),
     }
     if train:
@@ -515,10 +535,11 @@ def measure_workload(w, args, world, rank, full):
         return out
     out.update({
         "t_lsd": t_lsd, "committed": committed, "windows": windows, "n_plain": n_plain, "st0": st0, "st1": st1,
-        "t_plain": t_plain, "pipelined": pipelined,
+        "t_plain": t_plain, "pipelined": pipelined, "window_stages": S or None,
         "value_unpipelined": None if value_unpipelined is None else round(value_unpipelined, 4),
+        "value_one_pass": None if value_one_pass is None else round(value_one_pass, 4),
         # the fused plain step (lc["plain"] == 0) is one launch for all n_plain steps
-        "gpu_launches": int(windows * (lc["round"] if pipelined else lc["window"]) +
+        "gpu_launches": int(_window_launches(h, lc, pipelined, S, windows, st0, st1) +
                             (1 if lc["plain"] == 0 else n_plain * lc["plain"])),
         "clocks": clk,
     })
@@ -544,9 +565,17 @@ def measure_workload(w, args, world, rank, full):
     out["e2e"] = {"value": round(whole_job_rate(e2e_committed, t_e2e, world) * w.integ.dt * NS_PER_DAY, 4),
                   "unit": "ns/day", "h2d_bytes_per_step": 2 * D * 8 + 16, "d2h_bytes_per_step": 2 * D * 8 + 32,
                   "calls": "lsd_window_host (pinned host state in and out)"}
-    out["roofline"] = roofline(h, w, _peaks()[0], _peaks()[1], pos)
+    out["roofline"] = roofline(h, w, _peaks()[0], _peaks()[1], pos, Kp=S or K)
     h.close()
     return out
+
+
+def _window_launches(h, lc, pipelined, S, windows, st0, st1):
+    """Kernels the timed windows launched: per round (pipelined), per window, or per stage run (staged)."""
+    if S:
+        sc = h.stage_launch_counts()
+        return windows * sc["first"] + (st1["stages"] - st0["stages"] - windows) * sc["later"]
+    return windows * (lc["round"] if pipelined else lc["window"])
 
 
 def run_ours(args):
@@ -588,12 +617,15 @@ def run_ours(args):
                    "draft": m["draft"], "parallelism": "replicas" if world > 1 else "single",
                    "l2": m["l2"]},
         "acceptance_rate": m["acceptance_rate"],
-        "analysis": _analysis(st1, st0, m["roofline"], K, m["t_plain"] / m["n_plain"]),
+        "analysis": _analysis(st1, st0, m["roofline"], K, m["t_plain"] / m["n_plain"],
+                              m["roofline"]["window_steps_profiled"]),
         "committed_per_window": m["committed_per_window"],
         "plain_target_ns_per_day": m["plain_target_ns_per_day"],
         "speedup_vs_plain": m["speedup_vs_plain"],
         "pipelined": m["pipelined"],
+        "window_stages": m["window_stages"],
         "value_unpipelined": m["value_unpipelined"],
+        "value_one_pass": m["value_one_pass"],
         "plain_ms_per_step": m["plain_ms_per_step"],
         "gpu_launches": m["gpu_launches"],
         "e2e": m["e2e"],
@@ -762,6 +794,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-pipeline", action="store_true", help="time the unpipelined window loop only")
     ap.add_argument("--pair-draft", action="store_true", help="the dense configurations with the bare LJ draft")
+    ap.add_argument("--stages", type=int, default=-1,
+                    help="steps per verification stage (0: one pass; default: per configuration, WINDOW_STAGES)")
     ap.add_argument("--train-rounds", type=int, default=3, help="online retrainings of the learned draft before timing")
     ap.add_argument("--train-every", type=int, default=200, help="accepted steps between retrainings before timing")
     ap.add_argument("--train-iters", type=int, default=40)

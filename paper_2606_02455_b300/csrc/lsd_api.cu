@@ -468,7 +468,7 @@ void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, f
 // else (pipelined loop) from the base (q, p) at step hdr->base, skipped when
 // hdr->skip is set.
 void enqueue_draft_buf(lsd_handle *h, int b, cudaStream_t s, WinHdr *hdr, const double *q, const double *p,
-                       bool redraft = false) {
+                       bool redraft = false, int Kd = 0) {   // Kd: steps to draft (0: the window's K)
     lsd_handle::WinBufs &w = h->wb[b];
     if (!h->vplan.all_pairs) {
         if (redraft) launch_redraft_flag(h->st, hdr, s);
@@ -477,7 +477,7 @@ void enqueue_draft_buf(lsd_handle *h, int b, cudaStream_t s, WinHdr *hdr, const 
     }
     // the speculative draft of the pipelined loop overlaps a verification: the cluster form, on a few SMs
     const bool grid = h->grid_draft && (!hdr || redraft);
-    launch_draft(grid ? h->gplan : h->dplan, h->learned_small, h->K, h->geo, h->draft.dev, h->coef, h->vplan, w.vb,
+    launch_draft(grid ? h->gplan : h->dplan, h->learned_small, Kd ? Kd : h->K, h->geo, h->draft.dev, h->coef, h->vplan, w.vb,
                  h->species, q, p, h->ec_dF, h->ec_on, h->st, w.qmid, w.pdraft, w.Fd, w.Fraw, w.fix, h->w_dEdX, s, hdr,
                  redraft ? 1 : 0, h->dsync);
 }
@@ -1529,16 +1529,25 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
     if (!h || !ms || n_phases < 0) return LSD_EINVAL;
     DevState s;
     TRY(read_state(h, &s));
-    TRY(set_target_step(h, s.step + h->K));
+    const int Kp = h->stage_len ? h->stage_len : h->K;   // staged windows: the launch shape of one stage
+    TRY(set_target_step(h, s.step + Kp));
     cudaEvent_t ev[LSD_N_PHASES + 1];
     for (int k = 0; k <= LSD_N_PHASES; ++k) CK(cudaEventCreate(&ev[k]));
     cudaStream_t st = h->stream;
-    const int M = h->K * h->N;
+    const int M = Kp * h->N;
     const PotDev &P = h->target.dev;
-    CK(cudaEventRecord(ev[0], st));
+    // events in time order: t[0] Verlet lists t[1] draft t[2] neighbours ... t[8] commit t[9]; phase k < 8 is
+    // t[k + 1] .. t[k + 2], the Verlet lists (phase 8) t[0] .. t[1]
+    cudaEvent_t *t = ev;
+    CK(cudaEventRecord(t[0], st));
     h->pipe_primed = false;
-    enqueue_draft(h, st);
-    CK(cudaEventRecord(ev[1], st));
+    lsd_handle::WinBufs &w0 = h->wb[0];
+    if (!h->vplan.all_pairs) launch_verlet_build(h->vplan, h->q, h->species, h->geo, w0.vb, h->st, st);
+    CK(cudaEventRecord(t[1], st));
+    launch_draft(h->grid_draft ? h->gplan : h->dplan, h->learned_small, Kp, h->geo, h->draft.dev, h->coef, h->vplan,
+                 w0.vb, h->species, h->q, h->p, h->ec_dF, h->ec_on, h->st, w0.qmid, w0.pdraft, w0.Fd, w0.Fraw, w0.fix,
+                 h->w_dEdX, st, nullptr, 0, h->dsync, 0);
+    CK(cudaEventRecord(t[2], st));
     if (h->vplan.all_pairs)
         launch_neigh_build(h->w_fix, M, h->geo, h->target.rmax2f, h->target.near2f, h->cap_near, h->cap_far,
                            h->near_keys, h->far_keys, h->n_near, h->n_far, h->st, st, &h->st->k_eff);
@@ -1546,28 +1555,31 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
         launch_neigh_list(h->w_fix, h->vbufs.vlist, h->vbufs.vcount, h->vplan.cap, M, h->geo, h->target.rmax2f,
                           h->target.near2f, h->cap_near, h->cap_far, h->near_keys, h->far_keys, h->n_near, h->n_far,
                           h->st, &h->st->k_eff, st);
-    CK(cudaEventRecord(ev[2], st));
+    CK(cudaEventRecord(t[3], st));
     if (P.has_mlp) launch_desc(h->w_fix, h->near_keys, h->n_near, h->cap_near, M, h->geo, P, h->X, st, mom_for(h, h->target));
-    CK(cudaEventRecord(ev[3], st));
+    CK(cudaEventRecord(t[4], st));
     if (P.has_mlp) enqueue_mlp(h, h->target, M, st);
-    CK(cudaEventRecord(ev[4], st));
+    CK(cudaEventRecord(t[5], st));
     launch_pairgrad(h->w_fix, h->near_keys, h->n_near, h->far_keys, h->n_far, h->cap_near, h->cap_far, M, h->geo, P,
                     h->dEdX, h->pair_g, h->Fpart, h->E_lj, st, mom_for(h, h->target));
-    CK(cudaEventRecord(ev[5], st));
+    CK(cudaEventRecord(t[6], st));
     launch_force_gather(h->near_keys, h->n_near, h->cap_near, M, h->N, P.has_mlp, h->pair_g, h->Fpart, h->E_lj,
                         h->E_mlp, h->w_Ft, nullptr, h->st, st);
-    CK(cudaEventRecord(ev[6], st));
-    launch_transport_reduce(h->K, h->geo, h->coef, h->species, h->w_Fd, h->w_Ft, h->st, h->partials, &h->st->k_eff, st);
-    CK(cudaEventRecord(ev[7], st));
-    launch_transport_commit(h->K, h->geo, h->coef, h->species, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Ft, h->w_Fraw,
+    CK(cudaEventRecord(t[7], st));
+    launch_transport_reduce(Kp, h->geo, h->coef, h->species, h->w_Fd, h->w_Ft, h->st, h->partials, &h->st->k_eff, st);
+    CK(cudaEventRecord(t[8], st));
+    launch_transport_commit(Kp, h->geo, h->coef, h->species, h->w_qmid, h->w_pdraft, h->w_Fd, h->w_Ft, h->w_Fraw,
                             h->ec_dF, h->ec_on, h->q, h->p, h->p_obabo, h->st, h->partials, &h->st->k_eff, st);
-    CK(cudaEventRecord(ev[8], st));
+    CK(cudaEventRecord(t[9], st));
     CK(cudaGetLastError());
     TRY(wait_stream(h));
     for (int k = 0; k < LSD_N_PHASES && k < n_phases; ++k) {
-        float t = 0.f;
-        CK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
-        ms[k] = t;
+        float e = 0.f;
+        if (k < 8)
+            CK(cudaEventElapsedTime(&e, t[k + 1], t[k + 2]));
+        else
+            CK(cudaEventElapsedTime(&e, t[0], t[1]));
+        ms[k] = e;
     }
     for (int k = 0; k <= LSD_N_PHASES; ++k) cudaEventDestroy(ev[k]);
     TRY(read_state(h, &s));

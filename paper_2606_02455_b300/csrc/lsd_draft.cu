@@ -42,7 +42,11 @@ namespace lsd {
 
 constexpr int kDraftThreads = 512;
 constexpr int kDraftWarps = kDraftThreads / 32;
-constexpr int kLearnCap = 96;      // staged descriptor neighbours per warp (learned draft)
+constexpr int kSegCap = 128;       // staged descriptor neighbours per species per warp (learned draft)
+constexpr int kLearnW = 32;        // the learned draft's hidden units (one layer, one unit per lane)
+// floats of one warp's learned-draft stage ([S][2][kSegCap] + the input vector) and of the CTA's weight copies
+__host__ __device__ inline int learned_stage_floats(int S, int d0p) { return 2 * S * kSegCap + d0p; }
+__host__ __device__ inline int learned_weight_floats(int d0p) { return 2 * kLearnW * d0p + kLearnW; }
 constexpr int kMaxCluster = 16;    // largest draft cluster
 
 __device__ __forceinline__ void cluster_barrier() {
@@ -123,15 +127,34 @@ __device__ __forceinline__ void for_images(const Geo &g, uint4 fi, uint4 fk, flo
             }
 }
 
+// The draft's cutoff function, fc = (1 + cos(pi r / rc)) / 2 and its
+// derivative, from r and 1/rc (the target's descriptors divide by rc).
+__device__ __forceinline__ void draft_cutoff(float r, float inv_rc, float &fc, float &dfc) {
+    float sn, cs;
+    sincospif(r * inv_rc, &sn, &cs);
+    fc = 0.5f * (cs + 1.0f);
+    dfc = (-0.5f * 3.14159265358979f) * inv_rc * sn;
+}
+
 // Learned draft, first phase: radial descriptors of atom i from its candidate
-// list (all atoms when cand is null), the MLP (BF16 operands, FP32 accumulation), dE/dx written to g_out[d0p].
-__device__ void learned_atom_grad(const PotDev &P, const Geo &g, const FixView &fx, int i, const ListView cand, int nc,
-                                  bool minimg, float *stage, float *xbuf, float *g_out) {
+// list (all atoms when cand is null), the MLP (BF16 operands, FP32
+// accumulation), dE/dx written to g_out[d0p].  The warp's stage holds, per
+// species s, the (r, fc) of the atom's neighbours of species s in list order
+// ([S][2][kSegCap]), so the basis sums run over one species at a time; xbuf
+// holds the BF16-rounded input vector.  wf / wtf / wo: FP32 copies of the BF16
+// first layer ([W][d0p] and [d0p][W], W = 32 hidden units, one per lane) and
+// output weights, staged once per launch.  Returns false when some species
+// had more than kSegCap neighbours (its sum is then truncated).
+__device__ bool learned_atom_grad(const PotDev &P, const Geo &g, const FixView &fx, int i, const ListView cand, int nc,
+                                  bool minimg, float inv_rc, float *stage, float *xbuf, const float *wf,
+                                  const float *wtf, const float *wo, float *g_out) {
     const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const uint4 fi = fx[i];
-    float *sr = stage, *sfc = stage + kLearnCap;
-    int *ssp = (int *)(stage + 2 * kLearnCap);
-    int cnt = 0;
+    const int S = g.S;
+    int cnt[kMaxSpecies];
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s) cnt[s] = 0;
     // candidates four per lane in flight: their list entries and positions are loaded before any is tested
     constexpr int kB = 4;
     for (int base0 = 0; base0 < nc; base0 += 32 * kB) {
@@ -147,90 +170,114 @@ __device__ void learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
 #pragma unroll
         for (int u = 0; u < kB; ++u) {
             if (base0 + 32 * u >= nc) break;   // uniform over the warp
-            // the (at most 8) images of k within the descriptor cutoff, in enumeration order
-            float rs[8];
-            int nm = 0, sk = 0;
             const int k = kq[u];
-            if (k != i) {
-                const uint4 fk = fq[u];
-                sk = (int)fk.w;
-                for_images(g, fi, fk, P.desc_rc2f, minimg, [&](float, float, float, float d2) {
-                    if (d2 < P.desc_rc2f && nm < 8) rs[nm++] = sqrtf(d2);
-                });
-            }
-            int sc = nm;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, sc, o);
-                if (lane >= o) sc += v;
-            }
-            const int tot = __shfl_sync(0xffffffffu, sc, 31);
-            int w = cnt + sc - nm;
-            for (int c = 0; c < nm; ++c) {
-                if (w < kLearnCap) {
-                    const float r = rs[c];
-                    float fc, dfc;
-                    cutoff_fn(r, P.desc_rc, fc, dfc);
-                    sr[w] = r;
-                    sfc[w] = fc;
-                    ssp[w] = sk;
+            const uint4 fk = fq[u];
+            const int sk = (int)fk.w;
+            if (minimg) {
+                // at most one image within the cutoff: each species' neighbours placed by one ballot
+                bool in = false;
+                float r = 0.f, fc = 0.f;
+                if (k != i) {
+                    float dx, dy, dz;
+                    int kk;
+                    axis_min(fi.x, fk.x, g.scale_f[0], dx, kk);
+                    axis_min(fi.y, fk.y, g.scale_f[1], dy, kk);
+                    axis_min(fi.z, fk.z, g.scale_f[2], dz, kk);
+                    const float d2 = dist2_rule(dx, dy, dz);
+                    in = d2 < P.desc_rc2f;
+                    if (in) {
+                        float dfc;
+                        r = d2 * rsqrtf(d2);
+                        draft_cutoff(r, inv_rc, fc, dfc);
+                    }
                 }
-                ++w;
+#pragma unroll
+                for (int s = 0; s < kMaxSpecies; ++s) {
+                    if (s >= S) break;
+                    const bool mine = in && sk == s;
+                    const unsigned m = __ballot_sync(0xffffffffu, mine);
+                    const int w = cnt[s] + __popc(m & lt);
+                    if (mine && w < kSegCap) {
+                        stage[(2 * s) * kSegCap + w] = r;
+                        stage[(2 * s + 1) * kSegCap + w] = fc;
+                    }
+                    cnt[s] += __popc(m);
+                }
+            } else {
+                // the (at most 8) images of k within the descriptor cutoff, in enumeration order
+                float rs[8];
+                int nm = 0;
+                if (k != i)
+                    for_images(g, fi, fk, P.desc_rc2f, false, [&](float, float, float, float d2) {
+                        if (d2 < P.desc_rc2f && nm < 8) rs[nm++] = d2 * rsqrtf(d2);
+                    });
+#pragma unroll
+                for (int s = 0; s < kMaxSpecies; ++s) {
+                    if (s >= S) break;
+                    const int mine = (k != i && sk == s) ? nm : 0;
+                    int sc = mine;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, sc, o);
+                        if (lane >= o) sc += v;
+                    }
+                    int w = cnt[s] + sc - mine;
+                    for (int c = 0; c < mine; ++c, ++w)
+                        if (w < kSegCap) {
+                            float fc, dfc;
+                            draft_cutoff(rs[c], inv_rc, fc, dfc);
+                            stage[(2 * s) * kSegCap + w] = rs[c];
+                            stage[(2 * s + 1) * kSegCap + w] = fc;
+                        }
+                    cnt[s] += __shfl_sync(0xffffffffu, sc, 31);
+                }
             }
-            cnt += tot;
         }
     }
-    __syncwarp();
-    const int n = cnt < kLearnCap ? cnt : kLearnCap;
     const int nr = P.n_rbf;
+    for (int f = lane; f < P.d0p; f += 32) xbuf[f] = 0.f;
+    __syncwarp();
+    bool ok = true;
     {
-        float acc[kMaxSpecies];
-#pragma unroll
-        for (int s = 0; s < kMaxSpecies; ++s) acc[s] = 0.f;
-        // lanes over basis functions (8 or 16 wide), the groups of lanes over neighbours, then a reduction over
-        // the groups: every lane busy for n_rbf <= 8 as for 16
+        // lanes over basis functions (8 or 16 wide), the groups of lanes over one species' neighbours, then a
+        // reduction over the groups: every lane busy for n_rbf <= 8 as for 16
         const int nb = nr <= 8 ? 8 : 16;
         const int kb = lane & (nb - 1), ng = 32 / nb;
-        if (kb < nr) {
-            const float mu = (float)kb * P.rbf_w;
-            for (int p = lane / nb; p < n; p += ng) {
-                const float t = sr[p] - mu;
-                const float v = __expf(-t * t * P.rbf_inv2w2) * sfc[p];   // the hardware exponential, as the target's basis
+        const float mu = (float)kb * P.rbf_w;
 #pragma unroll
-                for (int s = 0; s < kMaxSpecies; ++s) acc[s] += (ssp[p] == s) ? v : 0.f;
-            }
+        for (int s = 0; s < kMaxSpecies; ++s) {
+            if (s >= S) break;
+            ok = ok && cnt[s] <= kSegCap;
+            const int n = cnt[s] < kSegCap ? cnt[s] : kSegCap;
+            const float *sr = stage + (2 * s) * kSegCap, *sfc = sr + kSegCap;
+            float acc = 0.f;
+            if (kb < nr)
+                for (int p = lane / nb; p < n; p += ng) {
+                    const float t = sr[p] - mu;
+                    acc += __expf(-t * t * P.rbf_inv2w2) * sfc[p];   // the hardware exponential, as the target's basis
+                }
+            for (int o = 16; o >= nb; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            if (lane < nr) xbuf[s * nr + lane] = __bfloat162float(__float2bfloat16(acc));
         }
-        for (int o = 16; o >= nb; o >>= 1)
-#pragma unroll
-            for (int s = 0; s < kMaxSpecies; ++s) acc[s] += __shfl_down_sync(0xffffffffu, acc[s], o);
-        for (int f = lane; f < P.d0p; f += 32) xbuf[f] = 0.f;
-        __syncwarp();
-        if (lane < nr)
-            for (int s = 0; s < g.S; ++s) xbuf[s * nr + lane] = acc[s];
-        if (lane == 0) xbuf[g.S * nr + P.n_ang + (int)fi.w] = 1.f;
+        if (lane == 0) xbuf[S * nr + P.n_ang + (int)fi.w] = 1.f;
     }
     __syncwarp();
-    const int W = P.width;
-    float gh = 0.f;
-    if (lane < W) {
-        float h = P.b[0][lane];
-        const __nv_bfloat16 *w1 = P.Wn_bf[0] + (size_t)lane * P.d0p;
-        for (int f = 0; f < P.d0; ++f)
-            h = fmaf(__bfloat162float(w1[f]), __bfloat162float(__float2bfloat16(xbuf[f])), h);
-        gh = __bfloat162float(P.wout_bf[lane]) * dsiluf_(h);   // linear head: dE/dy = 1
-    }
-    __syncwarp();
+    // one hidden unit per lane (W = 32): h = b + W x, dE/dh = w_out SiLU'(h) (linear head: dE/dy = 1)
+    float h = P.b[0][lane];
+    for (int f = 0; f < P.d0; ++f) h = fmaf(wtf[f * kLearnW + lane], xbuf[f], h);
+    const float gh = wo[lane] * dsiluf_(h);
     // dE/dx_f = sum_u W[u][f] gh_u: lane f over the hidden units, gh_u handed round by shuffles
     for (int f0 = 0; f0 < P.d0p; f0 += 32) {
         const int f = f0 + lane;
         float v = 0.f;
-        for (int u = 0; u < W; ++u) {
+        for (int u = 0; u < kLearnW; ++u) {
             const float gu = __shfl_sync(0xffffffffu, gh, u);
-            if (f < P.d0) v = fmaf(__bfloat162float(P.Wn_bf[0][(size_t)u * P.d0p + f]), gu, v);
+            if (f < P.d0) v = fmaf(wf[u * P.d0p + f], gu, v);
         }
         if (f < P.d0p) g_out[f] = v;
     }
     __syncwarp();
+    return ok;
 }
 
 // Store v at the same shared-memory offset as `local` in CTA `rank` of the cluster.
@@ -302,8 +349,12 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     float4 *sF = (float4 *)smraw;                               // [A]
     uint4 *sbase = (uint4 *)(sF + A);                           // [A] list base positions of owned atoms (lists)
     float *slj = (float *)(sbase + (use_list ? A : 0));         // sig2, eps24 tables
-    float *sstage = slj + 2 * kMaxSpecies * kMaxSpecies;        // learned: per warp 3*cap + d0p
-    uint4 *sfix = (uint4 *)(sstage + (LEARNED ? (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) : 0));  // [2][N]
+    float *sstage = slj + 2 * kMaxSpecies * kMaxSpecies;        // learned: per warp [S][2][kSegCap] + d0p
+    const int stage_stride = learned_stage_floats(g.S, P.d0p);
+    float *swf = sstage + (LEARNED ? (size_t)kDraftWarps * stage_stride : 0);   // learned: W1 [W][d0p], FP32
+    float *swtf = swf + kLearnW * P.d0p;                                         //          W1^T [d0p][W]
+    float *swo = swtf + kLearnW * P.d0p;                                         //          w_out [W]
+    uint4 *sfix = (uint4 *)(swf + (LEARNED ? learned_weight_floats(P.d0p) : 0));  // [2][N]
     // displacement flags: [2] (cluster-barrier exchange) or [2][kMaxCluster], one slot per sending CTA
     int *sflag = (int *)(sfix + (stage_fix ? 2 * (size_t)N : 0));
     // [3] mbarriers: the two exchange barriers (staged positions, by step parity) and the exit barrier of a
@@ -343,6 +394,15 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     for (int t = tid; t < g.S * g.S; t += blockDim.x) {
         slj[t] = P.lj_sig2[t];
         slj[kMaxSpecies * kMaxSpecies + t] = P.lj_eps24[t];
+    }
+    // the learned draft's single hidden layer, read by every atom of every step: FP32 copies of its BF16 values
+    const float inv_rc = LEARNED ? 1.f / P.desc_rc : 0.f;
+    if (LEARNED) {
+        for (int t = tid; t < kLearnW * P.d0p; t += blockDim.x) {
+            swf[t] = __bfloat162float(P.Wn_bf[0][t]);
+            swtf[t] = __bfloat162float(P.Wt_bf[0][t]);
+        }
+        if (tid < kLearnW) swo[tid] = __bfloat162float(P.wout_bf[tid]);
     }
     if (tid < 2 * kMaxCluster) sflag[tid] = 0;
     const uint32_t bar0 = tc::smem_u32(sbar);
@@ -598,15 +658,18 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
         }
         FixView fx{stage_fix ? sfix + (size_t)par * N : nullptr, w_fix + (size_t)j * N};
         if (LEARNED) {
-            float *stage = sstage + (size_t)warp * (3 * kLearnCap + P.d0p);
+            float *stage = sstage + (size_t)warp * stage_stride;
+            bool all_in = true;
             for (int ii = warp; ii < nown; ii += kDraftWarps) {
                 const int i = a0 + ii;
                 const ListView cand{use_list ? (stage_list ? svl + (size_t)ii * vcap : vlist + (size_t)i * vcap)
                                              : nullptr,
                                     stage_list != 0};
-                learned_atom_grad(P, g, fx, i, cand, use_list ? (stage_list ? svc[ii] : vcount[i]) : N,
-                                  minimg != 0, stage, stage + 3 * kLearnCap, w_dEdX + (size_t)i * P.d0p);
+                all_in &= learned_atom_grad(P, g, fx, i, cand, use_list ? (stage_list ? svc[ii] : vcount[i]) : N,
+                                            minimg != 0, inv_rc, stage, stage + 2 * g.S * kSegCap, swf, swtf, swo,
+                                            w_dEdX + (size_t)i * P.d0p);
             }
+            if (!all_in && lane == 0) atomicOr(&st->err, 1);   // a species' staged neighbours overflowed
             // dE/dx of every atom visible to every CTA
             if (GRID) {
                 if (!draft_grid_barrier(sync, (unsigned)C)) {
@@ -702,8 +765,10 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                     const int pr2 = si * g.S + (int)fk.w;
                     const float sig2 = slj[pr2], eps24 = slj[kMaxSpecies * kMaxSpecies + pr2];
                     for_images(g, fi, fk, rc2_all, minimg != 0, [&](float dx, float dy, float dz, float d2) {
+                        // the learned draft: 1/r once per pair (its cutoff spans the LJ one)
+                        const float ir = LEARNED ? rsqrtf(d2) : 0.f;
                         if (P.has_lj && d2 < P.lj_rc2f) {
-                            const float inv = 1.f / d2;
+                            const float inv = LEARNED ? ir * ir : 1.f / d2;
                             const float s2 = sig2 * inv;
                             const float s6 = s2 * s2 * s2, s12 = s6 * s6;
                             const float fr = -eps24 * (2.f * s12 - s6) * inv;
@@ -713,9 +778,9 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                         }
                         if (LEARNED && d2 < P.desc_rc2f) {
                             // radial adjoint in gather form: (c_ik + c_ki) d/r
-                            const float r = sqrtf(d2);
+                            const float r = d2 * ir;
                             float fc, dfc;
-                            cutoff_fn(r, P.desc_rc, fc, dfc);
+                            draft_cutoff(r, inv_rc, fc, dfc);
                             float cc = 0.f;
                             if (stage_dedx) {
                                 const int SR = g.S * P.n_rbf;
@@ -732,7 +797,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                                                                                     (int)fk.w * P.n_rbf);
                                 const float4 *gk = reinterpret_cast<const float4 *>(w_dEdX + (size_t)k * P.d0p +
                                                                                     si * P.n_rbf);
-                                for (int b4 = 0; b4 < P.n_rbf / 4; ++b4) {
+                                auto block4 = [&](int b4) {
                                     const float4 a = __ldcg(gi + b4), c = __ldcg(gk + b4);
                                     const float gs[4] = {a.x + c.x, a.y + c.y, a.z + c.z, a.w + c.w};
 #pragma unroll
@@ -741,6 +806,12 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                                         const float dg = __expf(-tt * tt * P.rbf_inv2w2) * (-tt * P.rbf_invw2 * fc + dfc);
                                         cc += gs[e] * dg;
                                     }
+                                };
+                                if (P.n_rbf == 8) {   // the usual basis: both blocks' loads issued together
+                                    block4(0);
+                                    block4(1);
+                                } else {
+                                    for (int b4 = 0; b4 < P.n_rbf / 4; ++b4) block4(b4);
                                 }
                             } else {
                                 const float *gi = w_dEdX + (size_t)i * P.d0p + (int)fk.w * P.n_rbf;
@@ -751,9 +822,10 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                                     cc += (__ldcg(gi + b) + __ldcg(gk + b)) * dg;
                                 }
                             }
-                            fxx += cc * dx / r;
-                            fyy += cc * dy / r;
-                            fzz += cc * dz / r;
+                            const float cr = cc * ir;
+                            fxx += cr * dx;
+                            fyy += cr * dy;
+                            fzz += cr * dz;
                         }
                     });
                 }
@@ -857,7 +929,10 @@ static size_t draft_smem_bytes(int N, int C, const PotDev &P, bool learned, bool
     if (vcap > 0) b += (size_t)A * sizeof(uint4);
     b += (size_t)A * sizeof(int);
     if (stage_list) b += (size_t)A * (vcap + 1) * sizeof(int);
-    if (learned) b += (size_t)kDraftWarps * (3 * kLearnCap + P.d0p) * sizeof(float);
+    if (learned) {
+        const int S = P.n_rbf > 0 ? (P.d0 - P.n_ang) / (P.n_rbf + 1) : 0;   // input = S n_rbf radial + one-hot S
+        b += ((size_t)kDraftWarps * learned_stage_floats(S, P.d0p) + learned_weight_floats(P.d0p)) * sizeof(float);
+    }
     if (stage_fix) b += 2 * (size_t)N * sizeof(uint4);
     return b + 2 * kMaxCluster * sizeof(int) + 3 * sizeof(uint64_t) + (size_t)noise_K * A * 3 * sizeof(float) +
            dedx_floats * sizeof(float);

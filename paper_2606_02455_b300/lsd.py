@@ -454,7 +454,7 @@ class LSD:
         return out
 
     PHASES = ("draft", "neighbors", "descriptors", "mlp", "pair_grad", "force_gather", "transport_reduce",
-              "transport_commit")
+              "transport_commit", "verlet_lists")
 
     def profile_window(self):
         """One window with CUDA events between its kernels: {phase: milliseconds}."""

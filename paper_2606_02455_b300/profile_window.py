@@ -1,12 +1,14 @@
 """Runs LSD windows of a benchmark configuration, for profilers (ncu) and quick timing.
 
     python -m paper_2606_02455_b300.profile_window --config 4 [--K 32] [--windows 2] [--equil 0] [--pipelined]
-                                                   [--plain 0]
+                                                   [--plain 0] [--learned] [--stages S]
 
 Builds one handle for the configuration (window length K overridable, to keep a profiled footprint small),
 optionally runs `equil` plain target steps, then `windows` windows through lsd_enqueue_windows on the handle's
 stream, prints the per-phase CUDA-event times of one more window (lsd_profile_window) and the run's counters, and
-then runs `plain` plain target steps in one call.
+then runs `plain` plain target steps in one call.  --learned drafts with the learned draft (LJ + MLP on radial
+basis functions, untrained weights: the kernels' cost does not depend on them); --stages S verifies the windows in
+stages of S steps (lsd_set_window_stages; the profiled window is then one stage long).
 The first kernels a handle launches are its set-up (the FP8 and FP32-split calibration runs the MLP once on N
 rows); window kernels follow.
 """
@@ -26,12 +28,16 @@ def main() -> None:
     ap.add_argument("--equil", type=int, default=0)
     ap.add_argument("--pipelined", action="store_true")
     ap.add_argument("--plain", type=int, default=0, help="plain target steps after the windows (one call)")
+    ap.add_argument("--learned", action="store_true", help="the learned draft instead of the configuration's")
+    ap.add_argument("--stages", type=int, default=0, help="steps per verification stage (0: one pass)")
     a = ap.parse_args()
     w = W.CONFIGS[a.config](a.K) if a.K else W.CONFIGS[a.config]()
-    h = lsd.LSD(w.system, w.draft, w.target, w.integ)
+    draft = W.learned_draft(w.target, w.system.n_species) if a.learned else w.draft
+    h = lsd.LSD(w.system, draft, w.target, w.integ)
     if a.equil:
         h.plain_step(a.equil)
     h.set_pipelining(a.pipelined)
+    h.set_window_stages(a.stages)
     h.enqueue_windows(a.windows)
     st = h.stats()
     ph = h.profile_window()

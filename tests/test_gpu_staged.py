@@ -150,3 +150,17 @@ def test_stages_and_pipelining_are_exclusive():
         h.set_window_stages(4)
     h.set_window_stages(16)   # S >= K: one pass, allowed
     h.close()
+
+
+def test_profile_window_follows_the_stage_length():
+    """lsd_profile_window of a staged handle profiles one stage-length window: at most S steps verified, every
+    phase timed, the Verlet lists as their own phase."""
+    from paper_2606_02455_b300 import lsd
+    w = W.config4()
+    h = _handle(w, stages=8)
+    a = h.stats()
+    ph = h.profile_window()
+    b = h.stats()
+    h.close()
+    assert tuple(ph) == lsd.LSD.PHASES and all(v >= 0.0 for v in ph.values()) and ph["verlet_lists"] > 0.0
+    assert b["windows"] - a["windows"] == 1 and 1 <= b["verified"] - a["verified"] <= 8
