@@ -409,10 +409,14 @@ def measure_workload(w, args, world, rank, full):
     S = S if S < K else 0
     h = lsd.LSD(s, w.draft, w.target, w.integ)
 
-    def set_mode(stages, pipe):
-        h.set_window_stages(0)   # pipelining and stages exclude each other
+    reuse = bool(S) and not args.no_list_reuse   # staged windows keep their Verlet lists while they stay valid
+
+    def set_mode(stages, pipe, keep=False):
+        h.set_window_stages(0)   # pipelining excludes stages and kept lists
+        h.set_list_reuse(False)
         h.set_pipelining(pipe)
         h.set_window_stages(stages)
+        h.set_list_reuse(keep)
     stream = torch.cuda.Stream()
     h.set_stream(stream)
     # equilibrate with plain target dynamics
@@ -423,7 +427,7 @@ def measure_workload(w, args, world, rank, full):
         # the learned draft, trained online on the run's own frames (untimed set-up)
         t0 = time.perf_counter()
         a = h.stats()
-        set_mode(S, pipelined)
+        set_mode(S, pipelined, reuse)
         h.set_frame_capture(args.train_frames)
         h.set_online_training(args.train_every, n_iters=args.train_iters, lr=3e-3, frames_per_iter=args.train_fpi)
         while h.online_status()[0] < args.train_rounds:
@@ -450,7 +454,7 @@ def measure_workload(w, args, world, rank, full):
             with torch.cuda.stream(stream):
                 flush.add_(1.0)
 
-    set_mode(S, pipelined)
+    set_mode(S, pipelined, reuse)
     for _ in range(args.warmup):
         h.step(K)
         h.plain_step(1)
@@ -499,7 +503,7 @@ def measure_workload(w, args, world, rank, full):
         h.step(K)
         t_o, c_o, _, _, _, _ = timed_windows(args.steps)
         value_one_pass = whole_job_rate(c_o, t_o, world) * w.integ.dt * NS_PER_DAY
-        set_mode(S, False)
+        set_mode(S, False, reuse)
     # plain target Langevin: the same number of steps as committed, back to back (one graph launch per step)
     h.set_state(q_eq, p_eq, step_eq)
     n_plain = max(committed, 32)
@@ -522,6 +526,8 @@ def measure_workload(w, args, world, rank, full):
         "workload": w.name, "value": round(value, 4), "ms_per_window": round(t_lsd * 1e3 / args.steps, 5),
         "acceptance_rate": round(1.0 - rejected / max(committed, 1), 5),
         "committed_per_window": round(committed / max(windows, 1), 3),
+        "list_builds_per_window": (round((st1["list_builds"] - st0["list_builds"]) / max(windows, 1), 3)
+                                   if reuse else None),
         "plain_target_ns_per_day": round(plain_value, 4), "plain_ms_per_step": round(t_plain * 1e3 / n_plain, 5),
         "speedup_vs_plain": round(value / plain_value, 4),
         "l2": "flushed (256 MB write) before every timed window and once before the plain steps" if flush is not None
@@ -624,6 +630,7 @@ def run_ours(args):
         "speedup_vs_plain": m["speedup_vs_plain"],
         "pipelined": m["pipelined"],
         "window_stages": m["window_stages"],
+        "list_builds_per_window": m["list_builds_per_window"],
         "value_unpipelined": m["value_unpipelined"],
         "value_one_pass": m["value_one_pass"],
         "plain_ms_per_step": m["plain_ms_per_step"],
@@ -794,9 +801,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-pipeline", action="store_true", help="time the unpipelined window loop only")
     ap.add_argument("--pair-draft", action="store_true", help="the dense configurations with the bare LJ draft")
+    ap.add_argument("--no-list-reuse", action="store_true",
+                    help="staged windows rebuild their Verlet lists every window")
     ap.add_argument("--stages", type=int, default=-1,
                     help="steps per verification stage (0: one pass; default: per configuration, WINDOW_STAGES)")
-    ap.add_argument("--train-rounds", type=int, default=3, help="online retrainings of the learned draft before timing")
+    ap.add_argument("--train-rounds", type=int, default=16, help="online retrainings of the learned draft before timing")
     ap.add_argument("--train-every", type=int, default=200, help="accepted steps between retrainings before timing")
     ap.add_argument("--train-iters", type=int, default=40)
     ap.add_argument("--train-frames", type=int, default=128)

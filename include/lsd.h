@@ -147,6 +147,8 @@ typedef struct {
     double sum_pred_reject;     /* sum of erf(|delta|/sqrt 8) over committed steps (Eq. 6)   */
     int64_t step;               /* index of the current state                               */
     int64_t stages;             /* verification passes: one per window, or per stage run     */
+    int64_t list_builds;        /* Verlet-list builds asked for by kept lists
+                                   (lsd_set_list_reuse; 0 while it is off)                  */
 } lsd_stats;
 
 typedef struct lsd_handle lsd_handle;
@@ -322,6 +324,21 @@ LSD_API int lsd_set_pipelining(lsd_handle *h, int32_t on);
  * lsd_set_pipelining(h, 1) returns LSD_ESTATE while stages are set.
  * LSD_EINVAL for S < 0. */
 LSD_API int lsd_set_window_stages(lsd_handle *h, int32_t steps_per_stage);
+
+/* lsd_set_list_reuse: 1 keeps the Verlet candidate lists of unpipelined
+ * windows (lsd_step / lsd_enqueue_windows / lsd_window_host / lsd_draft_window)
+ * from one window to the next: a one-CTA check compares the committed
+ * positions with the lists' base and the lists are rebuilt only when some
+ * atom has moved more than half the draft's displacement bound (0.45 skin, or
+ * lsd_set_max_displacement's), or when the last draft stopped at that bound.
+ * The lists stay complete for every drafted step either way (the draft checks
+ * each step against the same base and ends the window at the bound), so
+ * the chain is the same Markov chain; the draft's FP32 sums run over the
+ * list's candidates in list order, so trajectories differ in rounding from
+ * those with lists rebuilt every window.  Default 0.  Not with pipelining:
+ * LSD_ESTATE when pipelining is on, and lsd_set_pipelining(h, 1) returns
+ * LSD_ESTATE while reuse is on. */
+LSD_API int lsd_set_list_reuse(lsd_handle *h, int32_t on);
 
 /* lsd_set_integrator: the Langevin splitting of the chain.
  *   LSD_ABOBA (default): Eq. 2; the state is (q, p) after a full ABOBA step.

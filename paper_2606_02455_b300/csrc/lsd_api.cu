@@ -135,6 +135,7 @@ struct lsd_handle {
     float4 *pf_pg = nullptr;
     unsigned long long *pf_bar = nullptr;   // its grid-barrier counter
     int stage_len = 0;        // windows verified in stages of this many steps (0: in one pass)
+    bool list_reuse = false;  // unpipelined windows keep their Verlet lists while the committed state stays close
     bool drafted = false;
     bool unbounded = false;   // target_step set to "no cap" by lsd_enqueue_*
     // learned-draft training
@@ -463,6 +464,14 @@ void enqueue_eval(lsd_handle *h, const PotHost &pot, const uint4 *fix, int Kc, f
                         h->E_mlp, F, E_out, h->st, s);
 }
 
+// Lists kept across windows (lsd_set_list_reuse): rebuilt around the
+// committed state only when some atom has moved more than half the draft's
+// displacement bound from their base, or the last draft stopped at the bound.
+void enqueue_kept_lists(lsd_handle *h, lsd_handle::WinBufs &w, cudaStream_t s) {
+    launch_verlet_check(h->q, w.vb, h->geo, 0.25f * h->vplan.move2f, h->st, s);
+    launch_verlet_build(h->vplan, h->q, h->species, h->geo, w.vb, h->st, s, nullptr, &h->st->list_rebuild);
+}
+
 // The window's Verlet lists around the base state, then the draft, into
 // window buffer b.  hdr null: from the committed state (q, p, st->step);
 // else (pipelined loop) from the base (q, p) at step hdr->base, skipped when
@@ -472,8 +481,12 @@ void enqueue_draft_buf(lsd_handle *h, int b, cudaStream_t s, WinHdr *hdr, const 
     lsd_handle::WinBufs &w = h->wb[b];
     if (!h->vplan.all_pairs) {
         if (redraft) launch_redraft_flag(h->st, hdr, s);
-        launch_verlet_build(h->vplan, q, h->species, h->geo, w.vb, h->st, s,
-                            hdr ? (redraft ? &hdr->keep : &hdr->skip) : nullptr);
+        if (!hdr && h->list_reuse) {
+            enqueue_kept_lists(h, w, s);
+        } else {
+            launch_verlet_build(h->vplan, q, h->species, h->geo, w.vb, h->st, s,
+                                hdr ? (redraft ? &hdr->keep : &hdr->skip) : nullptr);
+        }
     }
     // the speculative draft of the pipelined loop overlaps a verification: the cluster form, on a few SMs
     const bool grid = h->grid_draft && (!hdr || redraft);
@@ -502,7 +515,12 @@ void enqueue_stage(lsd_handle *h, int j0, int j1, cudaGraphConditionalHandle nex
     lsd_handle::WinBufs &w = h->wb[0];
     const size_t N = h->N;
     const int *keff = &h->st->k_eff;
-    if (j0 == 0 && !h->vplan.all_pairs) launch_verlet_build(h->vplan, h->q, h->species, h->geo, w.vb, h->st, s);
+    if (j0 == 0 && !h->vplan.all_pairs) {
+        if (h->list_reuse)
+            enqueue_kept_lists(h, w, s);
+        else
+            launch_verlet_build(h->vplan, h->q, h->species, h->geo, w.vb, h->st, s);
+    }
     launch_draft(h->grid_draft ? h->gplan : h->dplan, h->learned_small, j1, h->geo, h->draft.dev, h->coef, h->vplan,
                  w.vb, h->species, h->q, h->p, h->ec_dF, h->ec_on, h->st, w.qmid, w.pdraft, w.Fd, w.Fraw, w.fix,
                  h->w_dEdX, s, nullptr, 0, h->dsync, j0);
@@ -1081,6 +1099,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     s0.target_step = 0;
     s0.first_reject_last = -1;
     s0.spec_ema = 1.f;
+    s0.list_force = 1;   // no lists yet
     if (cudaMemcpy(h->st, &s0, sizeof(DevState), cudaMemcpyHostToDevice) != cudaSuccess) return fail(LSD_ECUDA);
     if (sys->mom) {
         if (cudaMemcpy(h->p, sys->mom, D * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -1271,6 +1290,7 @@ int lsd_get_stats(const lsd_handle *h, lsd_stats *out) {
     out->sum_pred_reject = s.sum_pred;
     out->step = s.step;
     out->stages = s.stages;
+    out->list_builds = s.list_builds;
     return LSD_OK;
 }
 
@@ -1349,6 +1369,7 @@ int lsd_set_pipelining(lsd_handle *h, int32_t on) {
     if (!h) return LSD_EINVAL;
     if (on && h->ec_on) return LSD_ESTATE;   // the speculative draft would read the cache while it is rewritten
     if (on && h->stage_len) return LSD_ESTATE;   // staged windows end on the device; a round drafts past them
+    if (on && h->list_reuse) return LSD_ESTATE;  // a round always builds the lists of the window it drafts
     TRY(wait_stream(h));
     if (on && !h->pipe_alloc) {
         const size_t N = h->N, D = 3 * N, KN = (size_t)h->K * N, KD = (size_t)h->K * D;
@@ -1619,7 +1640,8 @@ int lsd_launch_counts(const lsd_handle *h, int32_t *per_window, int32_t *per_rou
     const int transport = nb == 1 ? 1 : 2;
     const int verify = eval + (h->train.capture_on ? 1 : 0) + transport;
     const int draft = verlet + 1;
-    if (per_window) *per_window = draft + verify;
+    const int check = (lists && h->list_reuse) ? 1 : 0;   // the kept lists' verdict
+    if (per_window) *per_window = check + draft + verify;
     // verify; spec_base; speculative draft; redraft (with its flag kernel in list mode)
     if (per_round) *per_round = verify + 1 + draft + (lists ? 1 : 0) + draft;
     if (per_plain) *per_plain = use_plain_fused(h) ? 0 : verlet + 1 + eval + 1;
@@ -1634,7 +1656,17 @@ int lsd_stage_launch_counts(const lsd_handle *h, int32_t *first, int32_t *later)
     const bool one_cell = h->vplan.nc[0] < 3 || h->vplan.nc[1] < 3 || h->vplan.nc[2] < 3;
     const int verlet = lists ? (one_cell ? 2 : 4) : 0;
     if (first) *first = w;
-    if (later) *later = h->stage_len ? w - verlet : 0;   // a stage past the first rebuilds no lists
+    const int check = (lists && h->list_reuse) ? 1 : 0;
+    if (later) *later = h->stage_len ? w - verlet - check : 0;   // a stage past the first rebuilds no lists
+    return LSD_OK;
+}
+
+int lsd_set_list_reuse(lsd_handle *h, int32_t on) {
+    if (!h) return LSD_EINVAL;
+    if (on && h->pipe_on) return LSD_ESTATE;
+    TRY(wait_stream(h));
+    if (h->list_reuse != (on != 0)) destroy_graphs(h);
+    h->list_reuse = on != 0;
     return LSD_OK;
 }
 

@@ -96,6 +96,10 @@ struct DevState {
     unsigned grid_count, grid_gen;   // the transport's grid barrier: arrivals of this generation, generation
     long long windows, committed, rejected, verified;
     long long stages;                // verification passes (one per window, or one per stage run)
+    // lists kept across windows (lsd_set_list_reuse): the draft stopped at the displacement bound (rebuild before
+    // the next window), this window's verdict, and the number of list builds the verdicts asked for
+    int list_force, list_rebuild;
+    long long list_builds;
     double sum_delta, sum_pred;
     // the pipelined loop's speculation policy (lsd_draft.cu; results do not depend on it): a running mean of
     // "the last committed window had no rejection", and whether the next round skips its speculative draft

@@ -66,8 +66,14 @@ struct VerletBufs {
     int *vlist = nullptr;        // [N][cap] sorted candidate atom indices
     int *vcount = nullptr;       // [N]
 };
+// skip (device, may be null): nonzero skips the build; rebuild (device, may be
+// null): zero skips it (the verdict of launch_verlet_check)
 void launch_verlet_build(const VerletPlan &vp, const double *q, const int *species, const Geo &g, VerletBufs &b,
-                         DevState *st, cudaStream_t s, const int *skip = nullptr);
+                         DevState *st, cudaStream_t s, const int *skip = nullptr, const int *rebuild = nullptr);
+// lists kept across windows: st->list_rebuild = some atom of q lies more than
+// sqrt(keep2f) from the lists' base, or st->list_force (then cleared)
+void launch_verlet_check(const double *q, const VerletBufs &b, const Geo &g, float keep2f, DevState *st,
+                         cudaStream_t s);
 cudaError_t verlet_setup(int max_smem);
 void launch_neigh_list(const uint4 *fix, const int *vlist, const int *vcount, int vcap, int M, const Geo &g,
                        float rmax2f, float near2f, int cap_near, int cap_far, int *near_keys, int *far_keys,

@@ -172,7 +172,11 @@ __device__ void commit_atoms(const CommitShared &C, int N, const Coef &cf, const
 }
 
 // Statistics of the window and the step advance (one block, all threads).
-__device__ void commit_stats(CommitShared &C, int K, DevState *__restrict__ st, long long n0) {
+// K: the window's drafted steps (k_eff, at most Kl, the steps the launch
+// covers).  A window that committed every drafted step, none reflected, and
+// was drafted short of Kl ended at the draft's displacement bound: kept lists
+// (lsd_set_list_reuse) are rebuilt before the next window.
+__device__ void commit_stats(CommitShared &C, int K, DevState *__restrict__ st, long long n0, int Kl) {
     const int nc = C.nc;
     for (int j = threadIdx.x; j < K; j += blockDim.x) {
         const double dn = sqrt(C.d[j]);
@@ -201,6 +205,7 @@ __device__ void commit_stats(CommitShared &C, int K, DevState *__restrict__ st, 
         st->windows += 1;
         st->verified += K;
         st->stages += 1;
+        if (nc == K && !C.rej && K < Kl) st->list_force = 1;
         st->committed += nc;
         st->rejected += C.rej;
         st->sum_delta += sd;
@@ -267,7 +272,7 @@ __global__ void __launch_bounds__(kTransThreads)
     commit_atoms(C, N, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, n0, 0, N);
     __syncthreads();
     if (threadIdx.x == 0) st->blocks_done = 0u;
-    commit_stats(C, Kw, st, n0);
+    commit_stats(C, Kw, st, n0, K);
 }
 
 // A barrier over the whole grid of a cooperative launch (every block resident):
@@ -376,7 +381,7 @@ __global__ void __launch_bounds__(kTransThreads)
     const int A = (N + nblk - 1) / nblk;
     commit_atoms(C, N, cf, species, w_qmid, w_pdraft, Fd, Ft, Fraw, ec_dF, ec_on, q, p, p_obabo, n0, blk * A,
                  min(N, blk * A + A));
-    if (blk == 0) commit_stats(C, Kw, st, n0);
+    if (blk == 0) commit_stats(C, Kw, st, n0, K);
 }
 
 __global__ void __launch_bounds__(kTransThreads)
@@ -414,7 +419,7 @@ __global__ void __launch_bounds__(kTransThreads)
     if (!s_last) return;
     __threadfence();
     if (threadIdx.x == 0) st->blocks_done = 0u;
-    commit_stats(C, K, st, n0);
+    commit_stats(C, K, st, n0, Kstage);
 }
 
 void launch_transport_reduce(int K, const Geo &g, const Coef &cf, const int *species, const float *Fd,

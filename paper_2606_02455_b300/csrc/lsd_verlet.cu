@@ -17,6 +17,8 @@
 //                     for a grid narrower than 3 cells), minimum-image test,
 //                     compaction in shared memory, a bitonic sort in registers
 //                     (up to 512 candidates) and the sorted list out
+// verlet_check_kernel lists kept across windows: whether this window needs new
+//                     lists (the build kernels return at once otherwise)
 #include "lsd_common.cuh"
 #include "lsd_kernels.h"
 
@@ -26,9 +28,10 @@ __device__ __forceinline__ int cell_of(uint32_t u, int nc) { return (int)(((unsi
 
 __global__ void cell_count_kernel(const double *__restrict__ q, const int *__restrict__ species, Geo g, int3 nc,
                                   uint4 *__restrict__ fix_base, int *__restrict__ cell_of_atom,
-                                  int *__restrict__ cell_count, const int *__restrict__ skip) {
+                                  int *__restrict__ cell_count, const int *__restrict__ skip,
+                                  const int *__restrict__ rebuild) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.N || (skip && *skip)) return;
+    if (i >= g.N || (skip && *skip) || (rebuild && !*rebuild)) return;
     const uint32_t ux = fixpoint(q[3 * i], g.scale[0]), uy = fixpoint(q[3 * i + 1], g.scale[1]),
                    uz = fixpoint(q[3 * i + 2], g.scale[2]);
     fix_base[i] = make_uint4(ux, uy, uz, (unsigned)species[i]);
@@ -38,10 +41,10 @@ __global__ void cell_count_kernel(const double *__restrict__ q, const int *__res
 }
 
 __global__ void cell_scan_kernel(int ncells, int *__restrict__ cell_count, int *__restrict__ cell_start,
-                                 const int *__restrict__ skip) {
+                                 const int *__restrict__ skip, const int *__restrict__ rebuild) {
     __shared__ int warp_tot[32];
     __shared__ int carry;
-    if (skip && *skip) return;
+    if ((skip && *skip) || (rebuild && !*rebuild)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
@@ -79,9 +82,10 @@ __global__ void cell_scan_kernel(int ncells, int *__restrict__ cell_count, int *
 }
 
 __global__ void cell_fill_kernel(int N, const int *__restrict__ cell_of_atom, const int *__restrict__ cell_start,
-                                 int *__restrict__ cursor, int *__restrict__ cell_atoms, const int *__restrict__ skip) {
+                                 int *__restrict__ cursor, int *__restrict__ cell_atoms, const int *__restrict__ skip,
+                                 const int *__restrict__ rebuild) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N || (skip && *skip)) return;
+    if (i >= N || (skip && *skip) || (rebuild && !*rebuild)) return;
     const int c = cell_of_atom[i];
     cell_atoms[cell_start[c] + atomicAdd(&cursor[c], 1)] = i;
 }
@@ -132,11 +136,12 @@ __device__ __forceinline__ void sort_out(const int *buf, int n, int *out, int la
 __global__ void verlet_list_kernel(const uint4 *__restrict__ fix_base, const int *__restrict__ cell_of_atom,
                                    const int *__restrict__ cell_start, const int *__restrict__ cell_atoms, Geo g,
                                    int3 nc, float rlist2f, int cap, int cap_pow2, int *__restrict__ vlist,
-                                   int *__restrict__ vcount, DevState *st, const int *__restrict__ skip) {
+                                   int *__restrict__ vcount, DevState *st, const int *__restrict__ skip,
+                                   const int *__restrict__ rebuild) {
     extern __shared__ int sbuf[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + wib;
-    if (i >= g.N || (skip && *skip)) return;
+    if (i >= g.N || (skip && *skip) || (rebuild && !*rebuild)) return;
     int *buf = sbuf + (size_t)wib * cap_pow2;
     const uint4 fi = fix_base[i];
     const bool one_cell = nc.x < 3 || nc.y < 3 || nc.z < 3;
@@ -234,24 +239,60 @@ __global__ void verlet_list_kernel(const uint4 *__restrict__ fix_base, const int
 
 // skip (device, may be null): when it points at a nonzero flag every kernel
 // returns at once (the pipelined loop keeps an already valid draft).
+// Lists kept across windows: one CTA compares the committed positions with
+// the lists' base (the fixed point of the draft's displacement check) and
+// decides whether this window rebuilds them: when some atom has moved more
+// than sqrt(keep2f), or the last draft stopped at the displacement bound.  The
+// lists stay correct either way: the draft checks every drafted step against
+// the same base and stops at the bound.
+__global__ void verlet_check_kernel(const double *__restrict__ q, const uint4 *__restrict__ fix_base, Geo g,
+                                    float keep2f, DevState *st) {
+    bool moved = false;
+    for (int i = threadIdx.x; i < g.N; i += blockDim.x) {
+        const uint4 b = fix_base[i];
+        float d, d2;
+        int kk;
+        axis_min(b.x, fixpoint(q[3 * i], g.scale[0]), g.scale_f[0], d, kk);
+        d2 = d * d;
+        axis_min(b.y, fixpoint(q[3 * i + 1], g.scale[1]), g.scale_f[1], d, kk);
+        d2 += d * d;
+        axis_min(b.z, fixpoint(q[3 * i + 2], g.scale[2]), g.scale_f[2], d, kk);
+        d2 += d * d;
+        moved |= d2 > keep2f;
+    }
+    const int any = __syncthreads_or(moved);
+    if (threadIdx.x == 0) {
+        const int rebuild = (any || st->list_force) ? 1 : 0;
+        st->list_rebuild = rebuild;
+        st->list_force = 0;
+        st->list_builds += rebuild;
+    }
+}
+
+void launch_verlet_check(const double *q, const VerletBufs &b, const Geo &g, float keep2f, DevState *st,
+                         cudaStream_t s) {
+    verlet_check_kernel<<<1, 1024, 0, s>>>(q, b.fix_base, g, keep2f, st);
+}
+
 void launch_verlet_build(const VerletPlan &vp, const double *q, const int *species, const Geo &g, VerletBufs &b,
-                         DevState *st, cudaStream_t s, const int *skip) {
+                         DevState *st, cudaStream_t s, const int *skip, const int *rebuild) {
     const int N = g.N;
     const int3 nc = make_int3(vp.nc[0], vp.nc[1], vp.nc[2]);
     const int ncells = vp.nc[0] * vp.nc[1] * vp.nc[2];
     const bool one_cell = vp.nc[0] < 3 || vp.nc[1] < 3 || vp.nc[2] < 3;
     if (!one_cell) cudaMemsetAsync(b.cell_count, 0, (size_t)ncells * sizeof(int), s);
     cell_count_kernel<<<(N + 255) / 256, 256, 0, s>>>(q, species, g, one_cell ? make_int3(1, 1, 1) : nc, b.fix_base,
-                                                       b.cell_of_atom, one_cell ? b.cell_scratch : b.cell_count, skip);
+                                                       b.cell_of_atom, one_cell ? b.cell_scratch : b.cell_count, skip,
+                                                       rebuild);
     if (!one_cell) {
-        cell_scan_kernel<<<1, 1024, 0, s>>>(ncells, b.cell_count, b.cell_start, skip);
+        cell_scan_kernel<<<1, 1024, 0, s>>>(ncells, b.cell_count, b.cell_start, skip, rebuild);
         cell_fill_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, b.cell_of_atom, b.cell_start, b.cell_count, b.cell_atoms,
-                                                          skip);
+                                                          skip, rebuild);
     }
     const int warps = 8;
     verlet_list_kernel<<<(N + warps - 1) / warps, warps * 32, (size_t)warps * vp.cap_pow2 * sizeof(int), s>>>(
         b.fix_base, b.cell_of_atom, b.cell_start, b.cell_atoms, g, nc, vp.rlist2f, vp.cap, vp.cap_pow2, b.vlist,
-        b.vcount, st, skip);
+        b.vcount, st, skip, rebuild);
 }
 
 cudaError_t verlet_setup(int max_smem) {

@@ -35,7 +35,7 @@ SYMBOLS = ["lsd_init", "lsd_draft_window", "lsd_verify_window", "lsd_step", "lsd
            "lsd_target_mlp_static_dev", "lsd_destroy",
            "lsd_strerror", "lsd_launch_counts", "lsd_window_host", "lsd_transport_window", "lsd_get_frames",
            "lsd_set_max_displacement", "lsd_set_plain_fused", "lsd_set_grid_draft", "lsd_set_angular_moments", "lsd_get_angular_moments", "lsd_set_online_training", "lsd_online_status",
-           "lsd_set_window_stages", "lsd_stage_launch_counts"]
+           "lsd_set_window_stages", "lsd_stage_launch_counts", "lsd_set_list_reuse"]
 
 
 class LSDError(RuntimeError):
@@ -62,7 +62,7 @@ class lsd_potential(ctypes.Structure):
 class lsd_stats(ctypes.Structure):
     _fields_ = [("windows", ctypes.c_int64), ("committed", ctypes.c_int64), ("rejected", ctypes.c_int64),
                 ("verified", ctypes.c_int64), ("sum_delta", ctypes.c_double), ("sum_pred_reject", ctypes.c_double),
-                ("step", ctypes.c_int64), ("stages", ctypes.c_int64)]
+                ("step", ctypes.c_int64), ("stages", ctypes.c_int64), ("list_builds", ctypes.c_int64)]
 
 
 _L = None
@@ -304,6 +304,11 @@ class LSD:
         """Verify each window in stages of this many steps, stopping at the first rejection (0: one pass)."""
         _check(_lib().lsd_set_window_stages(self.h, int(steps_per_stage)), "lsd_set_window_stages")
 
+    def set_list_reuse(self, on=True):
+        """Keep the Verlet lists of unpipelined windows while the committed state stays within half the
+        displacement bound of their base (lsd_set_list_reuse)."""
+        _check(_lib().lsd_set_list_reuse(self.h, int(bool(on))), "lsd_set_list_reuse")
+
     SCHEMES = {"aboba": 0, "obabo": 1}
 
     def set_integrator(self, scheme):
@@ -476,7 +481,8 @@ class LSD:
 
 def _stats_dict(st):
     return dict(windows=st.windows, committed=st.committed, rejected=st.rejected, verified=st.verified,
-                sum_delta=st.sum_delta, pred_rejected=st.sum_pred_reject, step=st.step, stages=st.stages)
+                sum_delta=st.sum_delta, pred_rejected=st.sum_pred_reject, step=st.step, stages=st.stages,
+                list_builds=st.list_builds)
 
 
 def _make_target_energy():
