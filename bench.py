@@ -528,6 +528,7 @@ def measure_workload(w, args, world, rank, full):
         "committed_per_window": round(committed / max(windows, 1), 3),
         "list_builds_per_window": (round((st1["list_builds"] - st0["list_builds"]) / max(windows, 1), 3)
                                    if reuse else None),
+        "stages_per_window": round((st1["stages"] - st0["stages"]) / max(windows, 1), 3) if S else None,
         "plain_target_ns_per_day": round(plain_value, 4), "plain_ms_per_step": round(t_plain * 1e3 / n_plain, 5),
         "speedup_vs_plain": round(value / plain_value, 4),
         "l2": "flushed (256 MB write) before every timed window and once before the plain steps" if flush is not None
@@ -631,6 +632,7 @@ def run_ours(args):
         "pipelined": m["pipelined"],
         "window_stages": m["window_stages"],
         "list_builds_per_window": m["list_builds_per_window"],
+        "stages_per_window": m["stages_per_window"],
         "value_unpipelined": m["value_unpipelined"],
         "value_one_pass": m["value_one_pass"],
         "plain_ms_per_step": m["plain_ms_per_step"],

@@ -78,11 +78,14 @@ struct lsd_handle {
     bool mom_on = false;            // the target's angular features and adjoint by moments
     float *mom = nullptr;           // their per-row moments [K N][kMomRowFloats]
     DraftPlan gplan{};              // the grid form of the draft (large systems), when the device co-schedules it
+    DraftPlan dplan0{}, gplan0{};   // both as planned for windows of K steps
     bool grid_draft = false;        // windows and redrafts draft in the grid form
     DraftSync *dsync = nullptr;     // its barrier and flag words
     VerletPlan vplan{};
     VerletBufs vbufs{};
     float *w_dEdX = nullptr;
+    int *w_nbr = nullptr;   // learned draft: each atom's neighbours within its largest cutoff [N][nbr_cap], counts [N]
+    int nbr_cap = 0;
     // device state
     double *q = nullptr, *p = nullptr;
     int *species = nullptr;
@@ -492,7 +495,7 @@ void enqueue_draft_buf(lsd_handle *h, int b, cudaStream_t s, WinHdr *hdr, const 
     const bool grid = h->grid_draft && (!hdr || redraft);
     launch_draft(grid ? h->gplan : h->dplan, h->learned_small, Kd ? Kd : h->K, h->geo, h->draft.dev, h->coef, h->vplan, w.vb,
                  h->species, q, p, h->ec_dF, h->ec_on, h->st, w.qmid, w.pdraft, w.Fd, w.Fraw, w.fix, h->w_dEdX, s, hdr,
-                 redraft ? 1 : 0, h->dsync);
+                 redraft ? 1 : 0, h->dsync, 0, h->w_nbr, h->nbr_cap);
 }
 
 // Verification, frames and transport of window buffer b; keff: the window's
@@ -523,7 +526,7 @@ void enqueue_stage(lsd_handle *h, int j0, int j1, cudaGraphConditionalHandle nex
     }
     launch_draft(h->grid_draft ? h->gplan : h->dplan, h->learned_small, j1, h->geo, h->draft.dev, h->coef, h->vplan,
                  w.vb, h->species, h->q, h->p, h->ec_dF, h->ec_on, h->st, w.qmid, w.pdraft, w.Fd, w.Fraw, w.fix,
-                 h->w_dEdX, s, nullptr, 0, h->dsync, j0);
+                 h->w_dEdX, s, nullptr, 0, h->dsync, j0, h->w_nbr, h->nbr_cap);
     enqueue_eval(h, h->target, w.fix + (size_t)j0 * N, j1 - j0, h->w_Ft + (size_t)j0 * 3 * N, nullptr, s,
                  !h->vplan.all_pairs, &w.vb, keff, j0);
     if (h->train.capture_on) enqueue_frame_capture(h->train, w.qmid, h->w_Ft, j1, h->N, h->st, keff, s, j0);
@@ -955,6 +958,10 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
     }
     h->cap_near = std::min(nb_capacity(rho, rnear, 32), (27 * h->N + 31) / 32 * 32);
     h->cap_far = std::min(nb_capacity(rho, rfar, 32), (27 * h->N + 31) / 32 * 32);
+    if (h->learned_small) {
+        const double rcd = std::max(h->draft.dev.has_lj ? h->draft.p.lj_cutoff : 0.0, h->draft.p.desc_cutoff);
+        h->nbr_cap = std::min(nb_capacity(rho, rcd, 32), (27 * h->N + 31) / 32 * 32);
+    }
     // the target's angular block by moments when rows hold many neighbours: 165 monomials per neighbour instead
     // of n / 2 pair terms pay from about 40 neighbours on
     if (h->target.dev.has_mlp && h->target.dev.n_ang) {
@@ -1010,6 +1017,8 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
             }
             cudaGetLastError();
         }
+        h->dplan0 = h->dplan;
+        h->gplan0 = h->gplan;
     }
     const size_t N = h->N, D = 3 * N, KN = (size_t)K * N, KD = (size_t)K * D;
     const int dmax = std::max(h->draft.dev.d0p, h->target.dev.d0p);
@@ -1025,6 +1034,7 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         (rc = dalloc(h, &h->pair_g, KN * h->cap_near)) || (rc = dalloc(h, &h->Fpart, KN)) ||
         (rc = dalloc(h, &h->partials, (size_t)K * ((h->N + 1023) / 1024 + 600))) ||
         (rc = dalloc(h, &h->w_dEdX, N * std::max(h->draft.dev.d0p, 32))) ||
+        (rc = dalloc(h, &h->w_nbr, h->learned_small ? N * ((size_t)h->nbr_cap + 1) : 1)) ||
         (rc = dalloc(h, &h->dsync, 1)) || (rc = dalloc(h, &h->mom, h->mom_on ? KN * kMomRowFloats : 1)) ||
         (rc = dalloc(h, &h->vbufs.fix_base, N)) || (rc = dalloc(h, &h->vbufs.cell_of_atom, N)) ||
         (rc = dalloc(h, &h->vbufs.cell_count, (size_t)h->vplan.nc[0] * h->vplan.nc[1] * h->vplan.nc[2])) ||
@@ -1567,7 +1577,7 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
     CK(cudaEventRecord(t[1], st));
     launch_draft(h->grid_draft ? h->gplan : h->dplan, h->learned_small, Kp, h->geo, h->draft.dev, h->coef, h->vplan,
                  w0.vb, h->species, h->q, h->p, h->ec_dF, h->ec_on, h->st, w0.qmid, w0.pdraft, w0.Fd, w0.Fraw, w0.fix,
-                 h->w_dEdX, st, nullptr, 0, h->dsync, 0);
+                 h->w_dEdX, st, nullptr, 0, h->dsync, 0, h->w_nbr, h->nbr_cap);
     CK(cudaEventRecord(t[2], st));
     if (h->vplan.all_pairs)
         launch_neigh_build(h->w_fix, M, h->geo, h->target.rmax2f, h->target.near2f, h->cap_near, h->cap_far,
@@ -1677,6 +1687,18 @@ int lsd_set_window_stages(lsd_handle *h, int32_t steps_per_stage) {
     TRY(wait_stream(h));
     if (S != h->stage_len) destroy_graphs(h);
     h->stage_len = S;
+    // the draft's up-front noise buffer sized for its launches: S steps (or K); the cluster form only shrinks it
+    const int steps = S ? S : h->K;
+    h->gplan = h->gplan0;
+    if (h->gplan0.ok) {
+        DraftPlan g2 = h->gplan0;
+        draft_plan_noise(g2, steps);
+        if (g2.ok && draft_grid_fits(g2, h->learned_small, h->n_sm)) h->gplan = g2;
+    }
+    h->dplan = h->dplan0;
+    DraftPlan d2 = h->dplan0;
+    draft_plan_noise(d2, steps);
+    if (d2.ok && d2.smem <= h->dplan0.smem) h->dplan = d2;
     return LSD_OK;
 }
 

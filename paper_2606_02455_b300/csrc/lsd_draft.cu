@@ -146,8 +146,9 @@ __device__ __forceinline__ void draft_cutoff(float r, float inv_rc, float &fc, f
 // output weights, staged once per launch.  Returns false when some species
 // had more than kSegCap neighbours (its sum is then truncated).
 __device__ bool learned_atom_grad(const PotDev &P, const Geo &g, const FixView &fx, int i, const ListView cand, int nc,
-                                  bool minimg, float inv_rc, float *stage, float *xbuf, const float *wf,
-                                  const float *wtf, const float *wo, float *g_out) {
+                                  bool minimg, float inv_rc, float rc2_all, float *stage, float *xbuf,
+                                  const float *wf, const float *wtf, const float *wo, float *g_out, int *nbr_row,
+                                  int *nbr_count, int ccap) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const uint4 fi = fx[i];
@@ -155,6 +156,7 @@ __device__ bool learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
     int cnt[kMaxSpecies];
 #pragma unroll
     for (int s = 0; s < kMaxSpecies; ++s) cnt[s] = 0;
+    int nn = 0;   // candidates with an image within the draft's largest cutoff, in list order (the second phase's)
     // candidates four per lane in flight: their list entries and positions are loaded before any is tested
     constexpr int kB = 4;
     for (int base0 = 0; base0 < nc; base0 += 32 * kB) {
@@ -173,6 +175,7 @@ __device__ bool learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
             const int k = kq[u];
             const uint4 fk = fq[u];
             const int sk = (int)fk.w;
+            bool any = false;   // some image of k within rc_all
             if (minimg) {
                 // at most one image within the cutoff: each species' neighbours placed by one ballot
                 bool in = false;
@@ -184,6 +187,7 @@ __device__ bool learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
                     axis_min(fi.y, fk.y, g.scale_f[1], dy, kk);
                     axis_min(fi.z, fk.z, g.scale_f[2], dz, kk);
                     const float d2 = dist2_rule(dx, dy, dz);
+                    any = d2 < rc2_all;
                     in = d2 < P.desc_rc2f;
                     if (in) {
                         float dfc;
@@ -208,7 +212,8 @@ __device__ bool learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
                 float rs[8];
                 int nm = 0;
                 if (k != i)
-                    for_images(g, fi, fk, P.desc_rc2f, false, [&](float, float, float, float d2) {
+                    for_images(g, fi, fk, rc2_all, false, [&](float, float, float, float d2) {
+                        any = any || d2 < rc2_all;
                         if (d2 < P.desc_rc2f && nm < 8) rs[nm++] = d2 * rsqrtf(d2);
                     });
 #pragma unroll
@@ -232,12 +237,17 @@ __device__ bool learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
                     cnt[s] += __shfl_sync(0xffffffffu, sc, 31);
                 }
             }
+            const unsigned ma = __ballot_sync(0xffffffffu, any);
+            const int wn = nn + __popc(ma & lt);
+            if (any && wn < ccap) nbr_row[wn] = k;
+            nn += __popc(ma);
         }
     }
+    if (lane == 0) *nbr_count = nn < ccap ? nn : ccap;
     const int nr = P.n_rbf;
     for (int f = lane; f < P.d0p; f += 32) xbuf[f] = 0.f;
     __syncwarp();
-    bool ok = true;
+    bool ok = nn <= ccap;
     {
         // lanes over basis functions (8 or 16 wide), the groups of lanes over one species' neighbours, then a
         // reduction over the groups: every lane busy for n_rbf <= 8 as for 16
@@ -338,6 +348,7 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                                 const float *__restrict__ ec_dF, int ec_on, DevState *__restrict__ st,
                                 double *__restrict__ w_qmid, double *__restrict__ w_pdraft, float *__restrict__ w_Fd,
                                 float *__restrict__ w_Fraw, uint4 *__restrict__ w_fix, float *__restrict__ w_dEdX,
+                                int *__restrict__ w_nbr, int ccap,
                                 WinHdr *__restrict__ hdr, int redraft, DraftSync *__restrict__ sync, int j0) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N;
@@ -360,11 +371,11 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
     // [3] mbarriers: the two exchange barriers (staged positions, by step parity) and the exit barrier of a
     // window that gave up waiting
     uint64_t *sbar = (uint64_t *)(sflag + 2 * kMaxCluster);
-    float *snoise = (float *)(sbar + 3);   // [K][A][3] when noise_smem: the window's xi, drawn up front
+    float *snoise = (float *)(sbar + 3);   // [K - j0][A][3] when noise_smem: the launch's xi, drawn up front
     // Read-only per-atom data of owned atoms, staged once: a cluster barrier's
     // acquire leaves no global line in L1, so a per-step global read is an L2
     // round trip on the step's critical path.
-    int *sspec = (int *)(snoise + (noise_smem ? (size_t)K * A * 3 : 0));   // [A] species
+    int *sspec = (int *)(snoise + (noise_smem ? (size_t)(K - j0) * A * 3 : 0));   // [A] species
     int *svc = sspec + A;                                                  // [A] list lengths (stage_list)
     int *svl = svc + A;                                                    // [A][vcap] lists (stage_list)
     // learned draft, small systems: the radial dE/dX of every atom, [N][S n_rbf], staged once per step
@@ -666,8 +677,9 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                                              : nullptr,
                                     stage_list != 0};
                 all_in &= learned_atom_grad(P, g, fx, i, cand, use_list ? (stage_list ? svc[ii] : vcount[i]) : N,
-                                            minimg != 0, inv_rc, stage, stage + 2 * g.S * kSegCap, swf, swtf, swo,
-                                            w_dEdX + (size_t)i * P.d0p);
+                                            minimg != 0, inv_rc, rc2_all, stage, stage + 2 * g.S * kSegCap, swf, swtf,
+                                            swo, w_dEdX + (size_t)i * P.d0p, w_nbr + (size_t)i * ccap,
+                                            w_nbr + (size_t)N * ccap + i, ccap);
             }
             if (!all_in && lane == 0) atomicOr(&st->err, 1);   // a species' staged neighbours overflowed
             // dE/dx of every atom visible to every CTA
@@ -745,20 +757,24 @@ __global__ void __launch_bounds__(kDraftThreads, 1)
                     gather([&](int k) { return fx[k]; }, [&](int t) { return use_list ? lst[t] : t; });
                 }
             }
-            // (the learned draft, or general images) candidates four per lane in flight, each lane's in list order
-            for (int t0 = lane; t0 < ((!LEARNED && minimg) ? 0 : nl); t0 += 128) {
+            // (the learned draft, or general images) candidates four per lane in flight, each lane's in list order;
+            // the learned draft's are the first phase's neighbours within its largest cutoff (no lanes idle on
+            // candidates outside it during the radial adjoint)
+            const int *nrow = w_nbr + (size_t)i * ccap;
+            const int nc2 = LEARNED ? __ldcg(w_nbr + (size_t)N * ccap + i) : nl;
+            for (int t0 = lane; t0 < ((!LEARNED && minimg) ? 0 : nc2); t0 += 128) {
                 int kq[4];
                 uint4 fq[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int t = t0 + 32 * u;
-                    kq[u] = t < nl ? (use_list ? lst[t] : t) : i;
+                    kq[u] = t < nc2 ? (LEARNED ? __ldcg(nrow + t) : (use_list ? lst[t] : t)) : i;
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) fq[u] = kq[u] != i ? fx[kq[u]] : fi;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    if (t0 + 32 * u >= nl) break;
+                    if (t0 + 32 * u >= nc2) break;
                     const int k = kq[u];
                     if (k == i) continue;
                     const uint4 fk = fq[u];
@@ -950,8 +966,7 @@ DraftPlan draft_plan(int N, int K, const PotDev &P, bool learned, int vcap, bool
     while (C < max_cluster && (N + C - 1) / C > 16) C *= 2;
     pl.cluster = C;
     pl.stage_fix = 2 * (size_t)N * sizeof(uint4) <= 128 * 1024;
-    const size_t noise = (size_t)K * ((N + C - 1) / C) * 3 * sizeof(float);
-    pl.noise_smem = noise <= kNoiseSmemMax;
+    pl.noise_step_bytes = (size_t)((N + C - 1) / C) * 3 * sizeof(float);
     pl.K = K;
     pl.stage_list = vcap > 0 && (size_t)((N + C - 1) / C) * (vcap + 1) * sizeof(int) <= kListSmemMax;
     // without a cell grid the kernel lists candidates itself when the lists fit
@@ -965,8 +980,9 @@ DraftPlan draft_plan(int N, int K, const PotDev &P, bool learned, int vcap, bool
     const int S = P.n_rbf > 0 ? (P.d0 - P.n_ang) / (P.n_rbf + 1) : 0;
     const size_t dedx = (size_t)N * S * P.n_rbf;
     pl.stage_dedx = learned && dedx > 0 && dedx * sizeof(float) <= kDedxSmemMax;
-    pl.smem = draft_smem_bytes(N, C, P, learned, pl.stage_fix, pl.noise_smem ? K : 0, vcap, pl.stage_list,
-                               pl.stage_dedx ? dedx : 0);
+    pl.smem_base = draft_smem_bytes(N, C, P, learned, pl.stage_fix, 0, vcap, pl.stage_list, pl.stage_dedx ? dedx : 0);
+    pl.max_smem = max_smem;
+    draft_plan_noise(pl, K);
     pl.reg = (N + C - 1) / C <= kRegPasses * kGroups;
     pl.ok = pl.smem <= max_smem;
     return pl;
@@ -986,23 +1002,30 @@ DraftPlan draft_grid_plan(int N, int K, const PotDev &P, bool learned, int vcap,
     pl.stage_fix = false;
     pl.self_list = false;
     pl.K = K;
-    pl.noise_smem = (size_t)K * A * 3 * sizeof(float) <= kNoiseSmemMax;
+    pl.noise_step_bytes = (size_t)A * 3 * sizeof(float);
     pl.stage_list = (size_t)A * (vcap + 1) * sizeof(int) <= kListSmemMax;
     const int S = P.n_rbf > 0 ? (P.d0 - P.n_ang) / (P.n_rbf + 1) : 0;
     const size_t dedx = (size_t)N * S * P.n_rbf;
     pl.stage_dedx = learned && dedx > 0 && dedx * sizeof(float) <= kDedxSmemMax;
-    pl.smem = draft_smem_bytes(N, C, P, learned, false, pl.noise_smem ? K : 0, vcap, pl.stage_list,
-                               pl.stage_dedx ? dedx : 0);
+    pl.smem_base = draft_smem_bytes(N, C, P, learned, false, 0, vcap, pl.stage_list, pl.stage_dedx ? dedx : 0);
+    pl.max_smem = max_smem;
+    draft_plan_noise(pl, K);
     pl.reg = A <= kRegPasses * kGroups;
-    pl.ok = pl.smem <= max_smem;
     return pl;
+}
+
+void draft_plan_noise(DraftPlan &pl, int steps) {
+    pl.noise_steps = (size_t)steps * pl.noise_step_bytes <= kNoiseSmemMax ? steps : 0;
+    pl.smem = pl.smem_base + (size_t)pl.noise_steps * pl.noise_step_bytes;
+    pl.ok = pl.smem <= pl.max_smem;
 }
 
 cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf,
                          const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
                          const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
                          double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX,
-                         cudaStream_t s, WinHdr *hdr, int redraft, DraftSync *sync, int j0) {
+                         cudaStream_t s, WinHdr *hdr, int redraft, DraftSync *sync, int j0, int *w_nbr, int ccap) {
+    if (learned && (!w_nbr || ccap <= 0)) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(pl.cluster, 1, 1);
     cfg.blockDim = dim3(kDraftThreads, 1, 1);
@@ -1026,7 +1049,7 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
     const int stage = pl.stage_fix ? 1 : 0;
     const int *vl = vp.all_pairs ? nullptr : (const int *)vb.vlist;
     const int mi = pl.minimg ? 1 : 0;
-    const int ns = (pl.noise_smem && K <= pl.K) ? 1 : 0;
+    const int ns = (K - j0 <= pl.noise_steps) ? 1 : 0;   // this launch drafts steps j0 .. K - 1
     const int self = (pl.self_list && vp.all_pairs) ? 1 : 0;
     const int sl = (pl.stage_list && (vl || self)) ? 1 : 0;
     const int sd = (learned && pl.stage_dedx) ? 1 : 0;
@@ -1039,7 +1062,7 @@ cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g,
     const Kern kern = kerns[(pl.grid ? 4 : 0) + (learned ? 2 : 0) + (pl.reg ? 1 : 0)];
     return cudaLaunchKernelEx(&cfg, kern, K, g, P, cf, vl, (const int *)vb.vcount, vp.cap, (const uint4 *)vb.fix_base,
                               vp.move2f, vp.rlist2f, stage, mi, ns, sl, self, sd, species, q, p, ec_dF, ec_on, st, w_qmid, w_pdraft, w_Fd,
-                              w_Fraw, w_fix, w_dEdX, hdr, redraft, sync, j0);
+                              w_Fraw, w_fix, w_dEdX, w_nbr, ccap, hdr, redraft, sync, j0);
 }
 
 static const void *draft_kernel_ptrs[8] = {

@@ -144,7 +144,10 @@ struct DraftPlan {
     size_t smem;      // dynamic shared memory per CTA
     bool reg;         // owned atoms' FP64 state in registers
     bool minimg;      // every draft cutoff below 0.499 of every box side: minimum images only
-    bool noise_smem;  // the window's noise drawn up front into shared memory
+    int noise_steps;  // a launch that drafts at most this many steps draws their noise up front into shared memory
+    size_t smem_base; // the shared memory without that noise buffer, and the buffer's bytes per step
+    size_t noise_step_bytes;
+    size_t max_smem;
     bool stage_list;  // owned atoms' Verlet lists copied to shared memory once per launch
     bool self_list;   // no cell grid: the kernel lists its atoms' candidates itself (in shared memory)
     bool stage_dedx;  // learned draft: every atom's radial dE/dX staged in shared memory each step
@@ -158,12 +161,18 @@ bool draft_grid_fits(const DraftPlan &pl, bool learned, int n_sm);
 DraftPlan draft_grid_plan(int N, int K, const PotDev &P, bool learned, int vcap, bool all_pairs, int n_sm,
                           size_t max_smem);
 int draft_max_cluster(size_t smem, bool learned);
+// Re-sizes a plan's up-front noise buffer for launches of `steps` drafted steps
+// (a window's K, or the stage length of windows verified in stages): the
+// buffer holds them when it fits the noise allowance, else it is dropped.
+void draft_plan_noise(DraftPlan &pl, int steps);
 cudaError_t launch_draft(const DraftPlan &pl, bool learned, int K, const Geo &g, const PotDev &P, const Coef &cf,
                          const VerletPlan &vp, const VerletBufs &vb, const int *species, const double *q,
                          const double *p, const float *ec_dF, int ec_on, DevState *st, double *w_qmid,
                          double *w_pdraft, float *w_Fd, float *w_Fraw, uint4 *w_fix, float *w_dEdX,
                          cudaStream_t s, WinHdr *hdr = nullptr, int redraft = 0, DraftSync *sync = nullptr,
-                         int j0 = 0);   // K: the last step + 1 of this launch; j0 > 0 continues a window from step j0
+                         int j0 = 0,   // K: the last step + 1 of this launch; j0 > 0 continues a window from step j0
+                         // learned draft: per-step neighbour scratch [N][ccap] + counts [N]
+                         int *w_nbr = nullptr, int ccap = 0);
 // the fused plain-target step (lsd_plain.cu)
 constexpr int kPlainMaxN = 512;
 struct PlainPlan {
