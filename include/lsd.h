@@ -147,8 +147,10 @@ typedef struct {
     double sum_pred_reject;     /* sum of erf(|delta|/sqrt 8) over committed steps (Eq. 6)   */
     int64_t step;               /* index of the current state                               */
     int64_t stages;             /* verification passes: one per window, or per stage run     */
-    int64_t list_builds;        /* Verlet-list builds asked for by kept lists
-                                   (lsd_set_list_reuse; 0 while it is off)                  */
+    int64_t list_builds;        /* Verlet-list builds asked for by the kept-list check
+                                   (windows under lsd_set_list_reuse; plain target steps,
+                                   which keep their lists while the evaluated positions
+                                   stay within the displacement bound of their base)        */
 } lsd_stats;
 
 typedef struct lsd_handle lsd_handle;

@@ -563,9 +563,19 @@ void enqueue_prime(lsd_handle *h) {
     h->pipe_cur = 0;
 }
 
+// One plain target step.  Its Verlet lists are kept from step to step while
+// the evaluated (half-step) positions stay within the displacement bound of
+// their base, the draft's criterion, and rebuilt around those positions
+// otherwise: every pair within the cutoff is listed either way, and the
+// neighbour keys are sorted, so the forces do not depend on which lists hold
+// them.
 void enqueue_plain(lsd_handle *h, cudaStream_t s) {
-    if (!h->vplan.all_pairs) launch_verlet_build(h->vplan, h->q, h->species, h->geo, h->vbufs, h->st, s);
     launch_plain_half(h->geo, h->coef, h->species, h->q, h->p, h->st, h->w_qmid, h->w_fix, s);
+    if (!h->vplan.all_pairs) {
+        launch_verlet_check(h->w_qmid, h->vbufs, h->geo, h->vplan.move2f, h->st, s);
+        launch_verlet_build(h->vplan, h->w_qmid, h->species, h->geo, h->vbufs, h->st, s, nullptr,
+                            &h->st->list_rebuild);
+    }
     enqueue_eval(h, h->target, h->w_fix, 1, h->w_Ft, nullptr, s, !h->vplan.all_pairs);
     launch_plain_finish(h->geo, h->coef, h->species, h->w_qmid, h->w_Ft, h->q, h->p, h->p_obabo, h->st, s);
 }
@@ -1654,7 +1664,7 @@ int lsd_launch_counts(const lsd_handle *h, int32_t *per_window, int32_t *per_rou
     if (per_window) *per_window = check + draft + verify;
     // verify; spec_base; speculative draft; redraft (with its flag kernel in list mode)
     if (per_round) *per_round = verify + 1 + draft + (lists ? 1 : 0) + draft;
-    if (per_plain) *per_plain = use_plain_fused(h) ? 0 : verlet + 1 + eval + 1;
+    if (per_plain) *per_plain = use_plain_fused(h) ? 0 : (lists ? 1 : 0) + verlet + 1 + eval + 1;
     return LSD_OK;
 }
 

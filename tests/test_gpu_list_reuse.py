@@ -102,3 +102,25 @@ def test_list_reuse_off_by_default_and_exclusive_with_pipelining():
     with pytest.raises(lsd.LSDError):
         h.set_list_reuse(True)
     h.close()
+
+
+def test_plain_steps_keep_lists_and_their_trajectory():
+    """Plain target steps keep their Verlet lists while the half-step positions stay within the displacement bound
+    of the lists' base.  A 1e-4 A bound rebuilds them every step; the trajectory is bit for bit the same (the
+    neighbour keys are canonical, so the forces do not depend on which complete lists hold them), with far fewer
+    builds under the default bound."""
+    from paper_2606_02455_b300 import lsd
+    w = W.config4()
+    out = []
+    for d_max in (0.0, 1e-4):
+        h = lsd.LSD(w.system, w.draft, w.target, w.integ)
+        if d_max:
+            h.set_max_displacement(d_max)
+        h.plain_step(60)
+        q, p, step = h.get_state()
+        out.append((q, p, step, h.stats()["list_builds"]))
+        h.close()
+    (qa, pa, sa, ba), (qb, pb, sb, bb) = out
+    assert sa == sb == 60
+    assert np.array_equal(qa, qb) and np.array_equal(pa, pb)
+    assert bb == 60 and 1 <= ba < 20
