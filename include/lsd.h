@@ -342,6 +342,18 @@ LSD_API int lsd_set_window_stages(lsd_handle *h, int32_t steps_per_stage);
  * LSD_ESTATE while reuse is on. */
 LSD_API int lsd_set_list_reuse(lsd_handle *h, int32_t on);
 
+/* lsd_set_list_skin / lsd_get_list_skin: the skin of the Verlet candidate
+ * lists (list radius = the largest cutoff + skin; the draft ends a window when
+ * an atom leaves 0.45 skin of the lists' base).  The handle plans it from the
+ * lightest species' thermal speed over a window of K steps (1 to 2.5 A), and
+ * sizes the lists' capacity and cells for that skin: a smaller skin (fewer
+ * candidates per atom, lists rebuilt more often; suited to windows verified in
+ * stages, which rarely draft K steps) may be set, a larger one gives
+ * LSD_EINVAL.  The next windows' and plain steps' lists use it.
+ * LSD_EUNSUPPORTED without cell-grid lists; lsd_get_list_skin returns 0 then. */
+LSD_API int lsd_set_list_skin(lsd_handle *h, double skin);
+LSD_API int lsd_get_list_skin(const lsd_handle *h, double *skin);
+
 /* lsd_set_integrator: the Langevin splitting of the chain.
  *   LSD_ABOBA (default): Eq. 2; the state is (q, p) after a full ABOBA step.
  *   LSD_OBABO: App. E.  The chain runs in the staggered frame, whose transition

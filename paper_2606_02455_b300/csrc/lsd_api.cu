@@ -123,6 +123,8 @@ struct lsd_handle {
     cudaEvent_t ev_sync = nullptr;   // wait_stream's event, created once
     cudaGraphExec_t g_round[2] = {nullptr, nullptr};
     float move2f_list = 0.f;   // (0.45 skin)^2: the largest displacement the lists stay complete for
+    float move2f_user = 0.f;   // lsd_set_max_displacement's bound squared (0: none)
+    double list_rcut = 0.0, list_skin0 = 0.0, list_skin = 0.0;   // the lists' cutoff, planned and current skin
     // online retraining of a learned draft (lsd_set_online_training)
     long long online_every = 0;        // accepted steps between retrainings (0: off)
     int online_iters = 0, online_fpi = 0;
@@ -994,6 +996,8 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         const double v1 = std::sqrt(kB * T * kap / mmin);
         const double skin = std::min(2.5, std::max(1.0, 5.0 * v1 * K * dt));
         const double rlist = rfar + skin;
+        h->list_rcut = rfar;
+        h->list_skin0 = h->list_skin = skin;
         VerletPlan &vp = h->vplan;
         for (int a = 0; a < 3; ++a) vp.nc[a] = std::max(1, (int)std::floor(h->box[a] / rlist));
         vp.all_pairs = vp.nc[0] < 3 || vp.nc[1] < 3 || vp.nc[2] < 3;
@@ -1444,9 +1448,28 @@ int lsd_set_max_displacement(lsd_handle *h, double d_max) {
     if (!h || !(d_max >= 0.0)) return LSD_EINVAL;
     if (h->vplan.all_pairs && !h->dplan.self_list) return LSD_EUNSUPPORTED;   // no lists: no displacement check
     TRY(wait_stream(h));
-    const float m2 = d_max == 0.0 ? h->move2f_list : (float)(d_max * d_max);
-    h->vplan.move2f = std::min(m2, h->move2f_list);
+    h->move2f_user = d_max == 0.0 ? 0.f : (float)(d_max * d_max);
+    h->vplan.move2f = h->move2f_user > 0.f ? std::min(h->move2f_user, h->move2f_list) : h->move2f_list;
     destroy_graphs(h);   // the bound is a launch argument of the draft
+    return LSD_OK;
+}
+
+int lsd_set_list_skin(lsd_handle *h, double skin) {
+    if (!h || !(skin > 0.0) || skin > h->list_skin0) return LSD_EINVAL;
+    if (h->vplan.all_pairs) return LSD_EUNSUPPORTED;   // no cell-grid lists
+    TRY(wait_stream(h));
+    const double rlist = h->list_rcut + skin;
+    h->list_skin = skin;
+    h->vplan.rlist2f = (float)(rlist * rlist);
+    h->move2f_list = (float)((0.45 * skin) * (0.45 * skin));
+    h->vplan.move2f = h->move2f_user > 0.f ? std::min(h->move2f_user, h->move2f_list) : h->move2f_list;
+    destroy_graphs(h);   // the list radius and the bound are launch arguments
+    return LSD_OK;
+}
+
+int lsd_get_list_skin(const lsd_handle *h, double *skin) {
+    if (!h || !skin) return LSD_EINVAL;
+    *skin = h->vplan.all_pairs ? 0.0 : h->list_skin;
     return LSD_OK;
 }
 

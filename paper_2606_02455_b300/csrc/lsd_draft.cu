@@ -179,7 +179,7 @@ __device__ bool learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
             if (minimg) {
                 // at most one image within the cutoff: each species' neighbours placed by one ballot
                 bool in = false;
-                float r = 0.f, fc = 0.f;
+                float r = 0.f;
                 if (k != i) {
                     float dx, dy, dz;
                     int kk;
@@ -189,11 +189,7 @@ __device__ bool learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
                     const float d2 = dist2_rule(dx, dy, dz);
                     any = d2 < rc2_all;
                     in = d2 < P.desc_rc2f;
-                    if (in) {
-                        float dfc;
-                        r = d2 * rsqrtf(d2);
-                        draft_cutoff(r, inv_rc, fc, dfc);
-                    }
+                    if (in) r = d2 * rsqrtf(d2);
                 }
 #pragma unroll
                 for (int s = 0; s < kMaxSpecies; ++s) {
@@ -201,10 +197,7 @@ __device__ bool learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
                     const bool mine = in && sk == s;
                     const unsigned m = __ballot_sync(0xffffffffu, mine);
                     const int w = cnt[s] + __popc(m & lt);
-                    if (mine && w < kSegCap) {
-                        stage[(2 * s) * kSegCap + w] = r;
-                        stage[(2 * s + 1) * kSegCap + w] = fc;
-                    }
+                    if (mine && w < kSegCap) stage[(2 * s) * kSegCap + w] = r;
                     cnt[s] += __popc(m);
                 }
             } else {
@@ -228,12 +221,7 @@ __device__ bool learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
                     }
                     int w = cnt[s] + sc - mine;
                     for (int c = 0; c < mine; ++c, ++w)
-                        if (w < kSegCap) {
-                            float fc, dfc;
-                            draft_cutoff(rs[c], inv_rc, fc, dfc);
-                            stage[(2 * s) * kSegCap + w] = rs[c];
-                            stage[(2 * s + 1) * kSegCap + w] = fc;
-                        }
+                        if (w < kSegCap) stage[(2 * s) * kSegCap + w] = rs[c];
                     cnt[s] += __shfl_sync(0xffffffffu, sc, 31);
                 }
             }
@@ -246,6 +234,19 @@ __device__ bool learned_atom_grad(const PotDev &P, const Geo &g, const FixView &
     if (lane == 0) *nbr_count = nn < ccap ? nn : ccap;
     const int nr = P.n_rbf;
     for (int f = lane; f < P.d0p; f += 32) xbuf[f] = 0.f;
+    __syncwarp();
+    // the cutoff function of every staged neighbour, lanes over neighbours (in the scan above most lanes of a
+    // candidate chunk lie outside the cutoff)
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s) {
+        if (s >= S) break;
+        const int n = cnt[s] < kSegCap ? cnt[s] : kSegCap;
+        for (int p = lane; p < n; p += 32) {
+            float fc, dfc;
+            draft_cutoff(stage[(2 * s) * kSegCap + p], inv_rc, fc, dfc);
+            stage[(2 * s + 1) * kSegCap + p] = fc;
+        }
+    }
     __syncwarp();
     bool ok = nn <= ccap;
     {

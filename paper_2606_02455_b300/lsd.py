@@ -35,7 +35,8 @@ SYMBOLS = ["lsd_init", "lsd_draft_window", "lsd_verify_window", "lsd_step", "lsd
            "lsd_target_mlp_static_dev", "lsd_destroy",
            "lsd_strerror", "lsd_launch_counts", "lsd_window_host", "lsd_transport_window", "lsd_get_frames",
            "lsd_set_max_displacement", "lsd_set_plain_fused", "lsd_set_grid_draft", "lsd_set_angular_moments", "lsd_get_angular_moments", "lsd_set_online_training", "lsd_online_status",
-           "lsd_set_window_stages", "lsd_stage_launch_counts", "lsd_set_list_reuse"]
+           "lsd_set_window_stages", "lsd_stage_launch_counts", "lsd_set_list_reuse",
+           "lsd_set_list_skin", "lsd_get_list_skin"]
 
 
 class LSDError(RuntimeError):
@@ -117,6 +118,11 @@ def _lib():
             "lsd_get_angular_moments": [P, ctypes.POINTER(ctypes.c_int32)],
             "lsd_set_online_training": [P, I64, I32, ctypes.c_float, I32],
             "lsd_online_status": [P, P, P],
+            "lsd_set_window_stages": [P, I32],
+            "lsd_stage_launch_counts": [P, P, P],
+            "lsd_set_list_reuse": [P, I32],
+            "lsd_set_list_skin": [P, D],
+            "lsd_get_list_skin": [P, P],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -308,6 +314,15 @@ class LSD:
         """Keep the Verlet lists of unpipelined windows while the committed state stays within half the
         displacement bound of their base (lsd_set_list_reuse)."""
         _check(_lib().lsd_set_list_reuse(self.h, int(bool(on))), "lsd_set_list_reuse")
+
+    def set_list_skin(self, skin):
+        """The Verlet lists' skin in Angstrom, at most the planned one (lsd_set_list_skin)."""
+        _check(_lib().lsd_set_list_skin(self.h, ctypes.c_double(skin)), "lsd_set_list_skin")
+
+    def list_skin(self):
+        v = ctypes.c_double()
+        _check(_lib().lsd_get_list_skin(self.h, ctypes.byref(v)), "lsd_get_list_skin")
+        return v.value
 
     SCHEMES = {"aboba": 0, "obabo": 1}
 

@@ -124,3 +124,20 @@ def test_plain_steps_keep_lists_and_their_trajectory():
     assert sa == sb == 60
     assert np.array_equal(qa, qb) and np.array_equal(pa, pb)
     assert bb == 60 and 1 <= ba < 20
+
+
+def test_list_skin_can_shrink_only():
+    """A smaller Verlet skin (the lists' capacity and cells stay those of the planned one): the run still commits
+    every requested step with kept lists; a larger skin than planned is refused."""
+    from paper_2606_02455_b300 import lsd
+    w = W.config4()
+    h = _handle(w, stages=8)
+    skin0 = h.list_skin()
+    assert skin0 >= 1.0
+    with pytest.raises(lsd.LSDError):
+        h.set_list_skin(skin0 + 0.5)
+    h.set_list_skin(0.8)
+    assert h.list_skin() == 0.8
+    st = h.step(120)
+    h.close()
+    assert st["committed"] == 120 and st["list_builds"] >= 1
