@@ -714,10 +714,10 @@ def oracle_slice_rate(w, threads, rows_target, rows_draft, seed=0):
     window = t_v * N / rows_target + K * t_d * N / rows_draft
     rate = K * w.integ.dt * NS_PER_DAY / window
     desc = ("slice of one window of %s: target energy/forces of centre atoms [0, %d) of %d in all %d configurations "
-            "(%.2f s on %d threads) and LJ draft of centre atoms [0, %d) of one configuration (%.2f s); one window "
+            "(%.2f s on %d threads) and %s draft of centre atoms [0, %d) of one configuration (%.2f s); one window "
             "extrapolated to %.0f s (verification x %.0f, draft x %d x %.0f), every drafted step counted as committed "
-            "(upper bound)" % (w.name, rows_target, N, K, t_v, threads, rows_draft, t_d, window, N / rows_target, K,
-                               N / rows_draft))
+            "(upper bound)" % (w.name, rows_target, N, K, t_v, threads, _draft_label(w), rows_draft, t_d, window,
+                               N / rows_target, K, N / rows_draft))
     return rate, t_v + t_d, desc
 
 

@@ -329,7 +329,7 @@ LSD_API int lsd_set_window_stages(lsd_handle *h, int32_t steps_per_stage);
 
 /* lsd_set_list_reuse: 1 keeps the Verlet candidate lists of unpipelined
  * windows (lsd_step / lsd_enqueue_windows / lsd_window_host / lsd_draft_window)
- * from one window to the next: a one-CTA check compares the committed
+ * from one window to the next: a check kernel compares the committed
  * positions with the lists' base and the lists are rebuilt only when some
  * atom has moved more than half the draft's displacement bound (0.45 skin, or
  * lsd_set_max_displacement's), or when the last draft stopped at that bound.

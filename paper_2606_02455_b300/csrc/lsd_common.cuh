@@ -98,7 +98,8 @@ struct DevState {
     long long stages;                // verification passes (one per window, or one per stage run)
     // lists kept across windows (lsd_set_list_reuse): the draft stopped at the displacement bound (rebuild before
     // the next window), this window's verdict, and the number of list builds the verdicts asked for
-    int list_force, list_rebuild;
+    int list_force, list_rebuild, list_moved;
+    unsigned list_done;   // blocks of the check kernel that finished (its last block resets it)
     long long list_builds;
     double sum_delta, sum_pred;
     // the pipelined loop's speculation policy (lsd_draft.cu; results do not depend on it): a running mean of

@@ -239,16 +239,19 @@ __global__ void verlet_list_kernel(const uint4 *__restrict__ fix_base, const int
 
 // skip (device, may be null): when it points at a nonzero flag every kernel
 // returns at once (the pipelined loop keeps an already valid draft).
-// Lists kept across windows: one CTA compares the committed positions with
-// the lists' base (the fixed point of the draft's displacement check) and
-// decides whether this window rebuilds them: when some atom has moved more
-// than sqrt(keep2f), or the last draft stopped at the displacement bound.  The
-// lists stay correct either way: the draft checks every drafted step against
-// the same base and stops at the bound.
+// Lists kept across windows (and plain steps): the blocks compare positions
+// with the lists' base (the fixed point of the draft's displacement check) and
+// the last block to finish decides whether the lists are rebuilt: when some
+// atom has moved more than sqrt(keep2f), or the last window ended at the
+// draft's displacement bound (list_force).  The lists stay correct either way:
+// the draft checks every drafted step against the same base and stops at the
+// bound.
 __global__ void verlet_check_kernel(const double *__restrict__ q, const uint4 *__restrict__ fix_base, Geo g,
                                     float keep2f, DevState *st) {
+    __shared__ bool s_last;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool moved = false;
-    for (int i = threadIdx.x; i < g.N; i += blockDim.x) {
+    if (i < g.N) {
         const uint4 b = fix_base[i];
         float d, d2;
         int kk;
@@ -258,20 +261,29 @@ __global__ void verlet_check_kernel(const double *__restrict__ q, const uint4 *_
         d2 += d * d;
         axis_min(b.z, fixpoint(q[3 * i + 2], g.scale[2]), g.scale_f[2], d, kk);
         d2 += d * d;
-        moved |= d2 > keep2f;
+        moved = d2 > keep2f;
     }
     const int any = __syncthreads_or(moved);
     if (threadIdx.x == 0) {
-        const int rebuild = (any || st->list_force) ? 1 : 0;
+        if (any) atomicOr(&st->list_moved, 1);
+        __threadfence();
+        s_last = atomicAdd(&st->list_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        const int rebuild = (atomicOr(&st->list_moved, 0) || st->list_force) ? 1 : 0;
         st->list_rebuild = rebuild;
+        st->list_moved = 0;
         st->list_force = 0;
+        st->list_done = 0u;
         st->list_builds += rebuild;
     }
 }
 
 void launch_verlet_check(const double *q, const VerletBufs &b, const Geo &g, float keep2f, DevState *st,
                          cudaStream_t s) {
-    verlet_check_kernel<<<1, 1024, 0, s>>>(q, b.fix_base, g, keep2f, st);
+    verlet_check_kernel<<<(g.N + 255) / 256, 256, 0, s>>>(q, b.fix_base, g, keep2f, st);
 }
 
 void launch_verlet_build(const VerletPlan &vp, const double *q, const int *species, const Geo &g, VerletBufs &b,

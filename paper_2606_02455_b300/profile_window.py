@@ -8,7 +8,9 @@ optionally runs `equil` plain target steps, then `windows` windows through lsd_e
 stream, prints the per-phase CUDA-event times of one more window (lsd_profile_window) and the run's counters, and
 then runs `plain` plain target steps in one call.  --learned drafts with the learned draft (LJ + MLP on radial
 basis functions, untrained weights: the kernels' cost does not depend on them); --stages S verifies the windows in
-stages of S steps (lsd_set_window_stages; the profiled window is then one stage long).
+stages of S steps (lsd_set_window_stages; the profiled window is then one stage long).  Windows verified in
+stages run as graphs with conditional nodes, whose kernel nodes ncu does not profile; --windows 0 --profiles N
+issues N stage-shaped windows kernel by kernel instead (the shape the bench's roofline pass times).
 The first kernels a handle launches are its set-up (the FP8 and FP32-split calibration runs the MLP once on N
 rows); window kernels follow.
 """
@@ -30,6 +32,8 @@ def main() -> None:
     ap.add_argument("--plain", type=int, default=0, help="plain target steps after the windows (one call)")
     ap.add_argument("--learned", action="store_true", help="the learned draft instead of the configuration's")
     ap.add_argument("--stages", type=int, default=0, help="steps per verification stage (0: one pass)")
+    ap.add_argument("--profiles", type=int, default=1,
+                    help="profiled windows (lsd_profile_window: kernels issued one by one, no graph)")
     a = ap.parse_args()
     w = W.CONFIGS[a.config](a.K) if a.K else W.CONFIGS[a.config]()
     draft = W.learned_draft(w.target, w.system.n_species) if a.learned else w.draft
@@ -38,9 +42,11 @@ def main() -> None:
         h.plain_step(a.equil)
     h.set_pipelining(a.pipelined)
     h.set_window_stages(a.stages)
-    h.enqueue_windows(a.windows)
+    if a.windows:
+        h.enqueue_windows(a.windows)
     st = h.stats()
-    ph = h.profile_window()
+    for _ in range(a.profiles):
+        ph = h.profile_window()
     if a.plain:
         h.plain_step(a.plain)
     print(json.dumps({"workload": w.name, "windows": st["windows"], "committed": st["committed"],
