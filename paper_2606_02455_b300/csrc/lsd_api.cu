@@ -140,6 +140,7 @@ struct lsd_handle {
     float4 *pf_pg = nullptr;
     unsigned long long *pf_bar = nullptr;   // its grid-barrier counter
     int stage_len = 0;        // windows verified in stages of this many steps (0: in one pass)
+    bool pdl_graphs = true;   // the captured graphs' kernels overlap their predecessors' tails (small systems)
     bool list_reuse = false;  // unpipelined windows keep their Verlet lists while the committed state stays close
     bool drafted = false;
     bool unbounded = false;   // target_step set to "no cap" by lsd_enqueue_*
@@ -606,7 +607,16 @@ void destroy_graphs(lsd_handle *h) {
     h->pipe_primed = false;   // a later pipelined run drafts its first window afresh
 }
 
+// Sets whether the launches captured into a graph are programmatic dependent
+// launches (the handle's choice), for the scope of one capture.
+struct PdlScope {
+    int saved;
+    explicit PdlScope(const lsd_handle *h) : saved(pdl_current()) { pdl_current() = h->pdl_graphs ? 1 : 0; }
+    ~PdlScope() { pdl_current() = saved; }
+};
+
 int build_graph(lsd_handle *h, void (*fn)(lsd_handle *, cudaStream_t), cudaGraphExec_t *out) {
+    PdlScope pdl(h);
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     fn(h, h->stream);
@@ -623,6 +633,7 @@ void window_fn(lsd_handle *h, cudaStream_t s) {
 }
 
 int build_round_graph(lsd_handle *h, int b, cudaGraphExec_t *out) {
+    PdlScope pdl(h);
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     enqueue_round(h, b);
@@ -637,6 +648,7 @@ int build_round_graph(lsd_handle *h, int b, cudaGraphExec_t *out) {
 // then stage s in the body of an IF node that follows stage s - 1's transport
 // (nested: each handle belongs to the graph whose kernel sets it).
 int build_staged_graph(lsd_handle *h, cudaGraphExec_t *out) {
+    PdlScope pdl(h);
     const int K = h->K, S = h->stage_len, n_stages = (K + S - 1) / S;
     cudaGraph_t top = nullptr;
     CK(cudaGraphCreate(&top, 0));
@@ -1033,6 +1045,9 @@ int lsd_init(const lsd_system *sys, const lsd_potential *draft, const lsd_potent
         }
         h->dplan0 = h->dplan;
         h->gplan0 = h->gplan;
+        // programmatic dependent launches pay in launch-bound windows and cost about a tenth of the window
+        // where kernels fill the GPU (4,096 and 32,768 atoms, measured)
+        h->pdl_graphs = h->N < kGridDraftMinAtoms;
     }
     const size_t N = h->N, D = 3 * N, KN = (size_t)K * N, KD = (size_t)K * D;
     const int dmax = std::max(h->draft.dev.d0p, h->target.dev.d0p);

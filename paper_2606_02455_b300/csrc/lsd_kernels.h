@@ -1,5 +1,6 @@
 // lsd_kernels.h -- host-side launchers of the kernels of liblsd.so (internal).
 #pragma once
+#include <cstdlib>
 
 #include <cuda_runtime.h>
 
@@ -12,6 +13,23 @@ namespace lsd {
 // Launches kern as a programmatic dependent of the stream's previous kernel
 // (its launch overlaps that kernel's tail).  Only for kernels that call
 // pdl_wait() before touching memory an earlier kernel writes.
+// Whether launch_dependent (and the cooperative transport) use programmatic
+// dependent launches: the launch of the moment (a handle sets it while it
+// captures its graphs), unless the environment fixes it (LSD_PDL=0 or 1, read
+// once per process, for comparisons).
+inline int &pdl_current() {
+    static int on = 1;
+    return on;
+}
+inline int pdl_env() {
+    static const int v = [] {
+        const char *e = std::getenv("LSD_PDL");
+        return (e && (e[0] == '0' || e[0] == '1')) ? e[0] - '0' : -1;
+    }();
+    return v;
+}
+inline bool pdl_enabled() { return pdl_env() >= 0 ? pdl_env() != 0 : pdl_current() != 0; }
+
 template <typename... KArgs, typename... Args>
 inline void launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                              Args &&...args) {
@@ -24,7 +42,7 @@ inline void launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block, size
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
     cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 

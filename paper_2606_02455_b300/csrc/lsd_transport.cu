@@ -470,12 +470,12 @@ void launch_transport(int K, const Geo &g, const Coef &cf, const int *species, c
         cfg.blockDim = dim3(kTransThreads);
         cfg.stream = s;
         cudaLaunchAttribute at[2];
-        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        at[0].val.programmaticStreamSerializationAllowed = 1;
-        at[1].id = cudaLaunchAttributeCooperative;
-        at[1].val.cooperative = 1;
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[1].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
-        cfg.numAttrs = 2;
+        cfg.numAttrs = pdl_enabled() ? 2 : 1;
         cudaLaunchKernelEx(&cfg, transport_coop_kernel, K, g, cf, species, Fd, Ft, st, partials, keff, apb, w_qmid,
                            w_pdraft, Fraw, ec_dF, ec_on, q, p, p_obabo, j0, staged, next);
         return;
