@@ -175,18 +175,21 @@ def _lj_pairs_per_atom(w, q):
     return tot / N
 
 
-# DRAM bytes (read + write) of one launch, from one ncu capture of the kernel as it is now (the summaries under
-# profiles/ give the command); a kernel changed since its capture has no entry here.
-NCU_TRAFFIC = {
-    # desc_mom_kernel: 501,708,288 B per launch on the 32,768-atom workload shortened to K = 8 (262,144 rows; the
-    # moments written, 1,344 B per row, and the staged geometry scale with rows: a K = 64 launch moves 8x that);
-    # 199,167,744 B on the 4,096-atom workload (131,072 rows)
-    ("fp8_mlp_32768atoms_K64", "descriptors"): 8 * 501708288,
-    ("bf16_mlp_4096atoms_K32", "descriptors"): 199167744,
-    # pairgrad_mom_kernel: 873,477,120 B per launch at K = 8 (the moments read back, the pair gradients written),
-    # 8x for K = 64; 368,440,576 B on the 4,096-atom workload
-    ("fp8_mlp_32768atoms_K64", "pair_grad"): 8 * 873477120,
-    ("bf16_mlp_4096atoms_K32", "pair_grad"): 368440576,
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from ncu captures of the kernels as they
+# are now (the summaries under profiles/ give the commands); a kernel changed since its capture has no entry here.
+# Per verified row for the kernels whose traffic grows with the rows (scaled to the profiled launch's K N rows):
+NCU_TRAFFIC_PER_ROW = {
+    # desc_mom_kernel: 501,708,288 B per launch of 262,144 rows (the 32,768-atom workload shortened to K = 8: the
+    # moments written, 1,344 B per row, and the staged geometry); 199,167,744 B per 131,072 rows at 4,096 atoms
+    ("fp8_mlp_32768atoms_K64", "descriptors"): 501708288 / 262144,
+    ("bf16_mlp_4096atoms_K32", "descriptors"): 199167744 / 131072,
+    # pairgrad_mom_kernel: the moments read back, the pair gradients written
+    ("fp8_mlp_32768atoms_K64", "pair_grad"): 873477120 / 262144,
+    ("bf16_mlp_4096atoms_K32", "pair_grad"): 368440576 / 131072,
+}
+# Per launch of a given number of drafted steps (the draft kernel: its lists and weights are read once per launch,
+# so its traffic does not grow with the steps): (workload, phase, steps per launch) -> bytes
+NCU_TRAFFIC_PER_LAUNCH = {
 }
 
 
@@ -331,7 +334,9 @@ def roofline(h, w, peaks, peak_kind, q, n_rep=20, Kp=None):
     amount, unit, bound, detail = work
     sec = phases[dom] * 1e-3
     out.update(detail)
-    traffic = NCU_TRAFFIC.get((w.name, dom))
+    per_row = NCU_TRAFFIC_PER_ROW.get((w.name, dom))
+    traffic = (round(per_row * Kp * w.system.n_atoms) if per_row is not None
+               else NCU_TRAFFIC_PER_LAUNCH.get((w.name, dom, Kp)))
     if bound == "alu":
         ach = amount / sec / 1e12
         out.update({"bound": "alu", "achieved": round(ach, 4), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
