@@ -190,6 +190,9 @@ NCU_TRAFFIC_PER_ROW = {
 # Per launch of a given number of drafted steps (the draft kernel: its lists and weights are read once per launch,
 # so its traffic does not grow with the steps): (workload, phase, steps per launch) -> bytes
 NCU_TRAFFIC_PER_LAUNCH = {
+    # the learned grid draft, 2 drafted steps at 32,768 atoms (a stage of the staged windows): 37,615,360 B read
+    # (lists, positions, first-layer weights), 941,568 B written
+    ("fp8_mlp_32768atoms_K64", "draft", 2): 37615360 + 941568,
 }
 
 
