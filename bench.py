@@ -52,7 +52,7 @@ LEARNED_ONLINE = {4: 0, 5: 10000}   # configuration -> retraining cadence (accep
 # configuration -> steps per verification stage of the timed windows (lsd_set_window_stages: the next stage runs
 # only while every step so far was accepted), from a sweep of S on a B300; the other configurations verify their
 # windows in one pass, pipelined
-WINDOW_STAGES = {4: 4, 5: 2}
+WINDOW_STAGES = {4: 4, 5: 1}
 
 
 def _workload(cfg, pair_draft=False):
@@ -193,6 +193,8 @@ NCU_TRAFFIC_PER_LAUNCH = {
     # the learned grid draft, 2 drafted steps at 32,768 atoms (a stage of the staged windows): 37,615,360 B read
     # (lists, positions, first-layer weights), 941,568 B written
     ("fp8_mlp_32768atoms_K64", "draft", 2): 37615360 + 941568,
+    # one drafted step (stages of 1 step): 37,255,168 B read, 339,712 B written
+    ("fp8_mlp_32768atoms_K64", "draft", 1): 37255168 + 339712,
 }
 
 

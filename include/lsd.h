@@ -474,7 +474,7 @@ LSD_API int lsd_restore(lsd_handle *h, const void *buf, size_t len);
  * 0 draft window, 1 neighbour lists, 2 descriptors, 3 MLP forward+backward,
  * 4 pair gradients + LJ, 5 force gather, 6 transport reduction,
  * 7 accept/reflect/commit, 8 the window's Verlet lists (built before the
- * draft; 0 without lists).  With window stages set (lsd_set_window_stages),
+ * draft, or checked and kept under lsd_set_list_reuse; 0 without lists).  With window stages set (lsd_set_window_stages),
  * the window profiled has the stage length S, the launch shape of a stage
  * (S drafted steps, S N verified rows).  Synchronises the stream. */
 #define LSD_N_PHASES 9

@@ -1621,7 +1621,12 @@ int lsd_profile_window(lsd_handle *h, double *ms, int32_t n_phases) {
     CK(cudaEventRecord(t[0], st));
     h->pipe_primed = false;
     lsd_handle::WinBufs &w0 = h->wb[0];
-    if (!h->vplan.all_pairs) launch_verlet_build(h->vplan, h->q, h->species, h->geo, w0.vb, h->st, st);
+    if (!h->vplan.all_pairs) {   // as the handle's windows do: kept lists are rebuilt only when they must be
+        if (h->list_reuse)
+            enqueue_kept_lists(h, w0, st);
+        else
+            launch_verlet_build(h->vplan, h->q, h->species, h->geo, w0.vb, h->st, st);
+    }
     CK(cudaEventRecord(t[1], st));
     launch_draft(h->grid_draft ? h->gplan : h->dplan, h->learned_small, Kp, h->geo, h->draft.dev, h->coef, h->vplan,
                  w0.vb, h->species, h->q, h->p, h->ec_dF, h->ec_on, h->st, w0.qmid, w0.pdraft, w0.Fd, w0.Fraw, w0.fix,
