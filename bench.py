@@ -295,7 +295,7 @@ def _algorithmic_work(w, phase, q, moments=False, K=None):
     return None
 
 
-def _analysis(st1, st0, rl, K, t_plain_step, Kp=None):
+def _analysis(st1, st0, rl, K, t_plain_step, Kp=None, S=None):
     """The paper's bounds at the measured operating point (paper_2606_02455_b300.analysis): per-step rejection
     rate <beta> = rejections / tested steps (every committed step was tested, in order; steps after a window's
     first rejection are flushed untested), cost ratio c = drafted-step time / plain-step time, the pipelined
@@ -306,10 +306,16 @@ def _analysis(st1, st0, rl, K, t_plain_step, Kp=None):
     ph = rl["phases_ms"]
     t_draft = ph["draft"] * 1e-3 / (Kp or K)   # the profiled window drafts Kp steps (a stage of a staged window)
     c = t_draft / t_plain_step
-    return {"beta": round(beta, 5), "c": round(c, 5),
-            "speedup_async_bound": round(float(A.speedup_async(beta, c)), 3),
-            "speedup_sync_bound_K": round(float(A.speedup_sync(beta, c, K)), 3),
-            "expected_committed_per_window": round(float(A.expected_committed(beta, K)), 3)}
+    out = {"beta": round(beta, 5), "c": round(c, 5),
+           "speedup_async_bound": round(float(A.speedup_async(beta, c)), 3),
+           "speedup_sync_bound_K": round(float(A.speedup_sync(beta, c, K)), 3),
+           "expected_committed_per_window": round(float(A.expected_committed(beta, K)), 3)}
+    if S:
+        # windows verified in stages: the i.i.d.-rejection model's stages and verified steps per window, beside the
+        # measured ones (stages_per_window)
+        out["expected_stages_per_window"] = round(A.expected_stages(beta, K, S), 3)
+        out["expected_verified_per_window"] = round(A.expected_verified(beta, K, S), 3)
+    return out
 
 
 def roofline(h, w, peaks, peak_kind, q, n_rep=20, Kp=None):
@@ -635,7 +641,7 @@ def run_ours(args):
                    "l2": m["l2"]},
         "acceptance_rate": m["acceptance_rate"],
         "analysis": _analysis(st1, st0, m["roofline"], K, m["t_plain"] / m["n_plain"],
-                              m["roofline"]["window_steps_profiled"]),
+                              m["roofline"]["window_steps_profiled"], m["window_stages"]),
         "committed_per_window": m["committed_per_window"],
         "plain_target_ns_per_day": m["plain_target_ns_per_day"],
         "speedup_vs_plain": m["speedup_vs_plain"],

@@ -11,7 +11,11 @@ implementation runs:
 - the one-GPU synchronous window of this implementation, in which the K target evaluations of a window are one
   batched launch instead of K parallel target models: a window of K steps commits (1 - a^K) / (1 - a) steps on
   average (the accepted prefix plus the reflected step) and costs K t_draft + t_verify(K), so the throughput
-  against plain target Langevin is F_window(K) = t_plain (1 - a^K) / ((1 - a)(K t_draft + t_verify(K))).
+  against plain target Langevin is F_window(K) = t_plain (1 - a^K) / ((1 - a)(K t_draft + t_verify(K)));
+- the same window verified in stages of S steps (the next stage runs only while every step so far was accepted):
+  stage s runs with probability a^(s S) and drafts and verifies min(S, K - s S) steps, so a window runs
+  sum_s a^(s S) stages and verifies sum_s a^(s S) min(S, K - s S) steps on average, and commits as many steps as
+  the one-pass window.
 """
 from __future__ import annotations
 
@@ -125,3 +129,43 @@ def summarize(beta: float, costs: WindowCosts, K: int) -> Dict[str, float]:
         "best_K_window_model": kb,
         "speedup_at_best_K": sb,
     }
+
+
+def expected_stages(beta, K: int, S: int) -> float:
+    """Mean number of stages a window of K steps verified in stages of S runs, with i.i.d. rejections at rate <beta>:
+    stage s (0-based) runs when the s S steps before it were all accepted, with probability a^(s S)."""
+    a = 1.0 - float(beta)
+    S = min(int(S), int(K))
+    return float(sum(a ** (s * S) for s in range(-(-int(K) // S))))
+
+
+def expected_verified(beta, K: int, S: int) -> float:
+    """Mean number of steps such a window drafts and verifies: sum_s a^(s S) min(S, K - s S).  S = 1 gives the
+    expected committed steps (no step past the first rejection is verified); S >= K gives K."""
+    a = 1.0 - float(beta)
+    S = min(int(S), int(K))
+    return float(sum(a ** (s * S) * min(S, int(K) - s * S) for s in range(-(-int(K) // S))))
+
+
+@dataclass
+class StageCosts:
+    """Costs of the staged window: per drafted and verified step (draft step plus one verified configuration), per
+    stage (its launches' fixed part) and per window (lists, the first stage's extras); t_plain per plain step."""
+    per_step: float
+    per_stage: float
+    per_window: float
+    t_plain: float
+
+
+def speedup_staged(beta, costs: StageCosts, K: int, S: int) -> float:
+    """Throughput of staged windows against plain target Langevin: expected committed steps per expected window
+    time, times t_plain."""
+    t = (costs.per_window + expected_stages(beta, K, S) * costs.per_stage +
+         expected_verified(beta, K, S) * costs.per_step)
+    return float(expected_committed(beta, K)) * costs.t_plain / t
+
+
+def best_stage_length(beta, costs: StageCosts, K: int) -> Tuple[int, float]:
+    """The stage length S in 1..K with the largest predicted speedup, and that speedup."""
+    best = max(((speedup_staged(beta, costs, K, S), S) for S in range(1, int(K) + 1)))
+    return best[1], best[0]

@@ -86,3 +86,26 @@ def test_t11_scaling_law_report():
     pred = float(A.predict_beta(eps, n2, 100.0, 2.0, 300.0))
     print("T11: <beta> measured %.4f at N=%d, %.4f at N=%d; Eq. 9 predicts %.4f" % (b1, n1, b2, n2, pred))
     assert 0.0 <= b1 <= 1.0 and 0.0 <= b2 <= 1.0 and 0.0 < pred < 1.0
+
+
+def test_staged_window_model_against_bernoulli_windows_and_limits():
+    """Windows verified in stages: the mean stages run and steps verified against simulated Bernoulli windows; S = 1
+    verifies exactly the committed steps, S >= K is the one-pass window (and the staged cost model then reduces to
+    the one-pass window model)."""
+    rng = np.random.default_rng(1)
+    for beta, K, S in ((0.2, 64, 2), (0.05, 32, 4), (0.5, 16, 3), (0.0, 8, 3)):
+        rej = rng.random((200000, K)) < beta
+        first = np.where(rej.any(axis=1), rej.argmax(axis=1) + 1, K)       # committed steps
+        n_st = -(-first // S)                                              # the stage holding the last committed step
+        verified = np.minimum(n_st * S, K)
+        assert A.expected_stages(beta, K, S) == pytest.approx(n_st.mean(), rel=5e-3, abs=5e-3)
+        assert A.expected_verified(beta, K, S) == pytest.approx(verified.mean(), rel=5e-3, abs=5e-3)
+        assert A.expected_verified(beta, K, 1) == pytest.approx(float(A.expected_committed(beta, K)))
+        assert A.expected_stages(beta, K, K) == 1.0 and A.expected_verified(beta, K, K + 5) == K
+    one = A.WindowCosts(t_draft=0.2, verify_fixed=0.3, verify_per_step=0.5, t_plain=0.55)
+    staged = A.StageCosts(per_step=0.7, per_stage=0.1, per_window=0.2, t_plain=0.55)
+    assert A.speedup_staged(0.2, staged, 64, 64) == pytest.approx(float(A.speedup_window(0.2, one, 64)))
+    S, sp = A.best_stage_length(0.2, staged, 64)
+    assert 1 <= S < 64 and sp > A.speedup_staged(0.2, staged, 64, 64)
+    # a free stage makes S = 1 optimal: no step past the first rejection is paid for
+    assert A.best_stage_length(0.2, A.StageCosts(0.7, 0.0, 0.2, 0.55), 64)[0] == 1
